@@ -1,0 +1,517 @@
+"""Pins of the FP64 oracle against what arXiv 2311.05646 and geometry fix.
+
+No test here compares the oracle with itself or retypes one of its formulas:
+each check uses an independent algorithm (polygon clipping, lattice
+supersampling, brute-force finite differences), a closed form printed in the
+paper, the paper's truth table, or an invariant of the mathematics.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2311_05646_gb300 import inputs as I
+
+from . import _geom as G
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+def _grid2d(nx, ny, h=1.0, off=(0.5, 0.5, 0.0), logic="product", eps=(1.0, 2.0)):
+    return I.Design((nx, ny, 1), (h, h, h), ncomp=1, off=[list(off)], eps_bg=eps[0],
+                    eps_fg=eps[1], logic=logic)
+
+
+def _centres(desc):
+    g = desc["grid"]
+    nx, ny, nz = g["n"]
+    off = g["off"][0]
+    xs = g["o"][0] + (np.arange(nx) + off[0]) * g["d"][0]
+    ys = g["o"][1] + (np.arange(ny) + off[1]) * g["d"][1]
+    return xs, ys
+
+
+# ---------------------------------------------------------------- P1 --------
+def test_p1_box_exact_on_lattice_supersampling(oracle_mod):
+    """Cuboid fill equals the exact volume average (Sec. 5.1, zero-error claim
+    of Sec. 5.2).  Edges on a 1/16-cell lattice make 16-point-per-axis midpoint
+    supersampling exact, an algorithm independent of the overlap formula."""
+    O = oracle_mod
+    rng = np.random.default_rng(1)
+    for trial in range(20):
+        D = I.Design((7, 5, 4), (1.0, 1.0, 1.0), ncomp=3)
+        lo = rng.integers(0, 48, size=3) / 16.0
+        ext = rng.integers(1, 64, size=3) / 16.0
+        D.box(x=(lo[0], lo[0] + ext[0]), y=(lo[1], lo[1] + ext[1]), z=(lo[2], lo[2] + ext[2]))
+        desc = D.to_desc()
+        f = O.fill(desc)
+        N = 16
+        sub = (np.arange(N) + 0.5) / N - 0.5
+        for c in range(3):
+            off = desc["grid"]["off"][c]
+            for k in range(4):
+                for j in range(5):
+                    for i in range(7):
+                        cx, cy, cz = i + off[0], j + off[1], k + off[2]
+                        ix = ((cx + sub >= lo[0]) & (cx + sub <= lo[0] + ext[0])).mean()
+                        iy = ((cy + sub >= lo[1]) & (cy + sub <= lo[1] + ext[1])).mean()
+                        iz = ((cz + sub >= lo[2]) & (cz + sub <= lo[2] + ext[2])).mean()
+                        assert abs(f[c, k, j, i] - ix * iy * iz) <= 1e-14
+
+
+def test_p1_box_exact_by_clipping_random_edges(oracle_mod):
+    """2D cuboids with arbitrary edges against exact square clipping."""
+    O = oracle_mod
+    rng = np.random.default_rng(2)
+    for trial in range(30):
+        h = float(rng.uniform(0.5, 2.0))
+        D = _grid2d(9, 7, h)
+        x0, y0 = rng.uniform(0, 4 * h), rng.uniform(0, 3 * h)
+        x1, y1 = x0 + rng.uniform(0.1, 5) * h, y0 + rng.uniform(0.1, 4) * h
+        D.box(x=(x0, x1), y=(y0, y1))
+        desc = D.to_desc()
+        f = O.fill(desc)[0, 0]
+        xs, ys = _centres(desc)
+        rect = [(x0, y0), (x1, y0), (x1, y1), (x0, y1)]
+        for j, cy in enumerate(ys):
+            for i, cx in enumerate(xs):
+                assert abs(f[j, i] - G.cell_fraction(rect, cx, cy, h)) <= 1e-12
+
+
+def test_p1_supersampling_converges_first_order(oracle_mod):
+    """Quadrature with N sub-samples converges to the oracle's fill as O(1/N)
+    (Sec. 5.2: exact averaging is the many-sample limit)."""
+    O = oracle_mod
+    D = _grid2d(6, 6)
+    D.box(x=(1.2345, 4.6789), y=(0.777, 3.3333))
+    desc = D.to_desc()
+    f = O.fill(desc)[0, 0]
+    xs, ys = _centres(desc)
+    errs = []
+    for N in (8, 32, 128, 512):
+        sub = (np.arange(N) + 0.5) / N - 0.5
+        e = 0.0
+        for j, cy in enumerate(ys):
+            for i, cx in enumerate(xs):
+                ix = ((cx + sub >= 1.2345) & (cx + sub <= 4.6789)).mean()
+                iy = ((cy + sub >= 0.777) & (cy + sub <= 3.3333)).mean()
+                e = max(e, abs(ix * iy - f[j, i]))
+        errs.append(e)
+        assert e <= 2.0 / N
+    assert errs[-1] < errs[0] / 16
+
+
+# ---------------------------------------------------------------- P2 --------
+def test_p2_linear_sigma_rect_is_eq_linear(oracle_mod):
+    """Paper-form Rect1D with linear sigma and k = 1/dx reproduces Eq. linear,
+    a_o = x/dx + 1/2 for an axis-parallel edge, x the signed distance."""
+    O = oracle_mod
+    h = 0.08
+    for a in (0.0123, 0.1, 0.2777, 0.333):
+        D = _grid2d(12, 1, h)
+        D.box(x=(a, 10.0), mode="sigma", sigma="linear", kr=1.0)
+        desc = D.to_desc()
+        f = O.fill(desc)[0, 0, 0]
+        xs, _ = _centres(desc)
+        for i, cx in enumerate(xs):
+            x = cx - a
+            if -0.5 <= x / h <= 0.5:
+                assert abs(f[i] - (x / h + 0.5)) <= 1e-13
+            else:
+                assert f[i] == (1.0 if x > 0 else 0.0)
+
+
+def test_p2_rect_forms_agree_for_wide_boxes_and_differ_for_thin(oracle_mod):
+    """The sigma-product Rect and the exact overlap agree whenever the box is
+    at least one cell wide; a 0.2-cell bar centred in a cell gives 0.36 vs 0.2."""
+    O = oracle_mod
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        D1, D2 = _grid2d(10, 8), _grid2d(10, 8)
+        x0, y0 = rng.uniform(0, 4), rng.uniform(0, 3)
+        x1, y1 = x0 + rng.uniform(1.0, 5), y0 + rng.uniform(1.0, 4)
+        D1.box(x=(x0, x1), y=(y0, y1), mode="exact")
+        D2.box(x=(x0, x1), y=(y0, y1), mode="sigma", sigma="linear", kr=1.0)
+        assert np.abs(O.fill(D1.to_desc()) - O.fill(D2.to_desc())).max() <= 1e-13
+    D1, D2 = _grid2d(3, 1), _grid2d(3, 1)
+    D1.box(x=(1.4, 1.6), mode="exact")
+    D2.box(x=(1.4, 1.6), mode="sigma", sigma="linear", kr=1.0)
+    assert abs(O.fill(D1.to_desc())[0, 0, 0, 1] - 0.2) < 1e-12
+    assert abs(O.fill(D2.to_desc())[0, 0, 0, 1] - 0.36) < 1e-12
+
+
+# ---------------------------------------------------------------- P3 --------
+def _diamond(R, cx=0.0, cy=0.0):
+    return [(cx + R, cy), (cx, cy + R), (cx - R, cy), (cx, cy - R)]
+
+
+def _edges_cutting(poly, cx, cy, h):
+    """How many polygon edge lines cross a cell that the polygon partly covers
+    (brute force: sign change of each edge's line function over the cell's
+    corners; 0 for cells the polygon misses or covers)."""
+    sq = G.square(cx, cy, h)
+    a = G.cell_fraction(poly, cx, cy, h)
+    if not (0.0 < a < 1.0):
+        return 0
+    n = 0
+    for i in range(len(poly)):
+        p, q = np.array(poly[i]), np.array(poly[(i + 1) % len(poly)])
+        e = q - p
+        vals = [e[0] * (y - p[1]) - e[1] * (x - p[0]) for x, y in sq]
+        if min(vals) < 0 < max(vals):
+            n += 1
+    return n
+
+
+def test_p3_quadratic_sigma_exact_for_45_degree_edges(oracle_mod):
+    """Quadratic sigma with k = 1/dx gives the exact area of a cell cut by one
+    45-degree edge (Eq. quadratic; Sec. 5.2).  Checked against clipping."""
+    O = oracle_mod
+    h = 0.08
+    R = 0.61
+    D = _grid2d(24, 24, h, logic="product")
+    D.grid["o"] = (-12 * h, -12 * h, 0.0)
+    verts = _diamond(R, 0.0123, -0.0071)
+    D.polygon(verts, sigma="quadratic", kr=1.0)
+    desc = D.to_desc()
+    f = O.fill(desc)[0, 0]
+    xs, ys = _centres(desc)
+    checked = 0
+    for j, cy in enumerate(ys):
+        for i, cx in enumerate(xs):
+            if _edges_cutting(verts, cx, cy, h) == 1:
+                assert abs(f[j, i] - G.cell_fraction(verts, cx, cy, h)) <= 1e-12
+                checked += 1
+    assert checked > 20
+
+
+def test_p3_linear_sigma_axis_aligned_polygon_is_exact(oracle_mod):
+    """An axis-aligned rectangle as a Poly2D with linear sigma, k = 1/dx: the
+    product of edge factors is the exact area in every cell (Eq. linear)."""
+    O = oracle_mod
+    h = 0.5
+    D = _grid2d(14, 12, h)
+    rect = [(1.13, 0.87), (5.41, 0.87), (5.41, 4.02), (1.13, 4.02)]
+    D.polygon(rect, sigma="linear", kr=1.0)
+    desc = D.to_desc()
+    f = O.fill(desc)[0, 0]
+    xs, ys = _centres(desc)
+    for j, cy in enumerate(ys):
+        for i, cx in enumerate(xs):
+            assert abs(f[j, i] - G.cell_fraction(rect, cx, cy, h)) <= 1e-12
+
+
+# ---------------------------------------------------------------- P4 --------
+def _dfill_dp(O, desc, flat_cell):
+    G_ = np.zeros(I.field_shape(desc), dtype=np.float32)
+    G_.reshape(-1)[flat_cell] = 1.0
+    g = O.grad_real(desc, G_)
+    return g / (desc["eps_fg"] - desc["eps_bg"])
+
+
+def test_p4_edge_derivative_eq_dlinear(oracle_mod):
+    """d a_o / dx = 1/dx for an axis-parallel edge (Eq. dlinear)."""
+    O = oracle_mod
+    h = 0.25
+    D = _grid2d(8, 1, h)
+    p = D.param(0.93)
+    D.box(x=(I.P(p), 5.0))
+    desc = D.to_desc()
+    # the cell whose window [i h, (i+1) h] contains 0.93 is i = 3
+    d = _dfill_dp(O, desc, 3)
+    assert abs(d[0] - (-1.0 / h)) <= 1e-12  # moving the left edge right removes material
+    for i in (0, 1, 2, 4, 5):
+        assert _dfill_dp(O, desc, i)[0] == 0.0
+
+
+def test_p4_45_degree_derivative_eq_dquadratic(oracle_mod):
+    """Translating a 45-degree edge: d fill / dt equals Eq. dquadratic times the
+    normal's x component, and the numerical derivative of the clipped area."""
+    O = oracle_mod
+    h = 0.08
+    D = _grid2d(24, 24, h)
+    D.grid["o"] = (-12 * h, -12 * h, 0.0)
+    t = D.param(0.0)
+    R = 0.61
+    base = _diamond(R, 0.0123, -0.0071)
+    D.polygon([(I.P(t, vx), vy) for vx, vy in base], sigma="quadratic", kr=1.0)
+    desc = D.to_desc()
+    xs, ys = _centres(desc)
+    checked = 0
+    for j, cy in enumerate(ys):
+        for i, cx in enumerate(xs):
+            if _edges_cutting(base, cx, cy, h) != 1:
+                continue
+            # the one edge: find its inward unit normal and signed distance
+            best = None
+            for e in range(4):
+                p, q = np.array(base[e]), np.array(base[(e + 1) % 4])
+                ev = q - p
+                n_in = np.array([-ev[1], ev[0]]) / np.linalg.norm(ev)  # ccw diamond
+                dist = n_in @ (np.array([cx, cy]) - p)
+                if best is None or abs(dist) < abs(best[1]):
+                    best = (n_in, dist)
+            n_in, x = best
+            if abs(x / h) < 1e-6:
+                continue
+            dq = (math.sqrt(2) * h + 2 * x) / h ** 2 if x < 0 else (math.sqrt(2) * h - 2 * x) / h ** 2
+            expect = dq * (-n_in[0])  # shifting the shape by +t moves the edge by n_x t
+            got = _dfill_dp(O, desc, j * 24 + i)[0]
+            assert abs(got - expect) <= 1e-9 * max(1.0, abs(expect))
+            eps_ = 1e-7
+            fd = (G.cell_fraction([(vx + eps_, vy) for vx, vy in base], cx, cy, h)
+                  - G.cell_fraction([(vx - eps_, vy) for vx, vy in base], cx, cy, h)) / (2 * eps_)
+            assert abs(got - fd) <= 1e-5 * max(1.0, abs(fd))
+            checked += 1
+    assert checked > 20
+
+
+# ---------------------------------------------------------------- P5 --------
+def _truth_table():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "union_truth_table.txt")
+    rows = []
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append(tuple(int(v) for v in line.split()))
+    return rows
+
+
+@pytest.mark.parametrize("logic", ["product", "clamp"])
+def test_p5_logic_on_binary_inputs(oracle_mod, logic):
+    """On binary inputs the union reproduces logical OR (Table 'Logical union
+    truth table'), intersection AND, difference AND-NOT, in both families."""
+    O = oracle_mod
+    table = _truth_table()
+    assert len(table) == 4
+
+    def run(prog):
+        D = _grid2d(2, 2, 1.0, logic=logic)
+        a = D.box(x=(0.0, 1.0))   # cells (i=0, j=*)
+        b = D.box(y=(0.0, 1.0))   # cells (i=*, j=0)
+        D.set_program(prog(a, b))
+        return O.fill(D.to_desc())[0, 0]
+
+    fu = run(lambda a, b: ("union", a, b))
+    fi = run(lambda a, b: ("intersect", a, b))
+    fd = run(lambda a, b: ("diff", a, b))
+    for b1, b2, orv in table:
+        # (a, b) = (b1, b2) at cell i = 1 - b1, j = 1 - b2
+        i, j = 1 - b1, 1 - b2
+        assert fu[j, i] == orv
+        assert fi[j, i] == (b1 & b2)
+        assert fd[j, i] == (b1 & (1 - b2))
+
+
+def test_p5_half_half_union(oracle_mod):
+    """Two shapes sharing a boundary inside a cell (0.5, 0.5): the clamped union
+    gives 1 (Appendix B.2), the product form 0.75."""
+    O = oracle_mod
+    out = {}
+    for logic in ("product", "clamp"):
+        D = _grid2d(1, 1, 1.0, logic=logic)
+        a = D.box(x=(-1.0, 0.5))
+        b = D.box(x=(0.5, 2.0))
+        D.set_program(("union", a, b))
+        out[logic] = O.fill(D.to_desc())[0, 0, 0, 0]
+    assert out["clamp"] == 1.0
+    assert abs(out["product"] - 0.75) < 1e-15
+
+
+# ---------------------------------------------------------------- P6 --------
+KINKS = {0: [-0.5, 0.5], 1: [], 2: [-1 / math.sqrt(2), 0.0, 1 / math.sqrt(2)],
+         3: [-math.pi / 2, math.pi / 2], 4: []}
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4])
+def test_p6_sigma_table_properties(oracle_mod, kind):
+    """Table 'Nonlinear function definitions': sigma(0) = 1/2, [0,1]-bounded,
+    monotone, sigma(-u) = 1 - sigma(u), and d sigma/du equals a central
+    finite difference of sigma away from kinks."""
+    O = oracle_mod
+    assert abs(O.sigma(kind, 0.0)[0] - 0.5) < 1e-15
+    us = np.linspace(-6, 6, 2401)
+    vals = np.array([O.sigma(kind, u)[0] for u in us])
+    assert vals.min() >= 0.0 and vals.max() <= 1.0
+    assert np.all(np.diff(vals) >= -1e-15)
+    for u in us[::7]:
+        assert abs(O.sigma(kind, -u)[0] - (1.0 - O.sigma(kind, u)[0])) < 1e-14
+        if any(abs(u - k) < 1e-4 for k in KINKS[kind]):
+            continue
+        hh = 1e-6
+        fd = (O.sigma(kind, u + hh)[0] - O.sigma(kind, u - hh)[0]) / (2 * hh)
+        assert abs(O.sigma(kind, u)[1] - fd) < 1e-7
+
+
+def test_p6_sigma_saturation_points(oracle_mod):
+    """Each piecewise function reaches exactly 0 and 1 at the ends of its
+    transition (linear +-1/2, quadratic +-1/sqrt 2, sin +-pi/2)."""
+    O = oracle_mod
+    assert O.sigma(0, 0.5)[0] == 1.0 and O.sigma(0, -0.5)[0] == 0.0
+    assert abs(O.sigma(2, 1 / math.sqrt(2))[0] - 1.0) < 1e-15
+    assert abs(O.sigma(2, -1 / math.sqrt(2))[0]) < 1e-15
+    assert abs(O.sigma(3, math.pi / 2)[0] - 1.0) < 1e-15 and O.sigma(3, -math.pi / 2)[0] == 0.0
+    # the sigmoid's slope at 0 is 1/4 of the unit scale (so k/4 = 1/dx for k = 4/dx)
+    assert abs(O.sigma(1, 0.0)[1] - 0.25) < 1e-15
+
+
+# ---------------------------------------------------------------- P7 --------
+def test_p7_single_edge_gradient_closed_form(oracle_mod):
+    """For one exact-overlap edge at x = a, dL/da = -(deps/dx) * sum over the
+    cells whose window holds a of Re(w E_adj E) (Eq. 1 with Eq. dlinear)."""
+    O = oracle_mod
+    h = 20.0
+    D = I.Design((30, 12, 1), (h, h, h), ncomp=1, eps_bg=2.085, eps_fg=12.11)
+    pa = D.param(211.7)
+    D.box(x=(I.P(pa), 480.3))
+    desc = D.to_desc()
+    ef = I.plane_wave_field(desc, 1)
+    ea = I.plane_wave_field(desc, 2)
+    w = np.complex64(0.3 - 1.7j)
+    g = O.grad(desc, ef, ea, w)
+    i = int(math.floor(211.7 / h - 0.5 + 0.5))  # window [ (i) h, (i+1) h ] with offset 0.5
+    z = (w * ea[0, 0, :, i].astype(np.complex128) * ef[0, 0, :, i].astype(np.complex128)).real
+    expect = -(desc["eps_fg"] - desc["eps_bg"]) / h * z.sum()
+    assert abs(g[0] - expect) <= 1e-12 * abs(expect)
+
+
+# ---------------------------------------------------------------- P8 --------
+def _fields(desc, s1, s2, wseed=5):
+    return (I.plane_wave_field(desc, s1), I.plane_wave_field(desc, s2),
+            I.seeded_w(desc["grid"]["ncomp"], wseed))
+
+
+@pytest.mark.parametrize("case", ["grating2d", "grating3d", "taper", "random", "clamp"])
+def test_p8_analytic_gradient_matches_central_fd(oracle_mod, case):
+    """The reverse sweep (Eqs. AD/jaceps) equals brute-force central finite
+    differences of L, the paper's baseline method, at h = 1e-3 nm."""
+    O = oracle_mod
+    if case == "grating2d":
+        desc = I.grating_2d()
+    elif case == "grating3d":
+        desc = I.grating_3d(n=(48, 6, 24), teeth=3, pitch=300.0)
+    elif case == "taper":
+        desc = I.taper_3d(n=(60, 30, 12), nverts=8)
+    elif case == "random":
+        desc = I.random_design(7, n=(40, 30, 12), nprims=14)
+    else:
+        desc = I.grating_2d()
+        desc["logic"] = "clamp"
+    ef, ea, w = _fields(desc, 12, 13)
+    g = O.grad(desc, ef, ea, w)
+    gfd = O.grad_fd(desc, ef, ea, w, 1e-3)
+    err = np.linalg.norm(g - gfd)
+    assert err <= 1e-6 * np.linalg.norm(g) + 1e-9 * np.abs(g).max()
+
+
+def test_p8_fd_converges_second_order(oracle_mod):
+    """Central FD error against the analytic gradient falls as O(h^2) on a
+    smooth (sigmoid) design."""
+    O = oracle_mod
+    desc = I.taper_3d(n=(60, 30, 12), nverts=6)
+    ef, ea, w = _fields(desc, 32, 33)
+    g = O.grad(desc, ef, ea, w)
+    errs = []
+    for h in (8.0, 4.0, 2.0):
+        errs.append(np.linalg.norm(O.grad_fd(desc, ef, ea, w, h) - g))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.0 < r1 < 5.0 and 3.0 < r2 < 5.0
+
+
+# ---------------------------------------------------------------- P9 --------
+def test_p9_invariants(oracle_mod):
+    O = oracle_mod
+    desc = I.random_design(9, n=(40, 32, 16), nprims=20)
+    f = O.fill(desc)
+    assert f.min() >= 0.0 and f.max() <= 1.0
+    e = O.eps(desc)
+    assert e.min() >= desc["eps_bg"] - 1e-12 and e.max() <= desc["eps_fg"] + 1e-12
+    # translating the grid by one cell shifts the fill by one cell
+    d2 = dict(desc)
+    g = dict(desc["grid"])
+    g["o"] = (g["o"][0] - g["d"][0], g["o"][1], g["o"][2])
+    d2["grid"] = g
+    f2 = O.fill(d2)
+    assert np.abs(f2[..., 1:] - f[..., :-1]).max() <= 1e-12
+    # g is linear in w; the complex seed equals the real seed G = Re(w E_adj E)
+    ef, ea, _ = _fields(desc, 3, 4)
+    w1 = np.array([0.3 + 0.1j, -1.0 + 0.5j, 0.2 - 0.9j], dtype=np.complex64)
+    w2 = np.array([1.1 - 0.4j, 0.0 + 1.0j, -0.5 + 0.5j], dtype=np.complex64)
+    g1, g2 = O.grad(desc, ef, ea, w1), O.grad(desc, ef, ea, w2)
+    g12 = O.grad(desc, ef, ea, w1.astype(np.complex128) + w2.astype(np.complex128))
+    assert np.linalg.norm(g12 - g1 - g2) <= 1e-9 * np.linalg.norm(g12)
+    Gr = np.empty(I.field_shape(desc), dtype=np.float64)
+    for c in range(3):
+        Gr[c] = (w1[c].astype(np.complex128) * ea[c].astype(np.complex128)
+                 * ef[c].astype(np.complex128)).real
+    # the real-seed form takes float32 cotangents; compare at that precision
+    gr = O.grad_real(desc, Gr.astype(np.float32))
+    assert np.linalg.norm(gr - g1) <= 1e-5 * np.linalg.norm(g1)
+
+
+# ---------------------------------------------------------------- P10 -------
+def test_p10_topology_special_case(oracle_mod):
+    """Independent one-cell boxes (B = I): each parameter moves one box's edge
+    inside its own cell, so g_i = deps * Re(w E E_adj)_i / dx (Eq. top_AD with
+    the exact pixel map)."""
+    O = oracle_mod
+    h = 1.0
+    nx, ny = 6, 5
+    D = I.Design((nx, ny, 1), (h, h, h), ncomp=1, off=[[0.5, 0.5, 0.0]], eps_bg=1.5, eps_fg=4.0)
+    rng = np.random.default_rng(4)
+    kids = []
+    for j in range(ny):
+        for i in range(nx):
+            p = D.param(i + rng.uniform(0.2, 0.8))
+            kids.append(D.box(x=(float(i), I.P(p)), y=(float(j), float(j + 1))))
+    D.set_program(("union",) + tuple(kids))
+    desc = D.to_desc()
+    ef, ea, _ = _fields(desc, 5, 6)
+    w = np.complex64(-2j)
+    g = O.grad(desc, ef, ea, w)
+    z = (w * ea[0, 0].astype(np.complex128) * ef[0, 0].astype(np.complex128)).real
+    # PRODUCT union of disjoint boxes: other children are 0 in the cell -> factor 1
+    expect = (desc["eps_fg"] - desc["eps_bg"]) * z.reshape(-1) / h
+    assert np.abs(g - expect).max() <= 1e-12 * np.abs(expect).max()
+
+
+# ------------------------------------------------ paper fixtures (Table 4) ---
+def test_fixture_circ2d_area(oracle_mod):
+    """Circ2D example (R = 0.5 at (0, -0.5), dx = 0.08): the grid sum of a
+    symmetric sigmoid edge integrates to pi R^2 + pi^3 / (3 k^2)."""
+    O = oracle_mod
+    h = 0.08
+    D = _grid2d(40, 40, h)
+    D.grid["o"] = (-1.6, -2.1, 0.0)
+    kr = 2.0
+    D.circle(0.0, -0.5, 0.5, sigma="sigmoid", kr=kr)
+    f = O.fill(D.to_desc())
+    k = kr / h
+    expect = math.pi * 0.25 + math.pi ** 3 / (3 * k * k)
+    assert abs(f.sum() * h * h - expect) <= 2e-4 * expect
+
+
+def test_fixture_poly2d_winding_independent(oracle_mod):
+    """Poly2D example vertices (-0.7,0.6), (0.7,0.5), (0,-0.5) are clockwise;
+    the inward normal reading makes the fill independent of winding, and
+    with a steep sigma the fill is 1/0 at cells well inside/outside."""
+    O = oracle_mod
+    h = 0.08
+    verts = [(-0.7, 0.6), (0.7, 0.5), (0.0, -0.5)]
+    out = []
+    for vv in (verts, verts[::-1]):
+        D = _grid2d(25, 20, h)
+        D.grid["o"] = (-1.0, -0.8, 0.0)
+        D.polygon(vv, sigma="sigmoid", kr=200.0)
+        out.append(O.fill(D.to_desc())[0, 0])
+        desc = D.to_desc()
+    assert np.abs(out[0] - out[1]).max() <= 1e-13  # edge order changes rounding only
+    xs, ys = _centres(desc)
+    for j, cy in enumerate(ys):
+        for i, cx in enumerate(xs):
+            a = G.cell_fraction(verts, cx, cy, h)
+            if a == 1.0:
+                assert out[0][j, i] > 1 - 1e-6
+            elif a == 0.0:
+                assert out[0][j, i] < 1e-6
