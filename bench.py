@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: eps(p) build + adjoint-gradient VJP.
+
+One step = one pass of the whole path over the 3D two-etch grating
+(600 x 200 x 120 Yee cells, 3 components, 60 etched boxes, 120 edge
+parameters): host FP64 parameter map, binner, eps/fill build, band VJP over
+the complex64 forward/adjoint fields, deterministic finalize.  The
+parameters change every step (as in an optimiser loop), so nothing is cached
+across steps.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.  Under torchrun each rank
+runs its own replica (the path shards across designs with no collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grid cells/s for eps(p)+VJP gradient"
+WORKLOAD = ("3D two-etch grating: Yee grid 600x200x120, Ex/Ey/Ez, dx=dy=40 nm, dz=20 nm, "
+            "220 nm slab, 2 etch depths x 30 teeth (60 exact-overlap boxes), 120 edge params, "
+            "complex64 fwd+adj fields (6 arrays, seeded plane waves x Gaussian)")
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampler (SM clock, max clock, throttle reasons) run alongside
+    the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms",
+                 "50", "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        import statistics
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def crop_z(desc, k0, nzs):
+    """The same design restricted to z-planes [k0, k0 + nzs) (for bounded CPU samples)."""
+    d = dict(desc)
+    g = dict(desc["grid"])
+    n = list(g["n"])
+    n[2] = nzs
+    g["n"] = tuple(n)
+    o = list(g["o"])
+    o[2] = o[2] + k0 * g["d"][2]
+    g["o"] = tuple(o)
+    d["grid"] = g
+    return d
+
+
+def oracle_sample(desc, ef, ea, w, target_s=12.0, max_planes=None):
+    """Time the oracle (fill + gradient, as it stands) on z-planes through the
+    slab, calibrated to about `target_s` of CPU work.  Returns (cells/s,
+    cores, description)."""
+    from oracle import oracle as O
+    nx, ny, nz = desc["grid"]["n"]
+    kc = nz // 2
+    one = crop_z(desc, kc, 1)
+    t0 = time.perf_counter()
+    O.fill(one)
+    O.grad(one, ef[:, kc:kc + 1], ea[:, kc:kc + 1], w)
+    t1 = max(time.perf_counter() - t0, 1e-3)
+    planes = int(max(1, min(nz if max_planes is None else max_planes, target_s / t1)))
+    k0 = max(0, kc - planes // 2)
+    sub = crop_z(desc, k0, planes)
+    efs, eas = ef[:, k0:k0 + planes].copy(), ea[:, k0:k0 + planes].copy()
+    t0 = time.perf_counter()
+    O.fill(sub)
+    O.grad(sub, efs, eas, w)
+    dt = time.perf_counter() - t0
+    cells = nx * ny * planes
+    return cells / dt, O.num_threads(), ("%d of %d z-planes (%d cells, %d components) through the "
+                                         "slab; one oracle fill + one oracle gradient, %.1f s"
+                                         % (planes, nz, cells, desc["grid"]["ncomp"], dt))
+
+
+def make_inputs():
+    import numpy as np
+    from paper_2311_05646_gb300 import inputs as I
+    desc = I.grating_3d()
+    ef = I.plane_wave_field(desc, 22)
+    ea = I.plane_wave_field(desc, 23)
+    w = np.full(3, -2j, dtype=np.complex64)  # Eq. 1: w = -2 i omega, omega = 1
+    return desc, ef, ea, w
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    desc, ef, ea, w = make_inputs()
+    from oracle import oracle as O
+    nx, ny, nz = desc["grid"]["n"]
+    # bounded sample per step: z-planes through the slab sized to ~2 s
+    kc = nz // 2
+    one = crop_z(desc, kc, 1)
+    t0 = time.perf_counter()
+    O.fill(one)
+    O.grad(one, ef[:, kc:kc + 1], ea[:, kc:kc + 1], w)
+    t1 = max(time.perf_counter() - t0, 1e-3)
+    planes = int(max(1, min(nz, 2.0 / t1)))
+    k0 = max(0, kc - planes // 2)
+    sub = crop_z(desc, k0, planes)
+    efs, eas = ef[:, k0:k0 + planes].copy(), ea[:, k0:k0 + planes].copy()
+    p0 = desc["params"]
+    for k in range(args.warmup):
+        O.fill(sub, p0 + 0.01 * (k % 2))
+        O.grad(sub, efs, eas, w, params=p0 + 0.01 * (k % 2))
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        O.fill(sub, p0 + 0.01 * (k % 2))
+        O.grad(sub, efs, eas, w, params=p0 + 0.01 * (k % 2))
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    cells = nx * ny * planes
+    value = cells / dt
+    sample = ("%d of %d z-planes (%d cells x 3 components) through the slab per step: one "
+              "oracle fill + one oracle gradient" % (planes, nz, cells))
+    line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": O.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_adg(args):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_2311_05646_gb300 import adg
+
+    desc, ef_h, ea_h, w = make_inputs()
+    nx, ny, nz = desc["grid"]["n"]
+    C = desc["grid"]["ncomp"]
+    cells = nx * ny * nz
+    ctx = adg.Context(local)
+    tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else None
+    design = adg.Design(ctx, desc, tile=tile)
+    efd = torch.from_numpy(ef_h).cuda()
+    ead = torch.from_numpy(ea_h).cuda()
+    fill = torch.empty(design.shape, dtype=torch.float32, device="cuda")
+    eps = torch.empty_like(fill)
+    g = torch.zeros(design.n_params, dtype=torch.float32, device="cuda")
+    p0 = desc["params"].copy()
+    params = [p0 + 0.01 * (k % 2) for k in range(2)]  # alternate: every step re-bins
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        p = params[k % 2]
+        adg.adg_build_eps(design, p, eps, fill=fill, stream=stream)
+        adg.adg_grad(design, p, efd, ead, w, g, stream=stream)
+
+    for k in range(args.warmup):
+        step(k)
+    adg.adg_sync(ctx, stream)
+
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(50):  # keep the GPU busy while the sampler starts
+        step(k)
+    torch.cuda.synchronize()
+    adg.adg_profile_read(ctx, reset=True)
+    adg.adg_profile_enable(ctx, True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.stop()
+    adg.adg_profile_enable(ctx, False)
+    prof = adg.adg_profile_read(ctx, reset=True)
+    adg.adg_sync(ctx, stream)
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    stats = adg.adg_design_stats(design, stream)
+    value = world * cells / (ms * 1e-3)
+
+    # roofline of the dominant kernel (HBM-bound): algorithmic bytes / launch
+    bytes_build = cells * C * 4 * 2  # fill + eps, fp32
+    bytes_vjp = stats["band_cells"] * C * 16  # E_fwd + E_adj complex64 in band tiles
+    kern = {"build": bytes_build, "vjp": bytes_vjp}
+    dom = max(kern, key=lambda k: prof[k][1])
+    n_l, tot_ms = prof[dom]
+    avg_ms = tot_ms / max(n_l, 1)
+    achieved = kern[dom] / (avg_ms * 1e-3) / 1e9
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        import hashlib
+        src = open(os.path.join(ROOT, "paper_2311_05646_gb300", "csrc", "adg_kernels.cu"), "rb").read()
+        if tr.get("source_sha256") == hashlib.sha256(src).hexdigest() and dom in tr.get("kernels", {}):
+            traffic = tr["kernels"][dom]["dram_bytes_per_launch"]
+    except Exception:
+        traffic = None
+    roof = {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "algorithmic_bytes_per_launch": kern[dom],
+            "peak_source": "measured" if peaks else "fallback"}
+    kernels = {k: {"launches": v[0], "ms_total": v[1],
+                   "us_per_launch": 1e3 * v[1] / max(v[0], 1)} for k, v in prof.items()}
+    for k in kern:
+        a = kern[k] / (kernels[k]["us_per_launch"] * 1e-6) / 1e9 if kernels[k]["launches"] else 0
+        kernels[k]["GBps"] = a
+        kernels[k]["frac_of_measured_hbm"] = a / peak
+    launches = sum(v[0] for v in prof.values())
+
+    # end to end through the public API: host (pinned) fields in, eps + g out
+    e2e = None
+    if not args.no_e2e:
+        efp = torch.from_numpy(ef_h).pin_memory()
+        eap = torch.from_numpy(ea_h).pin_memory()
+        eps_h = torch.empty(design.shape, dtype=torch.float32).pin_memory()
+        g_h = torch.empty(design.n_params, dtype=torch.float32).pin_memory()
+        ne = max(3, min(args.steps, 20))
+
+        def e2e_step(k):
+            efd.copy_(efp, non_blocking=True)
+            ead.copy_(eap, non_blocking=True)
+            step(k)
+            eps_h.copy_(eps, non_blocking=True)
+            g_h.copy_(g, non_blocking=True)
+
+        for k in range(2):
+            e2e_step(k)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for k in range(ne):
+            e2e_step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms_e = e0.elapsed_time(e1) / ne
+        if dist is not None:
+            t = torch.tensor([ms_e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e = float(t.item())
+        e2e = {"value": world * cells / (ms_e * 1e-3), "unit": "cells/s",
+               "h2d_bytes_per_step": int(efp.numel() * 8 * 2),
+               "d2h_bytes_per_step": int(eps_h.numel() * 4 + g_h.numel() * 4),
+               "ms_per_step": ms_e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = oracle_sample(desc, ef_h, ea_h, w)
+        cpu = {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells_per_design": cells, "components": C,
+                       "params": int(design.n_params), "parallelism": "replicas" if world > 1 else "single",
+                       "outputs": "fill + eps (fp32) + gradient",
+                       "vjp": "band tiles only (tiles crossed by an edge band)",
+                       "tile": list(stats["tile"]), "program_tiles": stats["program_tiles"],
+                       "tiles": stats["tiles"], "band_cells": stats["band_cells"],
+                       "l2": "inputs larger than L2 (fields 691 MB + outputs 346 MB per step)"},
+            "roofline": roof, "kernels": kernels, "gpu_launches": launches,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="adg", choices=["adg", "reference"])
+    ap.add_argument("--tile", default="")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_adg(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

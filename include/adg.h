@@ -1,0 +1,207 @@
+/*
+ * adg.h -- C ABI of libadg: a GB300 (sm_103a) implementation of the
+ * differentiable shape-to-material map ("AutoDiffGeo") and of the adjoint
+ * gradient sum reduction of arXiv 2311.05646 (Hooten et al.).
+ *
+ * The paper's problem statement (Sec. 2, the 7-step adjoint protocol): given
+ * shape parameters v (here `params`), compute the material distribution eps(v)
+ * (step 2) and, with the forward and adjoint fields treated as given
+ * quantities, the gradient of Eq. 1 (step 5).  libadg implements exactly those
+ * two steps; the simulators are outside its scope (Sec. 2, last paragraph).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; the library
+ *     never frees or retains them beyond the call's stream work.  Pointers
+ *     named h_* and every array inside adg_design_desc are HOST pointers; the
+ *     library copies what it needs before returning.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     All device work of a call is enqueued on it and is asynchronous.
+ *   - Every call returns adg_status; nothing throws or aborts across the ABI.
+ *     adg_last_error() returns a thread-local message for the last failure.
+ *   - Arguments are validated before any launch (ADG_EINVAL).  Device-side
+ *     checks (tile capacity) set an error word that adg_sync() reports as
+ *     ADG_EDEVICE; no kernel traps or faults on bad data.
+ *   - Layout of every per-cell array: [ncomp][nz][ny][nx], x fastest, fp32
+ *     (fields: complex64 = interleaved (re, im) fp32 pairs).
+ */
+#ifndef ADG_H
+#define ADG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ADG_OK = 0,
+  ADG_EINVAL = 1,   /* invalid argument or design description            */
+  ADG_ENOMEM = 2,   /* device or host allocation failed                  */
+  ADG_ECUDA = 3,    /* a CUDA runtime call failed                        */
+  ADG_ETIMEOUT = 4, /* a bounded wait ran out                            */
+  ADG_EBUSY = 5,    /* resource in use (e.g. batch queue full)           */
+  ADG_EDEVICE = 6   /* a device-side check tripped (see adg_last_error)  */
+} adg_status;
+
+/* ---- design description format ----------------------------------------
+ * Primitive kinds (Table "AutoDiffGeo definitions"; geometric scalars q in
+ * physical units, listed in the order the primitive reads them):
+ *   BOX      Rect1D/2D/dD: q = x0, x1, y0, y1, z0, z1; ADG_BOUND_* flags say
+ *            which axes are bounded.  Default: exact overlap of the box with
+ *            each cell's averaging window (Sec. 5.1, Eq. linear; zero error vs
+ *            volumetric averaging).  ADG_RECT_SIGMA: the paper's product
+ *            sigma_k(x - x0) sigma_k(x1 - x) per bounded axis, k = kr / d_axis.
+ *   CIRCLE   Circ2D: q = cx, cy, R, z0, z1; s = sigma_k(R - r), k = kr / dx.
+ *   POLYGON  Poly2D (convex): q = z0, z1, x1, y1, ..., xN, yN; product over edges
+ *            of sigma_k(n . (r - v_e)) with the inward normal whatever the
+ *            winding; k = kr / dx.
+ *   GRAPH    GeneralCartesian2D: q = z0, z1, X1..XM, Y1..YM; s = sigma_k(f(x) - y)
+ *            (or y - f(x) with ADG_GRAPH_ABOVE), f the piecewise-linear
+ *            interpolant through (X_j, Y_j), constant beyond the end knots;
+ *            k = kr / dy.
+ *   CIRCLE/POLYGON/GRAPH are extruded along z by the exact overlap of [z0, z1]
+ *   when ADG_BOUND_Z is set (planarity, Sec. 5.2).  CIRCLE and POLYGON need
+ *   dx == dy.
+ * Sigma kinds: Table "Nonlinear function definitions", sigma_k(x) = sigma(k x).
+ * Logic (Eqs. union/intersection, Appendix B.2):
+ *   PRODUCT: union a + b - ab, intersection ab, difference a (1 - b)
+ *   CLAMP:   union min{1, a + b}, intersection max{0, a + b - 1},
+ *            difference max{0, a - b}
+ *   n-ary operations are evaluated as left-to-right chains of binary ones
+ *   (the paper's recursive definition of union_2).
+ * Program: postfix int32 words (code << 24) | arg; PUSH arg = primitive id,
+ *   UNION/INTERSECT arg = operand count (>= 1), DIFF arg ignored (2 operands).
+ * Parameter map: q_j = q_base[j] + q_coeff[j] * params[q_param[j]], or
+ *   q_base[j] when q_param[j] = -1 (a fixed scalar).
+ */
+enum { ADG_PRIM_BOX = 0, ADG_PRIM_CIRCLE = 1, ADG_PRIM_POLYGON = 2, ADG_PRIM_GRAPH = 3 };
+enum {
+  ADG_SIGMA_LINEAR = 0,
+  ADG_SIGMA_SIGMOID = 1,
+  ADG_SIGMA_QUADRATIC = 2,
+  ADG_SIGMA_SIN = 3,
+  ADG_SIGMA_ERF = 4
+};
+enum { ADG_LOGIC_PRODUCT = 0, ADG_LOGIC_CLAMP = 1 };
+enum {
+  ADG_BOUND_X = 1,
+  ADG_BOUND_Y = 2,
+  ADG_BOUND_Z = 4,
+  ADG_RECT_SIGMA = 8,
+  ADG_GRAPH_ABOVE = 16
+};
+enum { ADG_OP_PUSH = 0, ADG_OP_UNION = 1, ADG_OP_INTERSECT = 2, ADG_OP_DIFF = 3 };
+
+/* Rectilinear grid.  Cell (i, j, k) of component c is sampled at
+ * o + ((i + off[c][0]) dx, (j + off[c][1]) dy, (k + off[c][2]) dz); its
+ * averaging window is the cell-sized box centred there.  The paper asks for
+ * eps at the Yee half-steps of each polarisation (Sec. 3) but does not fix
+ * them; the offsets are the caller's. */
+typedef struct {
+  int32_t nx, ny, nz, ncomp; /* nz = 1 for 2D; ncomp in {1, 2, 3}          */
+  double dx, dy, dz;         /* spacing                                     */
+  double ox, oy, oz;         /* origin                                      */
+  double off[3][3];          /* [component][axis] sample offset in cells    */
+} adg_grid;
+
+typedef struct {
+  adg_grid grid;
+  double eps_bg, eps_fg;     /* eps = eps_bg + (eps_fg - eps_bg) fill (Sec. 5.1) */
+  int32_t logic;             /* ADG_LOGIC_*                                 */
+  int32_t n_params;
+  int32_t n_q;
+  int32_t n_prims;
+  int32_t n_ops;
+  int32_t reserved;          /* must be 0                                   */
+  const double *q_base, *q_coeff;
+  const int32_t *q_param;
+  const int32_t *prim_kind, *prim_sigma, *prim_flags, *prim_q0, *prim_nq;
+  const double *prim_kr;
+  const int32_t *ops;
+} adg_design_desc;
+
+/* Tile shape (cells) of the binned kernels.  tx in {32, 64}, ty in
+ * {1, 2, 4, 8, 16}, tz in {1, 2, 4, 8}.  All zero = library default. */
+typedef struct {
+  int32_t tx, ty, tz;
+  int32_t reserved;
+} adg_tile_opts;
+
+/* Counters of the last binned call, for measurement (read with a sync). */
+typedef struct {
+  int64_t tiles;          /* tiles covering the grid                        */
+  int64_t program_tiles;  /* tiles where some primitive's edge band lies     */
+  int64_t cells;          /* nx * ny * nz                                   */
+  int64_t band_cells;     /* cells (per component) inside program tiles     */
+  int32_t tile[3];        /* tile shape in use                              */
+  int32_t max_ops;        /* longest folded per-tile program                */
+} adg_stats;
+
+typedef struct adg_ctx adg_ctx;       /* opaque: device, error word         */
+typedef struct adg_design adg_design; /* opaque: compiled design, scratch   */
+
+/* Create a context on CUDA device `device` (makes it current on this thread).
+ * Out: *out, owned by the caller, released by adg_ctx_destroy. */
+adg_status adg_ctx_create(int32_t device, adg_ctx **out);
+adg_status adg_ctx_destroy(adg_ctx *ctx);
+
+/* Compile a design: validates the description (primitive table, parameter map,
+ * postfix program), converts the program to its chained form and uploads the
+ * static tables.  `tiles` may be NULL.  Host arrays are copied. */
+adg_status adg_design_create(adg_ctx *ctx, const adg_design_desc *desc,
+                             const adg_tile_opts *tiles, adg_design **out);
+adg_status adg_design_destroy(adg_ctx *ctx, adg_design *design);
+
+/* Step 2 of the protocol (Sec. 2): v -> eps.  Eq. eps realised as
+ * parameter map -> primitives (sigma_k, Table 4) -> logic (Eqs. union,
+ * intersection) -> eps = eps_bg + deps * fill (Sec. 5.1).
+ * h_params: n_params host doubles.  d_fill (nullable) and d_eps: device fp32
+ * [ncomp][nz][ny][nx].  Asynchronous on `stream`. */
+adg_status adg_build_eps(adg_ctx *ctx, adg_design *design, const double *h_params,
+                         float *d_fill, float *d_eps, void *stream);
+
+/* Step 5 (Eq. 1, eps term): for every parameter k,
+ *   g_k = Re sum_c sum_cells w_c * E_adj,c * E_fwd,c * d eps_c / d p_k
+ * (no complex conjugate, as in Eq. 1; w_c = -2 i omega gives 2 omega Im(.)).
+ * Computed as the vector-Jacobian product of Eqs. AD/jaceps: the material
+ * Jacobian is never formed and fill is recomputed, not read.
+ * d_efwd[c], d_eadj[c]: device complex64 [nz][ny][nx] per component c.
+ * w: 2 * ncomp host floats (re, im per component).  d_grad: n_params device
+ * floats, overwritten.  Asynchronous on `stream`. */
+adg_status adg_grad(adg_ctx *ctx, adg_design *design, const double *h_params,
+                    const float *const d_efwd[3], const float *const d_eadj[3],
+                    const float *w, float *d_grad, void *stream);
+
+/* The same sweep seeded with a real cotangent G = dL/deps (the autograd form):
+ *   g_k = sum_c sum_cells G_c * d eps_c / d p_k.
+ * d_G: device fp32 [ncomp][nz][ny][nx]. */
+adg_status adg_grad_real(adg_ctx *ctx, adg_design *design, const double *h_params,
+                         const float *d_G, float *d_grad, void *stream);
+
+/* Wait for `stream` and report device-side errors (ADG_EDEVICE) recorded by
+ * any call of this context since the last adg_sync. */
+adg_status adg_sync(adg_ctx *ctx, void *stream);
+
+/* Counters of the design's last binning (synchronises `stream`). */
+adg_status adg_design_stats(adg_ctx *ctx, adg_design *design, void *stream, adg_stats *out);
+
+/* Per-kernel timing for measurement.  While enabled, every kernel launch of
+ * the context is bracketed by CUDA events recorded on the launching stream.
+ * adg_profile_read waits for the recorded events and returns, per kernel
+ * (index ADG_K_*), the launch count and the summed device time; `reset`
+ * clears the accumulators. */
+enum { ADG_K_BIN = 0, ADG_K_BUILD = 1, ADG_K_VJP = 2, ADG_K_FINALIZE = 3, ADG_K_COUNT = 8 };
+typedef struct {
+  int64_t launches[ADG_K_COUNT];
+  double ms[ADG_K_COUNT];
+} adg_profile_data;
+adg_status adg_profile_enable(adg_ctx *ctx, int32_t on);
+adg_status adg_profile_read(adg_ctx *ctx, adg_profile_data *out, int32_t reset);
+
+/* Thread-local description of the last error (never NULL). */
+const char *adg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADG_H */

@@ -1,0 +1,291 @@
+"""Thin ctypes binding of libadg (include/adg.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs inside libadg's
+CUDA kernels.  PyTorch supplies device memory and streams.  If libadg.so is
+missing this module raises at import of the first call -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libadg.so")
+_lock = threading.Lock()
+_lib = None
+
+ADG_OK, ADG_EINVAL, ADG_ENOMEM, ADG_ECUDA, ADG_ETIMEOUT, ADG_EBUSY, ADG_EDEVICE = range(7)
+_STATUS = {0: "ADG_OK", 1: "ADG_EINVAL", 2: "ADG_ENOMEM", 3: "ADG_ECUDA", 4: "ADG_ETIMEOUT",
+           5: "ADG_EBUSY", 6: "ADG_EDEVICE"}
+LOGIC = {"product": 0, "clamp": 1}
+
+
+class AdgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class adg_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("ncomp", ctypes.c_int32), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dz", ctypes.c_double), ("ox", ctypes.c_double), ("oy", ctypes.c_double),
+                ("oz", ctypes.c_double), ("off", (ctypes.c_double * 3) * 3)]
+
+
+class adg_design_desc(ctypes.Structure):
+    _fields_ = [("grid", adg_grid), ("eps_bg", ctypes.c_double), ("eps_fg", ctypes.c_double),
+                ("logic", ctypes.c_int32), ("n_params", ctypes.c_int32), ("n_q", ctypes.c_int32),
+                ("n_prims", ctypes.c_int32), ("n_ops", ctypes.c_int32),
+                ("reserved", ctypes.c_int32),
+                ("q_base", ctypes.c_void_p), ("q_coeff", ctypes.c_void_p),
+                ("q_param", ctypes.c_void_p), ("prim_kind", ctypes.c_void_p),
+                ("prim_sigma", ctypes.c_void_p), ("prim_flags", ctypes.c_void_p),
+                ("prim_q0", ctypes.c_void_p), ("prim_nq", ctypes.c_void_p),
+                ("prim_kr", ctypes.c_void_p), ("ops", ctypes.c_void_p)]
+
+
+class adg_tile_opts(ctypes.Structure):
+    _fields_ = [("tx", ctypes.c_int32), ("ty", ctypes.c_int32), ("tz", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+K_NAMES = {0: "bin", 1: "build", 2: "vjp", 3: "finalize"}
+
+
+class adg_profile_data(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 8), ("ms", ctypes.c_double * 8)]
+
+
+class adg_stats(ctypes.Structure):
+    _fields_ = [("tiles", ctypes.c_int64), ("program_tiles", ctypes.c_int64),
+                ("cells", ctypes.c_int64), ("band_cells", ctypes.c_int64),
+                ("tile", ctypes.c_int32 * 3), ("max_ops", ctypes.c_int32)]
+
+
+def lib():
+    """Load libadg.so (fails loudly when it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError("libadg.so not found at %s: run __graft_entry__.build() (nvcc, "
+                                  "sm_103a) first; there is no CPU fallback" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            P, I32 = ctypes.c_void_p, ctypes.c_int32
+            sig = {
+                "adg_ctx_create": [I32, ctypes.POINTER(P)],
+                "adg_ctx_destroy": [P],
+                "adg_design_create": [P, ctypes.POINTER(adg_design_desc),
+                                      ctypes.POINTER(adg_tile_opts), ctypes.POINTER(P)],
+                "adg_design_destroy": [P, P],
+                "adg_build_eps": [P, P, P, P, P, P],
+                "adg_grad": [P, P, P, P, P, P, P, P],
+                "adg_grad_real": [P, P, P, P, P, P],
+                "adg_sync": [P, P],
+                "adg_design_stats": [P, P, P, ctypes.POINTER(adg_stats)],
+                "adg_profile_enable": [P, I32],
+                "adg_profile_read": [P, ctypes.POINTER(adg_profile_data), I32],
+            }
+            for name, args in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = ctypes.c_int
+            L.adg_last_error.restype = ctypes.c_char_p
+            L.adg_last_error.argtypes = []
+            _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != ADG_OK:
+        raise AdgError(status, lib().adg_last_error().decode())
+
+
+def adg_last_error() -> str:
+    return lib().adg_last_error().decode()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dptr(t):
+    if t is None:
+        return ctypes.c_void_p(0)
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device tensors must be contiguous CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        self.handle = ctypes.c_void_p()
+        _check(lib().adg_ctx_create(int(device), ctypes.byref(self.handle)))
+        self.device = int(device)
+
+    def close(self):
+        if self.handle:
+            lib().adg_ctx_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Design:
+    """A compiled design (adg_design_create) built from a description dict."""
+
+    def __init__(self, ctx: Context, desc: dict, tile=None):
+        self.ctx = ctx
+        self.desc = desc
+        g = desc["grid"]
+        self._keep = []
+
+        def arr(x, dt):
+            a = np.ascontiguousarray(np.asarray(x, dtype=dt))
+            self._keep.append(a)
+            return a.ctypes.data_as(ctypes.c_void_p)
+
+        D = adg_design_desc()
+        D.grid.nx, D.grid.ny, D.grid.nz = (int(v) for v in g["n"])
+        D.grid.ncomp = int(g["ncomp"])
+        D.grid.dx, D.grid.dy, D.grid.dz = (float(v) for v in g["d"])
+        D.grid.ox, D.grid.oy, D.grid.oz = (float(v) for v in g["o"])
+        for c in range(int(g["ncomp"])):
+            for a in range(3):
+                D.grid.off[c][a] = float(g["off"][c][a])
+        D.eps_bg, D.eps_fg = float(desc["eps_bg"]), float(desc["eps_fg"])
+        D.logic = LOGIC[desc["logic"]]
+        D.n_params = int(len(desc["params"]))
+        D.n_q = int(len(desc["q_base"]))
+        pr = desc["prims"]
+        D.n_prims = int(len(pr["kind"]))
+        D.n_ops = int(len(desc["ops"]))
+        D.reserved = 0
+        D.q_base = arr(desc["q_base"], np.float64)
+        D.q_coeff = arr(desc["q_coeff"], np.float64)
+        D.q_param = arr(desc["q_param"], np.int32)
+        D.prim_kind = arr(pr["kind"], np.int32)
+        D.prim_sigma = arr(pr["sigma"], np.int32)
+        D.prim_flags = arr(pr["flags"], np.int32)
+        D.prim_q0 = arr(pr["q0"], np.int32)
+        D.prim_nq = arr(pr["nq"], np.int32)
+        D.prim_kr = arr(pr["kr"], np.float64)
+        D.ops = arr(desc["ops"], np.int32)
+        T = adg_tile_opts(0, 0, 0, 0)
+        if tile is not None:
+            T.tx, T.ty, T.tz = (int(v) for v in tile)
+        self.handle = ctypes.c_void_p()
+        _check(lib().adg_design_create(ctx.handle, ctypes.byref(D), ctypes.byref(T),
+                                       ctypes.byref(self.handle)))
+        self._keep = []
+        self.n_params = D.n_params
+        self.ncomp = D.grid.ncomp
+        self.shape = (D.grid.ncomp, D.grid.nz, D.grid.ny, D.grid.nx)
+
+    def close(self):
+        if self.handle:
+            lib().adg_design_destroy(self.ctx.handle, self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _params(design: Design, params):
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    if p.size != design.n_params:
+        raise ValueError("expected %d parameters, got %d" % (design.n_params, p.size))
+    return p
+
+
+def _check_cell_tensor(design, t, name, dtype):
+    import torch
+    if t.dtype != dtype or tuple(t.shape) != design.shape:
+        raise ValueError("%s must be %s of shape %s, got %s %s" % (name, dtype, design.shape,
+                                                                    t.dtype, tuple(t.shape)))
+    del torch
+
+
+def adg_build_eps(design: Design, params, eps, fill=None, stream=None):
+    """eps (and fill, if given) <- the material map at `params` (Eq. eps)."""
+    import torch
+    p = _params(design, params)
+    _check_cell_tensor(design, eps, "eps", torch.float32)
+    if fill is not None:
+        _check_cell_tensor(design, fill, "fill", torch.float32)
+    _check(lib().adg_build_eps(design.ctx.handle, design.handle,
+                               p.ctypes.data_as(ctypes.c_void_p), _dptr(fill), _dptr(eps),
+                               _stream_ptr(stream)))
+
+
+def adg_grad(design: Design, params, efwd, eadj, w, grad, stream=None):
+    """grad <- Re sum w_c E_adj,c E_fwd,c d eps_c / d p (Eq. 1, eps term)."""
+    import torch
+    p = _params(design, params)
+    _check_cell_tensor(design, efwd, "efwd", torch.complex64)
+    _check_cell_tensor(design, eadj, "eadj", torch.complex64)
+    if grad.dtype != torch.float32 or grad.numel() != design.n_params or not grad.is_cuda:
+        raise ValueError("grad must be a float32 CUDA tensor of n_params entries")
+    C = design.ncomp
+    ef = (ctypes.c_void_p * 3)(*[efwd[c].data_ptr() if c < C else 0 for c in range(3)])
+    ea = (ctypes.c_void_p * 3)(*[eadj[c].data_ptr() if c < C else 0 for c in range(3)])
+    wc = np.asarray(w, dtype=np.complex128).reshape(-1)
+    if wc.size == 1:
+        wc = np.repeat(wc, C)
+    ww = np.zeros(6, dtype=np.float32)
+    ww[0:2 * C:2] = wc.real[:C]
+    ww[1:2 * C:2] = wc.imag[:C]
+    _check(lib().adg_grad(design.ctx.handle, design.handle, p.ctypes.data_as(ctypes.c_void_p),
+                          ef, ea, ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad),
+                          _stream_ptr(stream)))
+
+
+def adg_grad_real(design: Design, params, G, grad, stream=None):
+    """grad <- sum G_c d eps_c / d p (real cotangent, the autograd form)."""
+    import torch
+    p = _params(design, params)
+    _check_cell_tensor(design, G, "G", torch.float32)
+    if grad.dtype != torch.float32 or grad.numel() != design.n_params or not grad.is_cuda:
+        raise ValueError("grad must be a float32 CUDA tensor of n_params entries")
+    _check(lib().adg_grad_real(design.ctx.handle, design.handle, p.ctypes.data_as(ctypes.c_void_p),
+                               _dptr(G), _dptr(grad), _stream_ptr(stream)))
+
+
+def adg_sync(ctx: Context, stream=None):
+    _check(lib().adg_sync(ctx.handle, _stream_ptr(stream)))
+
+
+def adg_design_stats(design: Design, stream=None) -> dict:
+    s = adg_stats()
+    _check(lib().adg_design_stats(design.ctx.handle, design.handle, _stream_ptr(stream),
+                                  ctypes.byref(s)))
+    return {"tiles": s.tiles, "program_tiles": s.program_tiles, "cells": s.cells,
+            "band_cells": s.band_cells, "tile": tuple(s.tile), "max_ops": s.max_ops}
+
+
+def adg_profile_enable(ctx: Context, on: bool = True):
+    _check(lib().adg_profile_enable(ctx.handle, 1 if on else 0))
+
+
+def adg_profile_read(ctx: Context, reset: bool = True) -> dict:
+    """{kernel name: (launches, total ms)} of the launches recorded while enabled."""
+    d = adg_profile_data()
+    _check(lib().adg_profile_read(ctx.handle, ctypes.byref(d), 1 if reset else 0))
+    return {K_NAMES[k]: (int(d.launches[k]), float(d.ms[k])) for k in K_NAMES}

@@ -1,0 +1,98 @@
+// adg_internal.h -- device records and launch interfaces shared by the host
+// side (adg_api.cu) and the kernels (adg_kernels.cu) of libadg.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace adg {
+
+// Per-tile capacities of the binned kernels.  A tile that would exceed one of
+// them is reported through the device error word (never written out of range).
+constexpr int kMaxLeaves = 48;  // primitives whose edge band crosses the tile
+constexpr int kMaxOps = 48;     // folded logic program length
+constexpr int kMaxDepth = 32;   // fold stack depth (checked at design creation)
+constexpr int kMaxSlots = 384;  // (primitive, active scalar) accumulators
+constexpr int kMaxPairs = 8;    // nonzero d s / d q terms one cell yields per leaf
+constexpr int kBlock = 128;     // threads per CTA of the build / VJP kernels
+constexpr int kWarps = kBlock / 32;
+
+enum : int32_t { kBox = 0, kCircle = 1, kPolygon = 2, kGraph = 3 };
+enum : int32_t { kLinear = 0, kSigmoid = 1, kQuadratic = 2, kSin = 3, kErf = 4 };
+enum : int32_t { kBoundX = 1, kBoundY = 2, kBoundZ = 4, kRectSigma = 8, kGraphAbove = 16 };
+// chained (binary) design program, one int32 word per op: (code << 24) | arg
+enum : int32_t { cPush = 0, cUnion = 1, cInter = 2, cDiff = 3 };
+// folded per-tile program, one uint16 per op: code | a << 3 | b << 9
+enum : int32_t { fPush = 0, fUnion = 1, fInter = 2, fDiff = 3, fCompl = 4 };
+// device error bits
+enum : int32_t {
+  eLeafOverflow = 1,
+  eOpsOverflow = 2,
+  eDepthOverflow = 4,
+  eSlotOverflow = 8,
+  ePartialRange = 16,
+  eBadProgram = 32
+};
+
+struct GridDev {
+  int nx, ny, nz, C;
+  int lx, ly, lz;  // log2 of the tile shape
+  int ntx, nty, ntz, T;
+  float off[3][3];  // [component][axis] sample offsets (cells)
+  float offmin[3], offmax[3];
+  float invd[3];  // 1 / spacing
+  float eps_bg, deps;
+  int logic;
+  int nchain;
+};
+
+// One primitive after the parameter map, in cell units of each axis:
+// a coordinate q along axis a becomes (q - o_a) / d_a = ai + af with ai an
+// integer and af in [0, 1), so that per-cell differences stay exact in fp32.
+struct alignas(16) PrimRec {
+  int kind, sigma, flags, nact;
+  float kr;    // sigma_k(x) = sigma(kr * x / d): kr in per-cell units
+  float band;  // transition half-width in cells (beyond it sigma is 0/1, flat)
+  int act_off; // act table: act[act_off + local q] = active slot, or -1
+  int auxd_off, auxf_off, naux;
+  int part_off;  // first partial of this primitive
+  int npb;       // tiles in the partial box
+  int tb[6];     // tile box of the value support   [x0,x1) [y0,y1) [z0,z1)
+  int pb[6];     // tile box of the derivative support (partials)
+  int ai[6];     // box: x0,x1,y0,y1,z0,z1; circle: cx, cy in [0],[1]; z0,z1 in [4],[5]
+  float af[6];
+  float g[4];  // circle: R, R^2 (hi, lo) in cells; [3] = 1 if R < 0
+};
+
+struct TileProg {
+  int nops;   // 0: constant tile, value cval
+  int nleaf;
+  float cval;
+  int nslot;
+  uint16_t ops[kMaxOps];
+  uint16_t leaf[kMaxLeaves];
+};
+
+struct VjpArgs {
+  const float2* ef[3];
+  const float2* ea[3];
+  float2 w[3];
+  const float* G;  // real-seed mode when non-null
+};
+
+cudaError_t launch_bin(const GridDev& g, const int* chain, const PrimRec* prims,
+                       const float* auxf, const double* auxd, TileProg* progs, int* list,
+                       int* counters, int* err, cudaStream_t s);
+cudaError_t launch_build(const GridDev& g, const TileProg* progs, const PrimRec* prims,
+                         const float* auxf, const double* auxd, float* fill, float* eps,
+                         int grid, cudaStream_t s);
+cudaError_t launch_vjp(const GridDev& g, const TileProg* progs, const int* list,
+                       const int* counters, const PrimRec* prims, const int* act,
+                       const float* auxf, const double* auxd, const VjpArgs& a,
+                       float* partial, int* err, int grid, cudaStream_t s);
+cudaError_t launch_finalize(int nparam, const int* ref_off, const int* ref_prim,
+                            const int* ref_qa, const double* ref_coeff, const PrimRec* prims,
+                            const float* partial, float* grad, cudaStream_t s);
+int build_blocks_per_sm();
+int vjp_blocks_per_sm();
+
+}  // namespace adg

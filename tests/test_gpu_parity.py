@@ -1,0 +1,207 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+fill: max abs <= 1e-6; eps: 1e-6 |deps| plus fp32 rounding of eps;
+gradients: ||g - g_ref||_2 <= 1e-4 ||g_ref||_2 + 1e-5 ||g_ref||_inf.
+Sizes span several tiles with ragged tails; the full-size 3D grating is
+checked on sampled cells for fill and in full for the gradient."""
+import numpy as np
+import pytest
+
+from paper_2311_05646_gb300 import inputs as I
+
+from . import _gpu as H
+from .conftest import cuda_ok
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2311_05646_gb300 import adg
+    return adg.Context(0)
+
+
+def _design(ctx, desc, tile=None):
+    from paper_2311_05646_gb300 import adg
+    return adg.Design(ctx, desc, tile=tile)
+
+
+def _check_build(ctx, desc, O, tile=None):
+    d = _design(ctx, desc, tile)
+    fill, eps = H.run_build(d, desc)
+    fref = O.fill(desc)
+    err = np.abs(fill - fref).max()
+    assert err <= H.FILL_TOL, err
+    eref = desc["eps_bg"] + (desc["eps_fg"] - desc["eps_bg"]) * fref
+    assert np.abs(eps - eref).max() <= H.eps_tol(desc)
+    return d
+
+
+def _check_grad(ctx, desc, O, seeds=(12, 13), tile=None, d=None):
+    d = d or _design(ctx, desc, tile)
+    ef, ea = I.plane_wave_field(desc, seeds[0]), I.plane_wave_field(desc, seeds[1])
+    w = I.seeded_w(desc["grid"]["ncomp"], 5)
+    g = H.run_grad(d, desc, ef, ea, w)
+    gref = O.grad(desc, ef, ea, w)
+    ok, err, bound = H.grad_ok(g, gref)
+    assert ok, (err, bound)
+    return d, g
+
+
+CASES = {
+    "grating2d_fit": lambda: I.grating_2d("fit"),
+    "grating2d_literal": lambda: I.grating_2d("literal"),
+    "grating3d_small": lambda: I.grating_3d(n=(150, 36, 60), teeth=8, pitch=600.0),
+    "taper_small": lambda: I.taper_3d(n=(200, 75, 25), nverts=16),
+    "holes_small": lambda: I.hole_lattice(n=(130, 100, 20), holes=5),
+    "holes_2d": lambda: I.hole_lattice(n=(96, 80, 1), d=(40.0, 40.0, 40.0), holes=4, ncomp=1),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fill_and_eps_match_oracle(ctx, oracle_mod, case):
+    _check_build(ctx, CASES[case](), oracle_mod)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_gradient_matches_oracle(ctx, oracle_mod, case):
+    _check_grad(ctx, CASES[case](), oracle_mod)
+
+
+@pytest.mark.parametrize("tile", [(32, 4, 4), (64, 2, 1), (32, 1, 8), (64, 16, 8)])
+def test_tile_shapes_agree(ctx, oracle_mod, tile):
+    desc = I.grating_3d(n=(150, 36, 60), teeth=8, pitch=600.0)
+    d = _check_build(ctx, desc, oracle_mod, tile=tile)
+    _check_grad(ctx, desc, oracle_mod, d=d)
+
+
+def test_clamp_logic_family(ctx, oracle_mod):
+    desc = I.grating_3d(n=(150, 36, 60), teeth=8, pitch=600.0)
+    desc["logic"] = "clamp"
+    d = _check_build(ctx, desc, oracle_mod)
+    _check_grad(ctx, desc, oracle_mod, d=d)
+
+
+@pytest.mark.parametrize("sigma", ["linear", "sigmoid", "quadratic", "sin", "erf"])
+def test_sigma_kinds_on_graph_boundaries(ctx, oracle_mod, sigma):
+    kr = {"linear": 1.0, "sigmoid": 4.0, "quadratic": 1.0, "sin": 1.5, "erf": 1.2}[sigma]
+    desc = I.taper_3d(n=(160, 60, 20), nverts=12, sigma=sigma, kr=kr)
+    d = _check_build(ctx, desc, oracle_mod)
+    _check_grad(ctx, desc, oracle_mod, d=d)
+
+
+def test_paper_form_rect_sigma_product(ctx, oracle_mod):
+    D = I.Design((70, 50, 1), (20.0, 20.0, 20.0), ncomp=1, eps_bg=1.0, eps_fg=3.0)
+    rng = np.random.default_rng(8)
+    kids = []
+    for _ in range(6):
+        x0, y0 = rng.uniform(0, 900), rng.uniform(0, 600)
+        px, py = D.param(x0), D.param(y0)
+        kids.append(D.box(x=(I.P(px), x0 + rng.uniform(30, 300)), y=(I.P(py), y0 + rng.uniform(30, 300)),
+                          mode="sigma", sigma=["linear", "sigmoid", "sin"][len(kids) % 3],
+                          kr=[1.0, 3.0, 1.2][len(kids) % 3]))
+    D.set_program(("union",) + tuple(kids))
+    desc = D.to_desc()
+    d = _check_build(ctx, desc, oracle_mod)
+    _check_grad(ctx, desc, oracle_mod, d=d)
+
+
+def test_real_seed_matches_oracle(ctx, oracle_mod):
+    desc = I.taper_3d(n=(200, 75, 25), nverts=16)
+    d = _design(ctx, desc)
+    G = np.random.default_rng(3).normal(size=I.field_shape(desc)).astype(np.float32)
+    g = H.run_grad_real(d, desc, G)
+    gref = oracle_mod.grad_real(desc, G)
+    ok, err, bound = H.grad_ok(g, gref)
+    assert ok, (err, bound)
+
+
+def test_gradient_is_deterministic(ctx):
+    desc = I.grating_3d(n=(150, 36, 60), teeth=8, pitch=600.0)
+    d = _design(ctx, desc)
+    ef, ea = I.plane_wave_field(desc, 1), I.plane_wave_field(desc, 2)
+    w = I.seeded_w(3, 3)
+    g1 = H.run_grad(d, desc, ef, ea, w)
+    p2 = desc["params"] + 1.0  # force a rebin in between
+    H.run_grad(d, desc, ef, ea, w, params=p2)
+    g2 = H.run_grad(d, desc, ef, ea, w)
+    assert np.array_equal(g1, g2)
+
+
+def test_param_change_rebins(ctx, oracle_mod):
+    desc = I.grating_2d()
+    d = _design(ctx, desc)
+    p2 = desc["params"] + np.random.default_rng(2).uniform(-30, 30, desc["params"].size)
+    fill, _ = H.run_build(d, desc, params=p2)
+    assert np.abs(fill - oracle_mod.fill(desc, p2)).max() <= H.FILL_TOL
+
+
+def test_degenerate_designs(ctx, oracle_mod):
+    # design entirely outside the grid: fill 0 everywhere, zero gradient
+    D = I.Design((40, 30, 1), (10.0, 10.0, 10.0), ncomp=1, eps_bg=1.0, eps_fg=2.0)
+    p = D.param(-500.0)
+    D.box(x=(I.P(p), -400.0), y=(0.0, 100.0))
+    desc = D.to_desc()
+    d = _design(ctx, desc)
+    fill, eps = H.run_build(d, desc)
+    assert fill.max() == 0.0 and np.all(eps == 1.0)
+    ef, ea = I.plane_wave_field(desc, 1), I.plane_wave_field(desc, 2)
+    assert np.all(H.run_grad(d, desc, ef, ea, 1.0) == 0.0)
+    # covering everything: constant 1, no parameters at all
+    D = I.Design((40, 30, 1), (10.0, 10.0, 10.0), ncomp=1, eps_bg=1.0, eps_fg=2.0)
+    D.box(x=(-100.0, 1000.0))
+    desc = D.to_desc()
+    d = _design(ctx, desc)
+    fill, eps = H.run_build(d, desc)
+    assert np.all(fill == 1.0) and np.all(eps == 2.0)
+    # a single-cell-thin feature and a box thinner than one cell
+    D = I.Design((33, 9, 1), (1.0, 1.0, 1.0), ncomp=1, eps_bg=1.0, eps_fg=2.0)
+    a = D.param(10.3)
+    D.set_program(("union", D.box(x=(I.P(a), 10.55)), D.box(x=(20.1, 20.2), y=(2.0, 7.0))))
+    desc = D.to_desc()
+    _check_build(ctx, desc, oracle_mod)
+    _check_grad(ctx, desc, oracle_mod)
+
+
+def test_invalid_descriptions_rejected(ctx):
+    from paper_2311_05646_gb300 import adg
+    desc = I.grating_2d()
+    bad = dict(desc)
+    bad["ops"] = np.asarray(list(desc["ops"]) + [(1 << 24) | 2], dtype=np.int32)  # stack underflow
+    with pytest.raises(adg.AdgError) as e:
+        adg.Design(ctx, bad)
+    assert e.value.status == adg.ADG_EINVAL
+    bad = dict(desc)
+    bad["q_param"] = desc["q_param"].copy()
+    bad["q_param"][5] = 999
+    with pytest.raises(adg.AdgError):
+        adg.Design(ctx, bad)
+    with pytest.raises(adg.AdgError):
+        adg.Design(ctx, desc, tile=(48, 4, 4))
+
+
+@pytest.mark.slow
+def test_full_size_grating3d(ctx, oracle_mod):
+    """600 x 200 x 120 x 3 components, 60 etches, 120 parameters, in the
+    launch configuration the benchmark times: fill on 20 000 sampled cells,
+    the full gradient against the oracle's full reverse sweep."""
+    import torch
+    from paper_2311_05646_gb300 import adg
+    desc = I.grating_3d()
+    d = _design(ctx, desc)
+    fill = torch.empty(d.shape, dtype=torch.float32, device="cuda")
+    eps = torch.empty_like(fill)
+    adg.adg_build_eps(d, desc["params"], eps, fill=fill)
+    adg.adg_sync(ctx)
+    rng = np.random.default_rng(0)
+    m = fill.numel()
+    idx = np.concatenate([rng.integers(0, m, 15000), np.arange(m - 5000, m)])
+    fref = oracle_mod.fill_at(desc, idx)
+    got = fill.reshape(-1)[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    assert np.abs(got - fref).max() <= H.FILL_TOL
+    ef, ea = I.plane_wave_field(desc, 22), I.plane_wave_field(desc, 23)
+    w = I.seeded_w(3, 24)
+    g = H.run_grad(d, desc, ef, ea, w)
+    gref = oracle_mod.grad(desc, ef, ea, w)
+    ok, err, bound = H.grad_ok(g, gref)
+    assert ok, (err, bound)
