@@ -35,6 +35,10 @@ __device__ __forceinline__ float sigma_f(int kind, float u, float& ds) {
       ds = 1.f;
       return u + 0.5f;
     case kSigmoid: {
+      // beyond |u| = 20 the tail (< 2.1e-9) is dropped, matching the binner's
+      // band, so derivatives vanish exactly outside the derivative tile box
+      if (u > 20.f) { ds = 0.f; return 1.f; }
+      if (u < -20.f) { ds = 0.f; return 0.f; }
       const float t = expf(-fabsf(u));
       const float r = 1.f / (1.f + t);
       ds = t * r * r;  // sigma (1 - sigma)
@@ -57,7 +61,9 @@ __device__ __forceinline__ float sigma_f(int kind, float u, float& ds) {
       ds = 0.5f * c;
       return 0.5f * (1.f + s);
     }
-    default:  // erf
+    default:  // erf (tail beyond |u| = 4.5 below 1.1e-10, dropped as for the sigmoid)
+      if (u > 4.5f) { ds = 0.f; return 1.f; }
+      if (u < -4.5f) { ds = 0.f; return 0.f; }
       ds = 0.56418958354775629f * expf(-u * u);
       return 0.5f * (1.f + erff(u));
   }
