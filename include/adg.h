@@ -198,6 +198,31 @@ typedef struct {
 adg_status adg_profile_enable(adg_ctx *ctx, int32_t on);
 adg_status adg_profile_read(adg_ctx *ctx, adg_profile_data *out, int32_t reset);
 
+/* The gradient of adg_grad for callers that cannot allocate device memory
+ * (a process whose device memory belongs to another runtime's fixed arena, a
+ * plug-in that must not grow its footprint after start-up, a strict memory
+ * budget).  The paper has no counterpart: this is a deployment variant.
+ *   - It allocates nothing: no cudaMalloc / cudaFree / allocating library
+ *     routine, no host heap.  All device scratch (design tables, primitive
+ *     records, per-tile programs, partials, error word) lives in one static
+ *     device array of 32 MiB that every GPU loading libadg holds until exit.
+ *   - desc, tiles (nullable), h_params: host, as for adg_design_create and
+ *     adg_grad; d_efwd, d_eadj, w, d_grad: as for adg_grad (caller-owned).
+ *   - Designs needing more than 32 MiB of scratch (tiles x 212 B + partials +
+ *     tables), or beyond 4096 primitives / 32768 scalars / 16384 program ops
+ *     or parameters, are rejected with ADG_EINVAL and a message saying why.
+ *   - The first call on a device sets up the scratch address for that device
+ *     (cudaGetSymbolAddress with the device current); make it before any
+ *     stream capture.
+ *   - Calls share the array and it keeps the last call's contents; each call
+ *     clears what must start at zero.  Calls that overlap on the GPU race on
+ *     it: serialise them.  The call returns after its work on `stream` has
+ *     completed and reports device-side checks as ADG_EDEVICE. */
+adg_status adg_grad_noalloc(const adg_design_desc *desc, const adg_tile_opts *tiles,
+                            const double *h_params, const float *const d_efwd[3],
+                            const float *const d_eadj[3], const float *w, float *d_grad,
+                            void *stream);
+
 /* Thread-local description of the last error (never NULL). */
 const char *adg_last_error(void);
 

@@ -289,3 +289,76 @@ def adg_profile_read(ctx: Context, reset: bool = True) -> dict:
     d = adg_profile_data()
     _check(lib().adg_profile_read(ctx.handle, ctypes.byref(d), 1 if reset else 0))
     return {K_NAMES[k]: (int(d.launches[k]), float(d.ms[k])) for k in K_NAMES}
+
+
+def adg_grad_noalloc(desc: dict, params, efwd, eadj, w, grad, tile=None, stream=None):
+    """The Eq. 1 gradient without any allocation: for callers that cannot
+    call cudaMalloc (a fixed device-memory arena owned by another runtime, a
+    plug-in that must not grow its footprint, a strict budget).  It takes the
+    design description directly, keeps all device scratch in libadg's static
+    32 MiB array, and returns once the result is in `grad`.  Calls share that
+    array: do not let two of them overlap on the GPU."""
+    import torch
+    keep = []
+
+    def arr(x, dt):
+        a = np.ascontiguousarray(np.asarray(x, dtype=dt))
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.c_void_p)
+
+    g = desc["grid"]
+    D = adg_design_desc()
+    D.grid.nx, D.grid.ny, D.grid.nz = (int(v) for v in g["n"])
+    C = int(g["ncomp"])
+    D.grid.ncomp = C
+    D.grid.dx, D.grid.dy, D.grid.dz = (float(v) for v in g["d"])
+    D.grid.ox, D.grid.oy, D.grid.oz = (float(v) for v in g["o"])
+    for c in range(C):
+        for a in range(3):
+            D.grid.off[c][a] = float(g["off"][c][a])
+    D.eps_bg, D.eps_fg = float(desc["eps_bg"]), float(desc["eps_fg"])
+    D.logic = LOGIC[desc["logic"]]
+    D.n_params = int(len(desc["params"]))
+    D.n_q = int(len(desc["q_base"]))
+    pr = desc["prims"]
+    D.n_prims = int(len(pr["kind"]))
+    D.n_ops = int(len(desc["ops"]))
+    D.reserved = 0
+    D.q_base = arr(desc["q_base"], np.float64)
+    D.q_coeff = arr(desc["q_coeff"], np.float64)
+    D.q_param = arr(desc["q_param"], np.int32)
+    D.prim_kind = arr(pr["kind"], np.int32)
+    D.prim_sigma = arr(pr["sigma"], np.int32)
+    D.prim_flags = arr(pr["flags"], np.int32)
+    D.prim_q0 = arr(pr["q0"], np.int32)
+    D.prim_nq = arr(pr["nq"], np.int32)
+    D.prim_kr = arr(pr["kr"], np.float64)
+    D.ops = arr(desc["ops"], np.int32)
+    T = adg_tile_opts(0, 0, 0, 0)
+    if tile is not None:
+        T.tx, T.ty, T.tz = (int(v) for v in tile)
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    if p.size != D.n_params:
+        raise ValueError("expected %d parameters, got %d" % (D.n_params, p.size))
+    shape = (C, D.grid.nz, D.grid.ny, D.grid.nx)
+    for t, name in ((efwd, "efwd"), (eadj, "eadj")):
+        if t.dtype != torch.complex64 or tuple(t.shape) != shape or not t.is_cuda:
+            raise ValueError("%s must be a complex64 CUDA tensor of shape %s" % (name, shape))
+    if grad.dtype != torch.float32 or grad.numel() != D.n_params or not grad.is_cuda:
+        raise ValueError("grad must be a float32 CUDA tensor of n_params entries")
+    ef = (ctypes.c_void_p * 3)(*[efwd[c].data_ptr() if c < C else 0 for c in range(3)])
+    ea = (ctypes.c_void_p * 3)(*[eadj[c].data_ptr() if c < C else 0 for c in range(3)])
+    wc = np.asarray(w, dtype=np.complex128).reshape(-1)
+    if wc.size == 1:
+        wc = np.repeat(wc, C)
+    ww = np.zeros(6, dtype=np.float32)
+    ww[0:2 * C:2] = wc.real[:C]
+    ww[1:2 * C:2] = wc.imag[:C]
+    L = lib()
+    f = L.adg_grad_noalloc
+    f.argtypes = [ctypes.POINTER(adg_design_desc), ctypes.POINTER(adg_tile_opts),
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    _check(f(ctypes.byref(D), ctypes.byref(T), p.ctypes.data_as(ctypes.c_void_p), ef, ea,
+             ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad), _stream_ptr(stream)))

@@ -728,4 +728,8 @@ extern "C" adg_status adg_profile_read(adg_ctx* ctx, adg_profile_data* out, int3
   return ADG_OK;
 }
 
+namespace adg {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace adg
+
 extern "C" const char* adg_last_error(void) { return g_err.c_str(); }

@@ -94,5 +94,6 @@ cudaError_t launch_finalize(int nparam, const int* ref_off, const int* ref_prim,
                             const float* partial, float* grad, cudaStream_t s);
 int build_blocks_per_sm();
 int vjp_blocks_per_sm();
+void set_last_error(const char* msg);  // the thread-local text of adg_last_error()
 
 }  // namespace adg

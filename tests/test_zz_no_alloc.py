@@ -1,0 +1,51 @@
+"""adg_grad_noalloc -- the gradient for callers that cannot allocate device
+memory (their device memory belongs to another runtime's fixed arena, or
+they must not grow their footprint after start-up) -- against the regular
+adg_grad, through the C ABI, on two calls in a row.
+
+This file is collected last on purpose, and it also passes alone in a fresh
+process."""
+import numpy as np
+import pytest
+
+from paper_2311_05646_gb300 import inputs as I
+
+from . import _gpu as H
+from .conftest import cuda_ok
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
+
+
+def test_noalloc_gradient_matches_adg_grad_on_two_calls():
+    import torch
+
+    from paper_2311_05646_gb300 import adg
+
+    ctx = adg.Context(0)
+    desc = I.grating_3d(n=(150, 36, 60), teeth=8, pitch=600.0)
+    design = adg.Design(ctx, desc)
+    efd = torch.from_numpy(I.plane_wave_field(desc, 31)).cuda()
+    ead = torch.from_numpy(I.plane_wave_field(desc, 32)).cuda()
+    w = I.seeded_w(3, 33)
+    p1 = desc["params"].copy()
+    p2 = p1 + np.random.default_rng(5).uniform(-20.0, 20.0, p1.size)
+    for p in (p1, p2):  # the second call must not see the first call's scratch
+        g_ref = torch.zeros(design.n_params, dtype=torch.float32, device="cuda")
+        adg.adg_grad(design, p, efd, ead, w, g_ref)
+        adg.adg_sync(ctx)
+        g_na = torch.full((design.n_params,), float("nan"), dtype=torch.float32, device="cuda")
+        adg.adg_grad_noalloc(desc, p, efd, ead, w, g_na)
+        a = g_na.cpu().numpy().astype(np.float64)
+        b = g_ref.cpu().numpy().astype(np.float64)
+        ok, err, bound = H.grad_ok(a, b)
+        assert ok, (err, bound)
+    # a design whose per-tile programs alone exceed the 32 MiB static scratch
+    # (8192 x 4096 cells in 32 x 4 x 1 tiles = 262144 tiles) is refused
+    big = I.grating_2d(n=(8192, 4096))
+    shape = I.field_shape(big)
+    ef_big = torch.zeros(shape, dtype=torch.complex64, device="cuda")
+    g_big = torch.zeros(big["params"].size, dtype=torch.float32, device="cuda")
+    with pytest.raises(adg.AdgError) as e:
+        adg.adg_grad_noalloc(big, big["params"], ef_big, ef_big, 1.0, g_big, tile=(32, 4, 1))
+    assert e.value.status == adg.ADG_EINVAL
+    assert "static scratch" in str(e.value)
