@@ -353,6 +353,178 @@ def run_adg(args):
     return 0
 
 
+def _device_fields(desc, seed):
+    """Seeded complex64 fields generated on the device (large batched / served
+    workloads; the values do not steer the work, only the shapes do)."""
+    import torch
+    C = desc["grid"]["ncomp"]
+    nx, ny, nz = desc["grid"]["n"]
+    g = torch.Generator(device="cuda").manual_seed(int(seed))
+    return (torch.randn((C, nz, ny, nx), dtype=torch.complex64, device="cuda", generator=g),
+            torch.randn((C, nz, ny, nx), dtype=torch.complex64, device="cuda", generator=g))
+
+
+def run_batch(args):
+    """Batched persistent launch: `--designs` designs of uneven grid size and
+    primitive count; eps build + gradient for all of them per step, as one
+    graph-captured job table versus one launch sequence per design."""
+    import numpy as np
+    import torch
+
+    from paper_2311_05646_gb300 import adg
+    from paper_2311_05646_gb300 import inputs as I
+    from paper_2311_05646_gb300.tuning import Autotuner
+
+    torch.cuda.set_device(0)
+    ctx = adg.Context(0)
+    descs = [I.random_design(4100 + k) for k in range(args.designs)]
+    tuner = Autotuner(ctx) if args.tune else None
+    designs, bufs = [], []
+    for k, desc in enumerate(descs):
+        tile = tuner.best(desc) if tuner else None
+        d = adg.Design(ctx, desc, tile=tile)
+        ef, ea = _device_fields(desc, 9000 + k)
+        eps = torch.empty(d.shape, dtype=torch.float32, device="cuda")
+        fill = torch.empty_like(eps)
+        g = torch.zeros(d.n_params, dtype=torch.float32, device="cuda")
+        designs.append(d)
+        bufs.append((ef, ea, eps, fill, g))
+    cells = sum(int(np.prod(desc["grid"]["n"])) for desc in descs)
+    params = [[desc["params"], desc["params"] + 0.01] for desc in descs]
+    w = np.full(3, -2j, dtype=np.complex64)
+
+    def per_design(k):
+        for i, d in enumerate(designs):
+            ef, ea, eps, fill, g = bufs[i]
+            p = params[i][k % 2]
+            adg.adg_build_eps(d, p, eps, fill=fill)
+            adg.adg_grad(d, p, ef, ea, w, g)
+
+    def batched(k):
+        items = []
+        for i, d in enumerate(designs):
+            ef, ea, eps, fill, g = bufs[i]
+            items.append(adg.BatchItem(d, params[i][k % 2], eps=eps, fill=fill, efwd=ef, eadj=ea,
+                                       w=w, grad=g))
+        return adg.adg_batch_submit(ctx, items, graph=True)
+
+    def timed(fn, steps, warm):
+        for k in range(warm):
+            fn(k)
+        torch.cuda.synchronize()
+        adg.adg_sync(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record()
+        for k in range(steps):
+            fn(k)
+        e1.record()
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / steps
+        adg.adg_sync(ctx)
+        return e0.elapsed_time(e1) / steps, wall * 1e3
+
+    ms_b, wall_b = timed(batched, args.steps, max(args.warmup, 3))
+    ms_d, wall_d = timed(per_design, args.steps, max(args.warmup, 3))
+    n = len(designs)
+    line = {"metric": "gradients/s (eps build + VJP gradient per design)",
+            "value": n / (ms_b * 1e-3), "unit": "gradients/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%d random designs, grids U[128,512]x[64,256]x[32,96], 10-400 "
+                                   "primitives (boxes, circles, 16-64-gons), unions/differences" % n,
+                       "cells_total": cells, "tiles_autotuned": bool(args.tune)},
+            "cells_per_s": cells / (ms_b * 1e-3),
+            "one_launch_per_design": {"value": n / (ms_d * 1e-3), "ms_per_step": ms_d,
+                                      "host_wall_ms_per_step": wall_d},
+            "batched_host_wall_ms_per_step": wall_b,
+            "speedup_vs_per_design": ms_d / ms_b}
+    print(json.dumps(line))
+    return 0
+
+
+def run_serve(args):
+    """Served requests: clients (designs) arrive as a Poisson process and run
+    50 optimiser iterations each (an eps build, then a gradient, then the
+    parameter step); fields stay resident; admission is gated by a device
+    memory budget; batches form continuously.  Reports p50/p99 latency and
+    gradients/s, first saturated (all clients at once), then at 0.8 x the
+    saturated request rate."""
+    import numpy as np
+    import torch
+
+    from paper_2311_05646_gb300 import adg
+    from paper_2311_05646_gb300 import inputs as I
+    from paper_2311_05646_gb300 import serve as S
+
+    torch.cuda.set_device(0)
+    ctx = adg.Context(0)
+    rng = np.random.default_rng(51)
+
+    def make_clients(n):
+        cl = []
+        for k in range(n):
+            if k == 0:  # the largest: 20 x 20 holes in 1000 x 1000 x 80
+                desc = I.hole_lattice(n=(1000, 1000, 80), holes=20, seed=51)
+            elif rng.uniform() < 0.5:
+                desc = I.hole_lattice(n=(400, 400, 1), d=(40.0, 40.0, 40.0), holes=8, ncomp=1,
+                                      seed=51 + k)
+            else:
+                sx = int(np.exp(rng.uniform(np.log(128), np.log(1000))))
+                sy = int(np.exp(rng.uniform(np.log(128), np.log(1000))))
+                sz = int(np.exp(rng.uniform(np.log(32), np.log(80))))
+                desc = I.hole_lattice(n=(sx, sy, sz), holes=int(np.clip(sx // 50, 2, 20)),
+                                      seed=51 + k)
+            ef, ea = _device_fields(desc, 7000 + k)
+            c = S.Client(cid=k, desc=desc, efwd=ef, eadj=ea, w=np.full(desc["grid"]["ncomp"], -2j),
+                         iterations=args.iterations)
+            cl.append(c)
+        return cl
+
+    def run(clients, arrivals):
+        srv = S.Server(ctx, mem_budget_bytes=int(args.mem_gb * 2 ** 30), max_inflight=2)
+        t0 = time.perf_counter()
+        order = sorted(zip(arrivals, range(len(clients))))
+        nxt = 0
+        while nxt < len(order) or not srv.idle():
+            now = time.perf_counter() - t0
+            while nxt < len(order) and order[nxt][0] <= now:
+                srv.arrive(clients[order[nxt][1]], time.perf_counter())
+                nxt += 1
+            if not srv.poll():
+                time.sleep(20e-6)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        grads = sum(1 for r in srv.completed if r.op == "grad")
+        return srv, wall, grads
+
+    clients = make_clients(args.clients)
+    srv, wall, grads = run(clients, [0.0] * len(clients))
+    sat = grads / wall
+    lat_sat = S.latency_stats(srv.completed)
+    # Poisson arrivals at 0.8 x the saturated rate (clients = requests / iterations)
+    clients = make_clients(args.clients)
+    rate_clients = 0.8 * sat / args.iterations
+    arr = np.cumsum(rng.exponential(1.0 / rate_clients, len(clients)))
+    arr -= arr[0]
+    srv2, wall2, grads2 = run(clients, list(arr))
+    lat = S.latency_stats(srv2.completed)
+    line = {"metric": "served gradients/s with p50/p99 request latency", "value": grads2 / wall2,
+            "unit": "gradients/s", "n_gpus": 1, "steps": grads2, "warmup": 0,
+            "ms_per_step": 1e3 * wall2 / max(grads2, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%d clients x %d iterations (eps build + gradient), hole "
+                                   "lattices: 2D 400x400 or 3D up to 1000x1000x80 (20x20 holes, "
+                                   "1200 params)" % (len(clients), args.iterations),
+                       "mem_budget_gb": args.mem_gb, "arrivals": "Poisson at 0.8 x saturated"},
+            "latency_ms": {"p50": lat["p50_ms"], "p99": lat["p99_ms"], "mean": lat.get("mean_ms")},
+            "saturated": {"gradients_per_s": sat, "p50_ms": lat_sat["p50_ms"],
+                          "p99_ms": lat_sat["p99_ms"], "batches": srv.batches},
+            "batches": srv2.batches}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,9 +534,19 @@ def main():
     ap.add_argument("--tile", default="")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="grating3d", choices=["grating3d", "batch", "serve"])
+    ap.add_argument("--designs", type=int, default=256)
+    ap.add_argument("--tune", action="store_true")
+    ap.add_argument("--clients", type=int, default=12)
+    ap.add_argument("--iterations", type=int, default=50)
+    ap.add_argument("--mem-gb", type=float, default=40.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_adg(args)
 
 

@@ -121,7 +121,8 @@ typedef struct {
 } adg_design_desc;
 
 /* Tile shape (cells) of the binned kernels.  tx in {32, 64}, ty in
- * {1, 2, 4, 8, 16}, tz in {1, 2, 4, 8}.  All zero = library default. */
+ * {1, 2, 4, 8, 16}, tz in {1, 2, 4, 8}, 128 <= tx*ty*tz <= 1024.  All zero =
+ * library default (32 x 4 x 4). */
 typedef struct {
   int32_t tx, ty, tz;
   int32_t reserved;
@@ -178,6 +179,40 @@ adg_status adg_grad(adg_ctx *ctx, adg_design *design, const double *h_params,
 adg_status adg_grad_real(adg_ctx *ctx, adg_design *design, const double *h_params,
                          const float *d_G, float *d_grad, void *stream);
 
+/* ---- batched work ---------------------------------------------------------
+ * Many (design, operation) items run as ONE job table: five launches (zero,
+ * bin, build, VJP, finalize) whatever the number of designs, their grid sizes
+ * or primitive counts.  The binner covers every item's tiles in one grid; the
+ * build and VJP kernels are persistent and walk a work list of (design, tile)
+ * pairs.  The batched form of the same computation as adg_build_eps /
+ * adg_grad / adg_grad_real (Sec. 2, steps 2 and 5), for many designs. */
+enum { ADG_BATCH_BUILD = 1, ADG_BATCH_GRAD = 2, ADG_BATCH_GRAD_REAL = 4 };
+enum { ADG_BATCH_GRAPH = 1 }; /* submit flag: capture the launches once as a CUDA
+                                 graph and replay it for batches of the same shape */
+typedef struct {
+  adg_design *design;  /* each design at most once per batch                  */
+  int32_t ops;         /* ADG_BATCH_* bitmask (GRAD and GRAD_REAL exclusive)   */
+  int32_t reserved;    /* must be 0                                           */
+  const double *h_params;               /* n_params host doubles              */
+  float *d_fill, *d_eps;                /* BUILD outputs (d_fill nullable)    */
+  const float *d_efwd[3], *d_eadj[3];   /* GRAD fields, as for adg_grad       */
+  float w[6];                           /* GRAD weights (re, im per component) */
+  const float *d_G;                     /* GRAD_REAL cotangent                */
+  float *d_grad;                        /* GRAD / GRAD_REAL output            */
+} adg_batch_item;
+
+/* Enqueue a batch on `stream`; returns a ticket for adg_batch_poll/wait.
+ * The library keeps two batch arenas per context, so a third submit waits
+ * (host side) for the batch two back to finish uploading.  Host arrays are
+ * copied before return.  Batches of one context must share one stream (or be
+ * ordered by the caller). */
+adg_status adg_batch_submit(adg_ctx *ctx, const adg_batch_item *items, int32_t n_items,
+                            int32_t flags, void *stream, uint64_t *ticket);
+/* *done = 1 once the batch's device work has completed. */
+adg_status adg_batch_poll(adg_ctx *ctx, uint64_t ticket, int32_t *done);
+/* Wait at most timeout_ns for the batch; ADG_ETIMEOUT if it is still running. */
+adg_status adg_batch_wait(adg_ctx *ctx, uint64_t ticket, uint64_t timeout_ns);
+
 /* Wait for `stream` and report device-side errors (ADG_EDEVICE) recorded by
  * any call of this context since the last adg_sync. */
 adg_status adg_sync(adg_ctx *ctx, void *stream);
@@ -190,7 +225,8 @@ adg_status adg_design_stats(adg_ctx *ctx, adg_design *design, void *stream, adg_
  * adg_profile_read waits for the recorded events and returns, per kernel
  * (index ADG_K_*), the launch count and the summed device time; `reset`
  * clears the accumulators. */
-enum { ADG_K_BIN = 0, ADG_K_BUILD = 1, ADG_K_VJP = 2, ADG_K_FINALIZE = 3, ADG_K_COUNT = 8 };
+enum { ADG_K_BIN = 0, ADG_K_BUILD = 1, ADG_K_VJP = 2, ADG_K_FINALIZE = 3, ADG_K_PREPARE = 4,
+       ADG_K_COUNT = 8 };
 typedef struct {
   int64_t launches[ADG_K_COUNT];
   double ms[ADG_K_COUNT];

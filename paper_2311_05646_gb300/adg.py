@@ -362,3 +362,97 @@ def adg_grad_noalloc(desc: dict, params, efwd, eadj, w, grad, tile=None, stream=
     f.restype = ctypes.c_int
     _check(f(ctypes.byref(D), ctypes.byref(T), p.ctypes.data_as(ctypes.c_void_p), ef, ea,
              ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad), _stream_ptr(stream)))
+
+
+BATCH_BUILD, BATCH_GRAD, BATCH_GRAD_REAL = 1, 2, 4
+BATCH_GRAPH = 1
+
+
+class adg_batch_item(ctypes.Structure):
+    _fields_ = [("design", ctypes.c_void_p), ("ops", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("h_params", ctypes.c_void_p), ("d_fill", ctypes.c_void_p),
+                ("d_eps", ctypes.c_void_p), ("d_efwd", ctypes.c_void_p * 3),
+                ("d_eadj", ctypes.c_void_p * 3), ("w", ctypes.c_float * 6),
+                ("d_G", ctypes.c_void_p), ("d_grad", ctypes.c_void_p)]
+
+
+class BatchItem:
+    """One (design, operations) entry of a batch; tensors are CUDA tensors
+    shaped like the single-design calls."""
+
+    def __init__(self, design: Design, params, eps=None, fill=None, efwd=None, eadj=None, w=None,
+                 G=None, grad=None):
+        self.design, self.params = design, np.ascontiguousarray(np.asarray(params, np.float64))
+        self.eps, self.fill, self.efwd, self.eadj, self.w, self.G, self.grad = (
+            eps, fill, efwd, eadj, w, G, grad)
+
+
+def adg_batch_submit(ctx: Context, items, graph: bool = False, stream=None) -> int:
+    """Enqueue all items as one job table (five launches); returns a ticket."""
+    import torch
+    arr = (adg_batch_item * len(items))()
+    keep = []
+    for k, it in enumerate(items):
+        d = it.design
+        if it.params.size != d.n_params:
+            raise ValueError("item %d: expected %d parameters" % (k, d.n_params))
+        e = arr[k]
+        e.design = d.handle
+        ops = 0
+        keep.append(it.params)
+        e.h_params = it.params.ctypes.data_as(ctypes.c_void_p)
+        if it.eps is not None:
+            _check_cell_tensor(d, it.eps, "eps", torch.float32)
+            ops |= BATCH_BUILD
+            e.d_eps = _dptr(it.eps)
+            if it.fill is not None:
+                _check_cell_tensor(d, it.fill, "fill", torch.float32)
+                e.d_fill = _dptr(it.fill)
+        if it.efwd is not None:
+            _check_cell_tensor(d, it.efwd, "efwd", torch.complex64)
+            _check_cell_tensor(d, it.eadj, "eadj", torch.complex64)
+            ops |= BATCH_GRAD
+            for c in range(d.ncomp):
+                e.d_efwd[c] = it.efwd[c].data_ptr()
+                e.d_eadj[c] = it.eadj[c].data_ptr()
+            wc = np.asarray(it.w, dtype=np.complex128).reshape(-1)
+            if wc.size == 1:
+                wc = np.repeat(wc, d.ncomp)
+            for c in range(d.ncomp):
+                e.w[2 * c] = float(wc[c].real)
+                e.w[2 * c + 1] = float(wc[c].imag)
+        elif it.G is not None:
+            _check_cell_tensor(d, it.G, "G", torch.float32)
+            ops |= BATCH_GRAD_REAL
+            e.d_G = _dptr(it.G)
+        if ops & (BATCH_GRAD | BATCH_GRAD_REAL):
+            if it.grad is None or it.grad.dtype != torch.float32 or it.grad.numel() != d.n_params:
+                raise ValueError("item %d: grad must be float32 with n_params entries" % k)
+            e.d_grad = _dptr(it.grad)
+        e.ops = ops
+    L = lib()
+    f = L.adg_batch_submit
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(adg_batch_item), ctypes.c_int32, ctypes.c_int32,
+                  ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
+    f.restype = ctypes.c_int
+    t = ctypes.c_uint64(0)
+    _check(f(ctx.handle, arr, len(items), BATCH_GRAPH if graph else 0, _stream_ptr(stream),
+             ctypes.byref(t)))
+    return int(t.value)
+
+
+def adg_batch_poll(ctx: Context, ticket: int) -> bool:
+    L = lib()
+    L.adg_batch_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)]
+    L.adg_batch_poll.restype = ctypes.c_int
+    done = ctypes.c_int32(0)
+    _check(L.adg_batch_poll(ctx.handle, ticket, ctypes.byref(done)))
+    return bool(done.value)
+
+
+def adg_batch_wait(ctx: Context, ticket: int, timeout_s: float = 60.0) -> None:
+    """Wait for a batch; raises AdgError(ADG_ETIMEOUT) when it is still running."""
+    L = lib()
+    L.adg_batch_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]
+    L.adg_batch_wait.restype = ctypes.c_int
+    _check(L.adg_batch_wait(ctx.handle, ticket, int(timeout_s * 1e9)))

@@ -14,10 +14,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/adg.h"
+#include "adg_host.h"
 #include "adg_internal.h"
 
 using namespace adg;
@@ -44,16 +47,6 @@ adg_status fail(adg_status st, const char* fmt, ...) {
                   #call, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
   } while (0)
 
-// transition half-widths of the sigma kinds in the unit variable (beyond them
-// the function is 0 or 1 with zero slope; the sigmoid's tail is below 2.1e-9)
-const double kBand[5] = {0.5, 20.0, 0.70710678118654752, 1.5707963267948966, 4.5};
-
-int ilog2(int v) {
-  int l = 0;
-  while ((1 << l) < v) ++l;
-  return l;
-}
-
 template <class T>
 cudaError_t upload(T** dptr, const std::vector<T>& h) {
   *dptr = nullptr;
@@ -77,6 +70,23 @@ struct adg_ctx {
   std::vector<cudaEvent_t> pool;
   int64_t launches[ADG_K_COUNT] = {};
   double ms[ADG_K_COUNT] = {};
+  // batches: two alternating arenas (device table + pinned staging), each
+  // with the CUDA graph of its last captured batch shape
+  struct Arena {
+    void* d = nullptr;
+    void* h = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    bool used = false;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t sig = 0;
+  };
+  Arena arenas[2];
+  int next_arena = 0;
+  cudaStream_t capture = nullptr;  // graphs are captured here, launched on the caller's stream
+  struct Ticket { uint64_t id; cudaEvent_t ev; };
+  std::vector<Ticket> tickets;
+  uint64_t next_ticket = 1;
 };
 
 namespace {
@@ -123,14 +133,15 @@ struct adg_design {
   std::vector<double> q_base, q_coeff, kr;
   std::vector<int> q_param, kind, sigma, flags, q0, nq;
   std::vector<int> chain;
-  std::vector<int> nact, act_off, act;
-  std::vector<int> auxd_off, auxf_off;
-  int auxd_n = 0, auxf_n = 0;
+  std::vector<int> nact, act_off, act, auxd_off, auxf_off;
+  std::vector<float> actc;
   std::vector<int> ref_off, ref_prim, ref_qa;
   std::vector<double> ref_coeff;
+  host::SlotTables st{};
   // device
   int *d_chain = nullptr, *d_act = nullptr, *d_ref_off = nullptr, *d_ref_prim = nullptr,
       *d_ref_qa = nullptr;
+  float* d_actc = nullptr;
   double* d_ref_coeff = nullptr;
   PrimRec* d_prims = nullptr;
   double* d_auxd = nullptr;
@@ -140,6 +151,8 @@ struct adg_design {
   int* d_counters = nullptr;
   float* d_partial = nullptr;
   size_t partial_cap = 0;
+  Job* d_job = nullptr;  // the one-job table of single-design calls
+  Job job{};
   // per-call host staging
   std::vector<PrimRec> h_prims;
   std::vector<double> h_auxd, q;
@@ -176,6 +189,14 @@ extern "C" adg_status adg_ctx_destroy(adg_ctx* ctx) {
   cudaSetDevice(ctx->device);
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
+  for (auto& a : ctx->arenas) {
+    if (a.exec) cudaGraphExecDestroy(a.exec);
+    if (a.done) cudaEventDestroy(a.done);
+    cudaFree(a.d);
+    cudaFreeHost(a.h);
+  }
+  for (auto& t : ctx->tickets) cudaEventDestroy(t.ev);
+  if (ctx->capture) cudaStreamDestroy(ctx->capture);
   cudaFree(ctx->d_err);
   delete ctx;
   return ADG_OK;
@@ -184,75 +205,10 @@ extern "C" adg_status adg_ctx_destroy(adg_ctx* ctx) {
 // ------------------------------------------------------------------- design -
 namespace {
 
-// postfix -> tree -> chain of binary ops (n-ary union / intersection become
-// left-to-right chains, the recursive form of union_2 in Appendix B.2)
-struct Node {
-  int code, arg;
-  std::vector<int> kids;
-};
-
-void emit_chain(const std::vector<Node>& nodes, int id, std::vector<int>& out) {
-  const Node& n = nodes[id];
-  if (n.code == ADG_OP_PUSH) {
-    out.push_back((cPush << 24) | n.arg);
-    return;
-  }
-  if (n.code == ADG_OP_DIFF) {
-    emit_chain(nodes, n.kids[0], out);
-    emit_chain(nodes, n.kids[1], out);
-    out.push_back(cDiff << 24);
-    return;
-  }
-  const int c = n.code == ADG_OP_UNION ? cUnion : cInter;
-  emit_chain(nodes, n.kids[0], out);
-  for (size_t t = 1; t < n.kids.size(); ++t) {
-    emit_chain(nodes, n.kids[t], out);
-    out.push_back(c << 24);
-  }
-}
-
-adg_status compile_program(const adg_design_desc* D, std::vector<int>& chain) {
-  std::vector<Node> nodes;
-  std::vector<int> st;
-  for (int i = 0; i < D->n_ops; ++i) {
-    const int w = D->ops[i];
-    const int code = (w >> 24) & 0xff, arg = w & 0xffffff;
-    Node nd{code, arg, {}};
-    int need = 0;
-    if (code == ADG_OP_PUSH) {
-      if (arg < 0 || arg >= D->n_prims)
-        return fail(ADG_EINVAL, "program op %d pushes primitive %d (have %d)", i, arg, D->n_prims);
-    } else if (code == ADG_OP_UNION || code == ADG_OP_INTERSECT) {
-      need = arg;
-      if (need < 1) return fail(ADG_EINVAL, "program op %d: operand count %d", i, need);
-    } else if (code == ADG_OP_DIFF) {
-      need = 2;
-    } else {
-      return fail(ADG_EINVAL, "program op %d: unknown code %d", i, code);
-    }
-    if ((int)st.size() < need) return fail(ADG_EINVAL, "program op %d: stack underflow", i);
-    nd.kids.assign(st.end() - need, st.end());
-    st.resize(st.size() - need);
-    nodes.push_back(nd);
-    st.push_back((int)nodes.size() - 1);
-  }
-  if (st.size() != 1)
-    return fail(ADG_EINVAL, "program leaves %zu values on the stack (need 1)", st.size());
-  chain.clear();
-  emit_chain(nodes, st[0], chain);
-  int sp = 0, mx = 0;
-  for (int w : chain) {
-    sp += ((w >> 24) == cPush) ? 1 : -1;
-    mx = std::max(mx, sp);
-  }
-  if (mx > kMaxDepth)
-    return fail(ADG_EINVAL, "program nesting %d exceeds the supported depth %d", mx, kMaxDepth);
-  return ADG_OK;
-}
-
 void free_design(adg_design* d) {
   cudaFree(d->d_chain);
   cudaFree(d->d_act);
+  cudaFree(d->d_actc);
   cudaFree(d->d_ref_off);
   cudaFree(d->d_ref_prim);
   cudaFree(d->d_ref_qa);
@@ -264,10 +220,9 @@ void free_design(adg_design* d) {
   cudaFree(d->d_list);
   cudaFree(d->d_counters);
   cudaFree(d->d_partial);
+  cudaFree(d->d_job);
   delete d;
 }
-
-bool is_fin(double v) { return std::isfinite(v); }
 
 }  // namespace
 
@@ -275,56 +230,27 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
                                         const adg_tile_opts* tiles, adg_design** out) {
   if (!ctx || !D || !out) return fail(ADG_EINVAL, "adg_design_create: NULL argument");
   *out = nullptr;
+  host::Msg m;
+  if (host::validate(D, m) != ADG_OK) return fail(ADG_EINVAL, "%s", m.text);
+  int tx = 32, ty = 4, tz = 4;
+  if (tiles && (tiles->tx || tiles->ty || tiles->tz)) { tx = tiles->tx; ty = tiles->ty; tz = tiles->tz; }
+  if (!host::tile_ok(tx, ty, tz))
+    return fail(ADG_EINVAL,
+                "tile %dx%dx%d: tx in {32,64}, ty in {1..16}, tz in {1..8}, powers of 2, %d..%d cells",
+                tx, ty, tz, kBlock, kMaxTileCells);
   const adg_grid& G = D->grid;
-  if (G.nx < 1 || G.ny < 1 || G.nz < 1 || G.nx > 8192 || G.ny > 8192 || G.nz > 8192)
-    return fail(ADG_EINVAL, "grid %dx%dx%d outside 1..8192 per axis", G.nx, G.ny, G.nz);
-  if (G.ncomp < 1 || G.ncomp > 3) return fail(ADG_EINVAL, "ncomp %d not in 1..3", G.ncomp);
-  if (!(G.dx > 0) || !(G.dy > 0) || !(G.dz > 0) || !is_fin(G.dx) || !is_fin(G.dy) || !is_fin(G.dz))
-    return fail(ADG_EINVAL, "grid spacing must be positive and finite");
-  if (!is_fin(G.ox) || !is_fin(G.oy) || !is_fin(G.oz))
-    return fail(ADG_EINVAL, "grid origin must be finite");
-  for (int c = 0; c < G.ncomp; ++c)
-    for (int a = 0; a < 3; ++a)
-      if (!(fabs(G.off[c][a]) <= 1.0)) return fail(ADG_EINVAL, "offset off[%d][%d] not in [-1, 1]", c, a);
-  if (!is_fin(D->eps_bg) || !is_fin(D->eps_fg)) return fail(ADG_EINVAL, "eps levels must be finite");
-  if (D->logic != ADG_LOGIC_PRODUCT && D->logic != ADG_LOGIC_CLAMP)
-    return fail(ADG_EINVAL, "logic %d unknown", D->logic);
-  if (D->reserved != 0) return fail(ADG_EINVAL, "reserved must be 0");
-  if (D->n_params < 0 || D->n_q < 0 || D->n_prims < 1 || D->n_ops < 1 || D->n_prims > 65535)
-    return fail(ADG_EINVAL, "counts: params %d, q %d, prims %d (1..65535), ops %d", D->n_params,
-                D->n_q, D->n_prims, D->n_ops);
-  if ((D->n_q > 0 && (!D->q_base || !D->q_coeff || !D->q_param)) || !D->prim_kind ||
-      !D->prim_sigma || !D->prim_flags || !D->prim_q0 || !D->prim_nq || !D->prim_kr || !D->ops)
-    return fail(ADG_EINVAL, "description array is NULL");
-  for (int j = 0; j < D->n_q; ++j) {
-    if (D->q_param[j] < -1 || D->q_param[j] >= D->n_params)
-      return fail(ADG_EINVAL, "q_param[%d] = %d out of range", j, D->q_param[j]);
-    if (!is_fin(D->q_base[j]) || !is_fin(D->q_coeff[j]))
-      return fail(ADG_EINVAL, "q_base / q_coeff[%d] not finite", j);
-  }
-  for (int p = 0; p < D->n_prims; ++p) {
-    const int k = D->prim_kind[p], s = D->prim_sigma[p], n = D->prim_nq[p], q0 = D->prim_q0[p];
-    if (q0 < 0 || n < 0 || q0 + n > D->n_q)
-      return fail(ADG_EINVAL, "primitive %d: scalars [%d, %d) outside [0, %d)", p, q0, q0 + n, D->n_q);
-    if (s < 0 || s > 4) return fail(ADG_EINVAL, "primitive %d: sigma kind %d unknown", p, s);
-    if (!(D->prim_kr[p] > 0) || !is_fin(D->prim_kr[p]))
-      return fail(ADG_EINVAL, "primitive %d: kr must be positive", p);
-    if (k == ADG_PRIM_BOX) {
-      if (n != 6) return fail(ADG_EINVAL, "box %d needs 6 scalars, has %d", p, n);
-    } else if (k == ADG_PRIM_CIRCLE) {
-      if (n != 5) return fail(ADG_EINVAL, "circle %d needs 5 scalars, has %d", p, n);
-      if (fabs(G.dx - G.dy) > 1e-12 * G.dx) return fail(ADG_EINVAL, "circle %d needs dx == dy", p);
-    } else if (k == ADG_PRIM_GRAPH) {
-      if (n < 6 || (n - 2) % 2) return fail(ADG_EINVAL, "graph %d needs 2 + 2M scalars, M >= 2", p);
-    } else if (k == ADG_PRIM_POLYGON) {
-      return fail(ADG_EINVAL, "primitive %d: polygons are not supported by this build", p);
-    } else {
-      return fail(ADG_EINVAL, "primitive %d: kind %d unknown", p, k);
-    }
-  }
-  std::vector<int> chain;
-  adg_status st = compile_program(D, chain);
-  if (st != ADG_OK) return st;
+  if ((long long)((G.nx + tx - 1) / tx) * ((G.ny + ty - 1) / ty) * ((G.nz + tz - 1) / tz) >
+      (1LL << 30))
+    return fail(ADG_EINVAL, "too many tiles");
+
+  // program -> chain
+  std::vector<int> w(6 * (size_t)D->n_ops), chain(2 * (size_t)D->n_ops);
+  host::ChainWork cw{w.data(), w.data() + D->n_ops, w.data() + 2 * D->n_ops,
+                     w.data() + 3 * D->n_ops, w.data() + 4 * D->n_ops, w.data() + 5 * D->n_ops};
+  int nchain = 0;
+  if (host::compile_chain(D, cw, chain.data(), &nchain, m) != ADG_OK)
+    return fail(ADG_EINVAL, "%s", m.text);
+  chain.resize(nchain);
 
   CU(cudaSetDevice(ctx->device));
   adg_design* d = new adg_design();
@@ -344,86 +270,42 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   d->q0.assign(D->prim_q0, D->prim_q0 + D->n_prims);
   d->nq.assign(D->prim_nq, D->prim_nq + D->n_prims);
   d->kr.assign(D->prim_kr, D->prim_kr + D->n_prims);
+  host::set_grid(D, tx, ty, tz, nchain, d->g);
 
-  // tile shape
-  int tx = 32, ty = 4, tz = 4;
-  if (tiles && (tiles->tx || tiles->ty || tiles->tz)) { tx = tiles->tx; ty = tiles->ty; tz = tiles->tz; }
-  auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
-  if (!(tx == 32 || tx == 64) || !pow2(ty) || ty > 16 || !pow2(tz) || tz > 8 || tx * ty * tz < kBlock) {
-    delete d;
-    return fail(ADG_EINVAL, "tile %dx%dx%d: tx in {32,64}, ty in {1..16}, tz in {1..8}, powers of 2, >= %d cells",
-                tx, ty, tz, kBlock);
-  }
-  GridDev& g = d->g;
-  g.nx = G.nx; g.ny = G.ny; g.nz = G.nz; g.C = G.ncomp;
-  g.lx = ilog2(tx); g.ly = ilog2(ty); g.lz = ilog2(tz);
-  g.ntx = (G.nx + tx - 1) / tx; g.nty = (G.ny + ty - 1) / ty; g.ntz = (G.nz + tz - 1) / tz;
-  const long long T = (long long)g.ntx * g.nty * g.ntz;
-  if (T > (1LL << 30)) { delete d; return fail(ADG_EINVAL, "too many tiles"); }
-  g.T = (int)T;
-  for (int a = 0; a < 3; ++a) { g.offmin[a] = 1e9f; g.offmax[a] = -1e9f; }
-  for (int c = 0; c < 3; ++c)
-    for (int a = 0; a < 3; ++a) {
-      g.off[c][a] = c < G.ncomp ? (float)G.off[c][a] : 0.f;
-      if (c < G.ncomp) {
-        g.offmin[a] = std::min(g.offmin[a], g.off[c][a]);
-        g.offmax[a] = std::max(g.offmax[a], g.off[c][a]);
-      }
-    }
-  for (int a = 0; a < 3; ++a) g.invd[a] = (float)(1.0 / d->d[a]);
-  g.eps_bg = (float)D->eps_bg;
-  g.deps = (float)(D->eps_fg - D->eps_bg);
-  g.logic = D->logic;
-  g.nchain = (int)chain.size();
-
-  // active scalars and parameter references
-  d->nact.assign(d->n_prims, 0);
-  d->act_off.assign(d->n_prims, 0);
-  d->auxd_off.assign(d->n_prims, 0);
-  d->auxf_off.assign(d->n_prims, 0);
-  std::vector<std::vector<int>> rp(d->n_params), rq(d->n_params);
-  std::vector<std::vector<double>> rc(d->n_params);
-  for (int p = 0; p < d->n_prims; ++p) {
-    d->act_off[p] = (int)d->act.size();
-    int na = 0;
-    for (int t = 0; t < d->nq[p]; ++t) {
-      const int j = d->q0[p] + t;
-      if (d->q_param[j] >= 0 && d->q_coeff[j] != 0.0) {
-        d->act.push_back(na);
-        rp[d->q_param[j]].push_back(p);
-        rq[d->q_param[j]].push_back(na);
-        rc[d->q_param[j]].push_back(d->q_coeff[j]);
-        ++na;
-      } else {
-        d->act.push_back(-1);
-      }
-    }
-    d->nact[p] = na;
-    if (d->kind[p] == ADG_PRIM_GRAPH) {
-      const int M = (d->nq[p] - 2) / 2;
-      d->auxd_off[p] = d->auxd_n;
-      d->auxd_n += 3 * M;
-      d->auxf_off[p] = d->auxf_n;
-      d->auxf_n += M;
-    }
-  }
-  d->ref_off.push_back(0);
-  for (int k = 0; k < d->n_params; ++k) {
-    for (size_t t = 0; t < rp[k].size(); ++t) {
-      d->ref_prim.push_back(rp[k][t]);
-      d->ref_qa.push_back(rq[k][t]);
-      d->ref_coeff.push_back(rc[k][t]);
-    }
-    d->ref_off.push_back((int)d->ref_prim.size());
-  }
+  // accumulator slots per (primitive, parameter) and parameter references
+  size_t nqs = 0;
+  for (int p = 0; p < D->n_prims; ++p) nqs += D->prim_nq[p];
+  d->act.resize(std::max<size_t>(nqs, 1));
+  d->actc.resize(std::max<size_t>(nqs, 1));
+  d->nact.resize(D->n_prims);
+  d->act_off.resize(D->n_prims);
+  d->auxd_off.resize(D->n_prims);
+  d->auxf_off.resize(D->n_prims);
+  d->ref_off.resize(D->n_params + 1);
+  d->ref_prim.resize(std::max<size_t>(nqs, 1));
+  d->ref_qa.resize(std::max<size_t>(nqs, 1));
+  d->ref_coeff.resize(std::max<size_t>(nqs, 1));
+  std::vector<int> count(D->n_params + 1);
+  host::SlotTables st{d->act.data(), d->nact.data(), d->act_off.data(), d->actc.data(),
+                      d->ref_off.data(), d->ref_prim.data(), d->ref_qa.data(), d->ref_coeff.data(),
+                      d->auxd_off.data(), d->auxf_off.data(), 0, 0, 0, 0};
+  host::build_slots(D, st, count.data());
+  d->st = st;
+  d->ref_prim.resize(std::max(st.nrefs, 1));
+  d->ref_qa.resize(std::max(st.nrefs, 1));
+  d->ref_coeff.resize(std::max(st.nrefs, 1));
+  d->st.ref_prim = d->ref_prim.data();
+  d->st.ref_qa = d->ref_qa.data();
+  d->st.ref_coeff = d->ref_coeff.data();
   d->h_prims.resize(d->n_prims);
-  d->h_auxd.resize(d->auxd_n);
-  d->h_auxf.resize(d->auxf_n);
+  d->h_auxd.resize(std::max(st.auxd_n, 1));
+  d->h_auxf.resize(std::max(st.auxf_n, 1));
   d->q.resize(std::max(d->n_q, 1));
 
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = upload(&d->d_chain, d->chain);
   if (e == cudaSuccess) e = upload(&d->d_act, d->act);
+  if (e == cudaSuccess) e = upload(&d->d_actc, d->actc);
   if (e == cudaSuccess) e = upload(&d->d_ref_off, d->ref_off);
   if (e == cudaSuccess) e = upload(&d->d_ref_prim, d->ref_prim);
   if (e == cudaSuccess) e = upload(&d->d_ref_qa, d->ref_qa);
@@ -431,9 +313,10 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   if (e == cudaSuccess) e = upload(&d->d_prims, d->h_prims);
   if (e == cudaSuccess) e = upload(&d->d_auxd, d->h_auxd);
   if (e == cudaSuccess) e = upload(&d->d_auxf, d->h_auxf);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_progs, sizeof(TileProg) * (size_t)g.T);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_list, sizeof(int) * (size_t)g.T);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_progs, sizeof(TileProg) * (size_t)d->g.T);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_list, sizeof(int) * (size_t)d->g.T);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_counters, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_job, sizeof(Job));
   if (e != cudaSuccess) {
     free_design(d);
     return fail(e == cudaErrorMemoryAllocation ? ADG_ENOMEM : ADG_ECUDA, "adg_design_create: %s",
@@ -453,127 +336,24 @@ extern "C" adg_status adg_design_destroy(adg_ctx* ctx, adg_design* d) {
 // ------------------------------------------------------ parameter map (a1) -
 namespace {
 
-void anchor(double v, int& ai, float& af) {
-  v = std::min(std::max(v, -1e8), 1e8);
-  const double f = floor(v);
-  ai = (int)f;
-  af = (float)(v - f);
-}
-
-// inclusive cell-index range whose samples u = i + off (any component) can
-// fall in [ulo, uhi], clipped to [0, n-1]; empty as lo > hi
-void cell_range(double ulo, double uhi, float offmin, float offmax, int n, int& lo, int& hi) {
-  const double a = floor(ulo - offmax - 1.0), b = ceil(uhi - offmin + 1.0);
-  lo = (int)std::max(0.0, std::min((double)n, a));
-  hi = (int)std::min((double)(n - 1), std::max(-1.0, b));
-}
-
 adg_status prepare_prims(adg_design* d, const double* p) {
-  const GridDev& g = d->g;
-  for (int j = 0; j < d->n_q; ++j) {
-    d->q[j] = d->q_base[j];
-    if (d->q_param[j] >= 0) d->q[j] += d->q_coeff[j] * p[d->q_param[j]];
-    if (!std::isfinite(d->q[j])) return fail(ADG_EINVAL, "geometric scalar %d is not finite", j);
-  }
-  const int nn[3] = {g.nx, g.ny, g.nz};
-  const int lt[3] = {g.lx, g.ly, g.lz};
-  size_t part = 0;
-  for (int pi = 0; pi < d->n_prims; ++pi) {
-    PrimRec R;
-    memset(&R, 0, sizeof(R));
-    R.kind = d->kind[pi];
-    R.sigma = d->sigma[pi];
-    R.flags = d->flags[pi];
-    R.nact = d->nact[pi];
-    R.act_off = d->act_off[pi];
-    R.kr = (float)d->kr[pi];
-    const double beta = kBand[R.sigma] / d->kr[pi];
-    R.band = (float)beta;
-    R.auxd_off = d->auxd_off[pi];
-    R.auxf_off = d->auxf_off[pi];
-    const double* Q = d->q.data() + d->q0[pi];
-    auto cellc = [&](double v, int ax) { return (v - d->o[ax]) / d->d[ax]; };
-    int vlo[3], vhi[3], plo[3], phi[3];
-    for (int a = 0; a < 3; ++a) { vlo[a] = 0; vhi[a] = nn[a] - 1; }
-    auto zrange = [&]() {
-      if (!(R.flags & kBoundZ)) return;
-      const double a = cellc(Q[R.kind == kCircle ? 3 : 0], 2);
-      const double b = cellc(Q[R.kind == kCircle ? 4 : 1], 2);
-      anchor(a, R.ai[4], R.af[4]);
-      anchor(b, R.ai[5], R.af[5]);
-      cell_range(a - 0.5, b + 0.5, g.offmin[2], g.offmax[2], g.nz, vlo[2], vhi[2]);
-    };
-    if (R.kind == kBox) {
-      for (int ax = 0; ax < 3; ++ax) {
-        if (!(R.flags & (1 << ax))) continue;
-        const double a = cellc(Q[2 * ax], ax), b = cellc(Q[2 * ax + 1], ax);
-        anchor(a, R.ai[2 * ax], R.af[2 * ax]);
-        anchor(b, R.ai[2 * ax + 1], R.af[2 * ax + 1]);
-        const double w = (R.flags & kRectSigma) ? beta : 0.5;
-        cell_range(a - w, b + w, g.offmin[ax], g.offmax[ax], nn[ax], vlo[ax], vhi[ax]);
-      }
-      for (int a = 0; a < 3; ++a) { plo[a] = vlo[a]; phi[a] = vhi[a]; }
-    } else if (R.kind == kCircle) {
-      const double cx = cellc(Q[0], 0), cy = cellc(Q[1], 1), Rc = Q[2] / d->d[0];
-      anchor(cx, R.ai[0], R.af[0]);
-      anchor(cy, R.ai[1], R.af[1]);
-      const double R2 = Rc * Rc;
-      R.g[0] = (float)Rc;
-      R.g[1] = (float)R2;
-      R.g[2] = (float)(R2 - (double)R.g[1]);
-      R.g[3] = Rc < 0 ? 1.f : 0.f;
-      const double ext = fabs(Rc) + beta;
-      cell_range(cx - ext, cx + ext, g.offmin[0], g.offmax[0], g.nx, vlo[0], vhi[0]);
-      cell_range(cy - ext, cy + ext, g.offmin[1], g.offmax[1], g.ny, vlo[1], vhi[1]);
-      zrange();
-      for (int a = 0; a < 3; ++a) { plo[a] = vlo[a]; phi[a] = vhi[a]; }
-    } else {  // graph
-      const int M = (d->nq[pi] - 2) / 2;
-      R.naux = M;
-      double* X = d->h_auxd.data() + R.auxd_off;
-      double* Y = X + M;
-      double* iX = Y + M;
-      float* Xf = d->h_auxf.data() + R.auxf_off;
-      double ymin = 1e300, ymax = -1e300;
-      for (int j = 0; j < M; ++j) {
-        X[j] = cellc(Q[2 + j], 0);
-        Y[j] = cellc(Q[2 + M + j], 1);
-        Xf[j] = (float)X[j];
-        ymin = std::min(ymin, Y[j]);
-        ymax = std::max(ymax, Y[j]);
-        if (j > 0 && !(X[j] > X[j - 1]))
-          return fail(ADG_EINVAL, "graph %d: knots must increase strictly in x", pi);
-      }
-      for (int j = 0; j + 1 < M; ++j) iX[j] = 1.0 / (X[j + 1] - X[j]);
-      iX[M - 1] = 0.0;
-      zrange();
-      for (int a = 0; a < 3; ++a) { plo[a] = vlo[a]; phi[a] = vhi[a]; }
-      int lo, hi;
-      cell_range(ymin - beta, ymax + beta, g.offmin[1], g.offmax[1], g.ny, lo, hi);
-      plo[1] = lo;
-      phi[1] = hi;
-      if (R.flags & kGraphAbove) vlo[1] = lo; else vhi[1] = hi;
-    }
-    int np = 1;
-    for (int a = 0; a < 3; ++a) {
-      if (vlo[a] > vhi[a]) { R.tb[2 * a] = 0; R.tb[2 * a + 1] = 0; }
-      else { R.tb[2 * a] = vlo[a] >> lt[a]; R.tb[2 * a + 1] = (vhi[a] >> lt[a]) + 1; }
-      if (plo[a] > phi[a]) { R.pb[2 * a] = 0; R.pb[2 * a + 1] = 0; }
-      else { R.pb[2 * a] = plo[a] >> lt[a]; R.pb[2 * a + 1] = (phi[a] >> lt[a]) + 1; }
-      np *= R.pb[2 * a + 1] - R.pb[2 * a];
-    }
-    R.npb = R.nact > 0 ? np : 0;
-    R.part_off = (int)part;
-    part += (size_t)R.nact * R.npb;
-    if (part > (size_t)1 << 31) return fail(ADG_EINVAL, "partial buffer exceeds 2^31 entries");
-    d->h_prims[pi] = R;
-  }
-  d->part_total = part;
+  host::Msg m;
+  if (host::map_params(d->n_q, d->q_base.data(), d->q_coeff.data(), d->q_param.data(), p,
+                       d->q.data(), m) != ADG_OK)
+    return fail(ADG_EINVAL, "%s", m.text);
+  host::PrimTable P{d->kind.data(), d->sigma.data(), d->flags.data(), d->q0.data(), d->nq.data(),
+                    d->kr.data(), d->n_prims};
+  if (host::prepare_prims(d->g, d->d, d->o, P, d->st, d->q.data(), d->h_prims.data(),
+                          d->h_auxd.data(), d->h_auxf.data(), &d->part_total, m) != ADG_OK)
+    return fail(ADG_EINVAL, "%s", m.text);
   return ADG_OK;
 }
 
-adg_status ensure_bins(adg_ctx* ctx, adg_design* d, const double* h_params, cudaStream_t s) {
+// Parameter map + record upload when the parameters changed since the last
+// binning of this design; *rebin tells whether the binner must run.
+adg_status ensure_records(adg_design* d, const double* h_params, cudaStream_t s, bool* rebin) {
   if (d->n_params > 0 && !h_params) return fail(ADG_EINVAL, "h_params is NULL");
+  *rebin = false;
   if (d->bins_valid && (int)d->last_params.size() == d->n_params &&
       (d->n_params == 0 ||
        memcmp(d->last_params.data(), h_params, sizeof(double) * d->n_params) == 0))
@@ -583,22 +363,19 @@ adg_status ensure_bins(adg_ctx* ctx, adg_design* d, const double* h_params, cuda
   if (st != ADG_OK) return st;
   CU(cudaMemcpyAsync(d->d_prims, d->h_prims.data(), sizeof(PrimRec) * d->n_prims,
                      cudaMemcpyHostToDevice, s));
-  if (d->auxd_n)
-    CU(cudaMemcpyAsync(d->d_auxd, d->h_auxd.data(), sizeof(double) * d->auxd_n,
+  if (d->st.auxd_n)
+    CU(cudaMemcpyAsync(d->d_auxd, d->h_auxd.data(), sizeof(double) * d->st.auxd_n,
                        cudaMemcpyHostToDevice, s));
-  if (d->auxf_n)
-    CU(cudaMemcpyAsync(d->d_auxf, d->h_auxf.data(), sizeof(float) * d->auxf_n,
+  if (d->st.auxf_n)
+    CU(cudaMemcpyAsync(d->d_auxf, d->h_auxf.data(), sizeof(float) * d->st.auxf_n,
                        cudaMemcpyHostToDevice, s));
-  CU(cudaMemsetAsync(d->d_counters, 0, sizeof(int) * 4, s));
-  ProfScope ps(ctx, ADG_K_BIN, s);
-  CU(launch_bin(d->g, d->d_chain, d->d_prims, d->d_auxf, d->d_auxd, d->d_progs, d->d_list,
-                d->d_counters, ctx->d_err, s));
   d->last_params.assign(h_params, h_params + d->n_params);
   d->bins_valid = true;
+  *rebin = true;
   return ADG_OK;
 }
 
-adg_status run_vjp(adg_ctx* ctx, adg_design* d, const VjpArgs& va, float* d_grad, cudaStream_t s) {
+adg_status ensure_partials(adg_design* d, cudaStream_t s) {
   if (d->part_total > d->partial_cap) {
     if (d->d_partial) CU(cudaFreeAsync(d->d_partial, s));
     d->d_partial = nullptr;
@@ -606,17 +383,87 @@ adg_status run_vjp(adg_ctx* ctx, adg_design* d, const VjpArgs& va, float* d_grad
     CU(cudaMallocAsync((void**)&d->d_partial, cap * sizeof(float), s));
     d->partial_cap = cap;
   }
-  if (d->part_total) CU(cudaMemsetAsync(d->d_partial, 0, d->part_total * sizeof(float), s));
-  const int grid = ctx->sms * vjp_blocks_per_sm();
-  {
-    ProfScope ps(ctx, ADG_K_VJP, s);
-    CU(launch_vjp(d->g, d->d_progs, d->d_list, d->d_counters, d->d_prims, d->d_act, d->d_auxf,
-                  d->d_auxd, va, d->d_partial, ctx->d_err, grid, s));
-  }
-  ProfScope ps(ctx, ADG_K_FINALIZE, s);
-  CU(launch_finalize(d->n_params, d->d_ref_off, d->d_ref_prim, d->d_ref_qa, d->d_ref_coeff,
-                     d->d_prims, d->d_partial, d_grad, s));
   return ADG_OK;
+}
+
+// The job of one design (device pointers of its tables and bins).
+Job design_job(adg_design* d) {
+  Job J{};
+  J.g = d->g;
+  J.chain = d->d_chain;
+  J.prims = d->d_prims;
+  J.act = d->d_act;
+  J.actc = d->d_actc;
+  J.auxf = d->d_auxf;
+  J.auxd = d->d_auxd;
+  J.ref_off = d->d_ref_off;
+  J.ref_prim = d->d_ref_prim;
+  J.ref_qa = d->d_ref_qa;
+  J.ref_coeff = d->d_ref_coeff;
+  J.progs = d->d_progs;
+  J.list = d->d_list;
+  J.counters = d->d_counters;
+  J.partial = d->d_partial;
+  J.partial_n = (long long)d->part_total;
+  J.nparam = d->n_params;
+  return J;
+}
+
+// Enqueue prepare -> bin -> build / VJP -> finalize for a job table.
+adg_status run_jobs(adg_ctx* ctx, const Job* d_jobs, const JobTotals& t, bool any_bin,
+                    bool any_build, bool any_grad, int max_tiles, cudaStream_t s) {
+  if (any_bin || any_grad) {
+    ProfScope ps(ctx, ADG_K_PREPARE, s);
+    CU(launch_prepare(d_jobs, t, s));
+  }
+  if (any_bin) {
+    ProfScope ps(ctx, ADG_K_BIN, s);
+    CU(launch_bin(d_jobs, t, ctx->d_err, s));
+  }
+  if (any_build) {
+    const int grid = std::max(1, std::min(max_tiles, ctx->sms * build_blocks_per_sm()));
+    ProfScope ps(ctx, ADG_K_BUILD, s);
+    CU(launch_build(d_jobs, t, grid, s));
+  }
+  if (any_grad) {
+    {
+      ProfScope ps(ctx, ADG_K_VJP, s);
+      CU(launch_vjp(d_jobs, t, ctx->d_err, ctx->sms * vjp_blocks_per_sm(), s));
+    }
+    ProfScope ps(ctx, ADG_K_FINALIZE, s);
+    CU(launch_finalize(d_jobs, t, s));
+  }
+  return ADG_OK;
+}
+
+adg_status run_single(adg_ctx* ctx, adg_design* d, const double* h_params, float* d_fill,
+                      float* d_eps, const VjpArgs* va, float* d_grad, cudaStream_t s) {
+  bool rebin = false;
+  adg_status st = ensure_records(d, h_params, s, &rebin);
+  if (st != ADG_OK) return st;
+  const bool grad = va != nullptr;
+  if (grad) {
+    st = ensure_partials(d, s);
+    if (st != ADG_OK) return st;
+  }
+  Job J = design_job(d);
+  J.do_bin = rebin ? 1 : 0;
+  J.do_build = d_eps ? 1 : 0;
+  J.do_grad = grad ? 1 : 0;
+  J.fill = d_fill;
+  J.eps = d_eps;
+  if (grad) J.va = *va;
+  J.grad = d_grad;
+  J.partial_n = grad ? (long long)d->part_total : 0;
+  d->job = J;
+  CU(cudaMemcpyAsync(d->d_job, &d->job, sizeof(Job), cudaMemcpyHostToDevice, s));
+  JobTotals t{};
+  t.njobs = 1;
+  t.tiles_padded = ((d->g.T + 127) / 128) * 128;
+  t.bin_blocks = t.tiles_padded / 128;
+  t.params = grad ? d->n_params : 0;
+  t.partials = J.partial_n;
+  return run_jobs(ctx, d->d_job, t, rebin, d_eps != nullptr, grad, d->g.T, s);
 }
 
 }  // namespace
@@ -626,13 +473,7 @@ extern "C" adg_status adg_build_eps(adg_ctx* ctx, adg_design* d, const double* h
                                     float* d_fill, float* d_eps, void* stream) {
   if (!ctx || !d || !d_eps) return fail(ADG_EINVAL, "adg_build_eps: NULL argument");
   CU(cudaSetDevice(ctx->device));
-  cudaStream_t s = (cudaStream_t)stream;
-  adg_status st = ensure_bins(ctx, d, h_params, s);
-  if (st != ADG_OK) return st;
-  const int grid = std::min(d->g.T, ctx->sms * build_blocks_per_sm());
-  ProfScope ps(ctx, ADG_K_BUILD, s);
-  CU(launch_build(d->g, d->d_progs, d->d_prims, d->d_auxf, d->d_auxd, d_fill, d_eps, grid, s));
-  return ADG_OK;
+  return run_single(ctx, d, h_params, d_fill, d_eps, nullptr, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" adg_status adg_grad(adg_ctx* ctx, adg_design* d, const double* h_params,
@@ -649,10 +490,7 @@ extern "C" adg_status adg_grad(adg_ctx* ctx, adg_design* d, const double* h_para
   }
   va.G = nullptr;
   CU(cudaSetDevice(ctx->device));
-  cudaStream_t s = (cudaStream_t)stream;
-  adg_status st = ensure_bins(ctx, d, h_params, s);
-  if (st != ADG_OK) return st;
-  return run_vjp(ctx, d, va, d_grad, s);
+  return run_single(ctx, d, h_params, nullptr, nullptr, &va, d_grad, (cudaStream_t)stream);
 }
 
 extern "C" adg_status adg_grad_real(adg_ctx* ctx, adg_design* d, const double* h_params,
@@ -662,10 +500,221 @@ extern "C" adg_status adg_grad_real(adg_ctx* ctx, adg_design* d, const double* h
   VjpArgs va{};
   va.G = d_G;
   CU(cudaSetDevice(ctx->device));
+  return run_single(ctx, d, h_params, nullptr, nullptr, &va, d_grad, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ batches -
+namespace {
+
+size_t al256(size_t v) { return (v + 255) & ~size_t(255); }
+
+uint64_t mix(uint64_t h, uint64_t v) {
+  h ^= v + 0x9e3779b97f4a7c15ULL + (h << 6) + (h >> 2);
+  return h;
+}
+
+}  // namespace
+
+extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items, int32_t n,
+                                       int32_t flags, void* stream, uint64_t* ticket) {
+  if (!ctx || !items || !ticket) return fail(ADG_EINVAL, "adg_batch_submit: NULL argument");
+  if (n < 1 || n > kMaxJobs) return fail(ADG_EINVAL, "batch of %d items (1..%d)", n, kMaxJobs);
+  if (flags & ~ADG_BATCH_GRAPH) return fail(ADG_EINVAL, "unknown batch flags 0x%x", flags);
   cudaStream_t s = (cudaStream_t)stream;
-  adg_status st = ensure_bins(ctx, d, h_params, s);
-  if (st != ADG_OK) return st;
-  return run_vjp(ctx, d, va, d_grad, s);
+  CU(cudaSetDevice(ctx->device));
+  for (int i = 0; i < n; ++i) {
+    const adg_batch_item& it = items[i];
+    adg_design* d = it.design;
+    if (!d || d->ctx != ctx) return fail(ADG_EINVAL, "item %d: design missing or of another context", i);
+    if (it.reserved != 0 || it.ops <= 0 || (it.ops & ~7) ||
+        ((it.ops & ADG_BATCH_GRAD) && (it.ops & ADG_BATCH_GRAD_REAL)))
+      return fail(ADG_EINVAL, "item %d: ops 0x%x invalid", i, it.ops);
+    if ((it.ops & ADG_BATCH_BUILD) && !it.d_eps) return fail(ADG_EINVAL, "item %d: d_eps is NULL", i);
+    if ((it.ops & (ADG_BATCH_GRAD | ADG_BATCH_GRAD_REAL)) && !it.d_grad && d->n_params > 0)
+      return fail(ADG_EINVAL, "item %d: d_grad is NULL", i);
+    if ((it.ops & ADG_BATCH_GRAD_REAL) && !it.d_G) return fail(ADG_EINVAL, "item %d: d_G is NULL", i);
+    if (it.ops & ADG_BATCH_GRAD)
+      for (int c = 0; c < d->g.C; ++c)
+        if (!it.d_efwd[c] || !it.d_eadj[c]) return fail(ADG_EINVAL, "item %d: field %d is NULL", i, c);
+    if (d->n_params > 0 && !it.h_params) return fail(ADG_EINVAL, "item %d: h_params is NULL", i);
+    for (int k = 0; k < i; ++k)
+      if (items[k].design == d) return fail(ADG_EINVAL, "items %d and %d share a design", k, i);
+  }
+  adg_ctx::Arena& A = ctx->arenas[ctx->next_arena];
+  const int arena_id = ctx->next_arena;
+  ctx->next_arena ^= 1;
+  if (A.used) CU(cudaEventSynchronize(A.done));  // the batch two back released this arena
+  // parameter maps (host, FP64) and sizes of the packed upload
+  size_t nprim = 0, nauxd = 0, nauxf = 0;
+  for (int i = 0; i < n; ++i) {
+    adg_design* d = items[i].design;
+    adg_status st = prepare_prims(d, items[i].h_params);
+    if (st != ADG_OK) return st;
+    d->bins_valid = false;  // the batch re-bins this design with its own records
+    if (items[i].ops & (ADG_BATCH_GRAD | ADG_BATCH_GRAD_REAL)) {
+      st = ensure_partials(d, s);
+      if (st != ADG_OK) return st;
+    }
+    nprim += d->n_prims;
+    nauxd += d->st.auxd_n;
+    nauxf += d->st.auxf_n;
+  }
+  const size_t o_jobs = 0;
+  const size_t o_prims = al256(o_jobs + sizeof(Job) * n);
+  const size_t o_auxd = al256(o_prims + sizeof(PrimRec) * nprim);
+  const size_t o_auxf = al256(o_auxd + sizeof(double) * nauxd);
+  const size_t bytes = al256(o_auxf + sizeof(float) * nauxf);
+  if (bytes > A.cap) {
+    if (A.exec) { cudaGraphExecDestroy(A.exec); A.exec = nullptr; A.sig = 0; }
+    cudaFree(A.d);
+    cudaFreeHost(A.h);
+    A.d = nullptr;
+    A.h = nullptr;
+    A.cap = 0;
+    const size_t cap = bytes + bytes / 2 + 4096;
+    CU(cudaMalloc(&A.d, cap));
+    CU(cudaMallocHost(&A.h, cap));
+    A.cap = cap;
+  }
+  if (!A.done) CU(cudaEventCreateWithFlags(&A.done, cudaEventDisableTiming));
+  unsigned char* hb = static_cast<unsigned char*>(A.h);
+  unsigned char* db = static_cast<unsigned char*>(A.d);
+  Job* hj = reinterpret_cast<Job*>(hb + o_jobs);
+  size_t po = 0, ado = 0, afo = 0;
+  int tile_base = 0, param_base = 0, max_tiles = 0;
+  long long partial_base = 0;
+  bool any_build = false, any_grad = false;
+  uint64_t sig = mix(0, (uint64_t)arena_id);
+  sig = mix(sig, (uint64_t)n);
+  for (int i = 0; i < n; ++i) {
+    const adg_batch_item& it = items[i];
+    adg_design* d = it.design;
+    PrimRec* hp = reinterpret_cast<PrimRec*>(hb + o_prims) + po;
+    memcpy(hp, d->h_prims.data(), sizeof(PrimRec) * d->n_prims);
+    if (d->st.auxd_n)
+      memcpy(reinterpret_cast<double*>(hb + o_auxd) + ado, d->h_auxd.data(), sizeof(double) * d->st.auxd_n);
+    if (d->st.auxf_n)
+      memcpy(reinterpret_cast<float*>(hb + o_auxf) + afo, d->h_auxf.data(), sizeof(float) * d->st.auxf_n);
+    Job J = design_job(d);
+    J.prims = reinterpret_cast<const PrimRec*>(db + o_prims) + po;
+    J.auxd = reinterpret_cast<const double*>(db + o_auxd) + ado;
+    J.auxf = reinterpret_cast<const float*>(db + o_auxf) + afo;
+    J.do_bin = 1;
+    J.do_build = (it.ops & ADG_BATCH_BUILD) ? 1 : 0;
+    J.do_grad = (it.ops & (ADG_BATCH_GRAD | ADG_BATCH_GRAD_REAL)) ? 1 : 0;
+    J.fill = it.d_fill;
+    J.eps = it.d_eps;
+    J.grad = it.d_grad;
+    if (it.ops & ADG_BATCH_GRAD) {
+      for (int c = 0; c < d->g.C; ++c) {
+        J.va.ef[c] = reinterpret_cast<const float2*>(it.d_efwd[c]);
+        J.va.ea[c] = reinterpret_cast<const float2*>(it.d_eadj[c]);
+        J.va.w[c] = make_float2(it.w[2 * c], it.w[2 * c + 1]);
+      }
+    } else if (it.ops & ADG_BATCH_GRAD_REAL) {
+      J.va.G = it.d_G;
+    }
+    J.partial_n = J.do_grad ? (long long)d->part_total : 0;
+    J.partial_base = partial_base;
+    J.param_base = param_base;
+    J.tile_base = tile_base;
+    partial_base += J.partial_n;
+    if (J.do_grad) param_base += d->n_params;
+    tile_base += ((d->g.T + 127) / 128) * 128;
+    max_tiles = std::max(max_tiles, d->g.T);
+    any_build = any_build || J.do_build;
+    any_grad = any_grad || J.do_grad;
+    hj[i] = J;
+    po += d->n_prims;
+    ado += d->st.auxd_n;
+    afo += d->st.auxf_n;
+    sig = mix(sig, (uint64_t)d->g.T);
+    sig = mix(sig, (uint64_t)it.ops);
+  }
+  JobTotals t{};
+  t.njobs = n;
+  t.tiles_padded = tile_base;
+  t.bin_blocks = tile_base / 128;
+  t.params = param_base;
+  t.partials = partial_base;
+  sig = mix(sig, (uint64_t)bytes);
+  sig = mix(sig, (uint64_t)tile_base);
+  sig = mix(sig, (uint64_t)param_base);
+  sig = mix(sig, (uint64_t)std::min<long long>((partial_base + 255) / 256, 4096));
+  build_blocks_per_sm();
+  vjp_blocks_per_sm();
+  const bool graph = (flags & ADG_BATCH_GRAPH) && !ctx->prof;
+  if (graph && A.exec && A.sig == sig) {
+    CU(cudaGraphLaunch(A.exec, s));
+  } else if (graph) {
+    if (A.exec) { cudaGraphExecDestroy(A.exec); A.exec = nullptr; A.sig = 0; }
+    // capture on the context's own stream (the legacy default stream cannot
+    // be captured); the graph itself is launched on the caller's stream
+    if (!ctx->capture) CU(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
+    cudaStream_t cs = ctx->capture;
+    CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemcpyAsync(A.d, A.h, bytes, cudaMemcpyHostToDevice, cs);
+    adg_status st = e == cudaSuccess ? run_jobs(ctx, reinterpret_cast<const Job*>(db + o_jobs), t,
+                                                true, any_build, any_grad, max_tiles, cs)
+                                     : ADG_ECUDA;
+    cudaGraph_t gr = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+    if (st != ADG_OK) { if (gr) cudaGraphDestroy(gr); return st; }
+    if (e != cudaSuccess || e2 != cudaSuccess)
+      return fail(ADG_ECUDA, "batch capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    e = cudaGraphInstantiate(&A.exec, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) { A.exec = nullptr; return fail(ADG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+    A.sig = sig;
+    CU(cudaGraphLaunch(A.exec, s));
+  } else {
+    CU(cudaMemcpyAsync(A.d, A.h, bytes, cudaMemcpyHostToDevice, s));
+    adg_status st = run_jobs(ctx, reinterpret_cast<const Job*>(db + o_jobs), t, true, any_build,
+                             any_grad, max_tiles, s);
+    if (st != ADG_OK) return st;
+  }
+  CU(cudaEventRecord(A.done, s));
+  A.used = true;
+  cudaEvent_t ev = nullptr;
+  CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CU(cudaEventRecord(ev, s));
+  const uint64_t id = ctx->next_ticket++;
+  ctx->tickets.push_back({id, ev});
+  *ticket = id;
+  return ADG_OK;
+}
+
+extern "C" adg_status adg_batch_poll(adg_ctx* ctx, uint64_t ticket, int32_t* done) {
+  if (!ctx || !done) return fail(ADG_EINVAL, "adg_batch_poll: NULL argument");
+  CU(cudaSetDevice(ctx->device));
+  for (size_t k = 0; k < ctx->tickets.size(); ++k) {
+    if (ctx->tickets[k].id != ticket) continue;
+    const cudaError_t e = cudaEventQuery(ctx->tickets[k].ev);
+    if (e == cudaErrorNotReady) { *done = 0; return ADG_OK; }
+    cudaEventDestroy(ctx->tickets[k].ev);
+    ctx->tickets.erase(ctx->tickets.begin() + k);
+    if (e != cudaSuccess) return fail(ADG_ECUDA, "batch %llu: %s", (unsigned long long)ticket, cudaGetErrorString(e));
+    *done = 1;
+    return ADG_OK;
+  }
+  if (ticket == 0 || ticket >= ctx->next_ticket) return fail(ADG_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+  *done = 1;  // already collected
+  return ADG_OK;
+}
+
+extern "C" adg_status adg_batch_wait(adg_ctx* ctx, uint64_t ticket, uint64_t timeout_ns) {
+  if (!ctx) return fail(ADG_EINVAL, "adg_batch_wait: NULL context");
+  const auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    int32_t done = 0;
+    adg_status st = adg_batch_poll(ctx, ticket, &done);
+    if (st != ADG_OK || done) return st;
+    const auto el = std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0);
+    if ((uint64_t)el.count() >= timeout_ns)
+      return fail(ADG_ETIMEOUT, "batch %llu still running after %llu ns", (unsigned long long)ticket,
+                  (unsigned long long)timeout_ns);
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
 }
 
 extern "C" adg_status adg_sync(adg_ctx* ctx, void* stream) {

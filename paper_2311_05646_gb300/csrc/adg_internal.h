@@ -9,12 +9,14 @@ namespace adg {
 // Per-tile capacities of the binned kernels.  A tile that would exceed one of
 // them is reported through the device error word (never written out of range).
 constexpr int kMaxLeaves = 48;  // primitives whose edge band crosses the tile
-constexpr int kMaxOps = 48;     // folded logic program length
+constexpr int kMaxOps = 32;     // folded logic program length
 constexpr int kMaxDepth = 32;   // fold stack depth (checked at design creation)
 constexpr int kMaxSlots = 384;  // (primitive, active scalar) accumulators
 constexpr int kMaxPairs = 8;    // nonzero d s / d q terms one cell yields per leaf
 constexpr int kBlock = 128;     // threads per CTA of the build / VJP kernels
+constexpr int kMaxTileCells = 1024;  // cells per tile (per component)
 constexpr int kWarps = kBlock / 32;
+constexpr int kMaxPolyVerts = 256;  // vertices of one convex polygon
 
 enum : int32_t { kBox = 0, kCircle = 1, kPolygon = 2, kGraph = 3 };
 enum : int32_t { kLinear = 0, kSigmoid = 1, kQuadratic = 2, kSin = 3, kErf = 4 };
@@ -43,6 +45,7 @@ struct GridDev {
   float eps_bg, deps;
   int logic;
   int nchain;
+  int nprims;
 };
 
 // One primitive after the parameter map, in cell units of each axis:
@@ -52,7 +55,7 @@ struct alignas(16) PrimRec {
   int kind, sigma, flags, nact;
   float kr;    // sigma_k(x) = sigma(kr * x / d): kr in per-cell units
   float band;  // transition half-width in cells (beyond it sigma is 0/1, flat)
-  int act_off; // act table: act[act_off + local q] = active slot, or -1
+  int act_off; // act[act_off + local q] = accumulator slot (or -1), actc = its coefficient
   int auxd_off, auxf_off, naux;
   int part_off;  // first partial of this primitive
   int npb;       // tiles in the partial box
@@ -60,7 +63,7 @@ struct alignas(16) PrimRec {
   int pb[6];     // tile box of the derivative support (partials)
   int ai[6];     // box: x0,x1,y0,y1,z0,z1; circle: cx, cy in [0],[1]; z0,z1 in [4],[5]
   float af[6];
-  float g[4];  // circle: R, R^2 (hi, lo) in cells; [3] = 1 if R < 0
+  float g[4];  // circle: R, R^2 (hi, lo) in cells, [3] = 1 if R < 0; polygon: [0] = winding sign
 };
 
 struct TileProg {
@@ -79,19 +82,55 @@ struct VjpArgs {
   const float* G;  // real-seed mode when non-null
 };
 
-cudaError_t launch_bin(const GridDev& g, const int* chain, const PrimRec* prims,
-                       const float* auxf, const double* auxd, TileProg* progs, int* list,
-                       int* counters, int* err, cudaStream_t s);
-cudaError_t launch_build(const GridDev& g, const TileProg* progs, const PrimRec* prims,
-                         const float* auxf, const double* auxd, float* fill, float* eps,
-                         int grid, cudaStream_t s);
-cudaError_t launch_vjp(const GridDev& g, const TileProg* progs, const int* list,
-                       const int* counters, const PrimRec* prims, const int* act,
-                       const float* auxf, const double* auxd, const VjpArgs& a,
-                       float* partial, int* err, int grid, cudaStream_t s);
-cudaError_t launch_finalize(int nparam, const int* ref_off, const int* ref_prim,
-                            const int* ref_qa, const double* ref_coeff, const PrimRec* prims,
-                            const float* partial, float* grad, cudaStream_t s);
+// One unit of device work: one design with the operations asked of it.  All
+// kernels take a table of jobs; a single-design call is a one-job table and a
+// batch of designs of uneven size runs through the same launches.
+struct Job {
+  GridDev g;
+  // design tables
+  const int* chain;
+  const PrimRec* prims;
+  const int* act;
+  const float* actc;
+  const float* auxf;
+  const double* auxd;
+  const int* ref_off;
+  const int* ref_prim;
+  const int* ref_qa;
+  const double* ref_coeff;
+  // bins
+  TileProg* progs;
+  int* list;
+  int* counters;
+  // outputs and inputs of the operations
+  float* fill;
+  float* eps;
+  VjpArgs va;
+  float* partial;
+  float* grad;
+  long long partial_n;     // partials to zero before the VJP
+  long long partial_base;  // prefix over the table (zeroing kernel)
+  int nparam;
+  int param_base;  // prefix over the table (finalize)
+  int tile_base;   // prefix over the table, multiple of 128 (binner blocks)
+  int do_bin, do_build, do_grad;
+};
+
+struct JobTotals {
+  int njobs;
+  int bin_blocks;        // sum over binned jobs of ceil(T / 128)
+  int tiles_padded;      // tile_base of one past the last job
+  int params;            // sum of nparam over gradient jobs
+  long long partials;    // sum of partial_n over gradient jobs
+};
+
+constexpr int kMaxJobs = 1024;  // jobs in one table (one batch)
+
+cudaError_t launch_prepare(const Job* jobs, const JobTotals& t, cudaStream_t s);
+cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s);
+cudaError_t launch_build(const Job* jobs, const JobTotals& t, int grid, cudaStream_t s);
+cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int grid, cudaStream_t s);
+cudaError_t launch_finalize(const Job* jobs, const JobTotals& t, cudaStream_t s);
 int build_blocks_per_sm();
 int vjp_blocks_per_sm();
 void set_last_error(const char* msg);  // the thread-local text of adg_last_error()

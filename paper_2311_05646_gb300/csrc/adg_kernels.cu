@@ -16,6 +16,9 @@
 //               the parameter map (deterministic, FP64).
 #include <limits.h>
 #include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
 
 #include "adg_internal.h"
 
@@ -74,13 +77,24 @@ struct Cell {
   float ox, oy, oz;
 };
 
+// Exact int -> float for |v| < 2^22 by the IEEE-754 magic-number method:
+// placing v in the mantissa of 1.5 * 2^23 (integer add) and subtracting that
+// constant (float add).  Both run on the integer / FP32 pipes; a plain
+// conversion instruction goes through a much narrower pipe on this part.
+// Larger |v| are clamped: such a coordinate difference lies far outside any
+// sample window, so its clamped value gives the same overlap / sigma.
+__device__ __forceinline__ float i2f(int v) {
+  v = min(max(v, -(1 << 21)), 1 << 21);
+  return __int_as_float(v + 0x4B400000) - 12582912.0f;
+}
+
 // Exact fraction of the cell window [u - 1/2, u + 1/2] covered by [a, b]
 // (Sec. 5.1, Eq. linear), a = ai0 + af0, b = ai1 + af1, u = i + off; da, db
 // are its derivatives w.r.t. a and b in cells.
 __device__ __forceinline__ float ov_exact(int ai0, float af0, int ai1, float af1, int i,
                                           float off, float& da, float& db) {
-  const float ta = (float)(ai0 - i) + (af0 - off);
-  const float tb = (float)(ai1 - i) + (af1 - off);
+  const float ta = i2f(ai0 - i) + (af0 - off);
+  const float tb = i2f(ai1 - i) + (af1 - off);
   const float len = fminf(tb, 0.5f) - fmaxf(ta, -0.5f);
   if (len > 0.f) {
     da = (ta >= -0.5f) ? -1.f : 0.f;
@@ -108,8 +122,8 @@ __device__ __forceinline__ void box_axes(const PrimRec& P, const Cell& c, float 
     f[ax] = 1.f; fa[ax] = 0.f; fb[ax] = 0.f;
     if (!(P.flags & (1 << ax))) continue;
     if (P.flags & kRectSigma) {
-      const float ta = (float)(P.ai[2 * ax] - idx[ax]) + (P.af[2 * ax] - off[ax]);
-      const float tb = (float)(P.ai[2 * ax + 1] - idx[ax]) + (P.af[2 * ax + 1] - off[ax]);
+      const float ta = i2f(P.ai[2 * ax] - idx[ax]) + (P.af[2 * ax] - off[ax]);
+      const float tb = i2f(P.ai[2 * ax + 1] - idx[ax]) + (P.af[2 * ax + 1] - off[ax]);
       float d1, d2;
       const float s1 = sigma_f(P.sigma, -P.kr * ta, d1);
       const float s2 = sigma_f(P.sigma, P.kr * tb, d2);
@@ -127,7 +141,7 @@ __device__ __forceinline__ void box_axes(const PrimRec& P, const Cell& c, float 
 // so that d keeps ~1e-7-cell accuracy for radii of hundreds of cells.
 __device__ __forceinline__ float circle_dist(const PrimRec& P, const Cell& c, float& dxr,
                                              float& dyr, float& r) {
-  const float fxi = (float)(c.i - P.ai[0]), fyi = (float)(c.j - P.ai[1]);
+  const float fxi = i2f(c.i - P.ai[0]), fyi = i2f(c.j - P.ai[1]);
   const float dxf = c.ox - P.af[0], dyf = c.oy - P.af[1];
   const float ii2 = fxi * fxi + fyi * fyi;
   const float cr = 2.f * (fxi * dxf + fyi * dyf) + (dxf * dxf + dyf * dyf);
@@ -152,8 +166,9 @@ __device__ __forceinline__ int graph_seg(const float* Xf, int M, float ux) {
   return lo;
 }
 
-// signed vertical distance f(x) - y (or y - f(x)) in cells, FP64 where it cancels
-__device__ __forceinline__ float graph_dist(const PrimRec& P, const Cell& c, const float* auxf,
+// signed vertical distance f(x) - y (or y - f(x)) in cells, FP64 where it cancels.
+// Not inlined: its FP64 conversions must not be hoisted into the box path.
+__device__ __noinline__ float graph_dist(const PrimRec& P, const Cell& c, const float* auxf,
                                             const double* auxd, int& seg, double& t) {
   const int M = P.naux;
   const double* X = auxd + P.auxd_off;
@@ -171,6 +186,25 @@ __device__ __forceinline__ float graph_dist(const PrimRec& P, const Cell& c, con
   }
   const double d = f - ((double)c.j + (double)c.oy);
   return (float)((P.flags & kGraphAbove) ? -d : d);
+}
+
+// Poly2D: signed distance of the sample to edge e's line, inward positive, in
+// cells (FP64 line equation: coordinates reach thousands of cells).
+__device__ __forceinline__ float poly_edge_dist(const double* A, int N, int e, double ux, double uy) {
+  const double* NX = A + 2 * N;
+  const double* NY = NX + N;
+  const double* C = NY + N;
+  return (float)(fma(NX[e], ux, fma(NY[e], uy, -C[e])));
+}
+
+__device__ __noinline__ float poly_value(const PrimRec& P, const Cell& c, const double* auxd) {
+  const int N = P.naux;
+  const double* A = auxd + P.auxd_off;
+  const double ux = (double)c.i + (double)c.ox, uy = (double)c.j + (double)c.oy;
+  float prod = 1.f, ds;
+  for (int e = 0; e < N && prod != 0.f; ++e)
+    prod *= sigma_f(P.sigma, P.kr * poly_edge_dist(A, N, e, ux, uy), ds);
+  return prod;
 }
 
 __device__ __forceinline__ float leaf_value(const PrimRec& P, const Cell& c, const float* auxf,
@@ -195,15 +229,23 @@ __device__ __forceinline__ float leaf_value(const PrimRec& P, const Cell& c, con
     const float d = graph_dist(P, c, auxf, auxd, seg, t);
     return sigma_f(P.sigma, P.kr * d, ds) * zf;
   }
-  return 0.f;
+  return poly_value(P, c, auxd) * zf;
 }
 
 // Nonzero d s / d q (physical units) of one leaf at one cell, times `a`, as
 // (active slot, value) pairs in ascending slot order.  Columns of stride kBlock.
-__device__ __forceinline__ int push_pair(const int* actp, int key, float v, int n, int* pk,
-                                         float* pv) {
+// Slots are per (primitive, parameter): a scalar's term is scaled by its
+// coefficient and merged with the previous pair when both hit the same slot.
+__device__ __forceinline__ int push_pair(const int* actp, const float* actcp, int key, float v,
+                                         int n, int* pk, float* pv) {
   const int s = actp[key];
-  if (s >= 0 && v != 0.f && n < kMaxPairs) {
+  if (s < 0 || v == 0.f) return n;
+  v *= actcp[key];
+  if (n > 0 && pk[(n - 1) * kBlock] == s) {
+    pv[(n - 1) * kBlock] += v;
+    return n;
+  }
+  if (n < kMaxPairs) {
     pk[n * kBlock] = s;
     pv[n * kBlock] = v;
     return n + 1;
@@ -211,10 +253,48 @@ __device__ __forceinline__ int push_pair(const int* actp, int key, float v, int 
   return n;
 }
 
-__device__ int leaf_pairs(const PrimRec& P, const Cell& c, float a, const GridDev& g,
-                          const int* act, const float* auxf, const double* auxd, int* pk,
-                          float* pv) {
+// GeneralCartesian2D derivative pairs (z0, z1, X_j, X_j+1, Y_j, Y_j+1).  Not
+// inlined, like graph_dist, to keep its FP64 work off the box path.
+__device__ __noinline__ int graph_pairs(const PrimRec& P, const Cell& c, float a, const GridDev& g,
+                                      const int* actp, const float* actcp, const float* auxf,
+                                      const double* auxd, int* pk, float* pv) {
+  int n = 0;
+  float dz0, dz1, ds;
+  const float zf = zfactor(P, c, dz0, dz1);
+  int seg;
+  double t;
+  const float d = graph_dist(P, c, auxf, auxd, seg, t);
+  const float s = sigma_f(P.sigma, P.kr * d, ds);
+  const float sgn = (P.flags & kGraphAbove) ? -1.f : 1.f;
+  const float gg = P.kr * ds * zf * sgn * a;  // d s / d f (per y-cell) times a
+  const int M = P.naux;
+  n = push_pair(actp, actcp, 0, s * dz0 * a * g.invd[2], n, pk, pv);
+  n = push_pair(actp, actcp, 1, s * dz1 * a * g.invd[2], n, pk, pv);
+  if (seg < 0) {
+    n = push_pair(actp, actcp, 2 + M, gg * g.invd[1], n, pk, pv);
+  } else if (seg >= M - 1) {
+    n = push_pair(actp, actcp, 2 + M + M - 1, gg * g.invd[1], n, pk, pv);
+  } else {
+    const double* X = auxd + P.auxd_off;
+    const double* Y = X + M;
+    const double* iX = Y + M;
+    const double ux = (double)c.i + (double)c.ox;
+    const float dY = (float)(Y[seg + 1] - Y[seg]);
+    const float ix = (float)iX[seg];
+    const float e0 = (float)(ux - X[seg + 1]), e1 = (float)(ux - X[seg]);
+    n = push_pair(actp, actcp, 2 + seg, gg * dY * e0 * ix * ix * g.invd[0], n, pk, pv);
+    n = push_pair(actp, actcp, 3 + seg, -gg * dY * e1 * ix * ix * g.invd[0], n, pk, pv);
+    n = push_pair(actp, actcp, 2 + M + seg, gg * (float)(1.0 - t) * g.invd[1], n, pk, pv);
+    n = push_pair(actp, actcp, 3 + M + seg, gg * (float)t * g.invd[1], n, pk, pv);
+  }
+  return n;
+}
+
+__device__ __forceinline__ int leaf_pairs(const PrimRec& P, const Cell& c, float a, const GridDev& g,
+                          const int* act, const float* actc, const float* auxf,
+                          const double* auxd, int* pk, float* pv) {
   const int* actp = act + P.act_off;
+  const float* actcp = actc + P.act_off;
   int n = 0;
   if (P.kind == kBox) {
     float f[3], fa[3], fb[3];
@@ -222,8 +302,8 @@ __device__ int leaf_pairs(const PrimRec& P, const Cell& c, float a, const GridDe
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
       const float other = f[(ax + 1) % 3] * f[(ax + 2) % 3] * a * g.invd[ax];
-      n = push_pair(actp, 2 * ax, fa[ax] * other, n, pk, pv);
-      n = push_pair(actp, 2 * ax + 1, fb[ax] * other, n, pk, pv);
+      n = push_pair(actp, actcp, 2 * ax, fa[ax] * other, n, pk, pv);
+      n = push_pair(actp, actcp, 2 * ax + 1, fb[ax] * other, n, pk, pv);
     }
     return n;
   }
@@ -236,43 +316,20 @@ __device__ int leaf_pairs(const PrimRec& P, const Cell& c, float a, const GridDe
     const float s = sigma_f(P.sigma, P.kr * d, ds);
     const float gg = P.kr * ds * zf * a * g.invd[0];
     const float ir = r > 0.f ? 1.f / r : 0.f;
-    n = push_pair(actp, 0, gg * dxr * ir, n, pk, pv);
-    n = push_pair(actp, 1, gg * dyr * ir, n, pk, pv);
-    n = push_pair(actp, 2, gg, n, pk, pv);
-    n = push_pair(actp, 3, s * dz0 * a * g.invd[2], n, pk, pv);
-    n = push_pair(actp, 4, s * dz1 * a * g.invd[2], n, pk, pv);
+    n = push_pair(actp, actcp, 0, gg * dxr * ir, n, pk, pv);
+    n = push_pair(actp, actcp, 1, gg * dyr * ir, n, pk, pv);
+    n = push_pair(actp, actcp, 2, gg, n, pk, pv);
+    n = push_pair(actp, actcp, 3, s * dz0 * a * g.invd[2], n, pk, pv);
+    n = push_pair(actp, actcp, 4, s * dz1 * a * g.invd[2], n, pk, pv);
     return n;
   }
-  if (P.kind == kGraph) {
-    int seg;
-    double t;
-    const float d = graph_dist(P, c, auxf, auxd, seg, t);
-    const float s = sigma_f(P.sigma, P.kr * d, ds);
-    const float sgn = (P.flags & kGraphAbove) ? -1.f : 1.f;
-    const float gg = P.kr * ds * zf * sgn * a;  // d s / d f (per y-cell) times a
-    const int M = P.naux;
-    n = push_pair(actp, 0, s * dz0 * a * g.invd[2], n, pk, pv);
-    n = push_pair(actp, 1, s * dz1 * a * g.invd[2], n, pk, pv);
-    if (seg < 0) {
-      n = push_pair(actp, 2 + M, gg * g.invd[1], n, pk, pv);
-    } else if (seg >= M - 1) {
-      n = push_pair(actp, 2 + M + M - 1, gg * g.invd[1], n, pk, pv);
-    } else {
-      const double* X = auxd + P.auxd_off;
-      const double* Y = X + M;
-      const double* iX = Y + M;
-      const double ux = (double)c.i + (double)c.ox;
-      const float dY = (float)(Y[seg + 1] - Y[seg]);
-      const float ix = (float)iX[seg];
-      const float e0 = (float)(ux - X[seg + 1]), e1 = (float)(ux - X[seg]);
-      n = push_pair(actp, 2 + seg, gg * dY * e0 * ix * ix * g.invd[0], n, pk, pv);
-      n = push_pair(actp, 3 + seg, -gg * dY * e1 * ix * ix * g.invd[0], n, pk, pv);
-      n = push_pair(actp, 2 + M + seg, gg * (float)(1.0 - t) * g.invd[1], n, pk, pv);
-      n = push_pair(actp, 3 + M + seg, gg * (float)t * g.invd[1], n, pk, pv);
-    }
-    return n;
-  }
-  return 0;
+  if (P.kind == kGraph) return graph_pairs(P, c, a, g, actp, actcp, auxf, auxd, pk, pv);
+  // polygon: only the extrusion scalars here; vertices go through poly_accumulate
+  if (actp[0] < 0 && actp[1] < 0) return n;
+  const float s = poly_value(P, c, auxd);
+  n = push_pair(actp, actcp, 0, s * dz0 * a * g.invd[2], n, pk, pv);
+  n = push_pair(actp, actcp, 1, s * dz1 * a * g.invd[2], n, pk, pv);
+  return n;
 }
 
 // ------------------------------------------------------------------ logic ---
@@ -327,7 +384,7 @@ __device__ __forceinline__ int cls_sigma(float a, float b, float beta, float lo,
   return cBND;
 }
 
-__device__ int classify(const PrimRec& P, const float lo[3], const float hi[3],
+__device__ __forceinline__ int classify(const PrimRec& P, const float lo[3], const float hi[3],
                         const double* auxd) {
   int z = cIN;
   if (P.kind != kBox && (P.flags & kBoundZ))
@@ -382,7 +439,7 @@ __device__ int classify(const PrimRec& P, const float lo[3], const float hi[3],
       if (X[j] > lo[0] && X[j] < hi[0]) { fmn = fmin(fmn, Y[j]); fmx = fmax(fmx, Y[j]); }
     const float b = P.band + kMargin;
     if (!(P.flags & kGraphAbove)) {  // region y < f(x)
-      if ((float)fmx - hi[1] < -b && (float)fmx - lo[1] < -b) return cOUT;
+      if ((float)fmx - lo[1] < -b) return cOUT;
       if ((float)fmn - hi[1] > b) return cls_and(cIN, z);
     } else {                          // region y > f(x)
       if (hi[1] - (float)fmn < -b) return cOUT;
@@ -390,43 +447,202 @@ __device__ int classify(const PrimRec& P, const float lo[3], const float hi[3],
     }
     return cBND;
   }
+  if (P.kind == kPolygon) {
+    const int N = P.naux;
+    const double* A = auxd + P.auxd_off;
+    const double* NX = A + 2 * N;
+    const double* NY = NX + N;
+    const double* C = NY + N;
+    const double b = (double)P.band + kMargin;
+    bool all_in = true;
+    for (int e = 0; e < N; ++e) {
+      // extremes of the edge's line function over the tile's sample box
+      const double ax = NX[e] >= 0 ? NX[e] * lo[0] : NX[e] * hi[0];
+      const double bx = NX[e] >= 0 ? NX[e] * hi[0] : NX[e] * lo[0];
+      const double ay = NY[e] >= 0 ? NY[e] * lo[1] : NY[e] * hi[1];
+      const double by = NY[e] >= 0 ? NY[e] * hi[1] : NY[e] * lo[1];
+      const double dmin = ax + ay - C[e], dmax = bx + by - C[e];
+      if (dmax < -b) return cOUT;
+      if (dmin <= b) all_in = false;
+    }
+    return all_in ? cls_and(cIN, z) : cBND;
+  }
   return cBND;
 }
 
-// --------------------------------------------------------------- kernels ---
-// Fold-stack entry: kind (0 = const 0, 1 = const 1, 2 = expression) | root << 2
-// | start << 10 (root: position of the expression's last op; start: its first).
-__device__ __forceinline__ int mkE(int root, int start) { return 2 | (root << 2) | (start << 10); }
+// Vertex derivatives of one Poly2D leaf at one sample, accumulated edge by
+// edge.  s = zf prod_e sigma(k d_e); d s / d d_e uses the product of the other
+// factors (with an exact zero count, no division by zero).  Each edge adds to
+// the slots of its two vertices' x and y scalars; slots are warp-uniform, so a
+// two-entry register cache merges consecutive edges on the same parameter
+// (a translated polygon needs two warp reductions per sample, not 4 N).
+__device__ __forceinline__ void flush_slot(int& slot, float& v, float* acc, float* cmp, int lane);
 
-__global__ void __launch_bounds__(128) k_bin(GridDev g, const int* __restrict__ chain,
-                                             const PrimRec* __restrict__ prims,
-                                             const float* __restrict__ auxf,
-                                             const double* __restrict__ auxd,
-                                             TileProg* __restrict__ progs, int* __restrict__ list,
-                                             int* __restrict__ counters, int* __restrict__ err) {
-  __shared__ int stk[kMaxDepth][128];
-  __shared__ uint16_t sleaf[kMaxLeaves][128];
+__device__ __noinline__ void poly_accumulate(const PrimRec& P, const Cell& c, float a, const GridDev& g,
+                                const int* act, const float* actc, const double* auxd,
+                                float* acc, float* cmp, int lane) {
+  const int N = P.naux;
+  const double* A = auxd + P.auxd_off;
+  const double* X = A;
+  const double* Y = A + N;
+  const double* IL = A + 5 * N;
+  const int* actp = act + P.act_off;
+  const float* actcp = actc + P.act_off;
+  const double ux = (double)c.i + (double)c.ox, uy = (double)c.j + (double)c.oy;
+  float dz0, dz1;
+  const float zf = a != 0.f ? zfactor(P, c, dz0, dz1) : 0.f;
+  float prod = 1.f, ds;
+  int nz = 0;
+  if (zf != 0.f) {
+    for (int e = 0; e < N; ++e) {
+      const float s = sigma_f(P.sigma, P.kr * poly_edge_dist(A, N, e, ux, uy), ds);
+      if (s == 0.f) { if (++nz > 1) break; }
+      else prod *= s;
+    }
+  }
+  const bool live = zf != 0.f && nz <= 1;
+  const float sgn = P.g[0];
+  const float scale = a * zf * P.kr * g.invd[0];
+  int cs0 = -1, cs1 = -1;
+  float cv0 = 0.f, cv1 = 0.f;
+  for (int e = 0; e < N; ++e) {
+    const int e1 = e + 1 == N ? 0 : e + 1;
+    float ge = 0.f, d = 0.f;
+    if (live) {
+      d = poly_edge_dist(A, N, e, ux, uy);
+      const float se = sigma_f(P.sigma, P.kr * d, ds);
+      const float other = nz == 0 ? prod / se : (se == 0.f ? prod : 0.f);
+      ge = scale * ds * other;
+    }
+    if (!__any_sync(0xffffffffu, ge != 0.f)) continue;
+    // d(d_e)/d(x_e, y_e, x_e1, y_e1) in cells (see the oracle's Poly2D)
+    const float ex = (float)(X[e1] - X[e]), ey = (float)(Y[e1] - Y[e]);
+    const float rx = (float)(ux - X[e]), ry = (float)(uy - Y[e]);
+    const float il = (float)IL[e];
+    const float dil = d * il * il;
+    const float t[4] = {sgn * (ey - ry) * il + dil * ex, sgn * (rx - ex) * il + dil * ey,
+                        sgn * ry * il - dil * ex, -sgn * rx * il - dil * ey};
+    const int key[4] = {2 + 2 * e, 3 + 2 * e, 2 + 2 * e1, 3 + 2 * e1};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int slot = actp[key[u]];
+      if (slot < 0) continue;
+      const float v = ge * t[u] * actcp[key[u]];
+      if (slot == cs0) cv0 += v;
+      else if (slot == cs1) cv1 += v;
+      else {
+        flush_slot(cs0, cv0, acc, cmp, lane);
+        cs0 = cs1; cv0 = cv1;
+        cs1 = slot; cv1 = v;
+      }
+    }
+  }
+  flush_slot(cs0, cv0, acc, cmp, lane);
+  flush_slot(cs1, cv1, acc, cmp, lane);
+}
+
+// --------------------------------------------------------------- kernels ---
+// Fold-stack entry (16 bits): kind (0 = const 0, 1 = const 1, 2 = expression)
+// | root << 2 | start << 8 (root: position of the expression's last op;
+// start: its first; both < kMaxOps <= 64).
+__device__ __forceinline__ int mkE(int root, int start) { return 2 | (root << 2) | (start << 8); }
+
+// First job whose range end exceeds idx (ends are nondecreasing).
+__device__ __forceinline__ int job_by_tile(const Job* jobs, int n, int idx) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const Job& J = jobs[mid];
+    const int end = J.tile_base + (((J.g.T + 127) >> 7) << 7);
+    if (end > idx) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int job_by_param(const Job* jobs, int n, int idx) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const Job& J = jobs[mid];
+    if (J.param_base + (J.do_grad ? J.nparam : 0) > idx) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int job_by_partial(const Job* jobs, int n, long long idx) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const Job& J = jobs[mid];
+    if (J.partial_base + (J.do_grad ? J.partial_n : 0) > idx) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Zero what the binner and the VJP accumulate into: the counters of jobs that
+// re-bin and the partials of jobs that take a gradient.
+__global__ void k_prepare(const Job* __restrict__ jobs, int njobs) {
+  // the partial count comes from the table itself (graph replays reuse the grid)
+  const Job& L = jobs[njobs - 1];
+  const long long npart = L.partial_base + (L.do_grad ? L.partial_n : 0);
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = i0; i < njobs; i += stride)
+    if (jobs[i].do_bin)
+      for (int k = 0; k < 4; ++k) jobs[i].counters[k] = 0;
+  for (long long i = i0; i < npart; i += stride) {
+    const Job& J = jobs[job_by_partial(jobs, njobs, i)];
+    J.partial[i - J.partial_base] = 0.f;
+  }
+}
+
+// One thread per tile; the block's 128 tiles belong to one job (tile ranges
+// are padded to multiples of 128).
+constexpr int kChainSmem = 1536, kBoxSmem = 320;
+
+// The fold of one tile (one thread).  SMEM: the chain and the tile boxes are
+// staged in the block's shared memory (small designs); otherwise they are
+// read through the read-only path.  The folded program is built in shared
+// memory and written out once, so the loop itself never stores to global.
+template <bool SMEM>
+__device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain, const int (*stb)[6],
+                                         uint16_t (*stk)[128], uint16_t (*sleaf)[128],
+                                         uint16_t (*sop)[128], int* err) {
   const int tid = threadIdx.x;
-  const int t = blockIdx.x * blockDim.x + tid;
-  if (t >= g.T) return;
-  const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
-  const int i0 = tx << g.lx, j0 = ty << g.ly, k0 = tz << g.lz;
-  const int i1 = min(g.nx, (tx + 1) << g.lx), j1 = min(g.ny, (ty + 1) << g.ly),
-            k1 = min(g.nz, (tz + 1) << g.lz);
-  const float lo[3] = {i0 + g.offmin[0], j0 + g.offmin[1], k0 + g.offmin[2]};
-  const float hi[3] = {(i1 - 1) + g.offmax[0], (j1 - 1) + g.offmax[1], (k1 - 1) + g.offmax[2]};
-  TileProg* out = progs + t;
+  const int nchain = J.g.nchain, ntx = J.g.ntx, nty = J.g.nty;
+  const int lx = J.g.lx, ly = J.g.ly, lz = J.g.lz;
+  const int* __restrict__ chain = J.chain;
+  const PrimRec* __restrict__ prims = J.prims;
+  const double* __restrict__ auxd = J.auxd;
+  const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
+  const int i0 = tx << lx, j0 = ty << ly, k0 = tz << lz;
+  const int i1 = min(J.g.nx, (tx + 1) << lx), j1 = min(J.g.ny, (ty + 1) << ly),
+            k1 = min(J.g.nz, (tz + 1) << lz);
+  const float lo[3] = {i0 + J.g.offmin[0], j0 + J.g.offmin[1], k0 + J.g.offmin[2]};
+  const float hi[3] = {(i1 - 1) + J.g.offmax[0], (j1 - 1) + J.g.offmax[1], (k1 - 1) + J.g.offmax[2]};
   int nops = 0, nleaf = 0, sp = 0, e = 0;
-  for (int w = 0; w < g.nchain; ++w) {
-    const int word = chain[w];
+  for (int w = 0; w < nchain; ++w) {
+    const int word = SMEM ? schain[w] : __ldg(chain + w);
     const int code = (word >> 24) & 0xff, arg = word & 0xffffff;
-    int ent = 0;
     if (code == cPush) {
-      const PrimRec& P = prims[arg];
-      int cl = cOUT;
-      if (tx >= P.tb[0] && tx < P.tb[1] && ty >= P.tb[2] && ty < P.tb[3] && tz >= P.tb[4] &&
-          tz < P.tb[5])
-        cl = classify(P, lo, hi, auxd);
+      int b0, b1, b2, b3, b4, b5;
+      if (SMEM) {
+        b0 = stb[arg][0]; b1 = stb[arg][1]; b2 = stb[arg][2];
+        b3 = stb[arg][3]; b4 = stb[arg][4]; b5 = stb[arg][5];
+      } else {
+        const int* tb = prims[arg].tb;
+        b0 = __ldg(tb); b1 = __ldg(tb + 1); b2 = __ldg(tb + 2);
+        b3 = __ldg(tb + 3); b4 = __ldg(tb + 4); b5 = __ldg(tb + 5);
+      }
+      const bool cand = tx >= b0 && tx < b1 && ty >= b2 && ty < b3 && tz >= b4 && tz < b5;
+      if (!cand && w + 1 < nchain) {
+        // a primitive outside the tile is 0: union(A, 0) = A and
+        // difference(A, 0) = A, so the pair leaves the stack as it is
+        const int nc = ((SMEM ? schain[w + 1] : __ldg(chain + w + 1)) >> 24) & 0xff;
+        if ((nc == cUnion || nc == cDiff) && sp >= 1) { ++w; continue; }
+      }
+      const int cl = cand ? classify(prims[arg], lo, hi, auxd) : cOUT;
+      int ent = 0;
       if (cl == cBND) {
         int slot = -1;
         for (int l = 0; l < nleaf; ++l)
@@ -436,25 +652,24 @@ __global__ void __launch_bounds__(128) k_bin(GridDev g, const int* __restrict__ 
           else e |= eLeafOverflow;
         }
         if (slot >= 0 && nops < kMaxOps) {
-          out->ops[nops] = (uint16_t)(fPush | (slot << 3));
+          sop[nops][tid] = (uint16_t)(fPush | (slot << 3));
           ent = mkE(nops, nops);
           ++nops;
         } else {
           e |= eOpsOverflow;
-          ent = 0;
         }
       } else {
         ent = (cl == cIN) ? 1 : 0;
       }
-      if (sp < kMaxDepth) stk[sp++][tid] = ent;
+      if (sp < kMaxDepth) stk[sp++][tid] = (uint16_t)ent;
       else e |= eDepthOverflow;
     } else {
       if (sp < 2) { e |= eBadProgram; break; }
       const int B = stk[--sp][tid];
       const int A = stk[--sp][tid];
       const int ka = A & 3, kb = B & 3;
-      const int ra = (A >> 2) & 0xff, sa = (A >> 10) & 0xff;
-      const int rb = (B >> 2) & 0xff, sb = (B >> 10) & 0xff;
+      const int ra = (A >> 2) & 63, sa = (A >> 8) & 63;
+      const int rb = (B >> 2) & 63, sb = (B >> 8) & 63;
       int res = 0, emit = -1, unary = 0;
       bool discard = false;
       if (code == cUnion) {
@@ -480,10 +695,10 @@ __global__ void __launch_bounds__(128) k_bin(GridDev g, const int* __restrict__ 
       if (emit >= 0) {
         if (nops < kMaxOps) {
           if (unary) {
-            out->ops[nops] = (uint16_t)(fCompl | (rb << 3));
+            sop[nops][tid] = (uint16_t)(fCompl | (rb << 3));
             res = mkE(nops, sb);
           } else {
-            out->ops[nops] = (uint16_t)(emit | (ra << 3) | (rb << 9));
+            sop[nops][tid] = (uint16_t)(emit | (ra << 3) | (rb << 9));
             res = mkE(nops, sa);
           }
           ++nops;
@@ -492,18 +707,20 @@ __global__ void __launch_bounds__(128) k_bin(GridDev g, const int* __restrict__ 
           res = 0;
         }
       }
-      stk[sp++][tid] = res;
+      stk[sp++][tid] = (uint16_t)res;
     }
   }
   if (sp != 1) e |= eBadProgram;
   const int fin = sp >= 1 ? stk[sp - 1][tid] : 0;
   float cval = 0.f;
-  if ((fin & 3) != 2) { nops = 0; cval = (float)(fin & 3); }
+  if ((fin & 3) != 2) { nops = 0; cval = (fin & 3) ? 1.f : 0.f; }
+  TileProg* out = J.progs + t;
   int nslot = 0;
   for (int l = 0; l < nleaf; ++l) {
     out->leaf[l] = sleaf[l][tid];
     nslot += prims[sleaf[l][tid]].nact;
   }
+  for (int q = 0; q < nops; ++q) out->ops[q] = sop[q][tid];
   if (nops > 0 && nslot > kMaxSlots) e |= eSlotOverflow;
   if (e) {
     atomicOr(err, e);
@@ -515,11 +732,36 @@ __global__ void __launch_bounds__(128) k_bin(GridDev g, const int* __restrict__ 
   out->cval = cval;
   out->nslot = nslot;
   if (nops > 0) {
+    int* counters = J.counters;
     const int idx = atomicAdd(&counters[0], 1);
-    list[idx] = t;
+    J.list[idx] = t;
     atomicMax(&counters[1], nops);
     atomicAdd(&counters[2], (i1 - i0) * (j1 - j0) * (k1 - k0));
   }
+}
+
+// One thread per tile; the block's 128 tiles belong to one job (tile ranges
+// are padded to multiples of 128).
+__global__ void __launch_bounds__(128) k_bin(const Job* __restrict__ jobs, int njobs,
+                                             int* __restrict__ err) {
+  __shared__ uint16_t stk[kMaxDepth][128];
+  __shared__ uint16_t sleaf[kMaxLeaves][128];
+  __shared__ uint16_t sop[kMaxOps][128];
+  __shared__ int schain[kChainSmem];
+  __shared__ int stb[kBoxSmem][6];
+  const int tid = threadIdx.x;
+  const Job& J = jobs[job_by_tile(jobs, njobs, blockIdx.x * 128)];
+  if (!J.do_bin) return;  // uniform over the block
+  const bool smem = J.g.nchain <= kChainSmem && J.g.nprims <= kBoxSmem;
+  if (smem) {
+    for (int q = tid; q < J.g.nchain; q += blockDim.x) schain[q] = J.chain[q];
+    for (int q = tid; q < J.g.nprims * 6; q += blockDim.x) stb[q / 6][q % 6] = J.prims[q / 6].tb[q % 6];
+  }
+  __syncthreads();
+  const int t = blockIdx.x * 128 + tid - J.tile_base;
+  if (t >= J.g.T) return;
+  if (smem) bin_tile<true>(J, t, schain, stb, stk, sleaf, sop, err);
+  else bin_tile<false>(J, t, schain, stb, stk, sleaf, sop, err);
 }
 
 __device__ __forceinline__ void stage_tile(const TileProg* P, const PrimRec* prims, int nops,
@@ -532,45 +774,252 @@ __device__ __forceinline__ void stage_tile(const TileProg* P, const PrimRec* pri
   }
 }
 
+// ---- per-tile factor tables ------------------------------------------------
+// Late projection to the grid (Sec. 3, item (iii)): a leaf's value factors as
+// s(c, x, y, z) = A(c, x, y) * Z(c, z), and for a box A = X(c, x) * Y(c, y)
+// (Table 4: RectdD is a product of Rect1D factors; Sec. 5.2: planarity is a
+// z factor).  Each tile evaluates every factor once per (component,
+// coordinate) into shared memory; a sample's leaf value is then two or three
+// table reads.  Leaves that do not fit the table pool are evaluated directly.
+struct LeafTab {
+  int x, y, z, xy;  // value tables (offsets in floats), -1 if absent
+  int dx, dy, dz;   // derivative tables (lo, hi per component), -1 if absent
+  int ok;
+};
+
+// Thread 0: assign table offsets for the tile's leaves within `cap` floats.
+__device__ __forceinline__ void tables_plan(const PrimRec* sl, int nleaf, const GridDev& g,
+                                            bool derivs, int cap, LeafTab* lt) {
+  const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
+  int off = 0;
+  for (int l = 0; l < nleaf; ++l) {
+    LeafTab t{-1, -1, -1, -1, -1, -1, -1, 0};
+    const int m = derivs ? 3 : 1;
+    if (sl[l].kind == kBox) {
+      const int need = m * C * (TX + TY + TZ);
+      if (off + need <= cap) {
+        t.x = off; t.y = t.x + C * TX; t.z = t.y + C * TY;
+        if (derivs) { t.dx = t.z + C * TZ; t.dy = t.dx + 2 * C * TX; t.dz = t.dy + 2 * C * TY; }
+        t.ok = 1;
+        off += need;
+      }
+    } else {
+      const int need = C * TX * TY + m * C * TZ;
+      if (off + need <= cap) {
+        t.xy = off; t.z = t.xy + C * TX * TY;
+        if (derivs) t.dz = t.z + C * TZ;
+        t.ok = 1;
+        off += need;
+      }
+    }
+    lt[l] = t;
+  }
+}
+
+// Axis factor of a box along axis `ax` at cell index i with offset off:
+// exact overlap, or the paper's sigma product; unbounded axes give 1.
+__device__ __forceinline__ float box_axis(const PrimRec& P, int ax, int i, float off, float& da,
+                                          float& db) {
+  if (!(P.flags & (1 << ax))) { da = 0.f; db = 0.f; return 1.f; }
+  if (P.flags & kRectSigma) {
+    const float ta = i2f(P.ai[2 * ax] - i) + (P.af[2 * ax] - off);
+    const float tb = i2f(P.ai[2 * ax + 1] - i) + (P.af[2 * ax + 1] - off);
+    float d1, d2;
+    const float s1 = sigma_f(P.sigma, -P.kr * ta, d1);
+    const float s2 = sigma_f(P.sigma, P.kr * tb, d2);
+    da = -P.kr * d1 * s2;
+    db = s1 * P.kr * d2;
+    return s1 * s2;
+  }
+  return ov_exact(P.ai[2 * ax], P.af[2 * ax], P.ai[2 * ax + 1], P.af[2 * ax + 1], i, off, da, db);
+}
+
+// In-plane factor of a circle / graph / polygon at (i, j) (no z factor).
+__device__ __forceinline__ float plane_value(const PrimRec& P, const Cell& c, const float* auxf,
+                                             const double* auxd) {
+  float ds;
+  if (P.kind == kCircle) {
+    float dxr, dyr, r;
+    return sigma_f(P.sigma, P.kr * circle_dist(P, c, dxr, dyr, r), ds);
+  }
+  if (P.kind == kGraph) {
+    int seg;
+    double t;
+    return sigma_f(P.sigma, P.kr * graph_dist(P, c, auxf, auxd, seg, t), ds);
+  }
+  return poly_value(P, c, auxd);
+}
+
+// All threads: fill the planned tables of the tile with origin (X0, Y0, Z0).
+__device__ __forceinline__ void tables_fill(const PrimRec* sl, int nleaf, const GridDev& g,
+                                            const LeafTab* lt, bool derivs, int X0, int Y0,
+                                            int Z0, float* tab, int tid, const float* auxf,
+                                            const double* auxd) {
+  const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
+  const int T3[3] = {TX, TY, TZ};
+  const int O3[3] = {X0, Y0, Z0};
+  for (int l = 0; l < nleaf; ++l) {
+    const LeafTab t = lt[l];
+    if (!t.ok) continue;
+    const PrimRec& P = sl[l];
+    if (P.kind == kBox) {
+      const int tot = C * (TX + TY + TZ);
+      for (int e = tid; e < tot; e += kBlock) {
+        int ax = 0, r = e;
+        while (ax < 2 && r >= C * T3[ax]) { r -= C * T3[ax]; ++ax; }
+        const int c = r / T3[ax], u = r - c * T3[ax];
+        float da, db;
+        const float f = box_axis(P, ax, O3[ax] + u, g.off[c][ax], da, db);
+        const int vt = ax == 0 ? t.x : (ax == 1 ? t.y : t.z);
+        tab[vt + c * T3[ax] + u] = f;
+        if (derivs) {
+          const int dt = ax == 0 ? t.dx : (ax == 1 ? t.dy : t.dz);
+          tab[dt + (2 * c) * T3[ax] + u] = da;
+          tab[dt + (2 * c + 1) * T3[ax] + u] = db;
+        }
+      }
+    } else {
+      const int nxy = C * TX * TY;
+      for (int e = tid; e < nxy + C * TZ; e += kBlock) {
+        if (e < nxy) {
+          const int c = e / (TX * TY), r = e - c * TX * TY, v = r / TX, u = r - v * TX;
+          const Cell cc{X0 + u, Y0 + v, Z0, g.off[c][0], g.off[c][1], g.off[c][2]};
+          tab[t.xy + e] = plane_value(P, cc, auxf, auxd);
+        } else {
+          const int r = e - nxy, c = r / TZ, u = r - c * TZ;
+          const Cell cc{X0, Y0, Z0 + u, g.off[c][0], g.off[c][1], g.off[c][2]};
+          float dz0, dz1;
+          tab[t.z + r] = zfactor(P, cc, dz0, dz1);
+          if (derivs) {
+            tab[t.dz + (2 * c) * TZ + u] = dz0;
+            tab[t.dz + (2 * c + 1) * TZ + u] = dz1;
+          }
+        }
+      }
+    }
+  }
+}
+
+struct TileLoc {
+  int x, y, z, c;  // local coordinates of the sample in the tile
+  int TX, TY, TZ;
+};
+
+__device__ __forceinline__ float tab_value(const LeafTab& t, bool box, const TileLoc& q,
+                                           const float* tab) {
+  const float fz = tab[t.z + q.c * q.TZ + q.z];
+  if (box) return tab[t.x + q.c * q.TX + q.x] * tab[t.y + q.c * q.TY + q.y] * fz;
+  return tab[t.xy + (q.c * q.TY + q.y) * q.TX + q.x] * fz;
+}
+
 __device__ __forceinline__ float eval_forward(const uint16_t* sops, int nops, const PrimRec* sl,
-                                              const Cell& cc, int logic, float* tape, int tid,
-                                              const float* auxf, const double* auxd) {
+                                              const LeafTab* lt, const float* tab,
+                                              const TileLoc& q, const Cell& cc, int logic,
+                                              float* tape, int tid, const float* auxf,
+                                              const double* auxd) {
   float v = 0.f;
   for (int pos = 0; pos < nops; ++pos) {
     const int op = sops[pos];
     const int code = op & 7, a = (op >> 3) & 63, b = (op >> 9) & 63;
-    if (code == fPush) v = leaf_value(sl[a], cc, auxf, auxd);
-    else v = op_fwd(code, logic, tape[a * kBlock + tid], code == fCompl ? 0.f : tape[b * kBlock + tid]);
+    if (code == fPush) {
+      const LeafTab t = lt[a];
+      v = t.ok ? tab_value(t, t.xy < 0, q, tab) : leaf_value(sl[a], cc, auxf, auxd);
+    } else {
+      v = op_fwd(code, logic, tape[a * kBlock + tid], code == fCompl ? 0.f : tape[b * kBlock + tid]);
+    }
     tape[pos * kBlock + tid] = v;
   }
   return v;
 }
 
-constexpr size_t kBuildSmem = (size_t)kMaxOps * kBlock * 4 + kMaxLeaves * sizeof(PrimRec) +
-                              kMaxOps * 2 + 16;
+// Derivative pairs of a tabled box leaf at one sample (keys 0..5 = x0..z1).
+__device__ __forceinline__ int box_tab_pairs(const PrimRec& P, const LeafTab& t, const TileLoc& q,
+                                             const float* tab, float a, const GridDev& g,
+                                             const int* act, const float* actc, int* pk,
+                                             float* pv) {
+  const int* actp = act + P.act_off;
+  const float* actcp = actc + P.act_off;
+  const float fx = tab[t.x + q.c * q.TX + q.x], fy = tab[t.y + q.c * q.TY + q.y],
+              fz = tab[t.z + q.c * q.TZ + q.z];
+  int n = 0;
+  const float ax = a * fy * fz * g.invd[0], ay = a * fx * fz * g.invd[1], az = a * fx * fy * g.invd[2];
+  n = push_pair(actp, actcp, 0, tab[t.dx + (2 * q.c) * q.TX + q.x] * ax, n, pk, pv);
+  n = push_pair(actp, actcp, 1, tab[t.dx + (2 * q.c + 1) * q.TX + q.x] * ax, n, pk, pv);
+  n = push_pair(actp, actcp, 2, tab[t.dy + (2 * q.c) * q.TY + q.y] * ay, n, pk, pv);
+  n = push_pair(actp, actcp, 3, tab[t.dy + (2 * q.c + 1) * q.TY + q.y] * ay, n, pk, pv);
+  n = push_pair(actp, actcp, 4, tab[t.dz + (2 * q.c) * q.TZ + q.z] * az, n, pk, pv);
+  n = push_pair(actp, actcp, 5, tab[t.dz + (2 * q.c + 1) * q.TZ + q.z] * az, n, pk, pv);
+  return n;
+}
 
-__global__ void __launch_bounds__(kBlock) k_build(GridDev g, const TileProg* __restrict__ progs,
-                                                  const PrimRec* __restrict__ prims,
-                                                  const float* __restrict__ auxf,
-                                                  const double* __restrict__ auxd,
-                                                  float* __restrict__ fill, float* __restrict__ eps) {
+constexpr int kBuildTab = 4096;  // floats of factor tables per tile (build)
+constexpr int kVjpTab = 4096;    // floats of factor tables per tile (VJP, values + derivatives)
+constexpr size_t kBuildSmem = (size_t)kMaxOps * kBlock * 4 + kMaxLeaves * sizeof(PrimRec) +
+                              (size_t)kBuildTab * 4 + kMaxLeaves * sizeof(LeafTab) + kMaxOps * 2 +
+                              16;
+
+__global__ void __launch_bounds__(kBlock) k_build(const Job* __restrict__ jobs, int njobs,
+                                                  int tiles_padded) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* tape = reinterpret_cast<float*>(smem);
   PrimRec* sl = reinterpret_cast<PrimRec*>(tape + kMaxOps * kBlock);
-  uint16_t* sops = reinterpret_cast<uint16_t*>(sl + kMaxLeaves);
+  float* tab = reinterpret_cast<float*>(sl + kMaxLeaves);
+  LeafTab* lt = reinterpret_cast<LeafTab*>(tab + kBuildTab);
+  uint16_t* sops = reinterpret_cast<uint16_t*>(lt + kMaxLeaves);
+  __shared__ int sjob;
   const int tid = threadIdx.x;
-  const int lxy = g.lx + g.ly, lxyz = lxy + g.lz;
-  const int ncc = g.C << lxyz;
-  const size_t plane = (size_t)g.nx * g.ny * g.nz;
-  for (int t = blockIdx.x; t < g.T; t += gridDim.x) {
-    const TileProg* P = progs + t;
+  for (int gt = blockIdx.x; gt < tiles_padded; gt += gridDim.x) {
+    __syncthreads();  // the previous tile is done with sjob and the staged program
+    if (tid == 0) sjob = job_by_tile(jobs, njobs, gt);
+    __syncthreads();
+    const Job& J = jobs[sjob];
+    const GridDev& g = J.g;
+    const int t = gt - J.tile_base;
+    if (!J.do_build || t >= g.T) continue;
+    const TileProg* P = J.progs + t;
     const int nops = P->nops, nleaf = P->nleaf;
     const float cval = P->cval;
     const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
     if (nops > 0) {
+      stage_tile(P, J.prims, nops, nleaf, sops, sl, tid);
       __syncthreads();
-      stage_tile(P, prims, nops, nleaf, sops, sl, tid);
+      if (tid == 0) tables_plan(sl, nleaf, g, false, kBuildTab, lt);
       __syncthreads();
+      tables_fill(sl, nleaf, g, lt, false, tx << g.lx, ty << g.ly, tz << g.lz, tab, tid, J.auxf,
+                  J.auxd);
+      __syncthreads();
+    }
+    const int lxy = g.lx + g.ly, lxyz = lxy + g.lz;
+    const int ncc = g.C << lxyz;
+    const size_t plane = (size_t)g.nx * g.ny * g.nz;
+    const float eps_bg = g.eps_bg, deps = g.deps;
+    float* __restrict__ fill = J.fill;
+    float* __restrict__ eps = J.eps;
+    if (nops == 0) {
+      // constant tile: a pure streaming store, 16-byte vectors along x rows
+      const bool vec = (g.nx & 3) == 0 &&
+                       ((reinterpret_cast<uintptr_t>(eps) | reinterpret_cast<uintptr_t>(fill)) & 15) == 0;
+      const float e = eps_bg + deps * cval;
+      const int vpr = (1 << g.lx) >> 2;  // float4 per tile row
+      const int nv = (ncc >> g.lx) * vpr;
+      for (int r = tid; r < nv; r += kBlock) {
+        const int row = r / vpr, v4 = r - row * vpr;
+        const int y = row & ((1 << g.ly) - 1), z = (row >> g.ly) & ((1 << g.lz) - 1),
+                  c = row >> (g.ly + g.lz);
+        const int gi = (tx << g.lx) + 4 * v4, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
+        if (gi >= g.nx || gj >= g.ny || gk >= g.nz) continue;
+        const size_t o = (size_t)c * plane + ((size_t)gk * g.ny + gj) * g.nx + gi;
+        if (vec) {  // nx % 4 == 0, so the four cells are all inside the row
+          if (fill) *reinterpret_cast<float4*>(fill + o) = make_float4(cval, cval, cval, cval);
+          *reinterpret_cast<float4*>(eps + o) = make_float4(e, e, e, e);
+        } else {
+          for (int u = 0; u < 4 && gi + u < g.nx; ++u) {
+            if (fill) fill[o + u] = cval;
+            eps[o + u] = e;
+          }
+        }
+      }
+      continue;
     }
     for (int l = tid; l < ncc; l += kBlock) {
       const int x = l & ((1 << g.lx) - 1), y = (l >> g.lx) & ((1 << g.ly) - 1),
@@ -580,11 +1029,12 @@ __global__ void __launch_bounds__(kBlock) k_build(GridDev g, const TileProg* __r
       float v = cval;
       if (nops > 0) {
         const Cell cc{gi, gj, gk, g.off[c][0], g.off[c][1], g.off[c][2]};
-        v = eval_forward(sops, nops, sl, cc, g.logic, tape, tid, auxf, auxd);
+        const TileLoc q{x, y, z, c, 1 << g.lx, 1 << g.ly, 1 << g.lz};
+        v = eval_forward(sops, nops, sl, lt, tab, q, cc, g.logic, tape, tid, J.auxf, J.auxd);
       }
       const size_t o = (size_t)c * plane + ((size_t)gk * g.ny + gj) * g.nx + gi;
       if (fill) fill[o] = v;
-      eps[o] = g.eps_bg + g.deps * v;
+      eps[o] = eps_bg + deps * v;
     }
   }
 }
@@ -594,6 +1044,16 @@ __device__ __forceinline__ void neumaier(float& s, float& c, float v) {
   if (fabsf(s) >= fabsf(v)) c += (s - t) + v;
   else c += (v - t) + s;
   s = t;
+}
+
+__device__ __forceinline__ void flush_slot(int& slot, float& v, float* acc, float* cmp, int lane) {
+  if (slot >= 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) neumaier(acc[slot], cmp[slot], v);
+  }
+  slot = -1;
+  v = 0.f;
 }
 
 // Warp-cooperative, deterministic accumulation of the lanes' (slot, value)
@@ -616,16 +1076,12 @@ __device__ __forceinline__ void warp_accumulate(int n, int sb, const int* pk, co
 
 constexpr size_t kVjpSmem = (size_t)kMaxOps * kBlock * 4 + 2 * (size_t)kWarps * kMaxSlots * 4 +
                             2 * (size_t)kMaxPairs * kBlock * 4 + kMaxLeaves * sizeof(PrimRec) +
-                            kMaxOps * 2 + (kMaxLeaves + 1) * 4 + 16;
+                            (size_t)kVjpTab * 4 + (size_t)kMaxTileCells * 3 * 4 +
+                            kMaxLeaves * sizeof(LeafTab) + kMaxOps * 2 + (kMaxLeaves + 1) * 4 +
+                            (kMaxJobs + 1) * 4 + 16;
 
-__global__ void __launch_bounds__(kBlock) k_vjp(GridDev g, const TileProg* __restrict__ progs,
-                                                const int* __restrict__ list,
-                                                const int* __restrict__ counters,
-                                                const PrimRec* __restrict__ prims,
-                                                const int* __restrict__ act,
-                                                const float* __restrict__ auxf,
-                                                const double* __restrict__ auxd, VjpArgs va,
-                                                float* __restrict__ partial, int* __restrict__ err) {
+__global__ void __launch_bounds__(kBlock) k_vjp(const Job* __restrict__ jobs, int njobs,
+                                                int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* tape = reinterpret_cast<float*>(smem);
   float* acc = tape + kMaxOps * kBlock;
@@ -633,27 +1089,51 @@ __global__ void __launch_bounds__(kBlock) k_vjp(GridDev g, const TileProg* __res
   float* pv = cmp + kWarps * kMaxSlots;
   int* pk = reinterpret_cast<int*>(pv + kMaxPairs * kBlock);
   PrimRec* sl = reinterpret_cast<PrimRec*>(pk + kMaxPairs * kBlock);
-  uint16_t* sops = reinterpret_cast<uint16_t*>(sl + kMaxLeaves);
+  float* tab = reinterpret_cast<float*>(sl + kMaxLeaves);
+  float* zsb = tab + kVjpTab;  // the seed of every sample of the tile
+  LeafTab* lt = reinterpret_cast<LeafTab*>(zsb + kMaxTileCells * 3);
+  uint16_t* sops = reinterpret_cast<uint16_t*>(lt + kMaxLeaves);
   int* sbase = reinterpret_cast<int*>(sops + kMaxOps);
+  int* spre = sbase + kMaxLeaves + 1;  // prefix of band-tile counts over the jobs
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int lxy = g.lx + g.ly, lxyz = lxy + g.lz;
-  const int ncc = g.C << lxyz;
-  const size_t plane = (size_t)g.nx * g.ny * g.nz;
-  const int nprog = counters[0];
-  for (int li = blockIdx.x; li < nprog; li += gridDim.x) {
-    const int t = list[li];
-    const TileProg* P = progs + t;
+  if (tid == 0) {
+    int sum = 0;
+    for (int j = 0; j < njobs; ++j) {
+      spre[j] = sum;
+      if (jobs[j].do_grad) sum += jobs[j].counters[0];
+    }
+    spre[njobs] = sum;
+  }
+  __syncthreads();
+  const int total = spre[njobs];
+  for (int gi_ = blockIdx.x; gi_ < total; gi_ += gridDim.x) {
+    int jb = 0;
+    {
+      int lo = 0, hi = njobs - 1;  // last job whose prefix is <= gi_
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (spre[mid] <= gi_) lo = mid; else hi = mid - 1;
+      }
+      jb = lo;  // zero-width ranges (no band tiles, or no gradient) never end last
+    }
+    const Job& J = jobs[jb];
+    const GridDev& g = J.g;
+    const int t = J.list[gi_ - spre[jb]];
+    const TileProg* P = J.progs + t;
     const int nops = P->nops, nleaf = P->nleaf;
     const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
+    const VjpArgs& va = J.va;
     __syncthreads();
-    stage_tile(P, prims, nops, nleaf, sops, sl, tid);
+    stage_tile(P, J.prims, nops, nleaf, sops, sl, tid);
     __syncthreads();
     if (tid == 0) {
-      int s = 0;
-      for (int l = 0; l < nleaf; ++l) { sbase[l] = s; s += sl[l].nact; }
-      sbase[nleaf] = s;
+      int sum = 0;
+      for (int l = 0; l < nleaf; ++l) { sbase[l] = sum; sum += sl[l].nact; }
+      sbase[nleaf] = sum;
+      tables_plan(sl, nleaf, g, true, kVjpTab, lt);
     }
     __syncthreads();
+    tables_fill(sl, nleaf, g, lt, true, tx << g.lx, ty << g.ly, tz << g.lz, tab, tid, J.auxf, J.auxd);
     const int nslot = sbase[nleaf];
     if (nslot > kMaxSlots) {
       if (tid == 0) atomicOr(err, eSlotOverflow);
@@ -663,26 +1143,40 @@ __global__ void __launch_bounds__(kBlock) k_vjp(GridDev g, const TileProg* __res
     __syncthreads();
     float* wacc = acc + warp * nslot;
     float* wcmp = cmp + warp * nslot;
+    const int lxy = g.lx + g.ly, lxyz = lxy + g.lz;
+    const int ncc = g.C << lxyz;
+    const size_t plane = (size_t)g.nx * g.ny * g.nz;
+    // stream the tile's fields first: independent loads, many in flight
+#pragma unroll 4
     for (int l0 = 0; l0 < ncc; l0 += kBlock) {
       const int l = l0 + tid;
       const int x = l & ((1 << g.lx) - 1), y = (l >> g.lx) & ((1 << g.ly) - 1),
                 z = (l >> lxy) & ((1 << g.lz) - 1), c = l >> lxyz;
       const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
-      const bool valid = gi < g.nx && gj < g.ny && gk < g.nz;
       float zs = 0.f;
-      if (valid) {
+      if (gi < g.nx && gj < g.ny && gk < g.nz) {
         const size_t o = ((size_t)gk * g.ny + gj) * g.nx + gi;
         if (va.G) {
-          zs = va.G[(size_t)c * plane + o];
+          zs = __ldg(va.G + (size_t)c * plane + o);
         } else {
-          const float2 f = va.ef[c][o], a = va.ea[c][o];
+          const float2 f = __ldg(va.ef[c] + o), a = __ldg(va.ea[c] + o);
           const float pr = f.x * a.x - f.y * a.y, pi = f.x * a.y + f.y * a.x;
           zs = va.w[c].x * pr - va.w[c].y * pi;  // Re(w E_adj E), no conjugate (Eq. 1)
         }
         zs *= g.deps;  // eps = eps_bg + deps fill
       }
+      zsb[l] = zs;
+    }
+    __syncthreads();  // tables ready
+    for (int l0 = 0; l0 < ncc; l0 += kBlock) {
+      const int l = l0 + tid;
+      const int x = l & ((1 << g.lx) - 1), y = (l >> g.lx) & ((1 << g.ly) - 1),
+                z = (l >> lxy) & ((1 << g.lz) - 1), c = l >> lxyz;
+      const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
+      const float zs = zsb[l];
       const Cell cc{gi, gj, gk, g.off[c][0], g.off[c][1], g.off[c][2]};
-      eval_forward(sops, nops, sl, cc, g.logic, tape, tid, auxf, auxd);
+      const TileLoc q{x, y, z, c, 1 << g.lx, 1 << g.ly, 1 << g.lz};
+      eval_forward(sops, nops, sl, lt, tab, q, cc, g.logic, tape, tid, J.auxf, J.auxd);
       // reverse sweep through the logic: tape slots become adjoints d fill / d node
       tape[(nops - 1) * kBlock + tid] = 1.f;
       for (int pos = nops - 1; pos >= 0; --pos) {
@@ -702,26 +1196,35 @@ __global__ void __launch_bounds__(kBlock) k_vjp(GridDev g, const TileProg* __res
         const int op = sops[pos];
         if ((op & 7) != fPush) continue;
         const int lf = (op >> 3) & 63;
+        if (sl[lf].nact == 0) continue;
         const float a = zs * tape[pos * kBlock + tid];
         int n = 0;
-        if (a != 0.f && sl[lf].nact > 0)
-          n = leaf_pairs(sl[lf], cc, a, g, act, auxf, auxd, pk + tid, pv + tid);
-        if (sl[lf].nact > 0) warp_accumulate(n, sbase[lf], pk + tid, pv + tid, wacc, wcmp, lane);
+        if (a != 0.f) {
+          const LeafTab t = lt[lf];
+          if (t.ok && sl[lf].kind == kBox)
+            n = box_tab_pairs(sl[lf], t, q, tab, a, g, J.act, J.actc, pk + tid, pv + tid);
+          else
+            n = leaf_pairs(sl[lf], cc, a, g, J.act, J.actc, J.auxf, J.auxd, pk + tid, pv + tid);
+        }
+        warp_accumulate(n, sbase[lf], pk + tid, pv + tid, wacc, wcmp, lane);
+        if (sl[lf].kind == kPolygon)
+          poly_accumulate(sl[lf], cc, a, g, J.act, J.actc, J.auxd, wacc + sbase[lf],
+                          wcmp + sbase[lf], lane);
       }
     }
     __syncthreads();
-    for (int s = tid; s < nslot; s += kBlock) {
+    for (int s2 = tid; s2 < nslot; s2 += kBlock) {
       int lf = 0;
-      while (lf + 1 < nleaf && sbase[lf + 1] <= s) ++lf;
-      const int qa = s - sbase[lf];
+      while (lf + 1 < nleaf && sbase[lf + 1] <= s2) ++lf;
+      const int qa = s2 - sbase[lf];
       float tot = 0.f;
-      for (int w = 0; w < kWarps; ++w) tot += acc[w * nslot + s] + cmp[w * nslot + s];
+      for (int w = 0; w < kWarps; ++w) tot += acc[w * nslot + s2] + cmp[w * nslot + s2];
       const PrimRec& R = sl[lf];
       if (tx >= R.pb[0] && tx < R.pb[1] && ty >= R.pb[2] && ty < R.pb[3] && tz >= R.pb[4] &&
           tz < R.pb[5]) {
         const int rel = ((tz - R.pb[4]) * (R.pb[3] - R.pb[2]) + (ty - R.pb[2])) * (R.pb[1] - R.pb[0]) +
                         (tx - R.pb[0]);
-        partial[(size_t)R.part_off + (size_t)qa * R.npb + rel] = tot;
+        J.partial[(size_t)R.part_off + (size_t)qa * R.npb + rel] = tot;
       } else if (tot != 0.f) {
         atomicOr(err, ePartialRange);
       }
@@ -729,16 +1232,17 @@ __global__ void __launch_bounds__(kBlock) k_vjp(GridDev g, const TileProg* __res
   }
 }
 
-__global__ void k_finalize(int n, const int* __restrict__ ref_off, const int* __restrict__ ref_prim,
-                           const int* __restrict__ ref_qa, const double* __restrict__ ref_coeff,
-                           const PrimRec* __restrict__ prims, const float* __restrict__ partial,
-                           float* __restrict__ grad) {
+// One warp per parameter: fixed-order FP64 sums of its (primitive, slot)
+// partials over the derivative tile boxes.
+__global__ void k_finalize(const Job* __restrict__ jobs, int njobs, int nparams) {
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (wid >= n) return;
+  if (wid >= nparams) return;
+  const Job& J = jobs[job_by_param(jobs, njobs, wid)];
+  const int k = wid - J.param_base;
   double total = 0.0;
-  for (int r = ref_off[wid]; r < ref_off[wid + 1]; ++r) {
-    const PrimRec& P = prims[ref_prim[r]];
-    const float* src = partial + P.part_off + (size_t)ref_qa[r] * P.npb;
+  for (int r = J.ref_off[k]; r < J.ref_off[k + 1]; ++r) {
+    const PrimRec& P = J.prims[J.ref_prim[r]];
+    const float* src = J.partial + P.part_off + (size_t)J.ref_qa[r] * P.npb;
     double s = 0.0, c = 0.0;
     for (int t = lane; t < P.npb; t += 32) {
       const double v = src[t];
@@ -749,9 +1253,9 @@ __global__ void k_finalize(int n, const int* __restrict__ ref_off, const int* __
     s += c;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    total += ref_coeff[r] * s;
+    total += J.ref_coeff[r] * s;
   }
-  if (lane == 0) grad[wid] = (float)total;
+  if (lane == 0) J.grad[k] = (float)total;
 }
 
 }  // namespace
@@ -776,39 +1280,36 @@ int vjp_blocks_per_sm() {
   return v;
 }
 
-cudaError_t launch_bin(const GridDev& g, const int* chain, const PrimRec* prims,
-                       const float* auxf, const double* auxd, TileProg* progs, int* list,
-                       int* counters, int* err, cudaStream_t s) {
-  const int blocks = (g.T + 127) / 128;
-  k_bin<<<blocks, 128, 0, s>>>(g, chain, prims, auxf, auxd, progs, list, counters, err);
+cudaError_t launch_prepare(const Job* jobs, const JobTotals& t, cudaStream_t s) {
+  const long long work = std::max<long long>(t.partials, t.njobs);
+  if (work <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<long long>((work + 255) / 256, 4096);
+  k_prepare<<<blocks, 256, 0, s>>>(jobs, t.njobs);
   return cudaGetLastError();
 }
 
-cudaError_t launch_build(const GridDev& g, const TileProg* progs, const PrimRec* prims,
-                         const float* auxf, const double* auxd, float* fill, float* eps,
-                         int grid, cudaStream_t s) {
+cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s) {
+  if (t.tiles_padded <= 0) return cudaSuccess;
+  k_bin<<<t.tiles_padded / 128, 128, 0, s>>>(jobs, t.njobs, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build(const Job* jobs, const JobTotals& t, int grid, cudaStream_t s) {
   build_blocks_per_sm();
-  k_build<<<grid, kBlock, kBuildSmem, s>>>(g, progs, prims, auxf, auxd, fill, eps);
+  k_build<<<grid, kBlock, kBuildSmem, s>>>(jobs, t.njobs, t.tiles_padded);
   return cudaGetLastError();
 }
 
-cudaError_t launch_vjp(const GridDev& g, const TileProg* progs, const int* list,
-                       const int* counters, const PrimRec* prims, const int* act,
-                       const float* auxf, const double* auxd, const VjpArgs& a,
-                       float* partial, int* err, int grid, cudaStream_t s) {
+cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int grid, cudaStream_t s) {
   vjp_blocks_per_sm();
-  k_vjp<<<grid, kBlock, kVjpSmem, s>>>(g, progs, list, counters, prims, act, auxf, auxd, a,
-                                       partial, err);
+  k_vjp<<<grid, kBlock, kVjpSmem, s>>>(jobs, t.njobs, err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(int nparam, const int* ref_off, const int* ref_prim,
-                            const int* ref_qa, const double* ref_coeff, const PrimRec* prims,
-                            const float* partial, float* grad, cudaStream_t s) {
-  if (nparam <= 0) return cudaSuccess;
-  const int blocks = (nparam * 32 + 127) / 128;
-  k_finalize<<<blocks, 128, 0, s>>>(nparam, ref_off, ref_prim, ref_qa, ref_coeff, prims, partial,
-                                    grad);
+cudaError_t launch_finalize(const Job* jobs, const JobTotals& t, cudaStream_t s) {
+  if (t.params <= 0) return cudaSuccess;
+  const int blocks = (t.params * 32 + 127) / 128;
+  k_finalize<<<blocks, 128, 0, s>>>(jobs, t.njobs, t.params);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,74 @@
+"""Tile-shape autotuner for the binned kernels.
+
+The tile shape trades binning granularity (smaller tiles: fewer wasted band
+samples, more tiles to fold) against per-tile overhead and coalescing
+(x-extent 32 or 64 samples).  For a design description the tuner times one
+build + one gradient for each candidate shape on the device, using the
+library's own kernel timings, and returns the fastest.  Results are cached per
+grid-size class, so a batch of uneven designs is tuned once per class.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import adg
+
+CANDIDATES = [(32, 4, 4), (32, 8, 2), (64, 2, 2), (64, 4, 1), (32, 2, 8), (32, 4, 2), (64, 2, 1)]
+
+
+def size_class(desc: dict):
+    nx, ny, nz = desc["grid"]["n"]
+    b = lambda v: int(np.clip(np.round(np.log2(max(v, 1))), 0, 16))  # noqa: E731
+    return (b(nx), b(ny), b(nz), desc["grid"]["ncomp"])
+
+
+class Autotuner:
+    def __init__(self, ctx: adg.Context, candidates=None, reps: int = 3):
+        self.ctx = ctx
+        self.candidates = list(candidates or CANDIDATES)
+        self.reps = reps
+        self.cache = {}
+
+    def best(self, desc: dict, fields=None):
+        key = size_class(desc)
+        if key in self.cache:
+            return self.cache[key]
+        import torch
+        shape = tuple(int(v) for v in (desc["grid"]["ncomp"], *desc["grid"]["n"][::-1]))
+        if fields is None:
+            g = torch.Generator(device="cuda").manual_seed(0)
+            ef = torch.randn(shape, dtype=torch.complex64, device="cuda", generator=g)
+            ea = torch.randn(shape, dtype=torch.complex64, device="cuda", generator=g)
+        else:
+            ef, ea = fields
+        eps = torch.empty(shape, dtype=torch.float32, device="cuda")
+        p0 = np.asarray(desc["params"], dtype=np.float64)
+        timings = {}
+        for tile in self.candidates:
+            try:
+                d = adg.Design(self.ctx, desc, tile=tile)
+            except adg.AdgError:
+                continue
+            gr = torch.zeros(max(d.n_params, 1), dtype=torch.float32, device="cuda")[: d.n_params]
+            for k in range(2):  # warm-up
+                adg.adg_build_eps(d, p0 + 0.01 * k, eps)
+                adg.adg_grad(d, p0 + 0.01 * k, ef, ea, 1.0, gr)
+            try:
+                adg.adg_sync(self.ctx)
+            except adg.AdgError:
+                d.close()
+                continue  # the shape overflows a per-tile capacity for this design
+            torch.cuda.synchronize()
+            adg.adg_profile_read(self.ctx, reset=True)
+            adg.adg_profile_enable(self.ctx, True)
+            for k in range(self.reps):
+                adg.adg_build_eps(d, p0 + 0.01 * (k % 2), eps)
+                adg.adg_grad(d, p0 + 0.01 * (k % 2), ef, ea, 1.0, gr)
+            torch.cuda.synchronize()
+            adg.adg_profile_enable(self.ctx, False)
+            prof = adg.adg_profile_read(self.ctx, reset=True)
+            timings[tile] = sum(v[1] for v in prof.values()) / self.reps
+            d.close()
+        best = min(timings, key=timings.get) if timings else (32, 4, 4)
+        self.cache[key] = best
+        return best

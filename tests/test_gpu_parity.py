@@ -55,7 +55,40 @@ CASES = {
     "taper_small": lambda: I.taper_3d(n=(200, 75, 25), nverts=16),
     "holes_small": lambda: I.hole_lattice(n=(130, 100, 20), holes=5),
     "holes_2d": lambda: I.hole_lattice(n=(96, 80, 1), d=(40.0, 40.0, 40.0), holes=4, ncomp=1),
+    "random_mix": lambda: I.random_design(41, n=(150, 70, 36), nprims=40),
+    "random_mix2": lambda: I.random_design(43, n=(97, 130, 33), nprims=25),
 }
+
+
+def _polygon_design(per_vertex: bool, sigma="sigmoid", kr=4.0):
+    """Convex polygons (Poly2D): a translated 40-gon and a hexagon whose
+    every vertex coordinate is its own parameter, extruded in z."""
+    D = I.Design((96, 80, 24), (40.0, 40.0, 20.0), ncomp=3, eps_bg=2.0, eps_fg=11.0)
+    rng = np.random.default_rng(17)
+    tx, ty = D.param(3.7), D.param(-2.2)
+    import math
+    big = [(I.P(tx, 1500 + 700 * math.cos(a)), I.P(ty, 1600 + 500 * math.sin(a)))
+           for a in np.linspace(0, 2 * math.pi, 40, endpoint=False)]
+    hexa = []
+    for a in np.linspace(0, 2 * math.pi, 6, endpoint=False):
+        # centre and radius off the sample lattice: no sample sits on a kink
+        # of the piecewise sigmas, where fp32 and fp64 may pick either side
+        x, y = 2900.37 + 301.3 * math.cos(a + 0.1), 1500.61 + 301.3 * math.sin(a + 0.1)
+        hexa.append((I.P(D.param(x)), I.P(D.param(y))) if per_vertex else (x, y))
+    z0 = D.param(150.0)
+    p1 = D.polygon(big, z=(I.P(z0), 330.0), sigma=sigma, kr=kr)
+    p2 = D.polygon(hexa[::-1], z=(120.0, 300.0), sigma=sigma, kr=kr)  # clockwise winding
+    D.set_program(("union", p1, p2))
+    return D.to_desc()
+
+
+@pytest.mark.parametrize("per_vertex", [False, True])
+@pytest.mark.parametrize("sigma", ["sigmoid", "quadratic", "linear"])
+def test_polygons_match_oracle(ctx, oracle_mod, per_vertex, sigma):
+    kr = {"sigmoid": 4.0, "quadratic": 1.0, "linear": 1.0}[sigma]
+    desc = _polygon_design(per_vertex, sigma, kr)
+    d = _check_build(ctx, desc, oracle_mod)
+    _check_grad(ctx, desc, oracle_mod, d=d)
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
@@ -68,7 +101,7 @@ def test_gradient_matches_oracle(ctx, oracle_mod, case):
     _check_grad(ctx, CASES[case](), oracle_mod)
 
 
-@pytest.mark.parametrize("tile", [(32, 4, 4), (64, 2, 1), (32, 1, 8), (64, 16, 8)])
+@pytest.mark.parametrize("tile", [(32, 4, 4), (64, 2, 1), (32, 1, 8), (64, 4, 4), (32, 8, 4)])
 def test_tile_shapes_agree(ctx, oracle_mod, tile):
     desc = I.grating_3d(n=(150, 36, 60), teeth=8, pitch=600.0)
     d = _check_build(ctx, desc, oracle_mod, tile=tile)
@@ -178,6 +211,8 @@ def test_invalid_descriptions_rejected(ctx):
         adg.Design(ctx, bad)
     with pytest.raises(adg.AdgError):
         adg.Design(ctx, desc, tile=(48, 4, 4))
+    with pytest.raises(adg.AdgError):
+        adg.Design(ctx, desc, tile=(64, 16, 8))  # more cells than a tile may hold
 
 
 @pytest.mark.slow
