@@ -260,9 +260,12 @@ def run_adg(args):
     value = world * cells / (ms * 1e-3)
 
     # roofline of the dominant kernel (HBM-bound): algorithmic bytes / launch
-    bytes_build = cells * C * 4 * 2  # fill + eps, fp32
-    bytes_vjp = stats["band_cells"] * C * 16  # E_fwd + E_adj complex64 in band tiles
-    kern = {"build": bytes_build, "vjp": bytes_vjp}
+    band = stats["band_cells"]
+    bytes_fill = (cells - band) * C * 4 * 2   # fill + eps of constant tiles, fp32
+    bytes_build = band * C * 4 * 2            # fill + eps of band tiles
+    # E_fwd + E_adj complex64 of the samples whose Jacobian row can be nonzero
+    bytes_vjp = stats["active_samples"] * 16
+    kern = {"fill": bytes_fill, "build": bytes_build, "vjp": bytes_vjp}
     dom = max(kern, key=lambda k: prof[k][1])
     n_l, tot_ms = prof[dom]
     avg_ms = tot_ms / max(n_l, 1)
@@ -283,9 +286,11 @@ def run_adg(args):
             "algorithmic_bytes_per_launch": kern[dom],
             "peak_source": "measured" if peaks else "fallback"}
     kernels = {k: {"launches": v[0], "ms_total": v[1],
-                   "us_per_launch": 1e3 * v[1] / max(v[0], 1)} for k, v in prof.items()}
+                   "us_per_launch": 1e3 * v[1] / max(v[0], 1)} for k, v in prof.items() if v[0]}
     for k in kern:
-        a = kern[k] / (kernels[k]["us_per_launch"] * 1e-6) / 1e9 if kernels[k]["launches"] else 0
+        if k not in kernels:
+            continue
+        a = kern[k] / (kernels[k]["us_per_launch"] * 1e-6) / 1e9
         kernels[k]["GBps"] = a
         kernels[k]["frac_of_measured_hbm"] = a / peak
     launches = sum(v[0] for v in prof.values())
@@ -343,6 +348,7 @@ def run_adg(args):
                        "vjp": "band tiles only (tiles crossed by an edge band)",
                        "tile": list(stats["tile"]), "program_tiles": stats["program_tiles"],
                        "tiles": stats["tiles"], "band_cells": stats["band_cells"],
+                       "vjp_active_samples": stats["active_samples"],
                        "l2": "inputs larger than L2 (fields 691 MB + outputs 346 MB per step)"},
             "roofline": roof, "kernels": kernels, "gpu_launches": launches,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),

@@ -136,6 +136,8 @@ typedef struct {
   int64_t band_cells;     /* cells (per component) inside program tiles     */
   int32_t tile[3];        /* tile shape in use                              */
   int32_t max_ops;        /* longest folded per-tile program                */
+  int64_t active_samples; /* samples the last VJP swept (a derivative of a
+                             parameter-driven primitive may be nonzero)     */
 } adg_stats;
 
 typedef struct adg_ctx adg_ctx;       /* opaque: device, error word         */
@@ -226,7 +228,7 @@ adg_status adg_design_stats(adg_ctx *ctx, adg_design *design, void *stream, adg_
  * (index ADG_K_*), the launch count and the summed device time; `reset`
  * clears the accumulators. */
 enum { ADG_K_BIN = 0, ADG_K_BUILD = 1, ADG_K_VJP = 2, ADG_K_FINALIZE = 3, ADG_K_PREPARE = 4,
-       ADG_K_COUNT = 8 };
+       ADG_K_FILL = 5, ADG_K_COUNT = 8 };
 typedef struct {
   int64_t launches[ADG_K_COUNT];
   double ms[ADG_K_COUNT];

@@ -54,7 +54,7 @@ class adg_tile_opts(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
-K_NAMES = {0: "bin", 1: "build", 2: "vjp", 3: "finalize"}
+K_NAMES = {0: "bin", 1: "build", 2: "vjp", 3: "finalize", 4: "prepare", 5: "fill"}
 
 
 class adg_profile_data(ctypes.Structure):
@@ -64,7 +64,8 @@ class adg_profile_data(ctypes.Structure):
 class adg_stats(ctypes.Structure):
     _fields_ = [("tiles", ctypes.c_int64), ("program_tiles", ctypes.c_int64),
                 ("cells", ctypes.c_int64), ("band_cells", ctypes.c_int64),
-                ("tile", ctypes.c_int32 * 3), ("max_ops", ctypes.c_int32)]
+                ("tile", ctypes.c_int32 * 3), ("max_ops", ctypes.c_int32),
+                ("active_samples", ctypes.c_int64)]
 
 
 def lib():
@@ -277,7 +278,8 @@ def adg_design_stats(design: Design, stream=None) -> dict:
     _check(lib().adg_design_stats(design.ctx.handle, design.handle, _stream_ptr(stream),
                                   ctypes.byref(s)))
     return {"tiles": s.tiles, "program_tiles": s.program_tiles, "cells": s.cells,
-            "band_cells": s.band_cells, "tile": tuple(s.tile), "max_ops": s.max_ops}
+            "band_cells": s.band_cells, "tile": tuple(s.tile), "max_ops": s.max_ops,
+            "active_samples": s.active_samples}
 
 
 def adg_profile_enable(ctx: Context, on: bool = True):

@@ -147,6 +147,7 @@ struct adg_design {
   double* d_auxd = nullptr;
   float* d_auxf = nullptr;
   TileProg* d_progs = nullptr;
+  unsigned char* d_tclass = nullptr;
   int* d_list = nullptr;
   int* d_counters = nullptr;
   float* d_partial = nullptr;
@@ -217,6 +218,7 @@ void free_design(adg_design* d) {
   cudaFree(d->d_auxd);
   cudaFree(d->d_auxf);
   cudaFree(d->d_progs);
+  cudaFree(d->d_tclass);
   cudaFree(d->d_list);
   cudaFree(d->d_counters);
   cudaFree(d->d_partial);
@@ -314,6 +316,7 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   if (e == cudaSuccess) e = upload(&d->d_auxd, d->h_auxd);
   if (e == cudaSuccess) e = upload(&d->d_auxf, d->h_auxf);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_progs, sizeof(TileProg) * (size_t)d->g.T);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_tclass, (size_t)d->g.T);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_list, sizeof(int) * (size_t)d->g.T);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_counters, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_job, sizeof(Job));
@@ -401,6 +404,7 @@ Job design_job(adg_design* d) {
   J.ref_qa = d->d_ref_qa;
   J.ref_coeff = d->d_ref_coeff;
   J.progs = d->d_progs;
+  J.tclass = d->d_tclass;
   J.list = d->d_list;
   J.counters = d->d_counters;
   J.partial = d->d_partial;
@@ -421,14 +425,17 @@ adg_status run_jobs(adg_ctx* ctx, const Job* d_jobs, const JobTotals& t, bool an
     CU(launch_bin(d_jobs, t, ctx->d_err, s));
   }
   if (any_build) {
-    const int grid = std::max(1, std::min(max_tiles, ctx->sms * build_blocks_per_sm()));
+    {
+      ProfScope ps(ctx, ADG_K_FILL, s);
+      CU(launch_fill(d_jobs, t, s));
+    }
     ProfScope ps(ctx, ADG_K_BUILD, s);
-    CU(launch_build(d_jobs, t, grid, s));
+    CU(launch_build(d_jobs, t, ctx->sms, s));
   }
   if (any_grad) {
     {
       ProfScope ps(ctx, ADG_K_VJP, s);
-      CU(launch_vjp(d_jobs, t, ctx->d_err, ctx->sms * vjp_blocks_per_sm(), s));
+      CU(launch_vjp(d_jobs, t, ctx->d_err, ctx->sms, s));
     }
     ProfScope ps(ctx, ADG_K_FINALIZE, s);
     CU(launch_finalize(d_jobs, t, s));
@@ -461,6 +468,7 @@ adg_status run_single(adg_ctx* ctx, adg_design* d, const double* h_params, float
   t.njobs = 1;
   t.tiles_padded = ((d->g.T + 127) / 128) * 128;
   t.bin_blocks = t.tiles_padded / 128;
+  t.fill_blocks = d_eps ? (d->g.C * d->g.nz * d->g.ny + kFillRows - 1) / kFillRows : 0;
   t.params = grad ? d->n_params : 0;
   t.partials = J.partial_n;
   return run_jobs(ctx, d->d_job, t, rebin, d_eps != nullptr, grad, d->g.T, s);
@@ -581,7 +589,7 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   unsigned char* db = static_cast<unsigned char*>(A.d);
   Job* hj = reinterpret_cast<Job*>(hb + o_jobs);
   size_t po = 0, ado = 0, afo = 0;
-  int tile_base = 0, param_base = 0, max_tiles = 0;
+  int tile_base = 0, param_base = 0, max_tiles = 0, row_base = 0;
   long long partial_base = 0;
   bool any_build = false, any_grad = false;
   uint64_t sig = mix(0, (uint64_t)arena_id);
@@ -618,6 +626,8 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
     J.partial_base = partial_base;
     J.param_base = param_base;
     J.tile_base = tile_base;
+    J.row_base = row_base;
+    if (J.do_build) row_base += (d->g.C * d->g.nz * d->g.ny + kFillRows - 1) / kFillRows;
     partial_base += J.partial_n;
     if (J.do_grad) param_base += d->n_params;
     tile_base += ((d->g.T + 127) / 128) * 128;
@@ -635,14 +645,15 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   t.njobs = n;
   t.tiles_padded = tile_base;
   t.bin_blocks = tile_base / 128;
+  t.fill_blocks = row_base;
   t.params = param_base;
   t.partials = partial_base;
   sig = mix(sig, (uint64_t)bytes);
   sig = mix(sig, (uint64_t)tile_base);
   sig = mix(sig, (uint64_t)param_base);
   sig = mix(sig, (uint64_t)std::min<long long>((partial_base + 255) / 256, 4096));
-  build_blocks_per_sm();
-  vjp_blocks_per_sm();
+  build_blocks_per_sm(t.njobs);  // kernel attributes are set before any capture
+  vjp_blocks_per_sm(t.njobs);
   const bool graph = (flags & ADG_BATCH_GRAPH) && !ctx->prof;
   if (graph && A.exec && A.sig == sig) {
     CU(cudaGraphLaunch(A.exec, s));
@@ -743,6 +754,7 @@ extern "C" adg_status adg_design_stats(adg_ctx* ctx, adg_design* d, void* stream
   out->program_tiles = c[0];
   out->max_ops = c[1];
   out->band_cells = c[2];
+  out->active_samples = c[3];
   out->cells = (int64_t)d->g.nx * d->g.ny * d->g.nz;
   out->tile[0] = 1 << d->g.lx;
   out->tile[1] = 1 << d->g.ly;

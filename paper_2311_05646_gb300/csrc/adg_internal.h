@@ -12,7 +12,7 @@ constexpr int kMaxLeaves = 48;  // primitives whose edge band crosses the tile
 constexpr int kMaxOps = 32;     // folded logic program length
 constexpr int kMaxDepth = 32;   // fold stack depth (checked at design creation)
 constexpr int kMaxSlots = 384;  // (primitive, active scalar) accumulators
-constexpr int kMaxPairs = 8;    // nonzero d s / d q terms one cell yields per leaf
+constexpr int kMaxPairs = 6;    // d s / d q terms one cell yields per leaf (box, graph 6; circle 5)
 constexpr int kBlock = 128;     // threads per CTA of the build / VJP kernels
 constexpr int kMaxTileCells = 1024;  // cells per tile (per component)
 constexpr int kWarps = kBlock / 32;
@@ -100,6 +100,7 @@ struct Job {
   const double* ref_coeff;
   // bins
   TileProg* progs;
+  unsigned char* tclass;  // per tile: 0 / 1 constant fill, 2 band (program) tile
   int* list;
   int* counters;
   // outputs and inputs of the operations
@@ -113,11 +114,15 @@ struct Job {
   int nparam;
   int param_base;  // prefix over the table (finalize)
   int tile_base;   // prefix over the table, multiple of 128 (binner blocks)
+  int row_base;    // prefix over build jobs of kFillRows-row groups (streaming fill)
   int do_bin, do_build, do_grad;
 };
 
+constexpr int kFillRows = 8;  // x-rows per block of the streaming fill
+
 struct JobTotals {
   int njobs;
+  int fill_blocks;       // sum over build jobs of ceil(C nz ny / kFillRows)
   int bin_blocks;        // sum over binned jobs of ceil(T / 128)
   int tiles_padded;      // tile_base of one past the last job
   int params;            // sum of nparam over gradient jobs
@@ -128,11 +133,12 @@ constexpr int kMaxJobs = 1024;  // jobs in one table (one batch)
 
 cudaError_t launch_prepare(const Job* jobs, const JobTotals& t, cudaStream_t s);
 cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s);
-cudaError_t launch_build(const Job* jobs, const JobTotals& t, int grid, cudaStream_t s);
-cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int grid, cudaStream_t s);
+cudaError_t launch_fill(const Job* jobs, const JobTotals& t, cudaStream_t s);
+cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s);
+cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, cudaStream_t s);
 cudaError_t launch_finalize(const Job* jobs, const JobTotals& t, cudaStream_t s);
-int build_blocks_per_sm();
-int vjp_blocks_per_sm();
+int build_blocks_per_sm(int njobs);
+int vjp_blocks_per_sm(int njobs);
 void set_last_error(const char* msg);  // the thread-local text of adg_last_error()
 
 }  // namespace adg

@@ -559,6 +559,18 @@ __device__ __forceinline__ int job_by_tile(const Job* jobs, int n, int idx) {
   return lo;
 }
 
+__device__ __forceinline__ int job_by_rows(const Job* jobs, int n, int idx) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const Job& J = jobs[mid];
+    const int rows = J.g.C * J.g.nz * J.g.ny;
+    if (J.row_base + (J.do_build ? (rows + kFillRows - 1) / kFillRows : 0) > idx) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ int job_by_param(const Job* jobs, int n, int idx) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -587,9 +599,11 @@ __global__ void k_prepare(const Job* __restrict__ jobs, int njobs) {
   const long long npart = L.partial_base + (L.do_grad ? L.partial_n : 0);
   const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = i0; i < njobs; i += stride)
+  for (long long i = i0; i < njobs; i += stride) {
     if (jobs[i].do_bin)
-      for (int k = 0; k < 4; ++k) jobs[i].counters[k] = 0;
+      for (int k = 0; k < 3; ++k) jobs[i].counters[k] = 0;
+    if (jobs[i].do_bin || jobs[i].do_grad) jobs[i].counters[3] = 0;  // active VJP samples
+  }
   for (long long i = i0; i < npart; i += stride) {
     const Job& J = jobs[job_by_partial(jobs, njobs, i)];
     J.partial[i - J.partial_base] = 0.f;
@@ -598,21 +612,21 @@ __global__ void k_prepare(const Job* __restrict__ jobs, int njobs) {
 
 // One thread per tile; the block's 128 tiles belong to one job (tile ranges
 // are padded to multiples of 128).
-constexpr int kChainSmem = 1536, kBoxSmem = 320;
+constexpr int kChainSmem = 1024, kPrimSmem = 96;
 
-// The fold of one tile (one thread).  SMEM: the chain and the tile boxes are
-// staged in the block's shared memory (small designs); otherwise they are
-// read through the read-only path.  The folded program is built in shared
-// memory and written out once, so the loop itself never stores to global.
+// The fold of one tile (one thread).  SMEM: the chain and the primitive
+// records are staged in the block's shared memory (small designs); otherwise
+// they are read through the read-only path.  The folded program is built in
+// shared memory and written out once, so the loop never stores to global.
 template <bool SMEM>
-__device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain, const int (*stb)[6],
+__device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain, const PrimRec* sprim,
                                          uint16_t (*stk)[128], uint16_t (*sleaf)[128],
                                          uint16_t (*sop)[128], int* err) {
   const int tid = threadIdx.x;
   const int nchain = J.g.nchain, ntx = J.g.ntx, nty = J.g.nty;
   const int lx = J.g.lx, ly = J.g.ly, lz = J.g.lz;
   const int* __restrict__ chain = J.chain;
-  const PrimRec* __restrict__ prims = J.prims;
+  const PrimRec* __restrict__ prims = SMEM ? sprim : J.prims;
   const double* __restrict__ auxd = J.auxd;
   const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
   const int i0 = tx << lx, j0 = ty << ly, k0 = tz << lz;
@@ -627,8 +641,8 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain,
     if (code == cPush) {
       int b0, b1, b2, b3, b4, b5;
       if (SMEM) {
-        b0 = stb[arg][0]; b1 = stb[arg][1]; b2 = stb[arg][2];
-        b3 = stb[arg][3]; b4 = stb[arg][4]; b5 = stb[arg][5];
+        const int* tb = sprim[arg].tb;
+        b0 = tb[0]; b1 = tb[1]; b2 = tb[2]; b3 = tb[3]; b4 = tb[4]; b5 = tb[5];
       } else {
         const int* tb = prims[arg].tb;
         b0 = __ldg(tb); b1 = __ldg(tb + 1); b2 = __ldg(tb + 2);
@@ -731,6 +745,7 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain,
   out->nleaf = nleaf;
   out->cval = cval;
   out->nslot = nslot;
+  J.tclass[t] = nops > 0 ? 2 : (cval != 0.f ? 1 : 0);
   if (nops > 0) {
     int* counters = J.counters;
     const int idx = atomicAdd(&counters[0], 1);
@@ -741,27 +756,34 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain,
 }
 
 // One thread per tile; the block's 128 tiles belong to one job (tile ranges
-// are padded to multiples of 128).
+// are padded to multiples of 128).  Threads walk the tiles y-fastest: tiles
+// that differ only in y usually see the same primitives, so a warp's lanes
+// take the same classification branches.
 __global__ void __launch_bounds__(128) k_bin(const Job* __restrict__ jobs, int njobs,
                                              int* __restrict__ err) {
   __shared__ uint16_t stk[kMaxDepth][128];
   __shared__ uint16_t sleaf[kMaxLeaves][128];
   __shared__ uint16_t sop[kMaxOps][128];
   __shared__ int schain[kChainSmem];
-  __shared__ int stb[kBoxSmem][6];
+  __shared__ __align__(16) PrimRec sprim[kPrimSmem];
   const int tid = threadIdx.x;
   const Job& J = jobs[job_by_tile(jobs, njobs, blockIdx.x * 128)];
   if (!J.do_bin) return;  // uniform over the block
-  const bool smem = J.g.nchain <= kChainSmem && J.g.nprims <= kBoxSmem;
+  const bool smem = J.g.nchain <= kChainSmem && J.g.nprims <= kPrimSmem;
   if (smem) {
     for (int q = tid; q < J.g.nchain; q += blockDim.x) schain[q] = J.chain[q];
-    for (int q = tid; q < J.g.nprims * 6; q += blockDim.x) stb[q / 6][q % 6] = J.prims[q / 6].tb[q % 6];
+    constexpr int W = sizeof(PrimRec) / 16;
+    for (int q = tid; q < J.g.nprims * W; q += blockDim.x)
+      reinterpret_cast<int4*>(sprim)[q] = reinterpret_cast<const int4*>(J.prims)[q];
   }
   __syncthreads();
-  const int t = blockIdx.x * 128 + tid - J.tile_base;
-  if (t >= J.g.T) return;
-  if (smem) bin_tile<true>(J, t, schain, stb, stk, sleaf, sop, err);
-  else bin_tile<false>(J, t, schain, stb, stk, sleaf, sop, err);
+  const int u = blockIdx.x * 128 + tid - J.tile_base;
+  if (u >= J.g.T) return;
+  const int nty = J.g.nty, ntx = J.g.ntx;
+  const int ty = u % nty, tx = (u / nty) % ntx, tz = u / (nty * ntx);
+  const int t = (tz * nty + ty) * ntx + tx;
+  if (smem) bin_tile<true>(J, t, schain, sprim, stk, sleaf, sop, err);
+  else bin_tile<false>(J, t, schain, sprim, stk, sleaf, sop, err);
 }
 
 __device__ __forceinline__ void stage_tile(const TileProg* P, const PrimRec* prims, int nops,
@@ -781,38 +803,62 @@ __device__ __forceinline__ void stage_tile(const TileProg* P, const PrimRec* pri
 // z factor).  Each tile evaluates every factor once per (component,
 // coordinate) into shared memory; a sample's leaf value is then two or three
 // table reads.  Leaves that do not fit the table pool are evaluated directly.
-struct LeafTab {
-  int x, y, z, xy;  // value tables (offsets in floats), -1 if absent
-  int dx, dy, dz;   // derivative tables (lo, hi per component), -1 if absent
-  int ok;
+struct __align__(16) LeafTab {
+  int4 v;         // value tables x, y, z, xy (offsets in floats), -1 if absent
+  int4 d;         // derivative tables dx, dy, dz (lo, hi per component); w = flags
+  int slot[6];    // box: accumulator slot and map coefficient of scalar k
+  float coef[6];
 };
+// LeafTab.d.w flags
+constexpr int tOK = 1, tBOX = 2, tACT = 4;  // tabled, box, drives some parameter
+constexpr int tKEYS = 8;                     // bits 8..13: box scalars driving a parameter
 
-// Thread 0: assign table offsets for the tile's leaves within `cap` floats.
+// All threads: the accumulator slot and map coefficient of each box scalar
+// (staged in parallel: these are global reads).
+__device__ __forceinline__ void stage_slots(const PrimRec* sl, int nleaf, const int* act,
+                                            const float* actc, LeafTab* lt, int tid) {
+  for (int q = tid; q < nleaf * 6; q += kBlock) {
+    const int l = q / 6, k = q - l * 6;
+    const bool box = sl[l].kind == kBox;
+    lt[l].slot[k] = box ? __ldg(act + sl[l].act_off + k) : -1;
+    lt[l].coef[k] = box ? __ldg(actc + sl[l].act_off + k) : 0.f;
+  }
+}
+
+// Thread 0: assign table offsets for the tile's leaves within `cap` floats;
+// with derivatives, the box key bits come from the staged slots.
 __device__ __forceinline__ void tables_plan(const PrimRec* sl, int nleaf, const GridDev& g,
                                             bool derivs, int cap, LeafTab* lt) {
   const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
   int off = 0;
   for (int l = 0; l < nleaf; ++l) {
-    LeafTab t{-1, -1, -1, -1, -1, -1, -1, 0};
+    int4 v = make_int4(-1, -1, -1, -1), d = make_int4(-1, -1, -1, 0);
     const int m = derivs ? 3 : 1;
-    if (sl[l].kind == kBox) {
+    const bool box = sl[l].kind == kBox;
+    if (box) {
       const int need = m * C * (TX + TY + TZ);
       if (off + need <= cap) {
-        t.x = off; t.y = t.x + C * TX; t.z = t.y + C * TY;
-        if (derivs) { t.dx = t.z + C * TZ; t.dy = t.dx + 2 * C * TX; t.dz = t.dy + 2 * C * TY; }
-        t.ok = 1;
+        v.x = off; v.y = v.x + C * TX; v.z = v.y + C * TY;
+        if (derivs) { d.x = v.z + C * TZ; d.y = d.x + 2 * C * TX; d.z = d.y + 2 * C * TY; }
+        d.w |= tOK;
         off += need;
       }
+      d.w |= tBOX;
     } else {
       const int need = C * TX * TY + m * C * TZ;
       if (off + need <= cap) {
-        t.xy = off; t.z = t.xy + C * TX * TY;
-        if (derivs) t.dz = t.z + C * TZ;
-        t.ok = 1;
+        v.w = off; v.z = v.w + C * TX * TY;
+        if (derivs) d.z = v.z + C * TZ;
+        d.w |= tOK;
         off += need;
       }
     }
-    lt[l] = t;
+    if (sl[l].nact > 0) d.w |= tACT;
+    if (derivs && box)
+      for (int k = 0; k < 6; ++k)
+        if (lt[l].slot[k] >= 0) d.w |= (tKEYS << k);
+    lt[l].v = v;
+    lt[l].d = d;
   }
 }
 
@@ -856,26 +902,26 @@ __device__ __forceinline__ void tables_fill(const PrimRec* sl, int nleaf, const 
                                             int Z0, float* tab, int tid, const float* auxf,
                                             const double* auxd) {
   const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
-  const int T3[3] = {TX, TY, TZ};
-  const int O3[3] = {X0, Y0, Z0};
   for (int l = 0; l < nleaf; ++l) {
-    const LeafTab t = lt[l];
-    if (!t.ok) continue;
+    const int4 tv = lt[l].v, td = lt[l].d;
+    if (!(td.w & tOK)) continue;
     const PrimRec& P = sl[l];
     if (P.kind == kBox) {
       const int tot = C * (TX + TY + TZ);
       for (int e = tid; e < tot; e += kBlock) {
-        int ax = 0, r = e;
-        while (ax < 2 && r >= C * T3[ax]) { r -= C * T3[ax]; ++ax; }
-        const int c = r / T3[ax], u = r - c * T3[ax];
+        // axis, component and coordinate of entry e (x block, y block, z block)
+        int ax = 0, r = e, T = TX, O = X0;
+        if (r >= C * TX) { r -= C * TX; ax = 1; T = TY; O = Y0; }
+        if (ax == 1 && r >= C * TY) { r -= C * TY; ax = 2; T = TZ; O = Z0; }
+        const int c = r / T, u = r - c * T;
         float da, db;
-        const float f = box_axis(P, ax, O3[ax] + u, g.off[c][ax], da, db);
-        const int vt = ax == 0 ? t.x : (ax == 1 ? t.y : t.z);
-        tab[vt + c * T3[ax] + u] = f;
+        const float f = box_axis(P, ax, O + u, g.off[c][ax], da, db);
+        const int vt = ax == 0 ? tv.x : (ax == 1 ? tv.y : tv.z);
+        tab[vt + c * T + u] = f;
         if (derivs) {
-          const int dt = ax == 0 ? t.dx : (ax == 1 ? t.dy : t.dz);
-          tab[dt + (2 * c) * T3[ax] + u] = da;
-          tab[dt + (2 * c + 1) * T3[ax] + u] = db;
+          const int dt = ax == 0 ? td.x : (ax == 1 ? td.y : td.z);
+          tab[dt + (2 * c) * T + u] = da;
+          tab[dt + (2 * c + 1) * T + u] = db;
         }
       }
     } else {
@@ -884,15 +930,15 @@ __device__ __forceinline__ void tables_fill(const PrimRec* sl, int nleaf, const 
         if (e < nxy) {
           const int c = e / (TX * TY), r = e - c * TX * TY, v = r / TX, u = r - v * TX;
           const Cell cc{X0 + u, Y0 + v, Z0, g.off[c][0], g.off[c][1], g.off[c][2]};
-          tab[t.xy + e] = plane_value(P, cc, auxf, auxd);
+          tab[tv.w + e] = plane_value(P, cc, auxf, auxd);
         } else {
           const int r = e - nxy, c = r / TZ, u = r - c * TZ;
           const Cell cc{X0, Y0, Z0 + u, g.off[c][0], g.off[c][1], g.off[c][2]};
           float dz0, dz1;
-          tab[t.z + r] = zfactor(P, cc, dz0, dz1);
+          tab[tv.z + r] = zfactor(P, cc, dz0, dz1);
           if (derivs) {
-            tab[t.dz + (2 * c) * TZ + u] = dz0;
-            tab[t.dz + (2 * c + 1) * TZ + u] = dz1;
+            tab[td.z + (2 * c) * TZ + u] = dz0;
+            tab[td.z + (2 * c + 1) * TZ + u] = dz1;
           }
         }
       }
@@ -905,11 +951,11 @@ struct TileLoc {
   int TX, TY, TZ;
 };
 
-__device__ __forceinline__ float tab_value(const LeafTab& t, bool box, const TileLoc& q,
+__device__ __forceinline__ float tab_value(const int4 v, bool box, const TileLoc& q,
                                            const float* tab) {
-  const float fz = tab[t.z + q.c * q.TZ + q.z];
-  if (box) return tab[t.x + q.c * q.TX + q.x] * tab[t.y + q.c * q.TY + q.y] * fz;
-  return tab[t.xy + (q.c * q.TY + q.y) * q.TX + q.x] * fz;
+  const float fz = tab[v.z + q.c * q.TZ + q.z];
+  if (box) return tab[v.x + q.c * q.TX + q.x] * tab[v.y + q.c * q.TY + q.y] * fz;
+  return tab[v.w + (q.c * q.TY + q.y) * q.TX + q.x] * fz;
 }
 
 __device__ __forceinline__ float eval_forward(const uint16_t* sops, int nops, const PrimRec* sl,
@@ -922,8 +968,8 @@ __device__ __forceinline__ float eval_forward(const uint16_t* sops, int nops, co
     const int op = sops[pos];
     const int code = op & 7, a = (op >> 3) & 63, b = (op >> 9) & 63;
     if (code == fPush) {
-      const LeafTab t = lt[a];
-      v = t.ok ? tab_value(t, t.xy < 0, q, tab) : leaf_value(sl[a], cc, auxf, auxd);
+      const int f = lt[a].d.w;
+      v = (f & tOK) ? tab_value(lt[a].v, (f & tBOX) != 0, q, tab) : leaf_value(sl[a], cc, auxf, auxd);
     } else {
       v = op_fwd(code, logic, tape[a * kBlock + tid], code == fCompl ? 0.f : tape[b * kBlock + tid]);
     }
@@ -932,109 +978,148 @@ __device__ __forceinline__ float eval_forward(const uint16_t* sops, int nops, co
   return v;
 }
 
-// Derivative pairs of a tabled box leaf at one sample (keys 0..5 = x0..z1).
-__device__ __forceinline__ int box_tab_pairs(const PrimRec& P, const LeafTab& t, const TileLoc& q,
-                                             const float* tab, float a, const GridDev& g,
-                                             const int* act, const float* actc, int* pk,
-                                             float* pv) {
-  const int* actp = act + P.act_off;
-  const float* actcp = actc + P.act_off;
-  const float fx = tab[t.x + q.c * q.TX + q.x], fy = tab[t.y + q.c * q.TY + q.y],
-              fz = tab[t.z + q.c * q.TZ + q.z];
-  int n = 0;
-  const float ax = a * fy * fz * g.invd[0], ay = a * fx * fz * g.invd[1], az = a * fx * fy * g.invd[2];
-  n = push_pair(actp, actcp, 0, tab[t.dx + (2 * q.c) * q.TX + q.x] * ax, n, pk, pv);
-  n = push_pair(actp, actcp, 1, tab[t.dx + (2 * q.c + 1) * q.TX + q.x] * ax, n, pk, pv);
-  n = push_pair(actp, actcp, 2, tab[t.dy + (2 * q.c) * q.TY + q.y] * ay, n, pk, pv);
-  n = push_pair(actp, actcp, 3, tab[t.dy + (2 * q.c + 1) * q.TY + q.y] * ay, n, pk, pv);
-  n = push_pair(actp, actcp, 4, tab[t.dz + (2 * q.c) * q.TZ + q.z] * az, n, pk, pv);
-  n = push_pair(actp, actcp, 5, tab[t.dz + (2 * q.c + 1) * q.TZ + q.z] * az, n, pk, pv);
-  return n;
+// Per-tile pools (floats): the staged leaves, their table descriptors, the
+// VJP's per-warp accumulators, then the factor tables in what is left.
+constexpr int kBuildPool = 4096;
+constexpr int kVjpPool = 6144;
+static_assert(kMaxLeaves * (int)(sizeof(PrimRec) + sizeof(LeafTab)) / 4 + 192 <= kBuildPool,
+              "build pool holds the staged leaves and some tables");
+static_assert(kMaxLeaves * (int)(sizeof(PrimRec) + sizeof(LeafTab)) / 4 + 2 * kWarps * kMaxSlots +
+                  192 <= kVjpPool,
+              "VJP pool holds the staged leaves, accumulators and some tables");
+// job-prefix entries in shared memory: a class for small tables, one for any
+__host__ __device__ constexpr int spre_len(int njobs) { return njobs < 16 ? 16 : kMaxJobs + 1; }
+constexpr size_t kBuildFixed = (size_t)kMaxOps * kBlock * 4 + (size_t)kBuildPool * 4 + kMaxOps * 2;
+size_t build_smem(int njobs) { return kBuildFixed + (size_t)spre_len(njobs) * 4; }
+
+// Pool carve of one tile: staged leaves, descriptors, then (VJP) accumulators.
+struct TilePool {
+  PrimRec* sl;
+  LeafTab* lt;
+  float* acc;
+  float* cmp;
+  float* tab;
+  int cap;
+};
+__device__ __forceinline__ TilePool carve_pool(float* pool, int size, int nleaf, int nacc) {
+  TilePool t;
+  t.sl = reinterpret_cast<PrimRec*>(pool);
+  t.lt = reinterpret_cast<LeafTab*>(t.sl + nleaf);
+  t.acc = reinterpret_cast<float*>(t.lt + nleaf);
+  t.cmp = t.acc + nacc;
+  const int used = ((int)(nleaf * (sizeof(PrimRec) + sizeof(LeafTab)) / 4) + 2 * nacc + 3) & ~3;
+  t.tab = pool + used;
+  t.cap = size - used;
+  return t;
 }
 
-constexpr int kBuildTab = 4096;  // floats of factor tables per tile (build)
-constexpr int kVjpTab = 4096;    // floats of factor tables per tile (VJP, values + derivatives)
-constexpr size_t kBuildSmem = (size_t)kMaxOps * kBlock * 4 + kMaxLeaves * sizeof(PrimRec) +
-                              (size_t)kBuildTab * 4 + kMaxLeaves * sizeof(LeafTab) + kMaxOps * 2 +
-                              16;
+// Thread 0: prefix of band-tile counts over the jobs that take part.
+__device__ __forceinline__ void job_prefix(const Job* jobs, int njobs, bool grad, int* spre) {
+  int sum = 0;
+  for (int j = 0; j < njobs; ++j) {
+    spre[j] = sum;
+    if (grad ? jobs[j].do_grad : jobs[j].do_build) sum += jobs[j].counters[0];
+  }
+  spre[njobs] = sum;
+}
 
-__global__ void __launch_bounds__(kBlock) k_build(const Job* __restrict__ jobs, int njobs,
-                                                  int tiles_padded) {
+// Last job whose prefix is <= i (zero-width ranges never end last).
+__device__ __forceinline__ int job_of(const int* spre, int njobs, int i) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (spre[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Streaming fill of every constant tile: fill = 0 or 1, eps = eps_bg or
+// eps_fg, 16-byte stores along x rows, one warp per row (a store instruction
+// covers 512 contiguous bytes).  Band tiles are left to k_build.
+__global__ void __launch_bounds__(256) k_fill(const Job* __restrict__ jobs, int njobs) {
+  const Job& J = jobs[job_by_rows(jobs, njobs, blockIdx.x)];
+  if (!J.do_build) return;
+  const int nx = J.g.nx, ny = J.g.ny, nz = J.g.nz;
+  const int lx = J.g.lx, ly = J.g.ly, lz = J.g.lz, ntx = J.g.ntx, nty = J.g.nty;
+  const int rows = J.g.C * nz * ny;
+  const float e0 = J.g.eps_bg, e1 = J.g.eps_bg + J.g.deps;
+  float* __restrict__ fill = J.fill;
+  float* __restrict__ eps = J.eps;
+  const bool vec = (nx & 3) == 0 &&
+                   ((reinterpret_cast<uintptr_t>(eps) | reinterpret_cast<uintptr_t>(fill)) & 15) == 0;
+  const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;  // 8 warps, 8 rows
+  const int row = (blockIdx.x - J.row_base) * kFillRows + wrow;
+  if (row >= rows) return;
+  const int j = row % ny, k = (row / ny) % nz;
+  const size_t base = (size_t)row * nx;
+  const unsigned char* __restrict__ tcl = J.tclass + ((k >> lz) * nty + (j >> ly)) * ntx;
+  if (vec) {
+    float4* f4 = reinterpret_cast<float4*>(fill + base);
+    float4* e4 = reinterpret_cast<float4*>(eps + base);
+    for (int v = lane; v < (nx >> 2); v += 32) {
+      const int cls = __ldg(tcl + ((4 * v) >> lx));
+      if (cls == 2) continue;
+      const float f = cls ? 1.f : 0.f, e = cls ? e1 : e0;
+      if (fill) f4[v] = make_float4(f, f, f, f);
+      e4[v] = make_float4(e, e, e, e);
+    }
+  } else {
+    for (int i = lane; i < nx; i += 32) {
+      const int cls = __ldg(tcl + (i >> lx));
+      if (cls == 2) continue;
+      if (fill) fill[base + i] = cls ? 1.f : 0.f;
+      eps[base + i] = cls ? e1 : e0;
+    }
+  }
+}
+
+// Band tiles of the build: persistent over the binner's compacted list, the
+// tile's primitives staged with their factor tables, the folded program run
+// at every sample of the tile.
+__global__ void __launch_bounds__(kBlock) k_build(const Job* __restrict__ jobs, int njobs) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* tape = reinterpret_cast<float*>(smem);
-  PrimRec* sl = reinterpret_cast<PrimRec*>(tape + kMaxOps * kBlock);
-  float* tab = reinterpret_cast<float*>(sl + kMaxLeaves);
-  LeafTab* lt = reinterpret_cast<LeafTab*>(tab + kBuildTab);
-  uint16_t* sops = reinterpret_cast<uint16_t*>(lt + kMaxLeaves);
-  __shared__ int sjob;
+  float* pool = tape + kMaxOps * kBlock;
+  uint16_t* sops = reinterpret_cast<uint16_t*>(pool + kBuildPool);
+  int* spre = reinterpret_cast<int*>(sops + kMaxOps);  // prefix of band-tile counts
   const int tid = threadIdx.x;
-  for (int gt = blockIdx.x; gt < tiles_padded; gt += gridDim.x) {
-    __syncthreads();  // the previous tile is done with sjob and the staged program
-    if (tid == 0) sjob = job_by_tile(jobs, njobs, gt);
-    __syncthreads();
-    const Job& J = jobs[sjob];
+  if (tid == 0) job_prefix(jobs, njobs, false, spre);
+  __syncthreads();
+  const int total = spre[njobs];
+  for (int gi_ = blockIdx.x; gi_ < total; gi_ += gridDim.x) {
+    const int jb = job_of(spre, njobs, gi_);
+    const Job& J = jobs[jb];
     const GridDev& g = J.g;
-    const int t = gt - J.tile_base;
-    if (!J.do_build || t >= g.T) continue;
+    const int t = J.list[gi_ - spre[jb]];
     const TileProg* P = J.progs + t;
     const int nops = P->nops, nleaf = P->nleaf;
-    const float cval = P->cval;
     const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
-    if (nops > 0) {
-      stage_tile(P, J.prims, nops, nleaf, sops, sl, tid);
-      __syncthreads();
-      if (tid == 0) tables_plan(sl, nleaf, g, false, kBuildTab, lt);
-      __syncthreads();
-      tables_fill(sl, nleaf, g, lt, false, tx << g.lx, ty << g.ly, tz << g.lz, tab, tid, J.auxf,
-                  J.auxd);
-      __syncthreads();
-    }
+    const TilePool tp = carve_pool(pool, kBuildPool, nleaf, 0);
+    __syncthreads();  // the previous tile is done with the staged program
+    stage_tile(P, J.prims, nops, nleaf, sops, tp.sl, tid);
+    __syncthreads();
+    if (tid == 0) tables_plan(tp.sl, nleaf, g, false, tp.cap, tp.lt);
+    __syncthreads();
+    tables_fill(tp.sl, nleaf, g, tp.lt, false, tx << g.lx, ty << g.ly, tz << g.lz, tp.tab, tid,
+                J.auxf, J.auxd);
+    __syncthreads();
     const int lxy = g.lx + g.ly, lxyz = lxy + g.lz;
     const int ncc = g.C << lxyz;
     const size_t plane = (size_t)g.nx * g.ny * g.nz;
-    const float eps_bg = g.eps_bg, deps = g.deps;
     float* __restrict__ fill = J.fill;
     float* __restrict__ eps = J.eps;
-    if (nops == 0) {
-      // constant tile: a pure streaming store, 16-byte vectors along x rows
-      const bool vec = (g.nx & 3) == 0 &&
-                       ((reinterpret_cast<uintptr_t>(eps) | reinterpret_cast<uintptr_t>(fill)) & 15) == 0;
-      const float e = eps_bg + deps * cval;
-      const int vpr = (1 << g.lx) >> 2;  // float4 per tile row
-      const int nv = (ncc >> g.lx) * vpr;
-      for (int r = tid; r < nv; r += kBlock) {
-        const int row = r / vpr, v4 = r - row * vpr;
-        const int y = row & ((1 << g.ly) - 1), z = (row >> g.ly) & ((1 << g.lz) - 1),
-                  c = row >> (g.ly + g.lz);
-        const int gi = (tx << g.lx) + 4 * v4, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
-        if (gi >= g.nx || gj >= g.ny || gk >= g.nz) continue;
-        const size_t o = (size_t)c * plane + ((size_t)gk * g.ny + gj) * g.nx + gi;
-        if (vec) {  // nx % 4 == 0, so the four cells are all inside the row
-          if (fill) *reinterpret_cast<float4*>(fill + o) = make_float4(cval, cval, cval, cval);
-          *reinterpret_cast<float4*>(eps + o) = make_float4(e, e, e, e);
-        } else {
-          for (int u = 0; u < 4 && gi + u < g.nx; ++u) {
-            if (fill) fill[o + u] = cval;
-            eps[o + u] = e;
-          }
-        }
-      }
-      continue;
-    }
     for (int l = tid; l < ncc; l += kBlock) {
       const int x = l & ((1 << g.lx) - 1), y = (l >> g.lx) & ((1 << g.ly) - 1),
                 z = (l >> lxy) & ((1 << g.lz) - 1), c = l >> lxyz;
       const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
       if (gi >= g.nx || gj >= g.ny || gk >= g.nz) continue;
-      float v = cval;
-      if (nops > 0) {
-        const Cell cc{gi, gj, gk, g.off[c][0], g.off[c][1], g.off[c][2]};
-        const TileLoc q{x, y, z, c, 1 << g.lx, 1 << g.ly, 1 << g.lz};
-        v = eval_forward(sops, nops, sl, lt, tab, q, cc, g.logic, tape, tid, J.auxf, J.auxd);
-      }
+      const Cell cc{gi, gj, gk, g.off[c][0], g.off[c][1], g.off[c][2]};
+      const TileLoc q{x, y, z, c, 1 << g.lx, 1 << g.ly, 1 << g.lz};
+      const float v = eval_forward(sops, nops, tp.sl, tp.lt, tp.tab, q, cc, g.logic, tape, tid,
+                                   J.auxf, J.auxd);
       const size_t o = (size_t)c * plane + ((size_t)gk * g.ny + gj) * g.nx + gi;
       if (fill) fill[o] = v;
-      eps[o] = eps_bg + deps * v;
+      eps[o] = g.eps_bg + g.deps * v;
     }
   }
 }
@@ -1074,151 +1159,251 @@ __device__ __forceinline__ void warp_accumulate(int n, int sb, const int* pk, co
   }
 }
 
-constexpr size_t kVjpSmem = (size_t)kMaxOps * kBlock * 4 + 2 * (size_t)kWarps * kMaxSlots * 4 +
-                            2 * (size_t)kMaxPairs * kBlock * 4 + kMaxLeaves * sizeof(PrimRec) +
-                            (size_t)kVjpTab * 4 + (size_t)kMaxTileCells * 3 * 4 +
-                            kMaxLeaves * sizeof(LeafTab) + kMaxOps * 2 + (kMaxLeaves + 1) * 4 +
-                            (kMaxJobs + 1) * 4 + 16;
+// One key of a tabled box: the warp's values reduced with a fixed xor tree,
+// added by lane 0 into the warp's compensated row (warp-uniform call).
+__device__ __forceinline__ void key_reduce(int slot, float v, float* acc, float* cmp, int lane) {
+  if (__ballot_sync(0xffffffffu, v != 0.f) == 0u) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) neumaier(acc[slot], cmp[slot], v);
+}
 
-__global__ void __launch_bounds__(kBlock) k_vjp(const Job* __restrict__ jobs, int njobs,
-                                                int* __restrict__ err) {
+// d s / d (box scalar k) * a for the six scalars of a tabled box leaf
+// (keys 0..5 = x0, x1, y0, y1, z0, z1), each reduced over the warp.
+__device__ __forceinline__ void box_tab_reduce(const LeafTab& t, const TileLoc& q, const float* tab,
+                                               float a, const GridDev& g, float* acc, float* cmp,
+                                               int lane) {
+  const int4 v = t.v, d = t.d;
+  const float fx = tab[v.x + q.c * q.TX + q.x], fy = tab[v.y + q.c * q.TY + q.y],
+              fz = tab[v.z + q.c * q.TZ + q.z];
+  const int k = d.w >> 3;
+  if (k & 3) {
+    const float ax = a * fy * fz * g.invd[0];
+    if (k & 1) key_reduce(t.slot[0], tab[d.x + (2 * q.c) * q.TX + q.x] * ax * t.coef[0], acc, cmp, lane);
+    if (k & 2) key_reduce(t.slot[1], tab[d.x + (2 * q.c + 1) * q.TX + q.x] * ax * t.coef[1], acc, cmp, lane);
+  }
+  if (k & 12) {
+    const float ay = a * fx * fz * g.invd[1];
+    if (k & 4) key_reduce(t.slot[2], tab[d.y + (2 * q.c) * q.TY + q.y] * ay * t.coef[2], acc, cmp, lane);
+    if (k & 8) key_reduce(t.slot[3], tab[d.y + (2 * q.c + 1) * q.TY + q.y] * ay * t.coef[3], acc, cmp, lane);
+  }
+  if (k & 48) {
+    const float az = a * fx * fy * g.invd[2];
+    if (k & 16) key_reduce(t.slot[4], tab[d.z + (2 * q.c) * q.TZ + q.z] * az * t.coef[4], acc, cmp, lane);
+    if (k & 32) key_reduce(t.slot[5], tab[d.z + (2 * q.c + 1) * q.TZ + q.z] * az * t.coef[5], acc, cmp, lane);
+  }
+}
+
+// Activity of the tile's samples, per axis: a sample can have a nonzero
+// Jacobian row only where some parameter-driven scalar of a tabled box has a
+// nonzero derivative-table entry at its x, y or z (each scalar moves one
+// face), or anywhere when a parameter-driven leaf is not a tabled box.
+// act1 holds one byte per (component, coordinate) of the x, y, z blocks.
+constexpr int kAct1 = 3 * (64 + 16 + 8);
+__device__ __forceinline__ void activity_axes(const LeafTab* lt, int nleaf, const GridDev& g,
+                                              const float* tab, unsigned char* act1, int tid) {
+  const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
+  for (int e = tid; e < C * (TX + TY + TZ); e += kBlock) {
+    int ax = 0, r = e, T = TX;
+    if (r >= C * TX) { r -= C * TX; ax = 1; T = TY; }
+    if (ax == 1 && r >= C * TY) { r -= C * TY; ax = 2; T = TZ; }
+    const int c = r / T, u = r - c * T;
+    bool on = false;
+    for (int lf = 0; lf < nleaf && !on; ++lf) {
+      const int4 d = lt[lf].d;
+      if ((d.w & (tACT | tOK | tBOX)) != (tACT | tOK | tBOX)) continue;
+      const int k = (d.w >> (3 + 2 * ax)) & 3;
+      const int dt = ax == 0 ? d.x : (ax == 1 ? d.y : d.z);
+      on = ((k & 1) && tab[dt + (2 * c) * T + u] != 0.f) ||
+           ((k & 2) && tab[dt + (2 * c + 1) * T + u] != 0.f);
+    }
+    act1[e] = on;
+  }
+}
+
+constexpr int kSeedChunk = 512;  // active samples whose seeds are staged at once
+constexpr size_t kVjpFixed = (size_t)kMaxOps * kBlock * 4 + (size_t)kVjpPool * 4 +
+                             2 * (size_t)kMaxPairs * kBlock * 4 + (size_t)kSeedChunk * 4 +
+                             (size_t)kMaxTileCells * 3 * 2 + kMaxOps * 2 + (kMaxLeaves + 1) * 4 +
+                             kAct1 + kWarps * 4 + 4;
+size_t vjp_smem(int njobs) { return ((kVjpFixed + 15) & ~(size_t)15) + (size_t)spre_len(njobs) * 4; }
+
+__global__ void __launch_bounds__(kBlock, 4) k_vjp(const Job* __restrict__ jobs, int njobs,
+                                                   int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* tape = reinterpret_cast<float*>(smem);
-  float* acc = tape + kMaxOps * kBlock;
-  float* cmp = acc + kWarps * kMaxSlots;
-  float* pv = cmp + kWarps * kMaxSlots;
+  float* pool = tape + kMaxOps * kBlock;
+  float* pv = pool + kVjpPool;
   int* pk = reinterpret_cast<int*>(pv + kMaxPairs * kBlock);
-  PrimRec* sl = reinterpret_cast<PrimRec*>(pk + kMaxPairs * kBlock);
-  float* tab = reinterpret_cast<float*>(sl + kMaxLeaves);
-  float* zsb = tab + kVjpTab;  // the seed of every sample of the tile
-  LeafTab* lt = reinterpret_cast<LeafTab*>(zsb + kMaxTileCells * 3);
-  uint16_t* sops = reinterpret_cast<uint16_t*>(lt + kMaxLeaves);
+  float* zsb = reinterpret_cast<float*>(pk + kMaxPairs * kBlock);  // seeds of a chunk
+  uint16_t* slist = reinterpret_cast<uint16_t*>(zsb + kSeedChunk);  // active samples
+  uint16_t* sops = slist + kMaxTileCells * 3;
   int* sbase = reinterpret_cast<int*>(sops + kMaxOps);
-  int* spre = sbase + kMaxLeaves + 1;  // prefix of band-tile counts over the jobs
+  unsigned char* act1 = reinterpret_cast<unsigned char*>(sbase + kMaxLeaves + 1);
+  int* swm = reinterpret_cast<int*>(act1 + kAct1);  // per-warp active counts, then the all-flag
+  int* spre = reinterpret_cast<int*>(smem + ((kVjpFixed + 15) & ~(size_t)15));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
-    int sum = 0;
-    for (int j = 0; j < njobs; ++j) {
-      spre[j] = sum;
-      if (jobs[j].do_grad) sum += jobs[j].counters[0];
-    }
-    spre[njobs] = sum;
-  }
+  if (tid == 0) job_prefix(jobs, njobs, true, spre);
   __syncthreads();
   const int total = spre[njobs];
   for (int gi_ = blockIdx.x; gi_ < total; gi_ += gridDim.x) {
-    int jb = 0;
-    {
-      int lo = 0, hi = njobs - 1;  // last job whose prefix is <= gi_
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (spre[mid] <= gi_) lo = mid; else hi = mid - 1;
-      }
-      jb = lo;  // zero-width ranges (no band tiles, or no gradient) never end last
-    }
+    const int jb = job_of(spre, njobs, gi_);
     const Job& J = jobs[jb];
     const GridDev& g = J.g;
     const int t = J.list[gi_ - spre[jb]];
     const TileProg* P = J.progs + t;
-    const int nops = P->nops, nleaf = P->nleaf;
+    const int nops = P->nops, nleaf = P->nleaf, nslot = P->nslot;
     const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
     const VjpArgs& va = J.va;
-    __syncthreads();
-    stage_tile(P, J.prims, nops, nleaf, sops, sl, tid);
-    __syncthreads();
-    if (tid == 0) {
-      int sum = 0;
-      for (int l = 0; l < nleaf; ++l) { sbase[l] = sum; sum += sl[l].nact; }
-      sbase[nleaf] = sum;
-      tables_plan(sl, nleaf, g, true, kVjpTab, lt);
-    }
-    __syncthreads();
-    tables_fill(sl, nleaf, g, lt, true, tx << g.lx, ty << g.ly, tz << g.lz, tab, tid, J.auxf, J.auxd);
-    const int nslot = sbase[nleaf];
-    if (nslot > kMaxSlots) {
+    if (nslot > kMaxSlots) {  // flagged by the binner too; uniform over the block
       if (tid == 0) atomicOr(err, eSlotOverflow);
       continue;
     }
-    for (int q = tid; q < kWarps * nslot; q += kBlock) { acc[q] = 0.f; cmp[q] = 0.f; }
+    const TilePool tp = carve_pool(pool, kVjpPool, nleaf, kWarps * nslot);
+    const PrimRec* sl = tp.sl;
+    const LeafTab* lt = tp.lt;
+    const float* tab = tp.tab;
+    __syncthreads();  // the previous tile is done with the pool
+    stage_tile(P, J.prims, nops, nleaf, sops, tp.sl, tid);
+    for (int q = tid; q < 2 * kWarps * nslot; q += kBlock) tp.acc[q] = 0.f;  // acc, cmp
     __syncthreads();
-    float* wacc = acc + warp * nslot;
-    float* wcmp = cmp + warp * nslot;
+    stage_slots(sl, nleaf, J.act, J.actc, tp.lt, tid);
+    __syncthreads();
+    if (tid == 0) {
+      int sum = 0, all = 0;
+      for (int l = 0; l < nleaf; ++l) { sbase[l] = sum; sum += sl[l].nact; }
+      sbase[nleaf] = sum;
+      tables_plan(sl, nleaf, g, true, tp.cap, tp.lt);
+      for (int l = 0; l < nleaf; ++l) {
+        const int f = lt[l].d.w;
+        if ((f & tACT) && (f & (tOK | tBOX)) != (tOK | tBOX)) all = 1;
+      }
+      swm[kWarps] = all;
+    }
+    __syncthreads();
+    tables_fill(sl, nleaf, g, lt, true, tx << g.lx, ty << g.ly, tz << g.lz, tp.tab, tid, J.auxf,
+                J.auxd);
+    __syncthreads();
+    activity_axes(lt, nleaf, g, tab, act1, tid);
+    __syncthreads();
+    float* wacc = tp.acc + warp * nslot;
+    float* wcmp = tp.cmp + warp * nslot;
     const int lxy = g.lx + g.ly, lxyz = lxy + g.lz;
     const int ncc = g.C << lxyz;
+    const int TXm = (1 << g.lx) - 1, TYm = (1 << g.ly) - 1, TZm = (1 << g.lz) - 1;
     const size_t plane = (size_t)g.nx * g.ny * g.nz;
-    // stream the tile's fields first: independent loads, many in flight
-#pragma unroll 4
-    for (int l0 = 0; l0 < ncc; l0 += kBlock) {
-      const int l = l0 + tid;
-      const int x = l & ((1 << g.lx) - 1), y = (l >> g.lx) & ((1 << g.ly) - 1),
-                z = (l >> lxy) & ((1 << g.lz) - 1), c = l >> lxyz;
-      const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
-      float zs = 0.f;
-      if (gi < g.nx && gj < g.ny && gk < g.nz) {
-        const size_t o = ((size_t)gk * g.ny + gj) * g.nx + gi;
-        if (va.G) {
-          zs = __ldg(va.G + (size_t)c * plane + o);
-        } else {
-          const float2 f = __ldg(va.ef[c] + o), a = __ldg(va.ea[c] + o);
-          const float pr = f.x * a.x - f.y * a.y, pi = f.x * a.y + f.y * a.x;
-          zs = va.w[c].x * pr - va.w[c].y * pi;  // Re(w E_adj E), no conjugate (Eq. 1)
-        }
-        zs *= g.deps;  // eps = eps_bg + deps fill
+    // Active samples, compacted per warp over its contiguous quarter of the
+    // tile (ncc is a multiple of 128) with ballots: active index i runs
+    // through the samples in order, so the accumulation order is fixed.
+    const int per = ncc / kWarps;
+    {
+      const bool all = swm[kWarps] != 0;
+      const int C = g.C, TX = TXm + 1, TY = TYm + 1;
+      uint16_t* wl = slist + warp * per;
+      int cnt = 0;
+      for (int l0 = warp * per; l0 < (warp + 1) * per; l0 += 32) {
+        const int l = l0 + lane;
+        const int x = l & TXm, y = (l >> g.lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
+        const bool in = (tx << g.lx) + x < g.nx && (ty << g.ly) + y < g.ny && (tz << g.lz) + z < g.nz;
+        const bool act = in && (all || act1[c * TX + x] || act1[C * TX + c * TY + y] ||
+                                act1[C * (TX + TY) + c * (TZm + 1) + z]);
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        if (act) wl[cnt + __popc(m & ((1u << lane) - 1u))] = (uint16_t)l;
+        cnt += __popc(m);
       }
-      zsb[l] = zs;
+      if (lane == 0) swm[warp] = cnt;  // the all-flag sits in swm[kWarps]
     }
-    __syncthreads();  // tables ready
-    for (int l0 = 0; l0 < ncc; l0 += kBlock) {
-      const int l = l0 + tid;
-      const int x = l & ((1 << g.lx) - 1), y = (l >> g.lx) & ((1 << g.ly) - 1),
-                z = (l >> lxy) & ((1 << g.lz) - 1), c = l >> lxyz;
-      const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
-      const float zs = zsb[l];
-      const Cell cc{gi, gj, gk, g.off[c][0], g.off[c][1], g.off[c][2]};
-      const TileLoc q{x, y, z, c, 1 << g.lx, 1 << g.ly, 1 << g.lz};
-      eval_forward(sops, nops, sl, lt, tab, q, cc, g.logic, tape, tid, J.auxf, J.auxd);
-      // reverse sweep through the logic: tape slots become adjoints d fill / d node
-      tape[(nops - 1) * kBlock + tid] = 1.f;
-      for (int pos = nops - 1; pos >= 0; --pos) {
-        const int op = sops[pos];
-        const int code = op & 7;
-        if (code == fPush) continue;
-        const int a = (op >> 3) & 63, b = (op >> 9) & 63;
-        const float adj = tape[pos * kBlock + tid];
-        const float vb = code == fCompl ? 0.f : tape[b * kBlock + tid];
-        float da, db;
-        op_bwd(code, g.logic, tape[a * kBlock + tid], vb, da, db);
-        tape[a * kBlock + tid] = adj * da;
-        if (code != fCompl) tape[b * kBlock + tid] = adj * db;
+    __syncthreads();
+    int wpre[kWarps + 1];
+    wpre[0] = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) wpre[w + 1] = wpre[w] + swm[w];
+    const int nact_cells = wpre[kWarps];
+    auto apos = [&](int i) {  // slist position of active index i
+      int w = 0;
+#pragma unroll
+      for (int v = 1; v < kWarps; ++v) w += i >= wpre[v];
+      return w * per + (i - wpre[w]);
+    };
+    if (tid == 0) atomicAdd(&J.counters[3], nact_cells);
+    for (int c0 = 0; c0 < nact_cells; c0 += kSeedChunk) {
+      const int c1 = min(nact_cells, c0 + kSeedChunk);
+      // stream the chunk's fields: independent loads, many in flight
+#pragma unroll
+      for (int i0 = c0; i0 < c0 + kSeedChunk; i0 += kBlock) {
+        const int i = i0 + tid;
+        if (i < c1) {
+          const int l = slist[apos(i)];
+          const int x = l & TXm, y = (l >> g.lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
+          const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
+          const size_t o = ((size_t)gk * g.ny + gj) * g.nx + gi;
+          float zs;
+          if (va.G) {
+            zs = __ldg(va.G + (size_t)c * plane + o);
+          } else {
+            const float2 f = __ldg(va.ef[c] + o), a = __ldg(va.ea[c] + o);
+            const float pr = f.x * a.x - f.y * a.y, pi = f.x * a.y + f.y * a.x;
+            zs = va.w[c].x * pr - va.w[c].y * pi;  // Re(w E_adj E), no conjugate (Eq. 1)
+          }
+          zsb[i - c0] = zs * g.deps;  // eps = eps_bg + deps fill
+        }
       }
-      // primitives: d s / d q times the seed, reduced per slot
-      for (int pos = 0; pos < nops; ++pos) {
-        const int op = sops[pos];
-        if ((op & 7) != fPush) continue;
-        const int lf = (op >> 3) & 63;
-        if (sl[lf].nact == 0) continue;
-        const float a = zs * tape[pos * kBlock + tid];
-        int n = 0;
-        if (a != 0.f) {
-          const LeafTab t = lt[lf];
-          if (t.ok && sl[lf].kind == kBox)
-            n = box_tab_pairs(sl[lf], t, q, tab, a, g, J.act, J.actc, pk + tid, pv + tid);
-          else
+      for (int i0 = c0; i0 < c1; i0 += kBlock) {
+        if (i0 + warp * 32 >= c1) continue;  // no live lane in this warp (warp-uniform)
+        const int i = i0 + tid;
+        const bool live = i < c1;
+        const int l = live ? slist[apos(i)] : 0;
+        const int x = l & TXm, y = (l >> g.lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
+        const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
+        const float zs = live ? zsb[i - c0] : 0.f;
+        const Cell cc{gi, gj, gk, g.off[c][0], g.off[c][1], g.off[c][2]};
+        const TileLoc q{x, y, z, c, 1 << g.lx, 1 << g.ly, 1 << g.lz};
+        eval_forward(sops, nops, sl, lt, tab, q, cc, g.logic, tape, tid, J.auxf, J.auxd);
+        // reverse sweep through the logic: tape slots become adjoints d fill / d node
+        tape[(nops - 1) * kBlock + tid] = 1.f;
+        for (int pos = nops - 1; pos >= 0; --pos) {
+          const int op = sops[pos];
+          const int code = op & 7;
+          if (code == fPush) continue;
+          const int a = (op >> 3) & 63, b = (op >> 9) & 63;
+          const float adj = tape[pos * kBlock + tid];
+          const float vb = code == fCompl ? 0.f : tape[b * kBlock + tid];
+          float da, db;
+          op_bwd(code, g.logic, tape[a * kBlock + tid], vb, da, db);
+          tape[a * kBlock + tid] = adj * da;
+          if (code != fCompl) tape[b * kBlock + tid] = adj * db;
+        }
+        // primitives: d s / d q times the seed, reduced per slot over the warp
+        for (int pos = 0; pos < nops; ++pos) {
+          const int op = sops[pos];
+          if ((op & 7) != fPush) continue;
+          const int lf = (op >> 3) & 63;
+          const int fl = lt[lf].d.w;
+          if (!(fl & tACT)) continue;
+          const float a = zs * tape[pos * kBlock + tid];
+          if (__ballot_sync(0xffffffffu, a != 0.f) == 0u) continue;
+          float* la = wacc + sbase[lf];
+          float* lc = wcmp + sbase[lf];
+          if ((fl & (tOK | tBOX)) == (tOK | tBOX)) {
+            box_tab_reduce(lt[lf], q, tab, a, g, la, lc, lane);
+            continue;
+          }
+          int n = 0;
+          if (a != 0.f)
             n = leaf_pairs(sl[lf], cc, a, g, J.act, J.actc, J.auxf, J.auxd, pk + tid, pv + tid);
+          warp_accumulate(n, 0, pk + tid, pv + tid, la, lc, lane);
+          if (sl[lf].kind == kPolygon)
+            poly_accumulate(sl[lf], cc, a, g, J.act, J.actc, J.auxd, la, lc, lane);
         }
-        warp_accumulate(n, sbase[lf], pk + tid, pv + tid, wacc, wcmp, lane);
-        if (sl[lf].kind == kPolygon)
-          poly_accumulate(sl[lf], cc, a, g, J.act, J.actc, J.auxd, wacc + sbase[lf],
-                          wcmp + sbase[lf], lane);
       }
-    }
+    }  // chunks of active samples
     __syncthreads();
     for (int s2 = tid; s2 < nslot; s2 += kBlock) {
       int lf = 0;
       while (lf + 1 < nleaf && sbase[lf + 1] <= s2) ++lf;
       const int qa = s2 - sbase[lf];
       float tot = 0.f;
-      for (int w = 0; w < kWarps; ++w) tot += acc[w * nslot + s2] + cmp[w * nslot + s2];
+      for (int w = 0; w < kWarps; ++w) tot += tp.acc[w * nslot + s2] + tp.cmp[w * nslot + s2];
       const PrimRec& R = sl[lf];
       if (tx >= R.pb[0] && tx < R.pb[1] && ty >= R.pb[2] && ty < R.pb[3] && tz >= R.pb[4] &&
           tz < R.pb[5]) {
@@ -1260,24 +1445,29 @@ __global__ void k_finalize(const Job* __restrict__ jobs, int njobs, int nparams)
 
 }  // namespace
 
-int build_blocks_per_sm() {
-  static int v = 0;
-  if (!v) {
-    cudaFuncSetAttribute(k_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBuildSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_build, kBlock, kBuildSmem);
-    if (v < 1) v = 1;
+// Resident blocks per SM for the two shared-memory classes of the job prefix.
+int build_blocks_per_sm(int njobs) {
+  static int v[2] = {0, 0};
+  const int k = njobs < 16 ? 0 : 1;
+  if (!v[k]) {
+    const size_t sm = build_smem(njobs);
+    cudaFuncSetAttribute(k_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem(kMaxJobs));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v[k], k_build, kBlock, sm);
+    if (v[k] < 1) v[k] = 1;
   }
-  return v;
+  return v[k];
 }
 
-int vjp_blocks_per_sm() {
-  static int v = 0;
-  if (!v) {
-    cudaFuncSetAttribute(k_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVjpSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_vjp, kBlock, kVjpSmem);
-    if (v < 1) v = 1;
+int vjp_blocks_per_sm(int njobs) {
+  static int v[2] = {0, 0};
+  const int k = njobs < 16 ? 0 : 1;
+  if (!v[k]) {
+    const size_t sm = vjp_smem(njobs);
+    cudaFuncSetAttribute(k_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vjp_smem(kMaxJobs));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v[k], k_vjp, kBlock, sm);
+    if (v[k] < 1) v[k] = 1;
   }
-  return v;
+  return v[k];
 }
 
 cudaError_t launch_prepare(const Job* jobs, const JobTotals& t, cudaStream_t s) {
@@ -1294,15 +1484,21 @@ cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_build(const Job* jobs, const JobTotals& t, int grid, cudaStream_t s) {
-  build_blocks_per_sm();
-  k_build<<<grid, kBlock, kBuildSmem, s>>>(jobs, t.njobs, t.tiles_padded);
+cudaError_t launch_fill(const Job* jobs, const JobTotals& t, cudaStream_t s) {
+  if (t.fill_blocks <= 0) return cudaSuccess;
+  k_fill<<<t.fill_blocks, 256, 0, s>>>(jobs, t.njobs);
   return cudaGetLastError();
 }
 
-cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int grid, cudaStream_t s) {
-  vjp_blocks_per_sm();
-  k_vjp<<<grid, kBlock, kVjpSmem, s>>>(jobs, t.njobs, err);
+cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s) {
+  const int grid = sms * build_blocks_per_sm(t.njobs);
+  k_build<<<grid, kBlock, build_smem(t.njobs), s>>>(jobs, t.njobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, cudaStream_t s) {
+  const int grid = sms * vjp_blocks_per_sm(t.njobs);
+  k_vjp<<<grid, kBlock, vjp_smem(t.njobs), s>>>(jobs, t.njobs, err);
   return cudaGetLastError();
 }
 

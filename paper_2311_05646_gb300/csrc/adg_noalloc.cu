@@ -164,6 +164,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   const size_t o_auxf = take(sizeof(float) * std::max(st.auxf_n, 1));
   const size_t o_progs = take(sizeof(TileProg) * (size_t)g.T);
   const size_t o_list = take(sizeof(int) * (size_t)g.T);
+  const size_t o_tcls = take((size_t)g.T);
   const size_t o_part = take(sizeof(float) * std::max<size_t>(part, 1));
   if (off > kNoAllocScratchBytes)
     return na_fail(ADG_EINVAL,
@@ -198,6 +199,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   float* d_auxf = reinterpret_cast<float*>(base + o_auxf);
   TileProg* d_progs = reinterpret_cast<TileProg*>(base + o_progs);
   int* d_list = reinterpret_cast<int*>(base + o_list);
+  unsigned char* d_tcls = base + o_tcls;
   float* d_part = reinterpret_cast<float*>(base + o_part);
   // ---- upload, clear, launch (prepare -> binner -> VJP -> finalize) ----
   NACU(cudaMemsetAsync(d_err, 0, sizeof(int), s));
@@ -231,6 +233,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   J.ref_qa = d_rqa;
   J.ref_coeff = d_rcoef;
   J.progs = d_progs;
+  J.tclass = d_tcls;
   J.list = d_list;
   J.counters = d_cnt;
   J.partial = d_part;
@@ -255,7 +258,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   NACU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   NACU(launch_prepare(d_job, t, s));
   NACU(launch_bin(d_job, t, d_err, s));
-  NACU(launch_vjp(d_job, t, d_err, sms * vjp_blocks_per_sm(), s));
+  NACU(launch_vjp(d_job, t, d_err, sms, s));
   NACU(launch_finalize(d_job, t, s));
   // ---- wait and report device-side checks ----
   int herr = 0;
