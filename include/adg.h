@@ -20,7 +20,12 @@
  *     adg_last_error() returns a thread-local message for the last failure.
  *   - Arguments are validated before any launch (ADG_EINVAL).  Device-side
  *     checks (tile capacity) set an error word that adg_sync() reports as
- *     ADG_EDEVICE; no kernel traps or faults on bad data.
+ *     ADG_EDEVICE; no kernel traps or faults on bad data.  Per tile, at most
+ *     64 primitives may have an edge band crossing it, its folded logic
+ *     program at most 120 ops (fold stack depth 32), with at most 384
+ *     (primitive, parameter) accumulators, and its staged primitives plus
+ *     accumulators must fit the VJP's 24 KB tile pool; a smaller tile shape
+ *     lowers all of these.
  *   - Layout of every per-cell array: [ncomp][nz][ny][nx], x fastest, fp32
  *     (fields: complex64 = interleaved (re, im) fp32 pairs).
  */

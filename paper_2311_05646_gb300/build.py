@@ -31,7 +31,8 @@ def nvcc() -> str:
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "adg_internal.h"), os.path.join(ROOT, "include", "adg.h")]
+    deps = [src, os.path.join(CSRC, "adg_internal.h"), os.path.join(CSRC, "adg_host.h"),
+            os.path.join(ROOT, "include", "adg.h")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps if os.path.exists(d))
 
 

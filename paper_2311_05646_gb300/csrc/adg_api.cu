@@ -63,6 +63,8 @@ struct adg_ctx {
   int device = 0;
   int sms = 1;
   int* d_err = nullptr;
+  float* d_gtape = nullptr;  // VJP tape for programs longer than the shared-memory tape
+  int gtape_blocks = 0;
   // measurement: event pairs around launches while profiling is on
   bool prof = false;
   struct Rec { int kernel; cudaEvent_t a, b; };
@@ -175,9 +177,15 @@ extern "C" adg_status adg_ctx_create(int32_t device, adg_ctx** out) {
   adg_ctx* c = new adg_ctx();
   c->device = device;
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
-  cudaError_t e = cudaMalloc((void**)&c->d_err, sizeof(int));
+  cudaError_t e = init_kernel_attributes();
+  c->gtape_blocks = c->sms * vjp_blocks_per_sm(1);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&c->d_gtape, sizeof(float) * kTapeBlockFloats * c->gtape_blocks);
   if (e != cudaSuccess) {
+    cudaFree(c->d_err);
+    cudaFree(c->d_gtape);
     delete c;
     return fail(ADG_ECUDA, "adg_ctx_create: %s", cudaGetErrorString(e));
   }
@@ -199,6 +207,7 @@ extern "C" adg_status adg_ctx_destroy(adg_ctx* ctx) {
   for (auto& t : ctx->tickets) cudaEventDestroy(t.ev);
   if (ctx->capture) cudaStreamDestroy(ctx->capture);
   cudaFree(ctx->d_err);
+  cudaFree(ctx->d_gtape);
   delete ctx;
   return ADG_OK;
 }
@@ -435,7 +444,7 @@ adg_status run_jobs(adg_ctx* ctx, const Job* d_jobs, const JobTotals& t, bool an
   if (any_grad) {
     {
       ProfScope ps(ctx, ADG_K_VJP, s);
-      CU(launch_vjp(d_jobs, t, ctx->d_err, ctx->sms, s));
+      CU(launch_vjp(d_jobs, t, ctx->d_err, ctx->sms, ctx->d_gtape, ctx->gtape_blocks, s));
     }
     ProfScope ps(ctx, ADG_K_FINALIZE, s);
     CU(launch_finalize(d_jobs, t, s));
@@ -738,7 +747,7 @@ extern "C" adg_status adg_sync(adg_ctx* ctx, void* stream) {
     CU(cudaMemset(ctx->d_err, 0, sizeof(int)));
     return fail(ADG_EDEVICE,
                 "device check failed (bits 0x%x: 1 leaves/tile, 2 ops/tile, 4 depth, 8 slots/tile, "
-                "16 partial range, 32 program); use a smaller tile shape",
+                "16 partial range, 32 program, 64 tile pool); use a smaller tile shape",
                 e);
   }
   return ADG_OK;

@@ -8,8 +8,10 @@ namespace adg {
 
 // Per-tile capacities of the binned kernels.  A tile that would exceed one of
 // them is reported through the device error word (never written out of range).
-constexpr int kMaxLeaves = 48;  // primitives whose edge band crosses the tile
-constexpr int kMaxOps = 32;     // folded logic program length
+constexpr int kMaxLeaves = 64;  // primitives whose edge band crosses the tile
+constexpr int kMaxOps = 120;    // folded logic program length (7-bit operand fields)
+constexpr int kSmemOps = 32;    // VJP tape entries kept in shared memory; longer
+                                // programs use a per-block slice of a global tape
 constexpr int kMaxDepth = 32;   // fold stack depth (checked at design creation)
 constexpr int kMaxSlots = 384;  // (primitive, active scalar) accumulators
 constexpr int kMaxPairs = 6;    // d s / d q terms one cell yields per leaf (box, graph 6; circle 5)
@@ -17,14 +19,25 @@ constexpr int kBlock = 128;     // threads per CTA of the build / VJP kernels
 constexpr int kMaxTileCells = 1024;  // cells per tile (per component)
 constexpr int kWarps = kBlock / 32;
 constexpr int kMaxPolyVerts = 256;  // vertices of one convex polygon
+static_assert(kMaxOps < 127 && kMaxLeaves < 127, "op operands are 7-bit fields, 127 = constant 1");
+// Per-tile pools of the band kernels (floats): staged leaves (PrimRec) and
+// their table descriptors (80 B each), the VJP's per-warp accumulator rows,
+// then factor tables in what is left (at least kPoolSpare floats).
+constexpr int kBuildPool = 4096;
+constexpr int kVjpPool = 6144;
+constexpr int kPoolSpare = 192;
+constexpr int kLeafTabBytes = 80;
+constexpr size_t kTapeBlockFloats = (size_t)kMaxOps * kBlock;  // global tape per VJP block
 
 enum : int32_t { kBox = 0, kCircle = 1, kPolygon = 2, kGraph = 3 };
 enum : int32_t { kLinear = 0, kSigmoid = 1, kQuadratic = 2, kSin = 3, kErf = 4 };
 enum : int32_t { kBoundX = 1, kBoundY = 2, kBoundZ = 4, kRectSigma = 8, kGraphAbove = 16 };
 // chained (binary) design program, one int32 word per op: (code << 24) | arg
 enum : int32_t { cPush = 0, cUnion = 1, cInter = 2, cDiff = 3 };
-// folded per-tile program, one uint16 per op: code | a << 3 | b << 9
+// folded per-tile program, one uint16 per op: code | a << 2 | b << 9 (code 2
+// bits, operands 7 bits); the complement of b is stored as difference(kOne, b)
 enum : int32_t { fPush = 0, fUnion = 1, fInter = 2, fDiff = 3, fCompl = 4 };
+constexpr int kOne = 127;
 // device error bits
 enum : int32_t {
   eLeafOverflow = 1,
@@ -32,7 +45,8 @@ enum : int32_t {
   eDepthOverflow = 4,
   eSlotOverflow = 8,
   ePartialRange = 16,
-  eBadProgram = 32
+  eBadProgram = 32,
+  ePoolOverflow = 64
 };
 
 struct GridDev {
@@ -65,6 +79,14 @@ struct alignas(16) PrimRec {
   float af[6];
   float g[4];  // circle: R, R^2 (hi, lo) in cells, [3] = 1 if R < 0; polygon: [0] = winding sign
 };
+
+// Floats of a tile's pool taken by nleaf staged leaves with their descriptors
+// and nacc accumulators (plus as many compensation terms).
+__host__ __device__ constexpr int pool_need(int nleaf, int nacc) {
+  return (nleaf * ((int)sizeof(PrimRec) + kLeafTabBytes) / 4 + 2 * nacc + 3) & ~3;
+}
+static_assert(pool_need(kMaxLeaves, 0) + kPoolSpare <= kBuildPool,
+              "the build pool holds any tile's leaves");
 
 struct TileProg {
   int nops;   // 0: constant tile, value cval
@@ -135,8 +157,13 @@ cudaError_t launch_prepare(const Job* jobs, const JobTotals& t, cudaStream_t s);
 cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s);
 cudaError_t launch_fill(const Job* jobs, const JobTotals& t, cudaStream_t s);
 cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s);
-cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, cudaStream_t s);
+// gtape: kTapeBlockFloats floats per block for gtape_blocks blocks; the grid
+// never exceeds gtape_blocks.
+cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, float* gtape,
+                       int gtape_blocks, cudaStream_t s);
 cudaError_t launch_finalize(const Job* jobs, const JobTotals& t, cudaStream_t s);
+// Shared-memory limits of the kernels; call once per device before any capture.
+cudaError_t init_kernel_attributes();
 int build_blocks_per_sm(int njobs);
 int vjp_blocks_per_sm(int njobs);
 void set_last_error(const char* msg);  // the thread-local text of adg_last_error()

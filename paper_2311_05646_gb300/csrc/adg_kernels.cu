@@ -19,6 +19,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "adg_internal.h"
 
@@ -545,7 +546,18 @@ __device__ __noinline__ void poly_accumulate(const PrimRec& P, const Cell& c, fl
 // Fold-stack entry (16 bits): kind (0 = const 0, 1 = const 1, 2 = expression)
 // | root << 2 | start << 8 (root: position of the expression's last op;
 // start: its first; both < kMaxOps <= 64).
-__device__ __forceinline__ int mkE(int root, int start) { return 2 | (root << 2) | (start << 8); }
+__device__ __forceinline__ int mkE(int root, int start) { return 2 | (root << 2) | (start << 9); }
+
+// Folded op words (code 2 bits, operands 7 bits; complement = difference(kOne, b)).
+__device__ __forceinline__ int mk_op(int code, int a, int b) { return code | (a << 2) | (b << 9); }
+struct FoldOp {
+  int code, a, b;  // complement: code fCompl, operand in a
+};
+__device__ __forceinline__ FoldOp fold_op(int op) {
+  FoldOp f{op & 3, (op >> 2) & 127, (op >> 9) & 127};
+  if (f.code == fDiff && f.a == kOne) { f.code = fCompl; f.a = f.b; }
+  return f;
+}
 
 // First job whose range end exceeds idx (ends are nondecreasing).
 __device__ __forceinline__ int job_by_tile(const Job* jobs, int n, int idx) {
@@ -666,7 +678,7 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain,
           else e |= eLeafOverflow;
         }
         if (slot >= 0 && nops < kMaxOps) {
-          sop[nops][tid] = (uint16_t)(fPush | (slot << 3));
+          sop[nops][tid] = (uint16_t)mk_op(fPush, slot, 0);
           ent = mkE(nops, nops);
           ++nops;
         } else {
@@ -682,8 +694,8 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain,
       const int B = stk[--sp][tid];
       const int A = stk[--sp][tid];
       const int ka = A & 3, kb = B & 3;
-      const int ra = (A >> 2) & 63, sa = (A >> 8) & 63;
-      const int rb = (B >> 2) & 63, sb = (B >> 8) & 63;
+      const int ra = (A >> 2) & 127, sa = (A >> 9) & 127;
+      const int rb = (B >> 2) & 127, sb = (B >> 9) & 127;
       int res = 0, emit = -1, unary = 0;
       bool discard = false;
       if (code == cUnion) {
@@ -709,10 +721,10 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain,
       if (emit >= 0) {
         if (nops < kMaxOps) {
           if (unary) {
-            sop[nops][tid] = (uint16_t)(fCompl | (rb << 3));
+            sop[nops][tid] = (uint16_t)mk_op(fDiff, kOne, rb);
             res = mkE(nops, sb);
           } else {
-            sop[nops][tid] = (uint16_t)(emit | (ra << 3) | (rb << 9));
+            sop[nops][tid] = (uint16_t)mk_op(emit, ra, rb);
             res = mkE(nops, sa);
           }
           ++nops;
@@ -736,6 +748,7 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain,
   }
   for (int q = 0; q < nops; ++q) out->ops[q] = sop[q][tid];
   if (nops > 0 && nslot > kMaxSlots) e |= eSlotOverflow;
+  if (nops > 0 && pool_need(nleaf, kWarps * nslot) + kPoolSpare > kVjpPool) e |= ePoolOverflow;
   if (e) {
     atomicOr(err, e);
     nops = 0;
@@ -759,18 +772,22 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain,
 // are padded to multiples of 128).  Threads walk the tiles y-fastest: tiles
 // that differ only in y usually see the same primitives, so a warp's lanes
 // take the same classification branches.
+constexpr size_t kBinSmem = sizeof(PrimRec) * kPrimSmem + sizeof(uint16_t) * 128 *
+                               (kMaxDepth + kMaxLeaves + kMaxOps) + sizeof(int) * kChainSmem;
+
 __global__ void __launch_bounds__(128) k_bin(const Job* __restrict__ jobs, int njobs,
                                              int* __restrict__ err) {
-  __shared__ uint16_t stk[kMaxDepth][128];
-  __shared__ uint16_t sleaf[kMaxLeaves][128];
-  __shared__ uint16_t sop[kMaxOps][128];
-  __shared__ int schain[kChainSmem];
-  __shared__ __align__(16) PrimRec sprim[kPrimSmem];
+  extern __shared__ __align__(16) unsigned char smem[];
+  PrimRec* sprim = reinterpret_cast<PrimRec*>(smem);
+  auto stk = reinterpret_cast<uint16_t(*)[128]>(sprim + kPrimSmem);
+  auto sleaf = stk + kMaxDepth;
+  auto sop = sleaf + kMaxLeaves;
+  int* schain = reinterpret_cast<int*>(sop + kMaxOps);
   const int tid = threadIdx.x;
   const Job& J = jobs[job_by_tile(jobs, njobs, blockIdx.x * 128)];
   if (!J.do_bin) return;  // uniform over the block
-  const bool smem = J.g.nchain <= kChainSmem && J.g.nprims <= kPrimSmem;
-  if (smem) {
+  const bool staged = J.g.nchain <= kChainSmem && J.g.nprims <= kPrimSmem;
+  if (staged) {
     for (int q = tid; q < J.g.nchain; q += blockDim.x) schain[q] = J.chain[q];
     constexpr int W = sizeof(PrimRec) / 16;
     for (int q = tid; q < J.g.nprims * W; q += blockDim.x)
@@ -782,7 +799,7 @@ __global__ void __launch_bounds__(128) k_bin(const Job* __restrict__ jobs, int n
   const int nty = J.g.nty, ntx = J.g.ntx;
   const int ty = u % nty, tx = (u / nty) % ntx, tz = u / (nty * ntx);
   const int t = (tz * nty + ty) * ntx + tx;
-  if (smem) bin_tile<true>(J, t, schain, sprim, stk, sleaf, sop, err);
+  if (staged) bin_tile<true>(J, t, schain, sprim, stk, sleaf, sop, err);
   else bin_tile<false>(J, t, schain, sprim, stk, sleaf, sop, err);
 }
 
@@ -965,8 +982,8 @@ __device__ __forceinline__ float eval_forward(const uint16_t* sops, int nops, co
                                               const double* auxd) {
   float v = 0.f;
   for (int pos = 0; pos < nops; ++pos) {
-    const int op = sops[pos];
-    const int code = op & 7, a = (op >> 3) & 63, b = (op >> 9) & 63;
+    const FoldOp fo = fold_op(sops[pos]);
+    const int code = fo.code, a = fo.a, b = fo.b;
     if (code == fPush) {
       const int f = lt[a].d.w;
       v = (f & tOK) ? tab_value(lt[a].v, (f & tBOX) != 0, q, tab) : leaf_value(sl[a], cc, auxf, auxd);
@@ -978,18 +995,11 @@ __device__ __forceinline__ float eval_forward(const uint16_t* sops, int nops, co
   return v;
 }
 
-// Per-tile pools (floats): the staged leaves, their table descriptors, the
-// VJP's per-warp accumulators, then the factor tables in what is left.
-constexpr int kBuildPool = 4096;
-constexpr int kVjpPool = 6144;
-static_assert(kMaxLeaves * (int)(sizeof(PrimRec) + sizeof(LeafTab)) / 4 + 192 <= kBuildPool,
-              "build pool holds the staged leaves and some tables");
-static_assert(kMaxLeaves * (int)(sizeof(PrimRec) + sizeof(LeafTab)) / 4 + 2 * kWarps * kMaxSlots +
-                  192 <= kVjpPool,
-              "VJP pool holds the staged leaves, accumulators and some tables");
+static_assert(sizeof(LeafTab) == kLeafTabBytes, "pool accounting");
 // job-prefix entries in shared memory: a class for small tables, one for any
 __host__ __device__ constexpr int spre_len(int njobs) { return njobs < 16 ? 16 : kMaxJobs + 1; }
-constexpr size_t kBuildFixed = (size_t)kMaxOps * kBlock * 4 + (size_t)kBuildPool * 4 + kMaxOps * 2;
+constexpr size_t kBuildFixed = (size_t)kMaxDepth * kBlock * 4 + (size_t)kBuildPool * 4 +
+                               kMaxOps * 16 + kMaxOps * 2 + 16;
 size_t build_smem(int njobs) { return kBuildFixed + (size_t)spre_len(njobs) * 4; }
 
 // Pool carve of one tile: staged leaves, descriptors, then (VJP) accumulators.
@@ -1007,7 +1017,7 @@ __device__ __forceinline__ TilePool carve_pool(float* pool, int size, int nleaf,
   t.lt = reinterpret_cast<LeafTab*>(t.sl + nleaf);
   t.acc = reinterpret_cast<float*>(t.lt + nleaf);
   t.cmp = t.acc + nacc;
-  const int used = ((int)(nleaf * (sizeof(PrimRec) + sizeof(LeafTab)) / 4) + 2 * nacc + 3) & ~3;
+  const int used = pool_need(nleaf, nacc);  // the binner keeps it <= size - kPoolSpare
   t.tab = pool + used;
   t.cap = size - used;
   return t;
@@ -1073,15 +1083,144 @@ __global__ void __launch_bounds__(256) k_fill(const Job* __restrict__ jobs, int 
   }
 }
 
+// ---- forward-only evaluation (build) ----------------------------------------
+// The folded program is postfix: every op takes the top two values of a
+// stack (the complement the top one) and pushes one, so the build, which
+// needs no tape, runs it on a four-deep register stack.  Each op is resolved
+// once per tile into a descriptor: x = kind (0 tabled box, 1 tabled in-plane
+// leaf, 2 direct leaf, 8 + logic code), y/z/w = table offsets or the leaf.
+constexpr int kRegStack = 4;
+constexpr int dBox = 0, dPlane = 1, dDirect = 2, dLogic = 8;
+
+// Thread 0, after tables_plan: descriptors of the tile's ops; returns the
+// largest stack depth the program reaches.
+__device__ __forceinline__ int plan_descs(const uint16_t* sops, int nops, const LeafTab* lt,
+                                          int4* desc) {
+  int depth = 0, maxd = 0;
+  for (int pos = 0; pos < nops; ++pos) {
+    const FoldOp fo = fold_op(sops[pos]);
+    const int code = fo.code;
+    if (code == fPush) {
+      const int a = fo.a;
+      const int f = lt[a].d.w;
+      const int4 v = lt[a].v;
+      if (!(f & tOK)) desc[pos] = make_int4(dDirect, a, 0, 0);
+      else if (f & tBOX) desc[pos] = make_int4(dBox, v.x, v.y, v.z);
+      else desc[pos] = make_int4(dPlane, v.w, 0, v.z);
+      ++depth;
+    } else {
+      desc[pos] = make_int4(dLogic + code, 0, 0, 0);
+      if (code != fCompl) --depth;
+    }
+    maxd = max(maxd, depth);
+  }
+  return maxd;
+}
+
+template <int LOGIC>
+__device__ __forceinline__ float logic_fwd(int code, float a, float b) {
+  if (code == fUnion) return LOGIC == 0 ? (a + b - a * b) : fminf(1.f, a + b);
+  if (code == fInter) return LOGIC == 0 ? a * b : fmaxf(0.f, a + b - 1.f);
+  return LOGIC == 0 ? a * (1.f - b) : fmaxf(0.f, a - b);
+}
+
+// Table offsets of one sample: x, y, z blocks and the in-plane block.
+struct SampleOff {
+  int x, y, z, xy;
+};
+
+// The same program on a stack in shared memory (column of stride kBlock), for
+// programs deeper than the register stack; depth <= kMaxDepth by construction.
+template <int LOGIC>
+__device__ __forceinline__ float eval_stack_smem(const int4* desc, int nops, const float* tab,
+                                                 const PrimRec* sl, const SampleOff& o, int4 p,
+                                                 const GridDev& g, const float* auxf,
+                                                 const double* auxd, float* stk) {
+  int sp = 0;
+  for (int pos = 0; pos < nops; ++pos) {
+    const int4 d = desc[pos];
+    if (d.x < dLogic) {
+      float v;
+      if (d.x == dBox) {
+        v = tab[d.y + o.x] * tab[d.z + o.y] * tab[d.w + o.z];
+      } else if (d.x == dPlane) {
+        v = tab[d.y + o.xy] * tab[d.w + o.z];
+      } else {
+        const Cell c{p.x, p.y, p.z, g.off[p.w][0], g.off[p.w][1], g.off[p.w][2]};
+        v = leaf_value(sl[d.y], c, auxf, auxd);
+      }
+      if (sp < kMaxDepth) stk[(sp++) * kBlock] = v;
+    } else if (sp >= 1) {
+      const int code = d.x - dLogic;
+      float* top = stk + (sp - 1) * kBlock;
+      if (code == fCompl) {
+        *top = 1.f - *top;
+      } else if (sp >= 2) {
+        const float b = *top;
+        --sp;
+        top -= kBlock;
+        *top = logic_fwd<LOGIC>(code, *top, b);
+      }
+    }
+  }
+  return sp >= 1 ? stk[0] : 0.f;
+}
+
+template <int LOGIC>
+__device__ __forceinline__ void eval_stack2(const int4* desc, int nops, const float* tab,
+                                            const PrimRec* sl, const SampleOff& o0,
+                                            const SampleOff& o1, int4 p0, int4 p1,
+                                            const GridDev& g, const float* auxf,
+                                            const double* auxd, float& r0, float& r1) {
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;  // stack of sample 0, a0 on top
+  float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;  // stack of sample 1
+  for (int pos = 0; pos < nops; ++pos) {
+    const int4 d = desc[pos];
+    if (d.x < dLogic) {
+      float v0, v1;
+      if (d.x == dBox) {
+        v0 = tab[d.y + o0.x] * tab[d.z + o0.y] * tab[d.w + o0.z];
+        v1 = tab[d.y + o1.x] * tab[d.z + o1.y] * tab[d.w + o1.z];
+      } else if (d.x == dPlane) {
+        v0 = tab[d.y + o0.xy] * tab[d.w + o0.z];
+        v1 = tab[d.y + o1.xy] * tab[d.w + o1.z];
+      } else {  // cells built here only: the direct path takes them by reference
+        const Cell c0{p0.x, p0.y, p0.z, g.off[p0.w][0], g.off[p0.w][1], g.off[p0.w][2]};
+        const Cell c1{p1.x, p1.y, p1.z, g.off[p1.w][0], g.off[p1.w][1], g.off[p1.w][2]};
+        v0 = leaf_value(sl[d.y], c0, auxf, auxd);
+        v1 = leaf_value(sl[d.y], c1, auxf, auxd);
+      }
+      a3 = a2; a2 = a1; a1 = a0; a0 = v0;
+      b3 = b2; b2 = b1; b1 = b0; b0 = v1;
+    } else {
+      const int code = d.x - dLogic;
+      if (code == fCompl) {
+        a0 = 1.f - a0;
+        b0 = 1.f - b0;
+      } else {
+        a0 = logic_fwd<LOGIC>(code, a1, a0);
+        b0 = logic_fwd<LOGIC>(code, b1, b0);
+        a1 = a2; a2 = a3;
+        b1 = b2; b2 = b3;
+      }
+    }
+  }
+  r0 = a0;
+  r1 = b0;
+}
+
 // Band tiles of the build: persistent over the binner's compacted list, the
 // tile's primitives staged with their factor tables, the folded program run
-// at every sample of the tile.
+// at every sample of the tile (two samples per thread, register stack; the
+// tape evaluator for programs deeper than the register stack).
 __global__ void __launch_bounds__(kBlock) k_build(const Job* __restrict__ jobs, int njobs) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float* tape = reinterpret_cast<float*>(smem);
-  float* pool = tape + kMaxOps * kBlock;
-  uint16_t* sops = reinterpret_cast<uint16_t*>(pool + kBuildPool);
-  int* spre = reinterpret_cast<int*>(sops + kMaxOps);  // prefix of band-tile counts
+  float* stk = reinterpret_cast<float*>(smem);  // stack of the deep-program fallback
+  float* pool = stk + kMaxDepth * kBlock;
+  int4* desc = reinterpret_cast<int4*>(pool + kBuildPool);
+  uint16_t* sops = reinterpret_cast<uint16_t*>(desc + kMaxOps);
+  int* sdepth = reinterpret_cast<int*>(sops + kMaxOps);
+  int* spre = sdepth + 4;  // prefix of band-tile counts
   const int tid = threadIdx.x;
   if (tid == 0) job_prefix(jobs, njobs, false, spre);
   __syncthreads();
@@ -1098,25 +1237,64 @@ __global__ void __launch_bounds__(kBlock) k_build(const Job* __restrict__ jobs, 
     __syncthreads();  // the previous tile is done with the staged program
     stage_tile(P, J.prims, nops, nleaf, sops, tp.sl, tid);
     __syncthreads();
-    if (tid == 0) tables_plan(tp.sl, nleaf, g, false, tp.cap, tp.lt);
+    if (tid == 0) {
+      tables_plan(tp.sl, nleaf, g, false, tp.cap, tp.lt);
+      sdepth[0] = plan_descs(sops, nops, tp.lt, desc);
+    }
     __syncthreads();
     tables_fill(tp.sl, nleaf, g, tp.lt, false, tx << g.lx, ty << g.ly, tz << g.lz, tp.tab, tid,
                 J.auxf, J.auxd);
     __syncthreads();
     const int lxy = g.lx + g.ly, lxyz = lxy + g.lz;
     const int ncc = g.C << lxyz;
+    const int TXm = (1 << g.lx) - 1, TYm = (1 << g.ly) - 1, TZm = (1 << g.lz) - 1;
     const size_t plane = (size_t)g.nx * g.ny * g.nz;
     float* __restrict__ fill = J.fill;
     float* __restrict__ eps = J.eps;
+    if (sdepth[0] <= kRegStack) {
+      const int half = ncc >> 1;  // a multiple of 64
+      for (int l = tid; l < half; l += kBlock) {
+        SampleOff o[2];
+        int4 pc[2];
+        size_t off[2];
+        bool in[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int m = l + h * half;
+          const int x = m & TXm, y = (m >> g.lx) & TYm, z = (m >> lxy) & TZm, c = m >> lxyz;
+          const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
+          in[h] = gi < g.nx && gj < g.ny && gk < g.nz;
+          o[h] = SampleOff{(c << g.lx) + x, (c << g.ly) + y, (c << g.lz) + z,
+                           (((c << g.ly) + y) << g.lx) + x};
+          pc[h] = make_int4(gi, gj, gk, c);
+          off[h] = (size_t)c * plane + ((size_t)gk * g.ny + gj) * g.nx + gi;
+        }
+        float v0, v1;
+        if (g.logic == 0)
+          eval_stack2<0>(desc, nops, tp.tab, tp.sl, o[0], o[1], pc[0], pc[1], g, J.auxf, J.auxd, v0, v1);
+        else
+          eval_stack2<1>(desc, nops, tp.tab, tp.sl, o[0], o[1], pc[0], pc[1], g, J.auxf, J.auxd, v0, v1);
+        if (in[0]) {
+          if (fill) fill[off[0]] = v0;
+          eps[off[0]] = g.eps_bg + g.deps * v0;
+        }
+        if (in[1]) {
+          if (fill) fill[off[1]] = v1;
+          eps[off[1]] = g.eps_bg + g.deps * v1;
+        }
+      }
+      continue;
+    }
     for (int l = tid; l < ncc; l += kBlock) {
-      const int x = l & ((1 << g.lx) - 1), y = (l >> g.lx) & ((1 << g.ly) - 1),
-                z = (l >> lxy) & ((1 << g.lz) - 1), c = l >> lxyz;
+      const int x = l & TXm, y = (l >> g.lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
       const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
       if (gi >= g.nx || gj >= g.ny || gk >= g.nz) continue;
-      const Cell cc{gi, gj, gk, g.off[c][0], g.off[c][1], g.off[c][2]};
-      const TileLoc q{x, y, z, c, 1 << g.lx, 1 << g.ly, 1 << g.lz};
-      const float v = eval_forward(sops, nops, tp.sl, tp.lt, tp.tab, q, cc, g.logic, tape, tid,
-                                   J.auxf, J.auxd);
+      const SampleOff so{(c << g.lx) + x, (c << g.ly) + y, (c << g.lz) + z,
+                         (((c << g.ly) + y) << g.lx) + x};
+      const int4 pc = make_int4(gi, gj, gk, c);
+      const float v = g.logic == 0
+          ? eval_stack_smem<0>(desc, nops, tp.tab, tp.sl, so, pc, g, J.auxf, J.auxd, stk + tid)
+          : eval_stack_smem<1>(desc, nops, tp.tab, tp.sl, so, pc, g, J.auxf, J.auxd, stk + tid);
       const size_t o = (size_t)c * plane + ((size_t)gk * g.ny + gj) * g.nx + gi;
       if (fill) fill[o] = v;
       eps[o] = g.eps_bg + g.deps * v;
@@ -1222,17 +1400,18 @@ __device__ __forceinline__ void activity_axes(const LeafTab* lt, int nleaf, cons
 }
 
 constexpr int kSeedChunk = 512;  // active samples whose seeds are staged at once
-constexpr size_t kVjpFixed = (size_t)kMaxOps * kBlock * 4 + (size_t)kVjpPool * 4 +
+constexpr size_t kVjpFixed = (size_t)kSmemOps * kBlock * 4 + (size_t)kVjpPool * 4 +
                              2 * (size_t)kMaxPairs * kBlock * 4 + (size_t)kSeedChunk * 4 +
                              (size_t)kMaxTileCells * 3 * 2 + kMaxOps * 2 + (kMaxLeaves + 1) * 4 +
                              kAct1 + kWarps * 4 + 4;
 size_t vjp_smem(int njobs) { return ((kVjpFixed + 15) & ~(size_t)15) + (size_t)spre_len(njobs) * 4; }
 
 __global__ void __launch_bounds__(kBlock, 4) k_vjp(const Job* __restrict__ jobs, int njobs,
-                                                   int* __restrict__ err) {
+                                                   int* __restrict__ err,
+                                                   float* __restrict__ gtape) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* tape = reinterpret_cast<float*>(smem);
-  float* pool = tape + kMaxOps * kBlock;
+  float* pool = tape + kSmemOps * kBlock;
   float* pv = pool + kVjpPool;
   int* pk = reinterpret_cast<int*>(pv + kMaxPairs * kBlock);
   float* zsb = reinterpret_cast<float*>(pk + kMaxPairs * kBlock);  // seeds of a chunk
@@ -1348,54 +1527,63 @@ __global__ void __launch_bounds__(kBlock, 4) k_vjp(const Job* __restrict__ jobs,
           zsb[i - c0] = zs * g.deps;  // eps = eps_bg + deps fill
         }
       }
-      for (int i0 = c0; i0 < c1; i0 += kBlock) {
-        if (i0 + warp * 32 >= c1) continue;  // no live lane in this warp (warp-uniform)
-        const int i = i0 + tid;
-        const bool live = i < c1;
-        const int l = live ? slist[apos(i)] : 0;
-        const int x = l & TXm, y = (l >> g.lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
-        const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
-        const float zs = live ? zsb[i - c0] : 0.f;
-        const Cell cc{gi, gj, gk, g.off[c][0], g.off[c][1], g.off[c][2]};
-        const TileLoc q{x, y, z, c, 1 << g.lx, 1 << g.ly, 1 << g.lz};
-        eval_forward(sops, nops, sl, lt, tab, q, cc, g.logic, tape, tid, J.auxf, J.auxd);
-        // reverse sweep through the logic: tape slots become adjoints d fill / d node
-        tape[(nops - 1) * kBlock + tid] = 1.f;
-        for (int pos = nops - 1; pos >= 0; --pos) {
-          const int op = sops[pos];
-          const int code = op & 7;
-          if (code == fPush) continue;
-          const int a = (op >> 3) & 63, b = (op >> 9) & 63;
-          const float adj = tape[pos * kBlock + tid];
-          const float vb = code == fCompl ? 0.f : tape[b * kBlock + tid];
-          float da, db;
-          op_bwd(code, g.logic, tape[a * kBlock + tid], vb, da, db);
-          tape[a * kBlock + tid] = adj * da;
-          if (code != fCompl) tape[b * kBlock + tid] = adj * db;
-        }
-        // primitives: d s / d q times the seed, reduced per slot over the warp
-        for (int pos = 0; pos < nops; ++pos) {
-          const int op = sops[pos];
-          if ((op & 7) != fPush) continue;
-          const int lf = (op >> 3) & 63;
-          const int fl = lt[lf].d.w;
-          if (!(fl & tACT)) continue;
-          const float a = zs * tape[pos * kBlock + tid];
-          if (__ballot_sync(0xffffffffu, a != 0.f) == 0u) continue;
-          float* la = wacc + sbase[lf];
-          float* lc = wcmp + sbase[lf];
-          if ((fl & (tOK | tBOX)) == (tOK | tBOX)) {
-            box_tab_reduce(lt[lf], q, tab, a, g, la, lc, lane);
-            continue;
+      // The tape: shared memory for short programs, else this block's slice of
+      // the global tape (the two variants are separate instantiations, so the
+      // shared one keeps shared-memory addressing).
+      auto samples = [&](auto big) {
+        constexpr bool kBig = decltype(big)::value;
+        float* tap = kBig ? gtape + (size_t)blockIdx.x * kTapeBlockFloats : tape;
+        for (int i0 = c0; i0 < c1; i0 += kBlock) {
+          if (i0 + warp * 32 >= c1) continue;  // no live lane in this warp (warp-uniform)
+          const int i = i0 + tid;
+          const bool live = i < c1;
+          const int l = live ? slist[apos(i)] : 0;
+          const int x = l & TXm, y = (l >> g.lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
+          const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
+          const float zs = live ? zsb[i - c0] : 0.f;
+          const Cell cc{gi, gj, gk, g.off[c][0], g.off[c][1], g.off[c][2]};
+          const TileLoc q{x, y, z, c, 1 << g.lx, 1 << g.ly, 1 << g.lz};
+          eval_forward(sops, nops, sl, lt, tab, q, cc, g.logic, tap, tid, J.auxf, J.auxd);
+          // reverse sweep through the logic: tape slots become adjoints d fill / d node
+          tap[(nops - 1) * kBlock + tid] = 1.f;
+          for (int pos = nops - 1; pos >= 0; --pos) {
+            const FoldOp fo = fold_op(sops[pos]);
+            const int code = fo.code;
+            if (code == fPush) continue;
+            const int a = fo.a, b = fo.b;
+            const float adj = tap[pos * kBlock + tid];
+            const float vb = code == fCompl ? 0.f : tap[b * kBlock + tid];
+            float da, db;
+            op_bwd(code, g.logic, tap[a * kBlock + tid], vb, da, db);
+            tap[a * kBlock + tid] = adj * da;
+            if (code != fCompl) tap[b * kBlock + tid] = adj * db;
           }
-          int n = 0;
-          if (a != 0.f)
-            n = leaf_pairs(sl[lf], cc, a, g, J.act, J.actc, J.auxf, J.auxd, pk + tid, pv + tid);
-          warp_accumulate(n, 0, pk + tid, pv + tid, la, lc, lane);
-          if (sl[lf].kind == kPolygon)
-            poly_accumulate(sl[lf], cc, a, g, J.act, J.actc, J.auxd, la, lc, lane);
+          // primitives: d s / d q times the seed, reduced per slot over the warp
+          for (int pos = 0; pos < nops; ++pos) {
+            const FoldOp fo = fold_op(sops[pos]);
+            if (fo.code != fPush) continue;
+            const int lf = fo.a;
+            const int fl = lt[lf].d.w;
+            if (!(fl & tACT)) continue;
+            const float a = zs * tap[pos * kBlock + tid];
+            if (__ballot_sync(0xffffffffu, a != 0.f) == 0u) continue;
+            float* la = wacc + sbase[lf];
+            float* lc = wcmp + sbase[lf];
+            if ((fl & (tOK | tBOX)) == (tOK | tBOX)) {
+              box_tab_reduce(lt[lf], q, tab, a, g, la, lc, lane);
+              continue;
+            }
+            int n = 0;
+            if (a != 0.f)
+              n = leaf_pairs(sl[lf], cc, a, g, J.act, J.actc, J.auxf, J.auxd, pk + tid, pv + tid);
+            warp_accumulate(n, 0, pk + tid, pv + tid, la, lc, lane);
+            if (sl[lf].kind == kPolygon)
+              poly_accumulate(sl[lf], cc, a, g, J.act, J.actc, J.auxd, la, lc, lane);
+          }
         }
-      }
+      };
+      if (nops > kSmemOps) samples(std::true_type{});
+      else samples(std::false_type{});
     }  // chunks of active samples
     __syncthreads();
     for (int s2 = tid; s2 < nslot; s2 += kBlock) {
@@ -1445,6 +1633,18 @@ __global__ void k_finalize(const Job* __restrict__ jobs, int njobs, int nparams)
 
 }  // namespace
 
+cudaError_t init_kernel_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_bin, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kBinSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)build_smem(kMaxJobs));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)vjp_smem(kMaxJobs));
+  return e;
+}
+
 // Resident blocks per SM for the two shared-memory classes of the job prefix.
 int build_blocks_per_sm(int njobs) {
   static int v[2] = {0, 0};
@@ -1480,7 +1680,7 @@ cudaError_t launch_prepare(const Job* jobs, const JobTotals& t, cudaStream_t s) 
 
 cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s) {
   if (t.tiles_padded <= 0) return cudaSuccess;
-  k_bin<<<t.tiles_padded / 128, 128, 0, s>>>(jobs, t.njobs, err);
+  k_bin<<<t.tiles_padded / 128, 128, kBinSmem, s>>>(jobs, t.njobs, err);
   return cudaGetLastError();
 }
 
@@ -1496,9 +1696,11 @@ cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, cudaStream_t s) {
-  const int grid = sms * vjp_blocks_per_sm(t.njobs);
-  k_vjp<<<grid, kBlock, vjp_smem(t.njobs), s>>>(jobs, t.njobs, err);
+cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, float* gtape,
+                       int gtape_blocks, cudaStream_t s) {
+  const int grid = std::min(sms * vjp_blocks_per_sm(t.njobs), gtape_blocks);
+  if (grid < 1 || !gtape) return cudaErrorInvalidValue;
+  k_vjp<<<grid, kBlock, vjp_smem(t.njobs), s>>>(jobs, t.njobs, err, gtape);
   return cudaGetLastError();
 }
 

@@ -166,6 +166,11 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   const size_t o_list = take(sizeof(int) * (size_t)g.T);
   const size_t o_tcls = take((size_t)g.T);
   const size_t o_part = take(sizeof(float) * std::max<size_t>(part, 1));
+  // the VJP's long-program tape: one slice per block, one block per SM
+  int dev = 0, sms = 1;
+  NACU(cudaGetDevice(&dev));
+  NACU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t o_gtape = take(sizeof(float) * kTapeBlockFloats * (size_t)sms);
   if (off > kNoAllocScratchBytes)
     return na_fail(ADG_EINVAL,
                    "adg_grad_noalloc: this design needs %zu bytes of scratch (%d tiles, %zu "
@@ -173,10 +178,9 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
                    "adg_grad",
                    off, g.T, part, kNoAllocScratchBytes);
   // ---- set-up once per device: the array's device address ----
-  int dev = 0;
-  NACU(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNAMaxDevices) return na_fail(ADG_EINVAL, "device %d out of range", dev);
   if (!g_sym_ok[dev]) {
+    NACU(init_kernel_attributes());
     void* ptr = nullptr;
     NACU(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
     g_sym[dev] = ptr;
@@ -201,6 +205,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   int* d_list = reinterpret_cast<int*>(base + o_list);
   unsigned char* d_tcls = base + o_tcls;
   float* d_part = reinterpret_cast<float*>(base + o_part);
+  float* d_gtape = reinterpret_cast<float*>(base + o_gtape);
   // ---- upload, clear, launch (prepare -> binner -> VJP -> finalize) ----
   NACU(cudaMemsetAsync(d_err, 0, sizeof(int), s));
   NACU(cudaMemcpyAsync(d_chain, H.chain, sizeof(int) * nchain, cudaMemcpyHostToDevice, s));
@@ -254,11 +259,9 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   t.bin_blocks = t.tiles_padded / 128;
   t.params = D->n_params;
   t.partials = (long long)part;
-  int sms = 1;
-  NACU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   NACU(launch_prepare(d_job, t, s));
   NACU(launch_bin(d_job, t, d_err, s));
-  NACU(launch_vjp(d_job, t, d_err, sms, s));
+  NACU(launch_vjp(d_job, t, d_err, sms, d_gtape, sms, s));
   NACU(launch_finalize(d_job, t, s));
   // ---- wait and report device-side checks ----
   int herr = 0;

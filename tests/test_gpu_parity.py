@@ -108,6 +108,50 @@ def test_tile_shapes_agree(ctx, oracle_mod, tile):
     _check_grad(ctx, desc, oracle_mod, d=d)
 
 
+def _crowded_design(nbox: int, nested: bool, logic: str = "product"):
+    """`nbox` parameterised boxes whose x and z edges all fall in the first
+    tile column: a band tile there folds to 2 nbox - 1 ops.  nested: the
+    program's stack is nbox deep (right-nested unions around one difference);
+    else one n-ary union."""
+    D = I.Design((64, 12, 6), (20.0, 20.0, 20.0), ncomp=3, eps_bg=1.5, eps_fg=4.0)
+    rng = np.random.default_rng(23 + nbox)
+    kids = []
+    for _ in range(nbox):
+        x0 = rng.uniform(10.0, 500.0)
+        pa = D.param(x0)
+        kids.append(D.box(x=(I.P(pa), x0 + rng.uniform(30.0, 120.0)),
+                          z=(rng.uniform(3.0, 40.0), rng.uniform(70.0, 110.0))))
+    if nested:
+        prog = ("diff", kids[-1], kids[-2])
+        for b in reversed(kids[:-2]):
+            prog = ("union", b, prog)
+    else:
+        prog = ("union",) + tuple(kids)
+    D.set_program(prog)
+    desc = D.to_desc()
+    desc["logic"] = logic
+    return desc
+
+
+@pytest.mark.parametrize("logic", ["product", "clamp"])
+@pytest.mark.parametrize("nbox", [24, 40])
+def test_long_programs_use_the_global_tape(ctx, oracle_mod, logic, nbox):
+    from paper_2311_05646_gb300 import adg
+    desc = _crowded_design(nbox, nested=False, logic=logic)
+    d = _check_build(ctx, desc, oracle_mod)
+    _check_grad(ctx, desc, oracle_mod, d=d)
+    st = adg.adg_design_stats(d)
+    # beyond the shared-memory tape (32 ops); 79 ops need 7-bit operand fields
+    assert st["max_ops"] == 2 * nbox - 1, st
+
+
+@pytest.mark.parametrize("logic", ["product", "clamp"])
+def test_deep_programs_use_the_stack_fallback(ctx, oracle_mod, logic):
+    desc = _crowded_design(20, nested=True, logic=logic)
+    d = _check_build(ctx, desc, oracle_mod)
+    _check_grad(ctx, desc, oracle_mod, d=d)
+
+
 def test_clamp_logic_family(ctx, oracle_mod):
     desc = I.grating_3d(n=(150, 36, 60), teeth=8, pitch=600.0)
     desc["logic"] = "clamp"
