@@ -295,6 +295,48 @@ def run_adg(args):
         kernels[k]["frac_of_measured_hbm"] = a / peak
     launches = sum(v[0] for v in prof.values())
 
+    # the dense form of the gradient (every cell's fields streamed for the
+    # material-level derivatives) against the plain one, each call timed alone
+    dense = None
+    if not args.no_dense:
+        gm = torch.zeros(2, dtype=torch.float64, device="cuda")
+        p = params[0]
+        adg.adg_build_eps(design, p, eps, fill=fill, stream=stream)
+        nd = max(20, min(args.steps, 200))
+
+        def t_calls(fn):
+            for _ in range(5):
+                fn()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(nd):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / nd
+
+        ms_plain = t_calls(lambda: adg.adg_grad(design, p, efd, ead, w, g, stream=stream))
+        adg.adg_profile_read(ctx, reset=True)
+        adg.adg_profile_enable(ctx, True)
+        ms_dense = t_calls(lambda: adg.adg_grad_dense(design, p, efd, ead, w, fill, g, gm,
+                                                      stream=stream))
+        adg.adg_profile_enable(ctx, False)
+        dprof = adg.adg_profile_read(ctx, reset=True)
+        adg.adg_sync(ctx, stream)
+        stream_bytes = cells * C * (8 + 8 + 4)  # E_fwd, E_adj complex64 + fill fp32
+        n_l, tot = dprof["dense"]
+        us_k = 1e3 * tot / max(n_l, 1)
+        dense = {"grad_ms": ms_dense, "plain_grad_ms": ms_plain,
+                 "cells_per_s": world * cells / (ms_dense * 1e-3),
+                 "outputs": "g (band VJP) + dL/d eps_bg, dL/d eps_fg (every cell)",
+                 "stream_kernel": "k_dense (+ fixed-order sum)",
+                 "stream_bytes_per_launch": stream_bytes, "stream_us_per_launch": us_k,
+                 "stream_GBps": stream_bytes / (us_k * 1e-6) / 1e9,
+                 "stream_frac_of_measured_hbm": stream_bytes / (us_k * 1e-6) / 1e9 / peak,
+                 "call_GBps": (stream_bytes + kern["vjp"]) / (ms_dense * 1e-3) / 1e9,
+                 "call_frac_of_measured_hbm": (stream_bytes + kern["vjp"]) / (ms_dense * 1e-3) / 1e9 / peak,
+                 "vjp_us_per_launch": 1e3 * dprof["vjp"][1] / max(dprof["vjp"][0], 1)}
+
     # end to end through the public API: host (pinned) fields in, eps + g out
     e2e = None
     if not args.no_e2e:
@@ -351,7 +393,7 @@ def run_adg(args):
                        "vjp_active_samples": stats["active_samples"],
                        "l2": "inputs larger than L2 (fields 691 MB + outputs 346 MB per step)"},
             "roofline": roof, "kernels": kernels, "gpu_launches": launches,
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks.summary(),
+            "cpu_baseline": cpu, "e2e": e2e, "dense_vjp": dense, "clocks": clocks.summary(),
         }
         print(json.dumps(line))
     if dist is not None:
@@ -540,6 +582,7 @@ def main():
     ap.add_argument("--tile", default="")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--workload", default="grating3d", choices=["grating3d", "batch", "serve"])
     ap.add_argument("--designs", type=int, default=256)
     ap.add_argument("--tune", action="store_true")

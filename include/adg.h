@@ -186,6 +186,23 @@ adg_status adg_grad(adg_ctx *ctx, adg_design *design, const double *h_params,
 adg_status adg_grad_real(adg_ctx *ctx, adg_design *design, const double *h_params,
                          const float *d_G, float *d_grad, void *stream);
 
+/* The dense form of step 5: the same g as adg_grad (bit for bit), plus the
+ * derivatives of the same L with respect to the two material levels of
+ * eps = eps_bg + (eps_fg - eps_bg) * fill (Sec. 5.1):
+ *   d_gmat[0] = dL/d eps_bg = sum_c sum_cells Re(w_c E_adj,c E_fwd,c) (1 - fill_c)
+ *   d_gmat[1] = dL/d eps_fg = sum_c sum_cells Re(w_c E_adj,c E_fwd,c) fill_c
+ * These depend on every cell, so every cell's fields are streamed (no band
+ * culling of the field reads); g still comes from the band tiles, the only
+ * place where d eps / d p can be nonzero.  d_fill: the design's fill at the
+ * same h_params (as written by adg_build_eps), device fp32
+ * [ncomp][nz][ny][nx].  d_gmat: 2 device doubles, overwritten.  The field
+ * stream follows the band kernels on `stream`; its sums are formed in a
+ * fixed order (reproducible bit for bit).  Asynchronous on `stream`. */
+adg_status adg_grad_dense(adg_ctx *ctx, adg_design *design, const double *h_params,
+                          const float *const d_efwd[3], const float *const d_eadj[3],
+                          const float *w, const float *d_fill, float *d_grad, double *d_gmat,
+                          void *stream);
+
 /* ---- batched work ---------------------------------------------------------
  * Many (design, operation) items run as ONE job table: five launches (zero,
  * bin, build, VJP, finalize) whatever the number of designs, their grid sizes
@@ -233,7 +250,8 @@ adg_status adg_design_stats(adg_ctx *ctx, adg_design *design, void *stream, adg_
  * (index ADG_K_*), the launch count and the summed device time; `reset`
  * clears the accumulators. */
 enum { ADG_K_BIN = 0, ADG_K_BUILD = 1, ADG_K_VJP = 2, ADG_K_FINALIZE = 3, ADG_K_PREPARE = 4,
-       ADG_K_FILL = 5, ADG_K_COUNT = 8 };
+       ADG_K_FILL = 5, ADG_K_DENSE = 6 /* field stream + its fixed-order sum */,
+       ADG_K_COUNT = 8 };
 typedef struct {
   int64_t launches[ADG_K_COUNT];
   double ms[ADG_K_COUNT];

@@ -86,6 +86,8 @@ def _load():
             lib.od_grad_real.argtypes = [P, P, P, P, P]
             lib.od_loss.restype = ctypes.c_double
             lib.od_loss.argtypes = [P, P, P, P, P]
+            lib.od_grad_material.restype = ctypes.c_int
+            lib.od_grad_material.argtypes = [P, P, P, P, P, P]
             lib.od_grad_fd.restype = ctypes.c_int
             lib.od_grad_fd.argtypes = [P, P, P, P, P, ctypes.c_double, P]
             lib.od_num_threads.restype = ctypes.c_int
@@ -283,6 +285,19 @@ def loss(desc: dict, efwd, eadj, w, params=None) -> float:
     ef = _field(efwd, m.shape)
     ea = _field(eadj, m.shape)
     return float(_load().od_loss(m.ref, _ptr(p), _ptr(ef), _ptr(ea), _ptr(_w(desc, w))))
+
+
+def grad_material(desc: dict, efwd, eadj, w, params=None) -> np.ndarray:
+    """[dL/d eps_bg, dL/d eps_fg] of L = Re sum w E_adj E_fwd eps (Sec. 5.1)."""
+    m = _Marshalled(desc)
+    p = _params(desc, params)
+    ef = _field(efwd, m.shape)
+    ea = _field(eadj, m.shape)
+    out = np.zeros(2)
+    rc = _load().od_grad_material(m.ref, _ptr(p), _ptr(ef), _ptr(ea), _ptr(_w(desc, w)), _ptr(out))
+    if rc:
+        raise ValueError("od_grad_material failed (%d)" % rc)
+    return out
 
 
 def grad_fd(desc: dict, efwd, eadj, w, h: float, params=None) -> np.ndarray:

@@ -54,7 +54,7 @@ class adg_tile_opts(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
-K_NAMES = {0: "bin", 1: "build", 2: "vjp", 3: "finalize", 4: "prepare", 5: "fill"}
+K_NAMES = {0: "bin", 1: "build", 2: "vjp", 3: "finalize", 4: "prepare", 5: "fill", 6: "dense"}
 
 
 class adg_profile_data(ctypes.Structure):
@@ -87,6 +87,7 @@ def lib():
                 "adg_build_eps": [P, P, P, P, P, P],
                 "adg_grad": [P, P, P, P, P, P, P, P],
                 "adg_grad_real": [P, P, P, P, P, P],
+                "adg_grad_dense": [P, P, P, P, P, P, P, P, P, P],
                 "adg_sync": [P, P],
                 "adg_design_stats": [P, P, P, ctypes.POINTER(adg_stats)],
                 "adg_profile_enable": [P, I32],
@@ -221,6 +222,8 @@ def _check_cell_tensor(design, t, name, dtype):
     if t.dtype != dtype or tuple(t.shape) != design.shape:
         raise ValueError("%s must be %s of shape %s, got %s %s" % (name, dtype, design.shape,
                                                                     t.dtype, tuple(t.shape)))
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA tensor" % name)
     del torch
 
 
@@ -236,10 +239,8 @@ def adg_build_eps(design: Design, params, eps, fill=None, stream=None):
                                _stream_ptr(stream)))
 
 
-def adg_grad(design: Design, params, efwd, eadj, w, grad, stream=None):
-    """grad <- Re sum w_c E_adj,c E_fwd,c d eps_c / d p (Eq. 1, eps term)."""
+def _grad_args(design: Design, efwd, eadj, w, grad):
     import torch
-    p = _params(design, params)
     _check_cell_tensor(design, efwd, "efwd", torch.complex64)
     _check_cell_tensor(design, eadj, "eadj", torch.complex64)
     if grad.dtype != torch.float32 or grad.numel() != design.n_params or not grad.is_cuda:
@@ -253,9 +254,31 @@ def adg_grad(design: Design, params, efwd, eadj, w, grad, stream=None):
     ww = np.zeros(6, dtype=np.float32)
     ww[0:2 * C:2] = wc.real[:C]
     ww[1:2 * C:2] = wc.imag[:C]
+    return ef, ea, ww
+
+
+def adg_grad(design: Design, params, efwd, eadj, w, grad, stream=None):
+    """grad <- Re sum w_c E_adj,c E_fwd,c d eps_c / d p (Eq. 1, eps term)."""
+    p = _params(design, params)
+    ef, ea, ww = _grad_args(design, efwd, eadj, w, grad)
     _check(lib().adg_grad(design.ctx.handle, design.handle, p.ctypes.data_as(ctypes.c_void_p),
                           ef, ea, ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad),
                           _stream_ptr(stream)))
+
+
+def adg_grad_dense(design: Design, params, efwd, eadj, w, fill, grad, gmat, stream=None):
+    """The dense form: grad as adg_grad, and gmat (2 float64 on the device)
+    <- [dL/d eps_bg, dL/d eps_fg]; every cell's fields and `fill` (the fill at
+    the same params) are streamed."""
+    import torch
+    p = _params(design, params)
+    ef, ea, ww = _grad_args(design, efwd, eadj, w, grad)
+    _check_cell_tensor(design, fill, "fill", torch.float32)
+    if gmat.dtype != torch.float64 or gmat.numel() != 2 or not gmat.is_cuda or not gmat.is_contiguous():
+        raise ValueError("gmat must be a contiguous float64 CUDA tensor of 2 entries")
+    _check(lib().adg_grad_dense(design.ctx.handle, design.handle, p.ctypes.data_as(ctypes.c_void_p),
+                                ef, ea, ww.ctypes.data_as(ctypes.c_void_p), _dptr(fill),
+                                _dptr(grad), _dptr(gmat), _stream_ptr(stream)))
 
 
 def adg_grad_real(design: Design, params, G, grad, stream=None):

@@ -156,6 +156,9 @@ struct adg_design {
   size_t partial_cap = 0;
   Job* d_job = nullptr;  // the one-job table of single-design calls
   Job job{};
+  // dense field stream (adg_grad_dense): per-chunk partials and work counter
+  double2* d_dense_part = nullptr;
+  int* d_dense_ctr = nullptr;
   // per-call host staging
   std::vector<PrimRec> h_prims;
   std::vector<double> h_auxd, q;
@@ -232,6 +235,8 @@ void free_design(adg_design* d) {
   cudaFree(d->d_counters);
   cudaFree(d->d_partial);
   cudaFree(d->d_job);
+  cudaFree(d->d_dense_part);
+  cudaFree(d->d_dense_ctr);
   delete d;
 }
 
@@ -518,6 +523,45 @@ extern "C" adg_status adg_grad_real(adg_ctx* ctx, adg_design* d, const double* h
   va.G = d_G;
   CU(cudaSetDevice(ctx->device));
   return run_single(ctx, d, h_params, nullptr, nullptr, &va, d_grad, (cudaStream_t)stream);
+}
+
+extern "C" adg_status adg_grad_dense(adg_ctx* ctx, adg_design* d, const double* h_params,
+                                     const float* const d_efwd[3], const float* const d_eadj[3],
+                                     const float* w, const float* d_fill, float* d_grad,
+                                     double* d_gmat, void* stream) {
+  if (!ctx || !d || !d_efwd || !d_eadj || !w || !d_fill || !d_gmat || (!d_grad && d->n_params > 0))
+    return fail(ADG_EINVAL, "adg_grad_dense: NULL argument");
+  VjpArgs va{};
+  DenseArgs da{};
+  const GridDev& g = d->g;
+  for (int c = 0; c < g.C; ++c) {
+    if (!d_efwd[c] || !d_eadj[c])
+      return fail(ADG_EINVAL, "adg_grad_dense: field of component %d is NULL", c);
+    va.ef[c] = da.ef[c] = reinterpret_cast<const float2*>(d_efwd[c]);
+    va.ea[c] = da.ea[c] = reinterpret_cast<const float2*>(d_eadj[c]);
+    va.w[c] = da.w[c] = make_float2(w[2 * c], w[2 * c + 1]);
+  }
+  va.G = nullptr;
+  da.fill = d_fill;
+  da.plane = (long long)g.nx * g.ny * g.nz;
+  da.C = g.C;
+  da.chunks_per_c = (int)((da.plane + kDenseChunk - 1) / kDenseChunk);
+  da.gmat = d_gmat;
+  CU(cudaSetDevice(ctx->device));
+  if (!d->d_dense_part) {
+    CU(cudaMalloc((void**)&d->d_dense_part, sizeof(double2) * (size_t)da.C * da.chunks_per_c));
+    CU(cudaMalloc((void**)&d->d_dense_ctr, sizeof(int)));
+  }
+  da.part = d->d_dense_part;
+  da.ctr = d->d_dense_ctr;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the band gradient, then the field stream at full occupancy: run side by
+  // side on one SM the two slow each other (shared-memory and load pipes)
+  const adg_status st = run_single(ctx, d, h_params, nullptr, nullptr, &va, d_grad, s);
+  if (st != ADG_OK) return st;
+  ProfScope ps(ctx, ADG_K_DENSE, s);
+  CU(launch_dense(da, ctx->sms, s));
+  return ADG_OK;
 }
 
 // ------------------------------------------------------------------ batches -

@@ -104,6 +104,24 @@ struct VjpArgs {
   const float* G;  // real-seed mode when non-null
 };
 
+// The dense field stream of adg_grad_dense: every sample's
+// z = Re(w E_adj E_fwd) and z * fill, summed per chunk of kDenseChunk
+// samples (chunks handed out by an atomic counter, partials stored by chunk
+// index, summed in index order by one block).
+constexpr int kDenseChunk = 8192;
+struct DenseArgs {
+  const float2* ef[3];
+  const float2* ea[3];
+  float2 w[3];
+  const float* fill;  // [C][plane]
+  long long plane;    // nx ny nz
+  int C;
+  int chunks_per_c;   // ceil(plane / kDenseChunk)
+  int* ctr;           // work counter, zeroed by the launcher
+  double2* part;      // C * chunks_per_c partials (sum z, sum z fill)
+  double* gmat;       // out: dL/d eps_bg, dL/d eps_fg
+};
+
 // One unit of device work: one design with the operations asked of it.  All
 // kernels take a table of jobs; a single-design call is a one-job table and a
 // batch of designs of uneven size runs through the same launches.
@@ -162,6 +180,8 @@ cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStrea
 cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, float* gtape,
                        int gtape_blocks, cudaStream_t s);
 cudaError_t launch_finalize(const Job* jobs, const JobTotals& t, cudaStream_t s);
+// the dense field stream (zero the counter, stream, fixed-order sum) on `s`
+cudaError_t launch_dense(const DenseArgs& a, int sms, cudaStream_t s);
 // Shared-memory limits of the kernels; call once per device before any capture.
 cudaError_t init_kernel_attributes();
 int build_blocks_per_sm(int njobs);

@@ -1605,6 +1605,98 @@ __global__ void __launch_bounds__(kBlock, 4) k_vjp(const Job* __restrict__ jobs,
   }
 }
 
+// ---- the dense field stream --------------------------------------------------
+// Each warp takes chunks of kDenseChunk samples from the counter and streams
+// E_fwd, E_adj (complex64) and fill with 16-byte loads
+// (cache-streaming: read once), accumulating z = Re(w E_adj E_fwd) and
+// z * fill in compensated fp32 per lane, then in FP64 over the warp.  The
+// chunk's partial goes to its own slot, so the order of the final sum does not
+// depend on which warp took which chunk.
+__device__ __forceinline__ float dense_z(float fr, float fi, float ar, float ai, float2 w) {
+  const float pr = fr * ar - fi * ai, pi = fr * ai + fi * ar;
+  return w.x * pr - w.y * pi;
+}
+
+constexpr int kDenseBlock = 256;
+__global__ void __launch_bounds__(kDenseBlock, 4) k_dense(DenseArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int nch = a.C * a.chunks_per_c;
+  while (true) {
+    int ch = 0;
+    if (lane == 0) ch = atomicAdd(a.ctr, 1);
+    ch = __shfl_sync(0xffffffffu, ch, 0);
+    if (ch >= nch) break;
+    const int c = ch / a.chunks_per_c;
+    const long long i0 = (long long)(ch - c * a.chunks_per_c) * kDenseChunk;
+    const long long i1 = min(a.plane, i0 + kDenseChunk);
+    // component c's arrays, selected without indexing the parameter block
+    const float2 w = c == 0 ? a.w[0] : (c == 1 ? a.w[1] : a.w[2]);
+    const float2* __restrict__ ef = c == 0 ? a.ef[0] : (c == 1 ? a.ef[1] : a.ef[2]);
+    const float2* __restrict__ ea = c == 0 ? a.ea[0] : (c == 1 ? a.ea[1] : a.ea[2]);
+    const float* __restrict__ fl = a.fill + (size_t)c * a.plane;
+    float sz = 0.f, cz = 0.f, sf = 0.f, cf = 0.f;
+    const bool vec = ((a.plane & 3) == 0) &&
+                     (((reinterpret_cast<uintptr_t>(ef) | reinterpret_cast<uintptr_t>(ea) |
+                        reinterpret_cast<uintptr_t>(fl)) & 15) == 0);
+    if (vec) {  // i0, i1 are multiples of 4
+      const float4* __restrict__ e4 = reinterpret_cast<const float4*>(ef);
+      const float4* __restrict__ a4 = reinterpret_cast<const float4*>(ea);
+      const float4* __restrict__ f4 = reinterpret_cast<const float4*>(fl);
+#pragma unroll 8
+      for (long long q = (i0 >> 2) + lane; q < (i1 >> 2); q += 32) {
+        const float4 e0 = __ldcs(e4 + 2 * q), e1 = __ldcs(e4 + 2 * q + 1);
+        const float4 g0 = __ldcs(a4 + 2 * q), g1 = __ldcs(a4 + 2 * q + 1);
+        const float4 f = __ldcs(f4 + q);
+        const float z0 = dense_z(e0.x, e0.y, g0.x, g0.y, w), z1 = dense_z(e0.z, e0.w, g0.z, g0.w, w);
+        const float z2 = dense_z(e1.x, e1.y, g1.x, g1.y, w), z3 = dense_z(e1.z, e1.w, g1.z, g1.w, w);
+        neumaier(sz, cz, (z0 + z1) + (z2 + z3));
+        neumaier(sf, cf, (z0 * f.x + z1 * f.y) + (z2 * f.z + z3 * f.w));
+      }
+    } else {
+      for (long long i = i0 + lane; i < i1; i += 32) {
+        const float2 e = __ldcs(ef + i), g = __ldcs(ea + i);
+        const float z = dense_z(e.x, e.y, g.x, g.y, w);
+        neumaier(sz, cz, z);
+        neumaier(sf, cf, z * __ldcs(fl + i));
+      }
+    }
+    double vz = (double)sz + (double)cz, vf = (double)sf + (double)cf;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      vz += __shfl_xor_sync(0xffffffffu, vz, o);
+      vf += __shfl_xor_sync(0xffffffffu, vf, o);
+    }
+    if (lane == 0) a.part[ch] = make_double2(vz, vf);
+  }
+}
+
+// One block: the chunk partials in index order (per-thread strided sums, then
+// a fixed shared-memory tree).
+__global__ void __launch_bounds__(256) k_dense_final(DenseArgs a) {
+  __shared__ double sz[256], sf[256];
+  const int t = threadIdx.x, nch = a.C * a.chunks_per_c;
+  double z = 0.0, f = 0.0;
+  for (int ch = t; ch < nch; ch += 256) {
+    const double2 v = a.part[ch];
+    z += v.x;
+    f += v.y;
+  }
+  sz[t] = z;
+  sf[t] = f;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (t < h) {
+      sz[t] += sz[t + h];
+      sf[t] += sf[t + h];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    a.gmat[0] = sz[0] - sf[0];  // sum z (1 - fill)
+    a.gmat[1] = sf[0];          // sum z fill
+  }
+}
+
 // One warp per parameter: fixed-order FP64 sums of its (primitive, slot)
 // partials over the derivative tile boxes.
 __global__ void k_finalize(const Job* __restrict__ jobs, int njobs, int nparams) {
@@ -1701,6 +1793,17 @@ cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, f
   const int grid = std::min(sms * vjp_blocks_per_sm(t.njobs), gtape_blocks);
   if (grid < 1 || !gtape) return cudaErrorInvalidValue;
   k_vjp<<<grid, kBlock, vjp_smem(t.njobs), s>>>(jobs, t.njobs, err, gtape);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense(const DenseArgs& a, int sms, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(a.ctr, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const int nch = a.C * a.chunks_per_c;
+  const int warps = kDenseBlock / 32;
+  const int grid = std::max(1, std::min((nch + warps - 1) / warps, sms * 4));
+  k_dense<<<grid, kDenseBlock, 0, s>>>(a);
+  k_dense_final<<<1, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

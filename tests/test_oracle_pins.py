@@ -419,6 +419,45 @@ def test_p8_fd_converges_second_order(oracle_mod):
     assert 3.0 < r1 < 5.0 and 3.0 < r2 < 5.0
 
 
+# ------------------------------------------- material levels (dense form) ---
+def test_material_level_derivatives_match_fd_of_the_loss(oracle_mod):
+    """dL/d eps_bg and dL/d eps_fg (Sec. 5.1's eps = eps_bg + deps fill): L is
+    linear in both, so central differences of the loss are exact up to
+    rounding."""
+    O = oracle_mod
+    desc = I.random_design(13, n=(36, 28, 10), nprims=12)
+    ef, ea, w = _fields(desc, 21, 22)
+    gm = O.grad_material(desc, ef, ea, w)
+    h = 0.25
+    fd = []
+    for key in ("eps_bg", "eps_fg"):
+        dp, dm = dict(desc), dict(desc)
+        dp[key] = desc[key] + h
+        dm[key] = desc[key] - h
+        fd.append((O.loss(dp, ef, ea, w) - O.loss(dm, ef, ea, w)) / (2 * h))
+    scale = abs(O.loss(desc, ef, ea, w)) + np.abs(gm).sum()
+    assert np.abs(gm - np.array(fd)).max() <= 1e-11 * scale
+
+
+def test_material_level_derivatives_count_cells(oracle_mod):
+    """Unit fields and w = 1 make every sample's Re(w E_adj E) = 1: the two
+    derivatives count the samples outside and inside a lattice-aligned box."""
+    O = oracle_mod
+    D = I.Design((20, 12, 6), (10.0, 10.0, 10.0), ncomp=3, eps_bg=1.0, eps_fg=3.0)
+    D.box(x=(-100.0, 1000.0), y=(-100.0, 1000.0), z=(-100.0, 1000.0))
+    D.box(x=(-50.0, -10.0))  # entirely off the grid: adds nothing
+    desc = D.to_desc()
+    ones = np.ones(I.field_shape(desc), dtype=np.complex64)
+    gm = O.grad_material(desc, ones, ones, 1.0)
+    total = ones.size
+    assert gm[1] == total and gm[0] == 0.0
+    D = I.Design((20, 12, 6), (10.0, 10.0, 10.0), ncomp=3, eps_bg=1.0, eps_fg=3.0)
+    D.box(x=(-100.0, 1000.0), y=(-100.0, 1000.0), z=(-1000.0, -500.0))  # below the grid
+    desc = D.to_desc()
+    gm = O.grad_material(desc, ones, ones, 1.0)
+    assert gm[0] == total and gm[1] == 0.0
+
+
 # ---------------------------------------------------------------- P9 --------
 def test_p9_invariants(oracle_mod):
     O = oracle_mod
