@@ -15,6 +15,7 @@ runs its own replica (the path shards across designs with no collective).
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import os
 import subprocess
@@ -91,44 +92,72 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
-def crop_z(desc, k0, nzs):
-    """The same design restricted to z-planes [k0, k0 + nzs) (for bounded CPU samples)."""
+def crop(desc, k0, nzs, j0=0, nys=None):
+    """The same design restricted to z-planes [k0, k0 + nzs) and y-rows
+    [j0, j0 + nys) (bounded CPU samples)."""
     d = dict(desc)
     g = dict(desc["grid"])
     n = list(g["n"])
     n[2] = nzs
+    if nys is not None:
+        n[1] = nys
     g["n"] = tuple(n)
     o = list(g["o"])
+    o[1] = o[1] + j0 * g["d"][1]
     o[2] = o[2] + k0 * g["d"][2]
     g["o"] = tuple(o)
     d["grid"] = g
     return d
 
 
-def oracle_sample(desc, ef, ea, w, target_s=12.0, max_planes=None):
-    """Time the oracle (fill + gradient, as it stands) on z-planes through the
-    slab, calibrated to about `target_s` of CPU work.  Returns (cells/s,
-    cores, description)."""
+def _oracle_box(desc, ef, ea, w, target_s):
+    """A block of z-planes (through the middle of the grid) and y-rows whose
+    oracle fill + gradient take about `target_s` on this host.  The oracle
+    runs its z-planes in parallel, so the probe takes one plane per thread;
+    shorter targets keep the planes and drop y-rows."""
     from oracle import oracle as O
     nx, ny, nz = desc["grid"]["n"]
     kc = nz // 2
-    one = crop_z(desc, kc, 1)
+    probe = max(1, min(nz, O.num_threads()))
+    k0 = max(0, kc - probe // 2)
     t0 = time.perf_counter()
-    O.fill(one)
-    O.grad(one, ef[:, kc:kc + 1], ea[:, kc:kc + 1], w)
+    O.fill(crop(desc, k0, probe))
+    O.grad(crop(desc, k0, probe), ef[:, k0:k0 + probe].copy(), ea[:, k0:k0 + probe].copy(), w)
     t1 = max(time.perf_counter() - t0, 1e-3)
-    planes = int(max(1, min(nz if max_planes is None else max_planes, target_s / t1)))
-    k0 = max(0, kc - planes // 2)
-    sub = crop_z(desc, k0, planes)
-    efs, eas = ef[:, k0:k0 + planes].copy(), ea[:, k0:k0 + planes].copy()
+    if target_s >= t1:  # whole multiples of the thread count keep every thread busy
+        planes = int(max(1, min(nz, probe * math.ceil(target_s / t1))))
+        return max(0, kc - planes // 2), planes, 0, ny
+    rows = int(max(1, ny * target_s / t1))
+    return k0, probe, (ny - rows) // 2, rows
+
+
+def _sample(desc, ef, ea, box):
+    k0, nzs, j0, nys = box
+    return (crop(desc, k0, nzs, j0, nys), ef[:, k0:k0 + nzs, j0:j0 + nys].copy(),
+            ea[:, k0:k0 + nzs, j0:j0 + nys].copy())
+
+
+def _sample_text(desc, box):
+    nx, ny, nz = desc["grid"]["n"]
+    k0, nzs, j0, nys = box
+    return ("%d of %d z-planes x %d of %d y-rows (%d cells x %d components) through the middle "
+            "of the grid" % (nzs, nz, nys, ny, nx * nys * nzs, desc["grid"]["ncomp"]))
+
+
+def oracle_sample(desc, ef, ea, w, target_s=15.0):
+    """Time the oracle (fill + gradient, as it stands) on a block through the
+    slab, about `target_s` of CPU work.  Returns (cells/s, cores, description)."""
+    from oracle import oracle as O
+    nx = desc["grid"]["n"][0]
+    box = _oracle_box(desc, ef, ea, w, target_s)
+    sub, efs, eas = _sample(desc, ef, ea, box)
     t0 = time.perf_counter()
     O.fill(sub)
     O.grad(sub, efs, eas, w)
     dt = time.perf_counter() - t0
-    cells = nx * ny * planes
-    return cells / dt, O.num_threads(), ("%d of %d z-planes (%d cells, %d components) through the "
-                                         "slab; one oracle fill + one oracle gradient, %.1f s"
-                                         % (planes, nz, cells, desc["grid"]["ncomp"], dt))
+    cells = nx * box[1] * box[3]
+    return cells / dt, O.num_threads(), "%s; one oracle fill + one oracle gradient, %.1f s" % (
+        _sample_text(desc, box), dt)
 
 
 def make_inputs():
@@ -148,17 +177,11 @@ def run_reference(args):
     desc, ef, ea, w = make_inputs()
     from oracle import oracle as O
     nx, ny, nz = desc["grid"]["n"]
-    # bounded sample per step: z-planes through the slab sized to ~2 s
-    kc = nz // 2
-    one = crop_z(desc, kc, 1)
-    t0 = time.perf_counter()
-    O.fill(one)
-    O.grad(one, ef[:, kc:kc + 1], ea[:, kc:kc + 1], w)
-    t1 = max(time.perf_counter() - t0, 1e-3)
-    planes = int(max(1, min(nz, 2.0 / t1)))
-    k0 = max(0, kc - planes // 2)
-    sub = crop_z(desc, k0, planes)
-    efs, eas = ef[:, k0:k0 + planes].copy(), ea[:, k0:k0 + planes].copy()
+    # bounded sample per step: z-planes through the slab, sized so that the
+    # whole run (warm-up + timed steps) takes about two minutes
+    per_step = min(2.0, 120.0 / max(1, args.steps + args.warmup))
+    box = _oracle_box(desc, ef, ea, w, per_step)
+    sub, efs, eas = _sample(desc, ef, ea, box)
     p0 = desc["params"]
     for k in range(args.warmup):
         O.fill(sub, p0 + 0.01 * (k % 2))
@@ -168,10 +191,9 @@ def run_reference(args):
         O.fill(sub, p0 + 0.01 * (k % 2))
         O.grad(sub, efs, eas, w, params=p0 + 0.01 * (k % 2))
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
-    cells = nx * ny * planes
+    cells = nx * box[1] * box[3]
     value = cells / dt
-    sample = ("%d of %d z-planes (%d cells x 3 components) through the slab per step: one "
-              "oracle fill + one oracle gradient" % (planes, nz, cells))
+    sample = "%s per step: one oracle fill + one oracle gradient" % _sample_text(desc, box)
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
