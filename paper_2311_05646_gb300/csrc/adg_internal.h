@@ -10,7 +10,7 @@ namespace adg {
 // them is reported through the device error word (never written out of range).
 constexpr int kMaxLeaves = 64;  // primitives whose edge band crosses the tile
 constexpr int kMaxOps = 120;    // folded logic program length (7-bit operand fields)
-constexpr int kSmemOps = 32;    // VJP tape entries kept in shared memory; longer
+constexpr int kSmemOps = 16;    // VJP tape entries kept in shared memory; longer
                                 // programs use a per-block slice of a global tape
 constexpr int kMaxDepth = 32;   // fold stack depth (checked at design creation)
 constexpr int kMaxSlots = 384;  // (primitive, active scalar) accumulators
@@ -24,7 +24,7 @@ static_assert(kMaxOps < 127 && kMaxLeaves < 127, "op operands are 7-bit fields, 
 // their table descriptors (80 B each), the VJP's per-warp accumulator rows,
 // then factor tables in what is left (at least kPoolSpare floats).
 constexpr int kBuildPool = 4096;
-constexpr int kVjpPool = 6144;
+constexpr int kVjpPool = 7040;
 constexpr int kPoolSpare = 192;
 constexpr int kLeafTabBytes = 80;
 constexpr size_t kTapeBlockFloats = (size_t)kMaxOps * kBlock;  // global tape per VJP block
@@ -80,13 +80,17 @@ struct alignas(16) PrimRec {
   float g[4];  // circle: R, R^2 (hi, lo) in cells, [3] = 1 if R < 0; polygon: [0] = winding sign
 };
 
-// Floats of a tile's pool taken by nleaf staged leaves with their descriptors
-// and nacc accumulators (plus as many compensation terms).
-__host__ __device__ constexpr int pool_need(int nleaf, int nacc) {
-  return (nleaf * ((int)sizeof(PrimRec) + kLeafTabBytes) / 4 + 2 * nacc + 3) & ~3;
+// Floats of a tile's pool taken by nleaf staged leaves with their table
+// descriptors, nops op descriptors (16 B) with a list entry each (4 B), and
+// nacc accumulators (plus as many compensation terms).
+__host__ __device__ constexpr int pool_need(int nleaf, int nacc, int nops) {
+  return (nleaf * ((int)sizeof(PrimRec) + kLeafTabBytes) / 4 + 5 * nops + 2 * nacc + 3) & ~3;
 }
-static_assert(pool_need(kMaxLeaves, 0) + kPoolSpare <= kBuildPool,
+static_assert(pool_need(kMaxLeaves, 0, 0) + kPoolSpare <= kBuildPool,
               "the build pool holds any tile's leaves");
+// the VJP's (slot, value) pair columns of graph and polygon leaves, taken from
+// the pool only by tiles that have such leaves
+constexpr int kPairFloats = 2 * kMaxPairs * kBlock;
 
 struct TileProg {
   int nops;   // 0: constant tile, value cval

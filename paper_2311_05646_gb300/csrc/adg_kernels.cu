@@ -333,35 +333,6 @@ __device__ __forceinline__ int leaf_pairs(const PrimRec& P, const Cell& c, float
   return n;
 }
 
-// ------------------------------------------------------------------ logic ---
-__device__ __forceinline__ float op_fwd(int code, int logic, float a, float b) {
-  switch (code) {
-    case fUnion: return logic == 0 ? (a + b - a * b) : fminf(1.f, a + b);
-    case fInter: return logic == 0 ? a * b : fmaxf(0.f, a + b - 1.f);
-    case fDiff: return logic == 0 ? a * (1.f - b) : fmaxf(0.f, a - b);
-    default: return 1.f - a;  // complement: difference(1, a)
-  }
-}
-
-__device__ __forceinline__ void op_bwd(int code, int logic, float a, float b, float& da,
-                                       float& db) {
-  switch (code) {
-    case fUnion:
-      if (logic == 0) { da = 1.f - b; db = 1.f - a; }
-      else { const float on = (a + b <= 1.f) ? 1.f : 0.f; da = on; db = on; }
-      break;
-    case fInter:
-      if (logic == 0) { da = b; db = a; }
-      else { const float on = (a + b >= 1.f) ? 1.f : 0.f; da = on; db = on; }
-      break;
-    case fDiff:
-      if (logic == 0) { da = 1.f - b; db = -a; }
-      else { const float on = (a - b >= 0.f) ? 1.f : 0.f; da = on; db = -on; }
-      break;
-    default: da = -1.f; db = 0.f;
-  }
-}
-
 // ---------------------------------------------------------- classification --
 __device__ __forceinline__ int cls_and(int a, int b) {
   if (a == cOUT || b == cOUT) return cOUT;
@@ -630,12 +601,12 @@ constexpr int kChainSmem = 1024, kPrimSmem = 96;
 // records are staged in the block's shared memory (small designs); otherwise
 // they are read through the read-only path.  The folded program is built in
 // shared memory and written out once, so the loop never stores to global.
-template <bool SMEM>
-__device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain, const PrimRec* sprim,
-                                         uint16_t (*stk)[128], uint16_t (*sleaf)[128],
-                                         uint16_t (*sop)[128], int* err) {
+template <bool SMEM, bool SCHAIN>
+__device__ __forceinline__ void bin_tile(const Job& J, int t, int nchain, const int* schain,
+                                         const PrimRec* sprim, uint16_t (*stk)[128],
+                                         uint16_t (*sleaf)[128], uint16_t (*sop)[128], int* err) {
   const int tid = threadIdx.x;
-  const int nchain = J.g.nchain, ntx = J.g.ntx, nty = J.g.nty;
+  const int ntx = J.g.ntx, nty = J.g.nty;
   const int lx = J.g.lx, ly = J.g.ly, lz = J.g.lz;
   const int* __restrict__ chain = J.chain;
   const PrimRec* __restrict__ prims = SMEM ? sprim : J.prims;
@@ -648,7 +619,7 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain,
   const float hi[3] = {(i1 - 1) + J.g.offmax[0], (j1 - 1) + J.g.offmax[1], (k1 - 1) + J.g.offmax[2]};
   int nops = 0, nleaf = 0, sp = 0, e = 0;
   for (int w = 0; w < nchain; ++w) {
-    const int word = SMEM ? schain[w] : __ldg(chain + w);
+    const int word = SCHAIN ? schain[w] : __ldg(chain + w);
     const int code = (word >> 24) & 0xff, arg = word & 0xffffff;
     if (code == cPush) {
       int b0, b1, b2, b3, b4, b5;
@@ -664,7 +635,7 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain,
       if (!cand && w + 1 < nchain) {
         // a primitive outside the tile is 0: union(A, 0) = A and
         // difference(A, 0) = A, so the pair leaves the stack as it is
-        const int nc = ((SMEM ? schain[w + 1] : __ldg(chain + w + 1)) >> 24) & 0xff;
+        const int nc = ((SCHAIN ? schain[w + 1] : __ldg(chain + w + 1)) >> 24) & 0xff;
         if ((nc == cUnion || nc == cDiff) && sp >= 1) { ++w; continue; }
       }
       const int cl = cand ? classify(prims[arg], lo, hi, auxd) : cOUT;
@@ -742,13 +713,18 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain,
   if ((fin & 3) != 2) { nops = 0; cval = (fin & 3) ? 1.f : 0.f; }
   TileProg* out = J.progs + t;
   int nslot = 0;
+  bool pairs = false;  // a graph or polygon leaf: the VJP reserves pair columns
   for (int l = 0; l < nleaf; ++l) {
     out->leaf[l] = sleaf[l][tid];
-    nslot += prims[sleaf[l][tid]].nact;
+    const PrimRec& L = prims[sleaf[l][tid]];
+    nslot += L.nact;
+    pairs |= L.kind == kGraph || L.kind == kPolygon;
   }
   for (int q = 0; q < nops; ++q) out->ops[q] = sop[q][tid];
   if (nops > 0 && nslot > kMaxSlots) e |= eSlotOverflow;
-  if (nops > 0 && pool_need(nleaf, kWarps * nslot) + kPoolSpare > kVjpPool) e |= ePoolOverflow;
+  if (nops > 0 && pool_need(nleaf, kWarps * nslot, nops) + (pairs ? kPairFloats : 0) + kPoolSpare >
+                      kVjpPool)
+    e |= ePoolOverflow;
   if (e) {
     atomicOr(err, e);
     nops = 0;
@@ -759,13 +735,23 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, const int* schain,
   out->cval = cval;
   out->nslot = nslot;
   J.tclass[t] = nops > 0 ? 2 : (cval != 0.f ? 1 : 0);
-  if (nops > 0) {
+  // band-tile list and counters, one atomic of each kind per group of lanes
+  // that arrive together (any grouping is correct; the list order is free)
+  const unsigned am = __activemask();
+  const int lane = tid & 31, leader = __ffs(am) - 1;
+  const bool band = nops > 0;
+  const unsigned bm = __ballot_sync(am, band);
+  const int mx = __reduce_max_sync(am, band ? nops : 0);
+  const int cells = __reduce_add_sync(am, band ? (i1 - i0) * (j1 - j0) * (k1 - k0) : 0);
+  int base = 0;
+  if (lane == leader && bm) {
     int* counters = J.counters;
-    const int idx = atomicAdd(&counters[0], 1);
-    J.list[idx] = t;
-    atomicMax(&counters[1], nops);
-    atomicAdd(&counters[2], (i1 - i0) * (j1 - j0) * (k1 - k0));
+    base = atomicAdd(&counters[0], __popc(bm));
+    atomicMax(&counters[1], mx);
+    atomicAdd(&counters[2], cells);
   }
+  base = __shfl_sync(am, base, leader);
+  if (band) J.list[base + __popc(bm & ((1u << lane) - 1u))] = t;
 }
 
 // One thread per tile; the block's 128 tiles belong to one job (tile ranges
@@ -786,26 +772,113 @@ __global__ void __launch_bounds__(128) k_bin(const Job* __restrict__ jobs, int n
   const int tid = threadIdx.x;
   const Job& J = jobs[job_by_tile(jobs, njobs, blockIdx.x * 128)];
   if (!J.do_bin) return;  // uniform over the block
-  const bool staged = J.g.nchain <= kChainSmem && J.g.nprims <= kPrimSmem;
-  if (staged) {
+  const bool staged = J.g.nprims <= kPrimSmem;    // primitive records in shared memory
+  const bool cstaged = J.g.nchain <= kChainSmem;  // the chain too (then compacted below)
+  if (cstaged)
     for (int q = tid; q < J.g.nchain; q += blockDim.x) schain[q] = J.chain[q];
+  if (staged) {
     constexpr int W = sizeof(PrimRec) / 16;
     for (int q = tid; q < J.g.nprims * W; q += blockDim.x)
       reinterpret_cast<int4*>(sprim)[q] = reinterpret_cast<const int4*>(J.prims)[q];
   }
-  __syncthreads();
+  // Block prefilter: the box of tile coordinates the block's 128 tiles span
+  // (y fastest, then x, then z).  A primitive whose value tile box misses it
+  // is 0 on all of them; if every primitive misses it, every tile's program
+  // folds to the constant 0 (a chain of unions, intersections and differences
+  // of zeros) and no thread walks the chain.
+  const int nty = J.g.nty, ntx = J.g.ntx;
+  const int ub0 = blockIdx.x * 128 - J.tile_base;
+  if (ub0 >= J.g.T) return;  // padding block (uniform)
+  const int ub1 = min(ub0 + 128, J.g.T) - 1;
+  __syncthreads();  // staged records visible
+  int bx0 = 0, bx1 = ntx - 1, by0 = 0, by1 = nty - 1;
+  const int bz0 = ub0 / (nty * ntx), bz1 = ub1 / (nty * ntx);
+  if (bz0 == bz1) {
+    bx0 = (ub0 / nty) % ntx;
+    bx1 = (ub1 / nty) % ntx;
+    if (bx0 == bx1) { by0 = ub0 % nty; by1 = ub1 % nty; }
+  }
+  bool hit = false;
+  for (int q = tid; q < J.g.nprims && !hit; q += blockDim.x) {
+    const int* tb = staged ? sprim[q].tb : J.prims[q].tb;
+    hit = bx0 < tb[1] && bx1 >= tb[0] && by0 < tb[3] && by1 >= tb[2] && bz0 < tb[5] &&
+          bz1 >= tb[4];
+  }
+  const bool any = __syncthreads_or(hit);
+  // Block chain compaction: a push of a primitive that misses the block's
+  // tile box, followed by a union or a difference, changes nothing for any of
+  // the block's tiles (union(A, 0) = difference(A, 0) = A); both ops are
+  // dropped once here instead of being skipped by every thread.
+  int nchain = J.g.nchain;
+  if (any && cstaged) {
+    __shared__ int wtot[kBlock / 32];
+    constexpr int kSeg = kChainSmem / kBlock;  // ops per thread
+    const int w0 = tid * kSeg;
+    auto misses = [&](int w) {  // op w pushes a primitive outside the block's tiles
+      const int word = schain[w];
+      if (((word >> 24) & 0xff) != cPush) return false;
+      const int* tb = staged ? sprim[word & 0xffffff].tb : J.prims[word & 0xffffff].tb;
+      return !(bx0 < tb[1] && bx1 >= tb[0] && by0 < tb[3] && by1 >= tb[2] && bz0 < tb[5] &&
+               bz1 >= tb[4]);
+    };
+    auto ud = [&](int w) {
+      const int c = (schain[w] >> 24) & 0xff;
+      return c == cUnion || c == cDiff;
+    };
+    int words[kSeg];
+    unsigned keep = 0;
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < kSeg; ++k) {
+      const int w = w0 + k;
+      words[k] = w < nchain ? schain[w] : 0;
+      bool drop = false;
+      if (w < nchain) {
+        if (w + 1 < nchain && ud(w + 1) && misses(w)) drop = true;
+        if (w >= 1 && ud(w) && misses(w - 1)) drop = true;
+      }
+      if (w < nchain && !drop) { keep |= 1u << k; ++cnt; }
+    }
+    const int lane = tid & 31, warp = tid >> 5;
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (lane == 31) wtot[warp] = inc;
+    __syncthreads();  // every thread has read its segment and its neighbours
+    int off = inc - cnt;
+    for (int v = 0; v < warp; ++v) off += wtot[v];
+    int total = 0;
+    for (int v = 0; v < kBlock / 32; ++v) total += wtot[v];
+#pragma unroll
+    for (int k = 0; k < kSeg; ++k)
+      if (keep & (1u << k)) schain[off++] = words[k];
+    nchain = total;
+    __syncthreads();
+  }
   const int u = blockIdx.x * 128 + tid - J.tile_base;
   if (u >= J.g.T) return;
-  const int nty = J.g.nty, ntx = J.g.ntx;
   const int ty = u % nty, tx = (u / nty) % ntx, tz = u / (nty * ntx);
   const int t = (tz * nty + ty) * ntx + tx;
-  if (staged) bin_tile<true>(J, t, schain, sprim, stk, sleaf, sop, err);
-  else bin_tile<false>(J, t, schain, sprim, stk, sleaf, sop, err);
+  if (!any) {
+    J.tclass[t] = 0;  // constant 0; build and VJP read only the class and the band list
+    return;
+  }
+  if (staged) {
+    if (cstaged) bin_tile<true, true>(J, t, nchain, schain, sprim, stk, sleaf, sop, err);
+    else bin_tile<true, false>(J, t, nchain, schain, sprim, stk, sleaf, sop, err);
+  } else {
+    if (cstaged) bin_tile<false, true>(J, t, nchain, schain, sprim, stk, sleaf, sop, err);
+    else bin_tile<false, false>(J, t, nchain, schain, sprim, stk, sleaf, sop, err);
+  }
 }
 
 __device__ __forceinline__ void stage_tile(const TileProg* P, const PrimRec* prims, int nops,
                                            int nleaf, uint16_t* sops, PrimRec* sl, int tid) {
-  for (int q = tid; q < nops; q += kBlock) sops[q] = P->ops[q];
+  if (sops)
+    for (int q = tid; q < nops; q += kBlock) sops[q] = P->ops[q];
   constexpr int W = sizeof(PrimRec) / 16;
   for (int q = tid; q < nleaf * W; q += kBlock) {
     const int l = q / W, w = q - l * W;
@@ -830,46 +903,53 @@ struct __align__(16) LeafTab {
 constexpr int tOK = 1, tBOX = 2, tACT = 4;  // tabled, box, drives some parameter
 constexpr int tKEYS = 8;                     // bits 8..13: box scalars driving a parameter
 
-// All threads: the accumulator slot and map coefficient of each box scalar
-// (staged in parallel: these are global reads).
+// All threads: the accumulator slot and map coefficient of each scalar of the
+// box (6) and circle (5) leaves (staged in parallel: these are global reads).
 __device__ __forceinline__ void stage_slots(const PrimRec* sl, int nleaf, const int* act,
                                             const float* actc, LeafTab* lt, int tid) {
   for (int q = tid; q < nleaf * 6; q += kBlock) {
     const int l = q / 6, k = q - l * 6;
-    const bool box = sl[l].kind == kBox;
-    lt[l].slot[k] = box ? __ldg(act + sl[l].act_off + k) : -1;
-    lt[l].coef[k] = box ? __ldg(actc + sl[l].act_off + k) : 0.f;
+    const int kind = sl[l].kind;
+    const bool keyed = kind == kBox || (kind == kCircle && k < 5);
+    lt[l].slot[k] = keyed ? __ldg(act + sl[l].act_off + k) : -1;
+    lt[l].coef[k] = keyed ? __ldg(actc + sl[l].act_off + k) : 0.f;
   }
 }
 
-// Thread 0: assign table offsets for the tile's leaves within `cap` floats;
-// with derivatives, the box key bits come from the staged slots.
-__device__ __forceinline__ void tables_plan(const PrimRec* sl, int nleaf, const GridDev& g,
-                                            bool derivs, int cap, LeafTab* lt) {
+// Warp 0: table offsets for the tile's leaves from prefix sums over the
+// lanes (a leaf whose tables would pass `cap` is evaluated directly); with
+// derivatives, the box key bits come from the staged slots.
+__device__ __forceinline__ void tables_plan_warp(const PrimRec* sl, int nleaf, const GridDev& g,
+                                                 bool derivs, int cap, LeafTab* lt, int lane) {
   const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
-  int off = 0;
-  for (int l = 0; l < nleaf; ++l) {
+  const int m = derivs ? 3 : 1;
+  int base = 0;
+  for (int l0 = 0; l0 < nleaf; l0 += 32) {
+    const int l = l0 + lane;
+    const bool on = l < nleaf;
+    const bool box = on && sl[l].kind == kBox;
+    const int need = !on ? 0 : (box ? m * C * (TX + TY + TZ) : C * TX * TY + m * C * TZ);
+    int inc = need;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    const int off = base + inc - need;
+    base += __shfl_sync(0xffffffffu, inc, 31);
+    if (!on) continue;
     int4 v = make_int4(-1, -1, -1, -1), d = make_int4(-1, -1, -1, 0);
-    const int m = derivs ? 3 : 1;
-    const bool box = sl[l].kind == kBox;
-    if (box) {
-      const int need = m * C * (TX + TY + TZ);
-      if (off + need <= cap) {
+    if (off + need <= cap) {
+      if (box) {
         v.x = off; v.y = v.x + C * TX; v.z = v.y + C * TY;
         if (derivs) { d.x = v.z + C * TZ; d.y = d.x + 2 * C * TX; d.z = d.y + 2 * C * TY; }
-        d.w |= tOK;
-        off += need;
-      }
-      d.w |= tBOX;
-    } else {
-      const int need = C * TX * TY + m * C * TZ;
-      if (off + need <= cap) {
+      } else {
         v.w = off; v.z = v.w + C * TX * TY;
         if (derivs) d.z = v.z + C * TZ;
-        d.w |= tOK;
-        off += need;
       }
+      d.w |= tOK;
     }
+    if (box) d.w |= tBOX;
     if (sl[l].nact > 0) d.w |= tACT;
     if (derivs && box)
       for (int k = 0; k < 6; ++k)
@@ -968,33 +1048,6 @@ struct TileLoc {
   int TX, TY, TZ;
 };
 
-__device__ __forceinline__ float tab_value(const int4 v, bool box, const TileLoc& q,
-                                           const float* tab) {
-  const float fz = tab[v.z + q.c * q.TZ + q.z];
-  if (box) return tab[v.x + q.c * q.TX + q.x] * tab[v.y + q.c * q.TY + q.y] * fz;
-  return tab[v.w + (q.c * q.TY + q.y) * q.TX + q.x] * fz;
-}
-
-__device__ __forceinline__ float eval_forward(const uint16_t* sops, int nops, const PrimRec* sl,
-                                              const LeafTab* lt, const float* tab,
-                                              const TileLoc& q, const Cell& cc, int logic,
-                                              float* tape, int tid, const float* auxf,
-                                              const double* auxd) {
-  float v = 0.f;
-  for (int pos = 0; pos < nops; ++pos) {
-    const FoldOp fo = fold_op(sops[pos]);
-    const int code = fo.code, a = fo.a, b = fo.b;
-    if (code == fPush) {
-      const int f = lt[a].d.w;
-      v = (f & tOK) ? tab_value(lt[a].v, (f & tBOX) != 0, q, tab) : leaf_value(sl[a], cc, auxf, auxd);
-    } else {
-      v = op_fwd(code, logic, tape[a * kBlock + tid], code == fCompl ? 0.f : tape[b * kBlock + tid]);
-    }
-    tape[pos * kBlock + tid] = v;
-  }
-  return v;
-}
-
 static_assert(sizeof(LeafTab) == kLeafTabBytes, "pool accounting");
 // job-prefix entries in shared memory: a class for small tables, one for any
 __host__ __device__ constexpr int spre_len(int njobs) { return njobs < 16 ? 16 : kMaxJobs + 1; }
@@ -1017,7 +1070,7 @@ __device__ __forceinline__ TilePool carve_pool(float* pool, int size, int nleaf,
   t.lt = reinterpret_cast<LeafTab*>(t.sl + nleaf);
   t.acc = reinterpret_cast<float*>(t.lt + nleaf);
   t.cmp = t.acc + nacc;
-  const int used = pool_need(nleaf, nacc);  // the binner keeps it <= size - kPoolSpare
+  const int used = pool_need(nleaf, nacc, 0);  // <= size - kPoolSpare
   t.tab = pool + used;
   t.cap = size - used;
   return t;
@@ -1237,9 +1290,10 @@ __global__ void __launch_bounds__(kBlock) k_build(const Job* __restrict__ jobs, 
     __syncthreads();  // the previous tile is done with the staged program
     stage_tile(P, J.prims, nops, nleaf, sops, tp.sl, tid);
     __syncthreads();
-    if (tid == 0) {
-      tables_plan(tp.sl, nleaf, g, false, tp.cap, tp.lt);
-      sdepth[0] = plan_descs(sops, nops, tp.lt, desc);
+    if (tid < 32) {
+      tables_plan_warp(tp.sl, nleaf, g, false, tp.cap, tp.lt, tid);
+      __syncwarp();
+      if (tid == 0) sdepth[0] = plan_descs(sops, nops, tp.lt, desc);
     }
     __syncthreads();
     tables_fill(tp.sl, nleaf, g, tp.lt, false, tx << g.lx, ty << g.ly, tz << g.lz, tp.tab, tid,
@@ -1346,30 +1400,74 @@ __device__ __forceinline__ void key_reduce(int slot, float v, float* acc, float*
   if (lane == 0) neumaier(acc[slot], cmp[slot], v);
 }
 
+// Where a keyed leaf's terms go: a per-thread column of the tile's
+// accumulators (col[slot * kBlock], summed once per tile), or, when the tile
+// has too many slots for columns, a warp reduction per key into the warp's
+// compensated row.  `pt` is uniform over the block.
+struct KeySink {
+  float* col;
+  float* acc;
+  float* cmp;
+  int lane;
+  bool pt;
+  __device__ __forceinline__ void add(int slot, float v) const {
+    if (pt) col[slot * kBlock] += v;
+    else key_reduce(slot, v, acc, cmp, lane);
+  }
+};
+
 // d s / d (box scalar k) * a for the six scalars of a tabled box leaf
-// (keys 0..5 = x0, x1, y0, y1, z0, z1), each reduced over the warp.
+// (keys 0..5 = x0, x1, y0, y1, z0, z1).
 __device__ __forceinline__ void box_tab_reduce(const LeafTab& t, const TileLoc& q, const float* tab,
-                                               float a, const GridDev& g, float* acc, float* cmp,
-                                               int lane) {
+                                               float a, const GridDev& g, const KeySink& ks) {
   const int4 v = t.v, d = t.d;
   const float fx = tab[v.x + q.c * q.TX + q.x], fy = tab[v.y + q.c * q.TY + q.y],
               fz = tab[v.z + q.c * q.TZ + q.z];
   const int k = d.w >> 3;
   if (k & 3) {
     const float ax = a * fy * fz * g.invd[0];
-    if (k & 1) key_reduce(t.slot[0], tab[d.x + (2 * q.c) * q.TX + q.x] * ax * t.coef[0], acc, cmp, lane);
-    if (k & 2) key_reduce(t.slot[1], tab[d.x + (2 * q.c + 1) * q.TX + q.x] * ax * t.coef[1], acc, cmp, lane);
+    if (k & 1) ks.add(t.slot[0], tab[d.x + (2 * q.c) * q.TX + q.x] * ax * t.coef[0]);
+    if (k & 2) ks.add(t.slot[1], tab[d.x + (2 * q.c + 1) * q.TX + q.x] * ax * t.coef[1]);
   }
   if (k & 12) {
     const float ay = a * fx * fz * g.invd[1];
-    if (k & 4) key_reduce(t.slot[2], tab[d.y + (2 * q.c) * q.TY + q.y] * ay * t.coef[2], acc, cmp, lane);
-    if (k & 8) key_reduce(t.slot[3], tab[d.y + (2 * q.c + 1) * q.TY + q.y] * ay * t.coef[3], acc, cmp, lane);
+    if (k & 4) ks.add(t.slot[2], tab[d.y + (2 * q.c) * q.TY + q.y] * ay * t.coef[2]);
+    if (k & 8) ks.add(t.slot[3], tab[d.y + (2 * q.c + 1) * q.TY + q.y] * ay * t.coef[3]);
   }
   if (k & 48) {
     const float az = a * fx * fy * g.invd[2];
-    if (k & 16) key_reduce(t.slot[4], tab[d.z + (2 * q.c) * q.TZ + q.z] * az * t.coef[4], acc, cmp, lane);
-    if (k & 32) key_reduce(t.slot[5], tab[d.z + (2 * q.c + 1) * q.TZ + q.z] * az * t.coef[5], acc, cmp, lane);
+    if (k & 16) ks.add(t.slot[4], tab[d.z + (2 * q.c) * q.TZ + q.z] * az * t.coef[4]);
+    if (k & 32) ks.add(t.slot[5], tab[d.z + (2 * q.c + 1) * q.TZ + q.z] * az * t.coef[5]);
   }
+}
+
+// The same for a box whose factors are not tabled (evaluated at the sample).
+__device__ __forceinline__ void box_direct_reduce(const PrimRec& P, const LeafTab& t, const Cell& c,
+                                                  float a, const GridDev& g, const KeySink& ks) {
+  float f[3], fa[3], fb[3];
+  box_axes(P, c, f, fa, fb);
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const float other = f[(ax + 1) % 3] * f[(ax + 2) % 3] * a * g.invd[ax];
+    if (t.slot[2 * ax] >= 0) ks.add(t.slot[2 * ax], fa[ax] * other * t.coef[2 * ax]);
+    if (t.slot[2 * ax + 1] >= 0) ks.add(t.slot[2 * ax + 1], fb[ax] * other * t.coef[2 * ax + 1]);
+  }
+}
+
+// Circ2D (Table 4) extruded in z: keys cx, cy, r, z0, z1, each reduced over the
+// warp (every lane holds the same leaf, so the slots are warp-uniform).
+__device__ __forceinline__ void circle_reduce(const PrimRec& P, const LeafTab& t, const Cell& c,
+                                              float a, const GridDev& g, const KeySink& ks) {
+  float dz0, dz1, dxr, dyr, r, ds;
+  const float zf = zfactor(P, c, dz0, dz1);
+  const float s = sigma_f(P.sigma, P.kr * circle_dist(P, c, dxr, dyr, r), ds);
+  const float gg = P.kr * ds * zf * a * g.invd[0];
+  const float ir = r > 0.f ? 1.f / r : 0.f;
+  if (t.slot[0] >= 0) ks.add(t.slot[0], gg * dxr * ir * t.coef[0]);
+  if (t.slot[1] >= 0) ks.add(t.slot[1], gg * dyr * ir * t.coef[1]);
+  if (t.slot[2] >= 0) ks.add(t.slot[2], gg * t.coef[2]);
+  if (t.slot[3] >= 0) ks.add(t.slot[3], s * dz0 * a * g.invd[2] * t.coef[3]);
+  if (t.slot[4] >= 0) ks.add(t.slot[4], s * dz1 * a * g.invd[2] * t.coef[4]);
 }
 
 // Activity of the tile's samples, per axis: a sample can have a nonzero
@@ -1399,27 +1497,118 @@ __device__ __forceinline__ void activity_axes(const LeafTab* lt, int nleaf, cons
   }
 }
 
-constexpr int kSeedChunk = 512;  // active samples whose seeds are staged at once
-constexpr size_t kVjpFixed = (size_t)kSmemOps * kBlock * 4 + (size_t)kVjpPool * 4 +
-                             2 * (size_t)kMaxPairs * kBlock * 4 + (size_t)kSeedChunk * 4 +
-                             (size_t)kMaxTileCells * 3 * 2 + kMaxOps * 2 + (kMaxLeaves + 1) * 4 +
-                             kAct1 + kWarps * 4 + 4;
-size_t vjp_smem(int njobs) { return ((kVjpFixed + 15) & ~(size_t)15) + (size_t)spre_len(njobs) * 4; }
+// ---- VJP helpers ---------------------------------------------------------------
+// Warp 0: one descriptor per op (pushes as for the build; logic ops carry
+// their operand positions in y, z) and, in program order, the positions that
+// push a parameter-driven leaf (pos | leaf << 8).  Returns their number.
+__device__ __forceinline__ int descs_warp(const uint16_t* __restrict__ ops, int nops,
+                                          const LeafTab* lt, int4* desc, int* dl, int lane) {
+  int n = 0;
+  for (int p0 = 0; p0 < nops; p0 += 32) {
+    const int pos = p0 + lane;
+    bool act = false;
+    int leaf = 0;
+    if (pos < nops) {
+      const FoldOp fo = fold_op(__ldg(ops + pos));
+      if (fo.code == fPush) {
+        const int f = lt[fo.a].d.w;
+        const int4 v = lt[fo.a].v;
+        desc[pos] = !(f & tOK) ? make_int4(dDirect, fo.a, 0, 0)
+                  : (f & tBOX) ? make_int4(dBox, v.x, v.y, v.z) : make_int4(dPlane, v.w, 0, v.z);
+        act = (f & tACT) != 0;
+        leaf = fo.a;
+      } else {
+        desc[pos] = make_int4(dLogic + fo.code, fo.a, fo.b, 0);
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, act);
+    if (act) dl[n + __popc(m & ((1u << lane) - 1u))] = pos | (leaf << 8);
+    n += __popc(m);
+  }
+  return n;
+}
 
-__global__ void __launch_bounds__(kBlock, 4) k_vjp(const Job* __restrict__ jobs, int njobs,
+template <int LOGIC>
+__device__ __forceinline__ void logic_bwd(int code, float a, float b, float& da, float& db) {
+  if (code == fUnion) {
+    if (LOGIC == 0) { da = 1.f - b; db = 1.f - a; }
+    else { const float on = (a + b <= 1.f) ? 1.f : 0.f; da = on; db = on; }
+  } else if (code == fInter) {
+    if (LOGIC == 0) { da = b; db = a; }
+    else { const float on = (a + b >= 1.f) ? 1.f : 0.f; da = on; db = on; }
+  } else {
+    if (LOGIC == 0) { da = 1.f - b; db = -a; }
+    else { const float on = (a - b >= 0.f) ? 1.f : 0.f; da = on; db = -on; }
+  }
+}
+
+// Forward tape (value of every op at the sample), then the reverse sweep
+// through the logic (Eqs. AD / jaceps): afterwards tap[pos] holds d fill / d
+// value(pos).  tap: this thread's column, stride kBlock.
+template <int LOGIC>
+__device__ __forceinline__ void vjp_tape(const int4* desc, int nops, const float* tab,
+                                         const SampleOff& o, const PrimRec* sl, int4 pc,
+                                         const GridDev& g, const float* auxf, const double* auxd,
+                                         float* tap) {
+  for (int pos = 0; pos < nops; ++pos) {
+    const int4 d = desc[pos];
+    float v;
+    if (d.x == dBox) {
+      v = tab[d.y + o.x] * tab[d.z + o.y] * tab[d.w + o.z];
+    } else if (d.x == dPlane) {
+      v = tab[d.y + o.xy] * tab[d.w + o.z];
+    } else if (d.x == dDirect) {
+      const Cell c{pc.x, pc.y, pc.z, g.off[pc.w][0], g.off[pc.w][1], g.off[pc.w][2]};
+      v = leaf_value(sl[d.y], c, auxf, auxd);
+    } else if (d.x == dLogic + fCompl) {
+      v = 1.f - tap[d.y * kBlock];
+    } else {
+      v = logic_fwd<LOGIC>(d.x - dLogic, tap[d.y * kBlock], tap[d.z * kBlock]);
+    }
+    tap[pos * kBlock] = v;
+  }
+  tap[(nops - 1) * kBlock] = 1.f;
+  for (int pos = nops - 1; pos >= 0; --pos) {
+    const int4 d = desc[pos];
+    if (d.x < dLogic) continue;
+    const float adj = tap[pos * kBlock];
+    if (d.x == dLogic + fCompl) {
+      tap[d.y * kBlock] = -adj;
+      continue;
+    }
+    float da, db;
+    logic_bwd<LOGIC>(d.x - dLogic, tap[d.y * kBlock], tap[d.z * kBlock], da, db);
+    tap[d.y * kBlock] = adj * da;
+    tap[d.z * kBlock] = adj * db;
+  }
+}
+
+constexpr int kSeedChunk = 512;  // active samples whose seeds are staged at once
+// a tile's x-rows (C * TY * TZ <= 3 * 1024 / 32) fit the seed buffer they alias
+static_assert(3 * kMaxTileCells / 32 <= kSeedChunk, "row offsets alias the seed buffer");
+constexpr size_t kVjpFixed = (size_t)kSmemOps * kBlock * 4 + (size_t)kVjpPool * 4 +
+                             (size_t)kSeedChunk * 4 + (size_t)kMaxTileCells * 3 * 2 +
+                             (kMaxLeaves + 1) * 4 + kAct1 + 32 * 4;
+__host__ __device__ constexpr size_t vjp_smem(int njobs) {
+  return ((kVjpFixed + 15) & ~(size_t)15) + (size_t)spre_len(njobs) * 4;
+}
+// five blocks per SM (228 KB of shared memory, 1 KB reserved per block)
+static_assert(5 * (vjp_smem(1) + 1024) <= 228 * 1024, "VJP shared memory for five blocks per SM");
+
+__global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs, int njobs,
                                                    int* __restrict__ err,
                                                    float* __restrict__ gtape) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* tape = reinterpret_cast<float*>(smem);
   float* pool = tape + kSmemOps * kBlock;
-  float* pv = pool + kVjpPool;
-  int* pk = reinterpret_cast<int*>(pv + kMaxPairs * kBlock);
-  float* zsb = reinterpret_cast<float*>(pk + kMaxPairs * kBlock);  // seeds of a chunk
+  float* zsb = pool + kVjpPool;  // seeds of a chunk
+  int* rinfo = reinterpret_cast<int*>(zsb);  // before the seeds: per x-row offset << 2 | kind
   uint16_t* slist = reinterpret_cast<uint16_t*>(zsb + kSeedChunk);  // active samples
-  uint16_t* sops = slist + kMaxTileCells * 3;
-  int* sbase = reinterpret_cast<int*>(sops + kMaxOps);
+  int* sbase = reinterpret_cast<int*>(slist + kMaxTileCells * 3);
   unsigned char* act1 = reinterpret_cast<unsigned char*>(sbase + kMaxLeaves + 1);
-  int* swm = reinterpret_cast<int*>(act1 + kAct1);  // per-warp active counts, then the all-flag
+  // misc words: [0] active samples, [1] all-active flag, [2] parameter-driven
+  // pushes, [4..9] x-row masks per component (2 words each), [10..11] in-grid x
+  int* misc = reinterpret_cast<int*>(act1 + kAct1);
   int* spre = reinterpret_cast<int*>(smem + ((kVjpFixed + 15) & ~(size_t)15));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) job_prefix(jobs, njobs, true, spre);
@@ -1438,72 +1627,145 @@ __global__ void __launch_bounds__(kBlock, 4) k_vjp(const Job* __restrict__ jobs,
       if (tid == 0) atomicOr(err, eSlotOverflow);
       continue;
     }
-    const TilePool tp = carve_pool(pool, kVjpPool, nleaf, kWarps * nslot);
-    const PrimRec* sl = tp.sl;
-    const LeafTab* lt = tp.lt;
-    const float* tab = tp.tab;
+    // pool: staged leaves, descriptors, op descriptors, pushes list,
+    // accumulator rows, then per-thread columns and factor tables
+    PrimRec* slw = reinterpret_cast<PrimRec*>(pool);
+    LeafTab* ltw = reinterpret_cast<LeafTab*>(slw + nleaf);
+    int4* desc = reinterpret_cast<int4*>(ltw + nleaf);
+    int* dl = reinterpret_cast<int*>(desc + nops);
+    float* racc = reinterpret_cast<float*>(dl + nops);
+    float* rcmp = racc + kWarps * nslot;
+    const int used = pool_need(nleaf, kWarps * nslot, nops);
+    const PrimRec* sl = slw;
+    const LeafTab* lt = ltw;
     __syncthreads();  // the previous tile is done with the pool
-    stage_tile(P, J.prims, nops, nleaf, sops, tp.sl, tid);
-    for (int q = tid; q < 2 * kWarps * nslot; q += kBlock) tp.acc[q] = 0.f;  // acc, cmp
+    stage_tile(P, J.prims, 0, nleaf, nullptr, slw, tid);
+    for (int q = tid; q < 2 * kWarps * nslot; q += kBlock) racc[q] = 0.f;  // rows and compensation
     __syncthreads();
-    stage_slots(sl, nleaf, J.act, J.actc, tp.lt, tid);
+    stage_slots(sl, nleaf, J.act, J.actc, ltw, tid);
+    // After the rows: pair columns (tiles with graph or polygon leaves), then
+    // per-thread accumulator columns (nslot x kBlock) when they take at most
+    // half of what is left, then the factor tables.  The binner checked that
+    // the rows and the pair columns leave at least kPoolSpare floats.
+    bool pairs = false;
+    for (int l = 0; l < nleaf; ++l) pairs |= sl[l].kind == kGraph || sl[l].kind == kPolygon;
+    float* pv = pool + used;
+    int* pk = reinterpret_cast<int*>(pv + kMaxPairs * kBlock);
+    const int used2 = used + (pairs ? kPairFloats : 0);
+    const int cap = kVjpPool - used2;
+    const bool pt = nslot * kBlock <= cap / 2;
+    float* tcol = pool + used2;
+    float* tabw = pt ? tcol + nslot * kBlock : tcol;
+    const int tcap = pt ? cap - nslot * kBlock : cap;
+    const float* tab = tabw;
+    if (pt)
+      for (int q = 0; q < nslot; ++q) tcol[q * kBlock + tid] = 0.f;  // this thread's column
     __syncthreads();
-    if (tid == 0) {
-      int sum = 0, all = 0;
-      for (int l = 0; l < nleaf; ++l) { sbase[l] = sum; sum += sl[l].nact; }
-      sbase[nleaf] = sum;
-      tables_plan(sl, nleaf, g, true, tp.cap, tp.lt);
-      for (int l = 0; l < nleaf; ++l) {
-        const int f = lt[l].d.w;
-        if ((f & tACT) && (f & (tOK | tBOX)) != (tOK | tBOX)) all = 1;
+    if (warp == 0) {
+      tables_plan_warp(sl, nleaf, g, true, tcap, ltw, lane);
+      // (primitive, parameter) slot bases: exclusive prefix of nact
+      int base = 0;
+      bool all = false;
+      for (int l0 = 0; l0 < nleaf; l0 += 32) {
+        const int l = l0 + lane;
+        const int na = l < nleaf ? sl[l].nact : 0;
+        int inc = na;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += u;
+        }
+        if (l < nleaf) sbase[l] = base + inc - na;
+        base += __shfl_sync(0xffffffffu, inc, 31);
       }
-      swm[kWarps] = all;
+      __syncwarp();
+      for (int l = lane; l < nleaf; l += 32) {
+        const int f = lt[l].d.w;
+        if ((f & tACT) && (f & (tOK | tBOX)) != (tOK | tBOX)) all = true;
+      }
+      all = __any_sync(0xffffffffu, all);
+      const int ndl = descs_warp(P->ops, nops, lt, desc, dl, lane);
+      if (lane == 0) {
+        sbase[nleaf] = base;
+        misc[1] = all;
+        misc[2] = ndl;
+      }
     }
     __syncthreads();
-    tables_fill(sl, nleaf, g, lt, true, tx << g.lx, ty << g.ly, tz << g.lz, tp.tab, tid, J.auxf,
+    tables_fill(sl, nleaf, g, lt, true, tx << g.lx, ty << g.ly, tz << g.lz, tabw, tid, J.auxf,
                 J.auxd);
     __syncthreads();
     activity_axes(lt, nleaf, g, tab, act1, tid);
     __syncthreads();
-    float* wacc = tp.acc + warp * nslot;
-    float* wcmp = tp.cmp + warp * nslot;
+    float* wacc = racc + warp * nslot;
+    float* wcmp = rcmp + warp * nslot;
     const int lxy = g.lx + g.ly, lxyz = lxy + g.lz;
-    const int ncc = g.C << lxyz;
-    const int TXm = (1 << g.lx) - 1, TYm = (1 << g.ly) - 1, TZm = (1 << g.lz) - 1;
+    const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
+    const int TXm = TX - 1, TYm = TY - 1, TZm = TZ - 1;
     const size_t plane = (size_t)g.nx * g.ny * g.nz;
-    // Active samples, compacted per warp over its contiguous quarter of the
-    // tile (ncc is a multiple of 128) with ballots: active index i runs
-    // through the samples in order, so the accumulation order is fixed.
-    const int per = ncc / kWarps;
-    {
-      const bool all = swm[kWarps] != 0;
-      const int C = g.C, TX = TXm + 1, TY = TYm + 1;
-      uint16_t* wl = slist + warp * per;
-      int cnt = 0;
-      for (int l0 = warp * per; l0 < (warp + 1) * per; l0 += 32) {
-        const int l = l0 + lane;
-        const int x = l & TXm, y = (l >> g.lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
-        const bool in = (tx << g.lx) + x < g.nx && (ty << g.ly) + y < g.ny && (tz << g.lz) + z < g.nz;
-        const bool act = in && (all || act1[c * TX + x] || act1[C * TX + c * TY + y] ||
-                                act1[C * (TX + TY) + c * (TZm + 1) + z]);
-        const unsigned m = __ballot_sync(0xffffffffu, act);
-        if (act) wl[cnt + __popc(m & ((1u << lane) - 1u))] = (uint16_t)l;
-        cnt += __popc(m);
+    const int X0 = tx << g.lx, Y0 = ty << g.ly, Z0 = tz << g.lz;
+    const int nrows = C * TY * TZ;
+    const int nw = TX >> 5;  // 32-bit words per x-row
+    // Active samples, per x-row (c, z, y): the whole row when the sample's y
+    // or z moves a face (or a non-box leaf drives a parameter), else the
+    // component's x-pattern; out-of-grid samples never.  Row offsets come
+    // from one prefix sum, so the list runs through the samples in order and
+    // the accumulation order is fixed.
+    if (warp == 0) {
+      for (int c = 0; c < C; ++c)
+        for (int h = 0; h < nw; ++h) {
+          const int x = h * 32 + lane;
+          const bool in = X0 + x < g.nx;
+          const unsigned xm = __ballot_sync(0xffffffffu, in && act1[c * TX + x]);
+          const unsigned xi = __ballot_sync(0xffffffffu, in);
+          if (lane == 0) {
+            misc[4 + 2 * c + h] = (int)xm;
+            if (c == 0) misc[10 + h] = (int)xi;
+          }
+        }
+      __syncwarp();
+      const bool all = misc[1] != 0;
+      int base = 0;
+      for (int r0 = 0; r0 < nrows; r0 += 32) {
+        const int r = r0 + lane;
+        int kind = 0, cnt = 0;
+        if (r < nrows) {
+          const int c = r / (TY * TZ), rem = r - c * TY * TZ, z = rem / TY, y = rem - z * TY;
+          if (Y0 + y < g.ny && Z0 + z < g.nz) {
+            const bool full = all || act1[C * TX + c * TY + y] || act1[C * (TX + TY) + c * TZ + z];
+            kind = full ? 1 : 2;
+            for (int h = 0; h < nw; ++h)
+              cnt += __popc((unsigned)(full ? misc[10 + h] : misc[4 + 2 * c + h]));
+          }
+        }
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += u;
+        }
+        if (r < nrows) rinfo[r] = ((base + inc - cnt) << 2) | kind;
+        base += __shfl_sync(0xffffffffu, inc, 31);
       }
-      if (lane == 0) swm[warp] = cnt;  // the all-flag sits in swm[kWarps]
+      if (lane == 0) misc[0] = base;
     }
     __syncthreads();
-    int wpre[kWarps + 1];
-    wpre[0] = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) wpre[w + 1] = wpre[w] + swm[w];
-    const int nact_cells = wpre[kWarps];
-    auto apos = [&](int i) {  // slist position of active index i
-      int w = 0;
-#pragma unroll
-      for (int v = 1; v < kWarps; ++v) w += i >= wpre[v];
-      return w * per + (i - wpre[w]);
-    };
+    for (int r = warp; r < nrows; r += kWarps) {
+      const int e = rinfo[r];
+      const int kind = e & 3;
+      if (!kind) continue;
+      int off = e >> 2;
+      const int c = r / (TY * TZ), rem = r - c * TY * TZ, z = rem / TY, y = rem - z * TY;
+      const int lrow = ((c * TZ + z) * TY + y) << g.lx;
+      for (int h = 0; h < nw; ++h) {
+        const unsigned m = (unsigned)(kind == 1 ? misc[10 + h] : misc[4 + 2 * c + h]);
+        if ((m >> lane) & 1u) slist[off + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(lrow + h * 32 + lane);
+        off += __popc(m);
+      }
+    }
+    __syncthreads();
+    const int nact_cells = misc[0];
+    const int ndl = misc[2];
     if (tid == 0) atomicAdd(&J.counters[3], nact_cells);
     for (int c0 = 0; c0 < nact_cells; c0 += kSeedChunk) {
       const int c1 = min(nact_cells, c0 + kSeedChunk);
@@ -1512,10 +1774,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_vjp(const Job* __restrict__ jobs,
       for (int i0 = c0; i0 < c0 + kSeedChunk; i0 += kBlock) {
         const int i = i0 + tid;
         if (i < c1) {
-          const int l = slist[apos(i)];
+          const int l = slist[i];
           const int x = l & TXm, y = (l >> g.lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
-          const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
-          const size_t o = ((size_t)gk * g.ny + gj) * g.nx + gi;
+          const size_t o = ((size_t)(Z0 + z) * g.ny + (Y0 + y)) * g.nx + (X0 + x);
           float zs;
           if (va.G) {
             zs = __ldg(va.G + (size_t)c * plane + o);
@@ -1528,70 +1789,85 @@ __global__ void __launch_bounds__(kBlock, 4) k_vjp(const Job* __restrict__ jobs,
         }
       }
       // The tape: shared memory for short programs, else this block's slice of
-      // the global tape (the two variants are separate instantiations, so the
-      // shared one keeps shared-memory addressing).
-      auto samples = [&](auto big) {
+      // the global tape; the logic family is a template parameter.  The
+      // variants are separate instantiations, so the shared one keeps
+      // shared-memory addressing.
+      auto samples = [&](auto big, auto logic) {
         constexpr bool kBig = decltype(big)::value;
-        float* tap = kBig ? gtape + (size_t)blockIdx.x * kTapeBlockFloats : tape;
+        constexpr int kLogic = decltype(logic)::value;
+        float* tap = (kBig ? gtape + (size_t)blockIdx.x * kTapeBlockFloats : tape) + tid;
         for (int i0 = c0; i0 < c1; i0 += kBlock) {
           if (i0 + warp * 32 >= c1) continue;  // no live lane in this warp (warp-uniform)
           const int i = i0 + tid;
           const bool live = i < c1;
-          const int l = live ? slist[apos(i)] : 0;
+          const int l = live ? slist[i] : 0;
           const int x = l & TXm, y = (l >> g.lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
-          const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
           const float zs = live ? zsb[i - c0] : 0.f;
-          const Cell cc{gi, gj, gk, g.off[c][0], g.off[c][1], g.off[c][2]};
-          const TileLoc q{x, y, z, c, 1 << g.lx, 1 << g.ly, 1 << g.lz};
-          eval_forward(sops, nops, sl, lt, tab, q, cc, g.logic, tap, tid, J.auxf, J.auxd);
-          // reverse sweep through the logic: tape slots become adjoints d fill / d node
-          tap[(nops - 1) * kBlock + tid] = 1.f;
-          for (int pos = nops - 1; pos >= 0; --pos) {
-            const FoldOp fo = fold_op(sops[pos]);
-            const int code = fo.code;
-            if (code == fPush) continue;
-            const int a = fo.a, b = fo.b;
-            const float adj = tap[pos * kBlock + tid];
-            const float vb = code == fCompl ? 0.f : tap[b * kBlock + tid];
-            float da, db;
-            op_bwd(code, g.logic, tap[a * kBlock + tid], vb, da, db);
-            tap[a * kBlock + tid] = adj * da;
-            if (code != fCompl) tap[b * kBlock + tid] = adj * db;
-          }
-          // primitives: d s / d q times the seed, reduced per slot over the warp
-          for (int pos = 0; pos < nops; ++pos) {
-            const FoldOp fo = fold_op(sops[pos]);
-            if (fo.code != fPush) continue;
-            const int lf = fo.a;
-            const int fl = lt[lf].d.w;
-            if (!(fl & tACT)) continue;
-            const float a = zs * tap[pos * kBlock + tid];
+          const int4 pc = make_int4(X0 + x, Y0 + y, Z0 + z, c);
+          const SampleOff so{(c << g.lx) + x, (c << g.ly) + y, (c << g.lz) + z,
+                             (((c << g.ly) + y) << g.lx) + x};
+          vjp_tape<kLogic>(desc, nops, tab, so, sl, pc, g, J.auxf, J.auxd, tap);
+          const Cell cc{pc.x, pc.y, pc.z, g.off[c][0], g.off[c][1], g.off[c][2]};
+          const TileLoc q{x, y, z, c, TX, TY, TZ};
+          // primitives: d s / d q times the seed
+          for (int k = 0; k < ndl; ++k) {
+            const int e = dl[k];
+            const int pos = e & 255, lf = e >> 8;
+            const float a = zs * tap[pos * kBlock];
             if (__ballot_sync(0xffffffffu, a != 0.f) == 0u) continue;
+            const int fl = lt[lf].d.w;
             float* la = wacc + sbase[lf];
             float* lc = wcmp + sbase[lf];
+            const KeySink ks{tcol + sbase[lf] * kBlock + tid, la, lc, lane, pt};
             if ((fl & (tOK | tBOX)) == (tOK | tBOX)) {
-              box_tab_reduce(lt[lf], q, tab, a, g, la, lc, lane);
+              box_tab_reduce(lt[lf], q, tab, a, g, ks);
+              continue;
+            }
+            const int kind = sl[lf].kind;
+            if (kind == kBox) {
+              box_direct_reduce(sl[lf], lt[lf], cc, a, g, ks);
+              continue;
+            }
+            if (kind == kCircle) {
+              circle_reduce(sl[lf], lt[lf], cc, a, g, ks);
               continue;
             }
             int n = 0;
             if (a != 0.f)
               n = leaf_pairs(sl[lf], cc, a, g, J.act, J.actc, J.auxf, J.auxd, pk + tid, pv + tid);
             warp_accumulate(n, 0, pk + tid, pv + tid, la, lc, lane);
-            if (sl[lf].kind == kPolygon)
+            if (kind == kPolygon)
               poly_accumulate(sl[lf], cc, a, g, J.act, J.actc, J.auxd, la, lc, lane);
           }
         }
       };
-      if (nops > kSmemOps) samples(std::true_type{});
-      else samples(std::false_type{});
+      using kS = std::false_type;
+      using kG = std::true_type;
+      using kP = std::integral_constant<int, 0>;
+      using kC = std::integral_constant<int, 1>;
+      if (nops > kSmemOps) {
+        if (g.logic == 0) samples(kG{}, kP{}); else samples(kG{}, kC{});
+      } else {
+        if (g.logic == 0) samples(kS{}, kP{}); else samples(kS{}, kC{});
+      }
     }  // chunks of active samples
     __syncthreads();
+    if (pt) {  // each slot's column sum, one warp per slot, fixed order
+      for (int s2 = warp; s2 < nslot; s2 += kWarps) {
+        const float* c = tcol + s2 * kBlock;
+        float v = ((c[lane] + c[lane + 32]) + c[lane + 64]) + c[lane + 96];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) tcol[s2 * kBlock] = v;  // only this warp reads slot s2's column
+      }
+      __syncthreads();
+    }
     for (int s2 = tid; s2 < nslot; s2 += kBlock) {
       int lf = 0;
       while (lf + 1 < nleaf && sbase[lf + 1] <= s2) ++lf;
       const int qa = s2 - sbase[lf];
-      float tot = 0.f;
-      for (int w = 0; w < kWarps; ++w) tot += tp.acc[w * nslot + s2] + tp.cmp[w * nslot + s2];
+      float tot = pt ? tcol[s2 * kBlock] : 0.f;
+      for (int w = 0; w < kWarps; ++w) tot += racc[w * nslot + s2] + rcmp[w * nslot + s2];
       const PrimRec& R = sl[lf];
       if (tx >= R.pb[0] && tx < R.pb[1] && ty >= R.pb[2] && ty < R.pb[3] && tz >= R.pb[4] &&
           tz < R.pb[5]) {
@@ -1697,30 +1973,29 @@ __global__ void __launch_bounds__(256) k_dense_final(DenseArgs a) {
   }
 }
 
-// One warp per parameter: fixed-order FP64 sums of its (primitive, slot)
-// partials over the derivative tile boxes.
-__global__ void k_finalize(const Job* __restrict__ jobs, int njobs, int nparams) {
-  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (wid >= nparams) return;
+// One block per parameter: its (primitive, slot) partials over the derivative
+// tile boxes, in a fixed order -- each warp takes every fourth partial of each
+// reference (compensated fp32 per lane), FP64 across lanes, references and
+// the four warps.
+__global__ void __launch_bounds__(128) k_finalize(const Job* __restrict__ jobs, int njobs, int nparams) {
+  __shared__ double wsum[4];
+  const int wid = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const Job& J = jobs[job_by_param(jobs, njobs, wid)];
   const int k = wid - J.param_base;
   double total = 0.0;
   for (int r = J.ref_off[k]; r < J.ref_off[k + 1]; ++r) {
     const PrimRec& P = J.prims[J.ref_prim[r]];
-    const float* src = J.partial + P.part_off + (size_t)J.ref_qa[r] * P.npb;
-    double s = 0.0, c = 0.0;
-    for (int t = lane; t < P.npb; t += 32) {
-      const double v = src[t];
-      const double u = s + v;
-      c += (fabs(s) >= fabs(v)) ? (s - u) + v : (v - u) + s;
-      s = u;
-    }
-    s += c;
+    const float* __restrict__ src = J.partial + P.part_off + (size_t)J.ref_qa[r] * P.npb;
+    float s = 0.f, c = 0.f;
+    for (int t = threadIdx.x; t < P.npb; t += 128) neumaier(s, c, __ldg(src + t));
+    double v = (double)s + (double)c;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    total += J.ref_coeff[r] * s;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    total += J.ref_coeff[r] * v;
   }
-  if (lane == 0) J.grad[k] = (float)total;
+  if (lane == 0) wsum[warp] = total;
+  __syncthreads();
+  if (threadIdx.x == 0) J.grad[k] = (float)(((wsum[0] + wsum[1]) + wsum[2]) + wsum[3]);
 }
 
 }  // namespace
@@ -1809,8 +2084,7 @@ cudaError_t launch_dense(const DenseArgs& a, int sms, cudaStream_t s) {
 
 cudaError_t launch_finalize(const Job* jobs, const JobTotals& t, cudaStream_t s) {
   if (t.params <= 0) return cudaSuccess;
-  const int blocks = (t.params * 32 + 127) / 128;
-  k_finalize<<<blocks, 128, 0, s>>>(jobs, t.njobs, t.params);
+  k_finalize<<<t.params, 128, 0, s>>>(jobs, t.njobs, t.params);
   return cudaGetLastError();
 }
 
