@@ -1136,6 +1136,58 @@ __global__ void __launch_bounds__(256) k_fill(const Job* __restrict__ jobs, int 
   }
 }
 
+// ---- axis collapse -------------------------------------------------------------
+// Whether a band tile's folded program has the same value at every y of the
+// tile (okY), and at every z (okZ): every leaf is tabled and its y (z)
+// factors are bitwise equal along the axis -- for the VJP also the derivative
+// entries, and a parameter-driven in-plane leaf (whose derivatives are not
+// tabled) blocks the y collapse.  Then the build evaluates one y (z) and
+// writes it to all, and the VJP sums the seeds along the axis first (the
+// projection to the grid comes last, Sec. 3; extruded and planar designs
+// are uniform along whole axes, Sec. 3.1).  All threads; per-thread flags.
+__device__ __forceinline__ void uniform_axes(const LeafTab* lt, int nleaf, const GridDev& g,
+                                             const float* tab, bool derivs, int tid, bool& okY,
+                                             bool& okZ) {
+  const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
+  okY = true;
+  okZ = true;
+  for (int l = 0; l < nleaf; ++l) {  // axes that cannot collapse are not checked
+    const int f = lt[l].d.w;
+    if (!(f & tOK)) { okY = false; okZ = false; return; }  // same for every thread
+    if (derivs && !(f & tBOX) && (f & tACT)) okY = false;
+  }
+  for (int l = 0; l < nleaf; ++l) {
+    const int4 v = lt[l].v, d = lt[l].d;
+    const bool box = (d.w & tBOX) != 0;
+    for (int e = tid; e < C * TZ; e += kBlock) {
+      const int c = e / TZ, z = e - c * TZ;
+      if (z == 0) continue;
+      okZ &= tab[v.z + c * TZ + z] == tab[v.z + c * TZ];
+      if (derivs && d.z >= 0) {
+        okZ &= tab[d.z + 2 * c * TZ + z] == tab[d.z + 2 * c * TZ];
+        okZ &= tab[d.z + (2 * c + 1) * TZ + z] == tab[d.z + (2 * c + 1) * TZ];
+      }
+    }
+    if (box) {
+      for (int e = tid; e < C * TY; e += kBlock) {
+        const int c = e / TY, y = e - c * TY;
+        if (y == 0) continue;
+        okY &= tab[v.y + c * TY + y] == tab[v.y + c * TY];
+        if (derivs) {
+          okY &= tab[d.y + 2 * c * TY + y] == tab[d.y + 2 * c * TY];
+          okY &= tab[d.y + (2 * c + 1) * TY + y] == tab[d.y + (2 * c + 1) * TY];
+        }
+      }
+    } else if (okY || !derivs) {
+      for (int e = tid; e < C * TX * TY; e += kBlock) {
+        const int c = e / (TX * TY), r = e - c * TX * TY, y = r / TX, x = r - y * TX;
+        if (y == 0) continue;
+        okY &= tab[v.w + (c * TY + y) * TX + x] == tab[v.w + c * TY * TX + x];
+      }
+    }
+  }
+}
+
 // ---- forward-only evaluation (build) ----------------------------------------
 // The folded program is postfix: every op takes the top two values of a
 // stack (the complement the top one) and pushes one, so the build, which
@@ -1299,59 +1351,71 @@ __global__ void __launch_bounds__(kBlock) k_build(const Job* __restrict__ jobs, 
     tables_fill(tp.sl, nleaf, g, tp.lt, false, tx << g.lx, ty << g.ly, tz << g.lz, tp.tab, tid,
                 J.auxf, J.auxd);
     __syncthreads();
-    const int lxy = g.lx + g.ly, lxyz = lxy + g.lz;
+    bool okY, okZ;
+    uniform_axes(tp.lt, nleaf, g, tp.tab, false, tid, okY, okZ);
+    const bool uy = __syncthreads_and(okY);
+    const bool uz = __syncthreads_and(okZ);
+    // evaluated lattice: x, then y (one row if y collapses), z, component
+    const int lyr = uy ? 0 : g.ly, lzr = uz ? 0 : g.lz;
+    const int lxy = g.lx + lyr, lxyz = lxy + lzr;
     const int ncc = g.C << lxyz;
-    const int TXm = (1 << g.lx) - 1, TYm = (1 << g.ly) - 1, TZm = (1 << g.lz) - 1;
+    const int TXm = (1 << g.lx) - 1, TYm = (1 << lyr) - 1, TZm = (1 << lzr) - 1;
+    const int X0 = tx << g.lx, Y0 = ty << g.ly, Z0 = tz << g.lz;
+    // the y and z each evaluated sample stands for (in the grid)
+    const int ny_r = uy ? min(1 << g.ly, g.ny - Y0) : 1, nz_r = uz ? min(1 << g.lz, g.nz - Z0) : 1;
     const size_t plane = (size_t)g.nx * g.ny * g.nz;
     float* __restrict__ fill = J.fill;
     float* __restrict__ eps = J.eps;
+    auto store = [&](int x, int y, int z, int c, float v) {
+      if (X0 + x >= g.nx || Y0 + y >= g.ny || Z0 + z >= g.nz) return;
+      const float e = g.eps_bg + g.deps * v;
+      if (!uy && !uz) {  // uniform over the block
+        const size_t o = (size_t)c * plane + ((size_t)(Z0 + z) * g.ny + (Y0 + y)) * g.nx + (X0 + x);
+        if (fill) fill[o] = v;
+        eps[o] = e;
+        return;
+      }
+      for (int zz = 0; zz < nz_r; ++zz)
+        for (int yy = 0; yy < ny_r; ++yy) {
+          const size_t o = (size_t)c * plane + ((size_t)(Z0 + z + zz) * g.ny + (Y0 + y + yy)) * g.nx +
+                           (X0 + x);
+          if (fill) fill[o] = v;
+          eps[o] = e;
+        }
+    };
     if (sdepth[0] <= kRegStack) {
-      const int half = ncc >> 1;  // a multiple of 64
+      const int half = ncc >> 1;  // even: TX >= 32
       for (int l = tid; l < half; l += kBlock) {
         SampleOff o[2];
         int4 pc[2];
-        size_t off[2];
-        bool in[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int m = l + h * half;
           const int x = m & TXm, y = (m >> g.lx) & TYm, z = (m >> lxy) & TZm, c = m >> lxyz;
-          const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
-          in[h] = gi < g.nx && gj < g.ny && gk < g.nz;
           o[h] = SampleOff{(c << g.lx) + x, (c << g.ly) + y, (c << g.lz) + z,
                            (((c << g.ly) + y) << g.lx) + x};
-          pc[h] = make_int4(gi, gj, gk, c);
-          off[h] = (size_t)c * plane + ((size_t)gk * g.ny + gj) * g.nx + gi;
+          pc[h] = make_int4(X0 + x, Y0 + y, Z0 + z, c);
         }
         float v0, v1;
         if (g.logic == 0)
           eval_stack2<0>(desc, nops, tp.tab, tp.sl, o[0], o[1], pc[0], pc[1], g, J.auxf, J.auxd, v0, v1);
         else
           eval_stack2<1>(desc, nops, tp.tab, tp.sl, o[0], o[1], pc[0], pc[1], g, J.auxf, J.auxd, v0, v1);
-        if (in[0]) {
-          if (fill) fill[off[0]] = v0;
-          eps[off[0]] = g.eps_bg + g.deps * v0;
-        }
-        if (in[1]) {
-          if (fill) fill[off[1]] = v1;
-          eps[off[1]] = g.eps_bg + g.deps * v1;
-        }
+        store(pc[0].x - X0, pc[0].y - Y0, pc[0].z - Z0, pc[0].w, v0);
+        store(pc[1].x - X0, pc[1].y - Y0, pc[1].z - Z0, pc[1].w, v1);
       }
       continue;
     }
     for (int l = tid; l < ncc; l += kBlock) {
       const int x = l & TXm, y = (l >> g.lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
-      const int gi = (tx << g.lx) + x, gj = (ty << g.ly) + y, gk = (tz << g.lz) + z;
-      if (gi >= g.nx || gj >= g.ny || gk >= g.nz) continue;
+      if (X0 + x >= g.nx || Y0 + y >= g.ny || Z0 + z >= g.nz) continue;
       const SampleOff so{(c << g.lx) + x, (c << g.ly) + y, (c << g.lz) + z,
                          (((c << g.ly) + y) << g.lx) + x};
-      const int4 pc = make_int4(gi, gj, gk, c);
+      const int4 pc = make_int4(X0 + x, Y0 + y, Z0 + z, c);
       const float v = g.logic == 0
           ? eval_stack_smem<0>(desc, nops, tp.tab, tp.sl, so, pc, g, J.auxf, J.auxd, stk + tid)
           : eval_stack_smem<1>(desc, nops, tp.tab, tp.sl, so, pc, g, J.auxf, J.auxd, stk + tid);
-      const size_t o = (size_t)c * plane + ((size_t)gk * g.ny + gj) * g.nx + gi;
-      if (fill) fill[o] = v;
-      eps[o] = g.eps_bg + g.deps * v;
+      store(x, y, z, c, v);
     }
   }
 }
@@ -1584,6 +1648,38 @@ __device__ __forceinline__ void vjp_tape(const int4* desc, int nops, const float
 }
 
 constexpr int kSeedChunk = 512;  // active samples whose seeds are staged at once
+
+// Seeds of active samples [c0, c1) of a tile: deps Re(w E_adj E_fwd) (Eq. 1,
+// no conjugate) or deps G, summed over the ny_r x nz_r positions an evaluated
+// sample stands for.  geo = (X0, Y0, Z0, lx | lyr << 8 | lzr << 16).  Once
+// per chunk, out of line: its values stay out of the sample loop's registers.
+__device__ __noinline__ void tile_seeds(const Job* J, const uint16_t* slist, float* zsb, int c0,
+                                        int c1, int4 geo, int ny_r, int nz_r) {
+  const GridDev& g = J->g;
+  const VjpArgs& va = J->va;
+  const int lx = geo.w & 255, lyr = (geo.w >> 8) & 255, lzr = geo.w >> 16;
+  const int TXm = (1 << lx) - 1, TYm = (1 << lyr) - 1, TZm = (1 << lzr) - 1;
+  const int lxy = lx + lyr, lxyz = lxy + lzr;
+  const size_t plane = (size_t)g.nx * g.ny * g.nz;
+#pragma unroll 4
+  for (int i = c0 + (int)threadIdx.x; i < c1; i += kBlock) {  // independent loads in flight
+    const int l = slist[i];
+    const int x = l & TXm, y = (l >> lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
+    float zs = 0.f;
+    for (int zz = 0; zz < nz_r; ++zz)
+      for (int yy = 0; yy < ny_r; ++yy) {
+        const size_t o = ((size_t)(geo.z + z + zz) * g.ny + (geo.y + y + yy)) * g.nx + (geo.x + x);
+        if (va.G) {
+          zs += __ldg(va.G + (size_t)c * plane + o);
+        } else {
+          const float2 f = __ldg(va.ef[c] + o), a = __ldg(va.ea[c] + o);
+          const float pr = f.x * a.x - f.y * a.y, pi = f.x * a.y + f.y * a.x;
+          zs += va.w[c].x * pr - va.w[c].y * pi;
+        }
+      }
+    zsb[i - c0] = zs * g.deps;  // eps = eps_bg + deps fill
+  }
+}
 // a tile's x-rows (C * TY * TZ <= 3 * 1024 / 32) fit the seed buffer they alias
 static_assert(3 * kMaxTileCells / 32 <= kSeedChunk, "row offsets alias the seed buffer");
 constexpr size_t kVjpFixed = (size_t)kSmemOps * kBlock * 4 + (size_t)kVjpPool * 4 +
@@ -1622,7 +1718,6 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
     const TileProg* P = J.progs + t;
     const int nops = P->nops, nleaf = P->nleaf, nslot = P->nslot;
     const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
-    const VjpArgs& va = J.va;
     if (nslot > kMaxSlots) {  // flagged by the binner too; uniform over the block
       if (tid == 0) atomicOr(err, eSlotOverflow);
       continue;
@@ -1696,15 +1791,22 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
                 J.auxd);
     __syncthreads();
     activity_axes(lt, nleaf, g, tab, act1, tid);
-    __syncthreads();
+    bool okY, okZ;
+    uniform_axes(lt, nleaf, g, tab, true, tid, okY, okZ);
+    const bool uy = __syncthreads_and(okY);
+    const bool uz = __syncthreads_and(okZ);
     float* wacc = racc + warp * nslot;
     float* wcmp = rcmp + warp * nslot;
-    const int lxy = g.lx + g.ly, lxyz = lxy + g.lz;
     const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
-    const int TXm = TX - 1, TYm = TY - 1, TZm = TZ - 1;
-    const size_t plane = (size_t)g.nx * g.ny * g.nz;
+    // evaluated lattice (x, y, z, c) with y and/or z collapsed to one
+    // position; each evaluated sample's seed sums the positions it stands for
+    const int lyr = uy ? 0 : g.ly, lzr = uz ? 0 : g.lz;
+    const int TYr = 1 << lyr, TZr = 1 << lzr;
+    const int lxy = g.lx + lyr, lxyz = lxy + lzr;
+    const int TXm = TX - 1, TYm = TYr - 1, TZm = TZr - 1;
     const int X0 = tx << g.lx, Y0 = ty << g.ly, Z0 = tz << g.lz;
-    const int nrows = C * TY * TZ;
+    const int ny_r = uy ? min(TY, g.ny - Y0) : 1, nz_r = uz ? min(TZ, g.nz - Z0) : 1;
+    const int nrows = C * TYr * TZr;
     const int nw = TX >> 5;  // 32-bit words per x-row
     // Active samples, per x-row (c, z, y): the whole row when the sample's y
     // or z moves a face (or a non-box leaf drives a parameter), else the
@@ -1730,7 +1832,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
         const int r = r0 + lane;
         int kind = 0, cnt = 0;
         if (r < nrows) {
-          const int c = r / (TY * TZ), rem = r - c * TY * TZ, z = rem / TY, y = rem - z * TY;
+          const int c = r / (TYr * TZr), rem = r - c * TYr * TZr, z = rem / TYr, y = rem - z * TYr;
           if (Y0 + y < g.ny && Z0 + z < g.nz) {
             const bool full = all || act1[C * TX + c * TY + y] || act1[C * (TX + TY) + c * TZ + z];
             kind = full ? 1 : 2;
@@ -1755,8 +1857,8 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
       const int kind = e & 3;
       if (!kind) continue;
       int off = e >> 2;
-      const int c = r / (TY * TZ), rem = r - c * TY * TZ, z = rem / TY, y = rem - z * TY;
-      const int lrow = ((c * TZ + z) * TY + y) << g.lx;
+      const int c = r / (TYr * TZr), rem = r - c * TYr * TZr, z = rem / TYr, y = rem - z * TYr;
+      const int lrow = ((c * TZr + z) * TYr + y) << g.lx;
       for (int h = 0; h < nw; ++h) {
         const unsigned m = (unsigned)(kind == 1 ? misc[10 + h] : misc[4 + 2 * c + h]);
         if ((m >> lane) & 1u) slist[off + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(lrow + h * 32 + lane);
@@ -1766,28 +1868,11 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
     __syncthreads();
     const int nact_cells = misc[0];
     const int ndl = misc[2];
-    if (tid == 0) atomicAdd(&J.counters[3], nact_cells);
+    if (tid == 0) atomicAdd(&J.counters[3], nact_cells * ny_r * nz_r);  // grid samples
     for (int c0 = 0; c0 < nact_cells; c0 += kSeedChunk) {
       const int c1 = min(nact_cells, c0 + kSeedChunk);
-      // stream the chunk's fields: independent loads, many in flight
-#pragma unroll
-      for (int i0 = c0; i0 < c0 + kSeedChunk; i0 += kBlock) {
-        const int i = i0 + tid;
-        if (i < c1) {
-          const int l = slist[i];
-          const int x = l & TXm, y = (l >> g.lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
-          const size_t o = ((size_t)(Z0 + z) * g.ny + (Y0 + y)) * g.nx + (X0 + x);
-          float zs;
-          if (va.G) {
-            zs = __ldg(va.G + (size_t)c * plane + o);
-          } else {
-            const float2 f = __ldg(va.ef[c] + o), a = __ldg(va.ea[c] + o);
-            const float pr = f.x * a.x - f.y * a.y, pi = f.x * a.y + f.y * a.x;
-            zs = va.w[c].x * pr - va.w[c].y * pi;  // Re(w E_adj E), no conjugate (Eq. 1)
-          }
-          zsb[i - c0] = zs * g.deps;  // eps = eps_bg + deps fill
-        }
-      }
+      tile_seeds(&J, slist, zsb, c0, c1, make_int4(X0, Y0, Z0, g.lx | (lyr << 8) | (lzr << 16)),
+                 ny_r, nz_r);
       // The tape: shared memory for short programs, else this block's slice of
       // the global tape; the logic family is a template parameter.  The
       // variants are separate instantiations, so the shared one keeps
@@ -1805,7 +1890,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
           const float zs = live ? zsb[i - c0] : 0.f;
           const int4 pc = make_int4(X0 + x, Y0 + y, Z0 + z, c);
           const SampleOff so{(c << g.lx) + x, (c << g.ly) + y, (c << g.lz) + z,
-                             (((c << g.ly) + y) << g.lx) + x};
+                             (((c << g.ly) + y) << g.lx) + x};  // tables keep full TY, TZ
           vjp_tape<kLogic>(desc, nops, tab, so, sl, pc, g, J.auxf, J.auxd, tap);
           const Cell cc{pc.x, pc.y, pc.z, g.off[c][0], g.off[c][1], g.off[c][2]};
           const TileLoc q{x, y, z, c, TX, TY, TZ};
