@@ -151,7 +151,8 @@ struct adg_design {
   TileProg* d_progs = nullptr;
   unsigned char* d_tclass = nullptr;
   int* d_list = nullptr;
-  int* d_counters = nullptr;
+  int* d_counters = nullptr;  // two sets of 4; the binning alternates between them
+  int gen = 0;                // the set of the last binning
   float* d_partial = nullptr;
   size_t partial_cap = 0;
   Job* d_job = nullptr;  // the one-job table of single-design calls
@@ -332,7 +333,8 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_progs, sizeof(TileProg) * (size_t)d->g.T);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_tclass, (size_t)d->g.T);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_list, sizeof(int) * (size_t)d->g.T);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_counters, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_counters, sizeof(int) * 8);
+  if (e == cudaSuccess) e = cudaMemset(d->d_counters, 0, sizeof(int) * 8);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_job, sizeof(Job));
   if (e != cudaSuccess) {
     free_design(d);
@@ -388,6 +390,7 @@ adg_status ensure_records(adg_design* d, const double* h_params, cudaStream_t s,
                        cudaMemcpyHostToDevice, s));
   d->last_params.assign(h_params, h_params + d->n_params);
   d->bins_valid = true;
+  d->gen ^= 1;  // this binning counts into the other set (cleared by the last one)
   *rebin = true;
   return ADG_OK;
 }
@@ -420,7 +423,8 @@ Job design_job(adg_design* d) {
   J.progs = d->d_progs;
   J.tclass = d->d_tclass;
   J.list = d->d_list;
-  J.counters = d->d_counters;
+  J.counters = d->d_counters + 4 * d->gen;
+  J.counters_next = d->d_counters + 4 * (d->gen ^ 1);
   J.partial = d->d_partial;
   J.partial_n = (long long)d->part_total;
   J.nparam = d->n_params;
@@ -430,7 +434,7 @@ Job design_job(adg_design* d) {
 // Enqueue prepare -> bin -> build / VJP -> finalize for a job table.
 adg_status run_jobs(adg_ctx* ctx, const Job* d_jobs, const JobTotals& t, bool any_bin,
                     bool any_build, bool any_grad, int max_tiles, cudaStream_t s) {
-  if (any_bin || any_grad) {
+  if (any_grad) {  // partials and the active-sample counter
     ProfScope ps(ctx, ADG_K_PREPARE, s);
     CU(launch_prepare(d_jobs, t, s));
   }
@@ -438,11 +442,7 @@ adg_status run_jobs(adg_ctx* ctx, const Job* d_jobs, const JobTotals& t, bool an
     ProfScope ps(ctx, ADG_K_BIN, s);
     CU(launch_bin(d_jobs, t, ctx->d_err, s));
   }
-  if (any_build) {
-    {
-      ProfScope ps(ctx, ADG_K_FILL, s);
-      CU(launch_fill(d_jobs, t, s));
-    }
+  if (any_build) {  // constant-tile fill and band tiles in one launch
     ProfScope ps(ctx, ADG_K_BUILD, s);
     CU(launch_build(d_jobs, t, ctx->sms, s));
   }
@@ -612,6 +612,7 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
     adg_status st = prepare_prims(d, items[i].h_params);
     if (st != ADG_OK) return st;
     d->bins_valid = false;  // the batch re-bins this design with its own records
+    d->gen ^= 1;            // into the other counter set (cleared by the last binning)
     if (items[i].ops & (ADG_BATCH_GRAD | ADG_BATCH_GRAD_REAL)) {
       st = ensure_partials(d, s);
       if (st != ADG_OK) return st;
@@ -802,7 +803,7 @@ extern "C" adg_status adg_design_stats(adg_ctx* ctx, adg_design* d, void* stream
   CU(cudaSetDevice(ctx->device));
   CU(cudaStreamSynchronize((cudaStream_t)stream));
   int c[4] = {0, 0, 0, 0};
-  CU(cudaMemcpy(c, d->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(c, d->d_counters + 4 * d->gen, sizeof(c), cudaMemcpyDeviceToHost));
   out->tiles = d->g.T;
   out->program_tiles = c[0];
   out->max_ops = c[1];

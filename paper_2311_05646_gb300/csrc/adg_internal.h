@@ -146,7 +146,8 @@ struct Job {
   TileProg* progs;
   unsigned char* tclass;  // per tile: 0 / 1 constant fill, 2 band (program) tile
   int* list;
-  int* counters;
+  int* counters;       // [band tiles, longest program, band cells, active samples]
+  int* counters_next;  // the other set: zeroed by this binning for the next one
   // outputs and inputs of the operations
   float* fill;
   float* eps;
@@ -162,11 +163,11 @@ struct Job {
   int do_bin, do_build, do_grad;
 };
 
-constexpr int kFillRows = 8;  // x-rows per block of the streaming fill
+constexpr int kFillRows = 8;  // x-rows per work unit of the streaming fill
 
 struct JobTotals {
   int njobs;
-  int fill_blocks;       // sum over build jobs of ceil(C nz ny / kFillRows)
+  int fill_blocks;       // fill work units: sum over build jobs of ceil(C nz ny / kFillRows)
   int bin_blocks;        // sum over binned jobs of ceil(T / 128)
   int tiles_padded;      // tile_base of one past the last job
   int params;            // sum of nparam over gradient jobs
@@ -177,7 +178,6 @@ constexpr int kMaxJobs = 1024;  // jobs in one table (one batch)
 
 cudaError_t launch_prepare(const Job* jobs, const JobTotals& t, cudaStream_t s);
 cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s);
-cudaError_t launch_fill(const Job* jobs, const JobTotals& t, cudaStream_t s);
 cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s);
 // gtape: kTapeBlockFloats floats per block for gtape_blocks blocks; the grid
 // never exceeds gtape_blocks.

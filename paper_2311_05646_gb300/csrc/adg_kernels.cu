@@ -583,9 +583,7 @@ __global__ void k_prepare(const Job* __restrict__ jobs, int njobs) {
   const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = i0; i < njobs; i += stride) {
-    if (jobs[i].do_bin)
-      for (int k = 0; k < 3; ++k) jobs[i].counters[k] = 0;
-    if (jobs[i].do_bin || jobs[i].do_grad) jobs[i].counters[3] = 0;  // active VJP samples
+    if (jobs[i].do_grad) jobs[i].counters[3] = 0;  // active VJP samples
   }
   for (long long i = i0; i < npart; i += stride) {
     const Job& J = jobs[job_by_partial(jobs, njobs, i)];
@@ -772,6 +770,9 @@ __global__ void __launch_bounds__(128) k_bin(const Job* __restrict__ jobs, int n
   const int tid = threadIdx.x;
   const Job& J = jobs[job_by_tile(jobs, njobs, blockIdx.x * 128)];
   if (!J.do_bin) return;  // uniform over the block
+  // this binning counts into J.counters (zeroed by the previous one) and
+  // clears the other set for the next
+  if (tid < 4 && blockIdx.x * 128 == J.tile_base) J.counters_next[tid] = 0;
   const bool staged = J.g.nprims <= kPrimSmem;    // primitive records in shared memory
   const bool cstaged = J.g.nchain <= kChainSmem;  // the chain too (then compacted below)
   if (cstaged)
@@ -1096,11 +1097,13 @@ __device__ __forceinline__ int job_of(const int* spre, int njobs, int i) {
   return lo;
 }
 
-// Streaming fill of every constant tile: fill = 0 or 1, eps = eps_bg or
-// eps_fg, 16-byte stores along x rows, one warp per row (a store instruction
-// covers 512 contiguous bytes).  Band tiles are left to k_build.
-__global__ void __launch_bounds__(256) k_fill(const Job* __restrict__ jobs, int njobs) {
-  const Job& J = jobs[job_by_rows(jobs, njobs, blockIdx.x)];
+// Streaming fill of the constant tiles of one group of kFillRows x-rows: fill
+// = 0 or 1, eps = eps_bg or eps_fg, 16-byte stores, one warp per row (a store
+// instruction covers 512 contiguous bytes); band tiles are left to the band
+// evaluation.  All threads of a kBlock-thread block.
+__device__ __forceinline__ void fill_rows(const Job* __restrict__ jobs, int njobs, int unit,
+                                          int tid) {
+  const Job& J = jobs[job_by_rows(jobs, njobs, unit)];
   if (!J.do_build) return;
   const int nx = J.g.nx, ny = J.g.ny, nz = J.g.nz;
   const int lx = J.g.lx, ly = J.g.ly, lz = J.g.lz, ntx = J.g.ntx, nty = J.g.nty;
@@ -1110,28 +1113,30 @@ __global__ void __launch_bounds__(256) k_fill(const Job* __restrict__ jobs, int 
   float* __restrict__ eps = J.eps;
   const bool vec = (nx & 3) == 0 &&
                    ((reinterpret_cast<uintptr_t>(eps) | reinterpret_cast<uintptr_t>(fill)) & 15) == 0;
-  const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;  // 8 warps, 8 rows
-  const int row = (blockIdx.x - J.row_base) * kFillRows + wrow;
-  if (row >= rows) return;
-  const int j = row % ny, k = (row / ny) % nz;
-  const size_t base = (size_t)row * nx;
-  const unsigned char* __restrict__ tcl = J.tclass + ((k >> lz) * nty + (j >> ly)) * ntx;
-  if (vec) {
-    float4* f4 = reinterpret_cast<float4*>(fill + base);
-    float4* e4 = reinterpret_cast<float4*>(eps + base);
-    for (int v = lane; v < (nx >> 2); v += 32) {
-      const int cls = __ldg(tcl + ((4 * v) >> lx));
-      if (cls == 2) continue;
-      const float f = cls ? 1.f : 0.f, e = cls ? e1 : e0;
-      if (fill) f4[v] = make_float4(f, f, f, f);
-      e4[v] = make_float4(e, e, e, e);
-    }
-  } else {
-    for (int i = lane; i < nx; i += 32) {
-      const int cls = __ldg(tcl + (i >> lx));
-      if (cls == 2) continue;
-      if (fill) fill[base + i] = cls ? 1.f : 0.f;
-      eps[base + i] = cls ? e1 : e0;
+  const int lane = tid & 31;
+  for (int wr = tid >> 5; wr < kFillRows; wr += kWarps) {
+    const int row = (unit - J.row_base) * kFillRows + wr;
+    if (row >= rows) break;
+    const int j = row % ny, k = (row / ny) % nz;
+    const size_t base = (size_t)row * nx;
+    const unsigned char* __restrict__ tcl = J.tclass + ((k >> lz) * nty + (j >> ly)) * ntx;
+    if (vec) {
+      float4* f4 = reinterpret_cast<float4*>(fill + base);
+      float4* e4 = reinterpret_cast<float4*>(eps + base);
+      for (int v = lane; v < (nx >> 2); v += 32) {
+        const int cls = __ldg(tcl + ((4 * v) >> lx));
+        if (cls == 2) continue;
+        const float f = cls ? 1.f : 0.f, e = cls ? e1 : e0;
+        if (fill) f4[v] = make_float4(f, f, f, f);
+        e4[v] = make_float4(e, e, e, e);
+      }
+    } else {
+      for (int i = lane; i < nx; i += 32) {
+        const int cls = __ldg(tcl + (i >> lx));
+        if (cls == 2) continue;
+        if (fill) fill[base + i] = cls ? 1.f : 0.f;
+        eps[base + i] = cls ? e1 : e0;
+      }
     }
   }
 }
@@ -1314,23 +1319,16 @@ __device__ __forceinline__ void eval_stack2(const int4* desc, int nops, const fl
   r1 = b0;
 }
 
-// Band tiles of the build: persistent over the binner's compacted list, the
-// tile's primitives staged with their factor tables, the folded program run
-// at every sample of the tile (two samples per thread, register stack; the
-// tape evaluator for programs deeper than the register stack).
-__global__ void __launch_bounds__(kBlock) k_build(const Job* __restrict__ jobs, int njobs) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// One band tile of the build (all threads of the block).
+__device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, int njobs,
+                                                const int* spre, int gi_, unsigned char* smem) {
   float* stk = reinterpret_cast<float*>(smem);  // stack of the deep-program fallback
   float* pool = stk + kMaxDepth * kBlock;
   int4* desc = reinterpret_cast<int4*>(pool + kBuildPool);
   uint16_t* sops = reinterpret_cast<uint16_t*>(desc + kMaxOps);
   int* sdepth = reinterpret_cast<int*>(sops + kMaxOps);
-  int* spre = sdepth + 4;  // prefix of band-tile counts
   const int tid = threadIdx.x;
-  if (tid == 0) job_prefix(jobs, njobs, false, spre);
-  __syncthreads();
-  const int total = spre[njobs];
-  for (int gi_ = blockIdx.x; gi_ < total; gi_ += gridDim.x) {
+  {
     const int jb = job_of(spre, njobs, gi_);
     const Job& J = jobs[jb];
     const GridDev& g = J.g;
@@ -1404,7 +1402,7 @@ __global__ void __launch_bounds__(kBlock) k_build(const Job* __restrict__ jobs, 
         store(pc[0].x - X0, pc[0].y - Y0, pc[0].z - Z0, pc[0].w, v0);
         store(pc[1].x - X0, pc[1].y - Y0, pc[1].z - Z0, pc[1].w, v1);
       }
-      continue;
+      return;
     }
     for (int l = tid; l < ncc; l += kBlock) {
       const int x = l & TXm, y = (l >> g.lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
@@ -1417,6 +1415,33 @@ __global__ void __launch_bounds__(kBlock) k_build(const Job* __restrict__ jobs, 
           : eval_stack_smem<1>(desc, nops, tp.tab, tp.sl, so, pc, g, J.auxf, J.auxd, stk + tid);
       store(x, y, z, c, v);
     }
+  }
+}
+
+// The build (constant and band tiles of every build job), persistent: band
+// tiles from the binner's compacted list -- the tile's primitives staged with
+// their factor tables, the folded program run at every sample (two samples
+// per thread, register stack; a shared-memory stack for deeper programs) --
+// and the streaming fill of the constant tiles.
+__global__ void __launch_bounds__(kBlock, 6) k_build(const Job* __restrict__ jobs, int njobs,
+                                                   int nfill) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  // layout: deep-program stack, pool, descriptors, ops, depth, job prefix
+  int* spre = reinterpret_cast<int*>(smem + (size_t)kMaxDepth * kBlock * 4 + (size_t)kBuildPool * 4 +
+                                     kMaxOps * 16 + kMaxOps * 2) + 4;
+  const int tid = threadIdx.x;
+  if (tid == 0) job_prefix(jobs, njobs, false, spre);
+  __syncthreads();
+  const int total = spre[njobs];
+  // Band tiles (issue-bound) and groups of constant-tile rows (store-bound)
+  // interleaved in every block, so that each SM holds both kinds of work.
+  const int G = gridDim.x;
+  const int per = total > 0 ? max(1, (nfill + total - 1) / total) : nfill;
+  int gi_ = blockIdx.x, fu = blockIdx.x;
+  while (gi_ < total || fu < nfill) {
+    if (gi_ < total) build_band_tile(jobs, njobs, spre, gi_, smem);
+    gi_ += G;
+    for (int r = 0; r < per && fu < nfill; ++r, fu += G) fill_rows(jobs, njobs, fu, tid);
   }
 }
 
@@ -2136,15 +2161,9 @@ cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_fill(const Job* jobs, const JobTotals& t, cudaStream_t s) {
-  if (t.fill_blocks <= 0) return cudaSuccess;
-  k_fill<<<t.fill_blocks, 256, 0, s>>>(jobs, t.njobs);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s) {
   const int grid = sms * build_blocks_per_sm(t.njobs);
-  k_build<<<grid, kBlock, build_smem(t.njobs), s>>>(jobs, t.njobs);
+  k_build<<<grid, kBlock, build_smem(t.njobs), s>>>(jobs, t.njobs, t.fill_blocks);
   return cudaGetLastError();
 }
 

@@ -151,7 +151,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
   const size_t o_err = take(sizeof(int));
   const size_t o_job = take(sizeof(Job));
-  const size_t o_cnt = take(4 * sizeof(int));
+  const size_t o_cnt = take(8 * sizeof(int));  // this call's set and the one its binning clears
   const size_t o_chain = take(sizeof(int) * nchain);
   const size_t o_act = take(sizeof(int) * std::max(st.nact_table, 1));
   const size_t o_actc = take(sizeof(float) * std::max(st.nact_table, 1));
@@ -208,6 +208,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   float* d_gtape = reinterpret_cast<float*>(base + o_gtape);
   // ---- upload, clear, launch (prepare -> binner -> VJP -> finalize) ----
   NACU(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+  NACU(cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), s));
   NACU(cudaMemcpyAsync(d_chain, H.chain, sizeof(int) * nchain, cudaMemcpyHostToDevice, s));
   if (st.nact_table) {
     NACU(cudaMemcpyAsync(d_act, H.act, sizeof(int) * st.nact_table, cudaMemcpyHostToDevice, s));
@@ -241,6 +242,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   J.tclass = d_tcls;
   J.list = d_list;
   J.counters = d_cnt;
+  J.counters_next = d_cnt + 4;
   J.partial = d_part;
   J.partial_n = (long long)part;
   J.grad = d_grad;
