@@ -1123,12 +1123,22 @@ __device__ __forceinline__ void fill_rows(const Job* __restrict__ jobs, int njob
     if (vec) {
       float4* f4 = reinterpret_cast<float4*>(fill + base);
       float4* e4 = reinterpret_cast<float4*>(eps + base);
-      for (int v = lane; v < (nx >> 2); v += 32) {
-        const int cls = __ldg(tcl + ((4 * v) >> lx));
-        if (cls == 2) continue;
-        const float f = cls ? 1.f : 0.f, e = cls ? e1 : e0;
-        if (fill) f4[v] = make_float4(f, f, f, f);
-        e4[v] = make_float4(e, e, e, e);
+      const int n4 = nx >> 2;
+      for (int v0 = lane; v0 < n4; v0 += 128) {  // four tile classes in flight, then the stores
+        int cls[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + 32 * u;
+          cls[u] = v < n4 ? __ldg(tcl + ((4 * v) >> lx)) : 2;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (cls[u] == 2) continue;
+          const int v = v0 + 32 * u;
+          const float f = cls[u] ? 1.f : 0.f, e = cls[u] ? e1 : e0;
+          if (fill) f4[v] = make_float4(f, f, f, f);
+          e4[v] = make_float4(e, e, e, e);
+        }
       }
     } else {
       for (int i = lane; i < nx; i += 32) {
