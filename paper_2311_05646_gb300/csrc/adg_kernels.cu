@@ -542,18 +542,6 @@ __device__ __forceinline__ int job_by_tile(const Job* jobs, int n, int idx) {
   return lo;
 }
 
-__device__ __forceinline__ int job_by_rows(const Job* jobs, int n, int idx) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    const Job& J = jobs[mid];
-    const int rows = J.g.C * J.g.nz * J.g.ny;
-    if (J.row_base + (J.do_build ? (rows + kFillRows - 1) / kFillRows : 0) > idx) hi = mid;
-    else lo = mid + 1;
-  }
-  return lo;
-}
-
 __device__ __forceinline__ int job_by_param(const Job* jobs, int n, int idx) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -616,6 +604,7 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, int nchain, const 
   const float lo[3] = {i0 + J.g.offmin[0], j0 + J.g.offmin[1], k0 + J.g.offmin[2]};
   const float hi[3] = {(i1 - 1) + J.g.offmax[0], (j1 - 1) + J.g.offmax[1], (k1 - 1) + J.g.offmax[2]};
   int nops = 0, nleaf = 0, sp = 0, e = 0;
+  int r0 = 0, r1 = 0, r2 = 0;  // fold stack: top, second, third; deeper in stk[0 .. sp-4]
   for (int w = 0; w < nchain; ++w) {
     const int word = SCHAIN ? schain[w] : __ldg(chain + w);
     const int code = (word >> 24) & 0xff, arg = word & 0xffffff;
@@ -656,12 +645,19 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, int nchain, const 
       } else {
         ent = (cl == cIN) ? 1 : 0;
       }
-      if (sp < kMaxDepth) stk[sp++][tid] = (uint16_t)ent;
-      else e |= eDepthOverflow;
+      if (sp < kMaxDepth) {  // push: the top three entries live in registers
+        if (sp >= 3) stk[sp - 3][tid] = (uint16_t)r2;
+        r2 = r1;
+        r1 = r0;
+        r0 = ent;
+        ++sp;
+      } else {
+        e |= eDepthOverflow;
+      }
     } else {
       if (sp < 2) { e |= eBadProgram; break; }
-      const int B = stk[--sp][tid];
-      const int A = stk[--sp][tid];
+      const int B = r0;
+      const int A = r1;
       const int ka = A & 3, kb = B & 3;
       const int ra = (A >> 2) & 127, sa = (A >> 9) & 127;
       const int rb = (B >> 2) & 127, sb = (B >> 9) & 127;
@@ -702,11 +698,15 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, int nchain, const 
           res = 0;
         }
       }
-      stk[sp++][tid] = (uint16_t)res;
+      // two popped, one pushed: the fourth entry (if any) comes back from memory
+      r0 = res;
+      r1 = r2;
+      r2 = sp >= 4 ? (int)stk[sp - 4][tid] : 0;
+      --sp;
     }
   }
   if (sp != 1) e |= eBadProgram;
-  const int fin = sp >= 1 ? stk[sp - 1][tid] : 0;
+  const int fin = sp >= 1 ? r0 : 0;
   float cval = 0.f;
   if ((fin & 3) != 2) { nops = 0; cval = (fin & 3) ? 1.f : 0.f; }
   TileProg* out = J.progs + t;
@@ -1051,10 +1051,10 @@ struct TileLoc {
 
 static_assert(sizeof(LeafTab) == kLeafTabBytes, "pool accounting");
 // job-prefix entries in shared memory: a class for small tables, one for any
-__host__ __device__ constexpr int spre_len(int njobs) { return njobs < 16 ? 16 : kMaxJobs + 1; }
+__host__ __device__ constexpr int spre_len(int njobs) { return (njobs + 16) & ~15; }
 constexpr size_t kBuildFixed = (size_t)kMaxDepth * kBlock * 4 + (size_t)kBuildPool * 4 +
                                kMaxOps * 16 + kMaxOps * 2 + 16;
-size_t build_smem(int njobs) { return kBuildFixed + (size_t)spre_len(njobs) * 4; }
+size_t build_smem(int njobs) { return kBuildFixed + 2 * (size_t)spre_len(njobs) * 4; }
 
 // Pool carve of one tile: staged leaves, descriptors, then (VJP) accumulators.
 struct TilePool {
@@ -1077,14 +1077,41 @@ __device__ __forceinline__ TilePool carve_pool(float* pool, int size, int nleaf,
   return t;
 }
 
-// Thread 0: prefix of band-tile counts over the jobs that take part.
-__device__ __forceinline__ void job_prefix(const Job* jobs, int njobs, bool grad, int* spre) {
-  int sum = 0;
-  for (int j = 0; j < njobs; ++j) {
-    spre[j] = sum;
-    if (grad ? jobs[j].do_grad : jobs[j].do_build) sum += jobs[j].counters[0];
+// All threads (a block-wide scan; ends with a barrier): spre[j] = prefix of
+// the band-tile counts of the jobs that take part, spre[njobs] = the total;
+// with rpre, also rpre[j] = job j's first fill unit, rpre[njobs] = nfill.
+__device__ __forceinline__ void job_prefix(const Job* jobs, int njobs, bool grad, int* spre,
+                                           int* rpre = nullptr, int nfill = 0) {
+  __shared__ int wsum[kWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int run = 0;
+  for (int b0 = 0; b0 < njobs; b0 += kBlock) {
+    const int j = b0 + tid;
+    int cnt = 0;
+    if (j < njobs) {
+      const Job& J = jobs[j];
+      if (grad ? J.do_grad : J.do_build) cnt = J.counters[0];
+      if (rpre) rpre[j] = J.row_base;
+    }
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    int off = run;
+    for (int w = 0; w < warp; ++w) off += wsum[w];
+    if (j < njobs) spre[j] = off + inc - cnt;
+    for (int w = 0; w < kWarps; ++w) run += wsum[w];
+    __syncthreads();
   }
-  spre[njobs] = sum;
+  if (tid == 0) {
+    spre[njobs] = run;
+    if (rpre) rpre[njobs] = nfill;
+  }
+  __syncthreads();
 }
 
 // Last job whose prefix is <= i (zero-width ranges never end last).
@@ -1101,9 +1128,9 @@ __device__ __forceinline__ int job_of(const int* spre, int njobs, int i) {
 // = 0 or 1, eps = eps_bg or eps_fg, 16-byte stores, one warp per row (a store
 // instruction covers 512 contiguous bytes); band tiles are left to the band
 // evaluation.  All threads of a kBlock-thread block.
-__device__ __forceinline__ void fill_rows(const Job* __restrict__ jobs, int njobs, int unit,
+__device__ __forceinline__ void fill_rows(const Job* __restrict__ jobs, int jb, int unit,
                                           int tid) {
-  const Job& J = jobs[job_by_rows(jobs, njobs, unit)];
+  const Job& J = jobs[jb];
   if (!J.do_build) return;
   const int nx = J.g.nx, ny = J.g.ny, nz = J.g.nz;
   const int lx = J.g.lx, ly = J.g.ly, lz = J.g.lz, ntx = J.g.ntx, nty = J.g.nty;
@@ -1439,9 +1466,9 @@ __global__ void __launch_bounds__(kBlock, 6) k_build(const Job* __restrict__ job
   // layout: deep-program stack, pool, descriptors, ops, depth, job prefix
   int* spre = reinterpret_cast<int*>(smem + (size_t)kMaxDepth * kBlock * 4 + (size_t)kBuildPool * 4 +
                                      kMaxOps * 16 + kMaxOps * 2) + 4;
+  int* rpre = spre + spre_len(njobs);  // first fill unit of each job
   const int tid = threadIdx.x;
-  if (tid == 0) job_prefix(jobs, njobs, false, spre);
-  __syncthreads();
+  job_prefix(jobs, njobs, false, spre, rpre, nfill);
   const int total = spre[njobs];
   // Band tiles (issue-bound) and groups of constant-tile rows (store-bound)
   // interleaved in every block, so that each SM holds both kinds of work.
@@ -1451,7 +1478,8 @@ __global__ void __launch_bounds__(kBlock, 6) k_build(const Job* __restrict__ job
   while (gi_ < total || fu < nfill) {
     if (gi_ < total) build_band_tile(jobs, njobs, spre, gi_, smem);
     gi_ += G;
-    for (int r = 0; r < per && fu < nfill; ++r, fu += G) fill_rows(jobs, njobs, fu, tid);
+    for (int r = 0; r < per && fu < nfill; ++r, fu += G)
+      fill_rows(jobs, job_of(rpre, njobs, fu), fu, tid);
   }
 }
 
@@ -1742,8 +1770,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
   int* misc = reinterpret_cast<int*>(act1 + kAct1);
   int* spre = reinterpret_cast<int*>(smem + ((kVjpFixed + 15) & ~(size_t)15));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) job_prefix(jobs, njobs, true, spre);
-  __syncthreads();
+  job_prefix(jobs, njobs, true, spre);
   const int total = spre[njobs];
   for (int gi_ = blockIdx.x; gi_ < total; gi_ += gridDim.x) {
     const int jb = job_of(spre, njobs, gi_);
@@ -2132,29 +2159,26 @@ cudaError_t init_kernel_attributes() {
   return e;
 }
 
-// Resident blocks per SM for the two shared-memory classes of the job prefix.
+// Resident blocks per SM for a job table of njobs jobs (the job prefix in
+// shared memory grows with it), cached per job count.
 int build_blocks_per_sm(int njobs) {
-  static int v[2] = {0, 0};
-  const int k = njobs < 16 ? 0 : 1;
-  if (!v[k]) {
-    const size_t sm = build_smem(njobs);
-    cudaFuncSetAttribute(k_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)build_smem(kMaxJobs));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v[k], k_build, kBlock, sm);
-    if (v[k] < 1) v[k] = 1;
+  static int v[kMaxJobs + 1] = {};
+  njobs = std::min(std::max(njobs, 1), kMaxJobs);
+  if (!v[njobs]) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v[njobs], k_build, kBlock, build_smem(njobs));
+    if (v[njobs] < 1) v[njobs] = 1;
   }
-  return v[k];
+  return v[njobs];
 }
 
 int vjp_blocks_per_sm(int njobs) {
-  static int v[2] = {0, 0};
-  const int k = njobs < 16 ? 0 : 1;
-  if (!v[k]) {
-    const size_t sm = vjp_smem(njobs);
-    cudaFuncSetAttribute(k_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vjp_smem(kMaxJobs));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v[k], k_vjp, kBlock, sm);
-    if (v[k] < 1) v[k] = 1;
+  static int v[kMaxJobs + 1] = {};
+  njobs = std::min(std::max(njobs, 1), kMaxJobs);
+  if (!v[njobs]) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v[njobs], k_vjp, kBlock, vjp_smem(njobs));
+    if (v[njobs] < 1) v[njobs] = 1;
   }
-  return v[k];
+  return v[njobs];
 }
 
 cudaError_t launch_prepare(const Job* jobs, const JobTotals& t, cudaStream_t s) {
