@@ -186,7 +186,9 @@ inline int aux_doubles(int kind, int nq) {
 }
 
 inline int aux_floats(int kind, int nq) {
-  return kind == ADG_PRIM_GRAPH ? vertices_of(kind, nq) : 0;
+  if (kind == ADG_PRIM_GRAPH) return vertices_of(kind, nq);
+  if (kind == ADG_PRIM_POLYGON) return kPolyEdgeFloats * vertices_of(kind, nq);
+  return 0;
 }
 
 inline void build_slots(const adg_design_desc* D, SlotTables& t, int* count) {
@@ -412,6 +414,36 @@ inline adg_status prepare_prims(const GridDev& g, const double d[3], const doubl
         NY[j] = sgn * ex / L;
         C[j] = NX[j] * X[j] + NY[j] * Y[j];
         IL[j] = 1.0 / L;
+      }
+      {  // rigid: all vertex x scalars share one slot and coefficient, all y too
+        const int* ac = t.act + t.act_off[pi];
+        const float* cc = t.actc + t.act_off[pi];
+        bool rigid = true;
+        for (int j = 1; j < N && rigid; ++j)
+          rigid = ac[2 + 2 * j] == ac[2] && cc[2 + 2 * j] == cc[2] && ac[3 + 2 * j] == ac[3] &&
+                  cc[3 + 2 * j] == cc[3];
+        if (rigid) R.flags |= kPolyRigid;
+      }
+      // fp32 edge table for the device: vertex relative to the anchor cell and
+      // the normal as hi + lo pairs (about 48 bits), so that a sample's edge
+      // distance needs no FP64
+      R.ai[0] = (int)std::floor(X[0]);
+      R.ai[1] = (int)std::floor(Y[0]);
+      float* E = auxf + R.auxf_off;
+      auto split = [](double v, float* hl) {
+        hl[0] = (float)v;
+        hl[1] = (float)(v - (double)hl[0]);
+      };
+      for (int j = 0; j < N; ++j) {
+        const int j1 = (j + 1) % N;
+        float* e = E + kPolyEdgeFloats * j;
+        split(X[j] - R.ai[0], e + 0);
+        split(Y[j] - R.ai[1], e + 2);
+        split(NX[j], e + 4);
+        split(NY[j], e + 6);
+        e[8] = (float)(X[j1] - X[j]);
+        e[9] = (float)(Y[j1] - Y[j]);
+        e[10] = (float)IL[j];
       }
       cell_range(xmin - beta, xmax + beta, g.offmin[0], g.offmax[0], g.nx, vlo[0], vhi[0]);
       cell_range(ymin - beta, ymax + beta, g.offmin[1], g.offmax[1], g.ny, vlo[1], vhi[1]);

@@ -19,6 +19,11 @@ constexpr int kBlock = 128;     // threads per CTA of the build / VJP kernels
 constexpr int kMaxTileCells = 1024;  // cells per tile (per component)
 constexpr int kWarps = kBlock / 32;
 constexpr int kMaxPolyVerts = 256;  // vertices of one convex polygon
+// Polygon edge table (fp32, kPolyEdgeFloats per edge): the edge's start vertex
+// relative to the polygon's integer anchor cell (PrimRec ai[0], ai[1]) as
+// (hi, lo) pairs, the unit inward normal as (hi, lo) pairs, the edge vector
+// and its inverse length (cells).
+constexpr int kPolyEdgeFloats = 11;
 static_assert(kMaxOps < 127 && kMaxLeaves < 127, "op operands are 7-bit fields, 127 = constant 1");
 // Per-tile pools of the band kernels (floats): staged leaves (PrimRec) and
 // their table descriptors (80 B each), the VJP's per-warp accumulator rows,
@@ -31,7 +36,8 @@ constexpr size_t kTapeBlockFloats = (size_t)kMaxOps * kBlock;  // global tape pe
 
 enum : int32_t { kBox = 0, kCircle = 1, kPolygon = 2, kGraph = 3 };
 enum : int32_t { kLinear = 0, kSigmoid = 1, kQuadratic = 2, kSin = 3, kErf = 4 };
-enum : int32_t { kBoundX = 1, kBoundY = 2, kBoundZ = 4, kRectSigma = 8, kGraphAbove = 16 };
+enum : int32_t { kBoundX = 1, kBoundY = 2, kBoundZ = 4, kRectSigma = 8, kGraphAbove = 16,
+                 kPolyRigid = 32 /* every vertex x (y) is the same scalar of one parameter */ };
 // chained (binary) design program, one int32 word per op: (code << 24) | arg
 enum : int32_t { cPush = 0, cUnion = 1, cInter = 2, cDiff = 3 };
 // folded per-tile program, one uint16 per op: code | a << 2 | b << 9 (code 2

@@ -191,20 +191,48 @@ __device__ __noinline__ float graph_dist(const PrimRec& P, const Cell& c, const 
 
 // Poly2D: signed distance of the sample to edge e's line, inward positive, in
 // cells (FP64 line equation: coordinates reach thousands of cells).
-__device__ __forceinline__ float poly_edge_dist(const double* A, int N, int e, double ux, double uy) {
-  const double* NX = A + 2 * N;
-  const double* NY = NX + N;
-  const double* C = NY + N;
-  return (float)(fma(NX[e], ux, fma(NY[e], uy, -C[e])));
+// Error-free sum (Knuth): a + b = s + e exactly (no contraction into fma).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-__device__ __noinline__ float poly_value(const PrimRec& P, const Cell& c, const double* auxd) {
+// Signed distance (cells, positive inside) of a sample from the line of one
+// polygon edge (Table 4, Poly2D): n . (u - v_e), with u relative to the
+// polygon's anchor cell (exact in fp32) and v_e, n stored as hi + lo pairs;
+// the products are split exactly with fma, so the distance carries about 48
+// bits however far the sample is from the anchor -- no FP64, whose rate on
+// this part is a small fraction of fp32.
+__device__ __forceinline__ float poly_d(const float* E, float ux, float uy) {
+  float dxh, dxl, dyh, dyl;
+  two_sum(ux, -E[0], dxh, dxl);
+  two_sum(uy, -E[2], dyh, dyl);
+  dxl = __fsub_rn(dxl, E[1]);
+  dyl = __fsub_rn(dyl, E[3]);
+  const float p1 = __fmul_rn(E[4], dxh), e1 = fmaf(E[4], dxh, -p1);
+  const float p2 = __fmul_rn(E[6], dyh), e2 = fmaf(E[6], dyh, -p2);
+  float sh, sl;
+  two_sum(p1, p2, sh, sl);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(sl, e1), e2),
+                             __fadd_rn(fmaf(E[4], dxl, E[5] * dxh), fmaf(E[6], dyl, E[7] * dyh)));
+  return __fadd_rn(sh, lo);
+}
+
+// Sample position relative to the polygon's anchor cell (exact in fp32).
+__device__ __forceinline__ void poly_rel(const PrimRec& P, const Cell& c, float& ux, float& uy) {
+  ux = (float)(c.i - P.ai[0]) + c.ox;
+  uy = (float)(c.j - P.ai[1]) + c.oy;
+}
+
+__device__ __noinline__ float poly_value(const PrimRec& P, const Cell& c, const float* auxf) {
   const int N = P.naux;
-  const double* A = auxd + P.auxd_off;
-  const double ux = (double)c.i + (double)c.ox, uy = (double)c.j + (double)c.oy;
+  const float* E = auxf + P.auxf_off;
+  float ux, uy;
+  poly_rel(P, c, ux, uy);
   float prod = 1.f, ds;
   for (int e = 0; e < N && prod != 0.f; ++e)
-    prod *= sigma_f(P.sigma, P.kr * poly_edge_dist(A, N, e, ux, uy), ds);
+    prod *= sigma_f(P.sigma, P.kr * poly_d(E + kPolyEdgeFloats * e, ux, uy), ds);
   return prod;
 }
 
@@ -230,7 +258,7 @@ __device__ __forceinline__ float leaf_value(const PrimRec& P, const Cell& c, con
     const float d = graph_dist(P, c, auxf, auxd, seg, t);
     return sigma_f(P.sigma, P.kr * d, ds) * zf;
   }
-  return poly_value(P, c, auxd) * zf;
+  return poly_value(P, c, auxf) * zf;
 }
 
 // Nonzero d s / d q (physical units) of one leaf at one cell, times `a`, as
@@ -327,7 +355,7 @@ __device__ __forceinline__ int leaf_pairs(const PrimRec& P, const Cell& c, float
   if (P.kind == kGraph) return graph_pairs(P, c, a, g, actp, actcp, auxf, auxd, pk, pv);
   // polygon: only the extrusion scalars here; vertices go through poly_accumulate
   if (actp[0] < 0 && actp[1] < 0) return n;
-  const float s = poly_value(P, c, auxd);
+  const float s = poly_value(P, c, auxf);
   n = push_pair(actp, actcp, 0, s * dz0 * a * g.invd[2], n, pk, pv);
   n = push_pair(actp, actcp, 1, s * dz1 * a * g.invd[2], n, pk, pv);
   return n;
@@ -357,7 +385,7 @@ __device__ __forceinline__ int cls_sigma(float a, float b, float beta, float lo,
 }
 
 __device__ __forceinline__ int classify(const PrimRec& P, const float lo[3], const float hi[3],
-                        const double* auxd) {
+                                        const double* auxd, const float* auxf) {
   int z = cIN;
   if (P.kind != kBox && (P.flags & kBoundZ))
     z = cls_exact(P.ai[4], P.af[4], P.ai[5], P.af[5], lo[2], hi[2]);
@@ -420,20 +448,23 @@ __device__ __forceinline__ int classify(const PrimRec& P, const float lo[3], con
     return cBND;
   }
   if (P.kind == kPolygon) {
+    // each edge's line function over the tile's sample box, relative to the
+    // anchor cell; fp32 rounding (~1e-7 of the polygon's extent) stays far
+    // inside the classification margin
     const int N = P.naux;
-    const double* A = auxd + P.auxd_off;
-    const double* NX = A + 2 * N;
-    const double* NY = NX + N;
-    const double* C = NY + N;
-    const double b = (double)P.band + kMargin;
+    const float* E = auxf + P.auxf_off;
+    const float lx = lo[0] - (float)P.ai[0], hx = hi[0] - (float)P.ai[0];
+    const float ly = lo[1] - (float)P.ai[1], hy = hi[1] - (float)P.ai[1];
+    const float b = P.band + kMargin;
     bool all_in = true;
     for (int e = 0; e < N; ++e) {
-      // extremes of the edge's line function over the tile's sample box
-      const double ax = NX[e] >= 0 ? NX[e] * lo[0] : NX[e] * hi[0];
-      const double bx = NX[e] >= 0 ? NX[e] * hi[0] : NX[e] * lo[0];
-      const double ay = NY[e] >= 0 ? NY[e] * lo[1] : NY[e] * hi[1];
-      const double by = NY[e] >= 0 ? NY[e] * hi[1] : NY[e] * lo[1];
-      const double dmin = ax + ay - C[e], dmax = bx + by - C[e];
+      const float* Ee = E + kPolyEdgeFloats * e;
+      const float nx = Ee[4], ny = Ee[6], rx = Ee[0], ry = Ee[2];
+      const float ax = nx >= 0.f ? nx * (lx - rx) : nx * (hx - rx);
+      const float bx = nx >= 0.f ? nx * (hx - rx) : nx * (lx - rx);
+      const float ay = ny >= 0.f ? ny * (ly - ry) : ny * (hy - ry);
+      const float by = ny >= 0.f ? ny * (hy - ry) : ny * (ly - ry);
+      const float dmin = ax + ay, dmax = bx + by;
       if (dmax < -b) return cOUT;
       if (dmin <= b) all_in = false;
     }
@@ -451,23 +482,21 @@ __device__ __forceinline__ int classify(const PrimRec& P, const float lo[3], con
 __device__ __forceinline__ void flush_slot(int& slot, float& v, float* acc, float* cmp, int lane);
 
 __device__ __noinline__ void poly_accumulate(const PrimRec& P, const Cell& c, float a, const GridDev& g,
-                                const int* act, const float* actc, const double* auxd,
+                                const int* act, const float* actc, const float* auxf,
                                 float* acc, float* cmp, int lane) {
   const int N = P.naux;
-  const double* A = auxd + P.auxd_off;
-  const double* X = A;
-  const double* Y = A + N;
-  const double* IL = A + 5 * N;
+  const float* E = auxf + P.auxf_off;
   const int* actp = act + P.act_off;
   const float* actcp = actc + P.act_off;
-  const double ux = (double)c.i + (double)c.ox, uy = (double)c.j + (double)c.oy;
+  float ux, uy;
+  poly_rel(P, c, ux, uy);
   float dz0, dz1;
   const float zf = a != 0.f ? zfactor(P, c, dz0, dz1) : 0.f;
   float prod = 1.f, ds;
   int nz = 0;
   if (zf != 0.f) {
     for (int e = 0; e < N; ++e) {
-      const float s = sigma_f(P.sigma, P.kr * poly_edge_dist(A, N, e, ux, uy), ds);
+      const float s = sigma_f(P.sigma, P.kr * poly_d(E + kPolyEdgeFloats * e, ux, uy), ds);
       if (s == 0.f) { if (++nz > 1) break; }
       else prod *= s;
     }
@@ -480,17 +509,18 @@ __device__ __noinline__ void poly_accumulate(const PrimRec& P, const Cell& c, fl
   for (int e = 0; e < N; ++e) {
     const int e1 = e + 1 == N ? 0 : e + 1;
     float ge = 0.f, d = 0.f;
+    const float* Ee = E + kPolyEdgeFloats * e;
     if (live) {
-      d = poly_edge_dist(A, N, e, ux, uy);
+      d = poly_d(Ee, ux, uy);
       const float se = sigma_f(P.sigma, P.kr * d, ds);
       const float other = nz == 0 ? prod / se : (se == 0.f ? prod : 0.f);
       ge = scale * ds * other;
     }
     if (!__any_sync(0xffffffffu, ge != 0.f)) continue;
     // d(d_e)/d(x_e, y_e, x_e1, y_e1) in cells (see the oracle's Poly2D)
-    const float ex = (float)(X[e1] - X[e]), ey = (float)(Y[e1] - Y[e]);
-    const float rx = (float)(ux - X[e]), ry = (float)(uy - Y[e]);
-    const float il = (float)IL[e];
+    const float ex = Ee[8], ey = Ee[9];
+    const float rx = (ux - Ee[0]) - Ee[1], ry = (uy - Ee[2]) - Ee[3];
+    const float il = Ee[10];
     const float dil = d * il * il;
     const float t[4] = {sgn * (ey - ry) * il + dil * ex, sgn * (rx - ex) * il + dil * ey,
                         sgn * ry * il - dil * ex, -sgn * rx * il - dil * ey};
@@ -625,7 +655,7 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, int nchain, const 
         const int nc = ((SCHAIN ? schain[w + 1] : __ldg(chain + w + 1)) >> 24) & 0xff;
         if ((nc == cUnion || nc == cDiff) && sp >= 1) { ++w; continue; }
       }
-      const int cl = cand ? classify(prims[arg], lo, hi, auxd) : cOUT;
+      const int cl = cand ? classify(prims[arg], lo, hi, auxd, J.auxf) : cOUT;
       int ent = 0;
       if (cl == cBND) {
         int slot = -1;
@@ -905,13 +935,15 @@ constexpr int tOK = 1, tBOX = 2, tACT = 4;  // tabled, box, drives some paramete
 constexpr int tKEYS = 8;                     // bits 8..13: box scalars driving a parameter
 
 // All threads: the accumulator slot and map coefficient of each scalar of the
-// box (6) and circle (5) leaves (staged in parallel: these are global reads).
+// box (6) and circle (5) leaves, and of a rigid polygon's z0, z1 and (shared)
+// vertex x, y scalars (staged in parallel: these are global reads).
 __device__ __forceinline__ void stage_slots(const PrimRec* sl, int nleaf, const int* act,
                                             const float* actc, LeafTab* lt, int tid) {
   for (int q = tid; q < nleaf * 6; q += kBlock) {
     const int l = q / 6, k = q - l * 6;
     const int kind = sl[l].kind;
-    const bool keyed = kind == kBox || (kind == kCircle && k < 5);
+    const bool keyed = kind == kBox || (kind == kCircle && k < 5) ||
+                       (kind == kPolygon && (sl[l].flags & kPolyRigid) && k < 4);
     lt[l].slot[k] = keyed ? __ldg(act + sl[l].act_off + k) : -1;
     lt[l].coef[k] = keyed ? __ldg(actc + sl[l].act_off + k) : 0.f;
   }
@@ -991,7 +1023,7 @@ __device__ __forceinline__ float plane_value(const PrimRec& P, const Cell& c, co
     double t;
     return sigma_f(P.sigma, P.kr * graph_dist(P, c, auxf, auxd, seg, t), ds);
   }
-  return poly_value(P, c, auxd);
+  return poly_value(P, c, auxf);
 }
 
 // All threads: fill the planned tables of the tile with origin (X0, Y0, Z0).
@@ -1597,6 +1629,49 @@ __device__ __forceinline__ void circle_reduce(const PrimRec& P, const LeafTab& t
   if (t.slot[4] >= 0) ks.add(t.slot[4], s * dz1 * a * g.invd[2] * t.coef[4]);
 }
 
+// Poly2D (Table 4) translated rigidly by its parameters: moving every vertex
+// by dx changes each edge distance by -n_x dx, so the vertex terms collapse to
+// two sums over the edges; keys z0, z1, x, y (slots staged as 0..3).
+__device__ __noinline__ void poly_rigid_reduce(const PrimRec& P, const LeafTab& t, const Cell& c,
+                                               float a, const GridDev& g, const float* auxf,
+                                               const KeySink& ks) {
+  const int N = P.naux;
+  const float* E = auxf + P.auxf_off;
+  float ux, uy, dz0 = 0.f, dz1 = 0.f, ds;
+  poly_rel(P, c, ux, uy);
+  const float zf = zfactor(P, c, dz0, dz1);
+  // one pass: prod = product of the nonzero factors, (sx, sy) = sum of
+  // (sigma'/sigma) n over them; an exactly-zero factor keeps only its own
+  // term (sigma' n times the others), two of them zero the derivative
+  float prod = 1.f, gx = 0.f, gy = 0.f;
+  int nz = 0;
+  if (a != 0.f) {
+    float sx = 0.f, sy = 0.f, zx = 0.f, zy = 0.f;
+    for (int e = 0; e < N; ++e) {
+      const float* Ee = E + kPolyEdgeFloats * e;
+      const float se = sigma_f(P.sigma, P.kr * poly_d(Ee, ux, uy), ds);
+      if (se == 0.f) {
+        if (++nz > 1) break;
+        zx = ds * Ee[4];
+        zy = ds * Ee[6];
+      } else {
+        prod *= se;
+        const float r = ds / se;
+        sx += r * Ee[4];
+        sy += r * Ee[6];
+      }
+    }
+    if (nz == 0) { gx = -prod * sx; gy = -prod * sy; }
+    else if (nz == 1) { gx = -prod * zx; gy = -prod * zy; }
+  }
+  const float v = nz == 0 ? prod : 0.f;  // the in-plane factor
+  const float scale = a * zf * P.kr * g.invd[0];
+  if (t.slot[0] >= 0) ks.add(t.slot[0], v * dz0 * a * g.invd[2] * t.coef[0]);
+  if (t.slot[1] >= 0) ks.add(t.slot[1], v * dz1 * a * g.invd[2] * t.coef[1]);
+  if (t.slot[2] >= 0) ks.add(t.slot[2], scale * gx * t.coef[2]);
+  if (t.slot[3] >= 0) ks.add(t.slot[3], scale * gy * t.coef[3]);
+}
+
 // Activity of the tile's samples, per axis: a sample can have a nonzero
 // Jacobian row only where some parameter-driven scalar of a tabled box has a
 // nonzero derivative-table entry at its x, y or z (each scalar moves one
@@ -1975,16 +2050,28 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
               box_direct_reduce(sl[lf], lt[lf], cc, a, g, ks);
               continue;
             }
+            // a tabled in-plane factor of exactly 0 means sigma is 0 with zero
+            // slope on every edge (truncated tails; not for the linear kind,
+            // whose closed-interval kink has slope 1 at 0): nothing to add
+            float an = a;
+            if ((fl & tOK) && sl[lf].sigma != kLinear &&
+                tab[lt[lf].v.w + (c * TY + y) * TX + x] == 0.f)
+              an = 0.f;
+            if (__ballot_sync(0xffffffffu, an != 0.f) == 0u) continue;
             if (kind == kCircle) {
-              circle_reduce(sl[lf], lt[lf], cc, a, g, ks);
+              circle_reduce(sl[lf], lt[lf], cc, an, g, ks);
+              continue;
+            }
+            if (kind == kPolygon && (sl[lf].flags & kPolyRigid)) {
+              poly_rigid_reduce(sl[lf], lt[lf], cc, an, g, J.auxf, ks);
               continue;
             }
             int n = 0;
-            if (a != 0.f)
-              n = leaf_pairs(sl[lf], cc, a, g, J.act, J.actc, J.auxf, J.auxd, pk + tid, pv + tid);
+            if (an != 0.f)
+              n = leaf_pairs(sl[lf], cc, an, g, J.act, J.actc, J.auxf, J.auxd, pk + tid, pv + tid);
             warp_accumulate(n, 0, pk + tid, pv + tid, la, lc, lane);
             if (kind == kPolygon)
-              poly_accumulate(sl[lf], cc, a, g, J.act, J.actc, J.auxd, la, lc, lane);
+              poly_accumulate(sl[lf], cc, an, g, J.act, J.actc, J.auxf, la, lc, lane);
           }
         }
       };

@@ -64,7 +64,7 @@ struct NoAllocHost {
   double q[kNAMaxQ];
   PrimRec prims[kNAMaxPrims];
   double auxd[6 * kNAMaxQ];
-  float auxf[kNAMaxQ];
+  float auxf[6 * kNAMaxQ];
   Job job;
 };
 
@@ -132,7 +132,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
     if (host::aux_doubles(D->prim_kind[p], D->prim_nq[p]) > 6 * kNAMaxQ)
       return na_fail(ADG_EINVAL, "primitive %d has too many vertices", p);
   host::build_slots(D, st, H.count);
-  if (st.auxd_n > 6 * kNAMaxQ || st.auxf_n > kNAMaxQ)
+  if (st.auxd_n > 6 * kNAMaxQ || st.auxf_n > 6 * kNAMaxQ)
     return na_fail(ADG_EINVAL, "graph / polygon vertices exceed the static limits");
   GridDev g;
   host::set_grid(D, tx, ty, tz, nchain, g);
