@@ -322,6 +322,13 @@ def run_adg(args):
                      "nonzero, so it is latency-bound, not HBM-bound; the HBM-bound kernels are "
                      "the build (kernels.build: fill + eps of every sample) and the dense field "
                      "stream (dense_vjp.stream_*)")}
+    # the whole step against the same peak: its algorithmic bytes (fill + eps
+    # of every sample, the fields of the active samples) over the step time
+    step_bytes = bytes_build + bytes_vjp
+    step_roof = {"algorithmic_bytes": step_bytes, "ms": ms,
+                 "achieved_GBps": step_bytes / (ms * 1e-3) / 1e9,
+                 "frac_of_measured_hbm": step_bytes / (ms * 1e-3) / 1e9 / peak,
+                 "floor_ms": step_bytes / (peak * 1e9) * 1e3}
     kernels = {k: {"launches": v[0], "ms_total": v[1],
                    "us_per_launch": 1e3 * v[1] / max(v[0], 1)} for k, v in prof.items() if v[0]}
     for k in kern:
@@ -431,7 +438,8 @@ def run_adg(args):
                        "tiles": stats["tiles"], "band_cells": stats["band_cells"],
                        "vjp_active_samples": stats["active_samples"],
                        "l2": "inputs larger than L2 (fields 691 MB + outputs 346 MB per step)"},
-            "roofline": roof, "kernels": kernels, "gpu_launches": launches,
+            "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
+            "gpu_launches": launches,
             "cpu_baseline": cpu, "e2e": e2e, "dense_vjp": dense, "clocks": clocks.summary(),
         }
         print(json.dumps(line))
