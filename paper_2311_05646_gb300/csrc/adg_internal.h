@@ -103,6 +103,8 @@ struct TileProg {
   int nleaf;
   float cval;
   int nslot;
+  int pairs;  // a graph or polygon leaf: the VJP reserves pair columns
+  int pad[3];
   uint16_t ops[kMaxOps];
   uint16_t leaf[kMaxLeaves];
 };

@@ -762,6 +762,7 @@ __device__ __forceinline__ void bin_tile(const Job& J, int t, int nchain, const 
   out->nleaf = nleaf;
   out->cval = cval;
   out->nslot = nslot;
+  out->pairs = pairs;
   J.tclass[t] = nops > 0 ? 2 : (cval != 0.f ? 1 : 0);
   // band-tile list and counters, one atomic of each kind per group of lanes
   // that arrive together (any grouping is correct; the list order is free)
@@ -937,15 +938,17 @@ constexpr int tKEYS = 8;                     // bits 8..13: box scalars driving 
 // All threads: the accumulator slot and map coefficient of each scalar of the
 // box (6) and circle (5) leaves, and of a rigid polygon's z0, z1 and (shared)
 // vertex x, y scalars (staged in parallel: these are global reads).
-__device__ __forceinline__ void stage_slots(const PrimRec* sl, int nleaf, const int* act,
-                                            const float* actc, LeafTab* lt, int tid) {
+__device__ __forceinline__ void stage_slots(const TileProg* P, const PrimRec* prims, int nleaf,
+                                            const int* act, const float* actc, LeafTab* lt,
+                                            int tid) {
   for (int q = tid; q < nleaf * 6; q += kBlock) {
     const int l = q / 6, k = q - l * 6;
-    const int kind = sl[l].kind;
+    const PrimRec& R = prims[P->leaf[l]];  // read from the records, not the staged copy
+    const int kind = R.kind;
     const bool keyed = kind == kBox || (kind == kCircle && k < 5) ||
-                       (kind == kPolygon && (sl[l].flags & kPolyRigid) && k < 4);
-    lt[l].slot[k] = keyed ? __ldg(act + sl[l].act_off + k) : -1;
-    lt[l].coef[k] = keyed ? __ldg(actc + sl[l].act_off + k) : 0.f;
+                       (kind == kPolygon && (R.flags & kPolyRigid) && k < 4);
+    lt[l].slot[k] = keyed ? __ldg(act + R.act_off + k) : -1;
+    lt[l].coef[k] = keyed ? __ldg(actc + R.act_off + k) : 0.f;
   }
 }
 
@@ -1223,17 +1226,26 @@ __device__ __forceinline__ void uniform_axes(const LeafTab* lt, int nleaf, const
                                              const float* tab, bool derivs, int tid, bool& okY,
                                              bool& okZ) {
   const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
+  const int lane = tid & 31;
+  // axes that cannot collapse are not checked (the flags are read by the
+  // lanes of every warp in parallel; the result is the same for every thread)
+  bool untabled = false, planeAct = false;
+  for (int l = lane; l < nleaf; l += 32) {
+    const int f = lt[l].d.w;
+    untabled |= !(f & tOK);
+    planeAct |= derivs && !(f & tBOX) && (f & tACT);
+  }
   okY = true;
   okZ = true;
-  for (int l = 0; l < nleaf; ++l) {  // axes that cannot collapse are not checked
-    const int f = lt[l].d.w;
-    if (!(f & tOK)) { okY = false; okZ = false; return; }  // same for every thread
-    if (derivs && !(f & tBOX) && (f & tACT)) okY = false;
-  }
-  for (int l = 0; l < nleaf; ++l) {
+  if (__any_sync(0xffffffffu, untabled)) { okY = false; okZ = false; return; }
+  if (__any_sync(0xffffffffu, planeAct)) okY = false;
+  // z tables of every leaf and y tables of the boxes, one pass over
+  // (leaf, entry) pairs
+  const int ez = C * TZ, e1 = ez + C * TY;
+  for (int q = tid; q < nleaf * e1; q += kBlock) {
+    const int l = q / e1, e = q - l * e1;
     const int4 v = lt[l].v, d = lt[l].d;
-    const bool box = (d.w & tBOX) != 0;
-    for (int e = tid; e < C * TZ; e += kBlock) {
+    if (e < ez) {
       const int c = e / TZ, z = e - c * TZ;
       if (z == 0) continue;
       okZ &= tab[v.z + c * TZ + z] == tab[v.z + c * TZ];
@@ -1241,25 +1253,27 @@ __device__ __forceinline__ void uniform_axes(const LeafTab* lt, int nleaf, const
         okZ &= tab[d.z + 2 * c * TZ + z] == tab[d.z + 2 * c * TZ];
         okZ &= tab[d.z + (2 * c + 1) * TZ + z] == tab[d.z + (2 * c + 1) * TZ];
       }
-    }
-    if (box) {
-      for (int e = tid; e < C * TY; e += kBlock) {
-        const int c = e / TY, y = e - c * TY;
-        if (y == 0) continue;
-        okY &= tab[v.y + c * TY + y] == tab[v.y + c * TY];
-        if (derivs) {
-          okY &= tab[d.y + 2 * c * TY + y] == tab[d.y + 2 * c * TY];
-          okY &= tab[d.y + (2 * c + 1) * TY + y] == tab[d.y + (2 * c + 1) * TY];
-        }
+    } else if (d.w & tBOX) {
+      const int r = e - ez, c = r / TY, y = r - c * TY;
+      if (y == 0) continue;
+      okY &= tab[v.y + c * TY + y] == tab[v.y + c * TY];
+      if (derivs) {
+        okY &= tab[d.y + 2 * c * TY + y] == tab[d.y + 2 * c * TY];
+        okY &= tab[d.y + (2 * c + 1) * TY + y] == tab[d.y + (2 * c + 1) * TY];
       }
-    } else if (okY || !derivs) {
+    }
+  }
+  // in-plane tables of the other leaves along y
+  if (okY || !derivs)
+    for (int l = 0; l < nleaf; ++l) {
+      const int4 v = lt[l].v;
+      if (lt[l].d.w & tBOX) continue;
       for (int e = tid; e < C * TX * TY; e += kBlock) {
         const int c = e / (TX * TY), r = e - c * TX * TY, y = r / TX, x = r - y * TX;
         if (y == 0) continue;
         okY &= tab[v.w + (c * TY + y) * TX + x] == tab[v.w + c * TY * TX + x];
       }
     }
-  }
 }
 
 // ---- forward-only evaluation (build) ----------------------------------------
@@ -1271,27 +1285,38 @@ __device__ __forceinline__ void uniform_axes(const LeafTab* lt, int nleaf, const
 constexpr int kRegStack = 4;
 constexpr int dBox = 0, dPlane = 1, dDirect = 2, dLogic = 8;
 
-// Thread 0, after tables_plan: descriptors of the tile's ops; returns the
-// largest stack depth the program reaches.
-__device__ __forceinline__ int plan_descs(const uint16_t* sops, int nops, const LeafTab* lt,
-                                          int4* desc) {
+// Warp 0, after tables_plan: descriptors of the tile's ops (one op per lane)
+// and the largest stack depth the program reaches (a prefix sum of the
+// pushes and pops over the lanes); every lane returns it.
+__device__ __forceinline__ int plan_descs_warp(const uint16_t* sops, int nops, const LeafTab* lt,
+                                               int4* desc, int lane) {
   int depth = 0, maxd = 0;
-  for (int pos = 0; pos < nops; ++pos) {
-    const FoldOp fo = fold_op(sops[pos]);
-    const int code = fo.code;
-    if (code == fPush) {
-      const int a = fo.a;
-      const int f = lt[a].d.w;
-      const int4 v = lt[a].v;
-      if (!(f & tOK)) desc[pos] = make_int4(dDirect, a, 0, 0);
-      else if (f & tBOX) desc[pos] = make_int4(dBox, v.x, v.y, v.z);
-      else desc[pos] = make_int4(dPlane, v.w, 0, v.z);
-      ++depth;
-    } else {
-      desc[pos] = make_int4(dLogic + code, 0, 0, 0);
-      if (code != fCompl) --depth;
+  for (int p0 = 0; p0 < nops; p0 += 32) {
+    const int pos = p0 + lane;
+    int delta = 0;
+    if (pos < nops) {
+      const FoldOp fo = fold_op(sops[pos]);
+      const int code = fo.code;
+      if (code == fPush) {
+        const int a = fo.a;
+        const int f = lt[a].d.w;
+        const int4 v = lt[a].v;
+        desc[pos] = !(f & tOK) ? make_int4(dDirect, a, 0, 0)
+                  : (f & tBOX) ? make_int4(dBox, v.x, v.y, v.z) : make_int4(dPlane, v.w, 0, v.z);
+        delta = 1;
+      } else {
+        desc[pos] = make_int4(dLogic + code, 0, 0, 0);
+        delta = code != fCompl ? -1 : 0;
+      }
     }
-    maxd = max(maxd, depth);
+    int inc = delta;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    maxd = max(maxd, __reduce_max_sync(0xffffffffu, depth + inc));
+    depth += __shfl_sync(0xffffffffu, inc, 31);
   }
   return maxd;
 }
@@ -1412,7 +1437,11 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
     if (tid < 32) {
       tables_plan_warp(tp.sl, nleaf, g, false, tp.cap, tp.lt, tid);
       __syncwarp();
-      if (tid == 0) sdepth[0] = plan_descs(sops, nops, tp.lt, desc);
+      const int depth = plan_descs_warp(sops, nops, tp.lt, desc, tid);
+      if (tid == 0) {
+        sdepth[0] = depth;
+        sdepth[1] = 1;  // z collapse until a thread finds otherwise
+      }
     }
     __syncthreads();
     tables_fill(tp.sl, nleaf, g, tp.lt, false, tx << g.lx, ty << g.ly, tz << g.lz, tp.tab, tid,
@@ -1420,8 +1449,9 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
     __syncthreads();
     bool okY, okZ;
     uniform_axes(tp.lt, nleaf, g, tp.tab, false, tid, okY, okZ);
+    if (!okZ) sdepth[1] = 0;
     const bool uy = __syncthreads_and(okY);
-    const bool uz = __syncthreads_and(okZ);
+    const bool uz = sdepth[1] != 0;
     // evaluated lattice: x, then y (one row if y collapses), z, component
     const int lyr = uy ? 0 : g.ly, lzr = uz ? 0 : g.lz;
     const int lxy = g.lx + lyr, lxyz = lxy + lzr;
@@ -1703,7 +1733,7 @@ __device__ __forceinline__ void activity_axes(const LeafTab* lt, int nleaf, cons
 // Warp 0: one descriptor per op (pushes as for the build; logic ops carry
 // their operand positions in y, z) and, in program order, the positions that
 // push a parameter-driven leaf (pos | leaf << 8).  Returns their number.
-__device__ __forceinline__ int descs_warp(const uint16_t* __restrict__ ops, int nops,
+__device__ __forceinline__ int descs_warp(const uint16_t* ops, int nops,
                                           const LeafTab* lt, int4* desc, int* dl, int lane) {
   int n = 0;
   for (int p0 = 0; p0 < nops; p0 += 32) {
@@ -1711,7 +1741,7 @@ __device__ __forceinline__ int descs_warp(const uint16_t* __restrict__ ops, int 
     bool act = false;
     int leaf = 0;
     if (pos < nops) {
-      const FoldOp fo = fold_op(__ldg(ops + pos));
+      const FoldOp fo = fold_op(ops[pos]);
       if (fo.code == fPush) {
         const int f = lt[fo.a].d.w;
         const int4 v = lt[fo.a].v;
@@ -1799,22 +1829,57 @@ __device__ __noinline__ void tile_seeds(const Job* J, const uint16_t* slist, flo
   const int TXm = (1 << lx) - 1, TYm = (1 << lyr) - 1, TZm = (1 << lzr) - 1;
   const int lxy = lx + lyr, lxyz = lxy + lzr;
   const size_t plane = (size_t)g.nx * g.ny * g.nz;
+  const int npos = ny_r * nz_r;
+  if (npos == 1) {  // one position per sample: several samples' loads in flight
 #pragma unroll 4
-  for (int i = c0 + (int)threadIdx.x; i < c1; i += kBlock) {  // independent loads in flight
+    for (int i = c0 + (int)threadIdx.x; i < c1; i += kBlock) {
+      const int l = slist[i];
+      const int x = l & TXm, y = (l >> lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
+      const size_t o = ((size_t)(geo.z + z) * g.ny + (geo.y + y)) * g.nx + (geo.x + x);
+      float zs;
+      if (va.G) {
+        zs = __ldg(va.G + (size_t)c * plane + o);
+      } else {
+        const float2 f = __ldg(va.ef[c] + o), a = __ldg(va.ea[c] + o);
+        const float pr = f.x * a.x - f.y * a.y, pi = f.x * a.y + f.y * a.x;
+        zs = 0.f + (va.w[c].x * pr - va.w[c].y * pi);
+      }
+      zsb[i - c0] = zs * g.deps;
+    }
+    return;
+  }
+  for (int i = c0 + (int)threadIdx.x; i < c1; i += kBlock) {
     const int l = slist[i];
     const int x = l & TXm, y = (l >> lx) & TYm, z = (l >> lxy) & TZm, c = l >> lxyz;
+    const size_t o0 = ((size_t)(geo.z + z) * g.ny + (geo.y + y)) * g.nx + (geo.x + x);
     float zs = 0.f;
-    for (int zz = 0; zz < nz_r; ++zz)
-      for (int yy = 0; yy < ny_r; ++yy) {
-        const size_t o = ((size_t)(geo.z + z + zz) * g.ny + (geo.y + y + yy)) * g.nx + (geo.x + x);
+    // positions in groups of four: the group's loads are all issued before
+    // the first product, and the sum runs through the positions in order
+    for (int p0 = 0; p0 < npos; p0 += 4) {
+      float2 f[4], a[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int p = p0 + k;
+        f[k] = make_float2(0.f, 0.f);
+        a[k] = make_float2(0.f, 0.f);
+        if (p < npos) {
+          const int zz = p / ny_r, yy = p - zz * ny_r;
+          const size_t o = o0 + ((size_t)zz * g.ny + yy) * g.nx;
+          if (va.G) f[k].x = __ldg(va.G + (size_t)c * plane + o);
+          else { f[k] = __ldg(va.ef[c] + o); a[k] = __ldg(va.ea[c] + o); }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (p0 + k >= npos) break;
         if (va.G) {
-          zs += __ldg(va.G + (size_t)c * plane + o);
+          zs += f[k].x;
         } else {
-          const float2 f = __ldg(va.ef[c] + o), a = __ldg(va.ea[c] + o);
-          const float pr = f.x * a.x - f.y * a.y, pi = f.x * a.y + f.y * a.x;
+          const float pr = f[k].x * a[k].x - f[k].y * a[k].y, pi = f[k].x * a[k].y + f[k].y * a[k].x;
           zs += va.w[c].x * pr - va.w[c].y * pi;
         }
       }
+    }
     zsb[i - c0] = zs * g.deps;  // eps = eps_bg + deps fill
   }
 }
@@ -1841,7 +1906,8 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
   int* sbase = reinterpret_cast<int*>(slist + kMaxTileCells * 3);
   unsigned char* act1 = reinterpret_cast<unsigned char*>(sbase + kMaxLeaves + 1);
   // misc words: [0] active samples, [1] all-active flag, [2] parameter-driven
-  // pushes, [4..9] x-row masks per component (2 words each), [10..11] in-grid x
+  // pushes, [3] z-collapse flag, [4..9] x-row masks per component (2 words
+  // each), [10..11] in-grid x
   int* misc = reinterpret_cast<int*>(act1 + kAct1);
   int* spre = reinterpret_cast<int*>(smem + ((kVjpFixed + 15) & ~(size_t)15));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1870,17 +1936,11 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
     const int used = pool_need(nleaf, kWarps * nslot, nops);
     const PrimRec* sl = slw;
     const LeafTab* lt = ltw;
-    __syncthreads();  // the previous tile is done with the pool
-    stage_tile(P, J.prims, 0, nleaf, nullptr, slw, tid);
-    for (int q = tid; q < 2 * kWarps * nslot; q += kBlock) racc[q] = 0.f;  // rows and compensation
-    __syncthreads();
-    stage_slots(sl, nleaf, J.act, J.actc, ltw, tid);
     // After the rows: pair columns (tiles with graph or polygon leaves), then
     // per-thread accumulator columns (nslot x kBlock) when they take at most
     // half of what is left, then the factor tables.  The binner checked that
     // the rows and the pair columns leave at least kPoolSpare floats.
-    bool pairs = false;
-    for (int l = 0; l < nleaf; ++l) pairs |= sl[l].kind == kGraph || sl[l].kind == kPolygon;
+    const bool pairs = P->pairs != 0;
     float* pv = pool + used;
     int* pk = reinterpret_cast<int*>(pv + kMaxPairs * kBlock);
     const int used2 = used + (pairs ? kPairFloats : 0);
@@ -1890,6 +1950,12 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
     float* tabw = pt ? tcol + nslot * kBlock : tcol;
     const int tcap = pt ? cap - nslot * kBlock : cap;
     const float* tab = tabw;
+    __syncthreads();  // the previous tile is done with the pool
+    // the program's ops go to the tape's space until the descriptors are made
+    uint16_t* sops = reinterpret_cast<uint16_t*>(tape);
+    stage_tile(P, J.prims, nops, nleaf, sops, slw, tid);
+    stage_slots(P, J.prims, nleaf, J.act, J.actc, ltw, tid);
+    for (int q = tid; q < 2 * kWarps * nslot; q += kBlock) racc[q] = 0.f;  // rows and compensation
     if (pt)
       for (int q = 0; q < nslot; ++q) tcol[q * kBlock + tid] = 0.f;  // this thread's column
     __syncthreads();
@@ -1916,11 +1982,12 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
         if ((f & tACT) && (f & (tOK | tBOX)) != (tOK | tBOX)) all = true;
       }
       all = __any_sync(0xffffffffu, all);
-      const int ndl = descs_warp(P->ops, nops, lt, desc, dl, lane);
+      const int ndl = descs_warp(sops, nops, lt, desc, dl, lane);
       if (lane == 0) {
         sbase[nleaf] = base;
         misc[1] = all;
         misc[2] = ndl;
+        misc[3] = 1;  // z collapse until a thread finds otherwise
       }
     }
     __syncthreads();
@@ -1930,8 +1997,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
     activity_axes(lt, nleaf, g, tab, act1, tid);
     bool okY, okZ;
     uniform_axes(lt, nleaf, g, tab, true, tid, okY, okZ);
+    if (!okZ) misc[3] = 0;  // set to 1 by warp 0 before the last barrier
     const bool uy = __syncthreads_and(okY);
-    const bool uz = __syncthreads_and(okZ);
+    const bool uz = misc[3] != 0;
     float* wacc = racc + warp * nslot;
     float* wcmp = rcmp + warp * nslot;
     const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
