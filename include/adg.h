@@ -249,8 +249,10 @@ adg_status adg_design_stats(adg_ctx *ctx, adg_design *design, void *stream, adg_
  * adg_profile_read waits for the recorded events and returns, per kernel
  * (index ADG_K_*), the launch count and the summed device time; `reset`
  * clears the accumulators. */
-enum { ADG_K_BIN = 0, ADG_K_BUILD = 1, ADG_K_VJP = 2, ADG_K_FINALIZE = 3, ADG_K_PREPARE = 4,
-       ADG_K_FILL = 5, ADG_K_DENSE = 6 /* field stream + its fixed-order sum */,
+enum { ADG_K_BIN = 0, ADG_K_BUILD = 1, ADG_K_VJP = 2, ADG_K_FINALIZE = 3,
+       ADG_K_PREPARE = 4 /* reserved, not launched: the finalize clears the partials */,
+       ADG_K_FILL = 5 /* reserved, not launched: the build fills the constant tiles */,
+       ADG_K_DENSE = 6 /* field stream + its fixed-order sum */,
        ADG_K_COUNT = 8 };
 typedef struct {
   int64_t launches[ADG_K_COUNT];

@@ -151,10 +151,12 @@ struct adg_design {
   TileProg* d_progs = nullptr;
   unsigned char* d_tclass = nullptr;
   int* d_list = nullptr;
-  int* d_counters = nullptr;  // two sets of 4; the binning alternates between them
+  int* d_counters = nullptr;  // two sets of 4 (the binning alternates between them),
+                              // then the active samples of the last VJP
   int gen = 0;                // the set of the last binning
-  float* d_partial = nullptr;
+  float* d_partial = nullptr;  // all zero between calls (the finalize clears what it sums)
   size_t partial_cap = 0;
+  bool partial_dirty = false;  // a call that enqueued the VJP did not complete its enqueue
   Job* d_job = nullptr;  // the one-job table of single-design calls
   Job job{};
   // dense field stream (adg_grad_dense): per-chunk partials and work counter
@@ -333,8 +335,8 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_progs, sizeof(TileProg) * (size_t)d->g.T);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_tclass, (size_t)d->g.T);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_list, sizeof(int) * (size_t)d->g.T);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_counters, sizeof(int) * 8);
-  if (e == cudaSuccess) e = cudaMemset(d->d_counters, 0, sizeof(int) * 8);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_counters, sizeof(int) * 9);
+  if (e == cudaSuccess) e = cudaMemset(d->d_counters, 0, sizeof(int) * 9);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_job, sizeof(Job));
   if (e != cudaSuccess) {
     free_design(d);
@@ -395,6 +397,9 @@ adg_status ensure_records(adg_design* d, const double* h_params, cudaStream_t s,
   return ADG_OK;
 }
 
+// The partial buffer starts zeroed and stays so: the VJP writes only
+// partials that the finalize then sums and clears.  A call whose enqueue
+// stopped between the two leaves it dirty; the next call clears it.
 adg_status ensure_partials(adg_design* d, cudaStream_t s) {
   if (d->part_total > d->partial_cap) {
     if (d->d_partial) CU(cudaFreeAsync(d->d_partial, s));
@@ -402,6 +407,11 @@ adg_status ensure_partials(adg_design* d, cudaStream_t s) {
     const size_t cap = d->part_total + d->part_total / 2 + 1024;
     CU(cudaMallocAsync((void**)&d->d_partial, cap * sizeof(float), s));
     d->partial_cap = cap;
+    d->partial_dirty = true;
+  }
+  if (d->partial_dirty) {
+    CU(cudaMemsetAsync(d->d_partial, 0, d->partial_cap * sizeof(float), s));
+    d->partial_dirty = false;
   }
   return ADG_OK;
 }
@@ -425,19 +435,16 @@ Job design_job(adg_design* d) {
   J.list = d->d_list;
   J.counters = d->d_counters + 4 * d->gen;
   J.counters_next = d->d_counters + 4 * (d->gen ^ 1);
+  J.counters_last = d->d_counters + 8;
   J.partial = d->d_partial;
   J.partial_n = (long long)d->part_total;
   J.nparam = d->n_params;
   return J;
 }
 
-// Enqueue prepare -> bin -> build / VJP -> finalize for a job table.
+// Enqueue bin -> build / VJP -> finalize for a job table.
 adg_status run_jobs(adg_ctx* ctx, const Job* d_jobs, const JobTotals& t, bool any_bin,
                     bool any_build, bool any_grad, int max_tiles, cudaStream_t s) {
-  if (any_grad) {  // partials and the active-sample counter
-    ProfScope ps(ctx, ADG_K_PREPARE, s);
-    CU(launch_prepare(d_jobs, t, s));
-  }
   if (any_bin) {
     ProfScope ps(ctx, ADG_K_BIN, s);
     CU(launch_bin(d_jobs, t, ctx->d_err, s));
@@ -477,6 +484,7 @@ adg_status run_single(adg_ctx* ctx, adg_design* d, const double* h_params, float
   J.grad = d_grad;
   J.partial_n = grad ? (long long)d->part_total : 0;
   d->job = J;
+  if (grad) d->partial_dirty = true;  // until the finalize is enqueued
   CU(cudaMemcpyAsync(d->d_job, &d->job, sizeof(Job), cudaMemcpyHostToDevice, s));
   JobTotals t{};
   t.njobs = 1;
@@ -484,8 +492,9 @@ adg_status run_single(adg_ctx* ctx, adg_design* d, const double* h_params, float
   t.bin_blocks = t.tiles_padded / 128;
   t.fill_blocks = d_eps ? (d->g.C * d->g.nz * d->g.ny + kFillRows - 1) / kFillRows : 0;
   t.params = grad ? d->n_params : 0;
-  t.partials = J.partial_n;
-  return run_jobs(ctx, d->d_job, t, rebin, d_eps != nullptr, grad, d->g.T, s);
+  st = run_jobs(ctx, d->d_job, t, rebin, d_eps != nullptr, grad, d->g.T, s);
+  if (st == ADG_OK) d->partial_dirty = false;
+  return st;
 }
 
 }  // namespace
@@ -644,7 +653,6 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   Job* hj = reinterpret_cast<Job*>(hb + o_jobs);
   size_t po = 0, ado = 0, afo = 0;
   int tile_base = 0, param_base = 0, max_tiles = 0, row_base = 0;
-  long long partial_base = 0;
   bool any_build = false, any_grad = false;
   uint64_t sig = mix(0, (uint64_t)arena_id);
   sig = mix(sig, (uint64_t)n);
@@ -677,13 +685,14 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
       J.va.G = it.d_G;
     }
     J.partial_n = J.do_grad ? (long long)d->part_total : 0;
-    J.partial_base = partial_base;
     J.param_base = param_base;
     J.tile_base = tile_base;
     J.row_base = row_base;
     if (J.do_build) row_base += (d->g.C * d->g.nz * d->g.ny + kFillRows - 1) / kFillRows;
-    partial_base += J.partial_n;
-    if (J.do_grad) param_base += d->n_params;
+    if (J.do_grad) {
+      param_base += d->n_params;
+      d->partial_dirty = true;  // until the finalize is enqueued
+    }
     tile_base += ((d->g.T + 127) / 128) * 128;
     max_tiles = std::max(max_tiles, d->g.T);
     any_build = any_build || J.do_build;
@@ -701,11 +710,9 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   t.bin_blocks = tile_base / 128;
   t.fill_blocks = row_base;
   t.params = param_base;
-  t.partials = partial_base;
   sig = mix(sig, (uint64_t)bytes);
   sig = mix(sig, (uint64_t)tile_base);
   sig = mix(sig, (uint64_t)param_base);
-  sig = mix(sig, (uint64_t)std::min<long long>((partial_base + 255) / 256, 4096));
   build_blocks_per_sm(t.njobs);  // kernel attributes are set before any capture
   vjp_blocks_per_sm(t.njobs);
   const bool graph = (flags & ADG_BATCH_GRAPH) && !ctx->prof;
@@ -738,6 +745,8 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
                              any_grad, max_tiles, s);
     if (st != ADG_OK) return st;
   }
+  for (int i = 0; i < n; ++i)  // the finalize of every gradient item is enqueued
+    if (items[i].ops & (ADG_BATCH_GRAD | ADG_BATCH_GRAD_REAL)) items[i].design->partial_dirty = false;
   CU(cudaEventRecord(A.done, s));
   A.used = true;
   cudaEvent_t ev = nullptr;
@@ -802,13 +811,14 @@ extern "C" adg_status adg_design_stats(adg_ctx* ctx, adg_design* d, void* stream
   if (!ctx || !d || !out) return fail(ADG_EINVAL, "adg_design_stats: NULL argument");
   CU(cudaSetDevice(ctx->device));
   CU(cudaStreamSynchronize((cudaStream_t)stream));
-  int c[4] = {0, 0, 0, 0};
+  int c[4] = {0, 0, 0, 0}, last = 0;
   CU(cudaMemcpy(c, d->d_counters + 4 * d->gen, sizeof(c), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(&last, d->d_counters + 8, sizeof(int), cudaMemcpyDeviceToHost));
   out->tiles = d->g.T;
   out->program_tiles = c[0];
   out->max_ops = c[1];
   out->band_cells = c[2];
-  out->active_samples = c[3];
+  out->active_samples = last;
   out->cells = (int64_t)d->g.nx * d->g.ny * d->g.nz;
   out->tile[0] = 1 << d->g.lx;
   out->tile[1] = 1 << d->g.ly;

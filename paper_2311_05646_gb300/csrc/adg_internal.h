@@ -156,14 +156,14 @@ struct Job {
   int* list;
   int* counters;       // [band tiles, longest program, band cells, active samples]
   int* counters_next;  // the other set: zeroed by this binning for the next one
+  int* counters_last;  // active samples of the last VJP (moved here by the finalize)
   // outputs and inputs of the operations
   float* fill;
   float* eps;
   VjpArgs va;
   float* partial;
   float* grad;
-  long long partial_n;     // partials to zero before the VJP
-  long long partial_base;  // prefix over the table (zeroing kernel)
+  long long partial_n;  // partials of the job (zero between calls: the finalize clears them)
   int nparam;
   int param_base;  // prefix over the table (finalize)
   int tile_base;   // prefix over the table, multiple of 128 (binner blocks)
@@ -179,12 +179,10 @@ struct JobTotals {
   int bin_blocks;        // sum over binned jobs of ceil(T / 128)
   int tiles_padded;      // tile_base of one past the last job
   int params;            // sum of nparam over gradient jobs
-  long long partials;    // sum of partial_n over gradient jobs
 };
 
 constexpr int kMaxJobs = 1024;  // jobs in one table (one batch)
 
-cudaError_t launch_prepare(const Job* jobs, const JobTotals& t, cudaStream_t s);
 cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s);
 cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s);
 // gtape: kTapeBlockFloats floats per block for gtape_blocks blocks; the grid

@@ -13,7 +13,8 @@
 //               adjoints, primitive derivatives, warp-shuffle reduction per
 //               (primitive, scalar) slot into compensated block partials.
 //   k_finalize  per parameter: fixed-order sum of the block partials through
-//               the parameter map (deterministic, FP64).
+//               the parameter map (deterministic, FP64); it clears every
+//               partial it reads, so the next VJP starts from zero.
 #include <limits.h>
 #include <math.h>
 #include <stdint.h>
@@ -582,33 +583,6 @@ __device__ __forceinline__ int job_by_param(const Job* jobs, int n, int idx) {
   return lo;
 }
 
-__device__ __forceinline__ int job_by_partial(const Job* jobs, int n, long long idx) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    const Job& J = jobs[mid];
-    if (J.partial_base + (J.do_grad ? J.partial_n : 0) > idx) hi = mid; else lo = mid + 1;
-  }
-  return lo;
-}
-
-// Zero what the binner and the VJP accumulate into: the counters of jobs that
-// re-bin and the partials of jobs that take a gradient.
-__global__ void k_prepare(const Job* __restrict__ jobs, int njobs) {
-  // the partial count comes from the table itself (graph replays reuse the grid)
-  const Job& L = jobs[njobs - 1];
-  const long long npart = L.partial_base + (L.do_grad ? L.partial_n : 0);
-  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = i0; i < njobs; i += stride) {
-    if (jobs[i].do_grad) jobs[i].counters[3] = 0;  // active VJP samples
-  }
-  for (long long i = i0; i < npart; i += stride) {
-    const Job& J = jobs[job_by_partial(jobs, njobs, i)];
-    J.partial[i - J.partial_base] = 0.f;
-  }
-}
-
 // One thread per tile; the block's 128 tiles belong to one job (tile ranges
 // are padded to multiples of 128).
 constexpr int kChainSmem = 1024, kPrimSmem = 96;
@@ -1087,6 +1061,8 @@ struct TileLoc {
 static_assert(sizeof(LeafTab) == kLeafTabBytes, "pool accounting");
 // job-prefix entries in shared memory: a class for small tables, one for any
 __host__ __device__ constexpr int spre_len(int njobs) { return (njobs + 16) & ~15; }
+constexpr int kFillWarps = 1;  // build: warps that stream constant-tile rows beside the band warps
+constexpr int kBuildThreads = kBlock + 32 * kFillWarps;
 constexpr size_t kBuildFixed = (size_t)kMaxDepth * kBlock * 4 + (size_t)kBuildPool * 4 +
                                kMaxOps * 16 + kMaxOps * 2 + 16;
 size_t build_smem(int njobs) { return kBuildFixed + 2 * (size_t)spre_len(njobs) * 4; }
@@ -1119,11 +1095,12 @@ __device__ __forceinline__ void job_prefix(const Job* jobs, int njobs, bool grad
                                            int* rpre = nullptr, int nfill = 0) {
   __shared__ int wsum[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool part = tid < kBlock;  // threads past the first kBlock only meet the barriers
   int run = 0;
   for (int b0 = 0; b0 < njobs; b0 += kBlock) {
     const int j = b0 + tid;
     int cnt = 0;
-    if (j < njobs) {
+    if (part && j < njobs) {
       const Job& J = jobs[j];
       if (grad ? J.do_grad : J.do_build) cnt = J.counters[0];
       if (rpre) rpre[j] = J.row_base;
@@ -1134,11 +1111,11 @@ __device__ __forceinline__ void job_prefix(const Job* jobs, int njobs, bool grad
       const int u = __shfl_up_sync(0xffffffffu, inc, o);
       if (lane >= o) inc += u;
     }
-    if (lane == 31) wsum[warp] = inc;
+    if (part && lane == 31) wsum[warp] = inc;
     __syncthreads();
     int off = run;
-    for (int w = 0; w < warp; ++w) off += wsum[w];
-    if (j < njobs) spre[j] = off + inc - cnt;
+    for (int w = 0; w < warp && w < kWarps; ++w) off += wsum[w];
+    if (part && j < njobs) spre[j] = off + inc - cnt;
     for (int w = 0; w < kWarps; ++w) run += wsum[w];
     __syncthreads();
   }
@@ -1160,11 +1137,11 @@ __device__ __forceinline__ int job_of(const int* spre, int njobs, int i) {
 }
 
 // Streaming fill of the constant tiles of one group of kFillRows x-rows: fill
-// = 0 or 1, eps = eps_bg or eps_fg, 16-byte stores, one warp per row (a store
-// instruction covers 512 contiguous bytes); band tiles are left to the band
-// evaluation.  All threads of a kBlock-thread block.
+// = 0 or 1, eps = eps_bg or eps_fg, 16-byte stores (a store instruction
+// covers 512 contiguous bytes); band tiles are left to the band evaluation.
+// One warp, row after row.
 __device__ __forceinline__ void fill_rows(const Job* __restrict__ jobs, int jb, int unit,
-                                          int tid) {
+                                          int lane) {
   const Job& J = jobs[jb];
   if (!J.do_build) return;
   const int nx = J.g.nx, ny = J.g.ny, nz = J.g.nz;
@@ -1175,8 +1152,7 @@ __device__ __forceinline__ void fill_rows(const Job* __restrict__ jobs, int jb, 
   float* __restrict__ eps = J.eps;
   const bool vec = (nx & 3) == 0 &&
                    ((reinterpret_cast<uintptr_t>(eps) | reinterpret_cast<uintptr_t>(fill)) & 15) == 0;
-  const int lane = tid & 31;
-  for (int wr = tid >> 5; wr < kFillRows; wr += kWarps) {
+  for (int wr = 0; wr < kFillRows; ++wr) {
     const int row = (unit - J.row_base) * kFillRows + wr;
     if (row >= rows) break;
     const int j = row % ny, k = (row / ny) % nz;
@@ -1413,7 +1389,21 @@ __device__ __forceinline__ void eval_stack2(const int4* desc, int nops, const fl
   r1 = b0;
 }
 
-// One band tile of the build (all threads of the block).
+// Barriers of the build's band warps (warps 0 .. kWarps-1; named barrier 1):
+// the fill warps of the block never wait on them.
+__device__ __forceinline__ void band_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kBlock) : "memory"); }
+__device__ __forceinline__ bool band_sync_and(bool p) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred a, b;\n\tsetp.ne.s32 a, %1, 0;\n\tbar.red.and.pred b, 1, %2, a;\n\t"
+      "selp.s32 %0, 1, 0, b;\n\t}"
+      : "=r"(r)
+      : "r"((int)p), "n"(kBlock)
+      : "memory");
+  return r != 0;
+}
+
+// One band tile of the build (the kBlock threads of the band warps).
 __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, int njobs,
                                                 const int* spre, int gi_, unsigned char* smem) {
   float* stk = reinterpret_cast<float*>(smem);  // stack of the deep-program fallback
@@ -1431,9 +1421,9 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
     const int nops = P->nops, nleaf = P->nleaf;
     const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
     const TilePool tp = carve_pool(pool, kBuildPool, nleaf, 0);
-    __syncthreads();  // the previous tile is done with the staged program
+    band_sync();  // the previous tile is done with the staged program
     stage_tile(P, J.prims, nops, nleaf, sops, tp.sl, tid);
-    __syncthreads();
+    band_sync();
     if (tid < 32) {
       tables_plan_warp(tp.sl, nleaf, g, false, tp.cap, tp.lt, tid);
       __syncwarp();
@@ -1443,14 +1433,14 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
         sdepth[1] = 1;  // z collapse until a thread finds otherwise
       }
     }
-    __syncthreads();
+    band_sync();
     tables_fill(tp.sl, nleaf, g, tp.lt, false, tx << g.lx, ty << g.ly, tz << g.lz, tp.tab, tid,
                 J.auxf, J.auxd);
-    __syncthreads();
+    band_sync();
     bool okY, okZ;
     uniform_axes(tp.lt, nleaf, g, tp.tab, false, tid, okY, okZ);
     if (!okZ) sdepth[1] = 0;
-    const bool uy = __syncthreads_and(okY);
+    const bool uy = band_sync_and(okY);
     const bool uz = sdepth[1] != 0;
     // evaluated lattice: x, then y (one row if y collapses), z, component
     const int lyr = uy ? 0 : g.ly, lzr = uz ? 0 : g.lz;
@@ -1522,26 +1512,35 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
 // their factor tables, the folded program run at every sample (two samples
 // per thread, register stack; a shared-memory stack for deeper programs) --
 // and the streaming fill of the constant tiles.
-__global__ void __launch_bounds__(kBlock, 6) k_build(const Job* __restrict__ jobs, int njobs,
-                                                   int nfill) {
+// five blocks of 160 threads per SM: 80 registers
+__global__ void __maxnreg__(80) k_build(const Job* __restrict__ jobs, int njobs, int nfill) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // layout: deep-program stack, pool, descriptors, ops, depth, job prefix
+  // layout: deep-program stack, pool, descriptors, ops, four words (depth,
+  // z flag, next fill unit), job prefix
   int* spre = reinterpret_cast<int*>(smem + (size_t)kMaxDepth * kBlock * 4 + (size_t)kBuildPool * 4 +
                                      kMaxOps * 16 + kMaxOps * 2) + 4;
   int* rpre = spre + spre_len(njobs);  // first fill unit of each job
+  int* snext = spre - 2;                 // the block's next fill unit (k)
   const int tid = threadIdx.x;
-  job_prefix(jobs, njobs, false, spre, rpre, nfill);
+  if (tid == 0) *snext = 0;
+  job_prefix(jobs, njobs, false, spre, rpre, nfill);  // ends with a barrier
   const int total = spre[njobs];
-  // Band tiles (issue-bound) and groups of constant-tile rows (store-bound)
-  // interleaved in every block, so that each SM holds both kinds of work.
+  // Warp-specialised: the band warps take band tiles (latency-bound, with
+  // their own barriers) while the fill warps stream the rows of constant
+  // tiles (store-bound), so that neither waits for the other.  The block's
+  // fill units (blockIdx.x + k G) are handed out by a shared counter; band
+  // warps that run out of band tiles take fill units too.  Each unit is
+  // written by exactly one warp, so the output does not depend on who.
   const int G = gridDim.x;
-  const int per = total > 0 ? max(1, (nfill + total - 1) / total) : nfill;
-  int gi_ = blockIdx.x, fu = blockIdx.x;
-  while (gi_ < total || fu < nfill) {
-    if (gi_ < total) build_band_tile(jobs, njobs, spre, gi_, smem);
-    gi_ += G;
-    for (int r = 0; r < per && fu < nfill; ++r, fu += G)
-      fill_rows(jobs, job_of(rpre, njobs, fu), fu, tid);
+  if (tid < kBlock)
+    for (int gi_ = blockIdx.x; gi_ < total; gi_ += G) build_band_tile(jobs, njobs, spre, gi_, smem);
+  const int lane = tid & 31;
+  while (true) {
+    int k = 0;
+    if (lane == 0) k = atomicAdd(snext, 1);
+    const int fu = blockIdx.x + __shfl_sync(0xffffffffu, k, 0) * G;
+    if (fu >= nfill) break;
+    fill_rows(jobs, job_of(rpre, njobs, fu), fu, lane);
   }
 }
 
@@ -2279,17 +2278,37 @@ __global__ void __launch_bounds__(256) k_dense_final(DenseArgs a) {
 // tile boxes, in a fixed order -- each warp takes every fourth partial of each
 // reference (compensated fp32 per lane), FP64 across lanes, references and
 // the four warps.
+// Also clears what the VJP accumulated: each (primitive, scalar) partial row
+// belongs to exactly one parameter, so the block that sums a row zeroes it,
+// and the first block of a job moves the active-sample count to
+// counters_last.
 __global__ void __launch_bounds__(128) k_finalize(const Job* __restrict__ jobs, int njobs, int nparams) {
   __shared__ double wsum[4];
   const int wid = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const Job& J = jobs[job_by_param(jobs, njobs, wid)];
   const int k = wid - J.param_base;
+  if (k == 0 && threadIdx.x == 0) {
+    *J.counters_last = J.counters[3];
+    J.counters[3] = 0;
+  }
   double total = 0.0;
   for (int r = J.ref_off[k]; r < J.ref_off[k + 1]; ++r) {
     const PrimRec& P = J.prims[J.ref_prim[r]];
-    const float* __restrict__ src = J.partial + P.part_off + (size_t)J.ref_qa[r] * P.npb;
+    float* src = J.partial + P.part_off + (size_t)J.ref_qa[r] * P.npb;
     float s = 0.f, c = 0.f;
-    for (int t = threadIdx.x; t < P.npb; t += 128) neumaier(s, c, __ldg(src + t));
+    // eight loads in flight per thread, summed in tile order; the nonzero
+    // ones (tiles the VJP wrote) are cleared
+    for (int t0 = threadIdx.x; t0 < P.npb; t0 += 8 * 128) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = t0 + u * 128 < P.npb ? src[t0 + u * 128] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (t0 + u * 128 < P.npb) {
+          neumaier(s, c, v[u]);
+          if (v[u] != 0.f) src[t0 + u * 128] = 0.f;
+        }
+    }
     double v = (double)s + (double)c;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -2320,7 +2339,7 @@ int build_blocks_per_sm(int njobs) {
   static int v[kMaxJobs + 1] = {};
   njobs = std::min(std::max(njobs, 1), kMaxJobs);
   if (!v[njobs]) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v[njobs], k_build, kBlock, build_smem(njobs));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v[njobs], k_build, kBuildThreads, build_smem(njobs));
     if (v[njobs] < 1) v[njobs] = 1;
   }
   return v[njobs];
@@ -2336,14 +2355,6 @@ int vjp_blocks_per_sm(int njobs) {
   return v[njobs];
 }
 
-cudaError_t launch_prepare(const Job* jobs, const JobTotals& t, cudaStream_t s) {
-  const long long work = std::max<long long>(t.partials, t.njobs);
-  if (work <= 0) return cudaSuccess;
-  const int blocks = (int)std::min<long long>((work + 255) / 256, 4096);
-  k_prepare<<<blocks, 256, 0, s>>>(jobs, t.njobs);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s) {
   if (t.tiles_padded <= 0) return cudaSuccess;
   k_bin<<<t.tiles_padded / 128, 128, kBinSmem, s>>>(jobs, t.njobs, err);
@@ -2352,7 +2363,7 @@ cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream
 
 cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s) {
   const int grid = sms * build_blocks_per_sm(t.njobs);
-  k_build<<<grid, kBlock, build_smem(t.njobs), s>>>(jobs, t.njobs, t.fill_blocks);
+  k_build<<<grid, kBuildThreads, build_smem(t.njobs), s>>>(jobs, t.njobs, t.fill_blocks);
   return cudaGetLastError();
 }
 

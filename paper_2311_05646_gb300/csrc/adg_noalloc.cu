@@ -151,7 +151,8 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
   const size_t o_err = take(sizeof(int));
   const size_t o_job = take(sizeof(Job));
-  const size_t o_cnt = take(8 * sizeof(int));  // this call's set and the one its binning clears
+  // this call's counter set, the one its binning clears, the moved active-sample count
+  const size_t o_cnt = take(9 * sizeof(int));
   const size_t o_chain = take(sizeof(int) * nchain);
   const size_t o_act = take(sizeof(int) * std::max(st.nact_table, 1));
   const size_t o_actc = take(sizeof(float) * std::max(st.nact_table, 1));
@@ -206,9 +207,11 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   unsigned char* d_tcls = base + o_tcls;
   float* d_part = reinterpret_cast<float*>(base + o_part);
   float* d_gtape = reinterpret_cast<float*>(base + o_gtape);
-  // ---- upload, clear, launch (prepare -> binner -> VJP -> finalize) ----
+  // ---- upload, clear, launch (binner -> VJP -> finalize) ----
   NACU(cudaMemsetAsync(d_err, 0, sizeof(int), s));
   NACU(cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), s));
+  // the partials' space held other tables in earlier calls
+  NACU(cudaMemsetAsync(d_part, 0, sizeof(float) * std::max<size_t>(part, 1), s));
   NACU(cudaMemcpyAsync(d_chain, H.chain, sizeof(int) * nchain, cudaMemcpyHostToDevice, s));
   if (st.nact_table) {
     NACU(cudaMemcpyAsync(d_act, H.act, sizeof(int) * st.nact_table, cudaMemcpyHostToDevice, s));
@@ -243,6 +246,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   J.list = d_list;
   J.counters = d_cnt;
   J.counters_next = d_cnt + 4;
+  J.counters_last = d_cnt + 8;
   J.partial = d_part;
   J.partial_n = (long long)part;
   J.grad = d_grad;
@@ -260,8 +264,6 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   t.tiles_padded = ((g.T + 127) / 128) * 128;
   t.bin_blocks = t.tiles_padded / 128;
   t.params = D->n_params;
-  t.partials = (long long)part;
-  NACU(launch_prepare(d_job, t, s));
   NACU(launch_bin(d_job, t, d_err, s));
   NACU(launch_vjp(d_job, t, d_err, sms, d_gtape, sms, s));
   NACU(launch_finalize(d_job, t, s));
