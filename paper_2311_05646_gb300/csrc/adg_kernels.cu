@@ -882,11 +882,12 @@ __global__ void __launch_bounds__(128) k_bin(const Job* __restrict__ jobs, int n
 }
 
 __device__ __forceinline__ void stage_tile(const TileProg* P, const PrimRec* prims, int nops,
-                                           int nleaf, uint16_t* sops, PrimRec* sl, int tid) {
+                                           int nleaf, uint16_t* sops, PrimRec* sl, int tid,
+                                           int nthr = kBlock) {
   if (sops)
-    for (int q = tid; q < nops; q += kBlock) sops[q] = P->ops[q];
+    for (int q = tid; q < nops; q += nthr) sops[q] = P->ops[q];
   constexpr int W = sizeof(PrimRec) / 16;
-  for (int q = tid; q < nleaf * W; q += kBlock) {
+  for (int q = tid; q < nleaf * W; q += nthr) {
     const int l = q / W, w = q - l * W;
     reinterpret_cast<int4*>(sl + l)[w] = reinterpret_cast<const int4*>(prims + P->leaf[l])[w];
   }
@@ -908,23 +909,6 @@ struct __align__(16) LeafTab {
 // LeafTab.d.w flags
 constexpr int tOK = 1, tBOX = 2, tACT = 4;  // tabled, box, drives some parameter
 constexpr int tKEYS = 8;                     // bits 8..13: box scalars driving a parameter
-
-// All threads: the accumulator slot and map coefficient of each scalar of the
-// box (6) and circle (5) leaves, and of a rigid polygon's z0, z1 and (shared)
-// vertex x, y scalars (staged in parallel: these are global reads).
-__device__ __forceinline__ void stage_slots(const TileProg* P, const PrimRec* prims, int nleaf,
-                                            const int* act, const float* actc, LeafTab* lt,
-                                            int tid) {
-  for (int q = tid; q < nleaf * 6; q += kBlock) {
-    const int l = q / 6, k = q - l * 6;
-    const PrimRec& R = prims[P->leaf[l]];  // read from the records, not the staged copy
-    const int kind = R.kind;
-    const bool keyed = kind == kBox || (kind == kCircle && k < 5) ||
-                       (kind == kPolygon && (R.flags & kPolyRigid) && k < 4);
-    lt[l].slot[k] = keyed ? __ldg(act + R.act_off + k) : -1;
-    lt[l].coef[k] = keyed ? __ldg(actc + R.act_off + k) : 0.f;
-  }
-}
 
 // Warp 0: table offsets for the tile's leaves from prefix sums over the
 // lanes (a leaf whose tables would pass `cap` is evaluated directly); with
@@ -1729,18 +1713,93 @@ __device__ __forceinline__ void activity_axes(const LeafTab* lt, int nleaf, cons
 }
 
 // ---- VJP helpers ---------------------------------------------------------------
-// Warp 0: one descriptor per op (pushes as for the build; logic ops carry
-// their operand positions in y, z) and, in program order, the positions that
-// push a parameter-driven leaf (pos | leaf << 8).  Returns their number.
-__device__ __forceinline__ int descs_warp(const uint16_t* ops, int nops,
-                                          const LeafTab* lt, int4* desc, int* dl, int lane) {
+// Warp 0 of the VJP, straight from the records in global memory (while the
+// other warps stage them): per leaf (one lane each) the accumulator slot and
+// map coefficient of each keyed scalar -- the box's 6, the circle's 5, a
+// rigid polygon's z0, z1 and shared vertex x, y -- the table offsets with
+// derivatives (prefix over the lanes; a leaf past `cap` is evaluated
+// directly) and flags, the slot bases (prefix of nact), the all-active flag,
+// and the op descriptors with the parameter-driven pushes.  Writes lt,
+// sbase, desc, dl and misc[1..3].
+__device__ __forceinline__ void vjp_plan_warp(const TileProg* P, const Job& J, int nleaf, int nops,
+                                              int cap, LeafTab* lt, int4* desc, int* dl,
+                                              int* sbase, int* misc, int lane) {
+  const GridDev& g = J.g;
+  const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
+  uint16_t opw[(kMaxOps + 31) / 32];  // the program, one op per lane and round
+#pragma unroll
+  for (int i = 0; i < (kMaxOps + 31) / 32; ++i) {
+    const int pos = i * 32 + lane;
+    opw[i] = pos < nops ? P->ops[pos] : (uint16_t)0;
+  }
+  int tbase = 0, sb = 0;
+  bool all = false;
+  for (int l0 = 0; l0 < nleaf; l0 += 32) {
+    const int l = l0 + lane;
+    const bool on = l < nleaf;
+    int kind = 0, flags = 0, nact = 0, aoff = 0;
+    if (on) {
+      const PrimRec* R = J.prims + P->leaf[l];
+      kind = R->kind;
+      flags = R->flags;
+      nact = R->nact;
+      aoff = R->act_off;
+    }
+    int keys = 0;
+    if (on) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const bool keyed = kind == kBox || (kind == kCircle && k < 5) ||
+                           (kind == kPolygon && (flags & kPolyRigid) && k < 4);
+        const int slot = keyed ? __ldg(J.act + aoff + k) : -1;
+        lt[l].slot[k] = slot;
+        lt[l].coef[k] = keyed ? __ldg(J.actc + aoff + k) : 0.f;
+        if (slot >= 0) keys |= tKEYS << k;
+      }
+    }
+    const bool box = on && kind == kBox;
+    const int need = !on ? 0 : (box ? 3 * C * (TX + TY + TZ) : C * TX * TY + 3 * C * TZ);
+    int inc = need, ninc = on ? nact : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      const int u = __shfl_up_sync(0xffffffffu, ninc, o);
+      if (lane >= o) { inc += t; ninc += u; }
+    }
+    const int off = tbase + inc - need;
+    tbase += __shfl_sync(0xffffffffu, inc, 31);
+    if (on) sbase[l] = sb + ninc - nact;
+    sb += __shfl_sync(0xffffffffu, ninc, 31);
+    if (!on) continue;
+    int4 v = make_int4(-1, -1, -1, -1), d = make_int4(-1, -1, -1, 0);
+    if (off + need <= cap) {
+      if (box) {
+        v.x = off; v.y = v.x + C * TX; v.z = v.y + C * TY;
+        d.x = v.z + C * TZ; d.y = d.x + 2 * C * TX; d.z = d.y + 2 * C * TY;
+      } else {
+        v.w = off; v.z = v.w + C * TX * TY;
+        d.z = v.z + C * TZ;
+      }
+      d.w |= tOK;
+    }
+    if (box) d.w |= tBOX | keys;
+    if (nact > 0) d.w |= tACT;
+    lt[l].v = v;
+    lt[l].d = d;
+    if ((d.w & tACT) && (d.w & (tOK | tBOX)) != (tOK | tBOX)) all = true;
+  }
+  all = __any_sync(0xffffffffu, all);
+  __syncwarp();  // lt of every leaf, for the descriptors
   int n = 0;
-  for (int p0 = 0; p0 < nops; p0 += 32) {
+#pragma unroll
+  for (int i = 0; i < (kMaxOps + 31) / 32; ++i) {
+    const int p0 = i * 32;
+    if (p0 >= nops) break;
     const int pos = p0 + lane;
     bool act = false;
     int leaf = 0;
     if (pos < nops) {
-      const FoldOp fo = fold_op(ops[pos]);
+      const FoldOp fo = fold_op(opw[i]);
       if (fo.code == fPush) {
         const int f = lt[fo.a].d.w;
         const int4 v = lt[fo.a].v;
@@ -1756,7 +1815,12 @@ __device__ __forceinline__ int descs_warp(const uint16_t* ops, int nops,
     if (act) dl[n + __popc(m & ((1u << lane) - 1u))] = pos | (leaf << 8);
     n += __popc(m);
   }
-  return n;
+  if (lane == 0) {
+    sbase[nleaf] = sb;
+    misc[1] = all;
+    misc[2] = n;
+    misc[3] = 1;  // z collapse until a thread finds otherwise
+  }
 }
 
 template <int LOGIC>
@@ -1950,45 +2014,16 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
     const int tcap = pt ? cap - nslot * kBlock : cap;
     const float* tab = tabw;
     __syncthreads();  // the previous tile is done with the pool
-    // the program's ops go to the tape's space until the descriptors are made
-    uint16_t* sops = reinterpret_cast<uint16_t*>(tape);
-    stage_tile(P, J.prims, nops, nleaf, sops, slw, tid);
-    stage_slots(P, J.prims, nleaf, J.act, J.actc, ltw, tid);
-    for (int q = tid; q < 2 * kWarps * nslot; q += kBlock) racc[q] = 0.f;  // rows and compensation
+    // warp 0 plans from the records in global memory while the other warps
+    // stage them and clear the accumulator rows
+    if (warp == 0) {
+      vjp_plan_warp(P, J, nleaf, nops, tcap, ltw, desc, dl, sbase, misc, lane);
+    } else {
+      stage_tile(P, J.prims, 0, nleaf, nullptr, slw, tid - 32, kBlock - 32);
+      for (int q = tid - 32; q < 2 * kWarps * nslot; q += kBlock - 32) racc[q] = 0.f;  // rows and compensation
+    }
     if (pt)
       for (int q = 0; q < nslot; ++q) tcol[q * kBlock + tid] = 0.f;  // this thread's column
-    __syncthreads();
-    if (warp == 0) {
-      tables_plan_warp(sl, nleaf, g, true, tcap, ltw, lane);
-      // (primitive, parameter) slot bases: exclusive prefix of nact
-      int base = 0;
-      bool all = false;
-      for (int l0 = 0; l0 < nleaf; l0 += 32) {
-        const int l = l0 + lane;
-        const int na = l < nleaf ? sl[l].nact : 0;
-        int inc = na;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int u = __shfl_up_sync(0xffffffffu, inc, o);
-          if (lane >= o) inc += u;
-        }
-        if (l < nleaf) sbase[l] = base + inc - na;
-        base += __shfl_sync(0xffffffffu, inc, 31);
-      }
-      __syncwarp();
-      for (int l = lane; l < nleaf; l += 32) {
-        const int f = lt[l].d.w;
-        if ((f & tACT) && (f & (tOK | tBOX)) != (tOK | tBOX)) all = true;
-      }
-      all = __any_sync(0xffffffffu, all);
-      const int ndl = descs_warp(sops, nops, lt, desc, dl, lane);
-      if (lane == 0) {
-        sbase[nleaf] = base;
-        misc[1] = all;
-        misc[2] = ndl;
-        misc[3] = 1;  // z collapse until a thread finds otherwise
-      }
-    }
     __syncthreads();
     tables_fill(sl, nleaf, g, lt, true, tx << g.lx, ty << g.ly, tz << g.lz, tabw, tid, J.auxf,
                 J.auxd);
