@@ -881,11 +881,10 @@ __global__ void __launch_bounds__(128) k_bin(const Job* __restrict__ jobs, int n
   }
 }
 
-__device__ __forceinline__ void stage_tile(const TileProg* P, const PrimRec* prims, int nops,
-                                           int nleaf, uint16_t* sops, PrimRec* sl, int tid,
-                                           int nthr = kBlock) {
-  if (sops)
-    for (int q = tid; q < nops; q += nthr) sops[q] = P->ops[q];
+// Threads [tid0, tid0 + nthr) of the block, one 16-byte word at a time:
+// the tile's primitive records into shared memory.
+__device__ __forceinline__ void stage_tile(const TileProg* P, const PrimRec* prims, int nleaf,
+                                           PrimRec* sl, int tid, int nthr) {
   constexpr int W = sizeof(PrimRec) / 16;
   for (int q = tid; q < nleaf * W; q += nthr) {
     const int l = q / W, w = q - l * W;
@@ -909,49 +908,6 @@ struct __align__(16) LeafTab {
 // LeafTab.d.w flags
 constexpr int tOK = 1, tBOX = 2, tACT = 4;  // tabled, box, drives some parameter
 constexpr int tKEYS = 8;                     // bits 8..13: box scalars driving a parameter
-
-// Warp 0: table offsets for the tile's leaves from prefix sums over the
-// lanes (a leaf whose tables would pass `cap` is evaluated directly); with
-// derivatives, the box key bits come from the staged slots.
-__device__ __forceinline__ void tables_plan_warp(const PrimRec* sl, int nleaf, const GridDev& g,
-                                                 bool derivs, int cap, LeafTab* lt, int lane) {
-  const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
-  const int m = derivs ? 3 : 1;
-  int base = 0;
-  for (int l0 = 0; l0 < nleaf; l0 += 32) {
-    const int l = l0 + lane;
-    const bool on = l < nleaf;
-    const bool box = on && sl[l].kind == kBox;
-    const int need = !on ? 0 : (box ? m * C * (TX + TY + TZ) : C * TX * TY + m * C * TZ);
-    int inc = need;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += t;
-    }
-    const int off = base + inc - need;
-    base += __shfl_sync(0xffffffffu, inc, 31);
-    if (!on) continue;
-    int4 v = make_int4(-1, -1, -1, -1), d = make_int4(-1, -1, -1, 0);
-    if (off + need <= cap) {
-      if (box) {
-        v.x = off; v.y = v.x + C * TX; v.z = v.y + C * TY;
-        if (derivs) { d.x = v.z + C * TZ; d.y = d.x + 2 * C * TX; d.z = d.y + 2 * C * TY; }
-      } else {
-        v.w = off; v.z = v.w + C * TX * TY;
-        if (derivs) d.z = v.z + C * TZ;
-      }
-      d.w |= tOK;
-    }
-    if (box) d.w |= tBOX;
-    if (sl[l].nact > 0) d.w |= tACT;
-    if (derivs && box)
-      for (int k = 0; k < 6; ++k)
-        if (lt[l].slot[k] >= 0) d.w |= (tKEYS << k);
-    lt[l].v = v;
-    lt[l].d = d;
-  }
-}
 
 // Axis factor of a box along axis `ax` at cell index i with offset off:
 // exact overlap, or the paper's sigma product; unbounded axes give 1.
@@ -1048,7 +1004,7 @@ __host__ __device__ constexpr int spre_len(int njobs) { return (njobs + 16) & ~1
 constexpr int kFillWarps = 1;  // build: warps that stream constant-tile rows beside the band warps
 constexpr int kBuildThreads = kBlock + 32 * kFillWarps;
 constexpr size_t kBuildFixed = (size_t)kMaxDepth * kBlock * 4 + (size_t)kBuildPool * 4 +
-                               kMaxOps * 16 + kMaxOps * 2 + 16;
+                               kMaxOps * 16 + 16;
 size_t build_smem(int njobs) { return kBuildFixed + 2 * (size_t)spre_len(njobs) * 4; }
 
 // Pool carve of one tile: staged leaves, descriptors, then (VJP) accumulators.
@@ -1245,42 +1201,6 @@ __device__ __forceinline__ void uniform_axes(const LeafTab* lt, int nleaf, const
 constexpr int kRegStack = 4;
 constexpr int dBox = 0, dPlane = 1, dDirect = 2, dLogic = 8;
 
-// Warp 0, after tables_plan: descriptors of the tile's ops (one op per lane)
-// and the largest stack depth the program reaches (a prefix sum of the
-// pushes and pops over the lanes); every lane returns it.
-__device__ __forceinline__ int plan_descs_warp(const uint16_t* sops, int nops, const LeafTab* lt,
-                                               int4* desc, int lane) {
-  int depth = 0, maxd = 0;
-  for (int p0 = 0; p0 < nops; p0 += 32) {
-    const int pos = p0 + lane;
-    int delta = 0;
-    if (pos < nops) {
-      const FoldOp fo = fold_op(sops[pos]);
-      const int code = fo.code;
-      if (code == fPush) {
-        const int a = fo.a;
-        const int f = lt[a].d.w;
-        const int4 v = lt[a].v;
-        desc[pos] = !(f & tOK) ? make_int4(dDirect, a, 0, 0)
-                  : (f & tBOX) ? make_int4(dBox, v.x, v.y, v.z) : make_int4(dPlane, v.w, 0, v.z);
-        delta = 1;
-      } else {
-        desc[pos] = make_int4(dLogic + code, 0, 0, 0);
-        delta = code != fCompl ? -1 : 0;
-      }
-    }
-    int inc = delta;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += u;
-    }
-    maxd = max(maxd, __reduce_max_sync(0xffffffffu, depth + inc));
-    depth += __shfl_sync(0xffffffffu, inc, 31);
-  }
-  return maxd;
-}
-
 template <int LOGIC>
 __device__ __forceinline__ float logic_fwd(int code, float a, float b) {
   if (code == fUnion) return LOGIC == 0 ? (a + b - a * b) : fminf(1.f, a + b);
@@ -1373,6 +1293,79 @@ __device__ __forceinline__ void eval_stack2(const int4* desc, int nops, const fl
   r1 = b0;
 }
 
+// Warp 0 of a build band tile, straight from the records in global memory
+// (while the other band warps stage them): the leaves' value-table offsets
+// (prefix over the lanes; a leaf past `cap` is evaluated directly) and
+// flags, the op descriptors, and the largest stack depth of the program.
+__device__ __forceinline__ int build_plan_warp(const TileProg* P, const Job& J, int nleaf, int nops,
+                                               int cap, LeafTab* lt, int4* desc, int lane) {
+  const GridDev& g = J.g;
+  const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
+  uint16_t opw[(kMaxOps + 31) / 32];
+#pragma unroll
+  for (int i = 0; i < (kMaxOps + 31) / 32; ++i) {
+    const int pos = i * 32 + lane;
+    opw[i] = pos < nops ? P->ops[pos] : (uint16_t)0;
+  }
+  int tbase = 0;
+  for (int l0 = 0; l0 < nleaf; l0 += 32) {
+    const int l = l0 + lane;
+    const bool on = l < nleaf;
+    const int kind = on ? J.prims[P->leaf[l]].kind : -1;
+    const bool box = kind == kBox;
+    const int need = !on ? 0 : (box ? C * (TX + TY + TZ) : C * TX * TY + C * TZ);
+    int inc = need;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    const int off = tbase + inc - need;
+    tbase += __shfl_sync(0xffffffffu, inc, 31);
+    if (!on) continue;
+    int4 v = make_int4(-1, -1, -1, -1), d = make_int4(-1, -1, -1, 0);
+    if (off + need <= cap) {
+      if (box) { v.x = off; v.y = v.x + C * TX; v.z = v.y + C * TY; }
+      else { v.w = off; v.z = v.w + C * TX * TY; }
+      d.w |= tOK;
+    }
+    if (box) d.w |= tBOX;
+    lt[l].v = v;
+    lt[l].d = d;
+  }
+  __syncwarp();  // lt of every leaf, for the descriptors
+  int depth = 0, maxd = 0;
+#pragma unroll
+  for (int i = 0; i < (kMaxOps + 31) / 32; ++i) {
+    const int p0 = i * 32;
+    if (p0 >= nops) break;
+    const int pos = p0 + lane;
+    int delta = 0;
+    if (pos < nops) {
+      const FoldOp fo = fold_op(opw[i]);
+      if (fo.code == fPush) {
+        const int f = lt[fo.a].d.w;
+        const int4 v = lt[fo.a].v;
+        desc[pos] = !(f & tOK) ? make_int4(dDirect, fo.a, 0, 0)
+                  : (f & tBOX) ? make_int4(dBox, v.x, v.y, v.z) : make_int4(dPlane, v.w, 0, v.z);
+        delta = 1;
+      } else {
+        desc[pos] = make_int4(dLogic + fo.code, 0, 0, 0);
+        delta = fo.code != fCompl ? -1 : 0;
+      }
+    }
+    int inc = delta;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    maxd = max(maxd, __reduce_max_sync(0xffffffffu, depth + inc));
+    depth += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  return maxd;
+}
+
 // Barriers of the build's band warps (warps 0 .. kWarps-1; named barrier 1):
 // the fill warps of the block never wait on them.
 __device__ __forceinline__ void band_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kBlock) : "memory"); }
@@ -1393,8 +1386,7 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
   float* stk = reinterpret_cast<float*>(smem);  // stack of the deep-program fallback
   float* pool = stk + kMaxDepth * kBlock;
   int4* desc = reinterpret_cast<int4*>(pool + kBuildPool);
-  uint16_t* sops = reinterpret_cast<uint16_t*>(desc + kMaxOps);
-  int* sdepth = reinterpret_cast<int*>(sops + kMaxOps);
+  int* sdepth = reinterpret_cast<int*>(desc + kMaxOps);
   const int tid = threadIdx.x;
   {
     const int jb = job_of(spre, njobs, gi_);
@@ -1406,16 +1398,14 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
     const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
     const TilePool tp = carve_pool(pool, kBuildPool, nleaf, 0);
     band_sync();  // the previous tile is done with the staged program
-    stage_tile(P, J.prims, nops, nleaf, sops, tp.sl, tid);
-    band_sync();
-    if (tid < 32) {
-      tables_plan_warp(tp.sl, nleaf, g, false, tp.cap, tp.lt, tid);
-      __syncwarp();
-      const int depth = plan_descs_warp(sops, nops, tp.lt, desc, tid);
+    if (tid < 32) {  // warp 0 plans from the records while warps 1.. stage them
+      const int depth = build_plan_warp(P, J, nleaf, nops, tp.cap, tp.lt, desc, tid);
       if (tid == 0) {
         sdepth[0] = depth;
         sdepth[1] = 1;  // z collapse until a thread finds otherwise
       }
+    } else {
+      stage_tile(P, J.prims, nleaf, tp.sl, tid - 32, kBlock - 32);
     }
     band_sync();
     tables_fill(tp.sl, nleaf, g, tp.lt, false, tx << g.lx, ty << g.ly, tz << g.lz, tp.tab, tid,
@@ -1499,10 +1489,10 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
 // five blocks of 160 threads per SM: 80 registers
 __global__ void __maxnreg__(80) k_build(const Job* __restrict__ jobs, int njobs, int nfill) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // layout: deep-program stack, pool, descriptors, ops, four words (depth,
-  // z flag, next fill unit), job prefix
+  // layout: deep-program stack, pool, descriptors, four words (depth, z flag,
+  // next fill unit), job prefix
   int* spre = reinterpret_cast<int*>(smem + (size_t)kMaxDepth * kBlock * 4 + (size_t)kBuildPool * 4 +
-                                     kMaxOps * 16 + kMaxOps * 2) + 4;
+                                     kMaxOps * 16) + 4;
   int* rpre = spre + spre_len(njobs);  // first fill unit of each job
   int* snext = spre - 2;                 // the block's next fill unit (k)
   const int tid = threadIdx.x;
@@ -2019,7 +2009,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
     if (warp == 0) {
       vjp_plan_warp(P, J, nleaf, nops, tcap, ltw, desc, dl, sbase, misc, lane);
     } else {
-      stage_tile(P, J.prims, 0, nleaf, nullptr, slw, tid - 32, kBlock - 32);
+      stage_tile(P, J.prims, nleaf, slw, tid - 32, kBlock - 32);
       for (int q = tid - 32; q < 2 * kWarps * nslot; q += kBlock - 32) racc[q] = 0.f;  // rows and compensation
     }
     if (pt)
