@@ -474,6 +474,77 @@ __device__ __forceinline__ int classify(const PrimRec& P, const float lo[3], con
   return cBND;
 }
 
+// The same classification by a whole warp (every lane, same result): a
+// polygon's edges or a graph's breakpoints spread over the lanes (the
+// binner's walk hands these kinds to the warp; one lane takes the others).
+__device__ __forceinline__ int classify_warp(const PrimRec& P, const float lo[3],
+                                             const float hi[3], const double* auxd,
+                                             const float* auxf, int lane) {
+  if (P.kind != kPolygon && P.kind != kGraph) return classify(P, lo, hi, auxd, auxf);
+  int z = cIN;
+  if (P.flags & kBoundZ) z = cls_exact(P.ai[4], P.af[4], P.ai[5], P.af[5], lo[2], hi[2]);
+  if (z == cOUT) return cOUT;
+  if (P.kind == kPolygon) {
+    const int N = P.naux;
+    const float* E = auxf + P.auxf_off;
+    const float lx = lo[0] - (float)P.ai[0], hx = hi[0] - (float)P.ai[0];
+    const float ly = lo[1] - (float)P.ai[1], hy = hi[1] - (float)P.ai[1];
+    const float b = P.band + kMargin;
+    bool out = false, all_in = true;
+    for (int e = lane; e < N; e += 32) {
+      const float* Ee = E + kPolyEdgeFloats * e;
+      const float nx = Ee[4], ny = Ee[6], rx = Ee[0], ry = Ee[2];
+      const float ax = nx >= 0.f ? nx * (lx - rx) : nx * (hx - rx);
+      const float bx = nx >= 0.f ? nx * (hx - rx) : nx * (lx - rx);
+      const float ay = ny >= 0.f ? ny * (ly - ry) : ny * (hy - ry);
+      const float by = ny >= 0.f ? ny * (hy - ry) : ny * (ly - ry);
+      const float dmin = ax + ay, dmax = bx + by;
+      if (dmax < -b) out = true;
+      if (dmin <= b) all_in = false;
+    }
+    if (__any_sync(0xffffffffu, out)) return cOUT;
+    return __all_sync(0xffffffffu, all_in) ? cls_and(cIN, z) : cBND;
+  }
+  // graph: f at both ends of the tile's x range (segment found by counting
+  // breakpoints, as the sequential search does) and at the interior ones
+  const int M = P.naux;
+  const double* X = auxd + P.auxd_off;
+  const double* Y = X + M;
+  double fmn = 1e300, fmx = -1e300;
+  for (int e = 0; e < 2; ++e) {
+    const double x = e ? hi[0] : lo[0];
+    double f;
+    if (x <= X[0]) f = Y[0];
+    else if (x >= X[M - 1]) f = Y[M - 1];
+    else {
+      int j = 0;  // the number of breakpoints 1 .. M-2 at or left of x
+      for (int k0 = 1; k0 < M - 1; k0 += 32) {
+        const int k = k0 + lane;
+        j += __popc(__ballot_sync(0xffffffffu, k < M - 1 && x >= X[k]));
+      }
+      f = Y[j] + (Y[j + 1] - Y[j]) * (x - X[j]) / (X[j + 1] - X[j]);
+    }
+    fmn = fmin(fmn, f);
+    fmx = fmax(fmx, f);
+  }
+  for (int j = lane; j < M; j += 32)
+    if (X[j] > lo[0] && X[j] < hi[0]) { fmn = fmin(fmn, Y[j]); fmx = fmax(fmx, Y[j]); }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fmn = fmin(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
+    fmx = fmax(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
+  }
+  const float b = P.band + kMargin;
+  if (!(P.flags & kGraphAbove)) {
+    if ((float)fmx - lo[1] < -b) return cOUT;
+    if ((float)fmn - hi[1] > b) return cls_and(cIN, z);
+  } else {
+    if (hi[1] - (float)fmn < -b) return cOUT;
+    if (lo[1] - (float)fmx > b) return cls_and(cIN, z);
+  }
+  return cBND;
+}
+
 // Vertex derivatives of one Poly2D leaf at one sample, accumulated edge by
 // edge.  s = zf prod_e sigma(k d_e); d s / d d_e uses the product of the other
 // factors (with an exact zero count, no division by zero).  Each edge adds to
@@ -546,8 +617,8 @@ __device__ __noinline__ void poly_accumulate(const PrimRec& P, const Cell& c, fl
 
 // --------------------------------------------------------------- kernels ---
 // Fold-stack entry (16 bits): kind (0 = const 0, 1 = const 1, 2 = expression)
-// | root << 2 | start << 8 (root: position of the expression's last op;
-// start: its first; both < kMaxOps <= 64).
+// | root << 2 | start << 9 (root: position of the expression's last op;
+// start: its first; 7-bit fields, both < kMaxOps).
 __device__ __forceinline__ int mkE(int root, int start) { return 2 | (root << 2) | (start << 9); }
 
 // Folded op words (code 2 bits, operands 7 bits; complement = difference(kOne, b)).
@@ -583,220 +654,150 @@ __device__ __forceinline__ int job_by_param(const Job* jobs, int n, int idx) {
   return lo;
 }
 
-// One thread per tile; the block's 128 tiles belong to one job (tile ranges
-// are padded to multiples of 128).
-constexpr int kChainSmem = 1024, kPrimSmem = 96;
+// ---- binner: one warp per tile ------------------------------------------------
+// A block takes kBinWarps consecutive tiles of one job (y fastest: tiles that
+// differ only in y usually see the same primitives).  The chain is walked in
+// segments: the block first drops, for all its tiles at once, the push of a
+// primitive that misses the block's tile box together with a union or
+// difference right after it (union(A, 0) = difference(A, 0) = A); then each
+// warp walks the rest for its tile 32 words at a time -- the lanes test the
+// tile box, drop the same pairs for the tile, and classify the remaining
+// pushes in parallel -- and lane 0 folds them with the constants (the fold
+// is sequential, the classification is not).
+constexpr int kBinWarps = 16;
+constexpr int kBinThreads = 32 * kBinWarps;
+constexpr int kBinSeg = 4096;  // chain words compacted per block pass
+static_assert(kBinSeg % kBinThreads == 0 && 128 % kBinWarps == 0, "binner layout");
+struct BinWarpBuf {
+  int word[32];              // the round's kept chain words
+  unsigned char cls[32];     // their classes (pushes)
+  uint16_t stk[kMaxDepth];   // fold stack below the three register entries
+  uint16_t leaf[kMaxLeaves];
+  uint16_t ops[kMaxOps];
+};
+constexpr size_t kBinSmem = sizeof(int) * kBinSeg + sizeof(BinWarpBuf) * kBinWarps;
 
-// The fold of one tile (one thread).  SMEM: the chain and the primitive
-// records are staged in the block's shared memory (small designs); otherwise
-// they are read through the read-only path.  The folded program is built in
-// shared memory and written out once, so the loop never stores to global.
-template <bool SMEM, bool SCHAIN>
-__device__ __forceinline__ void bin_tile(const Job& J, int t, int nchain, const int* schain,
-                                         const PrimRec* sprim, uint16_t (*stk)[128],
-                                         uint16_t (*sleaf)[128], uint16_t (*sop)[128], int* err) {
-  const int tid = threadIdx.x;
-  const int ntx = J.g.ntx, nty = J.g.nty;
-  const int lx = J.g.lx, ly = J.g.ly, lz = J.g.lz;
-  const int* __restrict__ chain = J.chain;
-  const PrimRec* __restrict__ prims = SMEM ? sprim : J.prims;
-  const double* __restrict__ auxd = J.auxd;
-  const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
-  const int i0 = tx << lx, j0 = ty << ly, k0 = tz << lz;
-  const int i1 = min(J.g.nx, (tx + 1) << lx), j1 = min(J.g.ny, (ty + 1) << ly),
-            k1 = min(J.g.nz, (tz + 1) << lz);
-  const float lo[3] = {i0 + J.g.offmin[0], j0 + J.g.offmin[1], k0 + J.g.offmin[2]};
-  const float hi[3] = {(i1 - 1) + J.g.offmax[0], (j1 - 1) + J.g.offmax[1], (k1 - 1) + J.g.offmax[2]};
-  int nops = 0, nleaf = 0, sp = 0, e = 0;
-  int r0 = 0, r1 = 0, r2 = 0;  // fold stack: top, second, third; deeper in stk[0 .. sp-4]
-  for (int w = 0; w < nchain; ++w) {
-    const int word = SCHAIN ? schain[w] : __ldg(chain + w);
-    const int code = (word >> 24) & 0xff, arg = word & 0xffffff;
-    if (code == cPush) {
-      int b0, b1, b2, b3, b4, b5;
-      if (SMEM) {
-        const int* tb = sprim[arg].tb;
-        b0 = tb[0]; b1 = tb[1]; b2 = tb[2]; b3 = tb[3]; b4 = tb[4]; b5 = tb[5];
-      } else {
-        const int* tb = prims[arg].tb;
-        b0 = __ldg(tb); b1 = __ldg(tb + 1); b2 = __ldg(tb + 2);
-        b3 = __ldg(tb + 3); b4 = __ldg(tb + 4); b5 = __ldg(tb + 5);
-      }
-      const bool cand = tx >= b0 && tx < b1 && ty >= b2 && ty < b3 && tz >= b4 && tz < b5;
-      if (!cand && w + 1 < nchain) {
-        // a primitive outside the tile is 0: union(A, 0) = A and
-        // difference(A, 0) = A, so the pair leaves the stack as it is
-        const int nc = ((SCHAIN ? schain[w + 1] : __ldg(chain + w + 1)) >> 24) & 0xff;
-        if ((nc == cUnion || nc == cDiff) && sp >= 1) { ++w; continue; }
-      }
-      const int cl = cand ? classify(prims[arg], lo, hi, auxd, J.auxf) : cOUT;
-      int ent = 0;
-      if (cl == cBND) {
-        int slot = -1;
-        for (int l = 0; l < nleaf; ++l)
-          if (sleaf[l][tid] == arg) { slot = l; break; }
-        if (slot < 0) {
-          if (nleaf < kMaxLeaves) { sleaf[nleaf][tid] = (uint16_t)arg; slot = nleaf++; }
-          else e |= eLeafOverflow;
-        }
-        if (slot >= 0 && nops < kMaxOps) {
-          sop[nops][tid] = (uint16_t)mk_op(fPush, slot, 0);
-          ent = mkE(nops, nops);
-          ++nops;
-        } else {
-          e |= eOpsOverflow;
-        }
-      } else {
-        ent = (cl == cIN) ? 1 : 0;
-      }
-      if (sp < kMaxDepth) {  // push: the top three entries live in registers
-        if (sp >= 3) stk[sp - 3][tid] = (uint16_t)r2;
-        r2 = r1;
-        r1 = r0;
-        r0 = ent;
-        ++sp;
-      } else {
-        e |= eDepthOverflow;
-      }
-    } else {
-      if (sp < 2) { e |= eBadProgram; break; }
-      const int B = r0;
-      const int A = r1;
-      const int ka = A & 3, kb = B & 3;
-      const int ra = (A >> 2) & 127, sa = (A >> 9) & 127;
-      const int rb = (B >> 2) & 127, sb = (B >> 9) & 127;
-      int res = 0, emit = -1, unary = 0;
-      bool discard = false;
-      if (code == cUnion) {
-        if (ka == 1 || kb == 1) { res = 1; discard = true; }
-        else if (ka == 0) res = B;
-        else if (kb == 0) res = A;
-        else emit = fUnion;
-      } else if (code == cInter) {
-        if (ka == 0 || kb == 0) { res = 0; discard = true; }
-        else if (ka == 1) res = B;
-        else if (kb == 1) res = A;
-        else emit = fInter;
-      } else {  // difference
-        if (ka == 0 || kb == 1) { res = 0; discard = true; }
-        else if (kb == 0) res = A;
-        else if (ka == 1) { emit = fCompl; unary = 1; }
-        else emit = fDiff;
-      }
-      if (discard) {
-        if (ka == 2) nops = sa;
-        else if (kb == 2) nops = sb;
-      }
-      if (emit >= 0) {
-        if (nops < kMaxOps) {
-          if (unary) {
-            sop[nops][tid] = (uint16_t)mk_op(fDiff, kOne, rb);
-            res = mkE(nops, sb);
-          } else {
-            sop[nops][tid] = (uint16_t)mk_op(emit, ra, rb);
-            res = mkE(nops, sa);
-          }
-          ++nops;
-        } else {
-          e |= eOpsOverflow;
-          res = 0;
-        }
-      }
-      // two popped, one pushed: the fourth entry (if any) comes back from memory
-      r0 = res;
-      r1 = r2;
-      r2 = sp >= 4 ? (int)stk[sp - 4][tid] : 0;
-      --sp;
-    }
-  }
-  if (sp != 1) e |= eBadProgram;
-  const int fin = sp >= 1 ? r0 : 0;
-  float cval = 0.f;
-  if ((fin & 3) != 2) { nops = 0; cval = (fin & 3) ? 1.f : 0.f; }
-  TileProg* out = J.progs + t;
-  int nslot = 0;
-  bool pairs = false;  // a graph or polygon leaf: the VJP reserves pair columns
-  for (int l = 0; l < nleaf; ++l) {
-    out->leaf[l] = sleaf[l][tid];
-    const PrimRec& L = prims[sleaf[l][tid]];
-    nslot += L.nact;
-    pairs |= L.kind == kGraph || L.kind == kPolygon;
-  }
-  for (int q = 0; q < nops; ++q) out->ops[q] = sop[q][tid];
-  if (nops > 0 && nslot > kMaxSlots) e |= eSlotOverflow;
-  if (nops > 0 && pool_need(nleaf, kWarps * nslot, nops) + (pairs ? kPairFloats : 0) + kPoolSpare >
-                      kVjpPool)
-    e |= ePoolOverflow;
-  if (e) {
-    atomicOr(err, e);
-    nops = 0;
-    cval = 0.f;
-  }
-  out->nops = nops;
-  out->nleaf = nleaf;
-  out->cval = cval;
-  out->nslot = nslot;
-  out->pairs = pairs;
-  J.tclass[t] = nops > 0 ? 2 : (cval != 0.f ? 1 : 0);
-  // band-tile list and counters, one atomic of each kind per group of lanes
-  // that arrive together (any grouping is correct; the list order is free)
-  const unsigned am = __activemask();
-  const int lane = tid & 31, leader = __ffs(am) - 1;
-  const bool band = nops > 0;
-  const unsigned bm = __ballot_sync(am, band);
-  const int mx = __reduce_max_sync(am, band ? nops : 0);
-  const int cells = __reduce_add_sync(am, band ? (i1 - i0) * (j1 - j0) * (k1 - k0) : 0);
-  int base = 0;
-  if (lane == leader && bm) {
-    int* counters = J.counters;
-    base = atomicAdd(&counters[0], __popc(bm));
-    atomicMax(&counters[1], mx);
-    atomicAdd(&counters[2], cells);
-  }
-  base = __shfl_sync(am, base, leader);
-  if (band) J.list[base + __popc(bm & ((1u << lane) - 1u))] = t;
+__device__ __forceinline__ bool tb_hits(const int* tb, int x0, int x1, int y0, int y1, int z0,
+                                        int z1) {  // tile box [x0, x1] x ... against tb
+  return x0 < __ldg(tb + 1) && x1 >= __ldg(tb) && y0 < __ldg(tb + 3) && y1 >= __ldg(tb + 2) &&
+         z0 < __ldg(tb + 5) && z1 >= __ldg(tb + 4);
+}
+__device__ __forceinline__ bool is_ud(int word) {
+  const int c = (word >> 24) & 0xff;
+  return c == cUnion || c == cDiff;
 }
 
-// One thread per tile; the block's 128 tiles belong to one job (tile ranges
-// are padded to multiples of 128).  Threads walk the tiles y-fastest: tiles
-// that differ only in y usually see the same primitives, so a warp's lanes
-// take the same classification branches.
-constexpr size_t kBinSmem = sizeof(PrimRec) * kPrimSmem + sizeof(uint16_t) * 128 *
-                               (kMaxDepth + kMaxLeaves + kMaxOps) + sizeof(int) * kChainSmem;
+// Lane 0's fold state of one tile.
+struct Fold {
+  int sp, r0, r1, r2;  // stack depth; top three entries (deeper ones in stk)
+  int nops, nleaf, e;
+};
 
-__global__ void __launch_bounds__(128) k_bin(const Job* __restrict__ jobs, int njobs,
-                                             int* __restrict__ err) {
+// One chain word of the tile (lane 0): a push with its class, or a logic op
+// folded with the constants (Eqs. union / intersection / difference on 0/1).
+__device__ __forceinline__ void fold_word(Fold& f, int word, int cl, BinWarpBuf& B) {
+  const int code = (word >> 24) & 0xff, arg = word & 0xffffff;
+  if (code == cPush) {
+    int ent = 0;
+    if (cl == cBND) {
+      int slot = -1;
+      for (int l = 0; l < f.nleaf; ++l)
+        if (B.leaf[l] == arg) { slot = l; break; }
+      if (slot < 0) {
+        if (f.nleaf < kMaxLeaves) { B.leaf[f.nleaf] = (uint16_t)arg; slot = f.nleaf++; }
+        else f.e |= eLeafOverflow;
+      }
+      if (slot >= 0 && f.nops < kMaxOps) {
+        B.ops[f.nops] = (uint16_t)mk_op(fPush, slot, 0);
+        ent = mkE(f.nops, f.nops);
+        ++f.nops;
+      } else {
+        f.e |= eOpsOverflow;
+      }
+    } else {
+      ent = (cl == cIN) ? 1 : 0;
+    }
+    if (f.sp < kMaxDepth) {
+      if (f.sp >= 3) B.stk[f.sp - 3] = (uint16_t)f.r2;
+      f.r2 = f.r1;
+      f.r1 = f.r0;
+      f.r0 = ent;
+      ++f.sp;
+    } else {
+      f.e |= eDepthOverflow;
+    }
+    return;
+  }
+  if (f.sp < 2) { f.e |= eBadProgram; return; }
+  const int B0 = f.r0, A = f.r1;
+  const int ka = A & 3, kb = B0 & 3;
+  const int ra = (A >> 2) & 127, sa = (A >> 9) & 127;
+  const int rb = (B0 >> 2) & 127, sb = (B0 >> 9) & 127;
+  int res = 0, emit = -1, unary = 0;
+  bool discard = false;
+  if (code == cUnion) {
+    if (ka == 1 || kb == 1) { res = 1; discard = true; }
+    else if (ka == 0) res = B0;
+    else if (kb == 0) res = A;
+    else emit = fUnion;
+  } else if (code == cInter) {
+    if (ka == 0 || kb == 0) { res = 0; discard = true; }
+    else if (ka == 1) res = B0;
+    else if (kb == 1) res = A;
+    else emit = fInter;
+  } else {  // difference
+    if (ka == 0 || kb == 1) { res = 0; discard = true; }
+    else if (kb == 0) res = A;
+    else if (ka == 1) { emit = fCompl; unary = 1; }
+    else emit = fDiff;
+  }
+  if (discard) {  // the dropped operand's ops were the last ones emitted
+    if (ka == 2) f.nops = sa;
+    else if (kb == 2) f.nops = sb;
+  }
+  if (emit >= 0) {
+    if (f.nops < kMaxOps) {
+      if (unary) {
+        B.ops[f.nops] = (uint16_t)mk_op(fDiff, kOne, rb);
+        res = mkE(f.nops, sb);
+      } else {
+        B.ops[f.nops] = (uint16_t)mk_op(emit, ra, rb);
+        res = mkE(f.nops, sa);
+      }
+      ++f.nops;
+    } else {
+      f.e |= eOpsOverflow;
+      res = 0;
+    }
+  }
+  f.r0 = res;  // two popped, one pushed: the fourth entry comes back from memory
+  f.r1 = f.r2;
+  f.r2 = f.sp >= 4 ? (int)B.stk[f.sp - 4] : 0;
+  --f.sp;
+}
+
+__global__ void __launch_bounds__(kBinThreads) k_bin(const Job* __restrict__ jobs, int njobs,
+                                                     int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem[];
-  PrimRec* sprim = reinterpret_cast<PrimRec*>(smem);
-  auto stk = reinterpret_cast<uint16_t(*)[128]>(sprim + kPrimSmem);
-  auto sleaf = stk + kMaxDepth;
-  auto sop = sleaf + kMaxLeaves;
-  int* schain = reinterpret_cast<int*>(sop + kMaxOps);
-  const int tid = threadIdx.x;
-  const Job& J = jobs[job_by_tile(jobs, njobs, blockIdx.x * 128)];
+  int* schain = reinterpret_cast<int*>(smem);
+  BinWarpBuf* wbuf = reinterpret_cast<BinWarpBuf*>(schain + kBinSeg);
+  __shared__ int wtot[kBinWarps];
+  __shared__ int sband[kBinWarps];  // the block's band tiles
+  __shared__ int sagg[4];           // band tiles, longest program, band cells, list base
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g0 = blockIdx.x * kBinWarps;  // first tile (padded numbering) of the block
+  const Job& J = jobs[job_by_tile(jobs, njobs, g0)];
   if (!J.do_bin) return;  // uniform over the block
   // this binning counts into J.counters (zeroed by the previous one) and
   // clears the other set for the next
-  if (tid < 4 && blockIdx.x * 128 == J.tile_base) J.counters_next[tid] = 0;
-  const bool staged = J.g.nprims <= kPrimSmem;    // primitive records in shared memory
-  const bool cstaged = J.g.nchain <= kChainSmem;  // the chain too (then compacted below)
-  if (cstaged)
-    for (int q = tid; q < J.g.nchain; q += blockDim.x) schain[q] = J.chain[q];
-  if (staged) {
-    constexpr int W = sizeof(PrimRec) / 16;
-    for (int q = tid; q < J.g.nprims * W; q += blockDim.x)
-      reinterpret_cast<int4*>(sprim)[q] = reinterpret_cast<const int4*>(J.prims)[q];
-  }
-  // Block prefilter: the box of tile coordinates the block's 128 tiles span
-  // (y fastest, then x, then z).  A primitive whose value tile box misses it
-  // is 0 on all of them; if every primitive misses it, every tile's program
-  // folds to the constant 0 (a chain of unions, intersections and differences
-  // of zeros) and no thread walks the chain.
+  if (tid < 4 && g0 == J.tile_base) J.counters_next[tid] = 0;
   const int nty = J.g.nty, ntx = J.g.ntx;
-  const int ub0 = blockIdx.x * 128 - J.tile_base;
+  const int ub0 = g0 - J.tile_base;
   if (ub0 >= J.g.T) return;  // padding block (uniform)
-  const int ub1 = min(ub0 + 128, J.g.T) - 1;
-  __syncthreads();  // staged records visible
+  const int ub1 = min(ub0 + kBinWarps, J.g.T) - 1;
+  const PrimRec* __restrict__ prims = J.prims;
+  const int* __restrict__ chain = J.chain;
+  // the block's box of tile coordinates
   int bx0 = 0, bx1 = ntx - 1, by0 = 0, by1 = nty - 1;
   const int bz0 = ub0 / (nty * ntx), bz1 = ub1 / (nty * ntx);
   if (bz0 == bz1) {
@@ -804,81 +805,167 @@ __global__ void __launch_bounds__(128) k_bin(const Job* __restrict__ jobs, int n
     bx1 = (ub1 / nty) % ntx;
     if (bx0 == bx1) { by0 = ub0 % nty; by1 = ub1 % nty; }
   }
+  if (tid < 4) sagg[tid] = 0;
   bool hit = false;
-  for (int q = tid; q < J.g.nprims && !hit; q += blockDim.x) {
-    const int* tb = staged ? sprim[q].tb : J.prims[q].tb;
-    hit = bx0 < tb[1] && bx1 >= tb[0] && by0 < tb[3] && by1 >= tb[2] && bz0 < tb[5] &&
-          bz1 >= tb[4];
-  }
+  for (int q = tid; q < J.g.nprims && !hit; q += kBinThreads)
+    hit = tb_hits(prims[q].tb, bx0, bx1, by0, by1, bz0, bz1);
   const bool any = __syncthreads_or(hit);
-  // Block chain compaction: a push of a primitive that misses the block's
-  // tile box, followed by a union or a difference, changes nothing for any of
-  // the block's tiles (union(A, 0) = difference(A, 0) = A); both ops are
-  // dropped once here instead of being skipped by every thread.
-  int nchain = J.g.nchain;
-  if (any && cstaged) {
-    __shared__ int wtot[kBlock / 32];
-    constexpr int kSeg = kChainSmem / kBlock;  // ops per thread
-    const int w0 = tid * kSeg;
-    auto misses = [&](int w) {  // op w pushes a primitive outside the block's tiles
-      const int word = schain[w];
-      if (((word >> 24) & 0xff) != cPush) return false;
-      const int* tb = staged ? sprim[word & 0xffffff].tb : J.prims[word & 0xffffff].tb;
-      return !(bx0 < tb[1] && bx1 >= tb[0] && by0 < tb[3] && by1 >= tb[2] && bz0 < tb[5] &&
-               bz1 >= tb[4]);
-    };
-    auto ud = [&](int w) {
-      const int c = (schain[w] >> 24) & 0xff;
-      return c == cUnion || c == cDiff;
-    };
-    int words[kSeg];
-    unsigned keep = 0;
-    int cnt = 0;
-#pragma unroll
-    for (int k = 0; k < kSeg; ++k) {
-      const int w = w0 + k;
-      words[k] = w < nchain ? schain[w] : 0;
-      bool drop = false;
-      if (w < nchain) {
-        if (w + 1 < nchain && ud(w + 1) && misses(w)) drop = true;
-        if (w >= 1 && ud(w) && misses(w - 1)) drop = true;
-      }
-      if (w < nchain && !drop) { keep |= 1u << k; ++cnt; }
-    }
-    const int lane = tid & 31, warp = tid >> 5;
-    int inc = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += v;
-    }
-    if (lane == 31) wtot[warp] = inc;
-    __syncthreads();  // every thread has read its segment and its neighbours
-    int off = inc - cnt;
-    for (int v = 0; v < warp; ++v) off += wtot[v];
-    int total = 0;
-    for (int v = 0; v < kBlock / 32; ++v) total += wtot[v];
-#pragma unroll
-    for (int k = 0; k < kSeg; ++k)
-      if (keep & (1u << k)) schain[off++] = words[k];
-    nchain = total;
-    __syncthreads();
-  }
-  const int u = blockIdx.x * 128 + tid - J.tile_base;
-  if (u >= J.g.T) return;
+  const int u = ub0 + warp;
+  const bool live = u < J.g.T;  // warp-uniform
   const int ty = u % nty, tx = (u / nty) % ntx, tz = u / (nty * ntx);
   const int t = (tz * nty + ty) * ntx + tx;
-  if (!any) {
-    J.tclass[t] = 0;  // constant 0; build and VJP read only the class and the band list
+  if (!any) {  // no primitive reaches the block: every tile folds to the constant 0
+    if (live && lane == 0) J.tclass[t] = 0;  // build and VJP read only the class and the list
     return;
   }
-  if (staged) {
-    if (cstaged) bin_tile<true, true>(J, t, nchain, schain, sprim, stk, sleaf, sop, err);
-    else bin_tile<true, false>(J, t, nchain, schain, sprim, stk, sleaf, sop, err);
-  } else {
-    if (cstaged) bin_tile<false, true>(J, t, nchain, schain, sprim, stk, sleaf, sop, err);
-    else bin_tile<false, false>(J, t, nchain, schain, sprim, stk, sleaf, sop, err);
+  const int lx = J.g.lx, ly = J.g.ly, lz = J.g.lz;
+  const int i0 = tx << lx, j0 = ty << ly, k0 = tz << lz;
+  const int i1 = min(J.g.nx, (tx + 1) << lx), j1 = min(J.g.ny, (ty + 1) << ly),
+            k1 = min(J.g.nz, (tz + 1) << lz);
+  const float lo[3] = {i0 + J.g.offmin[0], j0 + J.g.offmin[1], k0 + J.g.offmin[2]};
+  const float hi[3] = {(i1 - 1) + J.g.offmax[0], (j1 - 1) + J.g.offmax[1], (k1 - 1) + J.g.offmax[2]};
+  BinWarpBuf& B = wbuf[warp];
+  Fold f{0, 0, 0, 0, 0, 0, 0};
+  const int nchain = J.g.nchain;
+  auto misses_block = [&](int word) {
+    return ((word >> 24) & 0xff) == cPush &&
+           !tb_hits(prims[word & 0xffffff].tb, bx0, bx1, by0, by1, bz0, bz1);
+  };
+  auto misses_tile = [&](int word) {
+    return ((word >> 24) & 0xff) == cPush &&
+           !tb_hits(prims[word & 0xffffff].tb, tx, tx, ty, ty, tz, tz);
+  };
+  for (int s0 = 0; s0 < nchain; s0 += kBinSeg) {
+    const int s1 = min(nchain, s0 + kBinSeg);
+    // block pass, one word per thread and slab: the segment's words minus
+    // the pairs that miss the block, in order
+    int n = 0;
+    __syncthreads();  // the previous segment's walks are done with schain
+    for (int w0 = s0; w0 < s1; w0 += kBinThreads) {
+      const int w = w0 + tid;
+      int word = 0;
+      bool keep = false;
+      if (w < s1) {
+        word = __ldg(chain + w);
+        keep = !((w + 1 < nchain && is_ud(__ldg(chain + w + 1)) && misses_block(word)) ||
+                 (w >= 1 && is_ud(word) && misses_block(__ldg(chain + w - 1))));
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (lane == 0) wtot[warp] = __popc(m);
+      __syncthreads();  // warp counts of this slab
+      int off = n, tot = 0;
+      for (int v = 0; v < kBinWarps; ++v) {
+        if (v < warp) off += wtot[v];
+        tot += wtot[v];
+      }
+      if (keep) schain[off + __popc(m & ((1u << lane) - 1u))] = word;
+      n += tot;
+      __syncthreads();  // this slab's words are in place; wtot is free again
+    }
+    if (live) {
+      for (int r = 0; r < n; r += 32) {
+        const int i = r + lane;
+        int word = 0, cl = cOUT;
+        bool kept = false, defer = false;
+        if (i < n) {
+          word = schain[i];
+          if (((word >> 24) & 0xff) == cPush) {
+            const bool miss = misses_tile(word);
+            kept = !miss || !(i + 1 < n && is_ud(schain[i + 1]));
+            if (!miss) {
+              const PrimRec& R = prims[word & 0xffffff];
+              const int kind = R.kind;
+              if (kind == kPolygon || kind == kGraph) defer = true;
+              else cl = classify(R, lo, hi, J.auxd, J.auxf);
+            }
+          } else {
+            kept = !(i >= 1 && is_ud(word) && misses_tile(schain[i - 1]));
+          }
+        }
+        // polygons and graphs: classified by the whole warp, one at a time
+        for (unsigned dm = __ballot_sync(0xffffffffu, defer); dm; dm &= dm - 1) {
+          const int src = __ffs(dm) - 1;
+          const int wd = __shfl_sync(0xffffffffu, word, src);
+          const int c = classify_warp(prims[wd & 0xffffff], lo, hi, J.auxd, J.auxf, lane);
+          if (lane == src) cl = c;
+        }
+        const unsigned km = __ballot_sync(0xffffffffu, kept);
+        if (kept) {
+          const int p = __popc(km & ((1u << lane) - 1u));
+          B.word[p] = word;
+          B.cls[p] = (unsigned char)cl;
+        }
+        __syncwarp();
+        if (lane == 0)
+          for (int j = 0; j < __popc(km); ++j) fold_word(f, B.word[j], B.cls[j], B);
+        __syncwarp();
+      }
+    }
   }
+  // the tile's program: constant, or band ops over its leaves
+  int nops = 0, nleaf = 0, e = 0;
+  float cval = 0.f;
+  if (lane == 0) {
+    if (f.sp != 1) f.e |= eBadProgram;
+    const int fin = f.sp >= 1 ? f.r0 : 0;
+    nops = f.nops;
+    if ((fin & 3) != 2) { nops = 0; cval = (fin & 3) ? 1.f : 0.f; }
+    nleaf = f.nleaf;
+    e = f.e;
+  }
+  nops = __shfl_sync(0xffffffffu, nops, 0);
+  nleaf = __shfl_sync(0xffffffffu, nleaf, 0);
+  e = __shfl_sync(0xffffffffu, e, 0);
+  cval = __shfl_sync(0xffffffffu, cval, 0);
+  int nslot = 0;
+  bool pairs = false;  // a graph or polygon leaf: the VJP reserves pair columns
+  if (live && nops > 0) {
+    for (int l = lane; l < nleaf; l += 32) {
+      const PrimRec& L = prims[B.leaf[l]];
+      nslot += L.nact;
+      pairs |= L.kind == kGraph || L.kind == kPolygon;
+    }
+    nslot = __reduce_add_sync(0xffffffffu, nslot);
+    pairs = __any_sync(0xffffffffu, pairs);
+    if (nslot > kMaxSlots) e |= eSlotOverflow;
+    if (pool_need(nleaf, kWarps * nslot, nops) + (pairs ? kPairFloats : 0) + kPoolSpare > kVjpPool)
+      e |= ePoolOverflow;
+  }
+  if (live && e) {
+    if (lane == 0) atomicOr(err, e);
+    nops = 0;
+    cval = 0.f;
+  }
+  const bool band = live && nops > 0;
+  if (band) {  // constant tiles keep only their class
+    TileProg* out = J.progs + t;
+    for (int l = lane; l < nleaf; l += 32) out->leaf[l] = B.leaf[l];
+    for (int q = lane; q < nops; q += 32) out->ops[q] = B.ops[q];
+    if (lane == 0) {
+      out->nops = nops;
+      out->nleaf = nleaf;
+      out->cval = cval;
+      out->nslot = nslot;
+      out->pairs = pairs;
+      const int pos = atomicAdd(&sagg[0], 1);
+      sband[pos] = t;
+      atomicMax(&sagg[1], nops);
+      atomicAdd(&sagg[2], (i1 - i0) * (j1 - j0) * (k1 - k0));
+    }
+  }
+  if (live && lane == 0) J.tclass[t] = band ? 2 : (cval != 0.f ? 1 : 0);
+  // the block's band tiles into the list: one set of global atomics per block
+  // (the list order is free)
+  __syncthreads();
+  const int nb = sagg[0];
+  if (nb == 0) return;  // uniform
+  if (tid == 0) {
+    sagg[3] = atomicAdd(&J.counters[0], nb);
+    atomicMax(&J.counters[1], sagg[1]);
+    atomicAdd(&J.counters[2], sagg[2]);
+  }
+  __syncthreads();
+  if (tid < nb) J.list[sagg[3] + tid] = sband[tid];
 }
 
 // Threads [tid0, tid0 + nthr) of the block, one 16-byte word at a time:
@@ -2382,7 +2469,7 @@ int vjp_blocks_per_sm(int njobs) {
 
 cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s) {
   if (t.tiles_padded <= 0) return cudaSuccess;
-  k_bin<<<t.tiles_padded / 128, 128, kBinSmem, s>>>(jobs, t.njobs, err);
+  k_bin<<<t.tiles_padded / kBinWarps, kBinThreads, kBinSmem, s>>>(jobs, t.njobs, err);
   return cudaGetLastError();
 }
 
