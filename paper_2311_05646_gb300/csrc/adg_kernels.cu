@@ -1031,11 +1031,20 @@ __device__ __forceinline__ float plane_value(const PrimRec& P, const Cell& c, co
 }
 
 // All threads: fill the planned tables of the tile with origin (X0, Y0, Z0).
+// On the way, each thread checks its y and z entries of boxes and z entries
+// of the other leaves against the entry at y = 0 (z = 0), recomputed (the
+// same function of the same inputs, so bitwise what that thread wrote):
+// okY / okZ start the collapse test that uniform_finish completes.  With
+// act1 (VJP), a box entry whose keyed derivative is nonzero marks its
+// (axis, component, coordinate) active; act1 is cleared beforehand.
 __device__ __forceinline__ void tables_fill(const PrimRec* sl, int nleaf, const GridDev& g,
                                             const LeafTab* lt, bool derivs, int X0, int Y0,
                                             int Z0, float* tab, int tid, const float* auxf,
-                                            const double* auxd) {
+                                            const double* auxd, unsigned char* act1, bool& okY,
+                                            bool& okZ) {
   const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
+  okY = true;
+  okZ = true;
   for (int l = 0; l < nleaf; ++l) {
     const int4 tv = lt[l].v, td = lt[l].d;
     if (!(td.w & tOK)) continue;
@@ -1056,6 +1065,15 @@ __device__ __forceinline__ void tables_fill(const PrimRec* sl, int nleaf, const 
           const int dt = ax == 0 ? td.x : (ax == 1 ? td.y : td.z);
           tab[dt + (2 * c) * T + u] = da;
           tab[dt + (2 * c + 1) * T + u] = db;
+          const int k = (td.w >> (3 + 2 * ax)) & 3;
+          if (act1 && (td.w & tACT) && (((k & 1) && da != 0.f) || ((k & 2) && db != 0.f)))
+            act1[e] = 1;
+        }
+        if (ax > 0 && u > 0) {
+          float da0, db0;
+          const float f0 = box_axis(P, ax, O, g.off[c][ax], da0, db0);
+          const bool same = f == f0 && (!derivs || (da == da0 && db == db0));
+          if (ax == 1) okY &= same; else okZ &= same;
         }
       }
     } else {
@@ -1069,10 +1087,17 @@ __device__ __forceinline__ void tables_fill(const PrimRec* sl, int nleaf, const 
           const int r = e - nxy, c = r / TZ, u = r - c * TZ;
           const Cell cc{X0, Y0, Z0 + u, g.off[c][0], g.off[c][1], g.off[c][2]};
           float dz0, dz1;
-          tab[tv.z + r] = zfactor(P, cc, dz0, dz1);
+          const float zf = zfactor(P, cc, dz0, dz1);
+          tab[tv.z + r] = zf;
           if (derivs) {
             tab[td.z + (2 * c) * TZ + u] = dz0;
             tab[td.z + (2 * c + 1) * TZ + u] = dz1;
+          }
+          if (u > 0) {
+            const Cell c0{X0, Y0, Z0, g.off[c][0], g.off[c][1], g.off[c][2]};
+            float e0, e1;
+            const float z0 = zfactor(P, c0, e0, e1);
+            okZ &= zf == z0 && (!derivs || (dz0 == e0 && dz1 == e1));
           }
         }
       }
@@ -1224,49 +1249,26 @@ __device__ __forceinline__ void fill_rows(const Job* __restrict__ jobs, int jb, 
 // tabled) blocks the y collapse.  Then the build evaluates one y (z) and
 // writes it to all, and the VJP sums the seeds along the axis first (the
 // projection to the grid comes last, Sec. 3; extruded and planar designs
-// are uniform along whole axes, Sec. 3.1).  All threads; per-thread flags.
-__device__ __forceinline__ void uniform_axes(const LeafTab* lt, int nleaf, const GridDev& g,
-                                             const float* tab, bool derivs, int tid, bool& okY,
-                                             bool& okZ) {
-  const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
+// are uniform along whole axes, Sec. 3.1).  All threads, after the tables
+// (which checked the box and z entries); per-thread flags, to be voted.
+__device__ __forceinline__ void uniform_finish(const LeafTab* lt, int nleaf, const GridDev& g,
+                                               const float* tab, bool derivs, int tid, bool& okY,
+                                               bool& okZ) {
+  const int TX = 1 << g.lx, TY = 1 << g.ly, C = g.C;
   const int lane = tid & 31;
-  // axes that cannot collapse are not checked (the flags are read by the
-  // lanes of every warp in parallel; the result is the same for every thread)
-  bool untabled = false, planeAct = false;
+  // axes that cannot collapse (the flags are read by the lanes of every warp
+  // in parallel; the result is the same for every thread)
+  bool untabled = false, planeAct = false, plane = false;
   for (int l = lane; l < nleaf; l += 32) {
     const int f = lt[l].d.w;
     untabled |= !(f & tOK);
+    plane |= !(f & tBOX);
     planeAct |= derivs && !(f & tBOX) && (f & tACT);
   }
-  okY = true;
-  okZ = true;
   if (__any_sync(0xffffffffu, untabled)) { okY = false; okZ = false; return; }
   if (__any_sync(0xffffffffu, planeAct)) okY = false;
-  // z tables of every leaf and y tables of the boxes, one pass over
-  // (leaf, entry) pairs
-  const int ez = C * TZ, e1 = ez + C * TY;
-  for (int q = tid; q < nleaf * e1; q += kBlock) {
-    const int l = q / e1, e = q - l * e1;
-    const int4 v = lt[l].v, d = lt[l].d;
-    if (e < ez) {
-      const int c = e / TZ, z = e - c * TZ;
-      if (z == 0) continue;
-      okZ &= tab[v.z + c * TZ + z] == tab[v.z + c * TZ];
-      if (derivs && d.z >= 0) {
-        okZ &= tab[d.z + 2 * c * TZ + z] == tab[d.z + 2 * c * TZ];
-        okZ &= tab[d.z + (2 * c + 1) * TZ + z] == tab[d.z + (2 * c + 1) * TZ];
-      }
-    } else if (d.w & tBOX) {
-      const int r = e - ez, c = r / TY, y = r - c * TY;
-      if (y == 0) continue;
-      okY &= tab[v.y + c * TY + y] == tab[v.y + c * TY];
-      if (derivs) {
-        okY &= tab[d.y + 2 * c * TY + y] == tab[d.y + 2 * c * TY];
-        okY &= tab[d.y + (2 * c + 1) * TY + y] == tab[d.y + (2 * c + 1) * TY];
-      }
-    }
-  }
-  // in-plane tables of the other leaves along y
+  if (!__any_sync(0xffffffffu, plane)) return;
+  // in-plane tables of the non-box leaves along y
   if (okY || !derivs)
     for (int l = 0; l < nleaf; ++l) {
       const int4 v = lt[l].v;
@@ -1495,11 +1497,11 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
       stage_tile(P, J.prims, nleaf, tp.sl, tid - 32, kBlock - 32);
     }
     band_sync();
-    tables_fill(tp.sl, nleaf, g, tp.lt, false, tx << g.lx, ty << g.ly, tz << g.lz, tp.tab, tid,
-                J.auxf, J.auxd);
-    band_sync();
     bool okY, okZ;
-    uniform_axes(tp.lt, nleaf, g, tp.tab, false, tid, okY, okZ);
+    tables_fill(tp.sl, nleaf, g, tp.lt, false, tx << g.lx, ty << g.ly, tz << g.lz, tp.tab, tid,
+                J.auxf, J.auxd, nullptr, okY, okZ);
+    band_sync();
+    uniform_finish(tp.lt, nleaf, g, tp.tab, false, tid, okY, okZ);
     if (!okZ) sdepth[1] = 0;
     const bool uy = band_sync_and(okY);
     const bool uz = sdepth[1] != 0;
@@ -1766,28 +1768,9 @@ __device__ __noinline__ void poly_rigid_reduce(const PrimRec& P, const LeafTab& 
 // Jacobian row only where some parameter-driven scalar of a tabled box has a
 // nonzero derivative-table entry at its x, y or z (each scalar moves one
 // face), or anywhere when a parameter-driven leaf is not a tabled box.
-// act1 holds one byte per (component, coordinate) of the x, y, z blocks.
+// act1 holds one byte per (component, coordinate) of the x, y, z blocks
+// (set by the tables).
 constexpr int kAct1 = 3 * (64 + 16 + 8);
-__device__ __forceinline__ void activity_axes(const LeafTab* lt, int nleaf, const GridDev& g,
-                                              const float* tab, unsigned char* act1, int tid) {
-  const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
-  for (int e = tid; e < C * (TX + TY + TZ); e += kBlock) {
-    int ax = 0, r = e, T = TX;
-    if (r >= C * TX) { r -= C * TX; ax = 1; T = TY; }
-    if (ax == 1 && r >= C * TY) { r -= C * TY; ax = 2; T = TZ; }
-    const int c = r / T, u = r - c * T;
-    bool on = false;
-    for (int lf = 0; lf < nleaf && !on; ++lf) {
-      const int4 d = lt[lf].d;
-      if ((d.w & (tACT | tOK | tBOX)) != (tACT | tOK | tBOX)) continue;
-      const int k = (d.w >> (3 + 2 * ax)) & 3;
-      const int dt = ax == 0 ? d.x : (ax == 1 ? d.y : d.z);
-      on = ((k & 1) && tab[dt + (2 * c) * T + u] != 0.f) ||
-           ((k & 2) && tab[dt + (2 * c + 1) * T + u] != 0.f);
-    }
-    act1[e] = on;
-  }
-}
 
 // ---- VJP helpers ---------------------------------------------------------------
 // Warp 0 of the VJP, straight from the records in global memory (while the
@@ -2098,16 +2081,17 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
     } else {
       stage_tile(P, J.prims, nleaf, slw, tid - 32, kBlock - 32);
       for (int q = tid - 32; q < 2 * kWarps * nslot; q += kBlock - 32) racc[q] = 0.f;  // rows and compensation
+      for (int q = tid - 32; q < g.C * ((1 << g.lx) + (1 << g.ly) + (1 << g.lz)); q += kBlock - 32)
+        act1[q] = 0;  // activity, set by the tables
     }
     if (pt)
       for (int q = 0; q < nslot; ++q) tcol[q * kBlock + tid] = 0.f;  // this thread's column
     __syncthreads();
-    tables_fill(sl, nleaf, g, lt, true, tx << g.lx, ty << g.ly, tz << g.lz, tabw, tid, J.auxf,
-                J.auxd);
-    __syncthreads();
-    activity_axes(lt, nleaf, g, tab, act1, tid);
     bool okY, okZ;
-    uniform_axes(lt, nleaf, g, tab, true, tid, okY, okZ);
+    tables_fill(sl, nleaf, g, lt, true, tx << g.lx, ty << g.ly, tz << g.lz, tabw, tid, J.auxf,
+                J.auxd, act1, okY, okZ);
+    __syncthreads();
+    uniform_finish(lt, nleaf, g, tab, true, tid, okY, okZ);
     if (!okZ) misc[3] = 0;  // set to 1 by warp 0 before the last barrier
     const bool uy = __syncthreads_and(okY);
     const bool uz = misc[3] != 0;
