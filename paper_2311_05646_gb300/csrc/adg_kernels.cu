@@ -2006,8 +2006,8 @@ __device__ __noinline__ void tile_seeds(const Job* J, const uint16_t* slist, flo
     zsb[i - c0] = zs * g.deps;  // eps = eps_bg + deps fill
   }
 }
-// a tile's x-rows (C * TY * TZ <= 3 * 1024 / 32) fit the seed buffer they alias
-static_assert(3 * kMaxTileCells / 32 <= kSeedChunk, "row offsets alias the seed buffer");
+// a warp's share of a tile's x-rows (C * TY * TZ <= 3 * 1024 / 32) fits its lanes
+static_assert((3 * kMaxTileCells / 32 + kWarps - 1) / kWarps <= 32, "rows per warp");
 constexpr size_t kVjpFixed = (size_t)kSmemOps * kBlock * 4 + (size_t)kVjpPool * 4 +
                              (size_t)kSeedChunk * 4 + (size_t)kMaxTileCells * 3 * 2 +
                              (kMaxLeaves + 1) * 4 + kAct1 + 32 * 4;
@@ -2024,13 +2024,11 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
   float* tape = reinterpret_cast<float*>(smem);
   float* pool = tape + kSmemOps * kBlock;
   float* zsb = pool + kVjpPool;  // seeds of a chunk
-  int* rinfo = reinterpret_cast<int*>(zsb);  // before the seeds: per x-row offset << 2 | kind
   uint16_t* slist = reinterpret_cast<uint16_t*>(zsb + kSeedChunk);  // active samples
   int* sbase = reinterpret_cast<int*>(slist + kMaxTileCells * 3);
   unsigned char* act1 = reinterpret_cast<unsigned char*>(sbase + kMaxLeaves + 1);
-  // misc words: [0] active samples, [1] all-active flag, [2] parameter-driven
-  // pushes, [3] z-collapse flag, [4..9] x-row masks per component (2 words
-  // each), [10..11] in-grid x
+  // misc words: [1] all-active flag, [2] parameter-driven pushes, [3]
+  // z-collapse flag, [12..15] active samples per warp's rows
   int* misc = reinterpret_cast<int*>(act1 + kAct1);
   int* spre = reinterpret_cast<int*>(smem + ((kVjpFixed + 15) & ~(size_t)15));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -2110,63 +2108,66 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
     const int nw = TX >> 5;  // 32-bit words per x-row
     // Active samples, per x-row (c, z, y): the whole row when the sample's y
     // or z moves a face (or a non-box leaf drives a parameter), else the
-    // component's x-pattern; out-of-grid samples never.  Row offsets come
-    // from one prefix sum, so the list runs through the samples in order and
-    // the accumulation order is fixed.
-    if (warp == 0) {
-      for (int c = 0; c < C; ++c)
-        for (int h = 0; h < nw; ++h) {
-          const int x = h * 32 + lane;
-          const bool in = X0 + x < g.nx;
-          const unsigned xm = __ballot_sync(0xffffffffu, in && act1[c * TX + x]);
-          const unsigned xi = __ballot_sync(0xffffffffu, in);
-          if (lane == 0) {
-            misc[4 + 2 * c + h] = (int)xm;
-            if (c == 0) misc[10 + h] = (int)xi;
-          }
-        }
-      __syncwarp();
-      const bool all = misc[1] != 0;
-      int base = 0;
-      for (int r0 = 0; r0 < nrows; r0 += 32) {
-        const int r = r0 + lane;
-        int kind = 0, cnt = 0;
-        if (r < nrows) {
-          const int c = r / (TYr * TZr), rem = r - c * TYr * TZr, z = rem / TYr, y = rem - z * TYr;
-          if (Y0 + y < g.ny && Z0 + z < g.nz) {
-            const bool full = all || act1[C * TX + c * TY + y] || act1[C * (TX + TY) + c * TZ + z];
-            kind = full ? 1 : 2;
-            for (int h = 0; h < nw; ++h)
-              cnt += __popc((unsigned)(full ? misc[10 + h] : misc[4 + 2 * c + h]));
-          }
-        }
-        int inc = cnt;
+    // component's x-pattern; out-of-grid samples never.  Each warp takes a
+    // contiguous quarter of the rows: their counts, a warp prefix, the warp
+    // totals through shared memory, then the rows' entries -- so the list
+    // runs through the samples in order and the accumulation order is fixed.
+    unsigned xm[3][2], xi[2];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int u = __shfl_up_sync(0xffffffffu, inc, o);
-          if (lane >= o) inc += u;
-        }
-        if (r < nrows) rinfo[r] = ((base + inc - cnt) << 2) | kind;
-        base += __shfl_sync(0xffffffffu, inc, 31);
-      }
-      if (lane == 0) misc[0] = base;
+    for (int h = 0; h < 2; ++h) {
+      const int x = h * 32 + lane;
+      const bool in = h < nw && X0 + x < g.nx;
+      xi[h] = __ballot_sync(0xffffffffu, in);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) xm[c][h] = __ballot_sync(0xffffffffu, in && c < C && act1[c * TX + x]);
     }
-    __syncthreads();
-    for (int r = warp; r < nrows; r += kWarps) {
-      const int e = rinfo[r];
-      const int kind = e & 3;
-      if (!kind) continue;
-      int off = e >> 2;
-      const int c = r / (TYr * TZr), rem = r - c * TYr * TZr, z = rem / TYr, y = rem - z * TYr;
+    const bool all = misc[1] != 0;
+    const int rpw = (nrows + kWarps - 1) / kWarps;  // <= 24
+    const int ra = warp * rpw, rb = min(nrows, ra + rpw);
+    int kind = 0, cnt = 0, rc = 0, rz = 0, ry = 0;
+    if (ra + lane < rb) {
+      const int r = ra + lane;
+      rc = r / (TYr * TZr);
+      const int rem = r - rc * TYr * TZr;
+      rz = rem / TYr;
+      ry = rem - rz * TYr;
+      if (Y0 + ry < g.ny && Z0 + rz < g.nz) {
+        const bool full = all || act1[C * TX + rc * TY + ry] || act1[C * (TX + TY) + rc * TZ + rz];
+        kind = full ? 1 : 2;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          cnt += __popc(full ? xi[h] : (rc == 0 ? xm[0][h] : rc == 1 ? xm[1][h] : xm[2][h]));
+      }
+    }
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (lane == 31) misc[12 + warp] = inc;
+    __syncthreads();  // warp totals
+    int wbase = 0, nact_cells = 0;
+#pragma unroll
+    for (int v = 0; v < kWarps; ++v) {
+      const int tv = misc[12 + v];
+      if (v < warp) wbase += tv;
+      nact_cells += tv;
+    }
+    for (int rr = 0; rr < rb - ra; ++rr) {  // this warp's rows, all lanes per row
+      const int kd = __shfl_sync(0xffffffffu, kind, rr);
+      int off = wbase + __shfl_sync(0xffffffffu, inc - cnt, rr);
+      const int c = __shfl_sync(0xffffffffu, rc, rr), z = __shfl_sync(0xffffffffu, rz, rr),
+                y = __shfl_sync(0xffffffffu, ry, rr);
+      if (!kd) continue;
       const int lrow = ((c * TZr + z) * TYr + y) << g.lx;
       for (int h = 0; h < nw; ++h) {
-        const unsigned m = (unsigned)(kind == 1 ? misc[10 + h] : misc[4 + 2 * c + h]);
+        const unsigned m = kd == 1 ? xi[h] : (c == 0 ? xm[0][h] : c == 1 ? xm[1][h] : xm[2][h]);
         if ((m >> lane) & 1u) slist[off + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(lrow + h * 32 + lane);
         off += __popc(m);
       }
     }
-    __syncthreads();
-    const int nact_cells = misc[0];
+    __syncthreads();  // the list is complete; misc[12..] free again
     const int ndl = misc[2];
     if (tid == 0) atomicAdd(&J.counters[3], nact_cells * ny_r * nz_r);  // grid samples
     for (int c0 = 0; c0 < nact_cells; c0 += kSeedChunk) {
