@@ -392,20 +392,46 @@ def run_adg(args):
         g_h = torch.empty(design.n_params, dtype=torch.float32).pin_memory()
         ne = max(3, min(args.steps, 20))
 
+        # Copies on their own streams: the host link carries one direction at
+        # a time per stream, so the read-back of step k (D2H) runs while the
+        # fields of step k+1 come in (H2D).  Events keep the buffers safe: the
+        # fields are not overwritten before the VJP that reads them is done,
+        # nor eps before its read-back is done.
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+        state = {"comp": None, "out": None}
+
         def e2e_step(k):
-            efd.copy_(efp, non_blocking=True)
-            ead.copy_(eap, non_blocking=True)
+            if state["comp"] is not None:
+                s_in.wait_event(state["comp"])
+            with torch.cuda.stream(s_in):
+                efd.copy_(efp, non_blocking=True)
+                ead.copy_(eap, non_blocking=True)
+            ev_in = torch.cuda.Event()
+            ev_in.record(s_in)
+            stream.wait_event(ev_in)
+            if state["out"] is not None:
+                stream.wait_event(state["out"])
             step(k)
-            eps_h.copy_(eps, non_blocking=True)
-            g_h.copy_(g, non_blocking=True)
+            ev_comp = torch.cuda.Event()
+            ev_comp.record(stream)
+            s_out.wait_event(ev_comp)
+            with torch.cuda.stream(s_out):
+                eps_h.copy_(eps, non_blocking=True)
+                g_h.copy_(g, non_blocking=True)
+            ev_out = torch.cuda.Event()
+            ev_out.record(s_out)
+            state["comp"], state["out"] = ev_comp, ev_out
 
         for k in range(2):
             e2e_step(k)
         torch.cuda.synchronize()
         barrier()
         e0.record(stream)
+        s_in.wait_event(e0)
+        state["comp"] = state["out"] = None
         for k in range(ne):
             e2e_step(k)
+        stream.wait_event(state["out"])
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()

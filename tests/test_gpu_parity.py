@@ -205,6 +205,24 @@ def test_gradient_is_deterministic(ctx):
     assert np.array_equal(g1, g2)
 
 
+def test_long_chains_span_binner_segments(ctx, oracle_mod):
+    """A 48 x 48 hole lattice: 2306 primitives, a chained program of 4611
+    words, so the binner compacts and walks it in two segments and in many
+    512-word slabs.  The tile programs it writes are what the build and the
+    VJP run; they are checked through the fill, on sampled cells of a 3D grid
+    and in full on a 2D one (the oracle gradient of 6912 parameters on this
+    design takes minutes)."""
+    desc = I.hole_lattice(n=(192, 192, 8), d=(40.0, 40.0, 20.0), holes=48)
+    assert len(desc["prims"]["kind"]) == 2306
+    d = _design(ctx, desc)
+    fill, _ = H.run_build(d, desc)
+    idx = np.random.default_rng(9).choice(fill.size, 20000, replace=False)
+    fref = oracle_mod.fill_at(desc, idx)
+    assert np.abs(fill.reshape(-1)[idx] - fref).max() <= H.FILL_TOL
+    desc2 = I.hole_lattice(n=(192, 192, 1), d=(40.0, 40.0, 40.0), holes=48, ncomp=1)
+    _check_build(ctx, desc2, oracle_mod)
+
+
 def test_partials_and_counts_reset_between_calls(ctx):
     """The finalize clears the partials it sums and moves the active-sample
     count, so a call after others (same bins, or a rebin with another partial
