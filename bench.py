@@ -33,6 +33,23 @@ WORKLOAD = ("3D two-etch grating: Yee grid 600x200x120, Ex/Ey/Ez, dx=dy=40 nm, d
             "complex64 fwd+adj fields (6 arrays, seeded plane waves x Gaussian)")
 
 
+def reduce_max(x: float, dist, device) -> float:
+    """The largest of x over the ranks (the slowest replica's time); x itself
+    with one rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, units_per_rank: float, ms: float) -> float:
+    """Whole-job throughput of `world` replicas that each process
+    `units_per_rank` units per step, with the max-over-ranks step time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -293,12 +310,9 @@ def run_adg(args):
     adg.adg_profile_enable(ctx, False)
     prof = adg.adg_profile_read(ctx, reset=True)
     adg.adg_sync(ctx, stream)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, dist, "cuda")
     stats = adg.adg_design_stats(design, stream)
-    value = world * cells / (ms * 1e-3)
+    value = replica_value(world, cells, ms)
 
     # roofline of the dominant kernel (HBM-bound): algorithmic bytes / launch
     # the build writes fill + eps (fp32) of every sample: constant tiles by a
@@ -435,12 +449,8 @@ def run_adg(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms_e = e0.elapsed_time(e1) / ne
-        if dist is not None:
-            t = torch.tensor([ms_e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e = float(t.item())
-        e2e = {"value": world * cells / (ms_e * 1e-3), "unit": "cells/s",
+        ms_e = reduce_max(e0.elapsed_time(e1) / ne, dist, "cuda")
+        e2e = {"value": replica_value(world, cells, ms_e), "unit": "cells/s",
                "h2d_bytes_per_step": int(efp.numel() * 8 * 2),
                "d2h_bytes_per_step": int(eps_h.numel() * 4 + g_h.numel() * 4),
                "ms_per_step": ms_e}
