@@ -2046,6 +2046,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
       if (tid == 0) atomicOr(err, eSlotOverflow);
       continue;
     }
+    // No leaf of the tile is driven by a parameter: d eps / d p is zero on
+    // it (no slot, no active sample, no partial), so the tile is skipped.
+    if (nslot == 0) continue;
     // pool: staged leaves, descriptors, op descriptors, pushes list,
     // accumulator rows, then per-thread columns and factor tables
     PrimRec* slw = reinterpret_cast<PrimRec*>(pool);
