@@ -82,6 +82,7 @@ struct adg_ctx {
     bool used = false;
     cudaGraphExec_t exec = nullptr;
     uint64_t sig = 0;
+    int* d_work = nullptr;  // the batch launches' tile counters (zero between launches)
   };
   Arena arenas[2];
   int next_arena = 0;
@@ -152,7 +153,8 @@ struct adg_design {
   unsigned char* d_tclass = nullptr;
   int* d_list = nullptr;
   int* d_counters = nullptr;  // two sets of 4 (the binning alternates between them),
-                              // then the active samples of the last VJP
+                              // the active samples of the last VJP, then the
+                              // persistent kernels' 4 tile counters
   int gen = 0;                // the set of the last binning
   float* d_partial = nullptr;  // all zero between calls (the finalize clears what it sums)
   size_t partial_cap = 0;
@@ -209,6 +211,7 @@ extern "C" adg_status adg_ctx_destroy(adg_ctx* ctx) {
     if (a.done) cudaEventDestroy(a.done);
     cudaFree(a.d);
     cudaFreeHost(a.h);
+    cudaFree(a.d_work);
   }
   for (auto& t : ctx->tickets) cudaEventDestroy(t.ev);
   if (ctx->capture) cudaStreamDestroy(ctx->capture);
@@ -335,8 +338,8 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_progs, sizeof(TileProg) * (size_t)d->g.T);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_tclass, (size_t)d->g.T);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_list, sizeof(int) * (size_t)d->g.T);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_counters, sizeof(int) * 9);
-  if (e == cudaSuccess) e = cudaMemset(d->d_counters, 0, sizeof(int) * 9);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_counters, sizeof(int) * 16);
+  if (e == cudaSuccess) e = cudaMemset(d->d_counters, 0, sizeof(int) * 16);
   if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_job, sizeof(Job));
   if (e != cudaSuccess) {
     free_design(d);
@@ -492,6 +495,7 @@ adg_status run_single(adg_ctx* ctx, adg_design* d, const double* h_params, float
   t.bin_blocks = t.tiles_padded / 128;
   t.fill_blocks = d_eps ? (d->g.C * d->g.nz * d->g.ny + kFillRows - 1) / kFillRows : 0;
   t.params = grad ? d->n_params : 0;
+  t.work = d->d_counters + 12;
   st = run_jobs(ctx, d->d_job, t, rebin, d_eps != nullptr, grad, d->g.T, s);
   if (st == ADG_OK) d->partial_dirty = false;
   return st;
@@ -648,6 +652,10 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
     A.cap = cap;
   }
   if (!A.done) CU(cudaEventCreateWithFlags(&A.done, cudaEventDisableTiming));
+  if (!A.d_work) {
+    CU(cudaMalloc((void**)&A.d_work, sizeof(int) * 4));
+    CU(cudaMemset(A.d_work, 0, sizeof(int) * 4));
+  }
   unsigned char* hb = static_cast<unsigned char*>(A.h);
   unsigned char* db = static_cast<unsigned char*>(A.d);
   Job* hj = reinterpret_cast<Job*>(hb + o_jobs);
@@ -710,6 +718,7 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   t.bin_blocks = tile_base / 128;
   t.fill_blocks = row_base;
   t.params = param_base;
+  t.work = A.d_work;
   sig = mix(sig, (uint64_t)bytes);
   sig = mix(sig, (uint64_t)tile_base);
   sig = mix(sig, (uint64_t)param_base);

@@ -179,6 +179,10 @@ struct JobTotals {
   int bin_blocks;        // sum over binned jobs of ceil(T / 128)
   int tiles_padded;      // tile_base of one past the last job
   int params;            // sum of nparam over gradient jobs
+  // Tile counters of the persistent kernels, 4 ints: VJP next tile, VJP blocks
+  // done, build next tile, build blocks done.  Zero between launches: the
+  // last block of a launch resets its pair.  One launch at a time per array.
+  int* work;
 };
 
 constexpr int kMaxJobs = 1024;  // jobs in one table (one batch)

@@ -1576,10 +1576,11 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
 // per thread, register stack; a shared-memory stack for deeper programs) --
 // and the streaming fill of the constant tiles.
 // five blocks of 160 threads per SM: 80 registers
-__global__ void __maxnreg__(80) k_build(const Job* __restrict__ jobs, int njobs, int nfill) {
+__global__ void __maxnreg__(80) k_build(const Job* __restrict__ jobs, int njobs, int nfill,
+                                        int* work) {
   extern __shared__ __align__(16) unsigned char smem[];
   // layout: deep-program stack, pool, descriptors, four words (depth, z flag,
-  // next fill unit), job prefix
+  // next fill unit, next band tile), job prefix
   int* spre = reinterpret_cast<int*>(smem + (size_t)kMaxDepth * kBlock * 4 + (size_t)kBuildPool * 4 +
                                      kMaxOps * 16) + 4;
   int* rpre = spre + spre_len(njobs);  // first fill unit of each job
@@ -1595,8 +1596,33 @@ __global__ void __maxnreg__(80) k_build(const Job* __restrict__ jobs, int njobs,
   // warps that run out of band tiles take fill units too.  Each unit is
   // written by exactly one warp, so the output does not depend on who.
   const int G = gridDim.x;
-  if (tid < kBlock)
-    for (int gi_ = blockIdx.x; gi_ < total; gi_ += G) build_band_tile(jobs, njobs, spre, gi_, smem);
+  if (tid < kBlock) {  // band tiles: as in the VJP, the rest from work[2]
+    int* sgi = spre - 1;
+    int nxt = blockIdx.x;
+    bool have = true;
+    for (;;) {
+      if (tid == 0) {
+        if (!have) nxt = G + atomicAdd(work + 2, 1);
+        *sgi = nxt;
+      }
+      band_sync();
+      const int gi_ = *sgi;
+      if (gi_ >= total) break;
+      if (tid == 0) {
+        have = gi_ + 2 * G < total;
+        if (have) nxt = G + atomicAdd(work + 2, 1);
+      }
+      build_band_tile(jobs, njobs, spre, gi_, smem);  // starts with a band barrier
+    }
+    if (tid == 0) {
+      __threadfence();
+      if (atomicAdd(work + 3, 1) == G - 1) {
+        work[2] = 0;
+        work[3] = 0;
+        __threadfence();
+      }
+    }
+  }
   const int lane = tid & 31;
   while (true) {
     int k = 0;
@@ -2019,7 +2045,7 @@ static_assert(5 * (vjp_smem(1) + 1024) <= 228 * 1024, "VJP shared memory for fiv
 
 __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs, int njobs,
                                                    int* __restrict__ err,
-                                                   float* __restrict__ gtape) {
+                                                   float* __restrict__ gtape, int* work) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* tape = reinterpret_cast<float*>(smem);
   float* pool = tape + kSmemOps * kBlock;
@@ -2034,7 +2060,26 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   job_prefix(jobs, njobs, true, spre);
   const int total = spre[njobs];
-  for (int gi_ = blockIdx.x; gi_ < total; gi_ += gridDim.x) {
+  // Tiles: the first by block index, the rest from the launch's counter
+  // (work[0]); tiles cost very different amounts, so blocks balance.  While
+  // more than two waves of tiles are left the next one is fetched a tile
+  // ahead (the atomic's latency hides behind the tile); near the end only
+  // when free, so that no block holds a tile while it works on another.
+  __shared__ int s_gi[2];  // by iteration parity: a skipped tile has no barrier after the read
+  int nxt = blockIdx.x;    // thread 0's next tile
+  bool have = true;        // thread 0 holds it already
+  for (int it = 0;; ++it) {
+    if (tid == 0) {
+      if (!have) nxt = (int)gridDim.x + atomicAdd(work, 1);
+      s_gi[it & 1] = nxt;
+    }
+    __syncthreads();
+    const int gi_ = s_gi[it & 1];
+    if (gi_ >= total) break;
+    if (tid == 0) {  // fetch ahead while much is left; near the end, when free
+      have = gi_ + 2 * (int)gridDim.x < total;
+      if (have) nxt = (int)gridDim.x + atomicAdd(work, 1);
+    }
     const int jb = job_of(spre, njobs, gi_);
     const Job& J = jobs[jb];
     const GridDev& g = J.g;
@@ -2280,6 +2325,15 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
       }
     }
   }
+  // every block has made its last fetch: the last one to get here resets
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(work + 1, 1) == (int)gridDim.x - 1) {
+      work[0] = 0;
+      work[1] = 0;
+      __threadfence();
+    }
+  }
 }
 
 // ---- the dense field stream --------------------------------------------------
@@ -2462,16 +2516,17 @@ cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream
 }
 
 cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s) {
+  if (!t.work) return cudaErrorInvalidValue;
   const int grid = sms * build_blocks_per_sm(t.njobs);
-  k_build<<<grid, kBuildThreads, build_smem(t.njobs), s>>>(jobs, t.njobs, t.fill_blocks);
+  k_build<<<grid, kBuildThreads, build_smem(t.njobs), s>>>(jobs, t.njobs, t.fill_blocks, t.work);
   return cudaGetLastError();
 }
 
 cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, float* gtape,
                        int gtape_blocks, cudaStream_t s) {
   const int grid = std::min(sms * vjp_blocks_per_sm(t.njobs), gtape_blocks);
-  if (grid < 1 || !gtape) return cudaErrorInvalidValue;
-  k_vjp<<<grid, kBlock, vjp_smem(t.njobs), s>>>(jobs, t.njobs, err, gtape);
+  if (grid < 1 || !gtape || !t.work) return cudaErrorInvalidValue;
+  k_vjp<<<grid, kBlock, vjp_smem(t.njobs), s>>>(jobs, t.njobs, err, gtape, t.work);
   return cudaGetLastError();
 }
 

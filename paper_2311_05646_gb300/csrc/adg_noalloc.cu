@@ -151,8 +151,9 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
   const size_t o_err = take(sizeof(int));
   const size_t o_job = take(sizeof(Job));
-  // this call's counter set, the one its binning clears, the moved active-sample count
-  const size_t o_cnt = take(9 * sizeof(int));
+  // this call's counter set, the one its binning clears, the moved active-sample
+  // count, the persistent kernels' tile counters
+  const size_t o_cnt = take(16 * sizeof(int));
   const size_t o_chain = take(sizeof(int) * nchain);
   const size_t o_act = take(sizeof(int) * std::max(st.nact_table, 1));
   const size_t o_actc = take(sizeof(float) * std::max(st.nact_table, 1));
@@ -210,6 +211,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   // ---- upload, clear, launch (binner -> VJP -> finalize) ----
   NACU(cudaMemsetAsync(d_err, 0, sizeof(int), s));
   NACU(cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), s));
+  NACU(cudaMemsetAsync(d_cnt + 12, 0, 4 * sizeof(int), s));  // the space is shared by all calls
   // the partials' space held other tables in earlier calls
   NACU(cudaMemsetAsync(d_part, 0, sizeof(float) * std::max<size_t>(part, 1), s));
   NACU(cudaMemcpyAsync(d_chain, H.chain, sizeof(int) * nchain, cudaMemcpyHostToDevice, s));
@@ -264,6 +266,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   t.tiles_padded = ((g.T + 127) / 128) * 128;
   t.bin_blocks = t.tiles_padded / 128;
   t.params = D->n_params;
+  t.work = d_cnt + 12;
   NACU(launch_bin(d_job, t, d_err, s));
   NACU(launch_vjp(d_job, t, d_err, sms, d_gtape, sms, s));
   NACU(launch_finalize(d_job, t, s));
