@@ -335,7 +335,11 @@ def run_adg(args):
             "note": ("the VJP reads the fields only of the samples where d eps / d p can be "
                      "nonzero, so it is latency-bound, not HBM-bound; the HBM-bound kernels are "
                      "the build (kernels.build: fill + eps of every sample) and the dense field "
-                     "stream (dense_vjp.stream_*)")}
+                     "stream (dense_vjp.stream_*)") if dom == "vjp" else
+                    ("the build writes fill + eps of every sample; its band tiles (program "
+                     "evaluation, latency-bound) and the constant-tile stream run in separate "
+                     "warps; the VJP (kernels.vjp) reads the fields only where d eps / d p can "
+                     "be nonzero and is latency-bound")}
     # the whole step against the same peak: its algorithmic bytes (fill + eps
     # of every sample, the fields of the active samples) over the step time
     step_bytes = bytes_build + bytes_vjp
