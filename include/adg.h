@@ -204,9 +204,9 @@ adg_status adg_grad_dense(adg_ctx *ctx, adg_design *design, const double *h_para
                           void *stream);
 
 /* ---- batched work ---------------------------------------------------------
- * Many (design, operation) items run as ONE job table: five launches (zero,
- * bin, build, VJP, finalize) whatever the number of designs, their grid sizes
- * or primitive counts.  The binner covers every item's tiles in one grid; the
+ * Many (design, operation) items run as ONE job table: four launches (bin,
+ * build, VJP, finalize) whatever the number of designs, their grid sizes or
+ * primitive counts.  The binner covers every item's tiles in one grid; the
  * build and VJP kernels are persistent and walk a work list of (design, tile)
  * pairs.  The batched form of the same computation as adg_build_eps /
  * adg_grad / adg_grad_real (Sec. 2, steps 2 and 5), for many designs. */
@@ -271,7 +271,7 @@ adg_status adg_profile_read(adg_ctx *ctx, adg_profile_data *out, int32_t reset);
  *     device array of 32 MiB that every GPU loading libadg holds until exit.
  *   - desc, tiles (nullable), h_params: host, as for adg_design_create and
  *     adg_grad; d_efwd, d_eadj, w, d_grad: as for adg_grad (caller-owned).
- *   - Designs needing more than 32 MiB of scratch (tiles x 212 B + partials +
+ *   - Designs needing more than 32 MiB of scratch (tiles x 405 B + partials +
  *     tables), or beyond 4096 primitives / 32768 scalars / 16384 program ops
  *     or parameters, are rejected with ADG_EINVAL and a message saying why.
  *   - The first call on a device sets up the scratch address for that device
