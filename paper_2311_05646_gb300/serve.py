@@ -66,8 +66,9 @@ class Client:
 
 class Server:
     def __init__(self, ctx: adg.Context, mem_budget_bytes: int, max_inflight: int = 2,
-                 graph: bool = False, on_result=None):
+                 graph: bool = False, on_result=None, tuner=None):
         self.ctx = ctx
+        self.tuner = tuner  # tuning.Autotuner: the tile shape per design size class
         self.budget = int(mem_budget_bytes)
         self.used = 0
         self.max_inflight = max_inflight
@@ -96,7 +97,8 @@ class Server:
                 return  # wait for memory; an empty server always admits one
             self.waiting.popleft()
             self.used += need
-            c.design = adg.Design(self.ctx, c.desc)
+            tile = self.tuner.best(c.desc) if self.tuner is not None else None
+            c.design = adg.Design(self.ctx, c.desc, tile=tile)
             c.eps = torch.empty(c.design.shape, dtype=torch.float32, device="cuda")
             c.grad = torch.zeros(c.design.n_params, dtype=torch.float32, device="cuda")
             c.grad_host = torch.zeros(c.design.n_params, dtype=torch.float32).pin_memory()
