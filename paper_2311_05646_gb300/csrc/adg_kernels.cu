@@ -1,13 +1,14 @@
 // adg_kernels.cu -- sm_103a kernels of libadg.
 //
-//   k_bin       per tile: classify every primitive against the tile (outside /
-//               inside / edge band) and fold the chained logic program with
-//               the constants, leaving only the band primitives (hot-path row
-//               "binner"; the paper's suggestion of restricting work to the
-//               non-zero material-Jacobian support, Sec. 3 footnote, Sec. 7).
-//   k_build     per tile: eps_c = eps_bg + deps * fill_c, fill from the folded
-//               program evaluated at every Yee sample (Eq. eps; Table 4;
-//               Eqs. union / intersection; Sec. 5.1).
+//   k_bin       one warp per tile: classify every primitive against the tile
+//               (outside / inside / edge band) and fold the chained logic
+//               program with the constants, leaving only the band primitives
+//               (the restriction of work to the non-zero material-Jacobian
+//               support that the paper suggests, Sec. 3 footnote, Sec. 7).
+//   k_build     eps_c = eps_bg + deps * fill_c at every Yee sample (Eq. eps;
+//               Table 4; Eqs. union / intersection; Sec. 5.1): persistent,
+//               warp-specialised blocks -- band warps evaluate the folded
+//               program of band tiles, a fill warp streams constant tiles.
 //   k_vjp       per band tile: the reverse sweep of Eqs. AD / jaceps seeded
 //               with Re(w E_adj E) (Eq. 1): forward tape, reverse logic
 //               adjoints, primitive derivatives, warp-shuffle reduction per
@@ -15,6 +16,11 @@
 //   k_finalize  per parameter: fixed-order sum of the block partials through
 //               the parameter map (deterministic, FP64); it clears every
 //               partial it reads, so the next VJP starts from zero.
+//   k_dense,    the dense form's field stream: Re(w E_adj E) and its product
+//   k_dense_final  with fill summed over every sample, per chunk, then in
+//               chunk order.
+// The build and the VJP take band tiles from a counter of their launch, so
+// that tiles of very different cost balance over the blocks.
 #include <limits.h>
 #include <math.h>
 #include <stdint.h>
