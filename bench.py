@@ -489,6 +489,7 @@ def run_adg(args):
                        "outputs": "fill + eps (fp32) + gradient",
                        "vjp": "band tiles only (tiles crossed by an edge band)",
                        "tile": list(stats["tile"]), "tile_autotuned": tuned,
+                       "build_fill_warps": int(tile[3]) if tile is not None and len(tile) > 3 else 1,
                        "program_tiles": stats["program_tiles"],
                        "tiles": stats["tiles"], "band_cells": stats["band_cells"],
                        "vjp_active_samples": stats["active_samples"],

@@ -51,7 +51,7 @@ class adg_design_desc(ctypes.Structure):
 
 class adg_tile_opts(ctypes.Structure):
     _fields_ = [("tx", ctypes.c_int32), ("ty", ctypes.c_int32), ("tz", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("fill_warps", ctypes.c_int32)]
 
 
 K_NAMES = {0: "bin", 1: "build", 2: "vjp", 3: "finalize", 4: "prepare", 5: "fill", 6: "dense"}
@@ -188,8 +188,10 @@ class Design:
         D.prim_kr = arr(pr["kr"], np.float64)
         D.ops = arr(desc["ops"], np.int32)
         T = adg_tile_opts(0, 0, 0, 0)
-        if tile is not None:
-            T.tx, T.ty, T.tz = (int(v) for v in tile)
+        if tile is not None:  # (tx, ty, tz) or (tx, ty, tz, build fill warps)
+            T.tx, T.ty, T.tz = (int(v) for v in tile[:3])
+            if len(tile) > 3:
+                T.fill_warps = int(tile[3])
         self.handle = ctypes.c_void_p()
         _check(lib().adg_design_create(ctx.handle, ctypes.byref(D), ctypes.byref(T),
                                        ctypes.byref(self.handle)))
@@ -361,7 +363,7 @@ def adg_grad_noalloc(desc: dict, params, efwd, eadj, w, grad, tile=None, stream=
     D.ops = arr(desc["ops"], np.int32)
     T = adg_tile_opts(0, 0, 0, 0)
     if tile is not None:
-        T.tx, T.ty, T.tz = (int(v) for v in tile)
+        T.tx, T.ty, T.tz = (int(v) for v in tile[:3])
     p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
     if p.size != D.n_params:
         raise ValueError("expected %d parameters, got %d" % (D.n_params, p.size))

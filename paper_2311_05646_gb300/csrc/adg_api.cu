@@ -131,6 +131,7 @@ struct ProfScope {
 struct adg_design {
   adg_ctx* ctx = nullptr;
   GridDev g{};
+  int fill_warps = 1;  // build: warps streaming constant tiles per block
   double d[3]{}, o[3]{};
   int n_params = 0, n_q = 0, n_prims = 0;
   std::vector<double> q_base, q_coeff, kr;
@@ -256,6 +257,9 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   if (host::validate(D, m) != ADG_OK) return fail(ADG_EINVAL, "%s", m.text);
   int tx = 32, ty = 4, tz = 4;
   if (tiles && (tiles->tx || tiles->ty || tiles->tz)) { tx = tiles->tx; ty = tiles->ty; tz = tiles->tz; }
+  const int fill_warps = tiles && tiles->fill_warps ? tiles->fill_warps : 1;
+  if (fill_warps < 1 || fill_warps > kMaxFillWarps)
+    return fail(ADG_EINVAL, "fill_warps %d: 1 or 2 (0 = 1)", tiles->fill_warps);
   if (!host::tile_ok(tx, ty, tz))
     return fail(ADG_EINVAL,
                 "tile %dx%dx%d: tx in {32,64}, ty in {1..16}, tz in {1..8}, powers of 2, %d..%d cells",
@@ -276,6 +280,7 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
 
   CU(cudaSetDevice(ctx->device));
   adg_design* d = new adg_design();
+  d->fill_warps = fill_warps;
   d->ctx = ctx;
   d->chain = chain;
   d->n_params = D->n_params;
@@ -496,6 +501,7 @@ adg_status run_single(adg_ctx* ctx, adg_design* d, const double* h_params, float
   t.fill_blocks = d_eps ? (d->g.C * d->g.nz * d->g.ny + kFillRows - 1) / kFillRows : 0;
   t.params = grad ? d->n_params : 0;
   t.work = d->d_counters + 12;
+  t.fill_warps = d->fill_warps;
   st = run_jobs(ctx, d->d_job, t, rebin, d_eps != nullptr, grad, d->g.T, s);
   if (st == ADG_OK) d->partial_dirty = false;
   return st;
@@ -719,10 +725,11 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   t.fill_blocks = row_base;
   t.params = param_base;
   t.work = A.d_work;
+  t.fill_warps = 1;
   sig = mix(sig, (uint64_t)bytes);
   sig = mix(sig, (uint64_t)tile_base);
   sig = mix(sig, (uint64_t)param_base);
-  build_blocks_per_sm(t.njobs);  // kernel attributes are set before any capture
+  build_blocks_per_sm(t.njobs, t.fill_warps);  // kernel attributes are set before any capture
   vjp_blocks_per_sm(t.njobs);
   const bool graph = (flags & ADG_BATCH_GRAPH) && !ctx->prof;
   if (graph && A.exec && A.sig == sig) {

@@ -183,9 +183,11 @@ struct JobTotals {
   // done, build next tile, build blocks done.  Zero between launches: the
   // last block of a launch resets its pair.  One launch at a time per array.
   int* work;
+  int fill_warps;  // build: warps per block streaming constant tiles (1 .. kMaxFillWarps)
 };
 
 constexpr int kMaxJobs = 1024;  // jobs in one table (one batch)
+constexpr int kMaxFillWarps = 2;
 
 cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s);
 cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s);
@@ -198,7 +200,7 @@ cudaError_t launch_finalize(const Job* jobs, const JobTotals& t, cudaStream_t s)
 cudaError_t launch_dense(const DenseArgs& a, int sms, cudaStream_t s);
 // Shared-memory limits of the kernels; call once per device before any capture.
 cudaError_t init_kernel_attributes();
-int build_blocks_per_sm(int njobs);
+int build_blocks_per_sm(int njobs, int fill_warps);
 int vjp_blocks_per_sm(int njobs);
 void set_last_error(const char* msg);  // the thread-local text of adg_last_error()
 

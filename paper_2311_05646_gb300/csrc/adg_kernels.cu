@@ -1119,8 +1119,6 @@ struct TileLoc {
 static_assert(sizeof(LeafTab) == kLeafTabBytes, "pool accounting");
 // job-prefix entries in shared memory: a class for small tables, one for any
 __host__ __device__ constexpr int spre_len(int njobs) { return (njobs + 16) & ~15; }
-constexpr int kFillWarps = 1;  // build: warps that stream constant-tile rows beside the band warps
-constexpr int kBuildThreads = kBlock + 32 * kFillWarps;
 constexpr size_t kBuildFixed = (size_t)kMaxDepth * kBlock * 4 + (size_t)kBuildPool * 4 +
                                kMaxOps * 16 + 16;
 size_t build_smem(int njobs) { return kBuildFixed + 2 * (size_t)spre_len(njobs) * 4; }
@@ -1581,7 +1579,7 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
 // their factor tables, the folded program run at every sample (two samples
 // per thread, register stack; a shared-memory stack for deeper programs) --
 // and the streaming fill of the constant tiles.
-// five blocks of 160 threads per SM: 80 registers
+// 80 registers: four blocks of 160 or 192 threads per SM
 __global__ void __maxnreg__(80) k_build(const Job* __restrict__ jobs, int njobs, int nfill,
                                         int* work) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -2495,14 +2493,17 @@ cudaError_t init_kernel_attributes() {
 
 // Resident blocks per SM for a job table of njobs jobs (the job prefix in
 // shared memory grows with it), cached per job count.
-int build_blocks_per_sm(int njobs) {
-  static int v[kMaxJobs + 1] = {};
+int build_blocks_per_sm(int njobs, int fill_warps) {
+  static int v[kMaxFillWarps][kMaxJobs + 1] = {};
   njobs = std::min(std::max(njobs, 1), kMaxJobs);
-  if (!v[njobs]) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v[njobs], k_build, kBuildThreads, build_smem(njobs));
-    if (v[njobs] < 1) v[njobs] = 1;
+  fill_warps = std::min(std::max(fill_warps, 1), kMaxFillWarps);
+  int& r = v[fill_warps - 1][njobs];
+  if (!r) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_build, kBlock + 32 * fill_warps,
+                                                  build_smem(njobs));
+    if (r < 1) r = 1;
   }
-  return v[njobs];
+  return r;
 }
 
 int vjp_blocks_per_sm(int njobs) {
@@ -2522,9 +2523,10 @@ cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream
 }
 
 cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s) {
-  if (!t.work) return cudaErrorInvalidValue;
-  const int grid = sms * build_blocks_per_sm(t.njobs);
-  k_build<<<grid, kBuildThreads, build_smem(t.njobs), s>>>(jobs, t.njobs, t.fill_blocks, t.work);
+  if (!t.work || t.fill_warps < 1 || t.fill_warps > kMaxFillWarps) return cudaErrorInvalidValue;
+  const int grid = sms * build_blocks_per_sm(t.njobs, t.fill_warps);
+  k_build<<<grid, kBlock + 32 * t.fill_warps, build_smem(t.njobs), s>>>(jobs, t.njobs,
+                                                                       t.fill_blocks, t.work);
   return cudaGetLastError();
 }
 
