@@ -341,7 +341,9 @@ def run_adg(args):
     achieved = kern[dom] / (avg_ms * 1e-3) / 1e9
     peaks = _peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    traffic = _traffic(dom, stats["tile"])
+    fill_warps = int(tile[3]) if tile is not None and len(tile) > 3 else 1
+    opts = list(stats["tile"]) + ([fill_warps] if fill_warps > 1 else [])
+    traffic = _traffic(dom, opts)
     roof = {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "algorithmic_bytes_per_launch": kern[dom],
@@ -410,7 +412,7 @@ def run_adg(args):
                  "stream_bytes_per_launch": stream_bytes, "stream_us_per_launch": us_k,
                  "stream_GBps": stream_bytes / (us_k * 1e-6) / 1e9,
                  "stream_frac_of_measured_hbm": stream_bytes / (us_k * 1e-6) / 1e9 / peak,
-                 "stream_traffic": _traffic("dense", stats["tile"]),
+                 "stream_traffic": _traffic("dense", opts),
                  "call_GBps": (stream_bytes + kern["vjp"]) / (ms_dense * 1e-3) / 1e9,
                  "call_frac_of_measured_hbm": (stream_bytes + kern["vjp"]) / (ms_dense * 1e-3) / 1e9 / peak,
                  "vjp_us_per_launch": 1e3 * dprof["vjp"][1] / max(dprof["vjp"][0], 1)}
@@ -489,7 +491,7 @@ def run_adg(args):
                        "outputs": "fill + eps (fp32) + gradient",
                        "vjp": "band tiles only (tiles crossed by an edge band)",
                        "tile": list(stats["tile"]), "tile_autotuned": tuned,
-                       "build_fill_warps": int(tile[3]) if tile is not None and len(tile) > 3 else 1,
+                       "build_fill_warps": fill_warps,
                        "program_tiles": stats["program_tiles"],
                        "tiles": stats["tiles"], "band_cells": stats["band_cells"],
                        "vjp_active_samples": stats["active_samples"],

@@ -223,6 +223,20 @@ def test_long_chains_span_binner_segments(ctx, oracle_mod):
     _check_build(ctx, desc2, oracle_mod)
 
 
+def test_build_fill_warps_agree(ctx, oracle_mod):
+    """The build's second fill warp (tile option) changes who writes the
+    constant tiles, not what is written: fill and eps equal bit for bit, and
+    the fill matches the oracle.  Other counts are rejected."""
+    from paper_2311_05646_gb300 import adg
+    desc = I.grating_3d(n=(150, 36, 60), teeth=8, pitch=600.0)
+    f1, e1 = H.run_build(_design(ctx, desc, (32, 8, 4)), desc)
+    f2, e2 = H.run_build(_design(ctx, desc, (32, 8, 4, 2)), desc)
+    assert np.array_equal(f1, f2) and np.array_equal(e1, e2)
+    assert np.abs(f2 - oracle_mod.fill(desc)).max() <= H.FILL_TOL
+    with pytest.raises(adg.AdgError):
+        _design(ctx, desc, (32, 8, 4, 3))
+
+
 def test_partials_and_counts_reset_between_calls(ctx):
     """The finalize clears the partials it sums and moves the active-sample
     count, so a call after others (same bins, or a rebin with another partial
