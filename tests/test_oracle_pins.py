@@ -554,3 +554,65 @@ def test_fixture_poly2d_winding_independent(oracle_mod):
                 assert out[0][j, i] > 1 - 1e-6
             elif a == 0.0:
                 assert out[0][j, i] < 1e-6
+
+
+# ------------------------------------- topology special case (Sec. 3.1) ------
+def _topo_case(seed=3):
+    from oracle import topology as T
+    rng = np.random.default_rng(seed)
+    n, C = (7, 6, 5), 3
+    region = (1, 2, 4, 3, 1, 4)       # 4 x 3 pixels, broadcast to z = 1, 2, 3
+    v = rng.normal(0.0, 1.5, 12)
+    shape = (C, n[2], n[1], n[0])
+    ef = (rng.normal(size=shape) + 1j * rng.normal(size=shape)).astype(np.complex64)
+    ea = (rng.normal(size=shape) + 1j * rng.normal(size=shape)).astype(np.complex64)
+    w = rng.normal(size=C) + 1j * rng.normal(size=C)
+    return T, n, C, region, v, ef, ea, w
+
+
+def test_topology_gradient_matches_central_differences():
+    """Eq. top_AD against central differences of the loss whose gradient it
+    is (L is smooth in v; h = 1e-5 in FP64)."""
+    T, n, C, region, v, ef, ea, w = _topo_case()
+    g = T.grad(n, C, region, v, 8.0, ef, ea, w)
+    h = 1e-5
+    fd = np.zeros_like(g)
+    for i in range(v.size):
+        vp, vm = v.copy(), v.copy()
+        vp[i] += h
+        vm[i] -= h
+        fd[i] = (T.loss(n, C, region, vp, 2.0, 8.0, ef, ea, w) -
+                 T.loss(n, C, region, vm, 2.0, 8.0, ef, ea, w)) / (2 * h)
+    assert np.abs(g - fd).max() <= 1e-6 * np.abs(fd).max()
+
+
+def test_topology_forward_special_values():
+    """Eq. TO_example: sigma(0) = 1/2 puts every region sample halfway between
+    the bounds, saturated v reaches the bounds, and samples outside the
+    region (or outside its z cells) keep their value."""
+    T, n, C, region, v, ef, ea, w = _topo_case()
+    x0, y0, rx, ry, z0, z1 = region
+    e = T.eps(n, C, region, np.zeros(rx * ry), 2.0, 8.0, eps_out=-1.0)
+    assert np.all(e[:, z0:z1, y0:y0 + ry, x0:x0 + rx] == 6.0)
+    inside = np.zeros(e.shape, bool)
+    inside[:, z0:z1, y0:y0 + ry, x0:x0 + rx] = True
+    assert np.all(e[~inside] == -1.0)
+    hi = T.eps(n, C, region, np.full(rx * ry, 60.0), 2.0, 8.0)
+    lo = T.eps(n, C, region, np.full(rx * ry, -60.0), 2.0, 8.0)
+    assert np.allclose(hi[inside], 10.0, atol=1e-12) and np.allclose(lo[inside], 2.0, atol=1e-12)
+
+
+def test_topology_reduces_to_the_im_form():
+    """With w = -2 i omega (Eq. 1), one component and a one-cell z range, the
+    gradient at v = 0 (sigma (1 - sigma) = 1/4) is 2 omega deps Im(E E_adj) / 4
+    at each pixel: the paper's unconstrained form times the sigmoid slope."""
+    from oracle import topology as T
+    rng = np.random.default_rng(8)
+    n, region = (5, 4, 1), (0, 0, 5, 4, 0, 1)
+    shape = (1, 1, 4, 5)
+    ef = (rng.normal(size=shape) + 1j * rng.normal(size=shape)).astype(np.complex64)
+    ea = (rng.normal(size=shape) + 1j * rng.normal(size=shape)).astype(np.complex64)
+    omega, deps = 1.7, 3.0
+    g = T.grad(n, 1, region, np.zeros(20), deps, ef, ea, -2j * omega)
+    z = ef[0, 0].astype(np.complex128) * ea[0, 0].astype(np.complex128)
+    assert np.allclose(g, (2 * omega * deps * z.imag / 4).reshape(-1), rtol=1e-12, atol=0)
