@@ -417,6 +417,43 @@ def run_adg(args):
                  "call_frac_of_measured_hbm": (stream_bytes + kern["vjp"]) / (ms_dense * 1e-3) / 1e9 / peak,
                  "vjp_us_per_launch": 1e3 * dprof["vjp"][1] / max(dprof["vjp"][0], 1)}
 
+    # the topology special case (Sec. 3.1) on the same grid and fields: every
+    # (x, y) pixel of the grid a parameter, broadcast over 16 z cells through
+    # the slab; both kernels are HBM streams
+    topo = None
+    if not args.no_dense:
+        z0 = max(0, nz // 2 - 8)
+        region = (0, 0, nx, ny, z0, min(nz, z0 + 16))
+        npix = nx * ny
+        nsamp = npix * (region[5] - region[4]) * C
+        vt = torch.randn(npix, dtype=torch.float32, device="cuda")
+        gt = torch.empty(npix, dtype=torch.float32, device="cuda")
+        et = torch.empty_like(eps)
+        nt = 50
+
+        def t_topo(fn):
+            for _ in range(5):
+                fn()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(nt):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / nt
+
+        us_e = 1e3 * t_topo(lambda: adg.adg_topo_eps(ctx, (nx, ny, nz), C, region, vt, 2.085, 10.025,
+                                                      et, stream=stream))
+        us_g = 1e3 * t_topo(lambda: adg.adg_topo_grad(ctx, (nx, ny, nz), C, region, vt, 10.025, efd,
+                                                       ead, w, gt, stream=stream))
+        b_e, b_g = nsamp * 4 + npix * 4, nsamp * 16 + npix * 8
+        topo = {"region": list(region), "pixels": npix, "samples": nsamp,
+                "eps_us": us_e, "eps_GBps": b_e / (us_e * 1e-6) / 1e9,
+                "eps_frac_of_measured_hbm": b_e / (us_e * 1e-6) / 1e9 / peak,
+                "grad_us": us_g, "grad_GBps": b_g / (us_g * 1e-6) / 1e9,
+                "grad_frac_of_measured_hbm": b_g / (us_g * 1e-6) / 1e9 / peak,
+                "bytes": {"eps": b_e, "grad": b_g}}
+
     # end to end through the public API: host (pinned) fields in, eps + g out
     e2e = None
     if not args.no_e2e:
@@ -498,7 +535,8 @@ def run_adg(args):
                        "l2": "inputs larger than L2 (fields 691 MB + outputs 346 MB per step)"},
             "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
             "gpu_launches": launches,
-            "cpu_baseline": cpu, "e2e": e2e, "dense_vjp": dense, "clocks": clocks.summary(),
+            "cpu_baseline": cpu, "e2e": e2e, "dense_vjp": dense, "topology": topo,
+            "clocks": clocks.summary(),
         }
         print(json.dumps(line))
     if dist is not None:

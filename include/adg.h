@@ -206,6 +206,33 @@ adg_status adg_grad_dense(adg_ctx *ctx, adg_design *design, const double *h_para
                           const float *w, const float *d_fill, float *d_grad, double *d_gmat,
                           void *stream);
 
+/* ---- the bi-level topology special case (Sec. 3.1) ------------------------
+ * Every pixel of a 2D design region is its own parameter v_p, broadcast along z
+ * over the region's cells (the matrix B of Eq. TO_example):
+ *   eps_c(x, y, z) = eps_l + deps sigma(v_p), sigma the logistic sigmoid, for
+ *   every component c, pixel p = (x - x0, y - y0) and z0 <= z < z1;
+ *   g_p = deps sigma(v_p) (1 - sigma(v_p)) sum_c sum_{z0 <= z < z1}
+ *         Re(w_c E_adj,c E_fwd,c)(x, y, z)                       (Eq. top_AD)
+ * (w = -2 i omega gives the paper's 2 omega Im(E E_adj); no conjugate).
+ * grid: the field layout (nx, ny, nz, ncomp; spacing and offsets unused).
+ * d_v, d_grad: device fp32 [ny][nx] of the region (x fastest), caller-owned.
+ * d_eps: device fp32 [ncomp][nz][ny][nx]; only the region's samples are
+ * written.  d_efwd / d_eadj / w: as for adg_grad.  A region outside the grid,
+ * an empty one or a NULL argument returns ADG_EINVAL before any launch.
+ * Asynchronous on `stream`; g is reproducible bit for bit. */
+typedef struct {
+  int32_t x0, y0;  /* first pixel (cells)                               */
+  int32_t nx, ny;  /* pixels; v has nx * ny entries                      */
+  int32_t z0, z1;  /* the cells [z0, z1) every pixel is broadcast to     */
+} adg_topo_region;
+adg_status adg_topo_eps(adg_ctx *ctx, const adg_grid *grid, const adg_topo_region *region,
+                        const float *d_v, double eps_l, double deps, float *d_eps,
+                        void *stream);
+adg_status adg_topo_grad(adg_ctx *ctx, const adg_grid *grid, const adg_topo_region *region,
+                         const float *d_v, double deps, const float *const d_efwd[3],
+                         const float *const d_eadj[3], const float *w, float *d_grad,
+                         void *stream);
+
 /* ---- batched work ---------------------------------------------------------
  * Many (design, operation) items run as ONE job table: four launches (bin,
  * build, VJP, finalize) whatever the number of designs, their grid sizes or

@@ -37,6 +37,11 @@ class adg_grid(ctypes.Structure):
                 ("oz", ctypes.c_double), ("off", (ctypes.c_double * 3) * 3)]
 
 
+class adg_topo_region(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_int32), ("y0", ctypes.c_int32), ("nx", ctypes.c_int32),
+                ("ny", ctypes.c_int32), ("z0", ctypes.c_int32), ("z1", ctypes.c_int32)]
+
+
 class adg_design_desc(ctypes.Structure):
     _fields_ = [("grid", adg_grid), ("eps_bg", ctypes.c_double), ("eps_fg", ctypes.c_double),
                 ("logic", ctypes.c_int32), ("n_params", ctypes.c_int32), ("n_q", ctypes.c_int32),
@@ -92,6 +97,10 @@ def lib():
                 "adg_design_stats": [P, P, P, ctypes.POINTER(adg_stats)],
                 "adg_profile_enable": [P, I32],
                 "adg_profile_read": [P, ctypes.POINTER(adg_profile_data), I32],
+                "adg_topo_eps": [P, ctypes.POINTER(adg_grid), ctypes.POINTER(adg_topo_region), P,
+                                 ctypes.c_double, ctypes.c_double, P, P],
+                "adg_topo_grad": [P, ctypes.POINTER(adg_grid), ctypes.POINTER(adg_topo_region), P,
+                                  ctypes.c_double, P, P, P, P, P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -483,3 +492,62 @@ def adg_batch_wait(ctx: Context, ticket: int, timeout_s: float = 60.0) -> None:
     L.adg_batch_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]
     L.adg_batch_wait.restype = ctypes.c_int
     _check(L.adg_batch_wait(ctx.handle, ticket, int(timeout_s * 1e9)))
+
+
+# ------------------------------------------------------- topology (Sec. 3.1) --
+def _topo_grid(n, ncomp):
+    G = adg_grid()
+    G.nx, G.ny, G.nz = (int(v) for v in n)
+    G.ncomp = int(ncomp)
+    return G
+
+
+def _topo_region(region):
+    R = adg_topo_region()
+    R.x0, R.y0, R.nx, R.ny, R.z0, R.z1 = (int(v) for v in region)
+    return R
+
+
+def _topo_v(v, region, name="v"):
+    import torch
+    n = int(region[2]) * int(region[3])
+    if v.dtype != torch.float32 or v.numel() != n or not v.is_cuda or not v.is_contiguous():
+        raise ValueError("%s must be a contiguous float32 CUDA tensor of %d entries" % (name, n))
+
+
+def adg_topo_eps(ctx: Context, n, ncomp, region, v, eps_l, deps, eps, stream=None):
+    """eps (ncomp, nz, ny, nx) <- eps_l + deps sigmoid(v) over the region
+    (x0, y0, nx, ny, z0, z1), broadcast along z (Eq. TO_example)."""
+    import torch
+    _topo_v(v, region)
+    shape = (int(ncomp), int(n[2]), int(n[1]), int(n[0]))
+    if eps.dtype != torch.float32 or tuple(eps.shape) != shape or not eps.is_cuda or not eps.is_contiguous():
+        raise ValueError("eps must be a contiguous float32 CUDA tensor of shape %s" % (shape,))
+    G, R = _topo_grid(n, ncomp), _topo_region(region)
+    _check(lib().adg_topo_eps(ctx.handle, ctypes.byref(G), ctypes.byref(R), _dptr(v), float(eps_l),
+                              float(deps), _dptr(eps), _stream_ptr(stream)))
+
+
+def adg_topo_grad(ctx: Context, n, ncomp, region, v, deps, efwd, eadj, w, grad, stream=None):
+    """grad (per pixel) <- deps sigmoid'(v) sum_c sum_z Re(w_c E_adj,c E_fwd,c)
+    over the region (Eq. top_AD)."""
+    import torch
+    _topo_v(v, region)
+    _topo_v(grad, region, "grad")
+    C = int(ncomp)
+    shape = (C, int(n[2]), int(n[1]), int(n[0]))
+    for t, name in ((efwd, "efwd"), (eadj, "eadj")):
+        if t.dtype != torch.complex64 or tuple(t.shape) != shape or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous complex64 CUDA tensor of shape %s" % (name, shape))
+    ef = (ctypes.c_void_p * 3)(*[efwd[c].data_ptr() if c < C else 0 for c in range(3)])
+    ea = (ctypes.c_void_p * 3)(*[eadj[c].data_ptr() if c < C else 0 for c in range(3)])
+    wc = np.asarray(w, dtype=np.complex128).reshape(-1)
+    if wc.size == 1:
+        wc = np.repeat(wc, C)
+    ww = np.zeros(6, dtype=np.float32)
+    ww[0:2 * C:2] = wc.real[:C]
+    ww[1:2 * C:2] = wc.imag[:C]
+    G, R = _topo_grid(n, ncomp), _topo_region(region)
+    _check(lib().adg_topo_grad(ctx.handle, ctypes.byref(G), ctypes.byref(R), _dptr(v), float(deps),
+                               ef, ea, ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad),
+                               _stream_ptr(stream)))

@@ -583,6 +583,76 @@ extern "C" adg_status adg_grad_dense(adg_ctx* ctx, adg_design* d, const double* 
   return ADG_OK;
 }
 
+// ------------------------------------------------------- topology (Sec. 3.1) -
+namespace {
+
+adg_status topo_args(const adg_grid* grid, const adg_topo_region* r, const float* d_v,
+                     const char* who, TopoArgs& a) {
+  if (!grid || !r || !d_v) return fail(ADG_EINVAL, "%s: NULL argument", who);
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || grid->ncomp < 1 || grid->ncomp > 3)
+    return fail(ADG_EINVAL, "%s: grid %dx%dx%d with %d components", who, grid->nx, grid->ny,
+                grid->nz, grid->ncomp);
+  if (r->nx < 1 || r->ny < 1 || r->x0 < 0 || r->y0 < 0 || r->x0 + r->nx > grid->nx ||
+      r->y0 + r->ny > grid->ny || r->z0 < 0 || r->z1 <= r->z0 || r->z1 > grid->nz ||
+      (long long)r->nx * r->ny > (1LL << 30))
+    return fail(ADG_EINVAL, "%s: region x [%d, %d) y [%d, %d) z [%d, %d) outside the %dx%dx%d grid",
+                who, r->x0, r->x0 + r->nx, r->y0, r->y0 + r->ny, r->z0, r->z1, grid->nx, grid->ny,
+                grid->nz);
+  a = TopoArgs{};
+  a.nx = grid->nx;
+  a.ny = grid->ny;
+  a.nz = grid->nz;
+  a.C = grid->ncomp;
+  a.x0 = r->x0;
+  a.y0 = r->y0;
+  a.rx = r->nx;
+  a.ry = r->ny;
+  a.z0 = r->z0;
+  a.z1 = r->z1;
+  a.v = d_v;
+  return ADG_OK;
+}
+
+}  // namespace
+
+extern "C" adg_status adg_topo_eps(adg_ctx* ctx, const adg_grid* grid, const adg_topo_region* r,
+                                   const float* d_v, double eps_l, double deps, float* d_eps,
+                                   void* stream) {
+  if (!ctx || !d_eps) return fail(ADG_EINVAL, "adg_topo_eps: NULL argument");
+  TopoArgs a;
+  const adg_status st = topo_args(grid, r, d_v, "adg_topo_eps", a);
+  if (st != ADG_OK) return st;
+  a.eps_l = (float)eps_l;
+  a.deps = (float)deps;
+  a.eps = d_eps;
+  CU(cudaSetDevice(ctx->device));
+  CU(launch_topo_eps(a, ctx->sms, (cudaStream_t)stream));
+  return ADG_OK;
+}
+
+extern "C" adg_status adg_topo_grad(adg_ctx* ctx, const adg_grid* grid, const adg_topo_region* r,
+                                    const float* d_v, double deps, const float* const d_efwd[3],
+                                    const float* const d_eadj[3], const float* w, float* d_grad,
+                                    void* stream) {
+  if (!ctx || !d_efwd || !d_eadj || !w || !d_grad)
+    return fail(ADG_EINVAL, "adg_topo_grad: NULL argument");
+  TopoArgs a;
+  const adg_status st = topo_args(grid, r, d_v, "adg_topo_grad", a);
+  if (st != ADG_OK) return st;
+  for (int c = 0; c < a.C; ++c) {
+    if (!d_efwd[c] || !d_eadj[c])
+      return fail(ADG_EINVAL, "adg_topo_grad: field of component %d is NULL", c);
+    a.ef[c] = reinterpret_cast<const float2*>(d_efwd[c]);
+    a.ea[c] = reinterpret_cast<const float2*>(d_eadj[c]);
+    a.w[c] = make_float2(w[2 * c], w[2 * c + 1]);
+  }
+  a.deps = (float)deps;
+  a.grad = d_grad;
+  CU(cudaSetDevice(ctx->device));
+  CU(launch_topo_grad(a, ctx->sms, (cudaStream_t)stream));
+  return ADG_OK;
+}
+
 // ------------------------------------------------------------------ batches -
 namespace {
 

@@ -116,6 +116,22 @@ struct VjpArgs {
   const float* G;  // real-seed mode when non-null
 };
 
+// The topology special case (Sec. 3.1): a region of rx x ry pixels at
+// (x0, y0) broadcast along z over [z0, z1), one parameter v per pixel.
+struct TopoArgs {
+  int nx, ny, nz, C;
+  int x0, y0, rx, ry, z0, z1;
+  const float* v;     // rx ry, x fastest
+  float eps_l, deps;
+  float* eps;         // [C][nz][ny][nx] (eps build)
+  const float2* ef[3];
+  const float2* ea[3];
+  float2 w[3];
+  float* grad;        // rx ry (gradient)
+};
+cudaError_t launch_topo_eps(const TopoArgs& a, int sms, cudaStream_t s);
+cudaError_t launch_topo_grad(const TopoArgs& a, int sms, cudaStream_t s);
+
 // The dense field stream of adg_grad_dense: every sample's
 // z = Re(w E_adj E_fwd) and z * fill, summed per chunk of kDenseChunk
 // samples (chunks handed out by an atomic counter, partials stored by chunk
