@@ -277,7 +277,7 @@ def run_adg(args):
         tile = None
     else:
         from paper_2311_05646_gb300.tuning import Autotuner
-        tile = Autotuner(ctx, reps=8).best(desc, fields=(efd, ead))
+        tile = Autotuner(ctx, reps=16).best(desc, fields=(efd, ead))
         tuned = True
     design = adg.Design(ctx, desc, tile=tile)
     fill = torch.empty(design.shape, dtype=torch.float32, device="cuda")
