@@ -454,6 +454,38 @@ def run_adg(args):
                 "grad_frac_of_measured_hbm": b_g / (us_g * 1e-6) / 1e9 / peak,
                 "bytes": {"eps": b_e, "grad": b_g}}
 
+    # the paper's comparison (Sec. 3, Sec. 6): the finite-difference gradient
+    # -- two builds per parameter with the library's own exact mesher and a
+    # dot product with Re(w E_adj E) -- against the AutoDiff gradient, on the
+    # same GPU, fields and parameters
+    fdc = None
+    if not args.no_dense:
+        gfd = torch.zeros_like(g)
+        gad = torch.zeros_like(g)
+        adg.adg_grad(design, p0, efd, ead, w, gad, stream=stream)
+        adg.adg_grad_fd(design, p0, efd, ead, w, 0.5, gfd, stream=stream)
+        adg.adg_sync(ctx, stream)
+        torch.cuda.synchronize()
+        nf = 3
+        e0.record(stream)
+        for _ in range(nf):
+            adg.adg_grad_fd(design, p0, efd, ead, w, 0.5, gfd, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_fd = e0.elapsed_time(e1) / nf
+        e0.record(stream)
+        for _ in range(nf * 20):
+            adg.adg_grad(design, params[_ % 2], efd, ead, w, gad, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_ad = e0.elapsed_time(e1) / (nf * 20)
+        adg.adg_grad(design, p0, efd, ead, w, gad, stream=stream)
+        adg.adg_sync(ctx, stream)
+        ga, gf = gad.double(), gfd.double()
+        fdc = {"params": int(design.n_params), "h_nm": 0.5, "fd_builds": 2 * int(design.n_params),
+               "fd_ms": ms_fd, "ad_ms": ms_ad, "ad_speedup": ms_fd / ms_ad,
+               "fd_vs_ad_rel_l2": float((gf - ga).norm() / ga.norm())}
+
     # end to end through the public API: host (pinned) fields in, eps + g out
     e2e = None
     if not args.no_e2e:
@@ -536,6 +568,7 @@ def run_adg(args):
             "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
             "gpu_launches": launches,
             "cpu_baseline": cpu, "e2e": e2e, "dense_vjp": dense, "topology": topo,
+            "fd_vs_ad": fdc,
             "clocks": clocks.summary(),
         }
         print(json.dumps(line))

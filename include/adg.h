@@ -206,6 +206,19 @@ adg_status adg_grad_dense(adg_ctx *ctx, adg_design *design, const double *h_para
                           const float *w, const float *d_fill, float *d_grad, double *d_gmat,
                           void *stream);
 
+/* The finite-difference gradient that AutoDiff replaces (Sec. 3; the paper's
+ * baseline), on the GPU with the library's own build as the mesher:
+ *   g_k = deps sum_c sum_samples Re(w_c E_adj,c E_fwd,c)
+ *         (fill(p + h e_k) - fill(p - h e_k)) / 2h,
+ * two builds per parameter and one fixed-order dot product each.  Arguments
+ * as for adg_grad; h > 0 in parameter units.  Allocates, per design and on
+ * first use, four fp32 arrays of the grid (ncomp nz ny nx samples each).
+ * Asynchronous on `stream`; reproducible bit for bit.  For measurement and
+ * comparison, not for optimisation loops. */
+adg_status adg_grad_fd(adg_ctx *ctx, adg_design *design, const double *h_params,
+                       const float *const d_efwd[3], const float *const d_eadj[3],
+                       const float *w, double h, float *d_grad, void *stream);
+
 /* ---- the bi-level topology special case (Sec. 3.1) ------------------------
  * Every pixel of a 2D design region is its own parameter v_p, broadcast along z
  * over the region's cells (the matrix B of Eq. TO_example):

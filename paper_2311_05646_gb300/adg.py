@@ -97,6 +97,7 @@ def lib():
                 "adg_design_stats": [P, P, P, ctypes.POINTER(adg_stats)],
                 "adg_profile_enable": [P, I32],
                 "adg_profile_read": [P, ctypes.POINTER(adg_profile_data), I32],
+                "adg_grad_fd": [P, P, P, P, P, P, ctypes.c_double, P, P],
                 "adg_topo_eps": [P, ctypes.POINTER(adg_grid), ctypes.POINTER(adg_topo_region), P,
                                  ctypes.c_double, ctypes.c_double, P, P],
                 "adg_topo_grad": [P, ctypes.POINTER(adg_grid), ctypes.POINTER(adg_topo_region), P,
@@ -275,6 +276,16 @@ def adg_grad(design: Design, params, efwd, eadj, w, grad, stream=None):
     _check(lib().adg_grad(design.ctx.handle, design.handle, p.ctypes.data_as(ctypes.c_void_p),
                           ef, ea, ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad),
                           _stream_ptr(stream)))
+
+
+def adg_grad_fd(design: Design, params, efwd, eadj, w, h, grad, stream=None):
+    """The finite-difference baseline: grad <- central differences of the
+    loss through two builds per parameter (step h), on the GPU."""
+    p = _params(design, params)
+    ef, ea, ww = _grad_args(design, efwd, eadj, w, grad)
+    _check(lib().adg_grad_fd(design.ctx.handle, design.handle, p.ctypes.data_as(ctypes.c_void_p),
+                             ef, ea, ww.ctypes.data_as(ctypes.c_void_p), float(h), _dptr(grad),
+                             _stream_ptr(stream)))
 
 
 def adg_grad_dense(design: Design, params, efwd, eadj, w, fill, grad, gmat, stream=None):

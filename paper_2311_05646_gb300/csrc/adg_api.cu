@@ -165,6 +165,11 @@ struct adg_design {
   // dense field stream (adg_grad_dense): per-chunk partials and work counter
   double2* d_dense_part = nullptr;
   int* d_dense_ctr = nullptr;
+  // finite-difference baseline (adg_grad_fd): z, fill+, fill-, eps scratch;
+  // chunk partials; one FP64 sum per parameter
+  float* d_fd_buf = nullptr;
+  double* d_fd_part = nullptr;
+  double* d_fd_acc = nullptr;
   // per-call host staging
   std::vector<PrimRec> h_prims;
   std::vector<double> h_auxd, q;
@@ -244,6 +249,9 @@ void free_design(adg_design* d) {
   cudaFree(d->d_job);
   cudaFree(d->d_dense_part);
   cudaFree(d->d_dense_ctr);
+  cudaFree(d->d_fd_buf);
+  cudaFree(d->d_fd_part);
+  cudaFree(d->d_fd_acc);
   delete d;
 }
 
@@ -650,6 +658,55 @@ extern "C" adg_status adg_topo_grad(adg_ctx* ctx, const adg_grid* grid, const ad
   a.grad = d_grad;
   CU(cudaSetDevice(ctx->device));
   CU(launch_topo_grad(a, ctx->sms, (cudaStream_t)stream));
+  return ADG_OK;
+}
+
+extern "C" adg_status adg_grad_fd(adg_ctx* ctx, adg_design* d, const double* h_params,
+                                  const float* const d_efwd[3], const float* const d_eadj[3],
+                                  const float* w, double h, float* d_grad, void* stream) {
+  if (!ctx || !d || !d_efwd || !d_eadj || !w || (!d_grad && d->n_params > 0) ||
+      (!h_params && d->n_params > 0))
+    return fail(ADG_EINVAL, "adg_grad_fd: NULL argument");
+  if (!(h > 0.0)) return fail(ADG_EINVAL, "adg_grad_fd: step h = %g must be positive", h);
+  const GridDev& g = d->g;
+  FdSeedArgs sa{};
+  for (int c = 0; c < g.C; ++c) {
+    if (!d_efwd[c] || !d_eadj[c])
+      return fail(ADG_EINVAL, "adg_grad_fd: field of component %d is NULL", c);
+    sa.ef[c] = reinterpret_cast<const float2*>(d_efwd[c]);
+    sa.ea[c] = reinterpret_cast<const float2*>(d_eadj[c]);
+    sa.w[c] = make_float2(w[2 * c], w[2 * c + 1]);
+  }
+  sa.plane = (long long)g.nx * g.ny * g.nz;
+  sa.C = g.C;
+  const long long ns = sa.plane * g.C;  // samples
+  const int n = d->n_params;
+  CU(cudaSetDevice(ctx->device));
+  if (!d->d_fd_buf) {
+    CU(cudaMalloc((void**)&d->d_fd_buf, sizeof(float) * (size_t)ns * 4));
+    CU(cudaMalloc((void**)&d->d_fd_part, sizeof(double) * (size_t)std::max(fd_chunks(ns), 1)));
+    CU(cudaMalloc((void**)&d->d_fd_acc, sizeof(double) * (size_t)std::max(n, 1)));
+  }
+  float* z = d->d_fd_buf;
+  float* fa = z + ns;
+  float* fb = fa + ns;
+  float* es = fb + ns;
+  sa.z = z;
+  cudaStream_t s = (cudaStream_t)stream;
+  CU(launch_fd_seed(sa, ctx->sms, s));
+  std::vector<double> p(h_params, h_params + n);
+  for (int k = 0; k < n; ++k) {  // two builds per parameter, then one dot product
+    const double p0 = p[k];
+    p[k] = p0 + h;
+    adg_status st = run_single(ctx, d, p.data(), fa, es, nullptr, nullptr, s);
+    if (st != ADG_OK) return st;
+    p[k] = p0 - h;
+    st = run_single(ctx, d, p.data(), fb, es, nullptr, nullptr, s);
+    if (st != ADG_OK) return st;
+    p[k] = p0;
+    CU(launch_fd_dot(z, fa, fb, ns, d->d_fd_part, d->d_fd_acc + k, s));
+  }
+  CU(launch_fd_scale(d->d_fd_acc, n, (double)g.deps / (2.0 * h), d_grad, s));
   return ADG_OK;
 }
 

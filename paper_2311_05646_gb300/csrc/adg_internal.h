@@ -116,6 +116,24 @@ struct VjpArgs {
   const float* G;  // real-seed mode when non-null
 };
 
+// The finite-difference baseline (Sec. 3): z = Re(w E_adj E) once, then
+// sum z (a - b) per pair of fills, in kFdChunk-sample chunks summed in order.
+constexpr int kFdChunk = 8192;
+struct FdSeedArgs {
+  const float2* ef[3];
+  const float2* ea[3];
+  float2 w[3];
+  long long plane;  // nx ny nz
+  int C;
+  float* z;         // [C][plane]
+};
+cudaError_t launch_fd_seed(const FdSeedArgs& a, int sms, cudaStream_t s);
+int fd_chunks(long long n);
+cudaError_t launch_fd_scale(const double* acc, int n, double scale, float* grad, cudaStream_t s);
+// part: fd_chunks(n) doubles of scratch; out: one double
+cudaError_t launch_fd_dot(const float* z, const float* a, const float* b, long long n,
+                          double* part, double* out, cudaStream_t s);
+
 // The topology special case (Sec. 3.1): a region of rx x ry pixels at
 // (x0, y0) broadcast along z over [z0, z1), one parameter v per pixel.
 struct TopoArgs {
