@@ -206,6 +206,22 @@ adg_status adg_grad_dense(adg_ctx *ctx, adg_design *design, const double *h_para
                           const float *w, const float *d_fill, float *d_grad, double *d_gmat,
                           void *stream);
 
+/* Both terms of Eq. 1: the permittivity term through d_eps (fields E) plus
+ * the permeability term through d_mu (fields H), the reverse sweeps of
+ * Eqs. jaceps and jacmu seeded with E_adj E and H_adj H:
+ *   g = Re sum w_e E_adj E d eps/dp + Re sum w_h H_adj H d mu/dp.
+ * d_mu is a design of the composition mu(v) of Eq. mu: its own shapes and
+ * program over the same parameters, its grid offsets those of the H samples,
+ * and its eps_bg / eps_fg fields holding mu_bg / mu_fg.  Both designs must
+ * have the same n_params (ADG_EINVAL otherwise).  Fields, weights and d_grad
+ * as for adg_grad (w_h = -2 i omega gives the paper's mu term).  Allocates
+ * n_params floats on d_mu on first use.  Asynchronous on `stream`. */
+adg_status adg_grad_eh(adg_ctx *ctx, adg_design *d_eps, adg_design *d_mu, const double *h_params,
+                       const float *const d_efwd[3], const float *const d_eadj[3],
+                       const float *w_e, const float *const d_hfwd[3],
+                       const float *const d_hadj[3], const float *w_h, float *d_grad,
+                       void *stream);
+
 /* The finite-difference gradient that AutoDiff replaces (Sec. 3; the paper's
  * baseline), on the GPU with the library's own build as the mesher:
  *   g_k = deps sum_c sum_samples Re(w_c E_adj,c E_fwd,c)

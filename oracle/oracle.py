@@ -263,6 +263,13 @@ def grad(desc: dict, efwd, eadj, w, params=None, return_loss: bool = False):
     return (g, L.value) if return_loss else g
 
 
+def grad_eh(desc_eps: dict, desc_mu: dict, efwd, eadj, w_e, hfwd, hadj, w_h, params=None):
+    """Both terms of Eq. 1: the permittivity sweep seeded with E_adj E (Eq.
+    jaceps) plus the permeability sweep seeded with H_adj H (Eqs. mu, jacmu),
+    over the parameters the two compositions share."""
+    return grad(desc_eps, efwd, eadj, w_e, params) + grad(desc_mu, hfwd, hadj, w_h, params)
+
+
 def grad_real(desc: dict, G, params=None, return_loss: bool = False):
     """g_k = sum_c sum_cells G_c d eps_c / d p_k (real cotangent)."""
     m = _Marshalled(desc)

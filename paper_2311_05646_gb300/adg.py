@@ -98,6 +98,7 @@ def lib():
                 "adg_profile_enable": [P, I32],
                 "adg_profile_read": [P, ctypes.POINTER(adg_profile_data), I32],
                 "adg_grad_fd": [P, P, P, P, P, P, ctypes.c_double, P, P],
+                "adg_grad_eh": [P, P, P, P, P, P, P, P, P, P, P, P],
                 "adg_topo_eps": [P, ctypes.POINTER(adg_grid), ctypes.POINTER(adg_topo_region), P,
                                  ctypes.c_double, ctypes.c_double, P, P],
                 "adg_topo_grad": [P, ctypes.POINTER(adg_grid), ctypes.POINTER(adg_topo_region), P,
@@ -276,6 +277,22 @@ def adg_grad(design: Design, params, efwd, eadj, w, grad, stream=None):
     _check(lib().adg_grad(design.ctx.handle, design.handle, p.ctypes.data_as(ctypes.c_void_p),
                           ef, ea, ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad),
                           _stream_ptr(stream)))
+
+
+def adg_grad_eh(d_eps: Design, d_mu: Design, params, efwd, eadj, w_e, hfwd, hadj, w_h, grad,
+                stream=None):
+    """Both terms of Eq. 1: grad <- Re sum w_e E_adj E d eps/dp (through
+    d_eps) + Re sum w_h H_adj H d mu/dp (through d_mu, the permeability
+    composition of the same parameters at the H offsets)."""
+    if d_mu.n_params != d_eps.n_params:
+        raise ValueError("the two designs must share their parameters")
+    p = _params(d_eps, params)
+    ef, ea, we = _grad_args(d_eps, efwd, eadj, w_e, grad)
+    hf, ha, wh = _grad_args(d_mu, hfwd, hadj, w_h, grad)
+    _check(lib().adg_grad_eh(d_eps.ctx.handle, d_eps.handle, d_mu.handle,
+                             p.ctypes.data_as(ctypes.c_void_p), ef, ea,
+                             we.ctypes.data_as(ctypes.c_void_p), hf, ha,
+                             wh.ctypes.data_as(ctypes.c_void_p), _dptr(grad), _stream_ptr(stream)))
 
 
 def adg_grad_fd(design: Design, params, efwd, eadj, w, h, grad, stream=None):

@@ -170,6 +170,7 @@ struct adg_design {
   float* d_fd_buf = nullptr;
   double* d_fd_part = nullptr;
   double* d_fd_acc = nullptr;
+  float* d_eh_grad = nullptr;  // adg_grad_eh: this (mu) design's term
   // per-call host staging
   std::vector<PrimRec> h_prims;
   std::vector<double> h_auxd, q;
@@ -252,6 +253,7 @@ void free_design(adg_design* d) {
   cudaFree(d->d_fd_buf);
   cudaFree(d->d_fd_part);
   cudaFree(d->d_fd_acc);
+  cudaFree(d->d_eh_grad);
   delete d;
 }
 
@@ -658,6 +660,42 @@ extern "C" adg_status adg_topo_grad(adg_ctx* ctx, const adg_grid* grid, const ad
   a.grad = d_grad;
   CU(cudaSetDevice(ctx->device));
   CU(launch_topo_grad(a, ctx->sms, (cudaStream_t)stream));
+  return ADG_OK;
+}
+
+extern "C" adg_status adg_grad_eh(adg_ctx* ctx, adg_design* d_eps, adg_design* d_mu,
+                                  const double* h_params, const float* const d_efwd[3],
+                                  const float* const d_eadj[3], const float* w_e,
+                                  const float* const d_hfwd[3], const float* const d_hadj[3],
+                                  const float* w_h, float* d_grad, void* stream) {
+  if (!ctx || !d_eps || !d_mu || !d_efwd || !d_eadj || !w_e || !d_hfwd || !d_hadj || !w_h ||
+      (!d_grad && d_eps->n_params > 0))
+    return fail(ADG_EINVAL, "adg_grad_eh: NULL argument");
+  if (d_eps->n_params != d_mu->n_params)
+    return fail(ADG_EINVAL, "adg_grad_eh: the eps design has %d parameters, the mu design %d",
+                d_eps->n_params, d_mu->n_params);
+  VjpArgs ve{}, vh{};
+  for (int c = 0; c < d_eps->g.C; ++c) {
+    if (!d_efwd[c] || !d_eadj[c]) return fail(ADG_EINVAL, "adg_grad_eh: E of component %d is NULL", c);
+    ve.ef[c] = reinterpret_cast<const float2*>(d_efwd[c]);
+    ve.ea[c] = reinterpret_cast<const float2*>(d_eadj[c]);
+    ve.w[c] = make_float2(w_e[2 * c], w_e[2 * c + 1]);
+  }
+  for (int c = 0; c < d_mu->g.C; ++c) {
+    if (!d_hfwd[c] || !d_hadj[c]) return fail(ADG_EINVAL, "adg_grad_eh: H of component %d is NULL", c);
+    vh.ef[c] = reinterpret_cast<const float2*>(d_hfwd[c]);
+    vh.ea[c] = reinterpret_cast<const float2*>(d_hadj[c]);
+    vh.w[c] = make_float2(w_h[2 * c], w_h[2 * c + 1]);
+  }
+  CU(cudaSetDevice(ctx->device));
+  const int n = d_eps->n_params;
+  if (!d_mu->d_eh_grad && n > 0) CU(cudaMalloc((void**)&d_mu->d_eh_grad, sizeof(float) * n));
+  cudaStream_t s = (cudaStream_t)stream;
+  adg_status st = run_single(ctx, d_eps, h_params, nullptr, nullptr, &ve, d_grad, s);  // eps term
+  if (st != ADG_OK) return st;
+  st = run_single(ctx, d_mu, h_params, nullptr, nullptr, &vh, d_mu->d_eh_grad, s);      // mu term
+  if (st != ADG_OK) return st;
+  CU(launch_add(d_mu->d_eh_grad, d_grad, n, s));
   return ADG_OK;
 }
 

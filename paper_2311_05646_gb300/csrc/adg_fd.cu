@@ -9,7 +9,8 @@
 //               kFdChunk samples (16-byte loads), a fixed-order tree in the
 //               block, FP64 chunk partials; k_fd_final adds them in chunk
 //               order, so the result is reproducible bit for bit.
-// All three are HBM streams.
+// All three are HBM streams.  k_add (b += a, for the two terms of Eq. 1) is
+// kept here with the other small helpers.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -85,6 +86,17 @@ __global__ void k_fd_scale(const double* __restrict__ acc, int n, double scale,
 }
 
 }  // namespace
+
+__global__ void k_add(const float* __restrict__ a, float* __restrict__ b, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) b[k] += a[k];
+}
+
+cudaError_t launch_add(const float* a, float* b, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_add<<<(n + 255) / 256, 256, 0, s>>>(a, b, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fd_scale(const double* acc, int n, double scale, float* grad, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;

@@ -130,6 +130,7 @@ struct FdSeedArgs {
 cudaError_t launch_fd_seed(const FdSeedArgs& a, int sms, cudaStream_t s);
 int fd_chunks(long long n);
 cudaError_t launch_fd_scale(const double* acc, int n, double scale, float* grad, cudaStream_t s);
+cudaError_t launch_add(const float* a, float* b, int n, cudaStream_t s);  // b += a
 // part: fd_chunks(n) doubles of scratch; out: one double
 cudaError_t launch_fd_dot(const float* z, const float* a, const float* b, long long n,
                           double* part, double* out, cudaStream_t s);

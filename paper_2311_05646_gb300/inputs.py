@@ -26,6 +26,10 @@ OP_PUSH, OP_UNION, OP_INTERSECT, OP_DIFF = 0, 1, 2, 3
 # cell centre; 3D edge-centred E components Ex, Ey, Ez.
 OFF_2D = [[0.5, 0.5, 0.0]]
 OFF_3D = [[0.5, 0.0, 0.0], [0.0, 0.5, 0.0], [0.0, 0.0, 0.5]]
+# H sample offsets: 2D single component at the cell corner; 3D face-centred
+# H components Hx, Hy, Hz.
+OFF_H_2D = [[0.0, 0.0, 0.0]]
+OFF_H_3D = [[0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]]
 
 
 class P:
@@ -160,6 +164,20 @@ class Design:
                       for k, v in self.prims.items()},
             "ops": np.asarray(ops, dtype=np.int32),
         }
+
+
+def mu_design(desc: dict, mu_bg: float = 1.0, mu_fg: float = 1.5, off=None) -> dict:
+    """The permeability composition of a design (Eq. mu): the same shapes,
+    program and parameters, sampled at the H offsets, with the two material
+    levels mu_bg / mu_fg in the eps_bg / eps_fg slots of the description."""
+    C = int(desc["grid"]["ncomp"])
+    if off is None:
+        off = OFF_H_2D if C == 1 else OFF_H_3D
+    out = dict(desc)
+    out["grid"] = dict(desc["grid"])
+    out["grid"]["off"] = [list(map(float, r)) for r in off][:C]
+    out["eps_bg"], out["eps_fg"] = float(mu_bg), float(mu_fg)
+    return out
 
 
 def field_shape(desc: dict):

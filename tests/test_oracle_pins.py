@@ -419,6 +419,46 @@ def test_p8_fd_converges_second_order(oracle_mod):
     assert 3.0 < r1 < 5.0 and 3.0 < r2 < 5.0
 
 
+# ------------------------------------------------ both terms of Eq. 1 -------
+@pytest.mark.parametrize("case", ["grating2d", "random3d"])
+def test_eh_gradient_matches_fd_of_the_total_loss(oracle_mod, case):
+    """Eq. 1 with both terms: L = Re sum w_e E_adj E eps + Re sum w_h H_adj H
+    mu, eps and mu two compositions (Eqs. eps, mu) of the same parameters
+    sampled at the E and H offsets.  Central differences of L itself (loss
+    evaluations only, no reverse sweep) fix the sum of the two sweeps."""
+    O = oracle_mod
+    desc = I.grating_2d() if case == "grating2d" else I.random_design(5, n=(30, 24, 10), nprims=10)
+    dmu = I.mu_design(desc, mu_bg=1.0, mu_fg=1.7)
+    ef, ea, we = _fields(desc, 41, 42, 43)
+    hf, ha, wh = _fields(dmu, 44, 45, 46)
+    g = O.grad_eh(desc, dmu, ef, ea, we, hf, ha, wh)
+    p0 = np.asarray(desc["params"], dtype=np.float64)
+    h = 1e-3
+    fd = np.zeros_like(p0)
+    for k in range(p0.size):
+        pp, pm = p0.copy(), p0.copy()
+        pp[k] += h
+        pm[k] -= h
+        Lp = O.loss(desc, ef, ea, we, pp) + O.loss(dmu, hf, ha, wh, pp)
+        Lm = O.loss(desc, ef, ea, we, pm) + O.loss(dmu, hf, ha, wh, pm)
+        fd[k] = (Lp - Lm) / (2 * h)
+    assert np.linalg.norm(g - fd) <= 1e-6 * np.linalg.norm(g) + 1e-9 * np.abs(g).max()
+    # the H term is really there: it moves the gradient
+    g_e = O.grad(desc, ef, ea, we)
+    assert np.linalg.norm(g - g_e) > 1e-3 * np.linalg.norm(g_e)
+
+
+def test_eh_gradient_of_a_nonmagnetic_design_is_the_eps_term(oracle_mod):
+    """mu_fg = mu_bg: mu does not depend on the parameters, so Eq. 1's H term
+    vanishes identically (every d mu / dp is a multiple of mu_fg - mu_bg)."""
+    O = oracle_mod
+    desc = I.random_design(9, n=(30, 24, 10), nprims=10)
+    dmu = I.mu_design(desc, mu_bg=1.0, mu_fg=1.0)
+    ef, ea, we = _fields(desc, 51, 52, 53)
+    hf, ha, wh = _fields(dmu, 54, 55, 56)
+    assert np.array_equal(O.grad_eh(desc, dmu, ef, ea, we, hf, ha, wh), O.grad(desc, ef, ea, we))
+
+
 # ------------------------------------------- material levels (dense form) ---
 def test_material_level_derivatives_match_fd_of_the_loss(oracle_mod):
     """dL/d eps_bg and dL/d eps_fg (Sec. 5.1's eps = eps_bg + deps fill): L is
