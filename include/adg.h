@@ -206,6 +206,36 @@ adg_status adg_grad_dense(adg_ctx *ctx, adg_design *design, const double *h_para
                           const float *w, const float *d_fill, float *d_grad, double *d_gmat,
                           void *stream);
 
+/* Union over non-binary material levels (App. B, Alg. 1).  sets[0..K-1] are
+ * K designs, set k being one set of shapes with its own program (the set's
+ * union), all on one grid with one logic family and one parameter vector,
+ * each with material slots eps_bg = 0, eps_fg = 1 (so its fill is the set's
+ * union s^k).  levels[k] is set k's material level above the background,
+ * finite, with 0 < levels[0] <= ... <= levels[K-1]; 1 <= K <= 8.  Per sample:
+ *   s <- s^1;  s <- union((levels[k-1] / levels[k]) s, s^k), k = 2..K;
+ *   eps = eps_bg + levels[K-1] s,
+ * union being the sets' logic (Eq. union, or App. B.2's product form).
+ * ADG_EINVAL for a NULL argument, K outside [1, 8], unsorted or non-positive
+ * levels, or sets that differ in grid, logic, parameter count or material
+ * slots.  The first set owns the scratch: K fill-sized float slices for
+ * adg_levels_eps, 2K for adg_levels_grad, allocated on first use or growth
+ * (growth synchronises the device).  Asynchronous on `stream`; the K sets
+ * must not be used concurrently on another stream. */
+adg_status adg_levels_eps(adg_ctx *ctx, adg_design *const *sets, int32_t K, const double *levels,
+                          double eps_bg, const double *h_params, float *d_eps, void *stream);
+
+/* Eq. 1 (eps term) through Alg. 1: g = Re sum_c w_c E_adj,c E_fwd,c d eps_c / dp
+ * with eps the map of adg_levels_eps.  Each set's build, one pass turning
+ * the seed levels[K-1] Re(w E_adj E) into one real cotangent per set (the
+ * reverse of the loop), each set's real-cotangent sweep (as adg_grad_real),
+ * and the sum of the K rows into d_grad (n_params floats, overwritten).
+ * Fields and weights as for adg_grad; errors and scratch as above (sets 2..K
+ * also hold one n_params float row each). */
+adg_status adg_levels_grad(adg_ctx *ctx, adg_design *const *sets, int32_t K, const double *levels,
+                           const double *h_params, const float *const d_efwd[3],
+                           const float *const d_eadj[3], const float *w, float *d_grad,
+                           void *stream);
+
 /* Both terms of Eq. 1: the permittivity term through d_eps (fields E) plus
  * the permeability term through d_mu (fields H), the reverse sweeps of
  * Eqs. jaceps and jacmu seeded with E_adj E and H_adj H:
@@ -312,6 +342,7 @@ enum { ADG_K_BIN = 0, ADG_K_BUILD = 1, ADG_K_VJP = 2, ADG_K_FINALIZE = 3,
        ADG_K_PREPARE = 4 /* reserved, not launched: the finalize clears the partials */,
        ADG_K_FILL = 5 /* reserved, not launched: the build fills the constant tiles */,
        ADG_K_DENSE = 6 /* field stream + its fixed-order sum */,
+       ADG_K_LEVELS = 7 /* the per-sample pass of Alg. 1 (adg_levels_*) */,
        ADG_K_COUNT = 8 };
 typedef struct {
   int64_t launches[ADG_K_COUNT];

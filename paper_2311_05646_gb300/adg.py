@@ -59,7 +59,8 @@ class adg_tile_opts(ctypes.Structure):
                 ("fill_warps", ctypes.c_int32)]
 
 
-K_NAMES = {0: "bin", 1: "build", 2: "vjp", 3: "finalize", 4: "prepare", 5: "fill", 6: "dense"}
+K_NAMES = {0: "bin", 1: "build", 2: "vjp", 3: "finalize", 4: "prepare", 5: "fill", 6: "dense",
+           7: "levels"}
 
 
 class adg_profile_data(ctypes.Structure):
@@ -99,6 +100,8 @@ def lib():
                 "adg_profile_read": [P, ctypes.POINTER(adg_profile_data), I32],
                 "adg_grad_fd": [P, P, P, P, P, P, ctypes.c_double, P, P],
                 "adg_grad_eh": [P, P, P, P, P, P, P, P, P, P, P, P],
+                "adg_levels_eps": [P, P, I32, P, ctypes.c_double, P, P, P],
+                "adg_levels_grad": [P, P, I32, P, P, P, P, P, P, P],
                 "adg_topo_eps": [P, ctypes.POINTER(adg_grid), ctypes.POINTER(adg_topo_region), P,
                                  ctypes.c_double, ctypes.c_double, P, P],
                 "adg_topo_grad": [P, ctypes.POINTER(adg_grid), ctypes.POINTER(adg_topo_region), P,
@@ -293,6 +296,42 @@ def adg_grad_eh(d_eps: Design, d_mu: Design, params, efwd, eadj, w_e, hfwd, hadj
                              p.ctypes.data_as(ctypes.c_void_p), ef, ea,
                              we.ctypes.data_as(ctypes.c_void_p), hf, ha,
                              wh.ctypes.data_as(ctypes.c_void_p), _dptr(grad), _stream_ptr(stream)))
+
+
+def _level_sets(sets, levels):
+    sets = list(sets)
+    if not sets:
+        raise ValueError("at least one set")
+    lv = np.ascontiguousarray(np.asarray(levels, dtype=np.float64).reshape(-1))
+    if lv.size != len(sets):
+        raise ValueError("one material level per set")
+    handles = (ctypes.c_void_p * len(sets))(*[d.handle for d in sets])
+    return sets, lv, handles
+
+
+def adg_levels_eps(sets, levels, eps_bg, params, eps, stream=None):
+    """eps <- the union over non-binary material levels (App. B, Alg. 1) of
+    the level sets `sets` (Designs, material slots 0 / 1) at `levels`."""
+    import torch
+    sets, lv, handles = _level_sets(sets, levels)
+    p = _params(sets[0], params)
+    _check_cell_tensor(sets[0], eps, "eps", torch.float32)
+    _check(lib().adg_levels_eps(sets[0].ctx.handle, handles, len(sets),
+                                lv.ctypes.data_as(ctypes.c_void_p), float(eps_bg),
+                                p.ctypes.data_as(ctypes.c_void_p), _dptr(eps), _stream_ptr(stream)))
+
+
+def adg_levels_grad(sets, levels, params, efwd, eadj, w, grad, stream=None):
+    """grad <- Re sum w E_adj E d eps / dp (Eq. 1, eps term) with eps the map
+    of adg_levels_eps."""
+    sets, lv, handles = _level_sets(sets, levels)
+    p = _params(sets[0], params)
+    ef, ea, ww = _grad_args(sets[0], efwd, eadj, w, grad)
+    _check(lib().adg_levels_grad(sets[0].ctx.handle, handles, len(sets),
+                                 lv.ctypes.data_as(ctypes.c_void_p),
+                                 p.ctypes.data_as(ctypes.c_void_p), ef, ea,
+                                 ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad),
+                                 _stream_ptr(stream)))
 
 
 def adg_grad_fd(design: Design, params, efwd, eadj, w, h, grad, stream=None):

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <string>
 #include <thread>
 #include <vector>
@@ -170,7 +171,10 @@ struct adg_design {
   float* d_fd_buf = nullptr;
   double* d_fd_part = nullptr;
   double* d_fd_acc = nullptr;
-  float* d_eh_grad = nullptr;  // adg_grad_eh: this (mu) design's term
+  float* d_row = nullptr;  // n_params floats: this design's term of a sum
+                           // (adg_grad_eh, adg_levels_grad)
+  float* d_lv_buf = nullptr;  // adg_levels_*: fills and cotangents (first set)
+  size_t lv_cap = 0;          // floats
   // per-call host staging
   std::vector<PrimRec> h_prims;
   std::vector<double> h_auxd, q;
@@ -253,7 +257,8 @@ void free_design(adg_design* d) {
   cudaFree(d->d_fd_buf);
   cudaFree(d->d_fd_part);
   cudaFree(d->d_fd_acc);
-  cudaFree(d->d_eh_grad);
+  cudaFree(d->d_row);
+  cudaFree(d->d_lv_buf);
   delete d;
 }
 
@@ -689,13 +694,133 @@ extern "C" adg_status adg_grad_eh(adg_ctx* ctx, adg_design* d_eps, adg_design* d
   }
   CU(cudaSetDevice(ctx->device));
   const int n = d_eps->n_params;
-  if (!d_mu->d_eh_grad && n > 0) CU(cudaMalloc((void**)&d_mu->d_eh_grad, sizeof(float) * n));
+  if (!d_mu->d_row && n > 0) CU(cudaMalloc((void**)&d_mu->d_row, sizeof(float) * n));
   cudaStream_t s = (cudaStream_t)stream;
   adg_status st = run_single(ctx, d_eps, h_params, nullptr, nullptr, &ve, d_grad, s);  // eps term
   if (st != ADG_OK) return st;
-  st = run_single(ctx, d_mu, h_params, nullptr, nullptr, &vh, d_mu->d_eh_grad, s);      // mu term
+  st = run_single(ctx, d_mu, h_params, nullptr, nullptr, &vh, d_mu->d_row, s);      // mu term
   if (st != ADG_OK) return st;
-  CU(launch_add(d_mu->d_eh_grad, d_grad, n, s));
+  CU(launch_add(d_mu->d_row, d_grad, n, s));
+  return ADG_OK;
+}
+
+namespace {
+
+// Validates a list of level sets (App. B, Alg. 1) and fills the parts of
+// LevelArgs that do not depend on the pass; sizes the first set's scratch
+// to `slices` fill-sized slices.
+adg_status levels_setup(adg_ctx* ctx, adg_design* const* sets, int K, const double* levels,
+                        const char* who, int slices, LevelArgs& a) {
+  if (!ctx || !sets || !levels) return fail(ADG_EINVAL, "%s: NULL argument", who);
+  if (K < 1 || K > kMaxLevels)
+    return fail(ADG_EINVAL, "%s: %d sets (1 .. %d supported)", who, K, kMaxLevels);
+  for (int k = 0; k < K; ++k) {
+    if (!sets[k]) return fail(ADG_EINVAL, "%s: set %d is NULL", who, k);
+    if (!std::isfinite(levels[k]) || !(levels[k] > 0.0) || (k > 0 && levels[k] < levels[k - 1]))
+      return fail(ADG_EINVAL, "%s: levels must be finite, positive and ascending (level %d = %g)",
+                  who, k, levels[k]);
+    const GridDev &g = sets[k]->g, &g0 = sets[0]->g;
+    if (g.eps_bg != 0.0f || g.deps != 1.0f)
+      return fail(ADG_EINVAL, "%s: set %d needs material slots eps_bg = 0, eps_fg = 1", who, k);
+    bool same = g.nx == g0.nx && g.ny == g0.ny && g.nz == g0.nz && g.C == g0.C &&
+                g.logic == g0.logic && sets[k]->n_params == sets[0]->n_params;
+    for (int c = 0; c < 3 && same; ++c)
+      same = sets[k]->d[c] == sets[0]->d[c] && sets[k]->o[c] == sets[0]->o[c];
+    for (int c = 0; c < g.C && same; ++c)
+      for (int x = 0; x < 3; ++x) same = same && g.off[c][x] == g0.off[c][x];
+    if (!same)
+      return fail(ADG_EINVAL, "%s: set %d differs from set 0 in its grid, logic or parameters",
+                  who, k);
+  }
+  const GridDev& g = sets[0]->g;
+  a = LevelArgs{};
+  a.plane = (long long)g.nx * g.ny * g.nz;
+  a.C = g.C;
+  a.K = K;
+  a.logic = g.logic;
+  a.stride = (a.plane * g.C + 63) / 64 * 64;  // 256-byte aligned slices
+  a.lv_top = (float)levels[K - 1];
+  for (int k = 1; k < K; ++k) a.r[k] = (float)(levels[k - 1] / levels[k]);
+  const size_t need = (size_t)a.stride * slices;
+  CU(cudaSetDevice(ctx->device));
+  adg_design* d0 = sets[0];
+  if (d0->lv_cap < need) {
+    if (d0->d_lv_buf) {
+      CU(cudaDeviceSynchronize());
+      CU(cudaFree(d0->d_lv_buf));
+      d0->d_lv_buf = nullptr;
+      d0->lv_cap = 0;
+    }
+    CU(cudaMalloc((void**)&d0->d_lv_buf, sizeof(float) * need));
+    d0->lv_cap = need;
+  }
+  a.fill = d0->d_lv_buf;
+  return ADG_OK;
+}
+
+}  // namespace
+
+extern "C" adg_status adg_levels_eps(adg_ctx* ctx, adg_design* const* sets, int32_t K,
+                                     const double* levels, double eps_bg, const double* h_params,
+                                     float* d_eps, void* stream) {
+  LevelArgs a;
+  adg_status st = levels_setup(ctx, sets, K, levels, "adg_levels_eps", K, a);
+  if (st != ADG_OK) return st;
+  if (!d_eps) return fail(ADG_EINVAL, "adg_levels_eps: NULL eps");
+  if (!std::isfinite(eps_bg)) return fail(ADG_EINVAL, "adg_levels_eps: eps_bg not finite");
+  cudaStream_t s = (cudaStream_t)stream;
+  float* fills = sets[0]->d_lv_buf;
+  for (int k = 0; k < K; ++k) {  // each set's fill; d_eps is the builds' eps scratch
+    st = run_single(ctx, sets[k], h_params, fills + k * a.stride, d_eps, nullptr, nullptr, s);
+    if (st != ADG_OK) return st;
+  }
+  a.out = d_eps;
+  a.eps_bg = (float)eps_bg;
+  {
+    ProfScope ps(ctx, ADG_K_LEVELS, s);
+    CU(launch_levels(a, false, ctx->sms, s));
+  }
+  return ADG_OK;
+}
+
+extern "C" adg_status adg_levels_grad(adg_ctx* ctx, adg_design* const* sets, int32_t K,
+                                      const double* levels, const double* h_params,
+                                      const float* const d_efwd[3], const float* const d_eadj[3],
+                                      const float* w, float* d_grad, void* stream) {
+  LevelArgs a;
+  adg_status st = levels_setup(ctx, sets, K, levels, "adg_levels_grad", 2 * K, a);
+  if (st != ADG_OK) return st;
+  const int n = sets[0]->n_params;
+  if (!d_efwd || !d_eadj || !w || (!d_grad && n > 0))
+    return fail(ADG_EINVAL, "adg_levels_grad: NULL argument");
+  for (int c = 0; c < a.C; ++c) {
+    if (!d_efwd[c] || !d_eadj[c])
+      return fail(ADG_EINVAL, "adg_levels_grad: field of component %d is NULL", c);
+    a.ef[c] = reinterpret_cast<const float2*>(d_efwd[c]);
+    a.ea[c] = reinterpret_cast<const float2*>(d_eadj[c]);
+    a.w[c] = make_float2(w[2 * c], w[2 * c + 1]);
+  }
+  for (int k = 1; k < K; ++k)
+    if (!sets[k]->d_row && n > 0) CU(cudaMalloc((void**)&sets[k]->d_row, sizeof(float) * n));
+  cudaStream_t s = (cudaStream_t)stream;
+  float* fills = sets[0]->d_lv_buf;
+  float* cots = fills + (size_t)K * a.stride;
+  for (int k = 0; k < K; ++k) {  // each set's fill; the first cotangent slice is eps scratch
+    st = run_single(ctx, sets[k], h_params, fills + k * a.stride, cots, nullptr, nullptr, s);
+    if (st != ADG_OK) return st;
+  }
+  a.out = cots;
+  {
+    ProfScope ps(ctx, ADG_K_LEVELS, s);
+    CU(launch_levels(a, true, ctx->sms, s));
+  }
+  for (int k = 0; k < K; ++k) {  // each set's sweep with its cotangent, then the sum
+    VjpArgs va{};
+    va.G = cots + k * a.stride;
+    st = run_single(ctx, sets[k], h_params, nullptr, nullptr, &va, k ? sets[k]->d_row : d_grad, s);
+    if (st != ADG_OK) return st;
+    if (k) CU(launch_add(sets[k]->d_row, d_grad, n, s));
+  }
   return ADG_OK;
 }
 

@@ -131,6 +131,22 @@ cudaError_t launch_fd_seed(const FdSeedArgs& a, int sms, cudaStream_t s);
 int fd_chunks(long long n);
 cudaError_t launch_fd_scale(const double* acc, int n, double scale, float* grad, cudaStream_t s);
 cudaError_t launch_add(const float* a, float* b, int n, cudaStream_t s);  // b += a
+
+// Union over non-binary material levels (App. B, Alg. 1), adg_levels.cu.
+constexpr int kMaxLevels = 8;
+constexpr int kLogicClamp = 1;  // GridDev::logic of the clamped family (0: product)
+struct LevelArgs {
+  const float* fill;  // K fill slices, `stride` floats apart, each [C][plane]
+  float* out;         // eps [C][plane], or K cotangent slices `stride` apart
+  long long stride, plane;
+  int C, K, logic;
+  float lv_top, eps_bg;   // eps^K, the background
+  float r[kMaxLevels];    // r[k] = eps^{k-1} / eps^k for k >= 1
+  const float2* ef[3];    // cotangent pass: fields and weights
+  const float2* ea[3];
+  float2 w[3];
+};
+cudaError_t launch_levels(const LevelArgs& a, bool cot, int sms, cudaStream_t s);
 // part: fd_chunks(n) doubles of scratch; out: one double
 cudaError_t launch_fd_dot(const float* z, const float* a, const float* b, long long n,
                           double* part, double* out, cudaStream_t s);

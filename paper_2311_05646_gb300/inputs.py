@@ -411,3 +411,62 @@ def hole_lattice(n=(1000, 1000, 80), d=(40.0, 40.0, 20.0), holes: int = 20, seed
         shallow = D.box(x=(0.1 * ex, 0.3 * ex), y=(0.4 * ey, 0.45 * ey))
     D.set_program(("diff", slab, ("union",) + tuple(hs) + (shallow,)))
     return D.to_desc()
+
+
+def nonbinary_circles(n=(200, 200, 1), d=(20.0, 20.0, 20.0), levels=(0.1, 0.34, 0.62, 1.0),
+                      per_level: int = 3, t: float = 0.55, eps_bg: float = 0.0, seed: int = 61,
+                      ncomp=None, logic: str = "product", boxes: bool = True) -> dict:
+    """Overlapping shapes of several material levels (App. B, Alg. 1; its
+    example: circles of levels 0.1, 0.34, 0.62 and 1.0 over a background of 0,
+    brought in from the four quadrants towards the centre).
+
+    Level k's set is `per_level` circles (cx, cy, r parameters each) placed
+    around its quadrant's centre and moved a fraction `t` of the way to the
+    grid's centre, plus one fixed-size box (two x-edge parameters) when
+    `boxes`; in 3D the shapes are slabs of the middle half of z.  Every set is
+    one description with material slots 0 / 1 and its own union program; all
+    sets carry the same parameter vector, in the same order.  Returns
+    {"sets": [desc, ...], "levels": array of K, "eps_bg": float}."""
+    rng = np.random.default_rng(seed)
+    n = tuple(int(v) for v in n)
+    if len(n) == 2:
+        n = (n[0], n[1], 1)
+    nx, ny, nz = n
+    d = tuple(float(v) for v in d)
+    if ncomp is None:
+        ncomp = 1 if nz == 1 else 3
+    K = len(levels)
+    ex, ey = nx * d[0], ny * d[1]
+    zc = 0.5 * nz * d[2]
+    zr = (zc - 0.25 * nz * d[2], zc + 0.25 * nz * d[2]) if nz > 1 else None
+    sets = [Design(n, d, ncomp=ncomp, eps_bg=0.0, eps_fg=1.0, logic=logic) for _ in range(K)]
+    owned = [[] for _ in range(K)]
+    quad = [(0.25, 0.25), (0.75, 0.25), (0.25, 0.75), (0.75, 0.75)]
+    rmax = 0.2 * min(ex, ey)
+    for k in range(K):
+        qx, qy = quad[k % 4]
+        cx0 = ex * (qx + t * (0.5 - qx))
+        cy0 = ey * (qy + t * (0.5 - qy))
+        for _ in range(per_level):
+            vals = (cx0 + rng.uniform(-0.3, 0.3) * rmax, cy0 + rng.uniform(-0.3, 0.3) * rmax,
+                    rng.uniform(0.35, 0.7) * rmax)
+            idx = [[D.param(v) for v in vals] for D in sets][k]
+            owned[k].append(("circle", idx))
+        if boxes:
+            x0 = cx0 - rng.uniform(0.5, 1.0) * rmax
+            vals = (x0, x0 + rng.uniform(0.6, 1.2) * rmax)
+            idx = [[D.param(v) for v in vals] for D in sets][k]
+            y0 = cy0 + rng.uniform(-0.6, 0.2) * rmax
+            owned[k].append(("box", idx, (y0, y0 + 0.4 * rmax)))
+    for k, D in enumerate(sets):
+        prims = []
+        for item in owned[k]:
+            if item[0] == "circle":
+                i = item[1]
+                prims.append(D.circle(P(i[0]), P(i[1]), P(i[2]), z=zr, sigma="sigmoid", kr=4.0))
+            else:
+                i = item[1]
+                prims.append(D.box(x=(P(i[0]), P(i[1])), y=item[2], z=zr, sigma="linear"))
+        D.set_program(("union",) + tuple(prims))
+    return {"sets": [D.to_desc() for D in sets],
+            "levels": np.asarray(levels, dtype=np.float64), "eps_bg": float(eps_bg)}

@@ -459,6 +459,117 @@ def test_eh_gradient_of_a_nonmagnetic_design_is_the_eps_term(oracle_mod):
     assert np.array_equal(O.grad_eh(desc, dmu, ef, ea, we, hf, ha, wh), O.grad(desc, ef, ea, we))
 
 
+# ------------------------------------- non-binary union (App. B, Alg. 1) ----
+@pytest.mark.parametrize("logic", ["product", "clamp"])
+@pytest.mark.parametrize("dims", ["2d", "3d"])
+def test_levels_gradient_matches_fd_of_the_loss(logic, dims):
+    """The reverse of Alg. 1 (one cotangent per set, each set's sweep) equals
+    central differences of the loss of Alg. 1's forward result."""
+    from oracle import levels as LV
+    if dims == "2d":
+        m = I.nonbinary_circles(n=(90, 80, 1), d=(40.0, 40.0, 40.0), logic=logic, per_level=2)
+    else:
+        m = I.nonbinary_circles(n=(40, 36, 10), d=(80.0, 80.0, 40.0), logic=logic, per_level=2,
+                                levels=(0.5, 1.3, 2.0))
+    sets, lv, eb = m["sets"], m["levels"], m["eps_bg"]
+    ef, ea, w = _fields(sets[0], 71, 72, 73)
+    g = LV.grad(sets, lv, ef, ea, w)
+    p0 = np.asarray(sets[0]["params"], dtype=np.float64)
+    h = 1e-3
+    fd = np.zeros_like(p0)
+    for k in range(p0.size):
+        pp, pm = p0.copy(), p0.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd[k] = (LV.loss(sets, lv, eb, ef, ea, w, pp) - LV.loss(sets, lv, eb, ef, ea, w, pm)) / (2 * h)
+    # the set cotangents pass through float32 (6e-8 relative) on their way in
+    assert np.linalg.norm(g - fd) <= 1e-5 * np.linalg.norm(g) + 1e-9 * np.abs(g).max()
+    assert np.abs(g).max() > 0
+
+
+def test_levels_one_set_is_the_binary_design():
+    """K = 1: Alg. 1 returns eps_bg + eps^1 s^1, the two-level map of Sec. 5.1."""
+    from oracle import levels as LV
+    from oracle import oracle as O
+    m = I.nonbinary_circles(levels=(0.7,), eps_bg=1.5)
+    desc = dict(m["sets"][0])
+    desc["eps_bg"], desc["eps_fg"] = 1.5, 1.5 + 0.7
+    assert np.allclose(LV.eps(m["sets"], m["levels"], 1.5), O.eps(desc), rtol=0, atol=1e-15)
+
+
+def test_levels_product_closed_form():
+    """Unrolling Alg. 1 with the product union gives front-to-back compositing:
+    eps - eps_bg = sum_k eps^k s^k prod_{j > k} (1 - s^j)."""
+    from oracle import levels as LV
+    from oracle import oracle as O
+    m = I.nonbinary_circles(n=(120, 100, 1), d=(30.0, 30.0, 30.0), logic="product")
+    S = [O.fill(d) for d in m["sets"]]
+    lv = m["levels"]
+    want = np.zeros_like(S[0])
+    for k in range(len(S)):
+        term = lv[k] * S[k]
+        for j in range(k + 1, len(S)):
+            term = term * (1.0 - S[j])
+        want += term
+    got = LV.eps(m["sets"], lv, m["eps_bg"]) - m["eps_bg"]
+    assert np.abs(got - want).max() <= 1e-14
+    assert np.abs(want).max() > 0.9
+
+
+@pytest.mark.parametrize("logic", ["product", "clamp"])
+def test_levels_highest_covering_level_wins(logic):
+    """App. B: the algorithm gives priority to the set with the largest level.
+    Lattice-aligned boxes (exact 0 / 1 fills) of four levels, overlapping in a
+    staircase: every cell takes the largest level among the boxes covering it,
+    and the background where none does."""
+    from oracle import levels as LV
+    lv = np.array([0.1, 0.34, 0.62, 1.0])
+    nx, ny = 24, 20
+    sets, cover = [], np.zeros((len(lv), ny, nx), dtype=bool)
+    for k in range(len(lv)):
+        D = I.Design((nx, ny, 1), (1.0, 1.0, 1.0), ncomp=1, off=[[0.5, 0.5, 0.0]], eps_bg=0.0,
+                     eps_fg=1.0, logic=logic)
+        x0, y0 = 2 + 4 * k, 1 + 3 * k
+        D.param(0.0)
+        D.box(x=(float(x0), float(x0 + 9)), y=(float(y0), float(y0 + 8)), sigma="linear")
+        sets.append(D.to_desc())
+        cover[k, y0:y0 + 8, x0:x0 + 9] = True
+    e = LV.eps(sets, lv, 2.0)[0, 0]
+    want = np.full((ny, nx), 2.0)
+    for k in range(len(lv)):
+        want[cover[k]] = 2.0 + lv[k]
+    assert np.abs(e - want).max() <= 1e-15
+
+
+@pytest.mark.parametrize("logic", ["product", "clamp"])
+def test_levels_equal_levels_are_the_binary_union(logic):
+    """eps^1 = ... = eps^K: Alg. 1 is the plain union of all sets (Eq. union or
+    its product form) at that one level."""
+    from oracle import levels as LV
+    from oracle import oracle as O
+    m = I.nonbinary_circles(n=(100, 90, 1), d=(40.0, 40.0, 40.0), levels=(0.8, 0.8, 0.8, 0.8),
+                            logic=logic)
+    sets = m["sets"]
+    D = I.Design((100, 90, 1), (40.0, 40.0, 40.0), ncomp=1, eps_bg=0.0, eps_fg=1.0, logic=logic)
+    for _ in range(sets[0]["params"].size):
+        D.param(0.0)
+    # every set's primitives, in set order, as one union
+    one = dict(sets[0])
+    kinds = {k: np.concatenate([s["prims"][k] for s in sets]) for k in sets[0]["prims"]}
+    nq = [s["q_base"].size for s in sets]
+    q0 = np.concatenate([s["prims"]["q0"] + sum(nq[:i]) for i, s in enumerate(sets)])
+    kinds["q0"] = q0.astype(np.int32)
+    one["prims"] = kinds
+    for key in ("q_base", "q_coeff", "q_param"):
+        one[key] = np.concatenate([s[key] for s in sets])
+    npr = kinds["kind"].size
+    one["ops"] = np.asarray([(I.OP_PUSH << 24) | i for i in range(npr)] + [(I.OP_UNION << 24) | npr],
+                            dtype=np.int32)
+    one["eps_bg"], one["eps_fg"] = 1.0, 1.8
+    got = LV.eps(sets, m["levels"], 1.0)
+    assert np.abs(got - O.eps(one)).max() <= 1e-13
+
+
 # ------------------------------------------- material levels (dense form) ---
 def test_material_level_derivatives_match_fd_of_the_loss(oracle_mod):
     """dL/d eps_bg and dL/d eps_fg (Sec. 5.1's eps = eps_bg + deps fill): L is
