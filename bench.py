@@ -532,6 +532,51 @@ def run_adg(args):
                   "bytes": {"eps_pass": b_e, "cot_pass": b_g}}
         del sets
 
+    # Prop. 2 / Sec. 6.3 on the same grid and fields: hexagonal holes through
+    # the slab; the exact mesher's volume-averaged fill of the whole layer,
+    # the FD gradient that re-meshes each parameter's region twice, and the
+    # AutoDiffGeo gradient of the same holes as Poly2D hexagons
+    mesh = None
+    if not args.no_dense:
+        from paper_2311_05646_gb300 import inputs as I
+        spec = I.hex_hole_lattice(n=(nx, ny, nz), d=desc["grid"]["d"], holes=(20, 6), R=260.0,
+                                  ncomp=C)
+        hdesc = spec["desc"]
+        hp = hdesc["params"]
+        hdes = adg.Design(ctx, hdesc)
+        layer = I.hex_layer(spec, hp)
+        hfill = torch.empty_like(fill)
+        mh = 0.5
+        plus, minus, regions = I.hex_fd_layers(spec, hp, mh)
+        plus, minus = adg.MeshLayers(plus), adg.MeshLayers(minus)  # the layouts, marshalled once
+        hdeps = -(hdesc["eps_fg"] - hdesc["eps_bg"])
+        gfd = torch.zeros(hdes.n_params, dtype=torch.float32, device="cuda")
+        gad = torch.zeros_like(gfd)
+
+        def t_mesh(fn, reps):
+            fn()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        ms_mf = t_mesh(lambda: adg.adg_mesh_fill(ctx, hdesc["grid"], layer, hfill, stream=stream), 10)
+        ms_fd = t_mesh(lambda: adg.adg_mesh_grad_fd(ctx, hdesc["grid"], plus, minus, regions, mh,
+                                                    hdeps, efd, ead, w, gfd, stream=stream), 3)
+        ms_ad = t_mesh(lambda: adg.adg_grad(hdes, hp, efd, ead, w, gad, stream=stream), 20)
+        ga, gf = gad.double(), gfd.double()
+        rsamp = sum(C * r[2] * r[3] * (r[5] - r[4]) for r in regions)
+        mesh = {"holes": len(spec["centres"]), "params": int(hdes.n_params), "h_nm": mh,
+                "mesh_fill_ms": ms_mf, "fd_exact_ms": ms_fd, "fd_meshes": 2 * int(hdes.n_params),
+                "fd_region_samples": int(rsamp),
+                "fd_region_fraction_of_grid": rsamp / (hdes.n_params * cells * C),
+                "ad_ms": ms_ad, "ad_speedup": ms_fd / ms_ad,
+                "ad_vs_fd_exact_rel_l2": float((ga - gf).norm() / gf.norm())}
+        del hdes
+
     # end to end through the public API: host (pinned) fields in, eps + g out
     e2e = None
     if not args.no_e2e:
@@ -614,7 +659,7 @@ def run_adg(args):
             "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
             "gpu_launches": launches,
             "cpu_baseline": cpu, "e2e": e2e, "dense_vjp": dense, "topology": topo,
-            "fd_vs_ad": fdc, "levels": levels,
+            "fd_vs_ad": fdc, "levels": levels, "prop2_mesher": mesh,
             "clocks": clocks.summary(),
         }
         print(json.dumps(line))

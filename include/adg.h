@@ -292,6 +292,48 @@ adg_status adg_topo_grad(adg_ctx *ctx, const adg_grid *grid, const adg_topo_regi
                          const float *const d_eadj[3], const float *w, float *d_grad,
                          void *stream);
 
+/* ---- the exact polygon mesher (Prop. 2) and its FD gradient (Sec. 6.3) ----
+ * Prop. 2 simulates on the standard, exact shape representation: the
+ * volume-averaged material of the layout on the Yee grid.  A layer is a set
+ * of simple polygons (convex or concave, either winding, not overlapping one
+ * another) extruded over [z0, z1] (bound_z = 1) or over every z (bound_z = 0).
+ * The fill of the sample of component c at cell (i, j, k) is the exact
+ * average of the layer over the averaging cell centred at the sample
+ * (x_s +- dx/2, y_s +- dy/2, z_s +- dz/2; x_s = ox + (i + off[c][0]) dx):
+ *   fill = min(1, sum_p area(P_p n cell_xy) / (dx dy)) * |[z0, z1] n cell_z| / dz.
+ * Computed in FP64, written as float. */
+typedef struct {
+  int32_t n_polys;
+  const int32_t *vert_off; /* n_polys + 1 offsets into xy, from 0; >= 3 vertices each */
+  const double *xy;        /* x, y of every vertex (physical units), host memory     */
+  int32_t bound_z;         /* 1: the layer spans [z0, z1]; 0: every z                */
+  double z0, z1;
+} adg_mesh_layer;
+
+/* d_fill [ncomp][nz][ny][nx] <- the layer's fill over `region` (cells; NULL:
+ * the whole grid); samples outside the region are not written.  The layer is
+ * copied to the context's scratch (grown on demand, which synchronises the
+ * device): calls of one context must not run concurrently on two streams.
+ * ADG_EINVAL for a NULL argument, a bad grid or region, a polygon with fewer
+ * than 3 vertices, a non-finite coordinate or a reversed z range. */
+adg_status adg_mesh_fill(adg_ctx *ctx, const adg_grid *grid, const adg_mesh_layer *layer,
+                         const adg_topo_region *region, float *d_fill, void *stream);
+
+/* The finite-difference gradient with the exact mesher (Sec. 6.3's FD
+ * baseline): for each parameter k, plus[k] and minus[k] are the layer at
+ * p + h e_k and p - h e_k (built by the caller's parameterisation), and
+ * regions[k] (NULL: the whole grid for every k) a region outside which the
+ * two meshes agree.  g_k = deps sum_{c, samples in region} Re(w_c E_adj,c
+ * E_fwd,c) (fill(plus[k]) - fill(minus[k])) / 2h, each region meshed twice
+ * into scratch and reduced in a fixed order (reproducible bit for bit).
+ * d_grad: n_params floats.  Fields and weights as for adg_grad.  Errors and
+ * scratch as above; h must be positive. */
+adg_status adg_mesh_grad_fd(adg_ctx *ctx, const adg_grid *grid, int32_t n_params,
+                            const adg_mesh_layer *plus, const adg_mesh_layer *minus,
+                            const adg_topo_region *regions, double h, double deps,
+                            const float *const d_efwd[3], const float *const d_eadj[3],
+                            const float *w, float *d_grad, void *stream);
+
 /* ---- batched work ---------------------------------------------------------
  * Many (design, operation) items run as ONE job table: four launches (bin,
  * build, VJP, finalize) whatever the number of designs, their grid sizes or

@@ -42,6 +42,12 @@ class adg_topo_region(ctypes.Structure):
                 ("ny", ctypes.c_int32), ("z0", ctypes.c_int32), ("z1", ctypes.c_int32)]
 
 
+class adg_mesh_layer(ctypes.Structure):
+    _fields_ = [("n_polys", ctypes.c_int32), ("vert_off", ctypes.c_void_p),
+                ("xy", ctypes.c_void_p), ("bound_z", ctypes.c_int32), ("z0", ctypes.c_double),
+                ("z1", ctypes.c_double)]
+
+
 class adg_design_desc(ctypes.Structure):
     _fields_ = [("grid", adg_grid), ("eps_bg", ctypes.c_double), ("eps_fg", ctypes.c_double),
                 ("logic", ctypes.c_int32), ("n_params", ctypes.c_int32), ("n_q", ctypes.c_int32),
@@ -101,6 +107,10 @@ def lib():
                 "adg_grad_fd": [P, P, P, P, P, P, ctypes.c_double, P, P],
                 "adg_grad_eh": [P, P, P, P, P, P, P, P, P, P, P, P],
                 "adg_levels_eps": [P, P, I32, P, ctypes.c_double, P, P, P],
+                "adg_mesh_fill": [P, ctypes.POINTER(adg_grid), ctypes.POINTER(adg_mesh_layer), P,
+                                  P, P],
+                "adg_mesh_grad_fd": [P, ctypes.POINTER(adg_grid), I32, P, P, P, ctypes.c_double,
+                                     ctypes.c_double, P, P, P, P, P],
                 "adg_levels_grad": [P, P, I32, P, P, P, P, P, P, P],
                 "adg_topo_eps": [P, ctypes.POINTER(adg_grid), ctypes.POINTER(adg_topo_region), P,
                                  ctypes.c_double, ctypes.c_double, P, P],
@@ -618,3 +628,110 @@ def adg_topo_grad(ctx: Context, n, ncomp, region, v, deps, efwd, eadj, w, grad, 
     _check(lib().adg_topo_grad(ctx.handle, ctypes.byref(G), ctypes.byref(R), _dptr(v), float(deps),
                                ef, ea, ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad),
                                _stream_ptr(stream)))
+
+
+# ---- the exact polygon mesher (Prop. 2) and its FD gradient ------------------
+def _grid_struct(grid: dict):
+    G = adg_grid()
+    G.nx, G.ny, G.nz = (int(v) for v in grid["n"])
+    G.ncomp = int(grid["ncomp"])
+    G.dx, G.dy, G.dz = (float(v) for v in grid["d"])
+    G.ox, G.oy, G.oz = (float(v) for v in grid["o"])
+    for c, row in enumerate(grid["off"][:3]):
+        for a in range(3):
+            G.off[c][a] = float(row[a])
+    return G
+
+
+def _layer_struct(layer: dict, keep: list):
+    """{"polys": [(N, 2) vertices], "z": (z0, z1) or None} -> adg_mesh_layer;
+    the arrays it points to are appended to `keep`."""
+    polys = [np.ascontiguousarray(np.asarray(p, dtype=np.float64).reshape(-1, 2))
+             for p in layer["polys"]]
+    off = np.zeros(len(polys) + 1, dtype=np.int32)
+    off[1:] = np.cumsum([p.shape[0] for p in polys])
+    xy = np.ascontiguousarray(np.concatenate(polys) if polys else np.zeros((0, 2)))
+    keep += [off, xy]
+    L = adg_mesh_layer()
+    L.n_polys = len(polys)
+    L.vert_off = off.ctypes.data_as(ctypes.c_void_p)
+    L.xy = xy.ctypes.data_as(ctypes.c_void_p)
+    z = layer.get("z")
+    L.bound_z = 0 if z is None else 1
+    L.z0, L.z1 = (0.0, 0.0) if z is None else (float(z[0]), float(z[1]))
+    return L
+
+
+def _field_ptrs(grid: dict, efwd, eadj, w):
+    import torch
+    nx, ny, nz = (int(v) for v in grid["n"])
+    C = int(grid["ncomp"])
+    for t, name in ((efwd, "efwd"), (eadj, "eadj")):
+        if (t.dtype != torch.complex64 or tuple(t.shape) != (C, nz, ny, nx) or not t.is_cuda
+                or not t.is_contiguous()):
+            raise ValueError("%s must be a contiguous complex64 CUDA tensor of shape %s"
+                             % (name, (C, nz, ny, nx)))
+    ef = (ctypes.c_void_p * 3)(*[efwd[c].data_ptr() if c < C else 0 for c in range(3)])
+    ea = (ctypes.c_void_p * 3)(*[eadj[c].data_ptr() if c < C else 0 for c in range(3)])
+    wc = np.asarray(w, dtype=np.complex128).reshape(-1)
+    if wc.size == 1:
+        wc = np.repeat(wc, C)
+    ww = np.zeros(6, dtype=np.float32)
+    ww[0:2 * C:2] = wc.real[:C]
+    ww[1:2 * C:2] = wc.imag[:C]
+    return ef, ea, ww
+
+
+def adg_mesh_fill(ctx: Context, grid: dict, layer: dict, fill, region=None, stream=None):
+    """fill (ncomp, nz, ny, nx) <- the exact volume-averaged fill of a polygon
+    layer (Prop. 2's standard representation) over `region` (x0, y0, nx, ny,
+    z0, z1; None: the whole grid)."""
+    import torch
+    nx, ny, nz = (int(v) for v in grid["n"])
+    shape = (int(grid["ncomp"]), nz, ny, nx)
+    if (fill.dtype != torch.float32 or tuple(fill.shape) != shape or not fill.is_cuda
+            or not fill.is_contiguous()):
+        raise ValueError("fill must be a contiguous float32 CUDA tensor of shape %s" % (shape,))
+    keep = []
+    G, L = _grid_struct(grid), _layer_struct(layer, keep)
+    R = ctypes.byref(_topo_region(region)) if region is not None else None
+    _check(lib().adg_mesh_fill(ctx.handle, ctypes.byref(G), ctypes.byref(L), R, _dptr(fill),
+                               _stream_ptr(stream)))
+
+
+class MeshLayers:
+    """A list of polygon layers marshalled once into an adg_mesh_layer array
+    (the arrays it points to are kept alive with it)."""
+
+    def __init__(self, layers):
+        self._keep = []
+        self.n = len(layers)
+        self.array = (adg_mesh_layer * max(self.n, 1))(*[_layer_struct(l, self._keep)
+                                                          for l in layers])
+
+    def __len__(self):
+        return self.n
+
+
+def adg_mesh_grad_fd(ctx: Context, grid: dict, plus, minus, regions, h, deps, efwd, eadj, w, grad,
+                     stream=None):
+    """The finite-difference gradient with the exact mesher: plus[k] / minus[k]
+    are the layer at p +- h e_k (lists of layer dicts, or MeshLayers),
+    regions[k] (or None) where they can differ."""
+    import torch
+    plus = plus if isinstance(plus, MeshLayers) else MeshLayers(plus)
+    minus = minus if isinstance(minus, MeshLayers) else MeshLayers(minus)
+    n = len(plus)
+    if len(minus) != n or (regions is not None and len(regions) != n):
+        raise ValueError("one plus layer, minus layer and region per parameter")
+    if grad.dtype != torch.float32 or grad.numel() != n or not grad.is_cuda:
+        raise ValueError("grad must be a float32 CUDA tensor of n_params entries")
+    G = _grid_struct(grid)
+    rr = None
+    if regions is not None:
+        rr = (adg_topo_region * max(n, 1))(*[_topo_region(r) for r in regions])
+    ef, ea, ww = _field_ptrs(grid, efwd, eadj, w)
+    _check(lib().adg_mesh_grad_fd(ctx.handle, ctypes.byref(G), n, plus.array, minus.array, rr,
+                                  float(h), float(deps), ef, ea,
+                                  ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad),
+                                  _stream_ptr(stream)))

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libadg.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["adg_api.cu", "adg_kernels.cu", "adg_noalloc.cu", "adg_topo.cu", "adg_fd.cu", "adg_levels.cu"]
+SOURCES = ["adg_api.cu", "adg_kernels.cu", "adg_noalloc.cu", "adg_topo.cu", "adg_fd.cu", "adg_levels.cu", "adg_mesh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

@@ -65,6 +65,8 @@ struct adg_ctx {
   int sms = 1;
   int* d_err = nullptr;
   float* d_gtape = nullptr;  // VJP tape for programs longer than the shared-memory tape
+  void* d_mesh = nullptr;  // adg_mesh_*: polygon records, vertices, region buffers, sums
+  size_t mesh_cap = 0;     // bytes
   int gtape_blocks = 0;
   // measurement: event pairs around launches while profiling is on
   bool prof = false;
@@ -228,6 +230,7 @@ extern "C" adg_status adg_ctx_destroy(adg_ctx* ctx) {
   if (ctx->capture) cudaStreamDestroy(ctx->capture);
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_gtape);
+  cudaFree(ctx->d_mesh);
   delete ctx;
   return ADG_OK;
 }
@@ -820,6 +823,305 @@ extern "C" adg_status adg_levels_grad(adg_ctx* ctx, adg_design* const* sets, int
     st = run_single(ctx, sets[k], h_params, nullptr, nullptr, &va, k ? sets[k]->d_row : d_grad, s);
     if (st != ADG_OK) return st;
     if (k) CU(launch_add(sets[k]->d_row, d_grad, n, s));
+  }
+  return ADG_OK;
+}
+
+namespace {
+
+size_t al256b(size_t v) { return (v + 255) & ~size_t(255); }
+
+adg_status mesh_grid(const adg_grid* g, const char* who) {
+  if (!g) return fail(ADG_EINVAL, "%s: NULL grid", who);
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->ncomp < 1 || g->ncomp > 3)
+    return fail(ADG_EINVAL, "%s: grid %dx%dx%d with %d components", who, g->nx, g->ny, g->nz,
+                g->ncomp);
+  if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0) || !std::isfinite(g->dx) ||
+      !std::isfinite(g->dy) || !std::isfinite(g->dz) || !std::isfinite(g->ox) ||
+      !std::isfinite(g->oy) || !std::isfinite(g->oz))
+    return fail(ADG_EINVAL, "%s: spacing must be positive and finite", who);
+  return ADG_OK;
+}
+
+adg_status mesh_region(const adg_grid* g, const adg_topo_region* r, const char* who,
+                       adg_topo_region& out) {
+  if (!r) {
+    out = adg_topo_region{0, 0, g->nx, g->ny, 0, g->nz};
+    return ADG_OK;
+  }
+  if (r->nx < 1 || r->ny < 1 || r->x0 < 0 || r->y0 < 0 || r->x0 + r->nx > g->nx ||
+      r->y0 + r->ny > g->ny || r->z0 < 0 || r->z1 <= r->z0 || r->z1 > g->nz)
+    return fail(ADG_EINVAL, "%s: region x [%d, %d) y [%d, %d) z [%d, %d) outside the grid", who,
+                r->x0, r->x0 + r->nx, r->y0, r->y0 + r->ny, r->z0, r->z1);
+  out = *r;
+  return ADG_OK;
+}
+
+// One public layer -> device records in cell units, keeping only polygons
+// whose box can reach an averaging cell of the region.  The records' offsets
+// are relative to the packed arrays; the pointers are set after the upload.
+adg_status mesh_pack(const adg_grid* g, const adg_mesh_layer* L, const adg_topo_region& r,
+                     const char* who, std::vector<MeshPoly>& polys, std::vector<double2>& verts,
+                     MeshLayerDev& dev, int& first) {
+  if (!L) return fail(ADG_EINVAL, "%s: NULL layer", who);
+  if (L->n_polys < 0 || (L->n_polys > 0 && (!L->vert_off || !L->xy)))
+    return fail(ADG_EINVAL, "%s: layer with %d polygons and NULL arrays", who, L->n_polys);
+  if (L->bound_z && !(L->z0 <= L->z1 && std::isfinite(L->z0) && std::isfinite(L->z1)))
+    return fail(ADG_EINVAL, "%s: layer z range [%g, %g]", who, L->z0, L->z1);
+  double omin[2] = {1e300, 1e300}, omax[2] = {-1e300, -1e300};
+  for (int c = 0; c < g->ncomp; ++c)
+    for (int a = 0; a < 2; ++a) {
+      omin[a] = std::min(omin[a], g->off[c][a]);
+      omax[a] = std::max(omax[a], g->off[c][a]);
+    }
+  const double rx0 = r.x0 + omin[0] - 0.5, rx1 = r.x0 + r.nx - 1 + omax[0] + 0.5;
+  const double ry0 = r.y0 + omin[1] - 0.5, ry1 = r.y0 + r.ny - 1 + omax[1] + 0.5;
+  first = (int)polys.size();
+  for (int p = 0; p < L->n_polys; ++p) {
+    const int v0 = L->vert_off[p], v1 = L->vert_off[p + 1];
+    if (v0 < 0 || v1 - v0 < 3 || (p == 0 && v0 != 0))
+      return fail(ADG_EINVAL, "%s: polygon %d has vertices [%d, %d) (need >= 3, offsets from 0)",
+                  who, p, v0, v1);
+    MeshPoly P{};
+    P.bx0 = P.by0 = 1e300;
+    P.bx1 = P.by1 = -1e300;
+    P.v0 = (int)verts.size();
+    P.nv = v1 - v0;
+    double area2 = 0.0;
+    for (int v = v0; v < v1; ++v) {
+      const double x = (L->xy[2 * v] - g->ox) / g->dx, y = (L->xy[2 * v + 1] - g->oy) / g->dy;
+      if (!std::isfinite(x) || !std::isfinite(y))
+        return fail(ADG_EINVAL, "%s: polygon %d vertex %d not finite", who, p, v - v0);
+      verts.push_back(make_double2(x, y));
+      P.bx0 = std::min(P.bx0, x);
+      P.bx1 = std::max(P.bx1, x);
+      P.by0 = std::min(P.by0, y);
+      P.by1 = std::max(P.by1, y);
+    }
+    for (int v = 0; v < P.nv; ++v) {
+      const double2 a = verts[P.v0 + v], b = verts[P.v0 + (v + 1) % P.nv];
+      area2 += a.x * b.y - b.x * a.y;
+    }
+    P.sgn = area2 > 0.0 ? -1.0 : 1.0;
+    if (P.bx1 <= rx0 || P.bx0 >= rx1 || P.by1 <= ry0 || P.by0 >= ry1) {
+      verts.resize(P.v0);  // never reaches the region
+      continue;
+    }
+    polys.push_back(P);
+  }
+  dev = MeshLayerDev{};
+  dev.npolys = (int)polys.size() - first;
+  dev.bound_z = L->bound_z ? 1 : 0;
+  dev.zl0 = (L->z0 - g->oz) / g->dz;
+  dev.zl1 = (L->z1 - g->oz) / g->dz;
+  return ADG_OK;
+}
+
+// Device scratch of the mesher calls: grown on demand (which synchronises the
+// device), never shrunk.
+adg_status mesh_reserve(adg_ctx* ctx, size_t need) {
+  if (ctx->mesh_cap >= need) return ADG_OK;
+  if (ctx->d_mesh) {
+    CU(cudaDeviceSynchronize());
+    CU(cudaFree(ctx->d_mesh));
+    ctx->d_mesh = nullptr;
+    ctx->mesh_cap = 0;
+  }
+  CU(cudaMalloc(&ctx->d_mesh, need));
+  ctx->mesh_cap = need;
+  return ADG_OK;
+}
+
+MeshGridDev mesh_grid_dev(const adg_grid* g) {
+  MeshGridDev m{};
+  m.C = g->ncomp;
+  for (int c = 0; c < 3; ++c)
+    for (int x = 0; x < 3; ++x) m.off[c][x] = c < g->ncomp ? g->off[c][x] : 0.0;
+  return m;
+}
+
+// Host image of the device records, laid out as on the device: polygons,
+// vertices, mesh jobs, dot jobs, chunk table (each 256-byte aligned).
+struct MeshImage {
+  size_t o_poly = 0, o_vert = 0, o_job = 0, o_dot = 0, o_chunk = 0, bytes = 0;
+  std::vector<char> h;
+  void layout(size_t np, size_t nv, size_t nj, size_t nd, size_t nc) {
+    o_poly = 0;
+    o_vert = al256b(sizeof(MeshPoly) * np);
+    o_job = o_vert + al256b(sizeof(double2) * nv);
+    o_dot = o_job + al256b(sizeof(MeshJob) * nj);
+    o_chunk = o_dot + al256b(sizeof(MeshDotJob) * nd);
+    bytes = o_chunk + al256b(sizeof(int2) * nc);
+    h.assign(bytes, 0);
+  }
+};
+
+}  // namespace
+
+extern "C" adg_status adg_mesh_fill(adg_ctx* ctx, const adg_grid* grid, const adg_mesh_layer* layer,
+                                    const adg_topo_region* region, float* d_fill, void* stream) {
+  if (!ctx || !d_fill) return fail(ADG_EINVAL, "adg_mesh_fill: NULL argument");
+  adg_status st = mesh_grid(grid, "adg_mesh_fill");
+  if (st != ADG_OK) return st;
+  adg_topo_region r;
+  st = mesh_region(grid, region, "adg_mesh_fill", r);
+  if (st != ADG_OK) return st;
+  std::vector<MeshPoly> polys;
+  std::vector<double2> verts;
+  MeshLayerDev L;
+  int first = 0;
+  st = mesh_pack(grid, layer, r, "adg_mesh_fill", polys, verts, L, first);
+  if (st != ADG_OK) return st;
+  CU(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  MeshImage im;
+  im.layout(polys.size(), verts.size(), 1, 0, 0);
+  st = mesh_reserve(ctx, im.bytes);
+  if (st != ADG_OK) return st;
+  char* base = static_cast<char*>(ctx->d_mesh);
+  if (!polys.empty()) memcpy(im.h.data() + im.o_poly, polys.data(), sizeof(MeshPoly) * polys.size());
+  if (!verts.empty()) memcpy(im.h.data() + im.o_vert, verts.data(), sizeof(double2) * verts.size());
+  MeshJob J{};
+  J.L = L;
+  J.L.polys = reinterpret_cast<const MeshPoly*>(base + im.o_poly) + first;
+  J.L.verts = reinterpret_cast<const double2*>(base + im.o_vert);
+  J.x0 = r.x0;
+  J.y0 = r.y0;
+  J.z0 = r.z0;
+  J.rx = r.nx;
+  J.ry = r.ny;
+  J.rz = r.z1 - r.z0;
+  J.s_j = grid->nx;
+  J.s_k = (long long)grid->nx * grid->ny;
+  J.s_c = J.s_k * grid->nz;
+  J.out = d_fill + (long long)r.z0 * J.s_k + (long long)r.y0 * J.s_j + r.x0;
+  memcpy(im.h.data() + im.o_job, &J, sizeof(J));
+  CU(cudaMemcpyAsync(base, im.h.data(), im.bytes, cudaMemcpyHostToDevice, s));
+  CU(launch_mesh_fill(reinterpret_cast<const MeshJob*>(base + im.o_job), 1,
+                      (long long)r.nx * r.ny * grid->ncomp, mesh_grid_dev(grid), ctx->sms, s));
+  return ADG_OK;
+}
+
+extern "C" adg_status adg_mesh_grad_fd(adg_ctx* ctx, const adg_grid* grid, int32_t n_params,
+                                       const adg_mesh_layer* plus, const adg_mesh_layer* minus,
+                                       const adg_topo_region* regions, double h, double deps,
+                                       const float* const d_efwd[3], const float* const d_eadj[3],
+                                       const float* w, float* d_grad, void* stream) {
+  const char* who = "adg_mesh_grad_fd";
+  if (!ctx || n_params < 0 || (n_params > 0 && (!plus || !minus || !d_grad)) || !d_efwd ||
+      !d_eadj || !w)
+    return fail(ADG_EINVAL, "%s: NULL argument", who);
+  if (!(h > 0.0) || !std::isfinite(h) || !std::isfinite(deps))
+    return fail(ADG_EINVAL, "%s: step h = %g, deps = %g", who, h, deps);
+  adg_status st = mesh_grid(grid, who);
+  if (st != ADG_OK) return st;
+  MeshDotFields f{};
+  for (int c = 0; c < grid->ncomp; ++c) {
+    if (!d_efwd[c] || !d_eadj[c]) return fail(ADG_EINVAL, "%s: field of component %d is NULL", who, c);
+    f.ef[c] = reinterpret_cast<const float2*>(d_efwd[c]);
+    f.ea[c] = reinterpret_cast<const float2*>(d_eadj[c]);
+    f.w[c] = make_float2(w[2 * c], w[2 * c + 1]);
+  }
+  f.nx = grid->nx;
+  f.ny = grid->ny;
+  if (n_params == 0) return ADG_OK;
+  std::vector<adg_topo_region> rs(n_params);
+  std::vector<long long> ns(n_params);
+  for (int k = 0; k < n_params; ++k) {
+    st = mesh_region(grid, regions ? regions + k : nullptr, who, rs[k]);
+    if (st != ADG_OK) return st;
+    ns[k] = (long long)grid->ncomp * (rs[k].z1 - rs[k].z0) * rs[k].ny * rs[k].nx;
+    if (ns[k] > (1LL << 30))
+      return fail(ADG_EINVAL, "%s: region of parameter %d holds %lld samples (at most 2^30)", who,
+                  k, ns[k]);
+  }
+  CU(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const MeshGridDev gd = mesh_grid_dev(grid);
+  // Parameters go in groups whose two meshes per region fit the scratch
+  // budget; each group is three launches over all of its parameters.
+  const long long budget = 1LL << 28;  // floats of region scratch per group (1 GiB)
+  for (int k0 = 0; k0 < n_params;) {
+    int k1 = k0;
+    long long tot = 0;
+    while (k1 < n_params && (k1 == k0 || tot + 2 * ns[k1] <= budget)) tot += 2 * ns[k1++];
+    const int nk = k1 - k0;
+    std::vector<MeshPoly> polys;
+    std::vector<double2> verts;
+    std::vector<MeshLayerDev> lp(nk), lm(nk);
+    std::vector<int> fp(nk), fm(nk);
+    long long max_cols = 0, nch = 0;
+    for (int k = k0; k < k1; ++k) {
+      st = mesh_pack(grid, plus + k, rs[k], who, polys, verts, lp[k - k0], fp[k - k0]);
+      if (st != ADG_OK) return st;
+      st = mesh_pack(grid, minus + k, rs[k], who, polys, verts, lm[k - k0], fm[k - k0]);
+      if (st != ADG_OK) return st;
+      max_cols = std::max(max_cols, (long long)rs[k].nx * rs[k].ny * grid->ncomp);
+      nch += (ns[k] + kMeshChunk - 1) / kMeshChunk;
+    }
+    MeshImage im;
+    im.layout(polys.size(), verts.size(), 2 * nk, nk, (size_t)nch);
+    const size_t b_part = al256b(sizeof(double) * (size_t)std::max<long long>(nch, 1));
+    st = mesh_reserve(ctx, im.bytes + b_part + sizeof(float) * (size_t)tot);
+    if (st != ADG_OK) return st;
+    char* base = static_cast<char*>(ctx->d_mesh);
+    double* part = reinterpret_cast<double*>(base + im.bytes);
+    float* buf = reinterpret_cast<float*>(base + im.bytes + b_part);
+    const MeshPoly* dpol = reinterpret_cast<const MeshPoly*>(base + im.o_poly);
+    const double2* dver = reinterpret_cast<const double2*>(base + im.o_vert);
+    if (!polys.empty())
+      memcpy(im.h.data() + im.o_poly, polys.data(), sizeof(MeshPoly) * polys.size());
+    if (!verts.empty())
+      memcpy(im.h.data() + im.o_vert, verts.data(), sizeof(double2) * verts.size());
+    MeshJob* jobs = reinterpret_cast<MeshJob*>(im.h.data() + im.o_job);
+    MeshDotJob* dots = reinterpret_cast<MeshDotJob*>(im.h.data() + im.o_dot);
+    int2* chunks = reinterpret_cast<int2*>(im.h.data() + im.o_chunk);
+    long long off = 0;
+    int ch = 0;
+    for (int k = k0; k < k1; ++k) {
+      const int i = k - k0;
+      const adg_topo_region& r = rs[k];
+      float* A = buf + off;
+      float* B = A + ns[k];
+      off += 2 * ns[k];
+      for (int side = 0; side < 2; ++side) {
+        MeshJob& J = jobs[2 * i + side];
+        J.L = side ? lm[i] : lp[i];
+        J.L.polys = dpol + (side ? fm[i] : fp[i]);
+        J.L.verts = dver;
+        J.out = side ? B : A;
+        J.x0 = r.x0;
+        J.y0 = r.y0;
+        J.z0 = r.z0;
+        J.rx = r.nx;
+        J.ry = r.ny;
+        J.rz = r.z1 - r.z0;
+        J.s_j = r.nx;
+        J.s_k = (long long)r.nx * r.ny;
+        J.s_c = J.s_k * (r.z1 - r.z0);
+      }
+      MeshDotJob& D = dots[i];
+      D.a = A;
+      D.b = B;
+      D.x0 = r.x0;
+      D.y0 = r.y0;
+      D.z0 = r.z0;
+      D.rx = r.nx;
+      D.ry = r.ny;
+      D.rz = r.z1 - r.z0;
+      D.n = (int)ns[k];
+      D.param = k;
+      D.chunk0 = ch;
+      for (long long q = 0; q < ns[k]; q += kMeshChunk) chunks[ch++] = make_int2(i, (int)q);
+      D.chunk1 = ch;
+    }
+    CU(cudaMemcpyAsync(base, im.h.data(), im.bytes, cudaMemcpyHostToDevice, s));
+    const MeshJob* djobs = reinterpret_cast<const MeshJob*>(base + im.o_job);
+    const MeshDotJob* ddots = reinterpret_cast<const MeshDotJob*>(base + im.o_dot);
+    const int2* dchunks = reinterpret_cast<const int2*>(base + im.o_chunk);
+    CU(launch_mesh_fill(djobs, 2 * nk, max_cols, gd, ctx->sms, s));
+    CU(launch_mesh_dot(ddots, nk, dchunks, ch, f, part, deps / (2.0 * h), d_grad, ctx->sms, s));
+    k0 = k1;
   }
   return ADG_OK;
 }

@@ -147,6 +147,54 @@ struct LevelArgs {
   float2 w[3];
 };
 cudaError_t launch_levels(const LevelArgs& a, bool cot, int sms, cudaStream_t s);
+
+// Exact polygon mesher and its finite-difference gradient, adg_mesh.cu.
+// Coordinates in cell units of the grid: x -> (x - o_x) / dx and so on.
+struct MeshPoly {
+  double bx0, bx1, by0, by1;  // bounding box
+  double sgn;                 // -1 for a counter-clockwise polygon, +1 clockwise
+  int v0, nv;                 // vertices [v0, v0 + nv) of the layer's vertex array
+};
+struct MeshLayerDev {
+  const MeshPoly* polys;
+  const double2* verts;
+  int npolys;
+  int bound_z;
+  double zl0, zl1;
+};
+struct MeshGridDev {
+  int C;
+  double off[3][3];
+};
+// One mesh of one layer over one region: sample (c, x0 + i, y0 + j, z0 + k)
+// goes to out + c s_c + k s_k + j s_j + i.
+struct MeshJob {
+  MeshLayerDev L;
+  float* out;
+  int x0, y0, z0, rx, ry, rz;
+  long long s_c, s_k, s_j;
+};
+// One parameter's dot product over its region (compact [C][rz][ry][rx]
+// buffers a = fill at p + h e_k, b = at p - h e_k); chunks [chunk0, chunk1).
+struct MeshDotJob {
+  const float* a;
+  const float* b;
+  int x0, y0, z0, rx, ry, rz, n;
+  int chunk0, chunk1, param;
+};
+struct MeshDotFields {
+  const float2* ef[3];
+  const float2* ea[3];
+  float2 w[3];
+  int nx, ny;
+};
+constexpr int kMeshChunk = 2048;  // samples per dot-product block
+cudaError_t launch_mesh_fill(const MeshJob* jobs, int njobs, long long max_cols,
+                             const MeshGridDev& g, int sms, cudaStream_t s);
+// part: one double per chunk; grad[param] <- scale * (the job's chunks in order)
+cudaError_t launch_mesh_dot(const MeshDotJob* jobs, int njobs, const int2* chunks, int nchunks,
+                            const MeshDotFields& f, double* part, double scale, float* grad,
+                            int sms, cudaStream_t s);
 // part: fd_chunks(n) doubles of scratch; out: one double
 cudaError_t launch_fd_dot(const float* z, const float* a, const float* b, long long n,
                           double* part, double* out, cudaStream_t s);

@@ -470,3 +470,77 @@ def nonbinary_circles(n=(200, 200, 1), d=(20.0, 20.0, 20.0), levels=(0.1, 0.34, 
         D.set_program(("union",) + tuple(prims))
     return {"sets": [D.to_desc() for D in sets],
             "levels": np.asarray(levels, dtype=np.float64), "eps_bg": float(eps_bg)}
+
+
+def hex_hole_lattice(n=(300, 200, 40), d=(40.0, 40.0, 20.0), holes=(10, 6), R: float = 260.0,
+                     seed: int = 71, ncomp=None, sigma: str = "sigmoid", kr: float = 4.0) -> dict:
+    """Prop. 2's setting on a small scale: hexagonal holes (centre x, y
+    parameters each) etched through a 220 nm slab.  Returns the AutoDiffGeo
+    description ("desc": slab - union of Poly2D hexagons, eps 2.085 / 12.11)
+    and, for the exact mesher, the hole geometry ("R", "z", "centres": the
+    (x, y) parameter indices of each hole) from which `hex_layer` builds the
+    polygon layer at any parameter vector."""
+    rng = np.random.default_rng(seed)
+    n = tuple(int(v) for v in n)
+    nx, ny, nz = n
+    if ncomp is None:
+        ncomp = 1 if nz == 1 else 3
+    D = Design(n, d, ncomp=ncomp, eps_bg=2.085, eps_fg=12.11)
+    ex, ey = nx * d[0], ny * d[1]
+    zc = 0.5 * nz * d[2]
+    zr = (zc - 110.0, zc + 110.0) if nz > 1 else None
+    slab = D.box(z=zr) if nz > 1 else D.box(x=(-1e3, ex + 1e3))
+    hx, hy = holes
+    px, py = ex / hx, ey / hy
+    centres, hs = [], []
+    for a in range(hx):
+        for b in range(hy):
+            ix = D.param((a + 0.5) * px + rng.uniform(-0.1, 0.1) * px)
+            iy = D.param((b + 0.5) * py + rng.uniform(-0.1, 0.1) * py)
+            ang = [math.pi * m / 3.0 + math.pi / 6.0 for m in range(6)]
+            verts = [(P(ix, R * math.cos(t)), P(iy, R * math.sin(t))) for t in ang]
+            hs.append(D.polygon(verts, z=zr, sigma=sigma, kr=kr))
+            centres.append((ix, iy))
+    D.set_program(("diff", slab, ("union",) + tuple(hs)))
+    return {"desc": D.to_desc(), "R": float(R), "z": zr, "centres": centres}
+
+
+def hex_layer(spec: dict, params) -> dict:
+    """The holes of `hex_hole_lattice` at `params` as a polygon layer for the
+    exact mesher: {"polys": [(6, 2) vertices], "z": (z0, z1) or None}."""
+    p = np.asarray(params, dtype=np.float64)
+    R = spec["R"]
+    ang = np.array([math.pi * m / 3.0 + math.pi / 6.0 for m in range(6)])
+    polys = [np.stack([p[ix] + R * np.cos(ang), p[iy] + R * np.sin(ang)], axis=1)
+             for ix, iy in spec["centres"]]
+    return {"polys": polys, "z": spec["z"]}
+
+
+def hex_fd_layers(spec: dict, params, h: float):
+    """Per parameter: the layer at p + h e_k, at p - h e_k, and a cell region
+    (x0, y0, nx, ny, z0, z1) holding every sample whose fill the step moves
+    (the moved hole's box, two cells of margin, every z)."""
+    grid = spec["desc"]["grid"]
+    nx, ny, nz = grid["n"]
+    dx, dy, _ = grid["d"]
+    ox, oy, _ = grid["o"]
+    p0 = np.asarray(params, dtype=np.float64)
+    owner = {}
+    for hidx, (ix, iy) in enumerate(spec["centres"]):
+        owner[ix] = owner[iy] = hidx
+    plus, minus, regions = [], [], []
+    R = spec["R"]
+    for k in range(p0.size):
+        pp, pm = p0.copy(), p0.copy()
+        pp[k] += h
+        pm[k] -= h
+        plus.append(hex_layer(spec, pp))
+        minus.append(hex_layer(spec, pm))
+        ix, iy = spec["centres"][owner[k]]
+        x0 = int(math.floor((p0[ix] - R - h - ox) / dx)) - 2
+        x1 = int(math.ceil((p0[ix] + R + h - ox) / dx)) + 2
+        y0 = int(math.floor((p0[iy] - R - h - oy) / dy)) - 2
+        y1 = int(math.ceil((p0[iy] + R + h - oy) / dy)) + 2
+        x0, y0, x1, y1 = max(x0, 0), max(y0, 0), min(x1, nx), min(y1, ny)
+        regions.append((x0, y0, x1 - x0, y1 - y0, 0, nz))
+    return plus, minus, regions

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 from paper_2311_05646_gb300 import inputs as I
+from paper_2311_05646_gb300.inputs import P
 
 from . import _geom as G
 
@@ -568,6 +569,133 @@ def test_levels_equal_levels_are_the_binary_union(logic):
     one["eps_bg"], one["eps_fg"] = 1.0, 1.8
     got = LV.eps(sets, m["levels"], 1.0)
     assert np.abs(got - O.eps(one)).max() <= 1e-13
+
+
+# ----------------------------------- the exact polygon mesher (Prop. 2) -----
+def _star(rng, cx, cy, r, nv=9):
+    """A concave star-shaped polygon (radii alternate), counter-clockwise."""
+    t = np.sort(rng.uniform(0, 2 * np.pi, nv))
+    rad = r * np.where(np.arange(nv) % 2 == 0, 1.0, 0.45) * rng.uniform(0.8, 1.0, nv)
+    return np.stack([cx + rad * np.cos(t), cy + rad * np.sin(t)], axis=1)
+
+
+def _inside(poly, x, y):
+    """Even-odd ray casting (vectorised over points)."""
+    inside = np.zeros(np.broadcast(x, y).shape, dtype=bool)
+    n = len(poly)
+    for a in range(n):
+        (x0, y0), (x1, y1) = poly[a], poly[(a + 1) % n]
+        cross = (y0 > y) != (y1 > y)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            xi = x0 + (y - y0) * (x1 - x0) / (y1 - y0)
+        inside ^= cross & (x < xi)
+    return inside
+
+
+def _grid(n, d=(10.0, 10.0, 10.0), off=((0.5, 0.5, 0.0),), o=(0.0, 0.0, 0.0)):
+    return {"n": n, "ncomp": len(off), "d": d, "o": o, "off": [list(r) for r in off]}
+
+
+def test_mesh_total_area_is_the_polygons_area():
+    """Non-overlapping concave polygons inside the grid: the fills, times the
+    cell area, add up to the shoelace areas, for any sample offset."""
+    from oracle import mesh as M
+    rng = np.random.default_rng(3)
+    polys = [_star(rng, 120.0, 110.0, 60.0), _star(rng, 330.0, 200.0, 80.0, nv=12),
+             _star(rng, 260.0, 60.0, 35.0, nv=7)[::-1]]
+    want = sum(abs(G.area([tuple(v) for v in p])) for p in polys)
+    for off in ((0.5, 0.5, 0.0), (0.0, 0.0, 0.0), (0.25, 0.8, 0.0)):
+        f = M.fill(_grid((50, 52, 1), d=(10.0, 7.0, 10.0), off=(off,)), {"polys": polys, "z": None})
+        assert abs(f.sum() * 70.0 - want) <= 1e-9 * want
+
+
+def test_mesh_rectangle_is_the_product_of_overlaps():
+    from oracle import mesh as M
+    grid = _grid((20, 16, 1), off=((0.5, 0.5, 0.0), (0.0, 0.5, 0.0)))
+    x0, x1, y0, y1 = 23.7, 141.2, 38.05, 97.9
+    rect = np.array([[x0, y0], [x1, y0], [x1, y1], [x0, y1]])
+    f = M.fill(grid, {"polys": [rect], "z": None})
+    for c, off in enumerate(grid["off"]):
+        xs = (np.arange(20) + off[0]) * 10.0
+        ys = (np.arange(16) + off[1]) * 10.0
+        ox = np.clip(np.minimum(xs + 5, x1) - np.maximum(xs - 5, x0), 0, None) / 10.0
+        oy = np.clip(np.minimum(ys + 5, y1) - np.maximum(ys - 5, y0), 0, None) / 10.0
+        assert np.abs(f[c, 0] - oy[:, None] * ox[None, :]).max() <= 1e-13
+
+
+def test_mesh_box_matches_the_exact_autodiffgeo_box(oracle_mod):
+    """An axis-aligned box: the mesher and the AutoDiffGeo box with its exact
+    edge form (Eq. linear, zero error against volume averaging) agree, in 3D
+    with Yee offsets and a z range."""
+    from oracle import mesh as M
+    D = I.Design((24, 18, 12), (10.0, 10.0, 10.0), ncomp=3, eps_bg=0.0, eps_fg=1.0)
+    D.box(x=(31.3, 177.8), y=(12.6, 141.05), z=(22.2, 87.5))
+    desc = D.to_desc()
+    rect = np.array([[31.3, 12.6], [177.8, 12.6], [177.8, 141.05], [31.3, 141.05]])
+    f = M.fill(desc["grid"], {"polys": [rect], "z": (22.2, 87.5)})
+    assert np.abs(f - oracle_mod.fill(desc)).max() <= 1e-12
+
+
+def test_mesh_converges_to_supersampling():
+    """Lattice supersampling of a concave polygon's indicator converges to the
+    mesher's fill (first order in the sub-lattice step)."""
+    from oracle import mesh as M
+    rng = np.random.default_rng(8)
+    poly = _star(rng, 100.0, 90.0, 70.0, nv=11)
+    grid = _grid((20, 18, 1))
+    f = M.fill(grid, {"polys": [poly], "z": None})[0, 0]
+    errs = []
+    for s in (16, 64):
+        u = (np.arange(s) + 0.5) / s
+        X = (np.arange(20)[:, None] + u[None, :]).reshape(-1) * 10.0
+        Y = (np.arange(18)[:, None] + u[None, :]).reshape(-1) * 10.0
+        ins = _inside(poly, X[None, :], Y[:, None]).astype(np.float64)
+        ss = ins.reshape(18, s, 20, s).mean(axis=(1, 3))
+        errs.append(np.abs(ss - f).max())
+    assert errs[1] < 0.4 * errs[0] and errs[1] < 0.03
+
+
+def test_mesh_special_values():
+    """Half a cell cut along its diagonal is 0.5 in either winding; a polygon
+    covering everything gives the exact z overlap of the layer."""
+    from oracle import mesh as M
+    grid = _grid((4, 3, 1))
+    tri = np.array([[10.0, 10.0], [20.0, 10.0], [20.0, 20.0]])
+    for p in (tri, tri[::-1]):
+        f = M.fill(grid, {"polys": [p], "z": None})[0, 0]
+        assert f[1, 1] == 0.5 and f.sum() == 0.5
+    g3 = _grid((3, 2, 6), off=((0.5, 0.5, 0.5),))
+    big = np.array([[-100.0, -100.0], [100.0, -100.0], [100.0, 100.0], [-100.0, 100.0]])
+    f = M.fill(g3, {"polys": [big], "z": (13.0, 38.5)})
+    zs = (np.arange(6) + 0.5) * 10.0
+    want = np.clip(np.minimum(zs + 5, 38.5) - np.maximum(zs - 5, 13.0), 0, None) / 10.0
+    assert np.abs(f[0, :, 1, 1] - want).max() <= 1e-15
+
+
+def test_mesh_fd_on_boxes_is_the_exact_gradient(oracle_mod):
+    """Central differences of exactly meshed rectangles, with the step inside
+    a cell, equal the AutoDiffGeo gradient of the same boxes in their exact
+    edge form (both are the exact derivative of the volume average there)."""
+    from oracle import mesh as M
+    D = I.Design((40, 20, 1), (10.0, 10.0, 10.0), ncomp=1, eps_bg=1.0, eps_fg=3.5)
+    edges = [(33.2, 96.7), (151.4, 233.9), (288.1, 351.35)]
+    boxes = []
+    for a, b in edges:
+        ia, ib = D.param(a), D.param(b)
+        boxes.append(D.box(x=(P(ia), P(ib)), y=(41.3, 122.6)))
+    desc = D.to_desc()
+    ef, ea, w = _fields(desc, 91, 92, 93)
+
+    def layer(p):
+        return {"polys": [np.array([[p[2 * k], 41.3], [p[2 * k + 1], 41.3], [p[2 * k + 1], 122.6],
+                                    [p[2 * k], 122.6]]) for k in range(3)], "z": None}
+    p0 = desc["params"]
+    h = 0.01
+    plus = [layer(p0 + h * np.eye(p0.size)[k]) for k in range(p0.size)]
+    minus = [layer(p0 - h * np.eye(p0.size)[k]) for k in range(p0.size)]
+    g = M.grad_fd(desc["grid"], plus, minus, ef, ea, w, h, 2.5)
+    gad = oracle_mod.grad(desc, ef, ea, w)
+    assert np.abs(g - gad).max() <= 1e-9 * np.abs(gad).max()
 
 
 # ------------------------------------------- material levels (dense form) ---
