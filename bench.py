@@ -177,10 +177,22 @@ def oracle_sample(desc, ef, ea, w, target_s=15.0):
         _sample_text(desc, box), dt)
 
 
-def make_inputs():
+def grid_of(args):
+    """The grating's grid: 600x200x120 unless --grid NXxNYxNZ asks for another."""
+    g = getattr(args, "grid", "") or "600x200x120"
+    return tuple(int(v) for v in g.split("x"))
+
+
+def workload_name(n):
+    if tuple(n) == (600, 200, 120):
+        return WORKLOAD
+    return WORKLOAD.replace("600x200x120", "%dx%dx%d" % tuple(n))
+
+
+def make_inputs(n=(600, 200, 120)):
     import numpy as np
     from paper_2311_05646_gb300 import inputs as I
-    desc = I.grating_3d()
+    desc = I.grating_3d(n=tuple(n))
     ef = I.plane_wave_field(desc, 22)
     ea = I.plane_wave_field(desc, 23)
     w = np.full(3, -2j, dtype=np.complex64)  # Eq. 1: w = -2 i omega, omega = 1
@@ -191,7 +203,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    desc, ef, ea, w = make_inputs()
+    desc, ef, ea, w = make_inputs(grid_of(args))
     from oracle import oracle as O
     nx, ny, nz = desc["grid"]["n"]
     # bounded sample per step: z-planes through the slab, sized so that the
@@ -215,7 +227,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": sample},
+            "config": {"workload": workload_name(grid_of(args)), "sample": sample},
             "cpu_baseline": {"value": value, "unit": "cells/s", "cores": O.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0,
@@ -224,10 +236,12 @@ def run_reference(args):
     return 0
 
 
-def _traffic(kernel, tile=None):
+def _traffic(kernel, tile=None, grid=(600, 200, 120)):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when the kernel source (or the tile shape) changed since the counters
-    were taken."""
+    None when the kernel source (or the tile shape, or the grid) differs from
+    the one the counters were taken on."""
+    if tuple(grid) != (600, 200, 120):
+        return None
     try:
         import hashlib
         tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
@@ -260,7 +274,7 @@ def run_adg(args):
 
     from paper_2311_05646_gb300 import adg
 
-    desc, ef_h, ea_h, w = make_inputs()
+    desc, ef_h, ea_h, w = make_inputs(grid_of(args))
     nx, ny, nz = desc["grid"]["n"]
     C = desc["grid"]["ncomp"]
     cells = nx * ny * nz
@@ -343,7 +357,7 @@ def run_adg(args):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     fill_warps = int(tile[3]) if tile is not None and len(tile) > 3 else 1
     opts = list(stats["tile"]) + ([fill_warps] if fill_warps > 1 else [])
-    traffic = _traffic(dom, opts)
+    traffic = _traffic(dom, opts, (nx, ny, nz))
     roof = {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "algorithmic_bytes_per_launch": kern[dom],
@@ -412,7 +426,7 @@ def run_adg(args):
                  "stream_bytes_per_launch": stream_bytes, "stream_us_per_launch": us_k,
                  "stream_GBps": stream_bytes / (us_k * 1e-6) / 1e9,
                  "stream_frac_of_measured_hbm": stream_bytes / (us_k * 1e-6) / 1e9 / peak,
-                 "stream_traffic": _traffic("dense", opts),
+                 "stream_traffic": _traffic("dense", opts, (nx, ny, nz)),
                  "call_GBps": (stream_bytes + kern["vjp"]) / (ms_dense * 1e-3) / 1e9,
                  "call_frac_of_measured_hbm": (stream_bytes + kern["vjp"]) / (ms_dense * 1e-3) / 1e9 / peak,
                  "vjp_us_per_launch": 1e3 * dprof["vjp"][1] / max(dprof["vjp"][0], 1)}
@@ -539,8 +553,8 @@ def run_adg(args):
     mesh = None
     if not args.no_dense:
         from paper_2311_05646_gb300 import inputs as I
-        spec = I.hex_hole_lattice(n=(nx, ny, nz), d=desc["grid"]["d"], holes=(20, 6), R=260.0,
-                                  ncomp=C)
+        spec = I.hex_hole_lattice(n=(nx, ny, nz), d=desc["grid"]["d"], holes=(max(1, nx // 30), 6),
+                                  R=260.0, ncomp=C)
         hdesc = spec["desc"]
         hp = hdesc["params"]
         hdes = adg.Design(ctx, hdesc)
@@ -646,7 +660,8 @@ def run_adg(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells_per_design": cells, "components": C,
+            "config": {"workload": workload_name(grid_of(args)), "cells_per_design": cells,
+                       "components": C,
                        "params": int(design.n_params), "parallelism": "replicas" if world > 1 else "single",
                        "outputs": "fill + eps (fp32) + gradient",
                        "vjp": "band tiles only (tiles crossed by an edge band)",
@@ -880,6 +895,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--workload", default="grating3d", choices=["grating3d", "batch", "serve"])
+    ap.add_argument("--grid", default="")  # grating3d: NXxNYxNZ (default 600x200x120)
     ap.add_argument("--designs", type=int, default=256)
     ap.add_argument("--tune", action="store_true")  # batch: autotune tiles per size class
     ap.add_argument("--no-tune", action="store_true")  # grating: the library's default tile
