@@ -64,9 +64,15 @@ typedef enum {
  *            (or y - f(x) with ADG_GRAPH_ABOVE), f the piecewise-linear
  *            interpolant through (X_j, Y_j), constant beyond the end knots;
  *            k = kr / dy.
- *   CIRCLE/POLYGON/GRAPH are extruded along z by the exact overlap of [z0, z1]
- *   when ADG_BOUND_Z is set (planarity, Sec. 5.2).  CIRCLE and POLYGON need
- *   dx == dy.
+ *   POLAR    Polar2D (star-convex) with a Fourier boundary (the PSGC
+ *            scatterers' R(theta) = R0 + sum_n c_n cos(n theta) + s_n sin(n theta)):
+ *            q = cx, cy, R0, z0, z1, c1, s1, ..., cN, sN (0 <= N <= 32);
+ *            s = sigma_k(R(theta) - r), r and theta polar about (cx, cy);
+ *            k = kr / dx.  N = 0 is CIRCLE.  With ADG_PRIM_POLAR the derivative
+ *            w.r.t. the centre is 0 at r = 0.
+ *   CIRCLE/POLYGON/GRAPH/POLAR are extruded along z by the exact overlap of
+ *   [z0, z1] when ADG_BOUND_Z is set (planarity, Sec. 5.2).  CIRCLE, POLYGON
+ *   and POLAR need dx == dy.
  * Sigma kinds: Table "Nonlinear function definitions", sigma_k(x) = sigma(k x).
  * Logic (Eqs. union/intersection, Appendix B.2):
  *   PRODUCT: union a + b - ab, intersection ab, difference a (1 - b)
@@ -79,7 +85,8 @@ typedef enum {
  * Parameter map: q_j = q_base[j] + q_coeff[j] * params[q_param[j]], or
  *   q_base[j] when q_param[j] = -1 (a fixed scalar).
  */
-enum { ADG_PRIM_BOX = 0, ADG_PRIM_CIRCLE = 1, ADG_PRIM_POLYGON = 2, ADG_PRIM_GRAPH = 3 };
+enum { ADG_PRIM_BOX = 0, ADG_PRIM_CIRCLE = 1, ADG_PRIM_POLYGON = 2, ADG_PRIM_GRAPH = 3,
+       ADG_PRIM_POLAR = 4 };
 enum {
   ADG_SIGMA_LINEAR = 0,
   ADG_SIGMA_SIGMOID = 1,

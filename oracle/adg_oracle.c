@@ -31,7 +31,8 @@
  * notes): sample offsets are inputs; kinks take the closed interval; the
  * polygon normal points inward whatever the winding; difference(a,b) =
  * intersection(a, 1-b); clamp subgradients pass through at the boundary;
- * a circle's derivative w.r.t. its centre is 0 at r = 0.
+ * a circle's derivative w.r.t. its centre is 0 at r = 0, and so is a polar
+ * shape's (whose angle is then taken as 0).
  */
 #include <math.h>
 #include <stdint.h>
@@ -42,7 +43,7 @@
 #endif
 
 /* ---- description enums (the input format; see the design notes) ---------- */
-enum { OD_BOX = 0, OD_CIRCLE = 1, OD_POLYGON = 2, OD_GRAPH = 3 };
+enum { OD_BOX = 0, OD_CIRCLE = 1, OD_POLYGON = 2, OD_GRAPH = 3, OD_POLAR = 4 };
 enum { OD_LINEAR = 0, OD_SIGMOID = 1, OD_QUADRATIC = 2, OD_SIN = 3, OD_ERF = 4 };
 enum { OD_PRODUCT = 0, OD_CLAMP = 1 };
 enum {
@@ -194,6 +195,41 @@ int od_prim(const od_design *D, int pi, const double *q, const double r[3], doub
       if (rr > 0.0) {
         dsdq[0] = g * (ddx / rr); /* d(-r)/d cx = (x - cx)/r */
         dsdq[1] = g * (ddy / rr);
+      }
+    }
+  } else if (kind == OD_POLAR) {
+    /* Polar2D (Table 4) with the Fourier boundary of the PSGC scatterers:
+     * sigma_k(R(theta) - r), R(theta) = R0 + sum_n c_n cos(n theta) + s_n sin(n theta),
+     * theta and r the polar angle and radius about (cx, cy);
+     * q = cx, cy, R0, z0, z1, c_1, s_1, ..., c_N, s_N */
+    if (nq < 5 || (nq - 5) % 2) return -1;
+    const int N = (nq - 5) / 2;
+    double cx = Q[0], cy = Q[1];
+    zq0 = 3;
+    if (fl & OD_BOUND_Z) zf = overlap1d(Q[3], Q[4], r[2], D->d[2], &dz0, &dz1);
+    double ddx = r[0] - cx, ddy = r[1] - cy;
+    double rr = sqrt(ddx * ddx + ddy * ddy);
+    double th = rr > 0.0 ? atan2(ddy, ddx) : 0.0;
+    double Rth = Q[2], dR = 0.0; /* R(theta), dR / dtheta */
+    for (int n = 1; n <= N; ++n) {
+      double cn = Q[3 + 2 * n], sn = Q[4 + 2 * n];
+      Rth += cn * cos(n * th) + sn * sin(n * th);
+      dR += n * (sn * cos(n * th) - cn * sin(n * th));
+    }
+    double k = D->kr[pi] / D->d[0], ds;
+    double sg = od_sigma(sk, k * (Rth - rr), &ds);
+    *s_out = sg * zf;
+    if (dsdq) {
+      double g = k * ds * zf; /* d s / d (R(theta) - r) */
+      dsdq[2] = g;
+      for (int n = 1; n <= N; ++n) {
+        dsdq[3 + 2 * n] = g * cos(n * th);
+        dsdq[4 + 2 * n] = g * sin(n * th);
+      }
+      if (rr > 0.0) {
+        /* d theta / d cx = (y - cy) / r^2, d theta / d cy = -(x - cx) / r^2 */
+        dsdq[0] = g * (ddx / rr + dR * ddy / (rr * rr));
+        dsdq[1] = g * (ddy / rr - dR * ddx / (rr * rr));
       }
     }
   } else if (kind == OD_POLYGON) {

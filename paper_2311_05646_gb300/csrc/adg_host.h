@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "../../include/adg.h"
 #include "adg_internal.h"
@@ -80,14 +81,18 @@ inline adg_status validate(const adg_design_desc* D, Msg& m) {
       if (n != 5) return m.set(ADG_EINVAL, "circle %d needs 5 scalars, has %d", p, n);
     } else if (k == ADG_PRIM_GRAPH) {
       if (n < 6 || (n - 2) % 2) return m.set(ADG_EINVAL, "graph %d needs 2 + 2M scalars, M >= 2", p);
+    } else if (k == ADG_PRIM_POLAR) {
+      if (n < 5 || (n - 5) % 2 || (n - 5) / 2 > kMaxPolarHarm)
+        return m.set(ADG_EINVAL, "polar %d needs 5 + 2N scalars, 0 <= N <= %d", p, kMaxPolarHarm);
     } else if (k == ADG_PRIM_POLYGON) {
       if (n < 8 || (n - 2) % 2 || (n - 2) / 2 > kMaxPolyVerts)
         return m.set(ADG_EINVAL, "polygon %d needs 2 + 2N scalars, 3 <= N <= %d", p, kMaxPolyVerts);
     } else {
       return m.set(ADG_EINVAL, "primitive %d: kind %d unknown", p, k);
     }
-    if ((k == ADG_PRIM_CIRCLE || k == ADG_PRIM_POLYGON) && fabs(G.dx - G.dy) > 1e-12 * G.dx)
-      return m.set(ADG_EINVAL, "primitive %d (circle / polygon) needs dx == dy", p);
+    if ((k == ADG_PRIM_CIRCLE || k == ADG_PRIM_POLYGON || k == ADG_PRIM_POLAR) &&
+        fabs(G.dx - G.dy) > 1e-12 * G.dx)
+      return m.set(ADG_EINVAL, "primitive %d (circle / polygon / polar) needs dx == dy", p);
   }
   return ADG_OK;
 }
@@ -186,6 +191,7 @@ inline int aux_doubles(int kind, int nq) {
 }
 
 inline int aux_floats(int kind, int nq) {
+  if (kind == ADG_PRIM_POLAR) return 2 * (nq - 4);  // R0, c_n, s_n (cells) as hi + lo pairs
   if (kind == ADG_PRIM_GRAPH) return vertices_of(kind, nq);
   if (kind == ADG_PRIM_POLYGON) return kPolyEdgeFloats * vertices_of(kind, nq);
   return 0;
@@ -268,6 +274,8 @@ inline void set_grid(const adg_design_desc* D, int tx, int ty, int tz, int nchai
   g.logic = D->logic;
   g.nchain = nchain;
   g.nprims = D->n_prims;
+  g.polar = 0;
+  for (int p = 0; p < D->n_prims; ++p) g.polar |= D->prim_kind[p] == ADG_PRIM_POLAR;
 }
 
 inline bool tile_ok(int tx, int ty, int tz) {
@@ -327,8 +335,9 @@ inline adg_status prepare_prims(const GridDev& g, const double d[3], const doubl
     for (int a = 0; a < 3; ++a) { vlo[a] = 0; vhi[a] = nn[a] - 1; }
     auto zrange = [&]() {
       if (!(R.flags & kBoundZ)) return;
-      const double a = cellc(Q[R.kind == kCircle ? 3 : 0], 2);
-      const double b = cellc(Q[R.kind == kCircle ? 4 : 1], 2);
+      const bool c5 = R.kind == kCircle || R.kind == kPolar;  // z0, z1 after cx, cy, R
+      const double a = cellc(Q[c5 ? 3 : 0], 2);
+      const double b = cellc(Q[c5 ? 4 : 1], 2);
       anchor(a, R.ai[4], R.af[4]);
       anchor(b, R.ai[5], R.af[5]);
       cell_range(a - 0.5, b + 0.5, g.offmin[2], g.offmax[2], g.nz, vlo[2], vhi[2]);
@@ -353,6 +362,36 @@ inline adg_status prepare_prims(const GridDev& g, const double d[3], const doubl
       R.g[2] = (float)(R2 - (double)R.g[1]);
       R.g[3] = Rc < 0 ? 1.f : 0.f;
       const double ext = fabs(Rc) + beta;
+      cell_range(cx - ext, cx + ext, g.offmin[0], g.offmax[0], g.nx, vlo[0], vhi[0]);
+      cell_range(cy - ext, cy + ext, g.offmin[1], g.offmax[1], g.ny, vlo[1], vhi[1]);
+      zrange();
+      for (int a = 0; a < 3; ++a) { plo[a] = vlo[a]; phi[a] = vhi[a]; }
+    } else if (R.kind == kPolar) {
+      // Polar2D: R0 and the Fourier coefficients in cells (FP64 on the
+      // device); g[1] / g[2] bound R(theta) from above / below for the binner
+      const int N = (P.nq[pi] - 5) / 2;
+      R.naux = N;
+      const double cx = cellc(Q[0], 0), cy = cellc(Q[1], 1);
+      anchor(cx, R.ai[0], R.af[0]);
+      anchor(cy, R.ai[1], R.af[1]);
+      std::vector<double> A(1 + 2 * N);
+      A[0] = Q[2] / d[0];
+      double amp = 0.0;
+      for (int n = 1; n <= N; ++n) {
+        A[2 * n - 1] = Q[3 + 2 * n] / d[0];
+        A[2 * n] = Q[4 + 2 * n] / d[0];
+        amp += fabs(A[2 * n - 1]) + fabs(A[2 * n]);
+      }
+      float* F = auxf + R.auxf_off;  // hi + lo pairs: about 48 bits, read back in FP64
+      for (int j = 0; j <= 2 * N; ++j) {
+        F[2 * j] = (float)A[j];
+        F[2 * j + 1] = (float)(A[j] - (double)F[2 * j]);
+      }
+      const double rmax = A[0] + amp, rmin = A[0] - amp;
+      R.g[0] = (float)A[0];
+      R.g[1] = (float)rmax;
+      R.g[2] = (float)rmin;
+      const double ext = std::max(rmax, 0.0) + beta + 1e-6 * (1.0 + fabs(rmax));
       cell_range(cx - ext, cx + ext, g.offmin[0], g.offmax[0], g.nx, vlo[0], vhi[0]);
       cell_range(cy - ext, cy + ext, g.offmin[1], g.offmax[1], g.ny, vlo[1], vhi[1]);
       zrange();

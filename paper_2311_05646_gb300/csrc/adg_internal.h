@@ -34,7 +34,8 @@ constexpr int kPoolSpare = 192;
 constexpr int kLeafTabBytes = 80;
 constexpr size_t kTapeBlockFloats = (size_t)kMaxOps * kBlock;  // global tape per VJP block
 
-enum : int32_t { kBox = 0, kCircle = 1, kPolygon = 2, kGraph = 3 };
+enum : int32_t { kBox = 0, kCircle = 1, kPolygon = 2, kGraph = 3, kPolar = 4 };
+constexpr int kMaxPolarHarm = 32;  // Fourier harmonics of one Polar2D boundary
 enum : int32_t { kLinear = 0, kSigmoid = 1, kQuadratic = 2, kSin = 3, kErf = 4 };
 enum : int32_t { kBoundX = 1, kBoundY = 2, kBoundZ = 4, kRectSigma = 8, kGraphAbove = 16,
                  kPolyRigid = 32 /* every vertex x (y) is the same scalar of one parameter */ };
@@ -66,6 +67,7 @@ struct GridDev {
   int logic;
   int nchain;
   int nprims;
+  int polar;  // some primitive is Polar2D (the VJP then takes its polar-aware path)
 };
 
 // One primitive after the parameter map, in cell units of each axis:

@@ -162,6 +162,44 @@ __device__ __forceinline__ float circle_dist(const PrimRec& P, const Cell& c, fl
   return den > 0.f ? ((P.g[1] - ii2) + (P.g[2] - cr)) / den : 0.f;
 }
 
+// Polar2D with a Fourier boundary: R(theta) - r in cells, FP64 (R0 and the
+// coefficients come from auxf as hi + lo float pairs: R0, c_1, s_1, ..., c_N,
+// s_N).  cos(n theta),
+// sin(n theta) by the angle-addition recurrence from cos, sin theta = (dx,
+// dy) / r; at r = 0 theta is taken as 0.  Out: cos, sin theta, 1 / r (0 at
+// r = 0) and dR / dtheta.
+__device__ __forceinline__ double polar_coef(const float* F, int j) {
+  return (double)F[2 * j] + (double)F[2 * j + 1];
+}
+
+__device__ __forceinline__ double polar_geom(const PrimRec& P, const Cell& c, const float* auxf,
+                                             double& cth, double& sth, double& ir, double& dR) {
+  const double dx = (double)(c.i - P.ai[0]) + ((double)c.ox - (double)P.af[0]);
+  const double dy = (double)(c.j - P.ai[1]) + ((double)c.oy - (double)P.af[1]);
+  const double r = sqrt(dx * dx + dy * dy);
+  if (r > 0.0) { ir = 1.0 / r; cth = dx * ir; sth = dy * ir; }
+  else { ir = 0.0; cth = 1.0; sth = 0.0; }
+  const float* F = auxf + P.auxf_off;
+  double R = polar_coef(F, 0), d1 = 0.0, cn = cth, sn = sth;
+  for (int n = 1; n <= P.naux; ++n) {
+    const double a = polar_coef(F, 2 * n - 1), b = polar_coef(F, 2 * n);
+    R += a * cn + b * sn;
+    d1 += (double)n * (b * cn - a * sn);
+    const double c2 = cn * cth - sn * sth, s2 = sn * cth + cn * sth;
+    cn = c2;
+    sn = s2;
+  }
+  dR = d1;
+  return R - r;
+}
+
+// The value-only form for the build and the tables.  Not inlined, like
+// graph_dist: its FP64 work and outputs stay off the other kinds' paths.
+__device__ __noinline__ float polar_dist(const PrimRec& P, const Cell& c, const float* auxf) {
+  double cth, sth, ir, dR;
+  return (float)polar_geom(P, c, auxf, cth, sth, ir, dR);
+}
+
 // GeneralCartesian2D: segment of the piecewise-linear f containing u_x.
 __device__ __forceinline__ int graph_seg(const float* Xf, int M, float ux) {
   if (ux <= Xf[0]) return -1;
@@ -265,6 +303,7 @@ __device__ __forceinline__ float leaf_value(const PrimRec& P, const Cell& c, con
     const float d = graph_dist(P, c, auxf, auxd, seg, t);
     return sigma_f(P.sigma, P.kr * d, ds) * zf;
   }
+  if (P.kind == kPolar) return sigma_f(P.sigma, P.kr * polar_dist(P, c, auxf), ds) * zf;
   return poly_value(P, c, auxf) * zf;
 }
 
@@ -360,6 +399,7 @@ __device__ __forceinline__ int leaf_pairs(const PrimRec& P, const Cell& c, float
     return n;
   }
   if (P.kind == kGraph) return graph_pairs(P, c, a, g, actp, actcp, auxf, auxd, pk, pv);
+  if (P.kind == kPolar) return n;  // every scalar goes through polar_accumulate
   // polygon: only the extrusion scalars here; vertices go through poly_accumulate
   if (actp[0] < 0 && actp[1] < 0) return n;
   const float s = poly_value(P, c, auxf);
@@ -422,6 +462,18 @@ __device__ __forceinline__ int classify(const PrimRec& P, const float lo[3], con
     const float R = P.g[0];
     if (rmin > R + P.band + kMargin) return cOUT;
     if (rmax < R - P.band - kMargin) return cls_and(cIN, z);
+    return cBND;
+  }
+  if (P.kind == kPolar) {  // the annulus g[2] <= R(theta) <= g[1]
+    const float cx = (float)P.ai[0] + P.af[0], cy = (float)P.ai[1] + P.af[1];
+    const float nx = fmaxf(fmaxf(lo[0] - cx, cx - hi[0]), 0.f);
+    const float ny = fmaxf(fmaxf(lo[1] - cy, cy - hi[1]), 0.f);
+    const float fx = fmaxf(fabsf(lo[0] - cx), fabsf(hi[0] - cx));
+    const float fy = fmaxf(fabsf(lo[1] - cy), fabsf(hi[1] - cy));
+    const float rmin = sqrtf(nx * nx + ny * ny), rmax = sqrtf(fx * fx + fy * fy);
+    const float slack = P.band + kMargin + 1e-5f * (1.f + fabsf(P.g[1]));
+    if (rmin > P.g[1] + slack) return cOUT;
+    if (rmax < P.g[2] - slack) return cls_and(cIN, z);
     return cBND;
   }
   if (P.kind == kGraph) {
@@ -619,6 +671,74 @@ __device__ __noinline__ void poly_accumulate(const PrimRec& P, const Cell& c, fl
   }
   flush_slot(cs0, cv0, acc, cmp, lane);
   flush_slot(cs1, cv1, acc, cmp, lane);
+}
+
+// Polar2D's derivative terms at one sample, every scalar (keys cx, cy, R0, z0,
+// z1, c_1, s_1, ..., c_N, s_N): d/dR0 = 1, d/dc_n = cos(n theta), d/ds_n =
+// sin(n theta), d/dcx = cos theta + R'(theta) sin theta / r and d/dcy =
+// sin theta - R'(theta) cos theta / r (0 at r = 0), times kr sigma' zf a / d;
+// z0, z1 through the extrusion.  The distance inside sigma is FP64
+// (polar_dist); the angle factors are fp32 (hi parts of the coefficients).
+// Warp-uniform slots, merged by the same two-entry cache as the polygon's.
+__device__ __forceinline__ void polar_accumulate(const PrimRec& P, const Cell& c, float a,
+                                              const GridDev& g, const int* act, const float* actc,
+                                              const float* auxf, float* acc, float* cmp,
+                                              int lane) {
+  const int* actp = act + P.act_off;
+  const float* actcp = actc + P.act_off;
+  float dz0 = 0.f, dz1 = 0.f, s = 0.f, ds = 0.f;
+  const float zf = a != 0.f ? zfactor(P, c, dz0, dz1) : 0.f;
+  if (zf != 0.f) s = sigma_f(P.sigma, P.kr * polar_dist(P, c, auxf), ds);
+  const float gg = P.kr * ds * zf * a * g.invd[0];
+  const float gz = s * a * g.invd[2];
+  if (!__any_sync(0xffffffffu, gg != 0.f || gz != 0.f)) return;
+  // the angle terms in fp32: they scale derivatives, not the distance
+  const float dx = i2f(c.i - P.ai[0]) + (c.ox - P.af[0]);
+  const float dy = i2f(c.j - P.ai[1]) + (c.oy - P.af[1]);
+  const float r = sqrtf(dx * dx + dy * dy);
+  const float ir = r > 0.f ? 1.f / r : 0.f;
+  const float cth = r > 0.f ? dx * ir : 1.f, sth = r > 0.f ? dy * ir : 0.f;
+  const float* F = auxf + P.auxf_off;
+  float dR = 0.f, cn = cth, sn = sth;
+  for (int n = 1; n <= P.naux; ++n) {
+    dR += (float)n * (F[4 * n] * cn - F[4 * n - 2] * sn);
+    const float c2 = cn * cth - sn * sth, s2 = sn * cth + cn * sth;
+    cn = c2;
+    sn = s2;
+  }
+  // one warp reduction per driven scalar, in key order (slots are warp-uniform)
+  const int nq = 5 + 2 * P.naux;
+  cn = cth;
+  sn = sth;
+  for (int key = 0; key < nq; ++key) {
+    float v;
+    if (key == 0) v = gg * (r > 0.f ? cth + dR * sth * ir : 0.f);
+    else if (key == 1) v = gg * (r > 0.f ? sth - dR * cth * ir : 0.f);
+    else if (key == 2) v = gg;
+    else if (key == 3) v = gz * dz0;
+    else if (key == 4) v = gz * dz1;
+    else if (key & 1) v = gg * cn;
+    else {
+      v = gg * sn;
+      const float c2 = cn * cth - sn * sth, s2 = sn * cth + cn * sth;
+      cn = c2;
+      sn = s2;
+    }
+    int slot = actp[key];
+    if (slot < 0) continue;
+    v *= actcp[key];
+    flush_slot(slot, v, acc, cmp, lane);
+  }
+}
+
+// The VJP's call for the kinds whose scalars are not all keyed, in designs
+// with Polar2D primitives: polygon vertices and every Polar2D scalar (other
+// designs call poly_accumulate directly, so their sample loop is unchanged).
+__device__ __noinline__ void shape_accumulate(const PrimRec& P, const Cell& c, float a,
+                                              const GridDev& g, const int* act, const float* actc,
+                                              const float* auxf, float* acc, float* cmp, int lane) {
+  if (P.kind == kPolar) polar_accumulate(P, c, a, g, act, actc, auxf, acc, cmp, lane);
+  else poly_accumulate(P, c, a, g, act, actc, auxf, acc, cmp, lane);
 }
 
 // --------------------------------------------------------------- kernels ---
@@ -1020,7 +1140,7 @@ __device__ __forceinline__ float box_axis(const PrimRec& P, int ax, int i, float
   return ov_exact(P.ai[2 * ax], P.af[2 * ax], P.ai[2 * ax + 1], P.af[2 * ax + 1], i, off, da, db);
 }
 
-// In-plane factor of a circle / graph / polygon at (i, j) (no z factor).
+// In-plane factor of a circle / graph / polar shape / polygon at (i, j) (no z factor).
 __device__ __forceinline__ float plane_value(const PrimRec& P, const Cell& c, const float* auxf,
                                              const double* auxd) {
   float ds;
@@ -1033,6 +1153,7 @@ __device__ __forceinline__ float plane_value(const PrimRec& P, const Cell& c, co
     double t;
     return sigma_f(P.sigma, P.kr * graph_dist(P, c, auxf, auxd, seg, t), ds);
   }
+  if (P.kind == kPolar) return sigma_f(P.sigma, P.kr * polar_dist(P, c, auxf), ds);
   return poly_value(P, c, auxf);
 }
 
@@ -2230,9 +2351,10 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
       // the global tape; the logic family is a template parameter.  The
       // variants are separate instantiations, so the shared one keeps
       // shared-memory addressing.
-      auto samples = [&](auto big, auto logic) {
+      auto samples = [&](auto big, auto logic, auto polar) {
         constexpr bool kBig = decltype(big)::value;
         constexpr int kLogic = decltype(logic)::value;
+        constexpr bool kPolarT = decltype(polar)::value;
         float* tap = (kBig ? gtape + (size_t)blockIdx.x * kTapeBlockFloats : tape) + tid;
         for (int i0 = c0; i0 < c1; i0 += kBlock) {
           if (i0 + warp * 32 >= c1) continue;  // no live lane in this warp (warp-uniform)
@@ -2286,8 +2408,13 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
             if (an != 0.f)
               n = leaf_pairs(sl[lf], cc, an, g, J.act, J.actc, J.auxf, J.auxd, pk + tid, pv + tid);
             warp_accumulate(n, 0, pk + tid, pv + tid, la, lc, lane);
-            if (kind == kPolygon)
-              poly_accumulate(sl[lf], cc, an, g, J.act, J.actc, J.auxf, la, lc, lane);
+            if constexpr (kPolarT) {
+              if (kind == kPolygon || kind == kPolar)
+                shape_accumulate(sl[lf], cc, an, g, J.act, J.actc, J.auxf, la, lc, lane);
+            } else {
+              if (kind == kPolygon)
+                poly_accumulate(sl[lf], cc, an, g, J.act, J.actc, J.auxf, la, lc, lane);
+            }
           }
         }
       };
@@ -2295,10 +2422,18 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
       using kG = std::true_type;
       using kP = std::integral_constant<int, 0>;
       using kC = std::integral_constant<int, 1>;
-      if (nops > kSmemOps) {
-        if (g.logic == 0) samples(kG{}, kP{}); else samples(kG{}, kC{});
+      using kY = std::true_type;
+      using kN = std::false_type;
+      if (g.polar) {
+        if (nops > kSmemOps) {
+          if (g.logic == 0) samples(kG{}, kP{}, kY{}); else samples(kG{}, kC{}, kY{});
+        } else {
+          if (g.logic == 0) samples(kS{}, kP{}, kY{}); else samples(kS{}, kC{}, kY{});
+        }
+      } else if (nops > kSmemOps) {
+        if (g.logic == 0) samples(kG{}, kP{}, kN{}); else samples(kG{}, kC{}, kN{});
       } else {
-        if (g.logic == 0) samples(kS{}, kP{}); else samples(kS{}, kC{});
+        if (g.logic == 0) samples(kS{}, kP{}, kN{}); else samples(kS{}, kC{}, kN{});
       }
     }  // chunks of active samples
     __syncthreads();

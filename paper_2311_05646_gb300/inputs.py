@@ -17,7 +17,7 @@ import math
 import numpy as np
 
 # ---- format codes (values fixed by the description format) -----------------
-BOX, CIRCLE, POLYGON, GRAPH = 0, 1, 2, 3
+BOX, CIRCLE, POLYGON, GRAPH, POLAR = 0, 1, 2, 3, 4
 SIGMA = {"linear": 0, "sigmoid": 1, "quadratic": 2, "sin": 3, "erf": 4}
 BOUND_X, BOUND_Y, BOUND_Z, RECT_SIGMA, GRAPH_ABOVE = 1, 2, 4, 8, 16
 OP_PUSH, OP_UNION, OP_INTERSECT, OP_DIFF = 0, 1, 2, 3
@@ -110,6 +110,16 @@ class Design:
         flags = BOUND_Z if z is not None else 0
         zz = z if z is not None else (0.0, 0.0)
         return self._prim(CIRCLE, sigma, kr, flags, [cx, cy, r, zz[0], zz[1]])
+
+    def polar(self, cx, cy, R0, coeffs=(), z=None, sigma="sigmoid", kr=4.0) -> int:
+        """Polar2D with the Fourier boundary R(theta) = R0 + sum_n c_n cos(n
+        theta) + s_n sin(n theta); coeffs = [(c_1, s_1), ..., (c_N, s_N)]."""
+        flags = BOUND_Z if z is not None else 0
+        zz = z if z is not None else (0.0, 0.0)
+        specs = [cx, cy, R0, zz[0], zz[1]]
+        for c, s in coeffs:
+            specs += [c, s]
+        return self._prim(POLAR, sigma, kr, flags, specs)
 
     def polygon(self, verts, z=None, sigma="sigmoid", kr=4.0) -> int:
         flags = BOUND_Z if z is not None else 0
@@ -544,3 +554,42 @@ def hex_fd_layers(spec: dict, params, h: float):
         x0, y0, x1, y1 = max(x0, 0), max(y0, 0), min(x1, nx), min(y1, ny)
         regions.append((x0, y0, x1 - x0, y1 - y0, 0, nz))
     return plus, minus, regions
+
+
+def psgc_lattice(n=(200, 160, 40), d=(30.0, 30.0, 30.0), rows: int = 4, cols: int = 5,
+                 harmonics: int = 6, seed: int = 81, centres: bool = False, ncomp=None,
+                 sigma: str = "sigmoid", kr: float = 4.0) -> dict:
+    """A polarisation-splitting-grating-like layout (Sec. 5.3 / 6.3): a
+    `rows` x `cols` array of Polar2D scatterers with Fourier boundaries
+    R(theta) = R0 + sum_{n <= harmonics} c_n cos(n theta) + s_n sin(n theta),
+    etched through a 220 nm slab (eps = slab - union(scatterers)).  Each
+    scatterer's R0 is a parameter; the Fourier coefficients are parameters
+    shared by the scatterers of a row; with `centres`, each scatterer's
+    (cx, cy) are parameters too."""
+    rng = np.random.default_rng(seed)
+    n = tuple(int(v) for v in n)
+    nx, ny, nz = n
+    if ncomp is None:
+        ncomp = 1 if nz == 1 else 3
+    D = Design(n, d, ncomp=ncomp, eps_bg=2.085, eps_fg=12.11)
+    ex, ey = nx * d[0], ny * d[1]
+    zc = 0.5 * nz * d[2]
+    zr = (zc - 110.0, zc + 110.0) if nz > 1 else None
+    slab = D.box(z=zr) if nz > 1 else D.box(x=(-1e3, ex + 1e3))
+    px, py = ex / cols, ey / rows
+    base = 0.28 * min(px, py)
+    scat = []
+    for r in range(rows):
+        amp = base * 0.25 / max(harmonics, 1)
+        coef = [(D.param(rng.uniform(-amp, amp)), D.param(rng.uniform(-amp, amp)))
+                for _ in range(harmonics)]
+        for c in range(cols):
+            cx = (c + 0.5) * px + rng.uniform(-0.05, 0.05) * px
+            cy = (r + 0.5) * py + rng.uniform(-0.05, 0.05) * py
+            if centres:
+                cx, cy = P(D.param(cx)), P(D.param(cy))
+            R0 = P(D.param(base * rng.uniform(0.85, 1.0)))
+            scat.append(D.polar(cx, cy, R0, [(P(a), P(b)) for a, b in coef], z=zr, sigma=sigma,
+                                kr=kr))
+    D.set_program(("diff", slab, ("union",) + tuple(scat)))
+    return D.to_desc()

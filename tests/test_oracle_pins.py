@@ -383,7 +383,7 @@ def _fields(desc, s1, s2, wseed=5):
             I.seeded_w(desc["grid"]["ncomp"], wseed))
 
 
-@pytest.mark.parametrize("case", ["grating2d", "grating3d", "taper", "random", "clamp"])
+@pytest.mark.parametrize("case", ["grating2d", "grating3d", "taper", "random", "clamp", "polar"])
 def test_p8_analytic_gradient_matches_central_fd(oracle_mod, case):
     """The reverse sweep (Eqs. AD/jaceps) equals brute-force central finite
     differences of L, the paper's baseline method, at h = 1e-3 nm."""
@@ -396,6 +396,8 @@ def test_p8_analytic_gradient_matches_central_fd(oracle_mod, case):
         desc = I.taper_3d(n=(60, 30, 12), nverts=8)
     elif case == "random":
         desc = I.random_design(7, n=(40, 30, 12), nprims=14)
+    elif case == "polar":
+        desc = I.psgc_lattice(n=(48, 40, 10), rows=2, cols=2, harmonics=3, centres=True)
     else:
         desc = I.grating_2d()
         desc["logic"] = "clamp"
@@ -458,6 +460,62 @@ def test_eh_gradient_of_a_nonmagnetic_design_is_the_eps_term(oracle_mod):
     ef, ea, we = _fields(desc, 51, 52, 53)
     hf, ha, wh = _fields(dmu, 54, 55, 56)
     assert np.array_equal(O.grad_eh(desc, dmu, ef, ea, we, hf, ha, wh), O.grad(desc, ef, ea, we))
+
+
+# ------------------------------------------------------------ Polar2D ------
+def test_polar_without_harmonics_is_the_circle(oracle_mod):
+    """Polar2D with R(theta) = R0 (no harmonics) is Circ2D (Table 4): same
+    fill and same gradient, for every sigma kind."""
+    O = oracle_mod
+    for sk in ("linear", "sigmoid", "sin"):
+        a = I.Design((40, 36, 1), (10.0, 10.0, 10.0), ncomp=1)
+        b = I.Design((40, 36, 1), (10.0, 10.0, 10.0), ncomp=1)
+        for D in (a, b):
+            ix, iy, ir = D.param(191.3), D.param(173.8), D.param(97.6)
+        a.circle(P(ix), P(iy), P(ir), sigma=sk, kr=2.0)
+        b.polar(P(ix), P(iy), P(ir), (), sigma=sk, kr=2.0)
+        da, db = a.to_desc(), b.to_desc()
+        assert np.array_equal(O.fill(da), O.fill(db))
+        ef, ea, w = _fields(da, 61, 62, 63)
+        assert np.allclose(O.grad(da, ef, ea, w), O.grad(db, ef, ea, w), rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("phase", ["cos", "sin"])
+def test_polar_table_example_lobes(oracle_mod, phase):
+    """Table 4's Polar2D example, R(1 + delta cos(alpha theta)) with alpha = 4,
+    delta = 0.2: four lobes of radius R(1 + delta) on the axes and waists of
+    R(1 - delta) on the diagonals (with sin, all turned by pi/8).  A sharp
+    sigmoid puts samples just inside / outside those radii at ~1 / ~0."""
+    O = oracle_mod
+    R, delta, h = 50.0, 0.2, 1.0
+    D = I.Design((200, 200, 1), (h, h, h), ncomp=1, off=[[0.0, 0.0, 0.0]])
+    c = (D.param(100.0), D.param(100.0))
+    coef = [(0.0, 0.0)] * 3 + ([(R * delta, 0.0)] if phase == "cos" else [(0.0, R * delta)])
+    D.polar(P(c[0]), P(c[1]), R, coef, sigma="sigmoid", kr=200.0)
+    f = O.fill(D.to_desc())[0, 0]
+    rot = 0.0 if phase == "cos" else np.pi / 8
+    for k in range(8):
+        th = rot + k * np.pi / 4
+        Rt = R * (1 + delta) if k % 2 == 0 else R * (1 - delta)
+        for rr, want in ((Rt - 1.5, 1.0), (Rt + 1.5, 0.0)):
+            x, y = 100.0 + rr * np.cos(th), 100.0 + rr * np.sin(th)
+            i, j = int(round(x)), int(round(y))
+            # the sample nearest the point: its radius differs by < 0.71 cells
+            assert abs(f[j, i] - want) < 1e-6, (phase, k, rr, f[j, i])
+
+
+def test_polar_area_of_the_fourier_boundary(oracle_mod):
+    """The area inside r < R(theta) is the integral of R(theta)^2 / 2:
+    pi R0^2 + (pi / 2) sum_n (c_n^2 + s_n^2).  With the linear sigma at k = 1
+    / dx the fill sums to it up to the boundary's curvature (< 0.2% here)."""
+    O = oracle_mod
+    D = I.Design((160, 160, 1), (1.0, 1.0, 1.0), ncomp=1)
+    D.param(0.0)
+    coef = [(3.0, -2.0), (0.0, 4.5), (2.5, 1.0)]
+    D.polar(80.3, 79.6, 50.0, coef, sigma="linear", kr=1.0)
+    f = O.fill(D.to_desc())
+    want = np.pi * 50.0 ** 2 + 0.5 * np.pi * sum(a * a + b * b for a, b in coef)
+    assert abs(f.sum() - want) < 2e-3 * want
 
 
 # ------------------------------------- non-binary union (App. B, Alg. 1) ----
