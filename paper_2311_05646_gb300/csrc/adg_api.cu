@@ -199,7 +199,7 @@ extern "C" adg_status adg_ctx_create(int32_t device, adg_ctx** out) {
   c->device = device;
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = init_kernel_attributes();
-  c->gtape_blocks = c->sms * vjp_blocks_per_sm(1);
+  c->gtape_blocks = c->sms * std::max(vjp_blocks_per_sm(1, false), vjp_blocks_per_sm(1, true));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e == cudaSuccess)
@@ -520,6 +520,7 @@ adg_status run_single(adg_ctx* ctx, adg_design* d, const double* h_params, float
   t.params = grad ? d->n_params : 0;
   t.work = d->d_counters + 12;
   t.fill_warps = d->fill_warps;
+  t.polar = d->g.polar;
   st = run_jobs(ctx, d->d_job, t, rebin, d_eps != nullptr, grad, d->g.T, s);
   if (st == ADG_OK) d->partial_dirty = false;
   return st;
@@ -1259,7 +1260,7 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   Job* hj = reinterpret_cast<Job*>(hb + o_jobs);
   size_t po = 0, ado = 0, afo = 0;
   int tile_base = 0, param_base = 0, max_tiles = 0, row_base = 0;
-  bool any_build = false, any_grad = false;
+  bool any_build = false, any_grad = false, any_polar = false;
   uint64_t sig = mix(0, (uint64_t)arena_id);
   sig = mix(sig, (uint64_t)n);
   for (int i = 0; i < n; ++i) {
@@ -1303,6 +1304,7 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
     max_tiles = std::max(max_tiles, d->g.T);
     any_build = any_build || J.do_build;
     any_grad = any_grad || J.do_grad;
+    any_polar = any_polar || (J.do_grad && d->g.polar);
     hj[i] = J;
     po += d->n_prims;
     ado += d->st.auxd_n;
@@ -1318,11 +1320,13 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   t.params = param_base;
   t.work = A.d_work;
   t.fill_warps = 1;
+  t.polar = any_polar ? 1 : 0;
+  sig = mix(sig, (uint64_t)t.polar);  // the captured VJP kernel depends on it
   sig = mix(sig, (uint64_t)bytes);
   sig = mix(sig, (uint64_t)tile_base);
   sig = mix(sig, (uint64_t)param_base);
   build_blocks_per_sm(t.njobs, t.fill_warps);  // kernel attributes are set before any capture
-  vjp_blocks_per_sm(t.njobs);
+  vjp_blocks_per_sm(t.njobs, t.polar != 0);
   const bool graph = (flags & ADG_BATCH_GRAPH) && !ctx->prof;
   if (graph && A.exec && A.sig == sig) {
     CU(cudaGraphLaunch(A.exec, s));

@@ -285,6 +285,7 @@ struct JobTotals {
   // last block of a launch resets its pair.  One launch at a time per array.
   int* work;
   int fill_warps;  // build: warps per block streaming constant tiles (1 .. kMaxFillWarps)
+  int polar;       // some job's design has Polar2D primitives: the VJP is k_vjp_polar
 };
 
 constexpr int kMaxJobs = 1024;  // jobs in one table (one batch)
@@ -302,7 +303,7 @@ cudaError_t launch_dense(const DenseArgs& a, int sms, cudaStream_t s);
 // Shared-memory limits of the kernels; call once per device before any capture.
 cudaError_t init_kernel_attributes();
 int build_blocks_per_sm(int njobs, int fill_warps);
-int vjp_blocks_per_sm(int njobs);
+int vjp_blocks_per_sm(int njobs, bool polar);
 void set_last_error(const char* msg);  // the thread-local text of adg_last_error()
 
 }  // namespace adg

@@ -9,7 +9,8 @@
 //               Table 4; Eqs. union / intersection; Sec. 5.1): persistent,
 //               warp-specialised blocks -- band warps evaluate the folded
 //               program of band tiles, a fill warp streams constant tiles.
-//   k_vjp       per band tile: the reverse sweep of Eqs. AD / jaceps seeded
+//   k_vjp       per band tile (k_vjp_polar: the same for job tables that hold
+//               Polar2D primitives): the reverse sweep of Eqs. AD / jaceps seeded
 //               with Re(w E_adj E) (Eq. 1): forward tape, reverse logic
 //               adjoints, primitive derivatives, warp-shuffle reduction per
 //               (primitive, scalar) slot into compensated block partials.
@@ -2168,9 +2169,12 @@ __host__ __device__ constexpr size_t vjp_smem(int njobs) {
 // five blocks per SM (228 KB of shared memory, 1 KB reserved per block)
 static_assert(5 * (vjp_smem(1) + 1024) <= 228 * 1024, "VJP shared memory for five blocks per SM");
 
-__global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs, int njobs,
-                                                   int* __restrict__ err,
-                                                   float* __restrict__ gtape, int* work) {
+// The VJP body; kPolarT: the job table holds Polar2D primitives (k_vjp_polar),
+// else k_vjp, whose sample loop carries no Polar2D code at all.
+template <bool kPolarT>
+__device__ __forceinline__ void vjp_body(const Job* __restrict__ jobs, int njobs,
+                                         int* __restrict__ err, float* __restrict__ gtape,
+                                         int* work) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* tape = reinterpret_cast<float*>(smem);
   float* pool = tape + kSmemOps * kBlock;
@@ -2422,18 +2426,11 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
       using kG = std::true_type;
       using kP = std::integral_constant<int, 0>;
       using kC = std::integral_constant<int, 1>;
-      using kY = std::true_type;
-      using kN = std::false_type;
-      if (g.polar) {
-        if (nops > kSmemOps) {
-          if (g.logic == 0) samples(kG{}, kP{}, kY{}); else samples(kG{}, kC{}, kY{});
-        } else {
-          if (g.logic == 0) samples(kS{}, kP{}, kY{}); else samples(kS{}, kC{}, kY{});
-        }
-      } else if (nops > kSmemOps) {
-        if (g.logic == 0) samples(kG{}, kP{}, kN{}); else samples(kG{}, kC{}, kN{});
+      using kPol = std::integral_constant<bool, kPolarT>;
+      if (nops > kSmemOps) {
+        if (g.logic == 0) samples(kG{}, kP{}, kPol{}); else samples(kG{}, kC{}, kPol{});
       } else {
-        if (g.logic == 0) samples(kS{}, kP{}, kN{}); else samples(kS{}, kC{}, kN{});
+        if (g.logic == 0) samples(kS{}, kP{}, kPol{}); else samples(kS{}, kC{}, kPol{});
       }
     }  // chunks of active samples
     __syncthreads();
@@ -2473,6 +2470,18 @@ __global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs,
       __threadfence();
     }
   }
+}
+
+__global__ void __launch_bounds__(kBlock, 5) k_vjp(const Job* __restrict__ jobs, int njobs,
+                                                   int* __restrict__ err,
+                                                   float* __restrict__ gtape, int* work) {
+  vjp_body<false>(jobs, njobs, err, gtape, work);
+}
+
+__global__ void __launch_bounds__(kBlock, 5) k_vjp_polar(const Job* __restrict__ jobs, int njobs,
+                                                         int* __restrict__ err,
+                                                         float* __restrict__ gtape, int* work) {
+  vjp_body<true>(jobs, njobs, err, gtape, work);
 }
 
 // ---- the dense field stream --------------------------------------------------
@@ -2623,6 +2632,9 @@ cudaError_t init_kernel_attributes() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)vjp_smem(kMaxJobs));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_vjp_polar, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)vjp_smem(kMaxJobs));
   return e;
 }
 
@@ -2641,14 +2653,18 @@ int build_blocks_per_sm(int njobs, int fill_warps) {
   return r;
 }
 
-int vjp_blocks_per_sm(int njobs) {
-  static int v[kMaxJobs + 1] = {};
+int vjp_blocks_per_sm(int njobs, bool polar) {
+  static int v[2][kMaxJobs + 1] = {};
   njobs = std::min(std::max(njobs, 1), kMaxJobs);
-  if (!v[njobs]) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v[njobs], k_vjp, kBlock, vjp_smem(njobs));
-    if (v[njobs] < 1) v[njobs] = 1;
+  int& r = v[polar ? 1 : 0][njobs];
+  if (!r) {
+    if (polar)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_vjp_polar, kBlock, vjp_smem(njobs));
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_vjp, kBlock, vjp_smem(njobs));
+    if (r < 1) r = 1;
   }
-  return v[njobs];
+  return r;
 }
 
 cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s) {
@@ -2667,9 +2683,12 @@ cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStrea
 
 cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, float* gtape,
                        int gtape_blocks, cudaStream_t s) {
-  const int grid = std::min(sms * vjp_blocks_per_sm(t.njobs), gtape_blocks);
+  const int grid = std::min(sms * vjp_blocks_per_sm(t.njobs, t.polar != 0), gtape_blocks);
   if (grid < 1 || !gtape || !t.work) return cudaErrorInvalidValue;
-  k_vjp<<<grid, kBlock, vjp_smem(t.njobs), s>>>(jobs, t.njobs, err, gtape, t.work);
+  if (t.polar)
+    k_vjp_polar<<<grid, kBlock, vjp_smem(t.njobs), s>>>(jobs, t.njobs, err, gtape, t.work);
+  else
+    k_vjp<<<grid, kBlock, vjp_smem(t.njobs), s>>>(jobs, t.njobs, err, gtape, t.work);
   return cudaGetLastError();
 }
 

@@ -267,6 +267,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   t.bin_blocks = t.tiles_padded / 128;
   t.params = D->n_params;
   t.work = d_cnt + 12;
+  t.polar = g.polar;
   NACU(launch_bin(d_job, t, d_err, s));
   NACU(launch_vjp(d_job, t, d_err, sms, d_gtape, sms, s));
   NACU(launch_finalize(d_job, t, s));
