@@ -1,0 +1,39 @@
+"""Host-side pieces of bench.py, on the CPU: the grid option, the workload
+name, and the ncu traffic lookup, which must refuse counters taken on another
+grid or another kernel source, and whose committed counters belong to the
+kernel source in the tree."""
+import hashlib
+import json
+import os
+from types import SimpleNamespace
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_grid_option_and_workload_name():
+    assert bench.grid_of(SimpleNamespace(grid="")) == (600, 200, 120)
+    assert bench.grid_of(SimpleNamespace(grid="300x200x120")) == (300, 200, 120)
+    assert bench.workload_name((600, 200, 120)) == bench.WORKLOAD
+    assert "300x200x120" in bench.workload_name((300, 200, 120))
+    assert "600x200x120" not in bench.workload_name((300, 200, 120))
+
+
+def test_traffic_counters_match_the_kernel_source():
+    tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    src = open(os.path.join(ROOT, "paper_2311_05646_gb300", "csrc", "adg_kernels.cu"), "rb").read()
+    assert tr["source_sha256"] == hashlib.sha256(src).hexdigest()
+    tile = tr["tile"]
+    for k in ("build", "vjp", "dense"):
+        v = bench._traffic(k, tile)
+        assert v is not None and v > 0
+        assert bench._traffic(k, tile, (300, 200, 120)) is None  # another grid
+    assert bench._traffic("build", [64, 4, 4]) is None  # another tile
+
+
+def test_small_grid_inputs_have_the_grating_shape():
+    desc, ef, ea, w = bench.make_inputs((64, 40, 24))
+    assert tuple(desc["grid"]["n"]) == (64, 40, 24)
+    assert ef.shape == ea.shape == (3, 24, 40, 64)
+    assert ef.dtype.name == "complex64" and len(w) == 3
