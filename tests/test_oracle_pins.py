@@ -518,6 +518,52 @@ def test_polar_area_of_the_fourier_boundary(oracle_mod):
     assert abs(f.sum() - want) < 2e-3 * want
 
 
+def _table4():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table4_examples.txt")
+    out = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, *kv = line.split()
+        out[name] = {k: [float(v) for v in val.split(",")] if "," in val else float(val)
+                     for k, val in (t.split("=") for t in kv)}
+    return out
+
+
+@pytest.mark.parametrize("name", ["Rect2D", "Poly2D", "Circ2D", "Polar2D"])
+def test_table4_examples_have_their_closed_form_areas(oracle_mod, name):
+    """Table 4's printed examples, built on [-1, 1]^2 at dx = 0.005 with the
+    linear sigma at k = 1 / dx: the fills add up to each shape's area
+    (rectangle exactly; the paper's clockwise triangle, whose area is its
+    shoelace value in either winding; the circle; Polar2D with
+    R(theta) = R (1 + delta cos(alpha theta)), area pi R^2 (1 + delta^2 / 2))."""
+    O = oracle_mod
+    ex = _table4()[name]
+    h, n = 0.005, 400
+    D = I.Design((n, n, 1), (h, h, h), o=(-1.0, -1.0, 0.0), ncomp=1, off=[[0.5, 0.5, 0.0]])
+    D.param(0.0)
+    if name == "Rect2D":
+        D.box(x=(ex["x0"], ex["x1"]), y=(ex["y0"], ex["y1"]))
+        want, tol = (ex["x1"] - ex["x0"]) * (ex["y1"] - ex["y0"]), 1e-12
+    elif name == "Poly2D":
+        verts = list(zip(ex["x"], ex["y"]))
+        D.polygon(verts, sigma="linear", kr=1.0)
+        want, tol = G.area(verts), 2e-4
+        signed = 0.5 * sum(x0 * y1 - x1 * y0 for (x0, y0), (x1, y1) in zip(verts, verts[1:] + verts[:1]))
+        assert signed < 0  # the printed example winds clockwise
+    elif name == "Circ2D":
+        D.circle(ex["x0"], ex["y0"], ex["R"], sigma="linear", kr=1.0)
+        want, tol = np.pi * ex["R"] ** 2, 2e-4
+    else:
+        R, dl, a = ex["R"], ex["delta"], int(ex["alpha"])
+        coef = [(0.0, 0.0)] * (a - 1) + [(R * dl, 0.0)]
+        D.polar(ex["x0"], ex["y0"], R, coef, sigma="linear", kr=1.0)
+        want, tol = np.pi * R * R * (1 + 0.5 * dl * dl), 2e-4
+    got = O.fill(D.to_desc()).sum() * h * h
+    assert abs(got - want) <= tol * want, (got, want)
+
+
 # ------------------------------------- non-binary union (App. B, Alg. 1) ----
 @pytest.mark.parametrize("logic", ["product", "clamp"])
 @pytest.mark.parametrize("dims", ["2d", "3d"])
