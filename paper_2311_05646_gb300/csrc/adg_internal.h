@@ -67,7 +67,7 @@ struct GridDev {
   int logic;
   int nchain;
   int nprims;
-  int polar;  // some primitive is Polar2D (the VJP then takes its polar-aware path)
+  int polar;  // some primitive is Polar2D (its gradient runs on k_vjp_polar)
 };
 
 // One primitive after the parameter map, in cell units of each axis:
