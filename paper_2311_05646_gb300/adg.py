@@ -4,6 +4,18 @@ Argument marshalling only: every step of the method runs inside libadg's
 CUDA kernels.  PyTorch supplies device memory and streams.  If libadg.so is
 missing this module raises at import of the first call -- there is no CPU
 fallback.
+
+The calls, by the passage of arXiv 2311.05646 they follow:
+
+* ``adg_build_eps``                       -- Eq. eps (step 2 of Sec. 2)
+* ``adg_grad`` / ``adg_grad_real``        -- Eq. 1, eps term, by Eqs. AD / jaceps
+* ``adg_grad_dense``                      -- the same, plus d/d eps_bg and d/d eps_fg (Sec. 5.1)
+* ``adg_grad_eh``                         -- both terms of Eq. 1 (Eqs. mu, jacmu)
+* ``adg_levels_eps`` / ``adg_levels_grad``   -- non-binary union (App. B, Alg. 1)
+* ``adg_topo_eps`` / ``adg_topo_grad``       -- topology special case (Sec. 3.1)
+* ``adg_grad_fd``                         -- the finite-difference baseline (Sec. 3)
+* ``adg_mesh_fill`` / ``adg_mesh_grad_fd``   -- Prop. 2's exact mesher and its FD gradient
+* ``adg_batch_submit`` / ``poll`` / ``wait`` -- many designs as one job table
 """
 from __future__ import annotations
 
