@@ -320,6 +320,47 @@ def test_p5_half_half_union(oracle_mod):
     assert abs(out["product"] - 0.75) < 1e-15
 
 
+def _lattice_pairs():
+    # values on the 1/16 lattice: products and sums of them are exact in FP64
+    return [(a / 16.0, b / 16.0) for a in (1, 3, 6, 11, 13, 15) for b in (2, 5, 8, 9, 14)]
+
+
+@pytest.mark.parametrize("logic", ["product", "clamp"])
+def test_p5_logic_on_fractional_inputs(oracle_mod, logic):
+    """Away from {0, 1} the two families differ, and each must take its own
+    closed form (App. B.2 for the product family; Eqs. union / intersection
+    for the clamped one; difference = intersection(a, 1 - b)).  Box A covers
+    the window [0, 1] of the single sample by a fraction a along x, box B by b
+    along y, box C by c along x again: each leaf value is exact, so so is the
+    expected result.  The three-input forms fix the n-ary definitions too."""
+    O = oracle_mod
+
+    def run(prog, a, b, c=0.5):
+        D = _grid2d(1, 1, 1.0, logic=logic)
+        A = D.box(x=(-1.0, a))
+        B = D.box(y=(1.0 - b, 2.0))
+        C = D.box(x=(1.0 - c, 3.0))
+        D.set_program(prog(A, B, C))
+        return O.fill(D.to_desc())[0, 0, 0, 0]
+
+    for a, b in _lattice_pairs():
+        c = (a + b) / 2.0 if (a + b) < 1.0 else 0.5
+        fi = run(lambda A, B, C: ("intersect", A, B), a, b)
+        fd = run(lambda A, B, C: ("diff", A, B), a, b)
+        fu = run(lambda A, B, C: ("union", A, B), a, b)
+        fi3 = run(lambda A, B, C: ("intersect", A, B, C), a, b, c)
+        fu3 = run(lambda A, B, C: ("union", A, B, C), a, b, c)
+        if logic == "product":
+            want = (a * b, a * (1.0 - b), a + b - a * b, a * b * c,
+                    1.0 - (1.0 - a) * (1.0 - b) * (1.0 - c))
+        else:
+            want = (max(0.0, a + b - 1.0), max(0.0, a - b), min(1.0, a + b),
+                    max(2.0, a + b + c) - 2.0, min(1.0, a + b + c))
+        got = (fi, fd, fu, fi3, fu3)
+        for g_, w_ in zip(got, want):
+            assert abs(g_ - w_) <= 1e-15, (logic, a, b, c, got, want)
+
+
 # ---------------------------------------------------------------- P6 --------
 KINKS = {0: [-0.5, 0.5], 1: [], 2: [-1 / math.sqrt(2), 0.0, 1 / math.sqrt(2)],
          3: [-math.pi / 2, math.pi / 2], 4: []}
@@ -357,6 +398,40 @@ def test_p6_sigma_saturation_points(oracle_mod):
     assert abs(O.sigma(1, 0.0)[1] - 0.25) < 1e-15
 
 
+def test_p6_erf_sigma_is_the_table_form(oracle_mod):
+    """Table 'Nonlinear function definitions' prints erf(k, x) = (1 + Erf(k x))/2
+    with Erf the error function (not the normal CDF (1 + Erf(u / sqrt 2))/2).
+    Values against the standard library's erf; slope 1/sqrt(pi) at 0 (the
+    error function's derivative 2/sqrt(pi) e^(-u^2), halved) and against
+    central differences of math.erf elsewhere."""
+    O = oracle_mod
+    assert abs(O.sigma(4, 1.0)[0] - 0.5 * (1.0 + math.erf(1.0))) < 1e-15
+    assert abs(O.sigma(4, 0.0)[1] - 1.0 / math.sqrt(math.pi)) < 1e-15
+    hh = 1e-5
+    for u in np.linspace(-3.0, 3.0, 61):
+        u = float(u)
+        assert abs(O.sigma(4, u)[0] - 0.5 * (1.0 + math.erf(u))) < 2e-16
+        fd = 0.5 * (math.erf(u + hh) - math.erf(u - hh)) / (2 * hh)
+        assert abs(O.sigma(4, u)[1] - fd) < 1e-9
+
+
+def test_p6_erf_circle_uses_the_grid_scale(oracle_mod):
+    """sigma_k(x) = sigma(k x) with k = kr / dx (Sec. 4): an erf circle of
+    radius R at kr = 2 on a dx = 0.5 grid is (1 + Erf(4 (R - r)))/2 at every
+    sample, r the sample's distance from the centre."""
+    O = oracle_mod
+    h, R, cx, cy = 0.5, 2.3, 3.1, 2.7
+    D = _grid2d(13, 11, h)
+    D.circle(cx, cy, R, sigma="erf", kr=2.0)
+    desc = D.to_desc()
+    f = O.fill(desc)[0, 0]
+    xs, ys = _centres(desc)
+    for j, y in enumerate(ys):
+        for i, x in enumerate(xs):
+            r = math.hypot(x - cx, y - cy)
+            assert abs(f[j, i] - 0.5 * (1.0 + math.erf(4.0 * (R - r)))) < 1e-15
+
+
 # ---------------------------------------------------------------- P7 --------
 def test_p7_single_edge_gradient_closed_form(oracle_mod):
     """For one exact-overlap edge at x = a, dL/da = -(deps/dx) * sum over the
@@ -375,6 +450,83 @@ def test_p7_single_edge_gradient_closed_form(oracle_mod):
     z = (w * ea[0, 0, :, i].astype(np.complex128) * ef[0, 0, :, i].astype(np.complex128)).real
     expect = -(desc["eps_fg"] - desc["eps_bg"]) / h * z.sum()
     assert abs(g[0] - expect) <= 1e-12 * abs(expect)
+
+
+# ------------------------------------------------- GeneralCartesian2D ------
+def _graph_case(above, rng):
+    """A linear-sigma graph boundary with k = 1/dy on a dx != dy grid: knots
+    at irregular, off-lattice x (some columns lie beyond the end knots), knot
+    heights inside the grid with at least two cells of margin."""
+    nx, ny, dx, dy = 40, 30, 1.0, 0.5
+    D = I.Design((nx, ny, 1), (dx, dy, 1.0), ncomp=1, eps_bg=0.0, eps_fg=1.0)
+    M = 7
+    X = np.sort(rng.uniform(4.0, 36.0, size=M)) + 0.137
+    Y = rng.uniform(1.5, 13.5, size=M)
+    ids = [D.param(float(v)) for v in Y]
+    D.graph([float(v) for v in X], [P(i) for i in ids], above=above, sigma="linear", kr=1.0)
+    return D.to_desc(), X, Y, dy, ny
+
+
+@pytest.mark.parametrize("above", [False, True])
+def test_graph_column_sums_follow_the_interpolant(oracle_mod, above):
+    """GeneralCartesian2D (Table 4; Eq. taper_eps of Sec. 6.2) is
+    sigma_k(+-(f(x) - y)), f the piecewise-linear curve through the knots,
+    constant beyond the end knots.  With the linear sigma and k = 1/dy each
+    cell holds exactly the covered fraction of its y window (Eq. linear), so
+    the fill of a column sums to (f(x_i) - y_lo)/dy, or (y_hi - f(x_i))/dy for
+    the region above, and each cell is the covered fraction of its y window.
+    f(x_i) comes from numpy's interp, an independent implementation of the
+    same curve.  The derivatives of that column sum
+    w.r.t. the knot heights are numpy's hat weights over dy (interp of a unit
+    vector), taken from the oracle's reverse sweep with a one-column cotangent."""
+    O = oracle_mod
+    rng = np.random.default_rng(17 + int(above))
+    desc, X, Y, dy, ny = _graph_case(above, rng)
+    f = O.fill(desc)[0, 0]
+    xs, _ = _centres(desc)
+    fx = np.interp(xs, X, Y)
+    want = (ny * dy - fx) / dy if above else fx / dy
+    assert np.abs(f.sum(axis=0) - want).max() <= 1e-12
+    # cell by cell: the covered fraction of each y window [j dy, (j + 1) dy]
+    lo = np.arange(ny)[:, None] * dy
+    cover = np.clip((fx[None, :] - lo) / dy, 0.0, 1.0)
+    assert np.abs(f - ((1.0 - cover) if above else cover)).max() <= 1e-12
+    nx = len(xs)
+    sgn = -1.0 if above else 1.0
+    for i in range(0, nx, 3):
+        G = np.zeros((1, 1, ny, nx), dtype=np.float32)
+        G[0, 0, :, i] = 1.0
+        g = O.grad_real(desc, G)
+        hat = np.array([np.interp(xs[i], X, np.eye(len(X))[j]) for j in range(len(X))])
+        assert np.abs(g - sgn * hat / dy).max() <= 1e-12, (i, g, hat)
+
+
+def test_graph_knot_position_derivatives_follow_the_interpolant(oracle_mod):
+    """The same column sums as functions of the knots' x positions: their
+    derivatives are central differences of numpy's interp (exact for a curve
+    that is linear between knots, with every sample away from a knot)."""
+    O = oracle_mod
+    rng = np.random.default_rng(23)
+    nx, ny, dx, dy = 40, 30, 1.0, 0.5
+    D = I.Design((nx, ny, 1), (dx, dy, 1.0), ncomp=1, eps_bg=0.0, eps_fg=1.0)
+    M = 6
+    X = np.sort(rng.uniform(4.0, 36.0, size=M)) + 0.137
+    Y = rng.uniform(1.5, 13.5, size=M)
+    idx = [D.param(float(v)) for v in X]
+    D.graph([P(i) for i in idx], [float(v) for v in Y], sigma="linear", kr=1.0)
+    desc = D.to_desc()
+    xs, _ = _centres(desc)
+    hh = 1e-6
+    for i in range(0, nx, 3):
+        G = np.zeros((1, 1, ny, nx), dtype=np.float32)
+        G[0, 0, :, i] = 1.0
+        g = O.grad_real(desc, G)
+        for j in range(M):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[j] += hh
+            Xm[j] -= hh
+            fd = (np.interp(xs[i], Xp, Y) - np.interp(xs[i], Xm, Y)) / (2 * hh) / dy
+            assert abs(g[j] - fd) <= 1e-6 * max(1.0, abs(fd)), (i, j, g[j], fd)
 
 
 # ---------------------------------------------------------------- P8 --------
