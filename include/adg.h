@@ -24,8 +24,8 @@
  *     64 primitives may have an edge band crossing it, its folded logic
  *     program at most 120 ops (fold stack depth 32), with at most 384
  *     (primitive, parameter) accumulators, and its staged primitives plus
- *     accumulators must fit the VJP's 24 KB tile pool; a smaller tile shape
- *     lowers all of these.
+ *     accumulators must fit the VJP's 27.5 KB tile pool (7040 floats); a
+ *     smaller tile shape lowers all of these.
  *   - Layout of every per-cell array: [ncomp][nz][ny][nx], x fastest, fp32
  *     (fields: complex64 = interleaved (re, im) fp32 pairs).
  */
