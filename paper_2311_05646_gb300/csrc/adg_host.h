@@ -8,7 +8,6 @@
 #include <string.h>
 
 #include <algorithm>
-#include <vector>
 
 #include "../../include/adg.h"
 #include "adg_internal.h"
@@ -374,7 +373,7 @@ inline adg_status prepare_prims(const GridDev& g, const double d[3], const doubl
       const double cx = cellc(Q[0], 0), cy = cellc(Q[1], 1);
       anchor(cx, R.ai[0], R.af[0]);
       anchor(cy, R.ai[1], R.af[1]);
-      std::vector<double> A(1 + 2 * N);
+      double A[1 + 2 * kMaxPolarHarm];  // N <= kMaxPolarHarm (validated)
       A[0] = Q[2] / d[0];
       double amp = 0.0;
       for (int n = 1; n <= N; ++n) {

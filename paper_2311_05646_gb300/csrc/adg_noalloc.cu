@@ -190,6 +190,14 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   }
   unsigned char* base = static_cast<unsigned char*>(g_sym[dev]);
   cudaStream_t s = (cudaStream_t)stream;
+  // From the first enqueue on, every return waits for this call's stream work
+  // before the lock is released (the guard is destroyed first): a failed
+  // enqueue must not leave kernels reading the shared array while the next
+  // call overwrites it.
+  struct DrainOnExit {
+    cudaStream_t s;
+    ~DrainOnExit() { cudaStreamSynchronize(s); }
+  } drain{s};
   int* d_err = reinterpret_cast<int*>(base + o_err);
   Job* d_job = reinterpret_cast<Job*>(base + o_job);
   int* d_cnt = reinterpret_cast<int*>(base + o_cnt);

@@ -49,3 +49,37 @@ def test_noalloc_gradient_matches_adg_grad_on_two_calls():
         adg.adg_grad_noalloc(big, big["params"], ef_big, ef_big, 1.0, g_big, tile=(32, 4, 1))
     assert e.value.status == adg.ADG_EINVAL
     assert "static scratch" in str(e.value)
+
+
+@pytest.mark.parametrize("case", ["polar", "mixed"])
+def test_noalloc_gradient_of_polar_and_polygon_designs(case, oracle_mod):
+    """Designs whose primitive records carry auxiliary tables (Polar2D Fourier
+    coefficients; polygon edges, circles and boxes) through the no-allocation
+    entry point: against the FP64 oracle at the stated tolerance and against
+    adg_grad, on two calls in a row."""
+    import torch
+
+    from paper_2311_05646_gb300 import adg
+
+    ctx = adg.Context(0)
+    if case == "polar":
+        desc = I.psgc_lattice(n=(64, 56, 12), rows=2, cols=3, harmonics=6, centres=True)
+    else:
+        desc = I.random_design(44, n=(70, 52, 14), nprims=18)
+    design = adg.Design(ctx, desc)
+    ef, ea = I.plane_wave_field(desc, 41), I.plane_wave_field(desc, 42)
+    w = I.seeded_w(desc["grid"]["ncomp"], 43)
+    efd, ead = torch.from_numpy(ef).cuda(), torch.from_numpy(ea).cuda()
+    p1 = desc["params"].copy()
+    p2 = p1 + np.random.default_rng(6).uniform(-3.0, 3.0, p1.size)
+    for p in (p1, p2):
+        g_ref = torch.zeros(design.n_params, dtype=torch.float32, device="cuda")
+        adg.adg_grad(design, p, efd, ead, w, g_ref)
+        adg.adg_sync(ctx)
+        g_na = torch.full((design.n_params,), float("nan"), dtype=torch.float32, device="cuda")
+        adg.adg_grad_noalloc(desc, p, efd, ead, w, g_na)
+        a = g_na.cpu().numpy().astype(np.float64)
+        ok, err, bound = H.grad_ok(a, g_ref.cpu().numpy().astype(np.float64))
+        assert ok, ("vs adg_grad", err, bound)
+        ok, err, bound = H.grad_ok(a, oracle_mod.grad(desc, ef, ea, w, params=p))
+        assert ok, ("vs oracle", err, bound)
