@@ -419,11 +419,25 @@ adg_status adg_profile_read(adg_ctx *ctx, adg_profile_data *out, int32_t reset);
  *   - Calls share the array and it keeps the last call's contents; each call
  *     clears what must start at zero.  Calls that overlap on the GPU race on
  *     it: serialise them.  The call returns after its work on `stream` has
- *     completed and reports device-side checks as ADG_EDEVICE. */
+ *     completed -- also when it fails after enqueueing some of it -- and
+ *     reports device-side checks as ADG_EDEVICE.  Error messages go to a
+ *     fixed per-thread buffer (adg_last_error), so failures allocate nothing
+ *     either. */
 adg_status adg_grad_noalloc(const adg_design_desc *desc, const adg_tile_opts *tiles,
                             const double *h_params, const float *const d_efwd[3],
                             const float *const d_eadj[3], const float *w, float *d_grad,
                             void *stream);
+
+/* For tests of the error paths (host-side fault injection; the paper has no
+ * counterpart).  Every device and pinned-host allocation libadg makes goes
+ * through one counter: with fail_after = n >= 0, the next n allocations
+ * succeed and the one after fails as if memory were exhausted (the call that
+ * made it returns ADG_ENOMEM), after which injection is off again;
+ * fail_after = -1 switches injection off, -2 leaves it as it is.  *live
+ * (nullable) receives the number of allocations libadg holds now, so that a
+ * test can check that a failed call released what it had taken.
+ * Process-wide; not for production use. */
+adg_status adg_debug_alloc(int32_t fail_after, int64_t *live);
 
 /* Thread-local description of the last error (never NULL). */
 const char *adg_last_error(void);

@@ -489,6 +489,18 @@ def adg_grad_noalloc(desc: dict, params, efwd, eadj, w, grad, tile=None, stream=
              ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad), _stream_ptr(stream)))
 
 
+def adg_debug_alloc(fail_after: int = -2) -> int:
+    """Host-side fault injection for tests: let `fail_after` more of libadg's
+    allocations succeed and fail the next (-1: off, -2: unchanged).  Returns
+    the number of allocations libadg holds now."""
+    live = ctypes.c_int64(0)
+    L = lib()
+    L.adg_debug_alloc.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+    L.adg_debug_alloc.restype = ctypes.c_int
+    _check(L.adg_debug_alloc(int(fail_after), ctypes.byref(live)))
+    return int(live.value)
+
+
 BATCH_BUILD, BATCH_GRAD, BATCH_GRAD_REAL = 1, 2, 4
 BATCH_GRAPH = 1
 

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <atomic>
 #include <string>
 #include <thread>
 #include <vector>
@@ -28,15 +29,15 @@ using namespace adg;
 
 namespace {
 
-thread_local std::string g_err = "no error";
+// The last error message of this thread: a fixed buffer, so that reporting
+// an error allocates nothing (adg_grad_noalloc relies on it).
+thread_local char g_err[512] = "no error";
 
 adg_status fail(adg_status st, const char* fmt, ...) {
-  char buf[512];
   va_list ap;
   va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
   va_end(ap);
-  g_err = buf;
   return st;
 }
 
@@ -48,11 +49,60 @@ adg_status fail(adg_status st, const char* fmt, ...) {
                   #call, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
   } while (0)
 
+// ---- allocation accounting and host-side fault injection ----------------------
+// Every device and pinned-host allocation of the library goes through these,
+// so that a test can make one fail as if memory were exhausted
+// (adg_debug_alloc) and count what the library still holds afterwards.
+std::atomic<int> g_fail_after{-1};  // allocations to let through before one fails; -1: none
+std::atomic<long long> g_live{0};   // live allocations made by the library
+
+bool injected_failure() {
+  int b = g_fail_after.load();
+  while (b >= 0)
+    if (g_fail_after.compare_exchange_weak(b, b - 1)) return b == 0;
+  return false;
+}
+template <class T>
+cudaError_t lib_malloc(T** p, size_t bytes) {
+  if (injected_failure()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+  const cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e == cudaSuccess) ++g_live;
+  return e;
+}
+template <class T>
+cudaError_t lib_malloc_async(T** p, size_t bytes, cudaStream_t s) {
+  if (injected_failure()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+  const cudaError_t e = cudaMallocAsync((void**)p, bytes, s);
+  if (e == cudaSuccess) ++g_live;
+  return e;
+}
+cudaError_t lib_malloc_host(void** p, size_t bytes) {
+  if (injected_failure()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+  const cudaError_t e = cudaMallocHost(p, bytes);
+  if (e == cudaSuccess) ++g_live;
+  return e;
+}
+cudaError_t lib_free(void* p) {
+  if (!p) return cudaSuccess;
+  --g_live;
+  return cudaFree(p);
+}
+cudaError_t lib_free_async(void* p, cudaStream_t s) {
+  if (!p) return cudaSuccess;
+  --g_live;
+  return cudaFreeAsync(p, s);
+}
+cudaError_t lib_free_host(void* p) {
+  if (!p) return cudaSuccess;
+  --g_live;
+  return cudaFreeHost(p);
+}
+
 template <class T>
 cudaError_t upload(T** dptr, const std::vector<T>& h) {
   *dptr = nullptr;
   size_t n = std::max<size_t>(h.size(), 1);
-  cudaError_t e = cudaMalloc((void**)dptr, n * sizeof(T));
+  cudaError_t e = lib_malloc((void**)dptr, n * sizeof(T));
   if (e != cudaSuccess) return e;
   if (!h.empty()) e = cudaMemcpy(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
   return e;
@@ -184,7 +234,18 @@ struct adg_design {
   size_t part_total = 0;
   std::vector<double> last_params;
   bool bins_valid = false;
+  // a call failed between flipping the counter set and enqueueing its binning:
+  // both sets are cleared before the next binning
+  bool counters_dirty = false;
 };
+
+// After a call that had prepared a new binning failed before enqueueing all
+// of its work: the bins may not have been written, and the counter set the
+// design now points at may hold an older binning's counts.
+void invalidate_bins(adg_design* d) {
+  d->bins_valid = false;
+  d->counters_dirty = true;
+}
 
 // ------------------------------------------------------------------ context -
 extern "C" adg_status adg_ctx_create(int32_t device, adg_ctx** out) {
@@ -200,13 +261,13 @@ extern "C" adg_status adg_ctx_create(int32_t device, adg_ctx** out) {
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = init_kernel_attributes();
   c->gtape_blocks = c->sms * std::max(vjp_blocks_per_sm(1, false), vjp_blocks_per_sm(1, true));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_err, sizeof(int));
+  if (e == cudaSuccess) e = lib_malloc((void**)&c->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e == cudaSuccess)
-    e = cudaMalloc((void**)&c->d_gtape, sizeof(float) * kTapeBlockFloats * c->gtape_blocks);
+    e = lib_malloc((void**)&c->d_gtape, sizeof(float) * kTapeBlockFloats * c->gtape_blocks);
   if (e != cudaSuccess) {
-    cudaFree(c->d_err);
-    cudaFree(c->d_gtape);
+    lib_free(c->d_err);
+    lib_free(c->d_gtape);
     delete c;
     return fail(ADG_ECUDA, "adg_ctx_create: %s", cudaGetErrorString(e));
   }
@@ -222,15 +283,15 @@ extern "C" adg_status adg_ctx_destroy(adg_ctx* ctx) {
   for (auto& a : ctx->arenas) {
     if (a.exec) cudaGraphExecDestroy(a.exec);
     if (a.done) cudaEventDestroy(a.done);
-    cudaFree(a.d);
-    cudaFreeHost(a.h);
-    cudaFree(a.d_work);
+    lib_free(a.d);
+    lib_free_host(a.h);
+    lib_free(a.d_work);
   }
   for (auto& t : ctx->tickets) cudaEventDestroy(t.ev);
   if (ctx->capture) cudaStreamDestroy(ctx->capture);
-  cudaFree(ctx->d_err);
-  cudaFree(ctx->d_gtape);
-  cudaFree(ctx->d_mesh);
+  lib_free(ctx->d_err);
+  lib_free(ctx->d_gtape);
+  lib_free(ctx->d_mesh);
   delete ctx;
   return ADG_OK;
 }
@@ -239,29 +300,29 @@ extern "C" adg_status adg_ctx_destroy(adg_ctx* ctx) {
 namespace {
 
 void free_design(adg_design* d) {
-  cudaFree(d->d_chain);
-  cudaFree(d->d_act);
-  cudaFree(d->d_actc);
-  cudaFree(d->d_ref_off);
-  cudaFree(d->d_ref_prim);
-  cudaFree(d->d_ref_qa);
-  cudaFree(d->d_ref_coeff);
-  cudaFree(d->d_prims);
-  cudaFree(d->d_auxd);
-  cudaFree(d->d_auxf);
-  cudaFree(d->d_progs);
-  cudaFree(d->d_tclass);
-  cudaFree(d->d_list);
-  cudaFree(d->d_counters);
-  cudaFree(d->d_partial);
-  cudaFree(d->d_job);
-  cudaFree(d->d_dense_part);
-  cudaFree(d->d_dense_ctr);
-  cudaFree(d->d_fd_buf);
-  cudaFree(d->d_fd_part);
-  cudaFree(d->d_fd_acc);
-  cudaFree(d->d_row);
-  cudaFree(d->d_lv_buf);
+  lib_free(d->d_chain);
+  lib_free(d->d_act);
+  lib_free(d->d_actc);
+  lib_free(d->d_ref_off);
+  lib_free(d->d_ref_prim);
+  lib_free(d->d_ref_qa);
+  lib_free(d->d_ref_coeff);
+  lib_free(d->d_prims);
+  lib_free(d->d_auxd);
+  lib_free(d->d_auxf);
+  lib_free(d->d_progs);
+  lib_free(d->d_tclass);
+  lib_free(d->d_list);
+  lib_free(d->d_counters);
+  lib_free(d->d_partial);
+  lib_free(d->d_job);
+  lib_free(d->d_dense_part);
+  lib_free(d->d_dense_ctr);
+  lib_free(d->d_fd_buf);
+  lib_free(d->d_fd_part);
+  lib_free(d->d_fd_acc);
+  lib_free(d->d_row);
+  lib_free(d->d_lv_buf);
   delete d;
 }
 
@@ -358,12 +419,12 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   if (e == cudaSuccess) e = upload(&d->d_prims, d->h_prims);
   if (e == cudaSuccess) e = upload(&d->d_auxd, d->h_auxd);
   if (e == cudaSuccess) e = upload(&d->d_auxf, d->h_auxf);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_progs, sizeof(TileProg) * (size_t)d->g.T);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_tclass, (size_t)d->g.T);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_list, sizeof(int) * (size_t)d->g.T);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_counters, sizeof(int) * 16);
+  if (e == cudaSuccess) e = lib_malloc((void**)&d->d_progs, sizeof(TileProg) * (size_t)d->g.T);
+  if (e == cudaSuccess) e = lib_malloc((void**)&d->d_tclass, (size_t)d->g.T);
+  if (e == cudaSuccess) e = lib_malloc((void**)&d->d_list, sizeof(int) * (size_t)d->g.T);
+  if (e == cudaSuccess) e = lib_malloc((void**)&d->d_counters, sizeof(int) * 16);
   if (e == cudaSuccess) e = cudaMemset(d->d_counters, 0, sizeof(int) * 16);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d->d_job, sizeof(Job));
+  if (e == cudaSuccess) e = lib_malloc((void**)&d->d_job, sizeof(Job));
   if (e != cudaSuccess) {
     free_design(d);
     return fail(e == cudaErrorMemoryAllocation ? ADG_ENOMEM : ADG_ECUDA, "adg_design_create: %s",
@@ -408,6 +469,10 @@ adg_status ensure_records(adg_design* d, const double* h_params, cudaStream_t s,
   d->bins_valid = false;
   adg_status st = prepare_prims(d, h_params);
   if (st != ADG_OK) return st;
+  if (d->counters_dirty) {
+    CU(cudaMemsetAsync(d->d_counters, 0, sizeof(int) * 8, s));  // both counter sets
+    d->counters_dirty = false;
+  }
   CU(cudaMemcpyAsync(d->d_prims, d->h_prims.data(), sizeof(PrimRec) * d->n_prims,
                      cudaMemcpyHostToDevice, s));
   if (d->st.auxd_n)
@@ -428,10 +493,10 @@ adg_status ensure_records(adg_design* d, const double* h_params, cudaStream_t s,
 // stopped between the two leaves it dirty; the next call clears it.
 adg_status ensure_partials(adg_design* d, cudaStream_t s) {
   if (d->part_total > d->partial_cap) {
-    if (d->d_partial) CU(cudaFreeAsync(d->d_partial, s));
+    if (d->d_partial) CU(lib_free_async(d->d_partial, s));
     d->d_partial = nullptr;
     const size_t cap = d->part_total + d->part_total / 2 + 1024;
-    CU(cudaMallocAsync((void**)&d->d_partial, cap * sizeof(float), s));
+    CU(lib_malloc_async((void**)&d->d_partial, cap * sizeof(float), s));
     d->partial_cap = cap;
     d->partial_dirty = true;
   }
@@ -490,11 +555,22 @@ adg_status run_jobs(adg_ctx* ctx, const Job* d_jobs, const JobTotals& t, bool an
   return ADG_OK;
 }
 
+adg_status run_single_enqueue(adg_ctx* ctx, adg_design* d, bool rebin, float* d_fill,
+                              float* d_eps, const VjpArgs* va, float* d_grad, cudaStream_t s);
+
 adg_status run_single(adg_ctx* ctx, adg_design* d, const double* h_params, float* d_fill,
                       float* d_eps, const VjpArgs* va, float* d_grad, cudaStream_t s) {
   bool rebin = false;
   adg_status st = ensure_records(d, h_params, s, &rebin);
   if (st != ADG_OK) return st;
+  st = run_single_enqueue(ctx, d, rebin, d_fill, d_eps, va, d_grad, s);
+  if (st != ADG_OK && rebin) invalidate_bins(d);
+  return st;
+}
+
+adg_status run_single_enqueue(adg_ctx* ctx, adg_design* d, bool rebin, float* d_fill,
+                              float* d_eps, const VjpArgs* va, float* d_grad, cudaStream_t s) {
+  adg_status st = ADG_OK;
   const bool grad = va != nullptr;
   if (grad) {
     st = ensure_partials(d, s);
@@ -587,8 +663,8 @@ extern "C" adg_status adg_grad_dense(adg_ctx* ctx, adg_design* d, const double* 
   da.gmat = d_gmat;
   CU(cudaSetDevice(ctx->device));
   if (!d->d_dense_part) {
-    CU(cudaMalloc((void**)&d->d_dense_part, sizeof(double2) * (size_t)da.C * da.chunks_per_c));
-    CU(cudaMalloc((void**)&d->d_dense_ctr, sizeof(int)));
+    CU(lib_malloc((void**)&d->d_dense_part, sizeof(double2) * (size_t)da.C * da.chunks_per_c));
+    CU(lib_malloc((void**)&d->d_dense_ctr, sizeof(int)));
   }
   da.part = d->d_dense_part;
   da.ctr = d->d_dense_ctr;
@@ -698,7 +774,7 @@ extern "C" adg_status adg_grad_eh(adg_ctx* ctx, adg_design* d_eps, adg_design* d
   }
   CU(cudaSetDevice(ctx->device));
   const int n = d_eps->n_params;
-  if (!d_mu->d_row && n > 0) CU(cudaMalloc((void**)&d_mu->d_row, sizeof(float) * n));
+  if (!d_mu->d_row && n > 0) CU(lib_malloc((void**)&d_mu->d_row, sizeof(float) * n));
   cudaStream_t s = (cudaStream_t)stream;
   adg_status st = run_single(ctx, d_eps, h_params, nullptr, nullptr, &ve, d_grad, s);  // eps term
   if (st != ADG_OK) return st;
@@ -751,11 +827,11 @@ adg_status levels_setup(adg_ctx* ctx, adg_design* const* sets, int K, const doub
   if (d0->lv_cap < need) {
     if (d0->d_lv_buf) {
       CU(cudaDeviceSynchronize());
-      CU(cudaFree(d0->d_lv_buf));
+      CU(lib_free(d0->d_lv_buf));
       d0->d_lv_buf = nullptr;
       d0->lv_cap = 0;
     }
-    CU(cudaMalloc((void**)&d0->d_lv_buf, sizeof(float) * need));
+    CU(lib_malloc((void**)&d0->d_lv_buf, sizeof(float) * need));
     d0->lv_cap = need;
   }
   a.fill = d0->d_lv_buf;
@@ -805,7 +881,7 @@ extern "C" adg_status adg_levels_grad(adg_ctx* ctx, adg_design* const* sets, int
     a.w[c] = make_float2(w[2 * c], w[2 * c + 1]);
   }
   for (int k = 1; k < K; ++k)
-    if (!sets[k]->d_row && n > 0) CU(cudaMalloc((void**)&sets[k]->d_row, sizeof(float) * n));
+    if (!sets[k]->d_row && n > 0) CU(lib_malloc((void**)&sets[k]->d_row, sizeof(float) * n));
   cudaStream_t s = (cudaStream_t)stream;
   float* fills = sets[0]->d_lv_buf;
   float* cots = fills + (size_t)K * a.stride;
@@ -924,11 +1000,11 @@ adg_status mesh_reserve(adg_ctx* ctx, size_t need) {
   if (ctx->mesh_cap >= need) return ADG_OK;
   if (ctx->d_mesh) {
     CU(cudaDeviceSynchronize());
-    CU(cudaFree(ctx->d_mesh));
+    CU(lib_free(ctx->d_mesh));
     ctx->d_mesh = nullptr;
     ctx->mesh_cap = 0;
   }
-  CU(cudaMalloc(&ctx->d_mesh, need));
+  CU(lib_malloc(&ctx->d_mesh, need));
   ctx->mesh_cap = need;
   return ADG_OK;
 }
@@ -1149,9 +1225,9 @@ extern "C" adg_status adg_grad_fd(adg_ctx* ctx, adg_design* d, const double* h_p
   const int n = d->n_params;
   CU(cudaSetDevice(ctx->device));
   if (!d->d_fd_buf) {
-    CU(cudaMalloc((void**)&d->d_fd_buf, sizeof(float) * (size_t)ns * 4));
-    CU(cudaMalloc((void**)&d->d_fd_part, sizeof(double) * (size_t)std::max(fd_chunks(ns), 1)));
-    CU(cudaMalloc((void**)&d->d_fd_acc, sizeof(double) * (size_t)std::max(n, 1)));
+    CU(lib_malloc((void**)&d->d_fd_buf, sizeof(float) * (size_t)ns * 4));
+    CU(lib_malloc((void**)&d->d_fd_part, sizeof(double) * (size_t)std::max(fd_chunks(ns), 1)));
+    CU(lib_malloc((void**)&d->d_fd_acc, sizeof(double) * (size_t)std::max(n, 1)));
   }
   float* z = d->d_fd_buf;
   float* fa = z + ns;
@@ -1219,12 +1295,28 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   if (A.used) CU(cudaEventSynchronize(A.done));  // the batch two back released this arena
   // parameter maps (host, FP64) and sizes of the packed upload
   size_t nprim = 0, nauxd = 0, nauxf = 0;
+  // until the launches are enqueued, a failure leaves every flipped design to
+  // be re-binned from cleared counters
+  struct Flipped {
+    const adg_batch_item* items;
+    int n = 0;
+    bool done = false;
+    ~Flipped() {
+      if (!done)
+        for (int k = 0; k < n; ++k) invalidate_bins(items[k].design);
+    }
+  } flipped{items};
   for (int i = 0; i < n; ++i) {
     adg_design* d = items[i].design;
     adg_status st = prepare_prims(d, items[i].h_params);
     if (st != ADG_OK) return st;
+    if (d->counters_dirty) {
+      CU(cudaMemsetAsync(d->d_counters, 0, sizeof(int) * 8, s));  // both counter sets
+      d->counters_dirty = false;
+    }
     d->bins_valid = false;  // the batch re-bins this design with its own records
     d->gen ^= 1;            // into the other counter set (cleared by the last binning)
+    flipped.n = i + 1;
     if (items[i].ops & (ADG_BATCH_GRAD | ADG_BATCH_GRAD_REAL)) {
       st = ensure_partials(d, s);
       if (st != ADG_OK) return st;
@@ -1240,19 +1332,19 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   const size_t bytes = al256(o_auxf + sizeof(float) * nauxf);
   if (bytes > A.cap) {
     if (A.exec) { cudaGraphExecDestroy(A.exec); A.exec = nullptr; A.sig = 0; }
-    cudaFree(A.d);
-    cudaFreeHost(A.h);
+    lib_free(A.d);
+    lib_free_host(A.h);
     A.d = nullptr;
     A.h = nullptr;
     A.cap = 0;
     const size_t cap = bytes + bytes / 2 + 4096;
-    CU(cudaMalloc(&A.d, cap));
-    CU(cudaMallocHost(&A.h, cap));
+    CU(lib_malloc(&A.d, cap));
+    CU(lib_malloc_host(&A.h, cap));
     A.cap = cap;
   }
   if (!A.done) CU(cudaEventCreateWithFlags(&A.done, cudaEventDisableTiming));
   if (!A.d_work) {
-    CU(cudaMalloc((void**)&A.d_work, sizeof(int) * 4));
+    CU(lib_malloc((void**)&A.d_work, sizeof(int) * 4));
     CU(cudaMemset(A.d_work, 0, sizeof(int) * 4));
   }
   unsigned char* hb = static_cast<unsigned char*>(A.h);
@@ -1357,6 +1449,7 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
                              any_grad, max_tiles, s);
     if (st != ADG_OK) return st;
   }
+  flipped.done = true;  // every design's binning is enqueued
   for (int i = 0; i < n; ++i)  // the finalize of every gradient item is enqueued
     if (items[i].ops & (ADG_BATCH_GRAD | ADG_BATCH_GRAD_REAL)) items[i].design->partial_dirty = false;
   CU(cudaEventRecord(A.done, s));
@@ -1466,7 +1559,13 @@ extern "C" adg_status adg_profile_read(adg_ctx* ctx, adg_profile_data* out, int3
 }
 
 namespace adg {
-void set_last_error(const char* msg) { g_err = msg; }
+void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 }  // namespace adg
 
-extern "C" const char* adg_last_error(void) { return g_err.c_str(); }
+extern "C" const char* adg_last_error(void) { return g_err; }
+
+extern "C" adg_status adg_debug_alloc(int32_t fail_after, int64_t* live) {
+  if (fail_after >= -1) g_fail_after.store(fail_after);
+  if (live) *live = g_live.load();
+  return ADG_OK;
+}
