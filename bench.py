@@ -649,6 +649,16 @@ def run_adg(args):
                "d2h_bytes_per_step": int(eps_h.numel() * 4 + g_h.numel() * 4),
                "ms_per_step": ms_e}
 
+    # the other configurations: the batched launch, the served mix, the 2D TE
+    # design (launch-bound) and the taper through autograd, each with its own
+    # clock record
+    systems = {}
+    if rank == 0 and world == 1 and not args.no_systems:
+        systems["te2d"] = measure_te2d(ctx, device=local)
+        systems["taper_autograd"] = measure_taper_autograd(ctx, device=local)
+        systems["batch"] = measure_batch(ctx, 256, device=local)
+        systems["serve"] = measure_serve(ctx, device=local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = oracle_sample(desc, ef_h, ea_h, w)
@@ -675,6 +685,8 @@ def run_adg(args):
             "gpu_launches": launches,
             "cpu_baseline": cpu, "e2e": e2e, "dense_vjp": dense, "topology": topo,
             "fd_vs_ad": fdc, "levels": levels, "prop2_mesher": mesh,
+            "batch": systems.get("batch"), "serve": systems.get("serve"),
+            "te2d": systems.get("te2d"), "taper_autograd": systems.get("taper_autograd"),
             "clocks": clocks.summary(),
         }
         print(json.dumps(line))
@@ -694,10 +706,34 @@ def _device_fields(desc, seed):
             torch.randn((C, nz, ny, nx), dtype=torch.complex64, device="cuda", generator=g))
 
 
-def run_batch(args):
-    """Batched persistent launch: `--designs` designs of uneven grid size and
-    primitive count; eps build + gradient for all of them per step, as one
-    graph-captured job table versus one launch sequence per design."""
+def _timed_events(fn, steps, warm, sync):
+    """Device time per call (CUDA events on the current stream) and host wall
+    time per call, after `warm` untimed calls."""
+    import torch
+    for k in range(warm):
+        fn(k)
+    sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    for k in range(steps):
+        fn(k)
+    e1.record()
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / steps
+    sync()
+    return e0.elapsed_time(e1) / steps, wall * 1e3
+
+
+BATCH_TUNE_CANDIDATES = [(32, 4, 4), (32, 8, 4), (32, 4, 2), (32, 8, 2)]
+
+
+def measure_batch(ctx, designs_n=256, steps=5, warmup=3, tune=True, device=0):
+    """Batched persistent launch: designs_n random designs of uneven grid size
+    and primitive count; eps build + gradient for all of them per step, as
+    one graph-captured job table versus one launch sequence per design.  Both
+    tile policies are timed -- the library's default tile, and the
+    autotuner's tile per size class -- and the faster is the headline."""
     import numpy as np
     import torch
 
@@ -705,183 +741,291 @@ def run_batch(args):
     from paper_2311_05646_gb300 import inputs as I
     from paper_2311_05646_gb300.tuning import Autotuner
 
-    torch.cuda.set_device(0)
-    ctx = adg.Context(0)
-    descs = [I.random_design(4100 + k) for k in range(args.designs)]
-    tuner = Autotuner(ctx) if args.tune else None
-    designs, bufs = [], []
-    for k, desc in enumerate(descs):
-        tile = tuner.best(desc) if tuner else None
-        d = adg.Design(ctx, desc, tile=tile)
-        ef, ea = _device_fields(desc, 9000 + k)
-        eps = torch.empty(d.shape, dtype=torch.float32, device="cuda")
-        fill = torch.empty_like(eps)
-        g = torch.zeros(d.n_params, dtype=torch.float32, device="cuda")
-        designs.append(d)
-        bufs.append((ef, ea, eps, fill, g))
+    descs = [I.random_design(4100 + k) for k in range(designs_n)]
     cells = sum(int(np.prod(desc["grid"]["n"])) for desc in descs)
     params = [[desc["params"], desc["params"] + 0.01] for desc in descs]
     w = np.full(3, -2j, dtype=np.complex64)
+    bufs = []
+    for k, desc in enumerate(descs):
+        ef, ea = _device_fields(desc, 9000 + k)
+        sh = I.field_shape(desc)
+        eps = torch.empty(sh, dtype=torch.float32, device="cuda")
+        fill = torch.empty_like(eps)
+        g = torch.zeros(len(desc["params"]), dtype=torch.float32, device="cuda")
+        bufs.append((ef, ea, eps, fill, g))
+    sync = lambda: (torch.cuda.synchronize(), adg.adg_sync(ctx))  # noqa: E731
 
-    def per_design(k):
-        for i, d in enumerate(designs):
-            ef, ea, eps, fill, g = bufs[i]
-            p = params[i][k % 2]
-            adg.adg_build_eps(d, p, eps, fill=fill)
-            adg.adg_grad(d, p, ef, ea, w, g)
+    def run_policy(tiles):
+        designs = [adg.Design(ctx, desc, tile=t) for desc, t in zip(descs, tiles)]
 
-    def batched(k):
+        def batched(k):
+            items = []
+            for i, d in enumerate(designs):
+                ef, ea, eps, fill, g = bufs[i]
+                items.append(adg.BatchItem(d, params[i][k % 2], eps=eps, fill=fill, efwd=ef,
+                                           eadj=ea, w=w, grad=g))
+            return adg.adg_batch_submit(ctx, items, graph=True)
+
+        def per_design(k):
+            for i, d in enumerate(designs):
+                ef, ea, eps, fill, g = bufs[i]
+                p = params[i][k % 2]
+                adg.adg_build_eps(d, p, eps, fill=fill)
+                adg.adg_grad(d, p, ef, ea, w, g)
+
+        clocks = Clocks(device)
+        clocks.start()
+        ms_b, wall_b = _timed_events(batched, steps, warmup, sync)
+        ms_d, wall_d = _timed_events(per_design, steps, warmup, sync)
+        clocks.stop()
+        # per-kernel device time of one batched step (direct launches, events around each)
+        adg.adg_profile_read(ctx, reset=True)
+        adg.adg_profile_enable(ctx, True)
         items = []
         for i, d in enumerate(designs):
             ef, ea, eps, fill, g = bufs[i]
-            items.append(adg.BatchItem(d, params[i][k % 2], eps=eps, fill=fill, efwd=ef, eadj=ea,
-                                       w=w, grad=g))
-        return adg.adg_batch_submit(ctx, items, graph=True)
-
-    def timed(fn, steps, warm):
-        for k in range(warm):
-            fn(k)
+            items.append(adg.BatchItem(d, params[i][0], eps=eps, fill=fill, efwd=ef, eadj=ea, w=w,
+                                       grad=g))
+        adg.adg_batch_wait(ctx, adg.adg_batch_submit(ctx, items, graph=False))
         torch.cuda.synchronize()
-        adg.adg_sync(ctx)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        adg.adg_profile_enable(ctx, False)
+        prof = {k: round(1e3 * v[1] / max(v[0], 1), 1)
+                for k, v in adg.adg_profile_read(ctx, reset=True).items() if v[0]}
+        for d in designs:
+            d.close()
+        n = len(designs)
+        return {"gradients_per_s": n / (ms_b * 1e-3), "ms_per_step": ms_b,
+                "host_wall_ms_per_step": wall_b, "cells_per_s": cells / (ms_b * 1e-3),
+                "one_launch_per_design": {"gradients_per_s": n / (ms_d * 1e-3),
+                                          "ms_per_step": ms_d, "host_wall_ms_per_step": wall_d},
+                "speedup_vs_per_design": ms_d / ms_b, "batched_kernels_us": prof,
+                "clocks": clocks.summary()}
+
+    out = {"designs": len(descs), "cells_total": cells,
+           "workload": "%d random designs, grids U[128,512]x[64,256]x[32,96], 10-400 primitives "
+                       "(boxes, circles r 80-200 nm, 16-64-gons), unions/differences, complex64 "
+                       "fields" % len(descs),
+           "steps": steps, "warmup": warmup}
+    out["default_tile"] = run_policy([None] * len(descs))
+    if tune:
+        tuner = Autotuner(ctx, candidates=BATCH_TUNE_CANDIDATES)
         t0 = time.perf_counter()
-        e0.record()
-        for k in range(steps):
-            fn(k)
-        e1.record()
-        torch.cuda.synchronize()
-        wall = (time.perf_counter() - t0) / steps
-        adg.adg_sync(ctx)
-        return e0.elapsed_time(e1) / steps, wall * 1e3
+        tiles = [tuner.best(desc) for desc in descs]
+        out["autotuned_tile"] = run_policy(tiles)
+        out["autotuned_tile"]["tuning_s"] = time.perf_counter() - t0
+        out["autotuned_tile"]["size_classes"] = len(tuner.cache)
+    best = max((k for k in ("default_tile", "autotuned_tile") if k in out),
+               key=lambda k: out[k]["gradients_per_s"])
+    out["headline_tiles"] = best
+    out["gradients_per_s"] = out[best]["gradients_per_s"]
+    out["speedup_vs_per_design"] = out[best]["speedup_vs_per_design"]
+    del bufs
+    torch.cuda.empty_cache()
+    return out
 
-    ms_b, wall_b = timed(batched, args.steps, max(args.warmup, 3))
-    ms_d, wall_d = timed(per_design, args.steps, max(args.warmup, 3))
-    n = len(designs)
-    # per-kernel device time of one batched step (direct launches, events around each)
-    adg.adg_profile_read(ctx, reset=True)
-    adg.adg_profile_enable(ctx, True)
-    items = []
-    for i, d in enumerate(designs):
-        ef, ea, eps, fill, g = bufs[i]
-        items.append(adg.BatchItem(d, params[i][0], eps=eps, fill=fill, efwd=ef, eadj=ea, w=w, grad=g))
-    adg.adg_batch_wait(ctx, adg.adg_batch_submit(ctx, items, graph=False))
-    torch.cuda.synchronize()
-    adg.adg_profile_enable(ctx, False)
-    bprof = {k: round(1e3 * v[1] / max(v[0], 1), 1) for k, v in adg.adg_profile_read(ctx, reset=True).items() if v[0]}
+
+def run_batch(args):
+    import torch
+
+    from paper_2311_05646_gb300 import adg
+    torch.cuda.set_device(0)
+    ctx = adg.Context(0)
+    b = measure_batch(ctx, args.designs, args.steps, max(args.warmup, 3), tune=args.tune)
+    best = b[b["headline_tiles"]]
     line = {"metric": "gradients/s (eps build + VJP gradient per design)",
-            "value": n / (ms_b * 1e-3), "unit": "gradients/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "%d random designs, grids U[128,512]x[64,256]x[32,96], 10-400 "
-                                   "primitives (boxes, circles, 16-64-gons), unions/differences" % n,
-                       "cells_total": cells, "tiles_autotuned": bool(args.tune)},
-            "cells_per_s": cells / (ms_b * 1e-3),
-            "one_launch_per_design": {"value": n / (ms_d * 1e-3), "ms_per_step": ms_d,
-                                      "host_wall_ms_per_step": wall_d},
-            "batched_host_wall_ms_per_step": wall_b,
-            "batched_kernels_us": bprof,
-            "speedup_vs_per_design": ms_d / ms_b}
+            "value": b["gradients_per_s"], "unit": "gradients/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": b["workload"], "cells_total": b["cells_total"],
+                                            "tiles": b["headline_tiles"]},
+            "batch": b, "clocks": best["clocks"]}
     print(json.dumps(line))
     return 0
 
 
-def run_serve(args):
+def _serve_clients(I, np, rng, n, iterations):
+    """The served mix: the largest client a 20 x 20 hole lattice in 1000 x
+    1000 x 80 (1200 parameters), the others 2D 400 x 400 or 3D hole lattices
+    of log-uniform size; fields made on the device at admission."""
+    from paper_2311_05646_gb300 import serve as S
+    cl = []
+    for k in range(n):
+        if k == 0:
+            desc = I.hole_lattice(n=(1000, 1000, 80), holes=20, seed=51)
+        elif rng.uniform() < 0.5:
+            desc = I.hole_lattice(n=(400, 400, 1), d=(40.0, 40.0, 40.0), holes=8, ncomp=1,
+                                  seed=51 + k)
+        else:
+            sx = int(np.exp(rng.uniform(np.log(128), np.log(1000))))
+            sy = int(np.exp(rng.uniform(np.log(128), np.log(1000))))
+            sz = int(np.exp(rng.uniform(np.log(32), np.log(80))))
+            desc = I.hole_lattice(n=(sx, sy, sz), holes=int(np.clip(sx // 50, 2, 20)), seed=51 + k)
+        cl.append(S.Client(cid=k, desc=desc, w=np.full(desc["grid"]["ncomp"], -2j),
+                           iterations=iterations,
+                           make_fields=(lambda desc=desc, k=k: _device_fields(desc, 7000 + k))))
+    return cl
+
+
+def measure_serve(ctx, clients_n=12, iterations=50, mem_gb=40.0, rates=(0.5, 0.8, 0.95),
+                  tune=True, device=0):
     """Served requests: clients (designs) arrive as a Poisson process and run
-    50 optimiser iterations each (an eps build, then a gradient, then the
-    parameter step); fields stay resident; admission is gated by a device
-    memory budget; batches form continuously.  Reports p50/p99 latency and
-    gradients/s, first saturated (all clients at once), then at 0.8 x the
-    saturated request rate."""
+    `iterations` optimiser iterations each (an eps build, then a gradient,
+    then the parameter step); fields stay resident; admission is gated by
+    the bytes libadg reports plus the clients' buffers against a memory
+    budget and the device's free memory; batches form continuously.  First
+    saturated (all clients at once), then Poisson arrivals at each rate x the
+    saturated request rate: p50 / p99 request latency and gradients/s."""
     import numpy as np
     import torch
 
-    from paper_2311_05646_gb300 import adg
     from paper_2311_05646_gb300 import inputs as I
     from paper_2311_05646_gb300 import serve as S
 
-    torch.cuda.set_device(0)
-    ctx = adg.Context(0)
     rng = np.random.default_rng(51)
-
-    def make_clients(n):
-        cl = []
-        for k in range(n):
-            if k == 0:  # the largest: 20 x 20 holes in 1000 x 1000 x 80
-                desc = I.hole_lattice(n=(1000, 1000, 80), holes=20, seed=51)
-            elif rng.uniform() < 0.5:
-                desc = I.hole_lattice(n=(400, 400, 1), d=(40.0, 40.0, 40.0), holes=8, ncomp=1,
-                                      seed=51 + k)
-            else:
-                sx = int(np.exp(rng.uniform(np.log(128), np.log(1000))))
-                sy = int(np.exp(rng.uniform(np.log(128), np.log(1000))))
-                sz = int(np.exp(rng.uniform(np.log(32), np.log(80))))
-                desc = I.hole_lattice(n=(sx, sy, sz), holes=int(np.clip(sx // 50, 2, 20)),
-                                      seed=51 + k)
-            ef, ea = _device_fields(desc, 7000 + k)
-            c = S.Client(cid=k, desc=desc, efwd=ef, eadj=ea, w=np.full(desc["grid"]["ncomp"], -2j),
-                         iterations=args.iterations)
-            cl.append(c)
-        return cl
-
-    # tile shapes from the autotuner, tuned per design size class before the
-    # timed runs (admission then finds them cached)
     tuner = None
-    if not args.no_tune:
+    if tune:
         from paper_2311_05646_gb300.tuning import Autotuner
         tuner = Autotuner(ctx)
+    budget = int(mem_gb * 2 ** 30)
 
     def run(clients, arrivals):
-        srv = S.Server(ctx, mem_budget_bytes=int(args.mem_gb * 2 ** 30), max_inflight=2,
-                       tuner=tuner)
+        srv = S.Server(ctx, mem_budget_bytes=budget, max_inflight=2, tuner=tuner)
+        clocks = Clocks(device)
+        clocks.start()
         t0 = time.perf_counter()
         order = sorted(zip(arrivals, range(len(clients))))
         nxt = 0
+        peak = 0
         while nxt < len(order) or not srv.idle():
             now = time.perf_counter() - t0
             while nxt < len(order) and order[nxt][0] <= now:
                 srv.arrive(clients[order[nxt][1]], time.perf_counter())
                 nxt += 1
+            peak = max(peak, srv.used)
             if not srv.poll():
                 time.sleep(20e-6)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        clocks.stop()
         grads = sum(1 for r in srv.completed if r.op == "grad")
-        return srv, wall, grads
+        lat = S.latency_stats(srv.completed)
+        return {"gradients_per_s": grads / wall, "requests": len(srv.completed),
+                "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"], "mean_ms": lat.get("mean_ms"),
+                "batches": srv.batches, "wall_s": wall, "peak_admitted_bytes": peak,
+                "clocks": clocks.summary()}
 
-    clients = make_clients(args.clients)
+    t0 = time.perf_counter()
+    clients = _serve_clients(I, np, rng, clients_n, iterations)
     if tuner is not None:
         for c in clients:
             tuner.best(c.desc)
         torch.cuda.synchronize()
-    srv, wall, grads = run(clients, [0.0] * len(clients))
-    sat = grads / wall
-    lat_sat = S.latency_stats(srv.completed)
-    # Poisson arrivals at 0.8 x the saturated rate (clients = requests / iterations)
-    clients = make_clients(args.clients)
-    if tuner is not None:
-        for c in clients:
-            tuner.best(c.desc)
-        torch.cuda.synchronize()
-    rate_clients = 0.8 * sat / args.iterations
-    arr = np.cumsum(rng.exponential(1.0 / rate_clients, len(clients)))
-    arr -= arr[0]
-    srv2, wall2, grads2 = run(clients, list(arr))
-    lat = S.latency_stats(srv2.completed)
-    line = {"metric": "served gradients/s with p50/p99 request latency", "value": grads2 / wall2,
-            "unit": "gradients/s", "n_gpus": 1, "steps": grads2, "warmup": 0,
-            "ms_per_step": 1e3 * wall2 / max(grads2, 1), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "%d clients x %d iterations (eps build + gradient), hole "
-                                   "lattices: 2D 400x400 or 3D up to 1000x1000x80 (20x20 holes, "
-                                   "1200 params)" % (len(clients), args.iterations),
-                       "mem_budget_gb": args.mem_gb, "arrivals": "Poisson at 0.8 x saturated",
-                       "tiles_autotuned": tuner is not None},
-            "latency_ms": {"p50": lat["p50_ms"], "p99": lat["p99_ms"], "mean": lat.get("mean_ms")},
-            "saturated": {"gradients_per_s": sat, "p50_ms": lat_sat["p50_ms"],
-                          "p99_ms": lat_sat["p99_ms"], "batches": srv.batches},
-            "batches": srv2.batches}
+    tuning_s = time.perf_counter() - t0
+    sat = run(clients, [0.0] * len(clients))
+    out = {"workload": "%d clients x %d iterations (eps build + gradient), hole lattices: 2D "
+                       "400x400 or 3D up to 1000x1000x80 (20x20 holes, 1200 params)"
+                       % (clients_n, iterations),
+           "mem_budget_gb": mem_gb, "tiles_autotuned": tuner is not None, "tuning_s": tuning_s,
+           "saturated": sat, "poisson": {}}
+    for lam in rates:
+        clients = _serve_clients(I, np, np.random.default_rng(51), clients_n, iterations)
+        rate_clients = lam * sat["gradients_per_s"] / iterations
+        arr = np.cumsum(rng.exponential(1.0 / rate_clients, len(clients)))
+        arr -= arr[0]
+        out["poisson"]["%.2f" % lam] = run(clients, list(arr))
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(args):
+    import torch
+
+    from paper_2311_05646_gb300 import adg
+    torch.cuda.set_device(0)
+    ctx = adg.Context(0)
+    sv = measure_serve(ctx, args.clients, args.iterations, args.mem_gb, tune=not args.no_tune)
+    mid = sv["poisson"]["0.80"]
+    line = {"metric": "served gradients/s with p50/p99 request latency",
+            "value": mid["gradients_per_s"], "unit": "gradients/s", "n_gpus": 1,
+            "steps": mid["requests"], "warmup": 0,
+            "ms_per_step": 1e3 * mid["wall_s"] / max(mid["requests"], 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": sv["workload"],
+                                            "arrivals": "Poisson at 0.8 x saturated"},
+            "latency_ms": {"p50": mid["p50_ms"], "p99": mid["p99_ms"]},
+            "serve": sv, "clocks": mid["clocks"]}
     print(json.dumps(line))
     return 0
+
+
+def measure_te2d(ctx, steps=2000, warmup=50, device=0):
+    """The 2D TE single design (200 x 100 cells, 20 nm, a waveguide box minus a
+    20-tooth grating, 40 edge parameters, Ez fields of seeded plane waves):
+    launch-bound, so reported as the device time and host wall time per eps
+    build + gradient, with the parameters alternating (every step re-bins)."""
+    import torch
+
+    from paper_2311_05646_gb300 import adg
+    from paper_2311_05646_gb300 import inputs as I
+    desc = I.grating_2d("fit")
+    d = adg.Design(ctx, desc)
+    ef = torch.from_numpy(I.plane_wave_field(desc, 12)).cuda()
+    ea = torch.from_numpy(I.plane_wave_field(desc, 13)).cuda()
+    w = I.seeded_w(1, 5)
+    eps = torch.empty(d.shape, dtype=torch.float32, device="cuda")
+    fill = torch.empty_like(eps)
+    g = torch.zeros(d.n_params, dtype=torch.float32, device="cuda")
+    ps = [desc["params"], desc["params"] + 0.01]
+
+    def step(k):
+        adg.adg_build_eps(d, ps[k % 2], eps, fill=fill)
+        adg.adg_grad(d, ps[k % 2], ef, ea, w, g)
+
+    clocks = Clocks(device)
+    clocks.start()
+    ms, wall = _timed_events(step, steps, warmup, lambda: (torch.cuda.synchronize(), adg.adg_sync(ctx)))
+    clocks.stop()
+    cells = 200 * 100
+    d.close()
+    return {"workload": "2D TE grating 200x100 (Ez), 40 edge params", "cells": cells,
+            "device_us_per_step": 1e3 * ms, "host_us_per_step": 1e3 * wall,
+            "cells_per_s": cells / (ms * 1e-3), "steps": steps, "clocks": clocks.summary()}
+
+
+def measure_taper_autograd(ctx, steps=20, warmup=3, device=0):
+    """The differentiable taper through torch.autograd: eps = eps_of(design, p)
+    on the 800 x 300 x 100 grid (two 64-vertex graph boundaries, 128
+    parameters, sigmoid k = 4 / dx), then eps.backward(G) with a fixed real
+    cotangent: the forward keeps only p, the backward recomputes fill."""
+    import numpy as np
+    import torch
+
+    from paper_2311_05646_gb300 import adg
+    from paper_2311_05646_gb300 import inputs as I
+    from paper_2311_05646_gb300.autograd import eps_of
+    desc = I.taper_3d()
+    d = adg.Design(ctx, desc)
+    gen = torch.Generator(device="cuda").manual_seed(12)
+    G = torch.randn(d.shape, dtype=torch.float32, device="cuda", generator=gen)
+    p = torch.tensor(desc["params"], dtype=torch.float64, requires_grad=True)
+
+    def step(k):
+        with torch.no_grad():
+            p.add_(0.01 if k % 2 else -0.01)  # new parameters every step (re-binning)
+        p.grad = None
+        eps = eps_of(d, p)
+        eps.backward(G)
+
+    clocks = Clocks(device)
+    clocks.start()
+    ms, wall = _timed_events(step, steps, warmup, lambda: (torch.cuda.synchronize(), adg.adg_sync(ctx)))
+    clocks.stop()
+    cells = int(np.prod(desc["grid"]["n"]))
+    d.close()
+    return {"workload": "taper 800x300x100, 3 components, 128 vertex-offset params, autograd "
+                        "forward + backward", "cells": cells, "ms_per_step": ms,
+            "host_ms_per_step": wall, "cells_per_s": cells / (ms * 1e-3), "steps": steps,
+            "clocks": clocks.summary()}
 
 
 def main():
@@ -902,6 +1046,7 @@ def main():
     ap.add_argument("--clients", type=int, default=12)
     ap.add_argument("--iterations", type=int, default=50)
     ap.add_argument("--mem-gb", type=float, default=40.0)
+    ap.add_argument("--no-systems", action="store_true")  # skip batch / serve / TE / taper entries
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

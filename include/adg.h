@@ -382,6 +382,14 @@ adg_status adg_sync(adg_ctx *ctx, void *stream);
 /* Counters of the design's last binning (synchronises `stream`). */
 adg_status adg_design_stats(adg_ctx *ctx, adg_design *design, void *stream, adg_stats *out);
 
+/* Device memory the design holds, in bytes (host-side bookkeeping, no
+ * synchronisation): its tables, bins and counters, the partial buffer at the
+ * size its current parameters need (or its capacity, if larger), and the
+ * scratch of the optional calls it has made (dense form, FD, levels, E+H).
+ * Caller buffers (fields, eps, fill, gradients) are not included.  For
+ * admission control by a memory budget. */
+adg_status adg_design_bytes(adg_ctx *ctx, adg_design *design, int64_t *bytes);
+
 /* Per-kernel timing for measurement.  While enabled, every kernel launch of
  * the context is bracketed by CUDA events recorded on the launching stream.
  * adg_profile_read waits for the recorded events and returns, per kernel

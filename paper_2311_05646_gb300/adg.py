@@ -489,6 +489,17 @@ def adg_grad_noalloc(desc: dict, params, efwd, eadj, w, grad, tile=None, stream=
              ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad), _stream_ptr(stream)))
 
 
+def adg_design_bytes(design: Design) -> int:
+    """Device bytes the design holds (tables, bins, partial buffer, scratch of
+    the optional calls); the caller's own buffers are not included."""
+    b = ctypes.c_int64(0)
+    L = lib()
+    L.adg_design_bytes.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+    L.adg_design_bytes.restype = ctypes.c_int
+    _check(L.adg_design_bytes(design.ctx.handle, design.handle, ctypes.byref(b)))
+    return int(b.value)
+
+
 def adg_debug_alloc(fail_after: int = -2) -> int:
     """Host-side fault injection for tests: let `fail_after` more of libadg's
     allocations succeed and fail the next (-1: off, -2: unchanged).  Returns

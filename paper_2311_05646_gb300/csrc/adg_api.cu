@@ -1564,6 +1564,33 @@ void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg)
 
 extern "C" const char* adg_last_error(void) { return g_err; }
 
+// Device bytes a design holds: its tables, bins and counters, the partial
+// buffer at the size its current parameters need (or its capacity, if
+// larger), and the scratch of the optional calls it has made.
+size_t design_bytes(const adg_design* d) {
+  auto vb = [](const auto& v) { return std::max<size_t>(v.size(), 1) * sizeof(v[0]); };
+  size_t b = vb(d->chain) + vb(d->act) + vb(d->actc) + vb(d->ref_off) + vb(d->ref_prim) +
+             vb(d->ref_qa) + vb(d->ref_coeff) + vb(d->h_prims) + vb(d->h_auxd) + vb(d->h_auxf);
+  const size_t T = (size_t)d->g.T;
+  b += T * (sizeof(TileProg) + 1 + sizeof(int)) + 16 * sizeof(int) + sizeof(Job);
+  b += std::max(d->partial_cap, d->part_total) * sizeof(float);
+  const size_t plane = (size_t)d->g.nx * d->g.ny * d->g.nz, ns = plane * d->g.C;
+  if (d->d_dense_part)
+    b += sizeof(double2) * d->g.C * ((plane + kDenseChunk - 1) / kDenseChunk) + sizeof(int);
+  if (d->d_fd_buf)
+    b += sizeof(float) * ns * 4 + sizeof(double) * std::max(fd_chunks((long long)ns), 1) +
+         sizeof(double) * std::max(d->n_params, 1);
+  if (d->d_row) b += sizeof(float) * d->n_params;
+  b += sizeof(float) * d->lv_cap;
+  return b;
+}
+
+extern "C" adg_status adg_design_bytes(adg_ctx* ctx, adg_design* d, int64_t* bytes) {
+  if (!ctx || !d || !bytes) return fail(ADG_EINVAL, "adg_design_bytes: NULL argument");
+  *bytes = (int64_t)design_bytes(d);
+  return ADG_OK;
+}
+
 extern "C" adg_status adg_debug_alloc(int32_t fail_after, int64_t* live) {
   if (fail_after >= -1) g_fail_after.store(fail_after);
   if (live) *live = g_live.load();

@@ -6,8 +6,10 @@ whole optimisation run.  Each client issues requests one at a time (an eps
 build, then a gradient, then the next parameter update -- steps 2 and 5 of
 the protocol of Sec. 2, repeated as in step 7).  The service loop:
 
-* admits a new client only when its resident footprint fits under the device
-  memory budget (memory-gated admission); others wait in arrival order;
+* admits a new client only when its resident footprint -- the bytes libadg
+  reports for its compiled design (adg_design_bytes) plus its fields, eps
+  and gradient buffers -- fits under the memory budget and in the device's
+  free memory (memory-gated admission); others wait in arrival order;
 * forms a batch from all pending requests -- one per client, whatever their
   grid sizes -- and submits it as one job table (adg_batch_submit), while up
   to `max_inflight` earlier batches are still running: requests that arrive
@@ -40,11 +42,13 @@ class Request:
 
 @dataclass
 class Client:
-    """One design under optimisation with its resident device buffers."""
+    """One design under optimisation with its resident device buffers.  The
+    fields are given (efwd, eadj) or made at admission by make_fields()."""
     cid: int
     desc: dict
     efwd: object = None         # torch complex64 [C][nz][ny][nx]
     eadj: object = None
+    make_fields: object = None  # () -> (efwd, eadj), called once admitted
     w: object = None
     iterations: int = 50
     step_nm: float = 1.0
@@ -55,19 +59,32 @@ class Client:
     params: np.ndarray = None
     done_iters: int = 0
     t_arrive: float = 0.0
+    need: int = 0               # bytes counted against the budget while admitted
     history: list = field(default_factory=list)
 
-    def footprint(self) -> int:
+    def buffer_bytes(self) -> int:
+        """The client's own device buffers: forward and adjoint fields
+        (complex64), eps (fp32) and the gradient (fp32)."""
         nx, ny, nz = self.desc["grid"]["n"]
-        C = self.desc["grid"]["ncomp"]
-        cells = nx * ny * nz * C
-        return cells * (8 + 8 + 4) + 64 * 1024 * 1024 // 64  # fields, eps, tables
+        samples = nx * ny * nz * self.desc["grid"]["ncomp"]
+        return samples * (8 + 8 + 4) + 4 * len(self.desc["params"])
+
+
+def footprint(ctx: adg.Context, client: Client, tile=None) -> int:
+    """Resident bytes of a client: its compiled design as libadg reports it,
+    plus its buffers (the design is compiled and released again)."""
+    d = adg.Design(ctx, client.desc, tile=tile)
+    try:
+        return adg.adg_design_bytes(d) + client.buffer_bytes()
+    finally:
+        d.close()
 
 
 class Server:
     def __init__(self, ctx: adg.Context, mem_budget_bytes: int, max_inflight: int = 2,
-                 graph: bool = False, on_result=None, tuner=None):
+                 graph: bool = False, on_result=None, tuner=None, reserve_bytes: int = 1 << 30):
         self.ctx = ctx
+        self.reserve = int(reserve_bytes)  # device memory left free at admission
         self.tuner = tuner  # tuning.Autotuner: the tile shape per design size class
         self.budget = int(mem_budget_bytes)
         self.used = 0
@@ -92,13 +109,24 @@ class Server:
         import torch
         while self.waiting:
             c = self.waiting[0]
-            need = c.footprint()
-            if self.used + need > self.budget and self.active:
+            tile = self.tuner.best(c.desc) if self.tuner is not None else None
+            design = adg.Design(self.ctx, c.desc, tile=tile)
+            need = adg.adg_design_bytes(design) + c.buffer_bytes()
+            # buffers still to allocate must also fit in what the device has free
+            to_alloc = c.buffer_bytes()
+            if c.efwd is not None:
+                to_alloc -= 2 * int(c.efwd.numel()) * 8
+            # free on the device, plus what torch's allocator holds cached
+            free = torch.cuda.mem_get_info()[0] + torch.cuda.memory_reserved() - torch.cuda.memory_allocated()
+            if self.active and (self.used + need > self.budget or to_alloc + self.reserve > free):
+                design.close()
                 return  # wait for memory; an empty server always admits one
             self.waiting.popleft()
+            c.need = need
             self.used += need
-            tile = self.tuner.best(c.desc) if self.tuner is not None else None
-            c.design = adg.Design(self.ctx, c.desc, tile=tile)
+            c.design = design
+            if c.efwd is None and c.make_fields is not None:
+                c.efwd, c.eadj = c.make_fields()
             c.eps = torch.empty(c.design.shape, dtype=torch.float32, device="cuda")
             c.grad = torch.zeros(c.design.n_params, dtype=torch.float32, device="cuda")
             c.grad_host = torch.zeros(c.design.n_params, dtype=torch.float32).pin_memory()
@@ -108,7 +136,7 @@ class Server:
 
     def _release(self, c: Client):
         self.active.remove(c)
-        self.used -= c.footprint()
+        self.used -= c.need
         c.design.close()
         c.eps = c.grad = c.efwd = c.eadj = None
         self.finished_clients.append(c)

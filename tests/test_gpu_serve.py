@@ -1,6 +1,7 @@
 """Serving: continuous batching with memory-gated admission.  Each request's
-result equals what the same design and parameters give alone (the stated
-tolerance; in fact bitwise), admission respects the memory budget, and every
+gradient matches the FP64 oracle at the same parameters (the stated
+tolerance) and equals what the same design gives alone (bitwise), admission
+respects the memory budget counted from the bytes libadg reports, and every
 client completes its iterations."""
 import numpy as np
 import pytest
@@ -13,7 +14,7 @@ from .conftest import cuda_ok
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
 
 
-def test_served_results_equal_alone_and_admission_is_gated():
+def test_served_results_match_the_oracle_and_admission_is_gated(oracle_mod):
     import torch
     from paper_2311_05646_gb300 import adg
     from paper_2311_05646_gb300 import serve as S
@@ -28,8 +29,11 @@ def test_served_results_equal_alone_and_admission_is_gated():
         ea = torch.from_numpy(I.plane_wave_field(desc, 600 + k)).cuda()
         clients.append(S.Client(cid=k, desc=desc, efwd=ef, eadj=ea,
                                 w=I.seeded_w(desc["grid"]["ncomp"], 700 + k), iterations=4))
-    # a budget that holds about two clients at a time
-    budget = 2 * max(c.footprint() for c in clients) + 1
+    # a budget that holds about two clients at a time, from the bytes libadg
+    # reports for each compiled design plus its buffers
+    feet = [S.footprint(ctx, c) for c in clients]
+    assert all(f > c.buffer_bytes() for f, c in zip(feet, clients))
+    budget = 2 * max(feet) + 1
     seen = []
 
     def record(r):
@@ -67,3 +71,8 @@ def test_served_results_equal_alone_and_admission_is_gated():
         ok, err, bound = H.grad_ok(a, b)
         assert ok, (cid, err, bound)
         assert np.array_equal(a, b), cid
+        gref = oracle_mod.grad(c.desc, I.plane_wave_field(c.desc, 500 + cid),
+                               I.plane_wave_field(c.desc, 600 + cid), c.w, params=p)
+        ok, err, bound = H.grad_ok(a, gref)
+        assert ok, ("served vs oracle", cid, err, bound)
+    assert len(seen) == 4 * len(clients)
