@@ -32,7 +32,8 @@
  * polygon normal points inward whatever the winding; difference(a,b) =
  * intersection(a, 1-b); clamp subgradients pass through at the boundary;
  * a circle's derivative w.r.t. its centre is 0 at r = 0, and so is a polar
- * shape's (whose angle is then taken as 0).
+ * shape's (whose angle is then taken as 0); a rotation / aspect transform
+ * (Sec. 4, item iii) evaluates the primitive at p + S^-1 R(-theta) (r - p).
  */
 #include <math.h>
 #include <stdint.h>
@@ -49,7 +50,8 @@ enum { OD_PRODUCT = 0, OD_CLAMP = 1 };
 enum {
   OD_BOUND_X = 1, OD_BOUND_Y = 2, OD_BOUND_Z = 4, /* box: which axes are bounded */
   OD_RECT_SIGMA = 8,   /* box uses the paper's Rect product of sigma_k factors */
-  OD_GRAPH_ABOVE = 16  /* graph: region y > f(x) instead of y < f(x)          */
+  OD_GRAPH_ABOVE = 16, /* graph: region y > f(x) instead of y < f(x)          */
+  OD_XFORM = 64        /* in-plane rotation + aspect transform (last 5 scalars) */
 };
 enum { OD_OP_PUSH = 0, OD_OP_UNION = 1, OD_OP_INTERSECT = 2, OD_OP_DIFF = 3 };
 
@@ -129,14 +131,11 @@ static double overlap1d(double a, double b, double c, double h, double *dda, dou
   return 0.0;
 }
 
-/* Evaluate primitive `pi` at sample point r (physical coordinates).  `q` is the
- * full geometric-scalar vector; the primitive reads q[q0 .. q0 + nq - 1].
- * Writes s and, if dsdq != NULL, d s / d q_local for every local scalar.    */
-int od_prim(const od_design *D, int pi, const double *q, const double r[3], double *s_out,
-            double *dsdq) {
-  const int kind = D->kind[pi], sk = D->sigma[pi], fl = D->flags[pi];
-  const int nq = D->nqp[pi];
-  const double *Q = q + D->q0[pi];
+/* Evaluate primitive `pi` (flags fl, nq scalars Q) at the point r (physical
+ * coordinates).  Writes s and, if dsdq != NULL, d s / d Q for every scalar. */
+static int prim_eval(const od_design *D, int pi, int fl, int nq, const double *Q,
+                     const double r[3], double *s_out, double *dsdq) {
+  const int kind = D->kind[pi], sk = D->sigma[pi];
   if (dsdq)
     for (int t = 0; t < nq; ++t) dsdq[t] = 0.0;
 
@@ -334,6 +333,66 @@ int od_prim(const od_design *D, int pi, const double *q, const double r[3], doub
   return 0;
 }
 
+/* Rotation and aspect-ratio transform of a 2D primitive (Sec. 4, item iii:
+ * the primitives support parameterized aspect-ratio and rotation
+ * transforms; the paper gives no formula -- this is the reading).  The last
+ * five scalars are the pivot (px, py), the angle theta (radians) and the
+ * aspect (sx, sy > 0); the primitive, drawn with its own scalars, is stretched
+ * by (sx, sy) along its own axes and rotated by theta about the pivot, i.e.
+ * it is evaluated at the local point
+ *     u = p + S^-1 R(-theta) (r - p),   S = diag(sx, sy),
+ * with z untouched; its sigma_k acts on distances in local units.  Boxes take
+ * the paper's sigma-product form (the exact window overlap is for
+ * axis-aligned boxes), graphs are not transformed, and the grid must have
+ * dx == dy.  Derivatives: the primitive's own scalars are those of the base
+ * primitive at u; a transform scalar xi gives grad_u s . du/dxi, where the
+ * spatial gradient grad_u s is minus the derivative of s w.r.t. a rigid
+ * translation of the shape (the sum over its x, resp. y, position scalars). */
+static int prim_xform(const od_design *D, int pi, int fl, int nq, const double *Q,
+                      const double r[3], double *s_out, double *dsdq) {
+  const int kind = D->kind[pi], nb = nq - 5;
+  if (nb < 1 || kind == OD_GRAPH) return -1;
+  if (kind == OD_BOX && !(fl & OD_RECT_SIGMA)) return -1;
+  const double px = Q[nb], py = Q[nb + 1], th = Q[nb + 2], sx = Q[nb + 3], sy = Q[nb + 4];
+  if (!(sx > 0.0) || !(sy > 0.0)) return -1;
+  const double c = cos(th), s = sin(th);
+  const double dx = r[0] - px, dy = r[1] - py;
+  const double vx = c * dx + s * dy, vy = -s * dx + c * dy; /* R(-theta) (r - p) */
+  const double u[3] = {px + vx / sx, py + vy / sy, r[2]};
+  if (nb > 4096) return -1;
+  double db[nb];
+  int rc = prim_eval(D, pi, fl & ~OD_XFORM, nb, Q, u, s_out, dsdq ? db : NULL);
+  if (rc || !dsdq) return rc;
+  double gx = 0.0, gy = 0.0; /* grad_u s */
+  if (kind == OD_BOX) {
+    gx = -(db[0] + db[1]);
+    gy = -(db[2] + db[3]);
+  } else if (kind == OD_CIRCLE || kind == OD_POLAR) {
+    gx = -db[0];
+    gy = -db[1];
+  } else { /* polygon: q = z0, z1, x1, y1, ... */
+    for (int t = 2; t + 1 < nb; t += 2) { gx -= db[t]; gy -= db[t + 1]; }
+  }
+  for (int t = 0; t < nb; ++t) dsdq[t] = db[t];
+  dsdq[nb] = gx * (1.0 - c / sx) + gy * (s / sy);                       /* d/d px    */
+  dsdq[nb + 1] = gx * (-s / sx) + gy * (1.0 - c / sy);                  /* d/d py    */
+  dsdq[nb + 2] = gx * ((-s * dx + c * dy) / sx) + gy * ((-c * dx - s * dy) / sy); /* theta */
+  dsdq[nb + 3] = gx * (-vx / (sx * sx));                                 /* d/d sx    */
+  dsdq[nb + 4] = gy * (-vy / (sy * sy));                                 /* d/d sy    */
+  return 0;
+}
+
+/* Evaluate primitive `pi` at sample point r (physical coordinates).  `q` is the
+ * full geometric-scalar vector; the primitive reads q[q0 .. q0 + nq - 1].
+ * Writes s and, if dsdq != NULL, d s / d q_local for every local scalar.    */
+int od_prim(const od_design *D, int pi, const double *q, const double r[3], double *s_out,
+            double *dsdq) {
+  const int fl = D->flags[pi], nq = D->nqp[pi];
+  const double *Q = q + D->q0[pi];
+  if (fl & OD_XFORM) return prim_xform(D, pi, fl, nq, Q, r, s_out, dsdq);
+  return prim_eval(D, pi, fl, nq, Q, r, s_out, dsdq);
+}
+
 /* ---- the CSG program as an explicit tree --------------------------------- */
 typedef struct {
   int n;          /* nodes = ops */
@@ -479,6 +538,10 @@ int od_validate(const od_design *D) {
   if (D->nx < 1 || D->ny < 1 || D->nz < 1 || D->ncomp < 1 || D->ncomp > 3) return -1;
   for (int t = 0; t < D->nprim; ++t) {
     if (D->q0[t] < 0 || D->q0[t] + D->nqp[t] > D->nq) return -2;
+    if ((D->flags[t] & OD_XFORM) &&
+        (D->kind[t] == OD_GRAPH || D->nqp[t] < 6 || fabs(D->d[0] - D->d[1]) > 1e-12 * D->d[0] ||
+         (D->kind[t] == OD_BOX && !(D->flags[t] & OD_RECT_SIGMA))))
+      return -4;
   }
   for (int j = 0; j < D->nq; ++j)
     if (D->q_param[j] >= D->nparam) return -3;

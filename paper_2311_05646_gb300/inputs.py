@@ -19,7 +19,7 @@ import numpy as np
 # ---- format codes (values fixed by the description format) -----------------
 BOX, CIRCLE, POLYGON, GRAPH, POLAR = 0, 1, 2, 3, 4
 SIGMA = {"linear": 0, "sigmoid": 1, "quadratic": 2, "sin": 3, "erf": 4}
-BOUND_X, BOUND_Y, BOUND_Z, RECT_SIGMA, GRAPH_ABOVE = 1, 2, 4, 8, 16
+BOUND_X, BOUND_Y, BOUND_Z, RECT_SIGMA, GRAPH_ABOVE, XFORM = 1, 2, 4, 8, 16, 64
 OP_PUSH, OP_UNION, OP_INTERSECT, OP_DIFF = 0, 1, 2, 3
 
 # Yee sample offsets (in cells) used by default: 2D single component at the
@@ -80,7 +80,14 @@ class Design:
             self.q_param.append(-1)
         return len(self.q_base) - 1
 
-    def _prim(self, kind, sigma, kr, flags, specs) -> int:
+    def _prim(self, kind, sigma, kr, flags, specs, xform=None) -> int:
+        """xform = (px, py, theta, sx, sy): the in-plane rotation (radians) and
+        aspect transform about the pivot (px, py), appended as five scalars."""
+        if xform is not None:
+            if len(xform) != 5:
+                raise ValueError("xform = (px, py, theta, sx, sy)")
+            flags |= XFORM
+            specs = list(specs) + list(xform)
         q0 = len(self.q_base)
         for s in specs:
             self._q(s)
@@ -94,7 +101,7 @@ class Design:
         return len(pr["kind"]) - 1
 
     # primitives (Table "AutoDiffGeo definitions")
-    def box(self, x=None, y=None, z=None, mode="exact", sigma="linear", kr=1.0) -> int:
+    def box(self, x=None, y=None, z=None, mode="exact", sigma="linear", kr=1.0, xform=None) -> int:
         flags, specs = 0, []
         for ax, iv in enumerate((x, y, z)):
             if iv is None:
@@ -104,14 +111,14 @@ class Design:
                 specs += [iv[0], iv[1]]
         if mode == "sigma":
             flags |= RECT_SIGMA
-        return self._prim(BOX, sigma, kr, flags, specs)
+        return self._prim(BOX, sigma, kr, flags, specs, xform)
 
-    def circle(self, cx, cy, r, z=None, sigma="sigmoid", kr=4.0) -> int:
+    def circle(self, cx, cy, r, z=None, sigma="sigmoid", kr=4.0, xform=None) -> int:
         flags = BOUND_Z if z is not None else 0
         zz = z if z is not None else (0.0, 0.0)
-        return self._prim(CIRCLE, sigma, kr, flags, [cx, cy, r, zz[0], zz[1]])
+        return self._prim(CIRCLE, sigma, kr, flags, [cx, cy, r, zz[0], zz[1]], xform)
 
-    def polar(self, cx, cy, R0, coeffs=(), z=None, sigma="sigmoid", kr=4.0) -> int:
+    def polar(self, cx, cy, R0, coeffs=(), z=None, sigma="sigmoid", kr=4.0, xform=None) -> int:
         """Polar2D with the Fourier boundary R(theta) = R0 + sum_n c_n cos(n
         theta) + s_n sin(n theta); coeffs = [(c_1, s_1), ..., (c_N, s_N)]."""
         flags = BOUND_Z if z is not None else 0
@@ -119,15 +126,15 @@ class Design:
         specs = [cx, cy, R0, zz[0], zz[1]]
         for c, s in coeffs:
             specs += [c, s]
-        return self._prim(POLAR, sigma, kr, flags, specs)
+        return self._prim(POLAR, sigma, kr, flags, specs, xform)
 
-    def polygon(self, verts, z=None, sigma="sigmoid", kr=4.0) -> int:
+    def polygon(self, verts, z=None, sigma="sigmoid", kr=4.0, xform=None) -> int:
         flags = BOUND_Z if z is not None else 0
         zz = z if z is not None else (0.0, 0.0)
         specs = [zz[0], zz[1]]
         for vx, vy in verts:
             specs += [vx, vy]
-        return self._prim(POLYGON, sigma, kr, flags, specs)
+        return self._prim(POLYGON, sigma, kr, flags, specs, xform)
 
     def graph(self, X, Y, above=False, z=None, sigma="sigmoid", kr=4.0) -> int:
         flags = (BOUND_Z if z is not None else 0) | (GRAPH_ABOVE if above else 0)

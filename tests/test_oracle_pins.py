@@ -529,6 +529,150 @@ def test_graph_knot_position_derivatives_follow_the_interpolant(oracle_mod):
             assert abs(g[j] - fd) <= 1e-6 * max(1.0, abs(fd)), (i, j, g[j], fd)
 
 
+# ----------------------------------------------- rotation / aspect ---------
+# The paper notes that its primitives support rotation and aspect-ratio
+# transforms (Sec. 4, item iii) without a formula; the reading pinned here: a
+# primitive with transform (px, py, theta, sx, sy) is the untransformed one
+# stretched by (sx, sy) along its own axes and rotated by theta about (px, py).
+def _xbase(kind, xform=None, sigma="sigmoid", kr=4.0, D=None):
+    D = D or _grid2d(40, 36, 1.0)
+    if kind == "box":
+        D.box(x=(P(D.param(12.3)), P(D.param(25.6))), y=(P(D.param(9.2)), P(D.param(20.7))),
+              mode="sigma", sigma=sigma, kr=kr, xform=xform)
+    elif kind == "circle":
+        D.circle(P(D.param(19.4)), P(D.param(17.1)), P(D.param(7.3)), sigma=sigma, kr=kr,
+                 xform=xform)
+    elif kind == "polygon":
+        verts = [(11.2, 10.1), (27.3, 12.4), (24.6, 25.2), (13.1, 22.8)]
+        D.polygon([(P(D.param(x)), P(D.param(y))) for x, y in verts], sigma=sigma, kr=kr,
+                  xform=xform)
+    else:
+        D.polar(P(D.param(19.6)), P(D.param(17.7)), P(D.param(7.1)),
+                [(P(D.param(0.9)), P(D.param(-0.6))), (P(D.param(0.4)), P(D.param(0.2)))],
+                sigma=sigma, kr=kr, xform=xform)
+    return D
+
+
+@pytest.mark.parametrize("kind", ["box", "circle", "polygon", "polar"])
+def test_xform_identity_is_the_primitive(oracle_mod, kind):
+    """theta = 0 and sx = sy = 1 leave the primitive as it is, at any pivot:
+    fill and the derivatives w.r.t. its own scalars."""
+    O = oracle_mod
+    plain = _xbase(kind).to_desc()
+    xd = _xbase(kind, xform=(7.7, 31.1, 0.0, 1.0, 1.0)).to_desc()
+    assert np.abs(O.fill(xd) - O.fill(plain)).max() <= 1e-14
+    ef, ea = I.plane_wave_field(plain, 3), I.plane_wave_field(plain, 4)
+    w = I.seeded_w(1, 2)
+    g0, g1 = O.grad(plain, ef, ea, w), O.grad(xd, ef, ea, w)
+    assert np.abs(g1 - g0).max() <= 1e-12 * max(1.0, np.abs(g0).max())
+
+
+@pytest.mark.parametrize("turn", [1, 2, 3])
+def test_xform_quarter_turns_of_a_box(oracle_mod, turn):
+    """A sigma-box [x0, x1] x [y0, y1] turned by a multiple of 90 degrees
+    about a pivot is the untransformed box with the turned extents (the
+    sigma product is symmetric in its two edges): counter-clockwise,
+    (x, y) - p -> (-(y - py), x - px) per quarter turn."""
+    O = oracle_mod
+    x0, x1, y0, y1, px, py = 12.3, 25.6, 9.2, 20.7, 17.4, 16.1
+    D = _grid2d(44, 40, 1.0)
+    D.box(x=(x0, x1), y=(y0, y1), mode="sigma", sigma="sigmoid", kr=4.0,
+          xform=(px, py, turn * math.pi / 2, 1.0, 1.0))
+    corners = np.array([[x0, y0], [x1, y1]]) - [px, py]
+    for _ in range(turn):
+        corners = np.stack([-corners[:, 1], corners[:, 0]], axis=1)
+    corners += [px, py]
+    E = _grid2d(44, 40, 1.0)
+    E.box(x=tuple(sorted(corners[:, 0])), y=tuple(sorted(corners[:, 1])), mode="sigma",
+          sigma="sigmoid", kr=4.0)
+    assert np.abs(O.fill(D.to_desc()) - O.fill(E.to_desc())).max() <= 1e-12
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_xform_aspect_stretches_about_the_pivot(oracle_mod, axis):
+    """Aspect s along one local axis (theta = 0): a box bounded only along
+    that axis, [a, b], becomes [p + s (a - p), p + s (b - p)] with its sigma
+    transition s times wider, i.e. the untransformed box with those edges and
+    kr / s.  A box bounded along the other axis is untouched."""
+    O = oracle_mod
+    a, b, pv, sc, kr = 8.3, 17.9, 11.2, 2.5, 1.0
+    xf = (pv, 0.0, 0.0, sc, 1.0) if axis == 0 else (0.0, pv, 0.0, 1.0, sc)
+    D = _grid2d(60, 60, 1.0)
+    kw = {"x": (a, b)} if axis == 0 else {"y": (a, b)}
+    D.box(mode="sigma", sigma="linear", kr=kr, xform=xf, **kw)
+    E = _grid2d(60, 60, 1.0)
+    kw2 = {("x" if axis == 0 else "y"): (pv + sc * (a - pv), pv + sc * (b - pv))}
+    E.box(mode="sigma", sigma="linear", kr=kr / sc, **kw2)
+    assert np.abs(O.fill(D.to_desc()) - O.fill(E.to_desc())).max() <= 1e-12
+    F = _grid2d(60, 60, 1.0)
+    kw3 = {("y" if axis == 0 else "x"): (a, b)}
+    F.box(mode="sigma", sigma="linear", kr=kr, xform=xf, **kw3)
+    G_ = _grid2d(60, 60, 1.0)
+    G_.box(mode="sigma", sigma="linear", kr=kr, **kw3)
+    assert np.abs(O.fill(F.to_desc()) - O.fill(G_.to_desc())).max() <= 1e-12
+
+
+def test_xform_45_degree_box_is_exact_with_the_quadratic_sigma(oracle_mod):
+    """A square turned by 45 degrees with the quadratic sigma at k = 1/dx:
+    every cell cut by one edge holds exactly the clipped area of the turned
+    square (Eq. quadratic, Sec. 5.2), checked against polygon clipping."""
+    O = oracle_mod
+    h = 1.0
+    px, py, half = 20.37, 19.81, 9.6
+    D = _grid2d(40, 40, h)
+    D.box(x=(px - half, px + half), y=(py - half, py + half), mode="sigma", sigma="quadratic",
+          kr=1.0, xform=(px, py, math.pi / 4, 1.0, 1.0))
+    desc = D.to_desc()
+    f = O.fill(desc)[0, 0]
+    c, s_ = math.cos(math.pi / 4), math.sin(math.pi / 4)
+    verts = [(px + c * dx - s_ * dy, py + s_ * dx + c * dy)
+             for dx, dy in ((-half, -half), (half, -half), (half, half), (-half, half))]
+    xs, ys = _centres(desc)
+    checked = 0
+    for j, cy in enumerate(ys):
+        for i, cx in enumerate(xs):
+            if _edges_cutting(verts, cx, cy, h) == 1:
+                assert abs(f[j, i] - G.cell_fraction(verts, cx, cy, h)) <= 1e-12
+                checked += 1
+    assert checked > 40
+
+
+def test_xform_ellipse_area(oracle_mod):
+    """A circle of radius R with aspect (sx, sy) is an ellipse: with the
+    smooth sigmoid its fill sums (unit cells) to sx sy times the radial
+    integral 2 pi int rho sigma(k (R - rho)) d rho, whatever the rotation and
+    pivot.  The integral comes from scipy's quadrature and expit, the sum of
+    a smooth profile over the lattice matches it to ~1e-6."""
+    from scipy import integrate, special
+    O = oracle_mod
+    R, sx, sy, kr = 10.0, 2.2, 0.7, 1.0
+    radial, _ = integrate.quad(lambda r: 2 * math.pi * r * special.expit(kr * (R - r)), 0.0, R + 60.0,
+                               epsabs=1e-12, epsrel=1e-12, limit=200)
+    want = sx * sy * radial
+    for th, pv in ((0.3, (60.0, 59.0)), (1.1, (61.5, 57.2))):
+        D = _grid2d(120, 120, 1.0)
+        D.circle(60.3, 59.6, R, sigma="sigmoid", kr=kr, xform=(pv[0], pv[1], th, sx, sy))
+        v = O.fill(D.to_desc()).sum()
+        assert abs(v - want) <= 1e-5 * want, (v, want)
+
+
+@pytest.mark.parametrize("kind", ["box", "circle", "polygon", "polar"])
+def test_xform_gradient_matches_central_fd(oracle_mod, kind):
+    """The reverse sweep through the transform -- the primitive's own scalars
+    and the pivot, angle and aspect, each driven by a parameter -- equals
+    central finite differences of L."""
+    O = oracle_mod
+    D = _grid2d(40, 36, 1.0)
+    xf = (P(D.param(18.7)), P(D.param(16.2)), P(D.param(0.41)), P(D.param(1.3)), P(D.param(0.8)))
+    D = _xbase(kind, xform=xf, D=D)
+    desc = D.to_desc()
+    ef, ea, w = _fields(desc, 7, 8)
+    g = O.grad(desc, ef, ea, w)
+    gfd = O.grad_fd(desc, ef, ea, w, 1e-5)
+    assert np.linalg.norm(g - gfd) <= 1e-6 * np.linalg.norm(g) + 1e-9 * np.abs(g).max()
+    assert np.abs(g[:5]).min() > 0  # every transform scalar moves the loss
+
+
 # ---------------------------------------------------------------- P8 --------
 def _fields(desc, s1, s2, wseed=5):
     return (I.plane_wave_field(desc, s1), I.plane_wave_field(desc, s2),
