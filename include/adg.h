@@ -73,6 +73,18 @@ typedef enum {
  *   CIRCLE/POLYGON/GRAPH/POLAR are extruded along z by the exact overlap of
  *   [z0, z1] when ADG_BOUND_Z is set (planarity, Sec. 5.2).  CIRCLE, POLYGON
  *   and POLAR need dx == dy.
+ *   ADG_XFORM (rotation and aspect ratio, Sec. 4 item iii): five more
+ *   scalars after the primitive's own, px, py, theta, sx, sy (pivot in
+ *   physical units, angle in radians, aspect > 0).  The primitive drawn with
+ *   its own scalars is stretched by (sx, sy) along its own axes and rotated
+ *   by theta about (px, py): it is evaluated at the local point
+ *   u = p + S^-1 R(-theta)(r - p), S = diag(sx, sy), z unchanged, its sigma_k
+ *   acting on local distances.  For BOX with ADG_RECT_SIGMA (the paper's
+ *   Rect form; the exact overlap is for axis-aligned boxes), CIRCLE (an
+ *   ellipse with an aspect), POLYGON and POLAR; not GRAPH; needs dx == dy.
+ *   All five scalars may be driven by parameters: the gradient goes through
+ *   the spatial gradient of the primitive at u.  Evaluated in FP64 on the
+ *   device.
  * Sigma kinds: Table "Nonlinear function definitions", sigma_k(x) = sigma(k x).
  * Logic (Eqs. union/intersection, Appendix B.2):
  *   PRODUCT: union a + b - ab, intersection ab, difference a (1 - b)
@@ -100,7 +112,8 @@ enum {
   ADG_BOUND_Y = 2,
   ADG_BOUND_Z = 4,
   ADG_RECT_SIGMA = 8,
-  ADG_GRAPH_ABOVE = 16
+  ADG_GRAPH_ABOVE = 16,
+  ADG_XFORM = 64
 };
 enum { ADG_OP_PUSH = 0, ADG_OP_UNION = 1, ADG_OP_INTERSECT = 2, ADG_OP_DIFF = 3 };
 

@@ -597,6 +597,7 @@ adg_status run_single_enqueue(adg_ctx* ctx, adg_design* d, bool rebin, float* d_
   t.work = d->d_counters + 12;
   t.fill_warps = d->fill_warps;
   t.polar = d->g.polar;
+  t.xform = d->g.xform;
   st = run_jobs(ctx, d->d_job, t, rebin, d_eps != nullptr, grad, d->g.T, s);
   if (st == ADG_OK) d->partial_dirty = false;
   return st;
@@ -1352,7 +1353,7 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   Job* hj = reinterpret_cast<Job*>(hb + o_jobs);
   size_t po = 0, ado = 0, afo = 0;
   int tile_base = 0, param_base = 0, max_tiles = 0, row_base = 0;
-  bool any_build = false, any_grad = false, any_polar = false;
+  bool any_build = false, any_grad = false, any_polar = false, any_xform = false;
   uint64_t sig = mix(0, (uint64_t)arena_id);
   sig = mix(sig, (uint64_t)n);
   for (int i = 0; i < n; ++i) {
@@ -1397,6 +1398,7 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
     any_build = any_build || J.do_build;
     any_grad = any_grad || J.do_grad;
     any_polar = any_polar || (J.do_grad && d->g.polar);
+    any_xform = any_xform || d->g.xform;
     hj[i] = J;
     po += d->n_prims;
     ado += d->st.auxd_n;
@@ -1413,12 +1415,14 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   t.work = A.d_work;
   t.fill_warps = 1;
   t.polar = any_polar ? 1 : 0;
+  t.xform = any_xform ? 1 : 0;
   sig = mix(sig, (uint64_t)t.polar);  // the captured VJP kernel depends on it
+  sig = mix(sig, (uint64_t)t.xform);  // and the build and VJP kernels on this
   sig = mix(sig, (uint64_t)bytes);
   sig = mix(sig, (uint64_t)tile_base);
   sig = mix(sig, (uint64_t)param_base);
-  build_blocks_per_sm(t.njobs, t.fill_warps);  // kernel attributes are set before any capture
-  vjp_blocks_per_sm(t.njobs, t.polar != 0);
+  build_blocks_per_sm(t.njobs, t.fill_warps, t.xform != 0);  // set before any capture
+  vjp_blocks_per_sm(t.njobs, t.polar || t.xform);
   const bool graph = (flags & ADG_BATCH_GRAPH) && !ctx->prof;
   if (graph && A.exec && A.sig == sig) {
     CU(cudaGraphLaunch(A.exec, s));

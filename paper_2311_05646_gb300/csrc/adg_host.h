@@ -68,9 +68,17 @@ inline adg_status validate(const adg_design_desc* D, Msg& m) {
       return m.set(ADG_EINVAL, "q_base / q_coeff[%d] not finite", j);
   }
   for (int p = 0; p < D->n_prims; ++p) {
-    const int k = D->prim_kind[p], s = D->prim_sigma[p], n = D->prim_nq[p], q0 = D->prim_q0[p];
-    if (q0 < 0 || n < 0 || q0 + n > D->n_q)
-      return m.set(ADG_EINVAL, "primitive %d: scalars [%d, %d) outside [0, %d)", p, q0, q0 + n, D->n_q);
+    const int k = D->prim_kind[p], s = D->prim_sigma[p], q0 = D->prim_q0[p];
+    const bool xf = (D->prim_flags[p] & ADG_XFORM) != 0;
+    const int n = D->prim_nq[p] - (xf ? 5 : 0);  // the base primitive's scalars
+    if (q0 < 0 || D->prim_nq[p] < 0 || q0 + D->prim_nq[p] > D->n_q)
+      return m.set(ADG_EINVAL, "primitive %d: scalars [%d, %d) outside [0, %d)", p, q0,
+                   q0 + D->prim_nq[p], D->n_q);
+    if (xf && (k == ADG_PRIM_GRAPH || (k == ADG_PRIM_BOX && !(D->prim_flags[p] & ADG_RECT_SIGMA))))
+      return m.set(ADG_EINVAL, "primitive %d: a transform applies to sigma-form boxes, circles, "
+                               "polygons and polar shapes", p);
+    if (xf && fabs(G.dx - G.dy) > 1e-12 * G.dx)
+      return m.set(ADG_EINVAL, "primitive %d: a transformed primitive needs dx == dy", p);
     if (s < 0 || s > 4) return m.set(ADG_EINVAL, "primitive %d: sigma kind %d unknown", p, s);
     if (!(D->prim_kr[p] > 0) || !fin(D->prim_kr[p]))
       return m.set(ADG_EINVAL, "primitive %d: kr must be positive", p);
@@ -182,14 +190,22 @@ struct SlotTables {
   int nact_table, nrefs, auxd_n, auxf_n;
 };
 
-inline int aux_doubles(int kind, int nq) {
+inline int aux_doubles(int kind, int nq, int flags = 0) {
+  if (flags & ADG_XFORM) {  // see kXformHead
+    const int nb = nq - 5;
+    if (kind == ADG_PRIM_BOX) return kXformHead + 6;
+    if (kind == ADG_PRIM_CIRCLE) return kXformHead + 3;
+    if (kind == ADG_PRIM_POLAR) return kXformHead + nb - 2;  // cx, cy, R0, c_n, s_n
+    return kXformHead + 1 + (nb - 2);                       // polygon: sign, vertices
+  }
   const int N = vertices_of(kind, nq);
   if (kind == ADG_PRIM_GRAPH) return 3 * N;    // X, Y, 1/dX
   if (kind == ADG_PRIM_POLYGON) return 6 * N;  // X, Y, nx, ny, c, 1/L
   return 0;
 }
 
-inline int aux_floats(int kind, int nq) {
+inline int aux_floats(int kind, int nq, int flags = 0) {
+  if (flags & ADG_XFORM) return 0;
   if (kind == ADG_PRIM_POLAR) return 2 * (nq - 4);  // R0, c_n, s_n (cells) as hi + lo pairs
   if (kind == ADG_PRIM_GRAPH) return vertices_of(kind, nq);
   if (kind == ADG_PRIM_POLYGON) return kPolyEdgeFloats * vertices_of(kind, nq);
@@ -203,8 +219,8 @@ inline void build_slots(const adg_design_desc* D, SlotTables& t, int* count) {
     t.act_off[p] = na_tab;
     t.auxd_off[p] = auxd;
     t.auxf_off[p] = auxf;
-    auxd += aux_doubles(D->prim_kind[p], D->prim_nq[p]);
-    auxf += aux_floats(D->prim_kind[p], D->prim_nq[p]);
+    auxd += aux_doubles(D->prim_kind[p], D->prim_nq[p], D->prim_flags[p]);
+    auxf += aux_floats(D->prim_kind[p], D->prim_nq[p], D->prim_flags[p]);
     int na = 0;
     for (int u = 0; u < D->prim_nq[p]; ++u) {
       const int j = D->prim_q0[p] + u;
@@ -274,7 +290,11 @@ inline void set_grid(const adg_design_desc* D, int tx, int ty, int tz, int nchai
   g.nchain = nchain;
   g.nprims = D->n_prims;
   g.polar = 0;
-  for (int p = 0; p < D->n_prims; ++p) g.polar |= D->prim_kind[p] == ADG_PRIM_POLAR;
+  g.xform = 0;
+  for (int p = 0; p < D->n_prims; ++p) {
+    g.polar |= D->prim_kind[p] == ADG_PRIM_POLAR && !(D->prim_flags[p] & ADG_XFORM);
+    g.xform |= (D->prim_flags[p] & ADG_XFORM) != 0;
+  }
 }
 
 inline bool tile_ok(int tx, int ty, int tz) {
@@ -341,7 +361,131 @@ inline adg_status prepare_prims(const GridDev& g, const double d[3], const doubl
       anchor(b, R.ai[5], R.af[5]);
       cell_range(a - 0.5, b + 0.5, g.offmin[2], g.offmax[2], g.nz, vlo[2], vhi[2]);
     };
-    if (R.kind == kBox) {
+    if (R.flags & kXformFlag) {
+      // rotation / aspect transform (Sec. 4, item iii): the base evaluated at
+      // the local point u = p + S^-1 R(-theta)(r - p); geometry in FP64 cells
+      // relative to the pivot (dx == dy), see kXformHead
+      const int base = R.kind;
+      const int nb = P.nq[pi] - 5;
+      const double* X5 = Q + nb;  // px, py, theta, sx, sy
+      const double sx = X5[3], sy = X5[4];
+      if (!(sx > 0.0) || !(sy > 0.0) || !fin(sx) || !fin(sy) || !fin(X5[2]))
+        return m.set(ADG_EINVAL, "primitive %d: transform needs sx, sy > 0 and a finite angle", pi);
+      R.kind = kXform;
+      R.flags |= base << 8;
+      const double cth = cos(X5[2]), sth = sin(X5[2]);
+      const double pcx = cellc(X5[0], 0), pcy = cellc(X5[1], 1);
+      double* A = auxd + R.auxd_off;
+      A[0] = cth; A[1] = sth; A[2] = 1.0 / sx; A[3] = 1.0 / sy; A[4] = sx; A[5] = sy;
+      R.ai[0] = (int)floor(std::min(std::max(pcx, -1e8), 1e8));
+      R.ai[1] = (int)floor(std::min(std::max(pcy, -1e8), 1e8));
+      A[6] = pcx - R.ai[0];
+      A[7] = pcy - R.ai[1];
+      double* B = A + kXformHead;
+      auto lxy = [&](double v, int ax) { return (v - X5[ax]) / d[0]; };  // local cells
+      // points whose hull holds every sample where the base can be nonzero
+      double pts[2 * kMaxPolyVerts + 8];
+      int npt = 0;
+      auto square = [&](double cx, double cy, double h) {
+        const double sq[8] = {cx - h, cy - h, cx + h, cy - h, cx + h, cy + h, cx - h, cy + h};
+        for (int u = 0; u < 8; ++u) pts[npt++] = sq[u];
+      };
+      auto zext = [&](int iz0, int iz1) {  // exact z overlap (2D bases)
+        if (!(R.flags & kBoundZ)) return;
+        const double a = cellc(Q[iz0], 2), b = cellc(Q[iz1], 2);
+        anchor(a, R.ai[4], R.af[4]);
+        anchor(b, R.ai[5], R.af[5]);
+        cell_range(a - 0.5, b + 0.5, g.offmin[2], g.offmax[2], g.nz, vlo[2], vhi[2]);
+      };
+      const double big = 1e7;
+      if (base == kBox) {
+        const bool bx = R.flags & kBoundX, by = R.flags & kBoundY;
+        B[0] = bx ? lxy(Q[0], 0) : 0.0;
+        B[1] = bx ? lxy(Q[1], 0) : 0.0;
+        B[2] = by ? lxy(Q[2], 1) : 0.0;
+        B[3] = by ? lxy(Q[3], 1) : 0.0;
+        B[4] = cellc(Q[4], 2);
+        B[5] = cellc(Q[5], 2);
+        const double x0 = bx ? B[0] - beta : -big, x1 = bx ? B[1] + beta : big;
+        const double y0 = by ? B[2] - beta : -big, y1 = by ? B[3] + beta : big;
+        const double c4[8] = {x0, y0, x1, y0, x1, y1, x0, y1};
+        for (int u = 0; u < 8; ++u) pts[npt++] = c4[u];
+        if (R.flags & kBoundZ)
+          cell_range(B[4] - beta, B[5] + beta, g.offmin[2], g.offmax[2], g.nz, vlo[2], vhi[2]);
+      } else if (base == kCircle) {
+        B[0] = lxy(Q[0], 0);
+        B[1] = lxy(Q[1], 1);
+        B[2] = Q[2] / d[0];
+        square(B[0], B[1], fabs(B[2]) + beta);
+        zext(3, 4);
+      } else if (base == kPolar) {
+        const int N = (nb - 5) / 2;
+        R.naux = N;
+        B[0] = lxy(Q[0], 0);
+        B[1] = lxy(Q[1], 1);
+        B[2] = Q[2] / d[0];
+        double amp = 0.0;
+        for (int n = 1; n <= N; ++n) {
+          B[1 + 2 * n] = Q[3 + 2 * n] / d[0];
+          B[2 + 2 * n] = Q[4 + 2 * n] / d[0];
+          amp += fabs(B[1 + 2 * n]) + fabs(B[2 + 2 * n]);
+        }
+        square(B[0], B[1], std::max(B[2] + amp, 0.0) + beta);
+        zext(3, 4);
+      } else {  // polygon
+        const int N = (nb - 2) / 2;
+        R.naux = N;
+        double* V = B + 1;
+        double area2 = 0.0;
+        for (int j = 0; j < N; ++j) {
+          V[2 * j] = lxy(Q[2 + 2 * j], 0);
+          V[2 * j + 1] = lxy(Q[3 + 2 * j], 1);
+        }
+        for (int j = 0; j < N; ++j) {
+          const int j1 = (j + 1) % N;
+          area2 += V[2 * j] * V[2 * j1 + 1] - V[2 * j1] * V[2 * j + 1];
+        }
+        const double sgn = area2 >= 0.0 ? 1.0 : -1.0;
+        B[0] = sgn;
+        // the polygon grown by beta along every edge normal: its vertices are
+        // the crossings of consecutive offset edge lines n_e . x = c_e - beta
+        for (int j = 0; j < N; ++j) {
+          const int jp = (j + N - 1) % N, j1 = (j + 1) % N;
+          double nx[2], ny[2], cc[2];
+          const int es[2] = {jp, j};
+          for (int u = 0; u < 2; ++u) {
+            const int e = es[u], e1 = (e + 1) % N;
+            const double ex = V[2 * e1] - V[2 * e], ey = V[2 * e1 + 1] - V[2 * e + 1];
+            const double L = sqrt(ex * ex + ey * ey);
+            if (!(L > 0.0)) return m.set(ADG_EINVAL, "polygon %d: repeated vertex %d", pi, e);
+            nx[u] = -sgn * ey / L;
+            ny[u] = sgn * ex / L;
+            cc[u] = nx[u] * V[2 * e] + ny[u] * V[2 * e + 1] - beta;
+          }
+          const double det = nx[0] * ny[1] - ny[0] * nx[1];
+          if (fabs(det) > 1e-3) {
+            pts[npt++] = (cc[0] * ny[1] - ny[0] * cc[1]) / det;
+            pts[npt++] = (nx[0] * cc[1] - cc[0] * nx[1]) / det;
+          } else {  // nearly straight at vertex j: the vertex moved out by beta
+            pts[npt++] = V[2 * j] - beta * nx[1];
+            pts[npt++] = V[2 * j + 1] - beta * ny[1];
+          }
+          (void)j1;
+        }
+        zext(0, 1);
+      }
+      // the hull's image in world cells: r = p + R(theta) S u
+      double wx0 = 1e300, wx1 = -1e300, wy0 = 1e300, wy1 = -1e300;
+      for (int u = 0; u < npt; u += 2) {
+        const double ux = sx * pts[u], uy = sy * pts[u + 1];
+        const double wx = pcx + cth * ux - sth * uy, wy = pcy + sth * ux + cth * uy;
+        wx0 = std::min(wx0, wx); wx1 = std::max(wx1, wx);
+        wy0 = std::min(wy0, wy); wy1 = std::max(wy1, wy);
+      }
+      cell_range(wx0, wx1, g.offmin[0], g.offmax[0], g.nx, vlo[0], vhi[0]);
+      cell_range(wy0, wy1, g.offmin[1], g.offmax[1], g.ny, vlo[1], vhi[1]);
+      for (int a = 0; a < 3; ++a) { plo[a] = vlo[a]; phi[a] = vhi[a]; }
+    } else if (R.kind == kBox) {
       for (int ax = 0; ax < 3; ++ax) {
         if (!(R.flags & (1 << ax))) continue;
         const double a = cellc(Q[2 * ax], ax), b = cellc(Q[2 * ax + 1], ax);

@@ -34,11 +34,20 @@ constexpr int kPoolSpare = 192;
 constexpr int kLeafTabBytes = 80;
 constexpr size_t kTapeBlockFloats = (size_t)kMaxOps * kBlock;  // global tape per VJP block
 
-enum : int32_t { kBox = 0, kCircle = 1, kPolygon = 2, kGraph = 3, kPolar = 4 };
+enum : int32_t { kBox = 0, kCircle = 1, kPolygon = 2, kGraph = 3, kPolar = 4,
+                 kXform = 5 /* a box (sigma form), circle, polygon or polar shape under a
+                               rotation / aspect transform; base kind in flags bits 8..11 */ };
 constexpr int kMaxPolarHarm = 32;  // Fourier harmonics of one Polar2D boundary
 enum : int32_t { kLinear = 0, kSigmoid = 1, kQuadratic = 2, kSin = 3, kErf = 4 };
 enum : int32_t { kBoundX = 1, kBoundY = 2, kBoundZ = 4, kRectSigma = 8, kGraphAbove = 16,
-                 kPolyRigid = 32 /* every vertex x (y) is the same scalar of one parameter */ };
+                 kPolyRigid = 32 /* every vertex x (y) is the same scalar of one parameter */,
+                 kXformFlag = 64 /* ADG_XFORM: the last five scalars are px, py, theta, sx, sy */ };
+// FP64 record of a transformed primitive in auxd: cos theta, sin theta, 1/sx,
+// 1/sy, sx, sy, the pivot's fractional cell parts (x, y), then the base
+// geometry in cells relative to the pivot (local frame): box x0, x1, y0, y1
+// and z0, z1 (grid cells); circle cx, cy, R; polar cx, cy, R0, c_1, s_1, ...;
+// polygon the winding sign, then x_1, y_1, ...
+constexpr int kXformHead = 8;
 // chained (binary) design program, one int32 word per op: (code << 24) | arg
 enum : int32_t { cPush = 0, cUnion = 1, cInter = 2, cDiff = 3 };
 // folded per-tile program, one uint16 per op: code | a << 2 | b << 9 (code 2
@@ -68,6 +77,7 @@ struct GridDev {
   int nchain;
   int nprims;
   int polar;  // some primitive is Polar2D (its gradient runs on k_vjp_polar)
+  int xform;  // some primitive is transformed (k_build_x and k_vjp_polar)
 };
 
 // One primitive after the parameter map, in cell units of each axis:
@@ -286,6 +296,7 @@ struct JobTotals {
   int* work;
   int fill_warps;  // build: warps per block streaming constant tiles (1 .. kMaxFillWarps)
   int polar;       // some job's design has Polar2D primitives: the VJP is k_vjp_polar
+  int xform;       // some job's design has transformed primitives: k_build_x, k_vjp_polar
 };
 
 constexpr int kMaxJobs = 1024;  // jobs in one table (one batch)
@@ -302,7 +313,7 @@ cudaError_t launch_finalize(const Job* jobs, const JobTotals& t, cudaStream_t s)
 cudaError_t launch_dense(const DenseArgs& a, int sms, cudaStream_t s);
 // Shared-memory limits of the kernels; call once per device before any capture.
 cudaError_t init_kernel_attributes();
-int build_blocks_per_sm(int njobs, int fill_warps);
+int build_blocks_per_sm(int njobs, int fill_warps, bool xform);
 int vjp_blocks_per_sm(int njobs, bool polar);
 void set_last_error(const char* msg);  // the thread-local text of adg_last_error()
 

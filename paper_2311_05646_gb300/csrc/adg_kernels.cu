@@ -282,8 +282,181 @@ __device__ __noinline__ float poly_value(const PrimRec& P, const Cell& c, const 
   return prod;
 }
 
+// ---- rotation / aspect transforms (Sec. 4, item iii) -----------------------------
+// A transformed primitive (kXform; base kind in flags bits 8..11) is its base
+// evaluated at the local point u = p + S^-1 R(-theta)(r - p), with its
+// geometry in FP64 cells relative to the pivot (auxd, see kXformHead).  The
+// local point and every distance are FP64 (a sample far from the pivot must
+// keep sub-1e-7-cell accuracy); sigma and the products are fp32.  With
+// derivatives, add(key, v, unit) receives d s / d q_key per cell (unit 0: x /
+// y cells, 2: z cells, 3: dimensionless), keys in description order -- the
+// base scalars, then px, py, theta, sx, sy through the spatial gradient
+// grad_u s (minus the derivative w.r.t. a rigid translation of the shape).
+__device__ __forceinline__ int xform_base(const PrimRec& P) { return (P.flags >> 8) & 15; }
+
+struct NoAdd {
+  __device__ __forceinline__ void operator()(int, float, int) const {}
+};
+
+template <bool kD, class Add>
+__device__ __forceinline__ float xform_core(const PrimRec& P, const Cell& c, const double* auxd,
+                                            const Add& add) {
+  const double* A = auxd + P.auxd_off;
+  const double* B = A + kXformHead;
+  const double wx = (double)(c.i - P.ai[0]) + ((double)c.ox - A[6]);  // r - p, cells
+  const double wy = (double)(c.j - P.ai[1]) + ((double)c.oy - A[7]);
+  const double vx = A[0] * wx + A[1] * wy, vy = A[0] * wy - A[1] * wx;  // R(-theta)(r - p)
+  const double ux = vx * A[2], uy = vy * A[3];                            // local, rel. pivot
+  const int base = xform_base(P);
+  const float kr = P.kr;
+  double gx = 0.0, gy = 0.0;  // grad_u s (per local cell)
+  int nb = 0;
+  float s;
+  if (base == kBox) {  // the paper's Rect form per bounded axis, z untransformed
+    nb = 6;
+    float f[3] = {1.f, 1.f, 1.f}, fa[3] = {0.f, 0.f, 0.f}, fb[3] = {0.f, 0.f, 0.f};
+    const double pos[3] = {ux, uy, (double)c.k + (double)c.oz};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      if (!(P.flags & (1 << ax))) continue;
+      float d1, d2;
+      const float s1 = sigma_f(P.sigma, kr * (float)(pos[ax] - B[2 * ax]), d1);
+      const float s2 = sigma_f(P.sigma, kr * (float)(B[2 * ax + 1] - pos[ax]), d2);
+      f[ax] = s1 * s2;
+      fa[ax] = -kr * d1 * s2;
+      fb[ax] = s1 * kr * d2;
+    }
+    s = f[0] * f[1] * f[2];
+    if (kD) {
+      const float o0 = f[1] * f[2], o1 = f[0] * f[2], o2 = f[0] * f[1];
+      add(0, fa[0] * o0, 0);
+      add(1, fb[0] * o0, 0);
+      add(2, fa[1] * o1, 0);
+      add(3, fb[1] * o1, 0);
+      add(4, fa[2] * o2, 2);
+      add(5, fb[2] * o2, 2);
+      gx = -(double)((fa[0] + fb[0]) * o0);
+      gy = -(double)((fa[1] + fb[1]) * o1);
+    }
+  } else {
+    float dz0 = 0.f, dz1 = 0.f;
+    const float zf = zfactor(P, c, dz0, dz1);
+    if (base == kCircle || base == kPolar) {
+      const double dx = ux - B[0], dy = uy - B[1];
+      const double r = sqrt(dx * dx + dy * dy);
+      double Rt = B[2], dR = 0.0, cth = 1.0, sth = 0.0;
+      const int N = base == kPolar ? P.naux : 0;
+      nb = base == kPolar ? 5 + 2 * N : 5;
+      if (r > 0.0) { cth = dx / r; sth = dy / r; }
+      double cn = cth, sn = sth;
+      for (int n = 1; n <= N; ++n) {
+        Rt += B[1 + 2 * n] * cn + B[2 + 2 * n] * sn;
+        dR += n * (B[2 + 2 * n] * cn - B[1 + 2 * n] * sn);
+        const double c2 = cn * cth - sn * sth, s2 = sn * cth + cn * sth;
+        cn = c2;
+        sn = s2;
+      }
+      float ds;
+      const float sg = sigma_f(P.sigma, kr * (float)(Rt - r), ds);
+      s = sg * zf;
+      if (kD) {
+        const float gg = kr * ds * zf;  // d s / d (R(theta) - r)
+        float dcx = 0.f, dcy = 0.f;
+        if (r > 0.0) {
+          dcx = gg * (float)(cth + dR * sth / r);
+          dcy = gg * (float)(sth - dR * cth / r);
+        }
+        add(0, dcx, 0);
+        add(1, dcy, 0);
+        add(2, gg, 0);
+        add(3, sg * dz0, 2);
+        add(4, sg * dz1, 2);
+        cn = cth;
+        sn = sth;
+        for (int n = 1; n <= N; ++n) {
+          add(3 + 2 * n, gg * (float)cn, 0);
+          add(4 + 2 * n, gg * (float)sn, 0);
+          const double c2 = cn * cth - sn * sth, s2 = sn * cth + cn * sth;
+          cn = c2;
+          sn = s2;
+        }
+        gx = -(double)dcx;
+        gy = -(double)dcy;
+      }
+    } else {  // polygon: product over edges of sigma of the inward distance
+      const int N = P.naux;
+      nb = 2 + 2 * N;
+      const double sgn = B[0];
+      const double* V = B + 1;
+      float prod = 1.f, ds;
+      int nzero = 0;
+      if (zf != 0.f) {
+        for (int e = 0; e < N; ++e) {
+          const int e1 = e + 1 == N ? 0 : e + 1;
+          const double ex = V[2 * e1] - V[2 * e], ey = V[2 * e1 + 1] - V[2 * e + 1];
+          const double L = sqrt(ex * ex + ey * ey);
+          const double dist = sgn * (ex * (uy - V[2 * e + 1]) - ey * (ux - V[2 * e])) / L;
+          const float se = sigma_f(P.sigma, kr * (float)dist, ds);
+          if (se == 0.f) { if (++nzero > 1) break; }
+          else prod *= se;
+        }
+      }
+      s = (zf != 0.f && nzero == 0) ? prod * zf : 0.f;
+      if (kD) {
+        const float inplane = (zf != 0.f && nzero == 0) ? prod : 0.f;
+        add(0, inplane * dz0, 2);
+        add(1, inplane * dz1, 2);
+        const bool live = zf != 0.f && nzero <= 1;
+        for (int e = 0; e < N; ++e) {
+          const int e1 = e + 1 == N ? 0 : e + 1;
+          float ge = 0.f;
+          double ex = 0.0, ey = 0.0, L = 1.0, rx = 0.0, ry = 0.0, cross = 0.0;
+          if (live) {
+            ex = V[2 * e1] - V[2 * e];
+            ey = V[2 * e1 + 1] - V[2 * e + 1];
+            L = sqrt(ex * ex + ey * ey);
+            rx = ux - V[2 * e];
+            ry = uy - V[2 * e + 1];
+            cross = ex * ry - ey * rx;
+            const float se = sigma_f(P.sigma, kr * (float)(sgn * cross / L), ds);
+            const float other = nzero == 0 ? prod / se : (se == 0.f ? prod : 0.f);
+            ge = kr * ds * other * zf;  // d s / d dist_e
+          }
+          // d dist_e / d (x_e, y_e, x_e1, y_e1) (as the oracle's Poly2D)
+          const double il = 1.0 / L, cl = cross * il * il * il;
+          add(2 + 2 * e, ge * (float)(sgn * ((ey - ry) * il + cl * ex)), 0);
+          add(3 + 2 * e, ge * (float)(sgn * ((rx - ex) * il + cl * ey)), 0);
+          add(2 + 2 * e1, ge * (float)(sgn * (ry * il - cl * ex)), 0);
+          add(3 + 2 * e1, ge * (float)(sgn * (-rx * il - cl * ey)), 0);
+          gx += (double)ge * (-sgn * ey * il);
+          gy += (double)ge * (sgn * ex * il);
+        }
+      }
+    }
+  }
+  if (kD) {  // pivot, angle and aspect through grad_u s
+    const double cth = A[0], sth = A[1], isx = A[2], isy = A[3];
+    add(nb, (float)(gx * (1.0 - cth * isx) + gy * (sth * isy)), 0);
+    add(nb + 1, (float)(gx * (-sth * isx) + gy * (1.0 - cth * isy)), 0);
+    add(nb + 2, (float)(gx * ((-sth * wx + cth * wy) * isx) + gy * ((-cth * wx - sth * wy) * isy)), 3);
+    add(nb + 3, (float)(gx * (-vx * isx * isx)), 3);
+    add(nb + 4, (float)(gy * (-vy * isy * isy)), 3);
+  }
+  return s;
+}
+
+__device__ __noinline__ float xform_value(const PrimRec& P, const Cell& c, const double* auxd) {
+  return xform_core<false>(P, c, auxd, NoAdd{});
+}
+
+// kX: the job table may hold transformed primitives (the kernels compiled
+// for such tables; the others carry no transform code at all).
+template <bool kX = false>
 __device__ __forceinline__ float leaf_value(const PrimRec& P, const Cell& c, const float* auxf,
                                             const double* auxd) {
+  if constexpr (kX) {
+    if (P.kind == kXform) return xform_value(P, c, auxd);
+  }
   float ds;
   if (P.kind == kBox) {
     float f[3], fa[3], fb[3];
@@ -372,6 +545,7 @@ __device__ __forceinline__ int leaf_pairs(const PrimRec& P, const Cell& c, float
   const int* actp = act + P.act_off;
   const float* actcp = actc + P.act_off;
   int n = 0;
+  if (P.kind == kXform) return n;  // every scalar goes through xform_accumulate
   if (P.kind == kBox) {
     float f[3], fa[3], fb[3];
     box_axes(P, c, f, fa, fb);
@@ -434,6 +608,7 @@ __device__ __forceinline__ int cls_sigma(float a, float b, float beta, float lo,
 
 __device__ __forceinline__ int classify(const PrimRec& P, const float lo[3], const float hi[3],
                                         const double* auxd, const float* auxf) {
+  if (P.kind == kXform) return cBND;  // inside its value tile box: evaluated per sample
   int z = cIN;
   if (P.kind != kBox && (P.flags & kBoundZ))
     z = cls_exact(P.ai[4], P.af[4], P.ai[5], P.af[5], lo[2], hi[2]);
@@ -735,10 +910,44 @@ __device__ __forceinline__ void polar_accumulate(const PrimRec& P, const Cell& c
 // The VJP's call for the kinds whose scalars are not all keyed, in designs
 // with Polar2D primitives: polygon vertices and every Polar2D scalar (other
 // designs call poly_accumulate directly, so their sample loop is unchanged).
+// A transformed primitive's terms at one sample (every scalar, key order,
+// from xform_core) times a, to physical units; one warp reduction per
+// driven slot, merged by the same two-entry cache as the polygon's.
+__device__ __forceinline__ void xform_accumulate(const PrimRec& P, const Cell& c, float a,
+                                                 const GridDev& g, const int* act,
+                                                 const float* actc, const double* auxd,
+                                                 float* acc, float* cmp, int lane) {
+  const int* actp = act + P.act_off;
+  const float* actcp = actc + P.act_off;
+  int cs0 = -1, cs1 = -1;
+  float cv0 = 0.f, cv1 = 0.f;
+  const float unit[4] = {g.invd[0] * a, g.invd[1] * a, g.invd[2] * a, a};
+  auto add = [&](int key, float v, int u) {
+    const int slot = actp[key];
+    if (slot < 0) return;
+    v *= unit[u] * actcp[key];
+    if (slot == cs0) cv0 += v;
+    else if (slot == cs1) cv1 += v;
+    else {
+      flush_slot(cs0, cv0, acc, cmp, lane);
+      cs0 = cs1; cv0 = cv1;
+      cs1 = slot; cv1 = v;
+    }
+  };
+  xform_core<true>(P, c, auxd, add);
+  flush_slot(cs0, cv0, acc, cmp, lane);
+  flush_slot(cs1, cv1, acc, cmp, lane);
+}
+
+// The VJP's one out-of-line call for the kinds whose scalars are not all
+// keyed: polygon vertices, every Polar2D scalar (job tables with Polar2D
+// only) and every scalar of a transformed primitive.
 __device__ __noinline__ void shape_accumulate(const PrimRec& P, const Cell& c, float a,
                                               const GridDev& g, const int* act, const float* actc,
-                                              const float* auxf, float* acc, float* cmp, int lane) {
+                                              const float* auxf, const double* auxd, float* acc,
+                                              float* cmp, int lane) {
   if (P.kind == kPolar) polar_accumulate(P, c, a, g, act, actc, auxf, acc, cmp, lane);
+  else if (P.kind == kXform) xform_accumulate(P, c, a, g, act, actc, auxd, acc, cmp, lane);
   else poly_accumulate(P, c, a, g, act, actc, auxf, acc, cmp, lane);
 }
 
@@ -1155,7 +1364,7 @@ __device__ __forceinline__ float plane_value(const PrimRec& P, const Cell& c, co
     return sigma_f(P.sigma, P.kr * graph_dist(P, c, auxf, auxd, seg, t), ds);
   }
   if (P.kind == kPolar) return sigma_f(P.sigma, P.kr * polar_dist(P, c, auxf), ds);
-  return poly_value(P, c, auxf);
+  return poly_value(P, c, auxf);  // (transformed leaves are never tabled)
 }
 
 // All threads: fill the planned tables of the tile with origin (X0, Y0, Z0).
@@ -1430,7 +1639,7 @@ struct SampleOff {
 
 // The same program on a stack in shared memory (column of stride kBlock), for
 // programs deeper than the register stack; depth <= kMaxDepth by construction.
-template <int LOGIC>
+template <int LOGIC, bool kX>
 __device__ __forceinline__ float eval_stack_smem(const int4* desc, int nops, const float* tab,
                                                  const PrimRec* sl, const SampleOff& o, int4 p,
                                                  const GridDev& g, const float* auxf,
@@ -1446,7 +1655,7 @@ __device__ __forceinline__ float eval_stack_smem(const int4* desc, int nops, con
         v = tab[d.y + o.xy] * tab[d.w + o.z];
       } else {
         const Cell c{p.x, p.y, p.z, g.off[p.w][0], g.off[p.w][1], g.off[p.w][2]};
-        v = leaf_value(sl[d.y], c, auxf, auxd);
+        v = leaf_value<kX>(sl[d.y], c, auxf, auxd);
       }
       if (sp < kMaxDepth) stk[(sp++) * kBlock] = v;
     } else if (sp >= 1) {
@@ -1465,7 +1674,7 @@ __device__ __forceinline__ float eval_stack_smem(const int4* desc, int nops, con
   return sp >= 1 ? stk[0] : 0.f;
 }
 
-template <int LOGIC>
+template <int LOGIC, bool kX>
 __device__ __forceinline__ void eval_stack2(const int4* desc, int nops, const float* tab,
                                             const PrimRec* sl, const SampleOff& o0,
                                             const SampleOff& o1, int4 p0, int4 p1,
@@ -1486,8 +1695,8 @@ __device__ __forceinline__ void eval_stack2(const int4* desc, int nops, const fl
       } else {  // cells built here only: the direct path takes them by reference
         const Cell c0{p0.x, p0.y, p0.z, g.off[p0.w][0], g.off[p0.w][1], g.off[p0.w][2]};
         const Cell c1{p1.x, p1.y, p1.z, g.off[p1.w][0], g.off[p1.w][1], g.off[p1.w][2]};
-        v0 = leaf_value(sl[d.y], c0, auxf, auxd);
-        v1 = leaf_value(sl[d.y], c1, auxf, auxd);
+        v0 = leaf_value<kX>(sl[d.y], c0, auxf, auxd);
+        v1 = leaf_value<kX>(sl[d.y], c1, auxf, auxd);
       }
       a3 = a2; a2 = a1; a1 = a0; a0 = v0;
       b3 = b2; b2 = b1; b1 = b0; b0 = v1;
@@ -1539,7 +1748,7 @@ __device__ __forceinline__ int build_plan_warp(const TileProg* P, const Job& J, 
     tbase += __shfl_sync(0xffffffffu, inc, 31);
     if (!on) continue;
     int4 v = make_int4(-1, -1, -1, -1), d = make_int4(-1, -1, -1, 0);
-    if (off + need <= cap) {
+    if (off + need <= cap && kind != kXform) {  // transformed leaves are evaluated directly
       if (box) { v.x = off; v.y = v.x + C * TX; v.z = v.y + C * TY; }
       else { v.w = off; v.z = v.w + C * TX * TY; }
       d.w |= tOK;
@@ -1596,6 +1805,7 @@ __device__ __forceinline__ bool band_sync_and(bool p) {
 }
 
 // One band tile of the build (the kBlock threads of the band warps).
+template <bool kX>
 __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, int njobs,
                                                 const int* spre, int gi_, unsigned char* smem) {
   float* stk = reinterpret_cast<float*>(smem);  // stack of the deep-program fallback
@@ -1674,9 +1884,9 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
         }
         float v0, v1;
         if (g.logic == 0)
-          eval_stack2<0>(desc, nops, tp.tab, tp.sl, o[0], o[1], pc[0], pc[1], g, J.auxf, J.auxd, v0, v1);
+          eval_stack2<0, kX>(desc, nops, tp.tab, tp.sl, o[0], o[1], pc[0], pc[1], g, J.auxf, J.auxd, v0, v1);
         else
-          eval_stack2<1>(desc, nops, tp.tab, tp.sl, o[0], o[1], pc[0], pc[1], g, J.auxf, J.auxd, v0, v1);
+          eval_stack2<1, kX>(desc, nops, tp.tab, tp.sl, o[0], o[1], pc[0], pc[1], g, J.auxf, J.auxd, v0, v1);
         store(pc[0].x - X0, pc[0].y - Y0, pc[0].z - Z0, pc[0].w, v0);
         store(pc[1].x - X0, pc[1].y - Y0, pc[1].z - Z0, pc[1].w, v1);
       }
@@ -1689,8 +1899,8 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
                          (((c << g.ly) + y) << g.lx) + x};
       const int4 pc = make_int4(X0 + x, Y0 + y, Z0 + z, c);
       const float v = g.logic == 0
-          ? eval_stack_smem<0>(desc, nops, tp.tab, tp.sl, so, pc, g, J.auxf, J.auxd, stk + tid)
-          : eval_stack_smem<1>(desc, nops, tp.tab, tp.sl, so, pc, g, J.auxf, J.auxd, stk + tid);
+          ? eval_stack_smem<0, kX>(desc, nops, tp.tab, tp.sl, so, pc, g, J.auxf, J.auxd, stk + tid)
+          : eval_stack_smem<1, kX>(desc, nops, tp.tab, tp.sl, so, pc, g, J.auxf, J.auxd, stk + tid);
       store(x, y, z, c, v);
     }
   }
@@ -1701,9 +1911,11 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
 // their factor tables, the folded program run at every sample (two samples
 // per thread, register stack; a shared-memory stack for deeper programs) --
 // and the streaming fill of the constant tiles.
-// 80 registers: four blocks of 160 or 192 threads per SM
-__global__ void __maxnreg__(80) k_build(const Job* __restrict__ jobs, int njobs, int nfill,
-                                        int* work) {
+// 80 registers: four blocks of 160 or 192 threads per SM.  kX: compiled twice,
+// k_build_x for job tables with transformed primitives (FP64 evaluation)
+template <bool kX>
+__device__ __forceinline__ void build_body(const Job* __restrict__ jobs, int njobs, int nfill,
+                                           int* work) {
   extern __shared__ __align__(16) unsigned char smem[];
   // layout: deep-program stack, pool, descriptors, four words (depth, z flag,
   // next fill unit, next band tile), job prefix
@@ -1738,7 +1950,7 @@ __global__ void __maxnreg__(80) k_build(const Job* __restrict__ jobs, int njobs,
         have = gi_ + 2 * G < total;
         if (have) nxt = G + atomicAdd(work + 2, 1);
       }
-      build_band_tile(jobs, njobs, spre, gi_, smem);  // starts with a band barrier
+      build_band_tile<kX>(jobs, njobs, spre, gi_, smem);  // starts with a band barrier
     }
     if (tid == 0) {
       __threadfence();
@@ -1757,6 +1969,16 @@ __global__ void __maxnreg__(80) k_build(const Job* __restrict__ jobs, int njobs,
     if (fu >= nfill) break;
     fill_rows(jobs, job_of(rpre, njobs, fu), fu, lane);
   }
+}
+
+__global__ void __maxnreg__(80) k_build(const Job* __restrict__ jobs, int njobs, int nfill,
+                                        int* work) {
+  build_body<false>(jobs, njobs, nfill, work);
+}
+
+__global__ void __maxnreg__(80) k_build_x(const Job* __restrict__ jobs, int njobs, int nfill,
+                                          int* work) {
+  build_body<true>(jobs, njobs, nfill, work);
 }
 
 __device__ __forceinline__ void neumaier(float& s, float& c, float v) {
@@ -1984,7 +2206,7 @@ __device__ __forceinline__ void vjp_plan_warp(const TileProg* P, const Job& J, i
     sb += __shfl_sync(0xffffffffu, ninc, 31);
     if (!on) continue;
     int4 v = make_int4(-1, -1, -1, -1), d = make_int4(-1, -1, -1, 0);
-    if (off + need <= cap) {
+    if (off + need <= cap && kind != kXform) {  // transformed leaves are evaluated directly
       if (box) {
         v.x = off; v.y = v.x + C * TX; v.z = v.y + C * TY;
         d.x = v.z + C * TZ; d.y = d.x + 2 * C * TX; d.z = d.y + 2 * C * TY;
@@ -2052,7 +2274,7 @@ __device__ __forceinline__ void logic_bwd(int code, float a, float b, float& da,
 // Forward tape (value of every op at the sample), then the reverse sweep
 // through the logic (Eqs. AD / jaceps): afterwards tap[pos] holds d fill / d
 // value(pos).  tap: this thread's column, stride kBlock.
-template <int LOGIC>
+template <int LOGIC, bool kX>
 __device__ __forceinline__ void vjp_tape(const int4* desc, int nops, const float* tab,
                                          const SampleOff& o, const PrimRec* sl, int4 pc,
                                          const GridDev& g, const float* auxf, const double* auxd,
@@ -2066,7 +2288,7 @@ __device__ __forceinline__ void vjp_tape(const int4* desc, int nops, const float
       v = tab[d.y + o.xy] * tab[d.w + o.z];
     } else if (d.x == dDirect) {
       const Cell c{pc.x, pc.y, pc.z, g.off[pc.w][0], g.off[pc.w][1], g.off[pc.w][2]};
-      v = leaf_value(sl[d.y], c, auxf, auxd);
+      v = leaf_value<kX>(sl[d.y], c, auxf, auxd);
     } else if (d.x == dLogic + fCompl) {
       v = 1.f - tap[d.y * kBlock];
     } else {
@@ -2370,7 +2592,7 @@ __device__ __forceinline__ void vjp_body(const Job* __restrict__ jobs, int njobs
           const int4 pc = make_int4(X0 + x, Y0 + y, Z0 + z, c);
           const SampleOff so{(c << g.lx) + x, (c << g.ly) + y, (c << g.lz) + z,
                              (((c << g.ly) + y) << g.lx) + x};  // tables keep full TY, TZ
-          vjp_tape<kLogic>(desc, nops, tab, so, sl, pc, g, J.auxf, J.auxd, tap);
+          vjp_tape<kLogic, kPolarT>(desc, nops, tab, so, sl, pc, g, J.auxf, J.auxd, tap);
           const Cell cc{pc.x, pc.y, pc.z, g.off[c][0], g.off[c][1], g.off[c][2]};
           const TileLoc q{x, y, z, c, TX, TY, TZ};
           // primitives: d s / d q times the seed
@@ -2413,8 +2635,8 @@ __device__ __forceinline__ void vjp_body(const Job* __restrict__ jobs, int njobs
               n = leaf_pairs(sl[lf], cc, an, g, J.act, J.actc, J.auxf, J.auxd, pk + tid, pv + tid);
             warp_accumulate(n, 0, pk + tid, pv + tid, la, lc, lane);
             if constexpr (kPolarT) {
-              if (kind == kPolygon || kind == kPolar)
-                shape_accumulate(sl[lf], cc, an, g, J.act, J.actc, J.auxf, la, lc, lane);
+              if (kind == kPolygon || kind == kPolar || kind == kXform)
+                shape_accumulate(sl[lf], cc, an, g, J.act, J.actc, J.auxf, J.auxd, la, lc, lane);
             } else {
               if (kind == kPolygon)
                 poly_accumulate(sl[lf], cc, an, g, J.act, J.actc, J.auxf, la, lc, lane);
@@ -2630,6 +2852,9 @@ cudaError_t init_kernel_attributes() {
     e = cudaFuncSetAttribute(k_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)build_smem(kMaxJobs));
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_build_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)build_smem(kMaxJobs));
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)vjp_smem(kMaxJobs));
   if (e == cudaSuccess)
@@ -2640,14 +2865,18 @@ cudaError_t init_kernel_attributes() {
 
 // Resident blocks per SM for a job table of njobs jobs (the job prefix in
 // shared memory grows with it), cached per job count.
-int build_blocks_per_sm(int njobs, int fill_warps) {
-  static int v[kMaxFillWarps][kMaxJobs + 1] = {};
+int build_blocks_per_sm(int njobs, int fill_warps, bool xform) {
+  static int v[2][kMaxFillWarps][kMaxJobs + 1] = {};
   njobs = std::min(std::max(njobs, 1), kMaxJobs);
   fill_warps = std::min(std::max(fill_warps, 1), kMaxFillWarps);
-  int& r = v[fill_warps - 1][njobs];
+  int& r = v[xform ? 1 : 0][fill_warps - 1][njobs];
   if (!r) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_build, kBlock + 32 * fill_warps,
-                                                  build_smem(njobs));
+    if (xform)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_build_x, kBlock + 32 * fill_warps,
+                                                    build_smem(njobs));
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_build, kBlock + 32 * fill_warps,
+                                                    build_smem(njobs));
     if (r < 1) r = 1;
   }
   return r;
@@ -2675,17 +2904,23 @@ cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream
 
 cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s) {
   if (!t.work || t.fill_warps < 1 || t.fill_warps > kMaxFillWarps) return cudaErrorInvalidValue;
-  const int grid = sms * build_blocks_per_sm(t.njobs, t.fill_warps);
-  k_build<<<grid, kBlock + 32 * t.fill_warps, build_smem(t.njobs), s>>>(jobs, t.njobs,
-                                                                       t.fill_blocks, t.work);
+  const int grid = sms * build_blocks_per_sm(t.njobs, t.fill_warps, t.xform != 0);
+  if (t.xform)
+    k_build_x<<<grid, kBlock + 32 * t.fill_warps, build_smem(t.njobs), s>>>(jobs, t.njobs,
+                                                                           t.fill_blocks, t.work);
+  else
+    k_build<<<grid, kBlock + 32 * t.fill_warps, build_smem(t.njobs), s>>>(jobs, t.njobs,
+                                                                         t.fill_blocks, t.work);
   return cudaGetLastError();
 }
 
 cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, float* gtape,
                        int gtape_blocks, cudaStream_t s) {
-  const int grid = std::min(sms * vjp_blocks_per_sm(t.njobs, t.polar != 0), gtape_blocks);
+  // Polar2D and transformed primitives: the VJP compiled with their code
+  const bool shapes = t.polar || t.xform;
+  const int grid = std::min(sms * vjp_blocks_per_sm(t.njobs, shapes), gtape_blocks);
   if (grid < 1 || !gtape || !t.work) return cudaErrorInvalidValue;
-  if (t.polar)
+  if (shapes)
     k_vjp_polar<<<grid, kBlock, vjp_smem(t.njobs), s>>>(jobs, t.njobs, err, gtape, t.work);
   else
     k_vjp<<<grid, kBlock, vjp_smem(t.njobs), s>>>(jobs, t.njobs, err, gtape, t.work);

@@ -129,7 +129,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   host::SlotTables st{H.act, H.nact, H.act_off, H.actc, H.ref_off, H.ref_prim, H.ref_qa,
                       H.ref_coeff, H.auxd_off, H.auxf_off, 0, 0, 0, 0};
   for (int p = 0; p < D->n_prims; ++p)
-    if (host::aux_doubles(D->prim_kind[p], D->prim_nq[p]) > 6 * kNAMaxQ)
+    if (host::aux_doubles(D->prim_kind[p], D->prim_nq[p], D->prim_flags[p]) > 6 * kNAMaxQ)
       return na_fail(ADG_EINVAL, "primitive %d has too many vertices", p);
   host::build_slots(D, st, H.count);
   if (st.auxd_n > 6 * kNAMaxQ || st.auxf_n > 6 * kNAMaxQ)
@@ -276,6 +276,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   t.params = D->n_params;
   t.work = d_cnt + 12;
   t.polar = g.polar;
+  t.xform = g.xform;
   NACU(launch_bin(d_job, t, d_err, s));
   NACU(launch_vjp(d_job, t, d_err, sms, d_gtape, sms, s));
   NACU(launch_finalize(d_job, t, s));
