@@ -1382,38 +1382,44 @@ __device__ __forceinline__ void tables_fill(const PrimRec* sl, int nleaf, const 
   const int TX = 1 << g.lx, TY = 1 << g.ly, TZ = 1 << g.lz, C = g.C;
   okY = true;
   okZ = true;
+  // boxes: every (leaf, entry) pair of the tabled boxes over all the threads at
+  // once (a leaf's entries alone leave most threads idle in its last round)
+  const int tbx = C * (TX + TY + TZ);
+  for (int q = tid; q < nleaf * tbx; q += kBlock) {
+    const int l = q / tbx, e = q - l * tbx;
+    const int4 tv = lt[l].v, td = lt[l].d;
+    if ((td.w & (tOK | tBOX)) != (tOK | tBOX)) continue;
+    const PrimRec& P = sl[l];
+    // axis, component and coordinate of entry e (x block, y block, z block)
+    int ax = 0, r = e, T = TX, O = X0;
+    if (r >= C * TX) { r -= C * TX; ax = 1; T = TY; O = Y0; }
+    if (ax == 1 && r >= C * TY) { r -= C * TY; ax = 2; T = TZ; O = Z0; }
+    const int c = r / T, u = r - c * T;
+    float da, db;
+    const float f = box_axis(P, ax, O + u, g.off[c][ax], da, db);
+    const int vt = ax == 0 ? tv.x : (ax == 1 ? tv.y : tv.z);
+    tab[vt + c * T + u] = f;
+    if (derivs) {
+      const int dt = ax == 0 ? td.x : (ax == 1 ? td.y : td.z);
+      tab[dt + (2 * c) * T + u] = da;
+      tab[dt + (2 * c + 1) * T + u] = db;
+      const int k = (td.w >> (3 + 2 * ax)) & 3;
+      if (act1 && (td.w & tACT) && (((k & 1) && da != 0.f) || ((k & 2) && db != 0.f)))
+        act1[e] = 1;
+    }
+    if (ax > 0 && u > 0) {
+      float da0, db0;
+      const float f0 = box_axis(P, ax, O, g.off[c][ax], da0, db0);
+      const bool same = f == f0 && (!derivs || (da == da0 && db == db0));
+      if (ax == 1) okY &= same; else okZ &= same;
+    }
+  }
+  // the other tabled leaves: in-plane table and z factor
   for (int l = 0; l < nleaf; ++l) {
     const int4 tv = lt[l].v, td = lt[l].d;
-    if (!(td.w & tOK)) continue;
+    if ((td.w & (tOK | tBOX)) != tOK) continue;
     const PrimRec& P = sl[l];
-    if (P.kind == kBox) {
-      const int tot = C * (TX + TY + TZ);
-      for (int e = tid; e < tot; e += kBlock) {
-        // axis, component and coordinate of entry e (x block, y block, z block)
-        int ax = 0, r = e, T = TX, O = X0;
-        if (r >= C * TX) { r -= C * TX; ax = 1; T = TY; O = Y0; }
-        if (ax == 1 && r >= C * TY) { r -= C * TY; ax = 2; T = TZ; O = Z0; }
-        const int c = r / T, u = r - c * T;
-        float da, db;
-        const float f = box_axis(P, ax, O + u, g.off[c][ax], da, db);
-        const int vt = ax == 0 ? tv.x : (ax == 1 ? tv.y : tv.z);
-        tab[vt + c * T + u] = f;
-        if (derivs) {
-          const int dt = ax == 0 ? td.x : (ax == 1 ? td.y : td.z);
-          tab[dt + (2 * c) * T + u] = da;
-          tab[dt + (2 * c + 1) * T + u] = db;
-          const int k = (td.w >> (3 + 2 * ax)) & 3;
-          if (act1 && (td.w & tACT) && (((k & 1) && da != 0.f) || ((k & 2) && db != 0.f)))
-            act1[e] = 1;
-        }
-        if (ax > 0 && u > 0) {
-          float da0, db0;
-          const float f0 = box_axis(P, ax, O, g.off[c][ax], da0, db0);
-          const bool same = f == f0 && (!derivs || (da == da0 && db == db0));
-          if (ax == 1) okY &= same; else okZ &= same;
-        }
-      }
-    } else {
+    {
       const int nxy = C * TX * TY;
       for (int e = tid; e < nxy + C * TZ; e += kBlock) {
         if (e < nxy) {
