@@ -26,7 +26,9 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libadg.so")
+# ADG_LIBRARY selects another build of the same library (the ADG_DEBUG build,
+# libadg_debug.so, for the bound-check tests)
+LIB_PATH = os.environ.get("ADG_LIBRARY") or os.path.join(_HERE, "libadg.so")
 _lock = threading.Lock()
 _lib = None
 

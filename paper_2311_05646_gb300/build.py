@@ -17,6 +17,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libadg.so")
 BUILD = os.path.join(HERE, "_build")
+# The debug build (-DADG_DEBUG: bound checks in the kernels that record an
+# error bit instead of accessing out of range), built on request only.
+OUT_DEBUG = os.path.join(HERE, "libadg_debug.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 SOURCES = ["adg_api.cu", "adg_kernels.cu", "adg_noalloc.cu", "adg_topo.cu", "adg_fd.cu", "adg_levels.cu", "adg_mesh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -36,18 +40,20 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False,
+          debug: bool = False) -> str:
+    bdir, lib_out = (BUILD_DEBUG, OUT_DEBUG) if debug else (BUILD, OUT)
+    os.makedirs(bdir, exist_ok=True)
     jobs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(bdir, s.replace(".cu", ".o"))
         if force or _stale(obj, src):
-            cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
+            cmd = [nvcc(), *ARCH, *FLAGS, *(["-DADG_DEBUG"] if debug else []), "-c", src, "-o", obj]
             if ptxas_v:
                 cmd += ["-Xptxas", "-v"]
             jobs.append(cmd)
-    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
+    objs = [os.path.join(bdir, s.replace(".cu", ".o")) for s in SOURCES]
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,13 +65,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         for out in ex.map(run, jobs):
             if verbose and out.strip():
                 print(out, file=sys.stderr)
-    if jobs or not os.path.exists(OUT) or force:
-        tmp = OUT + ".tmp%d" % os.getpid()
+    if jobs or not os.path.exists(lib_out) or force:
+        tmp = lib_out + ".tmp%d" % os.getpid()
         cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-lcudart"]
         run(cmd)
-        os.replace(tmp, OUT)
-    return OUT
+        os.replace(tmp, lib_out)
+    return lib_out
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv,
+                debug="--debug" in sys.argv))

@@ -11,6 +11,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -469,6 +470,16 @@ adg_status ensure_records(adg_design* d, const double* h_params, cudaStream_t s,
   d->bins_valid = false;
   adg_status st = prepare_prims(d, h_params);
   if (st != ADG_OK) return st;
+#ifdef ADG_DEBUG
+  // Test hook of the debug build (ADG_DEBUG_PLANT=partials): the last
+  // primitive with partials is moved one entry past the design's range --
+  // still inside the buffer, which keeps at least 1024 spare entries -- so
+  // that the kernels' bound checks must catch it.
+  if (const char* pl = getenv("ADG_DEBUG_PLANT"))
+    if (!strcmp(pl, "partials"))
+      for (int p = d->n_prims - 1; p >= 0; --p)
+        if (d->h_prims[p].npb > 0) { d->h_prims[p].part_off += 1; break; }
+#endif
   if (d->counters_dirty) {
     CU(cudaMemsetAsync(d->d_counters, 0, sizeof(int) * 8, s));  // both counter sets
     d->counters_dirty = false;
@@ -511,6 +522,7 @@ adg_status ensure_partials(adg_design* d, cudaStream_t s) {
 Job design_job(adg_design* d) {
   Job J{};
   J.g = d->g;
+  J.err = d->ctx ? d->ctx->d_err : nullptr;
   J.chain = d->d_chain;
   J.prims = d->d_prims;
   J.act = d->d_act;
@@ -1510,7 +1522,8 @@ extern "C" adg_status adg_sync(adg_ctx* ctx, void* stream) {
     CU(cudaMemset(ctx->d_err, 0, sizeof(int)));
     return fail(ADG_EDEVICE,
                 "device check failed (bits 0x%x: 1 leaves/tile, 2 ops/tile, 4 depth, 8 slots/tile, "
-                "16 partial range, 32 program, 64 tile pool); use a smaller tile shape",
+                "16 partial range, 32 program, 64 tile pool, 128 debug bound check); use a "
+                "smaller tile shape",
                 e);
   }
   return ADG_OK;

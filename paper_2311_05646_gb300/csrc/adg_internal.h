@@ -62,8 +62,19 @@ enum : int32_t {
   eSlotOverflow = 8,
   ePartialRange = 16,
   eBadProgram = 32,
-  ePoolOverflow = 64
+  ePoolOverflow = 64,
+  eDebugBound = 128  // ADG_DEBUG builds: an index failed its bound check (the access was skipped)
 };
+// ADG_DEBUG builds (compiled with -DADG_DEBUG) check the indices of the
+// kernels' main global accesses -- band-tile list entries, tile programs,
+// partial sums -- against the ranges their buffers were sized for; a failed
+// check records eDebugBound in the error word and the access is skipped.
+// Release builds compile the checks away.
+#ifdef ADG_DEBUG
+#define ADG_CHECK(cond, err) ((cond) ? true : (atomicOr((err), eDebugBound), false))
+#else
+#define ADG_CHECK(cond, err) true
+#endif
 
 struct GridDev {
   int nx, ny, nz, C;
@@ -275,6 +286,7 @@ struct Job {
   float* partial;
   float* grad;
   long long partial_n;  // partials of the job (zero between calls: the finalize clears them)
+  int* err;             // the context's device error word
   int nparam;
   int param_base;  // prefix over the table (finalize)
   int tile_base;   // prefix over the table, multiple of 128 (binner blocks)

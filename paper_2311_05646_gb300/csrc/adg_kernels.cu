@@ -1301,7 +1301,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(const Job* __restrict__ job
     atomicAdd(&J.counters[2], sagg[2]);
   }
   __syncthreads();
-  if (tid < nb) J.list[sagg[3] + tid] = sband[tid];
+  if (tid < nb && ADG_CHECK(sagg[3] + tid < J.g.T, J.err)) J.list[sagg[3] + tid] = sband[tid];
 }
 
 // Threads [tid0, tid0 + nthr) of the block, one 16-byte word at a time:
@@ -1824,6 +1824,7 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
     const Job& J = jobs[jb];
     const GridDev& g = J.g;
     const int t = J.list[gi_ - spre[jb]];
+    if (!ADG_CHECK(t >= 0 && t < g.T, J.err)) return;  // uniform over the band warps
     const TileProg* P = J.progs + t;
     const int nops = P->nops, nleaf = P->nleaf;
     const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
@@ -2441,6 +2442,7 @@ __device__ __forceinline__ void vjp_body(const Job* __restrict__ jobs, int njobs
     const Job& J = jobs[jb];
     const GridDev& g = J.g;
     const int t = J.list[gi_ - spre[jb]];
+    if (!ADG_CHECK(t >= 0 && t < g.T, err)) continue;  // uniform over the block
     const TileProg* P = J.progs + t;
     const int nops = P->nops, nleaf = P->nleaf, nslot = P->nslot;
     const int tx = t % g.ntx, ty = (t / g.ntx) % g.nty, tz = t / (g.ntx * g.nty);
@@ -2683,7 +2685,8 @@ __device__ __forceinline__ void vjp_body(const Job* __restrict__ jobs, int njobs
           tz < R.pb[5]) {
         const int rel = ((tz - R.pb[4]) * (R.pb[3] - R.pb[2]) + (ty - R.pb[2])) * (R.pb[1] - R.pb[0]) +
                         (tx - R.pb[0]);
-        J.partial[(size_t)R.part_off + (size_t)qa * R.npb + rel] = tot;
+        const size_t idx = (size_t)R.part_off + (size_t)qa * R.npb + rel;
+        if (ADG_CHECK(idx < (size_t)J.partial_n, err)) J.partial[idx] = tot;
       } else if (tot != 0.f) {
         atomicOr(err, ePartialRange);
       }
@@ -2824,6 +2827,9 @@ __global__ void __launch_bounds__(128) k_finalize(const Job* __restrict__ jobs, 
   double total = 0.0;
   for (int r = J.ref_off[k]; r < J.ref_off[k + 1]; ++r) {
     const PrimRec& P = J.prims[J.ref_prim[r]];
+    if (!ADG_CHECK((size_t)P.part_off + (size_t)(J.ref_qa[r] + 1) * P.npb <= (size_t)J.partial_n,
+                   J.err))
+      continue;  // uniform over the block
     float* src = J.partial + P.part_off + (size_t)J.ref_qa[r] * P.npb;
     float s = 0.f, c = 0.f;
     // eight loads in flight per thread, summed in tile order; the nonzero

@@ -259,6 +259,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   J.counters_last = d_cnt + 8;
   J.partial = d_part;
   J.partial_n = (long long)part;
+  J.err = d_err;
   J.grad = d_grad;
   J.nparam = D->n_params;
   J.do_bin = 1;
