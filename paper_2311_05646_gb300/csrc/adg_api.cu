@@ -22,6 +22,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/adg.h"
 #include "adg_host.h"
 #include "adg_internal.h"
@@ -159,13 +161,19 @@ cudaEvent_t take_event(adg_ctx* c) {
   return e;
 }
 
-// Brackets one kernel launch with events on its stream when profiling is on.
+// Brackets one kernel launch with an NVTX range on the host (named after the
+// kernel; free when no tool is attached) and, when profiling is on, with
+// events on its stream.
+const char* const kKernelNames[ADG_K_COUNT] = {"adg/k_bin", "adg/k_build", "adg/k_vjp",
+                                               "adg/k_finalize", "adg/prepare", "adg/fill",
+                                               "adg/k_dense", "adg/k_levels"};
 struct ProfScope {
   adg_ctx* c;
   int k;
   cudaStream_t s;
   cudaEvent_t a = nullptr;
   ProfScope(adg_ctx* c_, int k_, cudaStream_t s_) : c(c_), k(k_), s(s_) {
+    nvtxRangePushA(kKernelNames[k]);
     if (c->prof) {
       a = take_event(c);
       cudaEventRecord(a, s);
@@ -177,7 +185,14 @@ struct ProfScope {
       cudaEventRecord(b, s);
       c->recs.push_back({k, a, b});
     }
+    nvtxRangePop();
   }
+};
+
+// An NVTX range over one entry point (host side).
+struct CallRange {
+  explicit CallRange(const char* name) { nvtxRangePushA(name); }
+  ~CallRange() { nvtxRangePop(); }
 };
 
 }  // namespace
@@ -331,6 +346,7 @@ void free_design(adg_design* d) {
 
 extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
                                         const adg_tile_opts* tiles, adg_design** out) {
+  CallRange nvtx_range("adg_design_create");
   if (!ctx || !D || !out) return fail(ADG_EINVAL, "adg_design_create: NULL argument");
   *out = nullptr;
   host::Msg m;
@@ -620,6 +636,7 @@ adg_status run_single_enqueue(adg_ctx* ctx, adg_design* d, bool rebin, float* d_
 // ------------------------------------------------------------------- calls --
 extern "C" adg_status adg_build_eps(adg_ctx* ctx, adg_design* d, const double* h_params,
                                     float* d_fill, float* d_eps, void* stream) {
+  CallRange nvtx_range("adg_build_eps");
   if (!ctx || !d || !d_eps) return fail(ADG_EINVAL, "adg_build_eps: NULL argument");
   CU(cudaSetDevice(ctx->device));
   return run_single(ctx, d, h_params, d_fill, d_eps, nullptr, nullptr, (cudaStream_t)stream);
@@ -628,6 +645,7 @@ extern "C" adg_status adg_build_eps(adg_ctx* ctx, adg_design* d, const double* h
 extern "C" adg_status adg_grad(adg_ctx* ctx, adg_design* d, const double* h_params,
                                const float* const d_efwd[3], const float* const d_eadj[3],
                                const float* w, float* d_grad, void* stream) {
+  CallRange nvtx_range("adg_grad");
   if (!ctx || !d || !d_efwd || !d_eadj || !w || (!d_grad && d->n_params > 0))
     return fail(ADG_EINVAL, "adg_grad: NULL argument");
   VjpArgs va{};
@@ -644,6 +662,7 @@ extern "C" adg_status adg_grad(adg_ctx* ctx, adg_design* d, const double* h_para
 
 extern "C" adg_status adg_grad_real(adg_ctx* ctx, adg_design* d, const double* h_params,
                                     const float* d_G, float* d_grad, void* stream) {
+  CallRange nvtx_range("adg_grad_real");
   if (!ctx || !d || !d_G || (!d_grad && d->n_params > 0))
     return fail(ADG_EINVAL, "adg_grad_real: NULL argument");
   VjpArgs va{};
@@ -656,6 +675,7 @@ extern "C" adg_status adg_grad_dense(adg_ctx* ctx, adg_design* d, const double* 
                                      const float* const d_efwd[3], const float* const d_eadj[3],
                                      const float* w, const float* d_fill, float* d_grad,
                                      double* d_gmat, void* stream) {
+  CallRange nvtx_range("adg_grad_dense");
   if (!ctx || !d || !d_efwd || !d_eadj || !w || !d_fill || !d_gmat || (!d_grad && d->n_params > 0))
     return fail(ADG_EINVAL, "adg_grad_dense: NULL argument");
   VjpArgs va{};
@@ -726,6 +746,7 @@ adg_status topo_args(const adg_grid* grid, const adg_topo_region* r, const float
 extern "C" adg_status adg_topo_eps(adg_ctx* ctx, const adg_grid* grid, const adg_topo_region* r,
                                    const float* d_v, double eps_l, double deps, float* d_eps,
                                    void* stream) {
+  CallRange nvtx_range("adg_topo_eps");
   if (!ctx || !d_eps) return fail(ADG_EINVAL, "adg_topo_eps: NULL argument");
   TopoArgs a;
   const adg_status st = topo_args(grid, r, d_v, "adg_topo_eps", a);
@@ -742,6 +763,7 @@ extern "C" adg_status adg_topo_grad(adg_ctx* ctx, const adg_grid* grid, const ad
                                     const float* d_v, double deps, const float* const d_efwd[3],
                                     const float* const d_eadj[3], const float* w, float* d_grad,
                                     void* stream) {
+  CallRange nvtx_range("adg_topo_grad");
   if (!ctx || !d_efwd || !d_eadj || !w || !d_grad)
     return fail(ADG_EINVAL, "adg_topo_grad: NULL argument");
   TopoArgs a;
@@ -766,6 +788,7 @@ extern "C" adg_status adg_grad_eh(adg_ctx* ctx, adg_design* d_eps, adg_design* d
                                   const float* const d_eadj[3], const float* w_e,
                                   const float* const d_hfwd[3], const float* const d_hadj[3],
                                   const float* w_h, float* d_grad, void* stream) {
+  CallRange nvtx_range("adg_grad_eh");
   if (!ctx || !d_eps || !d_mu || !d_efwd || !d_eadj || !w_e || !d_hfwd || !d_hadj || !w_h ||
       (!d_grad && d_eps->n_params > 0))
     return fail(ADG_EINVAL, "adg_grad_eh: NULL argument");
@@ -856,6 +879,7 @@ adg_status levels_setup(adg_ctx* ctx, adg_design* const* sets, int K, const doub
 extern "C" adg_status adg_levels_eps(adg_ctx* ctx, adg_design* const* sets, int32_t K,
                                      const double* levels, double eps_bg, const double* h_params,
                                      float* d_eps, void* stream) {
+  CallRange nvtx_range("adg_levels_eps");
   LevelArgs a;
   adg_status st = levels_setup(ctx, sets, K, levels, "adg_levels_eps", K, a);
   if (st != ADG_OK) return st;
@@ -880,6 +904,7 @@ extern "C" adg_status adg_levels_grad(adg_ctx* ctx, adg_design* const* sets, int
                                       const double* levels, const double* h_params,
                                       const float* const d_efwd[3], const float* const d_eadj[3],
                                       const float* w, float* d_grad, void* stream) {
+  CallRange nvtx_range("adg_levels_grad");
   LevelArgs a;
   adg_status st = levels_setup(ctx, sets, K, levels, "adg_levels_grad", 2 * K, a);
   if (st != ADG_OK) return st;
@@ -1050,6 +1075,7 @@ struct MeshImage {
 
 extern "C" adg_status adg_mesh_fill(adg_ctx* ctx, const adg_grid* grid, const adg_mesh_layer* layer,
                                     const adg_topo_region* region, float* d_fill, void* stream) {
+  CallRange nvtx_range("adg_mesh_fill");
   if (!ctx || !d_fill) return fail(ADG_EINVAL, "adg_mesh_fill: NULL argument");
   adg_status st = mesh_grid(grid, "adg_mesh_fill");
   if (st != ADG_OK) return st;
@@ -1097,6 +1123,7 @@ extern "C" adg_status adg_mesh_grad_fd(adg_ctx* ctx, const adg_grid* grid, int32
                                        const adg_topo_region* regions, double h, double deps,
                                        const float* const d_efwd[3], const float* const d_eadj[3],
                                        const float* w, float* d_grad, void* stream) {
+  CallRange nvtx_range("adg_mesh_grad_fd");
   const char* who = "adg_mesh_grad_fd";
   if (!ctx || n_params < 0 || (n_params > 0 && (!plus || !minus || !d_grad)) || !d_efwd ||
       !d_eadj || !w)
@@ -1219,6 +1246,7 @@ extern "C" adg_status adg_mesh_grad_fd(adg_ctx* ctx, const adg_grid* grid, int32
 extern "C" adg_status adg_grad_fd(adg_ctx* ctx, adg_design* d, const double* h_params,
                                   const float* const d_efwd[3], const float* const d_eadj[3],
                                   const float* w, double h, float* d_grad, void* stream) {
+  CallRange nvtx_range("adg_grad_fd");
   if (!ctx || !d || !d_efwd || !d_eadj || !w || (!d_grad && d->n_params > 0) ||
       (!h_params && d->n_params > 0))
     return fail(ADG_EINVAL, "adg_grad_fd: NULL argument");
@@ -1279,6 +1307,7 @@ uint64_t mix(uint64_t h, uint64_t v) {
 
 extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items, int32_t n,
                                        int32_t flags, void* stream, uint64_t* ticket) {
+  CallRange nvtx_range("adg_batch_submit");
   if (!ctx || !items || !ticket) return fail(ADG_EINVAL, "adg_batch_submit: NULL argument");
   if (n < 1 || n > kMaxJobs) return fail(ADG_EINVAL, "batch of %d items (1..%d)", n, kMaxJobs);
   if (flags & ~ADG_BATCH_GRAPH) return fail(ADG_EINVAL, "unknown batch flags 0x%x", flags);
