@@ -229,8 +229,13 @@ struct adg_design {
   float* d_partial = nullptr;  // all zero between calls (the finalize clears what it sums)
   size_t partial_cap = 0;
   bool partial_dirty = false;  // a call that enqueued the VJP did not complete its enqueue
-  Job* d_job = nullptr;  // the one-job table of single-design calls
-  Job job{};
+  // the one-job tables of single-design calls, one slot per (build?, gradient?,
+  // counter set): in an optimisation loop each call finds its table already
+  // uploaded, so no copy sits between the kernels of consecutive calls
+  static constexpr int kJobSlots = 8;
+  Job* d_job = nullptr;
+  Job jobs_h[kJobSlots]{};
+  bool job_ok[kJobSlots] = {};
   // dense field stream (adg_grad_dense): per-chunk partials and work counter
   double2* d_dense_part = nullptr;
   int* d_dense_ctr = nullptr;
@@ -441,7 +446,7 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_list, sizeof(int) * (size_t)d->g.T);
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_counters, sizeof(int) * 16);
   if (e == cudaSuccess) e = cudaMemset(d->d_counters, 0, sizeof(int) * 16);
-  if (e == cudaSuccess) e = lib_malloc((void**)&d->d_job, sizeof(Job));
+  if (e == cudaSuccess) e = lib_malloc((void**)&d->d_job, sizeof(Job) * adg_design::kJobSlots);
   if (e != cudaSuccess) {
     free_design(d);
     return fail(e == cudaErrorMemoryAllocation ? ADG_ENOMEM : ADG_ECUDA, "adg_design_create: %s",
@@ -562,8 +567,14 @@ Job design_job(adg_design* d) {
 }
 
 // Enqueue bin -> build / VJP -> finalize for a job table.
-adg_status run_jobs(adg_ctx* ctx, const Job* d_jobs, const JobTotals& t, bool any_bin,
+adg_status run_jobs(adg_ctx* ctx, const Job* d_jobs, const JobTotals& t_in, bool any_bin,
                     bool any_build, bool any_grad, int max_tiles, cudaStream_t s) {
+  // Programmatic dependent launch for the kernels after the first: not while
+  // profiling (events sit between the launches) or capturing a graph.
+  JobTotals t = t_in;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CU(cudaStreamIsCapturing(s, &cap));
+  t.pdl = (!ctx->prof && cap == cudaStreamCaptureStatusNone) ? 1 : 0;
   if (any_bin) {
     ProfScope ps(ctx, ADG_K_BIN, s);
     CU(launch_bin(d_jobs, t, ctx->d_err, s));
@@ -613,9 +624,14 @@ adg_status run_single_enqueue(adg_ctx* ctx, adg_design* d, bool rebin, float* d_
   if (grad) J.va = *va;
   J.grad = d_grad;
   J.partial_n = grad ? (long long)d->part_total : 0;
-  d->job = J;
   if (grad) d->partial_dirty = true;  // until the finalize is enqueued
-  CU(cudaMemcpyAsync(d->d_job, &d->job, sizeof(Job), cudaMemcpyHostToDevice, s));
+  const int slot = (d_eps ? 1 : 0) | (grad ? 2 : 0) | (d->gen << 2);
+  if (!d->job_ok[slot] || memcmp(&d->jobs_h[slot], &J, sizeof(Job)) != 0) {
+    d->job_ok[slot] = false;
+    memcpy(&d->jobs_h[slot], &J, sizeof(Job));
+    CU(cudaMemcpyAsync(d->d_job + slot, &d->jobs_h[slot], sizeof(Job), cudaMemcpyHostToDevice, s));
+    d->job_ok[slot] = true;
+  }
   JobTotals t{};
   t.njobs = 1;
   t.tiles_padded = ((d->g.T + 127) / 128) * 128;
@@ -626,7 +642,7 @@ adg_status run_single_enqueue(adg_ctx* ctx, adg_design* d, bool rebin, float* d_
   t.fill_warps = d->fill_warps;
   t.polar = d->g.polar;
   t.xform = d->g.xform;
-  st = run_jobs(ctx, d->d_job, t, rebin, d_eps != nullptr, grad, d->g.T, s);
+  st = run_jobs(ctx, d->d_job + slot, t, rebin, d_eps != nullptr, grad, d->g.T, s);
   if (st == ADG_OK) d->partial_dirty = false;
   return st;
 }

@@ -309,6 +309,7 @@ struct JobTotals {
   int fill_warps;  // build: warps per block streaming constant tiles (1 .. kMaxFillWarps)
   int polar;       // some job's design has Polar2D primitives: the VJP is k_vjp_polar
   int xform;       // some job's design has transformed primitives: k_build_x, k_vjp_polar
+  int pdl;         // launch the build, VJP and finalize with programmatic dependent launch
 };
 
 constexpr int kMaxJobs = 1024;  // jobs in one table (one batch)

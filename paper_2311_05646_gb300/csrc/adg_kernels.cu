@@ -990,6 +990,14 @@ __device__ __forceinline__ int job_by_param(const Job* jobs, int n, int idx) {
   return lo;
 }
 
+// Programmatic dependent launch: the build, the VJP and the finalize may be
+// launched to overlap the tail of the kernel before them on the stream (the
+// launch, block scheduling and a prologue that reads only tables uploaded
+// before that kernel).  They wait here for it to complete, and for its
+// memory to be visible, before reading anything it may have written; a
+// kernel launched without the attribute returns from this at once.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---- binner: one warp per tile ------------------------------------------------
 // A block takes kBinWarps consecutive tiles of one job (y fastest: tiles that
 // differ only in y usually see the same primitives).  The chain is walked in
@@ -1932,6 +1940,7 @@ __device__ __forceinline__ void build_body(const Job* __restrict__ jobs, int njo
   int* snext = spre - 2;                 // the block's next fill unit (k)
   const int tid = threadIdx.x;
   if (tid == 0) *snext = 0;
+  wait_prior_grid();  // the binner's counters, lists and programs
   job_prefix(jobs, njobs, false, spre, rpre, nfill);  // ends with a barrier
   const int total = spre[njobs];
   // Warp-specialised: the band warps take band tiles (latency-bound, with
@@ -2405,6 +2414,7 @@ __device__ __forceinline__ void vjp_body(const Job* __restrict__ jobs, int njobs
                                          int* __restrict__ err, float* __restrict__ gtape,
                                          int* work) {
   extern __shared__ __align__(16) unsigned char smem[];
+  wait_prior_grid();  // the binner's output, the fields, the partials' last clearing
   float* tape = reinterpret_cast<float*>(smem);
   float* pool = tape + kSmemOps * kBlock;
   float* zsb = pool + kVjpPool;  // seeds of a chunk
@@ -2820,12 +2830,14 @@ __global__ void __launch_bounds__(128) k_finalize(const Job* __restrict__ jobs, 
   const int wid = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const Job& J = jobs[job_by_param(jobs, njobs, wid)];
   const int k = wid - J.param_base;
+  const int r0 = J.ref_off[k], r1 = J.ref_off[k + 1];  // tables uploaded before the VJP
+  wait_prior_grid();  // the VJP's partials and counters
   if (k == 0 && threadIdx.x == 0) {
     *J.counters_last = J.counters[3];
     J.counters[3] = 0;
   }
   double total = 0.0;
-  for (int r = J.ref_off[k]; r < J.ref_off[k + 1]; ++r) {
+  for (int r = r0; r < r1; ++r) {
     const PrimRec& P = J.prims[J.ref_prim[r]];
     if (!ADG_CHECK((size_t)P.part_off + (size_t)(J.ref_qa[r] + 1) * P.npb <= (size_t)J.partial_n,
                    J.err))
@@ -2914,16 +2926,29 @@ cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream
   return cudaGetLastError();
 }
 
+// A launch, with programmatic stream serialisation when pdl is set (the
+// kernel then starts as the one before it drains; see wait_prior_grid).
+template <typename... P, typename... A>
+cudaError_t launch_k(bool pdl, void (*k)(P...), int grid, int block, size_t smem, cudaStream_t s,
+                     A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s) {
   if (!t.work || t.fill_warps < 1 || t.fill_warps > kMaxFillWarps) return cudaErrorInvalidValue;
   const int grid = sms * build_blocks_per_sm(t.njobs, t.fill_warps, t.xform != 0);
-  if (t.xform)
-    k_build_x<<<grid, kBlock + 32 * t.fill_warps, build_smem(t.njobs), s>>>(jobs, t.njobs,
-                                                                           t.fill_blocks, t.work);
-  else
-    k_build<<<grid, kBlock + 32 * t.fill_warps, build_smem(t.njobs), s>>>(jobs, t.njobs,
-                                                                         t.fill_blocks, t.work);
-  return cudaGetLastError();
+  return launch_k(t.pdl != 0, t.xform ? k_build_x : k_build, grid, kBlock + 32 * t.fill_warps,
+                  build_smem(t.njobs), s, jobs, t.njobs, t.fill_blocks, t.work);
 }
 
 cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, float* gtape,
@@ -2932,11 +2957,8 @@ cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, f
   const bool shapes = t.polar || t.xform;
   const int grid = std::min(sms * vjp_blocks_per_sm(t.njobs, shapes), gtape_blocks);
   if (grid < 1 || !gtape || !t.work) return cudaErrorInvalidValue;
-  if (shapes)
-    k_vjp_polar<<<grid, kBlock, vjp_smem(t.njobs), s>>>(jobs, t.njobs, err, gtape, t.work);
-  else
-    k_vjp<<<grid, kBlock, vjp_smem(t.njobs), s>>>(jobs, t.njobs, err, gtape, t.work);
-  return cudaGetLastError();
+  return launch_k(t.pdl != 0, shapes ? k_vjp_polar : k_vjp, grid, kBlock, vjp_smem(t.njobs), s,
+                  jobs, t.njobs, err, gtape, t.work);
 }
 
 cudaError_t launch_dense(const DenseArgs& a, int sms, cudaStream_t s) {
@@ -2952,8 +2974,7 @@ cudaError_t launch_dense(const DenseArgs& a, int sms, cudaStream_t s) {
 
 cudaError_t launch_finalize(const Job* jobs, const JobTotals& t, cudaStream_t s) {
   if (t.params <= 0) return cudaSuccess;
-  k_finalize<<<t.params, 128, 0, s>>>(jobs, t.njobs, t.params);
-  return cudaGetLastError();
+  return launch_k(t.pdl != 0, k_finalize, t.params, 128, 0, s, jobs, t.njobs, t.params);
 }
 
 }  // namespace adg
