@@ -146,7 +146,7 @@ typedef struct {
 } adg_design_desc;
 
 /* Tile shape (cells) of the binned kernels.  tx in {32, 64}, ty in
- * {1, 2, 4, 8, 16}, tz in {1, 2, 4, 8}, 128 <= tx*ty*tz <= 1024.  All zero =
+ * {1, 2, 4, 8, 16}, tz in {1, 2, 4, 8}, 128 <= tx*ty*tz <= 2048.  All zero =
  * library default (32 x 4 x 4).  fill_warps: warps of each build block that
  * stream the constant tiles beside its four band warps, 1 or 2 (0 = 1); a
  * design with much constant area and few band tiles builds faster with 2.

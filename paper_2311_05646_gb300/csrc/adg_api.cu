@@ -281,7 +281,7 @@ extern "C" adg_status adg_ctx_create(int32_t device, adg_ctx** out) {
   c->device = device;
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = init_kernel_attributes();
-  c->gtape_blocks = c->sms * std::max(vjp_blocks_per_sm(1, false), vjp_blocks_per_sm(1, true));
+  c->gtape_blocks = c->sms * std::max(vjp_blocks_per_sm(1, false, 128), vjp_blocks_per_sm(1, true, 128));
   if (e == cudaSuccess) e = lib_malloc((void**)&c->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e == cudaSuccess)
@@ -642,6 +642,7 @@ adg_status run_single_enqueue(adg_ctx* ctx, adg_design* d, bool rebin, float* d_
   t.fill_warps = d->fill_warps;
   t.polar = d->g.polar;
   t.xform = d->g.xform;
+  t.max_cells = 1 << (d->g.lx + d->g.ly + d->g.lz);
   st = run_jobs(ctx, d->d_job + slot, t, rebin, d_eps != nullptr, grad, d->g.T, s);
   if (st == ADG_OK) d->partial_dirty = false;
   return st;
@@ -1409,7 +1410,7 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   unsigned char* db = static_cast<unsigned char*>(A.d);
   Job* hj = reinterpret_cast<Job*>(hb + o_jobs);
   size_t po = 0, ado = 0, afo = 0;
-  int tile_base = 0, param_base = 0, max_tiles = 0, row_base = 0;
+  int tile_base = 0, param_base = 0, max_tiles = 0, row_base = 0, max_cells = 128;
   bool any_build = false, any_grad = false, any_polar = false, any_xform = false;
   uint64_t sig = mix(0, (uint64_t)arena_id);
   sig = mix(sig, (uint64_t)n);
@@ -1452,6 +1453,7 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
     }
     tile_base += ((d->g.T + 127) / 128) * 128;
     max_tiles = std::max(max_tiles, d->g.T);
+    if (J.do_grad) max_cells = std::max(max_cells, 1 << (d->g.lx + d->g.ly + d->g.lz));
     any_build = any_build || J.do_build;
     any_grad = any_grad || J.do_grad;
     any_polar = any_polar || (J.do_grad && d->g.polar);
@@ -1473,13 +1475,15 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   t.fill_warps = 1;
   t.polar = any_polar ? 1 : 0;
   t.xform = any_xform ? 1 : 0;
+  t.max_cells = max_cells;
   sig = mix(sig, (uint64_t)t.polar);  // the captured VJP kernel depends on it
   sig = mix(sig, (uint64_t)t.xform);  // and the build and VJP kernels on this
+  sig = mix(sig, (uint64_t)t.max_cells);  // the VJP's shared memory and grid
   sig = mix(sig, (uint64_t)bytes);
   sig = mix(sig, (uint64_t)tile_base);
   sig = mix(sig, (uint64_t)param_base);
   build_blocks_per_sm(t.njobs, t.fill_warps, t.xform != 0);  // set before any capture
-  vjp_blocks_per_sm(t.njobs, t.polar || t.xform);
+  vjp_blocks_per_sm(t.njobs, t.polar || t.xform, t.max_cells);
   const bool graph = (flags & ADG_BATCH_GRAPH) && !ctx->prof;
   if (graph && A.exec && A.sig == sig) {
     CU(cudaGraphLaunch(A.exec, s));

@@ -16,7 +16,7 @@ constexpr int kMaxDepth = 32;   // fold stack depth (checked at design creation)
 constexpr int kMaxSlots = 384;  // (primitive, active scalar) accumulators
 constexpr int kMaxPairs = 6;    // d s / d q terms one cell yields per leaf (box, graph 6; circle 5)
 constexpr int kBlock = 128;     // threads per CTA of the build / VJP kernels
-constexpr int kMaxTileCells = 1024;  // cells per tile (per component)
+constexpr int kMaxTileCells = 2048;  // cells per tile (per component)
 constexpr int kWarps = kBlock / 32;
 constexpr int kMaxPolyVerts = 256;  // vertices of one convex polygon
 // Polygon edge table (fp32, kPolyEdgeFloats per edge): the edge's start vertex
@@ -310,6 +310,7 @@ struct JobTotals {
   int polar;       // some job's design has Polar2D primitives: the VJP is k_vjp_polar
   int xform;       // some job's design has transformed primitives: k_build_x, k_vjp_polar
   int pdl;         // launch the build, VJP and finalize with programmatic dependent launch
+  int max_cells;   // largest tile (cells) of the table's jobs: sizes the VJP's sample list
 };
 
 constexpr int kMaxJobs = 1024;  // jobs in one table (one batch)
@@ -327,7 +328,7 @@ cudaError_t launch_dense(const DenseArgs& a, int sms, cudaStream_t s);
 // Shared-memory limits of the kernels; call once per device before any capture.
 cudaError_t init_kernel_attributes();
 int build_blocks_per_sm(int njobs, int fill_warps, bool xform);
-int vjp_blocks_per_sm(int njobs, bool polar);
+int vjp_blocks_per_sm(int njobs, bool polar, int cells);
 void set_last_error(const char* msg);  // the thread-local text of adg_last_error()
 
 }  // namespace adg

@@ -2396,16 +2396,23 @@ __device__ __noinline__ void tile_seeds(const Job* J, const uint16_t* slist, flo
     zsb[i - c0] = zs * g.deps;  // eps = eps_bg + deps fill
   }
 }
-// a warp's share of a tile's x-rows (C * TY * TZ <= 3 * 1024 / 32) fits its lanes
-static_assert((3 * kMaxTileCells / 32 + kWarps - 1) / kWarps <= 32, "rows per warp");
+// a warp's share of a tile's x-rows (C * TY * TZ <= 3 * 16 * 8) fits kRowRounds
+// rounds of its lanes
+constexpr int kRowRounds = 3;
+static_assert((3 * 16 * 8 + kWarps - 1) / kWarps <= 32 * kRowRounds, "rows per warp");
 constexpr size_t kVjpFixed = (size_t)kSmemOps * kBlock * 4 + (size_t)kVjpPool * 4 +
-                             (size_t)kSeedChunk * 4 + (size_t)kMaxTileCells * 3 * 2 +
-                             (kMaxLeaves + 1) * 4 + kAct1 + 32 * 4;
-__host__ __device__ constexpr size_t vjp_smem(int njobs) {
-  return ((kVjpFixed + 15) & ~(size_t)15) + (size_t)spre_len(njobs) * 4;
+                             (size_t)kSeedChunk * 4 + (kMaxLeaves + 1) * 4 + kAct1 + 32 * 4;
+// the job prefix, then the active-sample list (C x cells entries of 16 bits)
+__host__ __device__ constexpr size_t vjp_list_off(int njobs) {
+  return ((kVjpFixed + 15) & ~(size_t)15) + (((size_t)spre_len(njobs) * 4 + 15) & ~(size_t)15);
 }
-// five blocks per SM (228 KB of shared memory, 1 KB reserved per block)
-static_assert(5 * (vjp_smem(1) + 1024) <= 228 * 1024, "VJP shared memory for five blocks per SM");
+__host__ __device__ constexpr size_t vjp_smem(int njobs, int cells) {
+  return vjp_list_off(njobs) + (size_t)cells * 3 * 2;
+}
+// five blocks per SM up to 1024-cell tiles (228 KB of shared memory, 1 KB
+// reserved per block); 2048-cell tiles run four
+static_assert(5 * (vjp_smem(1, 1024) + 1024) <= 228 * 1024, "VJP shared memory for five blocks per SM");
+static_assert(4 * (vjp_smem(1, kMaxTileCells) + 1024) <= 228 * 1024, "VJP shared memory, largest tiles");
 
 // The VJP body; kPolarT: the job table holds Polar2D primitives (k_vjp_polar),
 // else k_vjp, whose sample loop carries no Polar2D code at all.
@@ -2418,13 +2425,13 @@ __device__ __forceinline__ void vjp_body(const Job* __restrict__ jobs, int njobs
   float* tape = reinterpret_cast<float*>(smem);
   float* pool = tape + kSmemOps * kBlock;
   float* zsb = pool + kVjpPool;  // seeds of a chunk
-  uint16_t* slist = reinterpret_cast<uint16_t*>(zsb + kSeedChunk);  // active samples
-  int* sbase = reinterpret_cast<int*>(slist + kMaxTileCells * 3);
+  int* sbase = reinterpret_cast<int*>(zsb + kSeedChunk);
   unsigned char* act1 = reinterpret_cast<unsigned char*>(sbase + kMaxLeaves + 1);
   // misc words: [1] all-active flag, [2] parameter-driven pushes, [3]
   // z-collapse flag, [12..15] active samples per warp's rows
   int* misc = reinterpret_cast<int*>(act1 + kAct1);
   int* spre = reinterpret_cast<int*>(smem + ((kVjpFixed + 15) & ~(size_t)15));
+  uint16_t* slist = reinterpret_cast<uint16_t*>(smem + vjp_list_off(njobs));  // active samples
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   job_prefix(jobs, njobs, true, spre);
   const int total = spre[njobs];
@@ -2539,30 +2546,45 @@ __device__ __forceinline__ void vjp_body(const Job* __restrict__ jobs, int njobs
       for (int c = 0; c < 3; ++c) xm[c][h] = __ballot_sync(0xffffffffu, in && c < C && act1[c * TX + x]);
     }
     const bool all = misc[1] != 0;
-    const int rpw = (nrows + kWarps - 1) / kWarps;  // <= 24
+    const int rpw = (nrows + kWarps - 1) / kWarps;  // <= 32 kRowRounds
     const int ra = warp * rpw, rb = min(nrows, ra + rpw);
-    int kind = 0, cnt = 0, rc = 0, rz = 0, ry = 0;
-    if (ra + lane < rb) {
-      const int r = ra + lane;
-      rc = r / (TYr * TZr);
-      const int rem = r - rc * TYr * TZr;
-      rz = rem / TYr;
-      ry = rem - rz * TYr;
-      if (Y0 + ry < g.ny && Z0 + rz < g.nz) {
-        const bool full = all || act1[C * TX + rc * TY + ry] || act1[C * (TX + TY) + rc * TZ + rz];
-        kind = full ? 1 : 2;
+    // the warp's rows in rounds of 32 (row ra + 32 j + lane): per row its kind
+    // (0 none, 1 whole, 2 pattern), first list entry within the warp and
+    // (c, z, y) packed as c << 16 | z << 8 | y
+    int rkind[kRowRounds], rbase[kRowRounds], rpack[kRowRounds];
+    int run = 0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-          cnt += __popc(full ? xi[h] : (rc == 0 ? xm[0][h] : rc == 1 ? xm[1][h] : xm[2][h]));
+    for (int j = 0; j < kRowRounds; ++j) {
+      rkind[j] = 0;
+      rbase[j] = 0;
+      rpack[j] = 0;
+      if (ra + 32 * j >= rb) continue;  // warp-uniform
+      const int r = ra + 32 * j + lane;
+      int cnt = 0;
+      if (r < rb) {
+        const int rc = r / (TYr * TZr);
+        const int rem = r - rc * TYr * TZr;
+        const int rz = rem / TYr;
+        const int ry = rem - rz * TYr;
+        rpack[j] = (rc << 16) | (rz << 8) | ry;
+        if (Y0 + ry < g.ny && Z0 + rz < g.nz) {
+          const bool full = all || act1[C * TX + rc * TY + ry] || act1[C * (TX + TY) + rc * TZ + rz];
+          rkind[j] = full ? 1 : 2;
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            cnt += __popc(full ? xi[h] : (rc == 0 ? xm[0][h] : rc == 1 ? xm[1][h] : xm[2][h]));
+        }
       }
-    }
-    int inc = cnt;
+      int inc = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += u;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+      }
+      rbase[j] = run + inc - cnt;
+      run += __shfl_sync(0xffffffffu, inc, 31);
     }
-    if (lane == 31) misc[12 + warp] = inc;
+    if (lane == 0) misc[12 + warp] = run;
     __syncthreads();  // warp totals
     int wbase = 0, nact_cells = 0;
 #pragma unroll
@@ -2571,17 +2593,21 @@ __device__ __forceinline__ void vjp_body(const Job* __restrict__ jobs, int njobs
       if (v < warp) wbase += tv;
       nact_cells += tv;
     }
-    for (int rr = 0; rr < rb - ra; ++rr) {  // this warp's rows, all lanes per row
-      const int kd = __shfl_sync(0xffffffffu, kind, rr);
-      int off = wbase + __shfl_sync(0xffffffffu, inc - cnt, rr);
-      const int c = __shfl_sync(0xffffffffu, rc, rr), z = __shfl_sync(0xffffffffu, rz, rr),
-                y = __shfl_sync(0xffffffffu, ry, rr);
-      if (!kd) continue;
-      const int lrow = ((c * TZr + z) * TYr + y) << g.lx;
-      for (int h = 0; h < nw; ++h) {
-        const unsigned m = kd == 1 ? xi[h] : (c == 0 ? xm[0][h] : c == 1 ? xm[1][h] : xm[2][h]);
-        if ((m >> lane) & 1u) slist[off + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(lrow + h * 32 + lane);
-        off += __popc(m);
+#pragma unroll
+    for (int j = 0; j < kRowRounds; ++j) {  // this warp's rows, all lanes per row
+      const int nr = min(32, rb - ra - 32 * j);
+      for (int rr = 0; rr < nr; ++rr) {
+        const int kd = __shfl_sync(0xffffffffu, rkind[j], rr);
+        int off = wbase + __shfl_sync(0xffffffffu, rbase[j], rr);
+        const int pk = __shfl_sync(0xffffffffu, rpack[j], rr);
+        if (!kd) continue;
+        const int c = pk >> 16, z = (pk >> 8) & 255, y = pk & 255;
+        const int lrow = ((c * TZr + z) * TYr + y) << g.lx;
+        for (int h = 0; h < nw; ++h) {
+          const unsigned m = kd == 1 ? xi[h] : (c == 0 ? xm[0][h] : c == 1 ? xm[1][h] : xm[2][h]);
+          if ((m >> lane) & 1u) slist[off + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(lrow + h * 32 + lane);
+          off += __popc(m);
+        }
       }
     }
     __syncthreads();  // the list is complete; misc[12..] free again
@@ -2880,10 +2906,10 @@ cudaError_t init_kernel_attributes() {
                              (int)build_smem(kMaxJobs));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)vjp_smem(kMaxJobs));
+                             (int)vjp_smem(kMaxJobs, kMaxTileCells));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_vjp_polar, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)vjp_smem(kMaxJobs));
+                             (int)vjp_smem(kMaxJobs, kMaxTileCells));
   return e;
 }
 
@@ -2906,15 +2932,21 @@ int build_blocks_per_sm(int njobs, int fill_warps, bool xform) {
   return r;
 }
 
-int vjp_blocks_per_sm(int njobs, bool polar) {
-  static int v[2][kMaxJobs + 1] = {};
+// cells: the largest tile of the table (a power of two, 128 .. kMaxTileCells).
+int vjp_blocks_per_sm(int njobs, bool polar, int cells) {
+  constexpr int kCellClasses = 5;  // 128, 256, ..., 2048 cells
+  static_assert(128 << (kCellClasses - 1) == kMaxTileCells, "tile cell classes");
+  static int v[2][kCellClasses][kMaxJobs + 1] = {};
   njobs = std::min(std::max(njobs, 1), kMaxJobs);
-  int& r = v[polar ? 1 : 0][njobs];
+  int cls = 0;
+  while (cls + 1 < kCellClasses && (128 << cls) < cells) ++cls;
+  cells = 128 << cls;
+  int& r = v[polar ? 1 : 0][cls][njobs];
   if (!r) {
     if (polar)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_vjp_polar, kBlock, vjp_smem(njobs));
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_vjp_polar, kBlock, vjp_smem(njobs, cells));
     else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_vjp, kBlock, vjp_smem(njobs));
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_vjp, kBlock, vjp_smem(njobs, cells));
     if (r < 1) r = 1;
   }
   return r;
@@ -2955,10 +2987,11 @@ cudaError_t launch_vjp(const Job* jobs, const JobTotals& t, int* err, int sms, f
                        int gtape_blocks, cudaStream_t s) {
   // Polar2D and transformed primitives: the VJP compiled with their code
   const bool shapes = t.polar || t.xform;
-  const int grid = std::min(sms * vjp_blocks_per_sm(t.njobs, shapes), gtape_blocks);
+  const int cells = t.max_cells > 0 ? std::min(t.max_cells, kMaxTileCells) : kMaxTileCells;
+  const int grid = std::min(sms * vjp_blocks_per_sm(t.njobs, shapes, cells), gtape_blocks);
   if (grid < 1 || !gtape || !t.work) return cudaErrorInvalidValue;
-  return launch_k(t.pdl != 0, shapes ? k_vjp_polar : k_vjp, grid, kBlock, vjp_smem(t.njobs), s,
-                  jobs, t.njobs, err, gtape, t.work);
+  return launch_k(t.pdl != 0, shapes ? k_vjp_polar : k_vjp, grid, kBlock, vjp_smem(t.njobs, cells),
+                  s, jobs, t.njobs, err, gtape, t.work);
 }
 
 cudaError_t launch_dense(const DenseArgs& a, int sms, cudaStream_t s) {

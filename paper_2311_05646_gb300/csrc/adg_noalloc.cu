@@ -278,6 +278,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   t.work = d_cnt + 12;
   t.polar = g.polar;
   t.xform = g.xform;
+  t.max_cells = 1 << (g.lx + g.ly + g.lz);
   NACU(launch_bin(d_job, t, d_err, s));
   NACU(launch_vjp(d_job, t, d_err, sms, d_gtape, sms, s));
   NACU(launch_finalize(d_job, t, s));

@@ -16,10 +16,11 @@ import numpy as np
 from . import adg
 
 # Larger tiles amortise the per-tile work of the band kernels over more samples
-# (the grating and hole lattices run fastest at 32x8x4); smaller ones cull
-# more finely (designs crowded with small features run fastest at 32x4x4).
-CANDIDATES = [(32, 4, 4), (32, 8, 4), (32, 16, 2), (32, 8, 2), (64, 2, 2), (64, 4, 1), (32, 2, 8),
-              (32, 4, 2), (64, 2, 1), (32, 16, 1)]
+# and put fewer tiles in the VJP's wave (the grating runs fastest at 32x16x4,
+# whose tiles collapse along y), smaller ones cull more finely (designs crowded
+# with small features run fastest at 32x4x4).
+CANDIDATES = [(32, 4, 4), (32, 8, 4), (32, 16, 4), (32, 8, 8), (32, 16, 2), (32, 8, 2), (64, 2, 2),
+              (64, 4, 1), (32, 2, 8), (32, 4, 2), (64, 2, 1), (32, 16, 1)]
 
 
 def size_class(desc: dict):

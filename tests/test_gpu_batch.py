@@ -1,6 +1,7 @@
 """Batched persistent launch: many designs of uneven size and primitive count
-in one job table.  Every item's eps and gradient equal, bit for bit, what the
-same design gives alone; graph replay equals direct launch; waits are bounded."""
+in one job table, at one tile shape or each at its own.  Every item's eps and
+gradient equal, bit for bit, what the same design gives alone; graph replay
+equals direct launch; waits are bounded."""
 import numpy as np
 import pytest
 
@@ -38,13 +39,19 @@ def _alloc(d, desc, rng):
     return ef, ea, eps, fill, g
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_batch_equals_alone(ctx, graph):
+# per-design tile shapes of the mixed table: the VJP's shared memory and grid
+# follow the largest tile among the gradient items (2048 cells here)
+MIXED_TILES = [(32, 8, 8), None, (64, 8, 4), (32, 4, 2), (32, 16, 4), (32, 8, 4), (64, 4, 4), None]
+
+
+@pytest.mark.parametrize("graph,mixed", [(False, False), (True, False), (False, True), (True, True)])
+def test_batch_equals_alone(ctx, graph, mixed):
     import torch
     from paper_2311_05646_gb300 import adg
     rng = np.random.default_rng(0)
     descs = _mix()
-    designs = [adg.Design(ctx, d) for d in descs]
+    tiles = MIXED_TILES if mixed else [None] * len(descs)
+    designs = [adg.Design(ctx, d, tile=t) for d, t in zip(descs, tiles)]
     bufs = [_alloc(d, desc, rng) for d, desc in zip(designs, descs)]
     w = I.seeded_w(3, 9)
     for rep in range(2):  # the second submit replays the captured graph

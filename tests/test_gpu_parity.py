@@ -102,9 +102,21 @@ def test_gradient_matches_oracle(ctx, oracle_mod, case):
     _check_grad(ctx, CASES[case](), oracle_mod)
 
 
-@pytest.mark.parametrize("tile", [(32, 4, 4), (64, 2, 1), (32, 1, 8), (64, 4, 4), (32, 8, 4)])
+@pytest.mark.parametrize("tile", [(32, 4, 4), (64, 2, 1), (32, 1, 8), (64, 4, 4), (32, 8, 4),
+                                  (32, 8, 8), (64, 8, 4), (32, 16, 4)])
 def test_tile_shapes_agree(ctx, oracle_mod, tile):
     desc = I.grating_3d(n=(150, 36, 60), teeth=8, pitch=600.0)
+    d = _check_build(ctx, desc, oracle_mod, tile=tile)
+    _check_grad(ctx, desc, oracle_mod, d=d)
+
+
+@pytest.mark.parametrize("tile", [(32, 16, 4), (32, 8, 8), (64, 16, 2), (64, 4, 8)])
+def test_largest_tiles_without_collapse(ctx, oracle_mod, tile):
+    """2048-cell tiles on a design that collapses neither y nor z (boxes,
+    circles and polygons at random places): up to 3 x 16 x 4 = 192 x-rows per
+    tile, so the VJP's row scan runs its warps' rows in several rounds of 32;
+    ragged in every axis."""
+    desc = I.random_design(4107, n=(75, 53, 27), nprims=14)
     d = _check_build(ctx, desc, oracle_mod, tile=tile)
     _check_grad(ctx, desc, oracle_mod, d=d)
 
@@ -312,14 +324,17 @@ def test_invalid_descriptions_rejected(ctx):
         adg.Design(ctx, desc, tile=(48, 4, 4))
     with pytest.raises(adg.AdgError):
         adg.Design(ctx, desc, tile=(64, 16, 8))  # more cells than a tile may hold
+    with pytest.raises(adg.AdgError):
+        adg.Design(ctx, desc, tile=(64, 8, 8))  # 4096 cells
 
 
 @pytest.mark.slow
 def test_full_size_grating3d(ctx, oracle_mod):
     """600 x 200 x 120 x 3 components, 60 etches, 120 parameters, in the
     launch configurations the benchmark times -- the library's default tile
-    and the autotuner's choice for this design (32x8x4 with two build fill
-    warps, and with one): every fill and eps value against the oracle's full
+    and the autotuner's choice for this design (32x16x4 with two build fill
+    warps, and with one; 32x8x4, the best 1024-cell shape): every fill and
+    eps value against the oracle's full
     fill, the full gradient against the oracle's full reverse sweep (the
     oracle runs once for both)."""
     import torch
@@ -330,7 +345,7 @@ def test_full_size_grating3d(ctx, oracle_mod):
     fref = oracle_mod.fill(desc)
     eref = desc["eps_bg"] + (desc["eps_fg"] - desc["eps_bg"]) * fref
     gref = oracle_mod.grad(desc, ef, ea, w)
-    for tile in (None, (32, 8, 4, 2), (32, 8, 4, 1)):
+    for tile in (None, (32, 16, 4, 2), (32, 16, 4, 1), (32, 8, 4, 2)):
         d = _design(ctx, desc, tile)
         fill = torch.empty(d.shape, dtype=torch.float32, device="cuda")
         eps = torch.empty_like(fill)
