@@ -223,8 +223,8 @@ struct adg_design {
   unsigned char* d_tclass = nullptr;
   int* d_list = nullptr;
   int* d_counters = nullptr;  // two sets of 4 (the binning alternates between them),
-                              // the active samples of the last VJP, then the
-                              // persistent kernels' 4 tile counters
+                              // the active samples of the last VJP, then (from
+                              // int 12) the persistent kernels' 6 work counters
   int gen = 0;                // the set of the last binning
   float* d_partial = nullptr;  // all zero between calls (the finalize clears what it sums)
   size_t partial_cap = 0;
@@ -444,8 +444,8 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_progs, sizeof(TileProg) * (size_t)d->g.T);
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_tclass, (size_t)d->g.T);
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_list, sizeof(int) * (size_t)d->g.T);
-  if (e == cudaSuccess) e = lib_malloc((void**)&d->d_counters, sizeof(int) * 16);
-  if (e == cudaSuccess) e = cudaMemset(d->d_counters, 0, sizeof(int) * 16);
+  if (e == cudaSuccess) e = lib_malloc((void**)&d->d_counters, sizeof(int) * 20);
+  if (e == cudaSuccess) e = cudaMemset(d->d_counters, 0, sizeof(int) * 20);
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_job, sizeof(Job) * adg_design::kJobSlots);
   if (e != cudaSuccess) {
     free_design(d);
@@ -1403,8 +1403,8 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
   }
   if (!A.done) CU(cudaEventCreateWithFlags(&A.done, cudaEventDisableTiming));
   if (!A.d_work) {
-    CU(lib_malloc((void**)&A.d_work, sizeof(int) * 4));
-    CU(cudaMemset(A.d_work, 0, sizeof(int) * 4));
+    CU(lib_malloc((void**)&A.d_work, sizeof(int) * 8));
+    CU(cudaMemset(A.d_work, 0, sizeof(int) * 8));
   }
   unsigned char* hb = static_cast<unsigned char*>(A.h);
   unsigned char* db = static_cast<unsigned char*>(A.d);

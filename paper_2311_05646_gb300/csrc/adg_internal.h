@@ -302,9 +302,10 @@ struct JobTotals {
   int bin_blocks;        // sum over binned jobs of ceil(T / 128)
   int tiles_padded;      // tile_base of one past the last job
   int params;            // sum of nparam over gradient jobs
-  // Tile counters of the persistent kernels, 4 ints: VJP next tile, VJP blocks
-  // done, build next tile, build blocks done.  Zero between launches: the
-  // last block of a launch resets its pair.  One launch at a time per array.
+  // Work counters of the persistent kernels, 6 ints: VJP next tile, VJP blocks
+  // done, build next band tile, build blocks done with band tiles, build next
+  // fill unit, build blocks done with fill units.  Zero between launches: the
+  // last block of a launch resets each pair.  One launch at a time per array.
   int* work;
   int fill_warps;  // build: warps per block streaming constant tiles (1 .. kMaxFillWarps)
   int polar;       // some job's design has Polar2D primitives: the VJP is k_vjp_polar

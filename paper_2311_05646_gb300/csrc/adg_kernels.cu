@@ -1933,22 +1933,20 @@ __device__ __forceinline__ void build_body(const Job* __restrict__ jobs, int njo
                                            int* work) {
   extern __shared__ __align__(16) unsigned char smem[];
   // layout: deep-program stack, pool, descriptors, four words (depth, z flag,
-  // next fill unit, next band tile), job prefix
+  // unused, next band tile), job prefix
   int* spre = reinterpret_cast<int*>(smem + (size_t)kMaxDepth * kBlock * 4 + (size_t)kBuildPool * 4 +
                                      kMaxOps * 16) + 4;
   int* rpre = spre + spre_len(njobs);  // first fill unit of each job
-  int* snext = spre - 2;                 // the block's next fill unit (k)
   const int tid = threadIdx.x;
-  if (tid == 0) *snext = 0;
   wait_prior_grid();  // the binner's counters, lists and programs
   job_prefix(jobs, njobs, false, spre, rpre, nfill);  // ends with a barrier
   const int total = spre[njobs];
   // Warp-specialised: the band warps take band tiles (latency-bound, with
   // their own barriers) while the fill warps stream the rows of constant
-  // tiles (store-bound), so that neither waits for the other.  The block's
-  // fill units (blockIdx.x + k G) are handed out by a shared counter; band
-  // warps that run out of band tiles take fill units too.  Each unit is
-  // written by exactly one warp, so the output does not depend on who.
+  // tiles (store-bound), so that neither waits for the other.  Fill units
+  // are handed out by a counter of the launch; band warps that run out of
+  // band tiles take fill units too.  Each unit is written by exactly one
+  // warp, so the output does not depend on who.
   const int G = gridDim.x;
   if (tid < kBlock) {  // band tiles: as in the VJP, the rest from work[2]
     int* sgi = spre - 1;
@@ -1977,13 +1975,25 @@ __device__ __forceinline__ void build_body(const Job* __restrict__ jobs, int njo
       }
     }
   }
+  // fill units from the launch's counter (work[4]), so that warps of blocks
+  // whose band tiles ended early take more of them
   const int lane = tid & 31;
   while (true) {
-    int k = 0;
-    if (lane == 0) k = atomicAdd(snext, 1);
-    const int fu = blockIdx.x + __shfl_sync(0xffffffffu, k, 0) * G;
+    int fu = 0;
+    if (lane == 0) fu = atomicAdd(work + 4, 1);
+    fu = __shfl_sync(0xffffffffu, fu, 0);
     if (fu >= nfill) break;
     fill_rows(jobs, job_of(rpre, njobs, fu), fu, lane);
+  }
+  // every warp of the block has made its last fetch: the last block resets
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(work + 5, 1) == G - 1) {
+      work[4] = 0;
+      work[5] = 0;
+      __threadfence();
+    }
   }
 }
 

@@ -153,7 +153,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   const size_t o_job = take(sizeof(Job));
   // this call's counter set, the one its binning clears, the moved active-sample
   // count, the persistent kernels' tile counters
-  const size_t o_cnt = take(16 * sizeof(int));
+  const size_t o_cnt = take(20 * sizeof(int));
   const size_t o_chain = take(sizeof(int) * nchain);
   const size_t o_act = take(sizeof(int) * std::max(st.nact_table, 1));
   const size_t o_actc = take(sizeof(float) * std::max(st.nact_table, 1));
@@ -219,7 +219,7 @@ extern "C" adg_status adg_grad_noalloc(const adg_design_desc* D, const adg_tile_
   // ---- upload, clear, launch (binner -> VJP -> finalize) ----
   NACU(cudaMemsetAsync(d_err, 0, sizeof(int), s));
   NACU(cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), s));
-  NACU(cudaMemsetAsync(d_cnt + 12, 0, 4 * sizeof(int), s));  // the space is shared by all calls
+  NACU(cudaMemsetAsync(d_cnt + 12, 0, 8 * sizeof(int), s));  // the space is shared by all calls
   // the partials' space held other tables in earlier calls
   NACU(cudaMemsetAsync(d_part, 0, sizeof(float) * std::max<size_t>(part, 1), s));
   NACU(cudaMemcpyAsync(d_chain, H.chain, sizeof(int) * nchain, cudaMemcpyHostToDevice, s));
