@@ -399,6 +399,13 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   d->nq.assign(D->prim_nq, D->prim_nq + D->n_prims);
   d->kr.assign(D->prim_kr, D->prim_kr + D->n_prims);
   host::set_grid(D, tx, ty, tz, nchain, d->g);
+  {
+    std::vector<unsigned char> pushed(D->n_prims, 0);
+    bool unique = true;
+    for (int i = 0; i < nchain && unique; ++i)
+      if (((chain[i] >> 24) & 0xff) == cPush) unique = pushed[chain[i] & 0xffffff]++ == 0;
+    d->g.unique_push = unique ? 1 : 0;
+  }
 
   // accumulator slots per (primitive, parameter) and parameter references
   size_t nqs = 0;

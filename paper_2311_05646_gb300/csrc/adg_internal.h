@@ -89,6 +89,8 @@ struct GridDev {
   int nprims;
   int polar;  // some primitive is Polar2D (its gradient runs on k_vjp_polar)
   int xform;  // some primitive is transformed (k_build_x and k_vjp_polar)
+  int unique_push;  // no primitive is pushed twice by the chain (the binner's
+                    // fold then gives each push its own leaf without a search)
 };
 
 // One primitive after the parameter map, in cell units of each axis:

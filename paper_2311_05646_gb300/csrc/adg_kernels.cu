@@ -1019,7 +1019,10 @@ struct BinWarpBuf {
   uint16_t leaf[kMaxLeaves];
   uint16_t ops[kMaxOps];
 };
-constexpr size_t kBinSmem = sizeof(int) * kBinSeg + sizeof(BinWarpBuf) * kBinWarps;
+// the tile boxes of the first kBinTbCache primitives, cached per block
+constexpr int kBinTbCache = kBinThreads;
+constexpr size_t kBinSmem =
+    sizeof(int) * kBinSeg + sizeof(BinWarpBuf) * kBinWarps + sizeof(int) * 6 * kBinTbCache;
 
 __device__ __forceinline__ bool tb_hits(const int* tb, int x0, int x1, int y0, int y1, int z0,
                                         int z1) {  // tile box [x0, x1] x ... against tb
@@ -1039,14 +1042,16 @@ struct Fold {
 
 // One chain word of the tile (lane 0): a push with its class, or a logic op
 // folded with the constants (Eqs. union / intersection / difference on 0/1).
-__device__ __forceinline__ void fold_word(Fold& f, int word, int cl, BinWarpBuf& B) {
+// uniq: no primitive is pushed twice by the chain, so a band push is a new leaf.
+__device__ __forceinline__ void fold_word(Fold& f, int word, int cl, BinWarpBuf& B, bool uniq) {
   const int code = (word >> 24) & 0xff, arg = word & 0xffffff;
   if (code == cPush) {
     int ent = 0;
     if (cl == cBND) {
       int slot = -1;
-      for (int l = 0; l < f.nleaf; ++l)
-        if (B.leaf[l] == arg) { slot = l; break; }
+      if (!uniq)
+        for (int l = 0; l < f.nleaf; ++l)
+          if (B.leaf[l] == arg) { slot = l; break; }
       if (slot < 0) {
         if (f.nleaf < kMaxLeaves) { B.leaf[f.nleaf] = (uint16_t)arg; slot = f.nleaf++; }
         else f.e |= eLeafOverflow;
@@ -1125,6 +1130,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(const Job* __restrict__ job
   extern __shared__ __align__(16) unsigned char smem[];
   int* schain = reinterpret_cast<int*>(smem);
   BinWarpBuf* wbuf = reinterpret_cast<BinWarpBuf*>(schain + kBinSeg);
+  int* stb = reinterpret_cast<int*>(wbuf + kBinWarps);  // cached primitive tile boxes
   __shared__ int wtot[kBinWarps];
   __shared__ int sband[kBinWarps];  // the block's band tiles
   __shared__ int sagg[4];           // band tiles, longest program, band cells, list base
@@ -1150,10 +1156,25 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(const Job* __restrict__ job
     if (bx0 == bx1) { by0 = ub0 % nty; by1 = ub1 % nty; }
   }
   if (tid < 4) sagg[tid] = 0;
+  // the first kBinTbCache primitives' tile boxes into shared memory (one per
+  // thread), testing them against the block's box on the way
+  const int nprims = J.g.nprims;
+  auto box_hits = [](const int* b, int x0, int x1, int y0, int y1, int z0, int z1) {
+    return x0 < b[1] && x1 >= b[0] && y0 < b[3] && y1 >= b[2] && z0 < b[5] && z1 >= b[4];
+  };
   bool hit = false;
-  for (int q = tid; q < J.g.nprims && !hit; q += kBinThreads)
+  if (tid < nprims && tid < kBinTbCache) {
+    int b[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      b[k] = __ldg(prims[tid].tb + k);
+      stb[6 * tid + k] = b[k];
+    }
+    hit = box_hits(b, bx0, bx1, by0, by1, bz0, bz1);
+  }
+  for (int q = tid + kBinTbCache; q < nprims && !hit; q += kBinThreads)
     hit = tb_hits(prims[q].tb, bx0, bx1, by0, by1, bz0, bz1);
-  const bool any = __syncthreads_or(hit);
+  const bool any = __syncthreads_or(hit);  // also publishes the cache
   const int u = ub0 + warp;
   const bool live = u < J.g.T;  // warp-uniform
   const int ty = u % nty, tx = (u / nty) % ntx, tz = u / (nty * ntx);
@@ -1171,14 +1192,17 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(const Job* __restrict__ job
   BinWarpBuf& B = wbuf[warp];
   Fold f{0, 0, 0, 0, 0, 0, 0};
   const int nchain = J.g.nchain;
+  auto hits = [&](int p, int x0, int x1, int y0, int y1, int z0, int z1) {
+    return p < kBinTbCache ? box_hits(stb + 6 * p, x0, x1, y0, y1, z0, z1)
+                           : tb_hits(prims[p].tb, x0, x1, y0, y1, z0, z1);
+  };
   auto misses_block = [&](int word) {
-    return ((word >> 24) & 0xff) == cPush &&
-           !tb_hits(prims[word & 0xffffff].tb, bx0, bx1, by0, by1, bz0, bz1);
+    return ((word >> 24) & 0xff) == cPush && !hits(word & 0xffffff, bx0, bx1, by0, by1, bz0, bz1);
   };
   auto misses_tile = [&](int word) {
-    return ((word >> 24) & 0xff) == cPush &&
-           !tb_hits(prims[word & 0xffffff].tb, tx, tx, ty, ty, tz, tz);
+    return ((word >> 24) & 0xff) == cPush && !hits(word & 0xffffff, tx, tx, ty, ty, tz, tz);
   };
+  const bool uniq = J.g.unique_push != 0;
   for (int s0 = 0; s0 < nchain; s0 += kBinSeg) {
     const int s1 = min(nchain, s0 + kBinSeg);
     // block pass, one word per thread and slab: the segment's words minus
@@ -1241,7 +1265,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(const Job* __restrict__ job
         }
         __syncwarp();
         if (lane == 0)
-          for (int j = 0; j < __popc(km); ++j) fold_word(f, B.word[j], B.cls[j], B);
+          for (int j = 0; j < __popc(km); ++j) fold_word(f, B.word[j], B.cls[j], B, uniq);
         __syncwarp();
       }
     }

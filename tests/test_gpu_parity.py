@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2311_05646_gb300 import inputs as I
+from paper_2311_05646_gb300.inputs import P
 
 from . import _gpu as H
 from .conftest import cuda_ok
@@ -107,6 +108,22 @@ def test_gradient_matches_oracle(ctx, oracle_mod, case):
 def test_tile_shapes_agree(ctx, oracle_mod, tile):
     desc = I.grating_3d(n=(150, 36, 60), teeth=8, pitch=600.0)
     d = _check_build(ctx, desc, oracle_mod, tile=tile)
+    _check_grad(ctx, desc, oracle_mod, d=d)
+
+
+@pytest.mark.parametrize("logic", ["product", "clamp"])
+def test_primitive_pushed_twice(ctx, oracle_mod, logic):
+    """A program that uses primitives more than once (a disc cut by a smaller
+    disc, the same disc intersected with a box, and the box again): the
+    binner's fold gives each repeated push the leaf it already has."""
+    D = I.Design((70, 50, 20), (40.0, 40.0, 40.0), ncomp=3, logic=logic)
+    a = D.circle(P(D.param(1400.0)), P(D.param(1000.0)), P(D.param(600.0)), sigma="sigmoid", kr=4.0)
+    b = D.box(x=(P(D.param(900.0)), P(D.param(1900.0))), y=(700.0, 1300.0), mode="sigma",
+              sigma="sigmoid", kr=4.0)
+    c = D.circle(1400.0, 1000.0, P(D.param(300.0)), sigma="sigmoid", kr=4.0)
+    D.set_program(("union", ("diff", a, c), ("intersect", b, a), b))
+    desc = D.to_desc()
+    d = _check_build(ctx, desc, oracle_mod)
     _check_grad(ctx, desc, oracle_mod, d=d)
 
 
