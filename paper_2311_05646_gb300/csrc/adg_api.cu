@@ -143,6 +143,7 @@ struct adg_ctx {
   Arena arenas[2];
   int next_arena = 0;
   cudaStream_t capture = nullptr;  // graphs are captured here, launched on the caller's stream
+  cudaStream_t upload = nullptr;   // designs' primitive records go to the device here
   struct Ticket { uint64_t id; cudaEvent_t ev; };
   std::vector<Ticket> tickets;
   uint64_t next_ticket = 1;
@@ -216,9 +217,16 @@ struct adg_design {
       *d_ref_qa = nullptr;
   float* d_actc = nullptr;
   double* d_ref_coeff = nullptr;
-  PrimRec* d_prims = nullptr;
-  double* d_auxd = nullptr;
-  float* d_auxf = nullptr;
+  // primitive records, two buffers (one per counter set, below): a binning's
+  // records are uploaded on the context's upload stream into the buffer of
+  // its set while kernels of the binning before still read the other one
+  PrimRec* d_prims = nullptr;  // 2 n_prims
+  double* d_auxd = nullptr;    // 2 auxd_stride
+  float* d_auxf = nullptr;     // 2 auxf_stride
+  size_t auxd_stride = 1, auxf_stride = 1;
+  void* h_pin[2] = {};             // pinned staging of each buffer: prims, auxd, auxf
+  cudaEvent_t up_done[2] = {};     // the last upload into buffer b
+  cudaEvent_t used[2] = {};        // after the last kernels that read buffer b
   TileProg* d_progs = nullptr;
   unsigned char* d_tclass = nullptr;
   int* d_list = nullptr;
@@ -260,6 +268,13 @@ struct adg_design {
   bool counters_dirty = false;
 };
 
+// Bytes of one record buffer: primitive records, FP64 and fp32 auxiliary
+// tables (the pinned staging lays them out in this order).
+size_t record_bytes(const adg_design* d) {
+  return sizeof(PrimRec) * d->n_prims + sizeof(double) * d->auxd_stride +
+         sizeof(float) * d->auxf_stride;
+}
+
 // After a call that had prepared a new binning failed before enqueueing all
 // of its work: the bins may not have been written, and the counter set the
 // design now points at may hold an older binning's counts.
@@ -286,9 +301,11 @@ extern "C" adg_status adg_ctx_create(int32_t device, adg_ctx** out) {
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e == cudaSuccess)
     e = lib_malloc((void**)&c->d_gtape, sizeof(float) * kTapeBlockFloats * c->gtape_blocks);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->upload, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     lib_free(c->d_err);
     lib_free(c->d_gtape);
+    if (c->upload) cudaStreamDestroy(c->upload);
     delete c;
     return fail(ADG_ECUDA, "adg_ctx_create: %s", cudaGetErrorString(e));
   }
@@ -310,6 +327,7 @@ extern "C" adg_status adg_ctx_destroy(adg_ctx* ctx) {
   }
   for (auto& t : ctx->tickets) cudaEventDestroy(t.ev);
   if (ctx->capture) cudaStreamDestroy(ctx->capture);
+  if (ctx->upload) cudaStreamDestroy(ctx->upload);
   lib_free(ctx->d_err);
   lib_free(ctx->d_gtape);
   lib_free(ctx->d_mesh);
@@ -321,6 +339,14 @@ extern "C" adg_status adg_ctx_destroy(adg_ctx* ctx) {
 namespace {
 
 void free_design(adg_design* d) {
+  for (int b = 0; b < 2; ++b) {
+    if (d->up_done[b]) {
+      cudaEventSynchronize(d->up_done[b]);  // no copy from the staging in flight
+      cudaEventDestroy(d->up_done[b]);
+    }
+    if (d->used[b]) cudaEventDestroy(d->used[b]);
+    lib_free_host(d->h_pin[b]);
+  }
   lib_free(d->d_chain);
   lib_free(d->d_act);
   lib_free(d->d_actc);
@@ -445,9 +471,16 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   if (e == cudaSuccess) e = upload(&d->d_ref_prim, d->ref_prim);
   if (e == cudaSuccess) e = upload(&d->d_ref_qa, d->ref_qa);
   if (e == cudaSuccess) e = upload(&d->d_ref_coeff, d->ref_coeff);
-  if (e == cudaSuccess) e = upload(&d->d_prims, d->h_prims);
-  if (e == cudaSuccess) e = upload(&d->d_auxd, d->h_auxd);
-  if (e == cudaSuccess) e = upload(&d->d_auxf, d->h_auxf);
+  d->auxd_stride = d->h_auxd.size();
+  d->auxf_stride = d->h_auxf.size();
+  if (e == cudaSuccess) e = lib_malloc((void**)&d->d_prims, 2 * sizeof(PrimRec) * d->n_prims);
+  if (e == cudaSuccess) e = lib_malloc((void**)&d->d_auxd, 2 * sizeof(double) * d->auxd_stride);
+  if (e == cudaSuccess) e = lib_malloc((void**)&d->d_auxf, 2 * sizeof(float) * d->auxf_stride);
+  for (int b = 0; b < 2; ++b) {
+    if (e == cudaSuccess) e = lib_malloc_host(&d->h_pin[b], record_bytes(d));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d->up_done[b], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d->used[b], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_progs, sizeof(TileProg) * (size_t)d->g.T);
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_tclass, (size_t)d->g.T);
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_list, sizeof(int) * (size_t)d->g.T);
@@ -512,17 +545,43 @@ adg_status ensure_records(adg_design* d, const double* h_params, cudaStream_t s,
     CU(cudaMemsetAsync(d->d_counters, 0, sizeof(int) * 8, s));  // both counter sets
     d->counters_dirty = false;
   }
-  CU(cudaMemcpyAsync(d->d_prims, d->h_prims.data(), sizeof(PrimRec) * d->n_prims,
-                     cudaMemcpyHostToDevice, s));
-  if (d->st.auxd_n)
-    CU(cudaMemcpyAsync(d->d_auxd, d->h_auxd.data(), sizeof(double) * d->st.auxd_n,
-                       cudaMemcpyHostToDevice, s));
-  if (d->st.auxf_n)
-    CU(cudaMemcpyAsync(d->d_auxf, d->h_auxf.data(), sizeof(float) * d->st.auxf_n,
-                       cudaMemcpyHostToDevice, s));
+  // this binning counts into the other set (cleared by the last one) and
+  // reads the records of the other buffer
+  const int b = d->gen ^ 1;
+  PrimRec* dp = d->d_prims + (size_t)b * d->n_prims;
+  double* dd = d->d_auxd + (size_t)b * d->auxd_stride;
+  float* df = d->d_auxf + (size_t)b * d->auxf_stride;
+  const size_t np = sizeof(PrimRec) * d->n_prims, nd = sizeof(double) * d->st.auxd_n,
+               nf = sizeof(float) * d->st.auxf_n;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CU(cudaStreamIsCapturing(s, &cap));
+  if (cap == cudaStreamCaptureStatusNone) {
+    // Off the caller's stream: the copy runs as soon as the kernels that read
+    // buffer b (two binnings ago) are done, usually long before the kernels
+    // before this call's binner finish, so no copy sits between them.
+    unsigned char* hp = static_cast<unsigned char*>(d->h_pin[b]);
+    CU(cudaEventSynchronize(d->up_done[b]));  // the staging's last copy has left it
+    memcpy(hp, d->h_prims.data(), np);
+    memcpy(hp + sizeof(PrimRec) * d->n_prims, d->h_auxd.data(), nd);
+    memcpy(hp + sizeof(PrimRec) * d->n_prims + sizeof(double) * d->auxd_stride, d->h_auxf.data(), nf);
+    cudaStream_t up = d->ctx->upload;
+    CU(cudaStreamWaitEvent(up, d->used[b], 0));
+    CU(cudaMemcpyAsync(dp, hp, np, cudaMemcpyHostToDevice, up));
+    if (nd)
+      CU(cudaMemcpyAsync(dd, hp + sizeof(PrimRec) * d->n_prims, nd, cudaMemcpyHostToDevice, up));
+    if (nf)
+      CU(cudaMemcpyAsync(df, hp + sizeof(PrimRec) * d->n_prims + sizeof(double) * d->auxd_stride,
+                         nf, cudaMemcpyHostToDevice, up));
+    CU(cudaEventRecord(d->up_done[b], up));
+    CU(cudaStreamWaitEvent(s, d->up_done[b], 0));
+  } else {  // captured into a graph: the copies on the caller's stream
+    CU(cudaMemcpyAsync(dp, d->h_prims.data(), np, cudaMemcpyHostToDevice, s));
+    if (nd) CU(cudaMemcpyAsync(dd, d->h_auxd.data(), nd, cudaMemcpyHostToDevice, s));
+    if (nf) CU(cudaMemcpyAsync(df, d->h_auxf.data(), nf, cudaMemcpyHostToDevice, s));
+  }
   d->last_params.assign(h_params, h_params + d->n_params);
   d->bins_valid = true;
-  d->gen ^= 1;  // this binning counts into the other set (cleared by the last one)
+  d->gen = b;
   *rebin = true;
   return ADG_OK;
 }
@@ -552,11 +611,11 @@ Job design_job(adg_design* d) {
   J.g = d->g;
   J.err = d->ctx ? d->ctx->d_err : nullptr;
   J.chain = d->d_chain;
-  J.prims = d->d_prims;
+  J.prims = d->d_prims + (size_t)d->gen * d->n_prims;
   J.act = d->d_act;
   J.actc = d->d_actc;
-  J.auxf = d->d_auxf;
-  J.auxd = d->d_auxd;
+  J.auxf = d->d_auxf + (size_t)d->gen * d->auxf_stride;
+  J.auxd = d->d_auxd + (size_t)d->gen * d->auxd_stride;
   J.ref_off = d->d_ref_off;
   J.ref_prim = d->d_ref_prim;
   J.ref_qa = d->d_ref_qa;
@@ -610,6 +669,9 @@ adg_status run_single(adg_ctx* ctx, adg_design* d, const double* h_params, float
   adg_status st = ensure_records(d, h_params, s, &rebin);
   if (st != ADG_OK) return st;
   st = run_single_enqueue(ctx, d, rebin, d_fill, d_eps, va, d_grad, s);
+  // the next upload into this call's record buffer waits for its kernels
+  const cudaError_t e = cudaEventRecord(d->used[d->gen], s);
+  if (st == ADG_OK && e != cudaSuccess) st = fail(ADG_ECUDA, "%s", cudaGetErrorString(e));
   if (st != ADG_OK && rebin) invalidate_bins(d);
   return st;
 }
@@ -1643,9 +1705,10 @@ extern "C" const char* adg_last_error(void) { return g_err; }
 size_t design_bytes(const adg_design* d) {
   auto vb = [](const auto& v) { return std::max<size_t>(v.size(), 1) * sizeof(v[0]); };
   size_t b = vb(d->chain) + vb(d->act) + vb(d->actc) + vb(d->ref_off) + vb(d->ref_prim) +
-             vb(d->ref_qa) + vb(d->ref_coeff) + vb(d->h_prims) + vb(d->h_auxd) + vb(d->h_auxf);
+             vb(d->ref_qa) + vb(d->ref_coeff) + 2 * record_bytes(d);
   const size_t T = (size_t)d->g.T;
-  b += T * (sizeof(TileProg) + 1 + sizeof(int)) + 16 * sizeof(int) + sizeof(Job);
+  b += T * (sizeof(TileProg) + 1 + sizeof(int)) + 20 * sizeof(int) +
+       sizeof(Job) * adg_design::kJobSlots;
   b += std::max(d->partial_cap, d->part_total) * sizeof(float);
   const size_t plane = (size_t)d->g.nx * d->g.ny * d->g.nz, ns = plane * d->g.C;
   if (d->d_dense_part)
