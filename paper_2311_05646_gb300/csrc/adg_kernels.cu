@@ -1561,6 +1561,12 @@ __device__ __forceinline__ int job_of(const int* spre, int njobs, int i) {
   return lo;
 }
 
+// Stores of the build's outputs (fill, eps), cache-streaming (evict first):
+// hundreds of MB written once, whose lines would otherwise crowd L2 and
+// drain to HBM under the next kernel's field loads.
+__device__ __forceinline__ void out_st(float4* p, float4 v) { __stcs(p, v); }
+__device__ __forceinline__ void out_st(float* p, float v) { __stcs(p, v); }
+
 // Streaming fill of the constant tiles of one group of kFillRows x-rows: fill
 // = 0 or 1, eps = eps_bg or eps_fg, 16-byte stores (a store instruction
 // covers 512 contiguous bytes); band tiles are left to the band evaluation.
@@ -1599,16 +1605,16 @@ __device__ __forceinline__ void fill_rows(const Job* __restrict__ jobs, int jb, 
           if (cls[u] == 2) continue;
           const int v = v0 + 32 * u;
           const float f = cls[u] ? 1.f : 0.f, e = cls[u] ? e1 : e0;
-          if (fill) f4[v] = make_float4(f, f, f, f);
-          e4[v] = make_float4(e, e, e, e);
+          if (fill) out_st(f4 + v, make_float4(f, f, f, f));
+          out_st(e4 + v, make_float4(e, e, e, e));
         }
       }
     } else {
       for (int i = lane; i < nx; i += 32) {
         const int cls = __ldg(tcl + (i >> lx));
         if (cls == 2) continue;
-        if (fill) fill[base + i] = cls ? 1.f : 0.f;
-        eps[base + i] = cls ? e1 : e0;
+        if (fill) out_st(fill + base + i, cls ? 1.f : 0.f);
+        out_st(eps + base + i, cls ? e1 : e0);
       }
     }
   }
@@ -1896,16 +1902,16 @@ __device__ __forceinline__ void build_band_tile(const Job* __restrict__ jobs, in
       const float e = g.eps_bg + g.deps * v;
       if (!uy && !uz) {  // uniform over the block
         const size_t o = (size_t)c * plane + ((size_t)(Z0 + z) * g.ny + (Y0 + y)) * g.nx + (X0 + x);
-        if (fill) fill[o] = v;
-        eps[o] = e;
+        if (fill) out_st(fill + o, v);
+        out_st(eps + o, e);
         return;
       }
       for (int zz = 0; zz < nz_r; ++zz)
         for (int yy = 0; yy < ny_r; ++yy) {
           const size_t o = (size_t)c * plane + ((size_t)(Z0 + z + zz) * g.ny + (Y0 + y + yy)) * g.nx +
                            (X0 + x);
-          if (fill) fill[o] = v;
-          eps[o] = e;
+          if (fill) out_st(fill + o, v);
+          out_st(eps + o, e);
         }
     };
     if (sdepth[0] <= kRegStack) {
