@@ -296,7 +296,8 @@ struct Job {
   int do_bin, do_build, do_grad;
 };
 
-constexpr int kFillRows = 8;  // x-rows per work unit of the streaming fill
+constexpr int kFillRows = 4;  // x-rows per work unit of the streaming fill (a shorter tail
+                              // than 8; 2 costs more in fetches than it saves)
 
 struct JobTotals {
   int njobs;
