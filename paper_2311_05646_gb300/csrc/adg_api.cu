@@ -225,8 +225,11 @@ struct adg_design {
   float* d_auxf = nullptr;     // 2 auxf_stride
   size_t auxd_stride = 1, auxf_stride = 1;
   void* h_pin[2] = {};             // pinned staging of each buffer: prims, auxd, auxf
-  cudaEvent_t up_done[2] = {};     // the last upload into buffer b
-  cudaEvent_t used[2] = {};        // after the last kernels that read buffer b
+  cudaEvent_t up_done[2] = {};     // the last copy out of staging b
+  cudaEvent_t used[2] = {};        // after the last kernels that read buffer b (recorded
+                                   // when a binning moves to the other buffer)
+  bool side_upload = false;        // copies on the upload stream (large grids), else
+                                   // on the caller's stream (launch-bound small ones)
   TileProg* d_progs = nullptr;
   unsigned char* d_tclass = nullptr;
   int* d_list = nullptr;
@@ -267,6 +270,12 @@ struct adg_design {
   // both sets are cleared before the next binning
   bool counters_dirty = false;
 };
+
+// Grids from this many samples up copy their records on the upload stream:
+// their kernels run long enough for the copy to hide behind the ones before.
+// Smaller grids are launch-bound: the fewer runtime calls of a copy on the
+// caller's stream win there.
+constexpr size_t kSideUploadSamples = (size_t)1 << 21;
 
 // Bytes of one record buffer: primitive records, FP64 and fp32 auxiliary
 // tables (the pinned staging lays them out in this order).
@@ -473,6 +482,7 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   if (e == cudaSuccess) e = upload(&d->d_ref_coeff, d->ref_coeff);
   d->auxd_stride = d->h_auxd.size();
   d->auxf_stride = d->h_auxf.size();
+  d->side_upload = (size_t)G.nx * G.ny * G.nz * G.ncomp >= kSideUploadSamples;
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_prims, 2 * sizeof(PrimRec) * d->n_prims);
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_auxd, 2 * sizeof(double) * d->auxd_stride);
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_auxf, 2 * sizeof(float) * d->auxf_stride);
@@ -554,27 +564,27 @@ adg_status ensure_records(adg_design* d, const double* h_params, cudaStream_t s,
   const size_t np = sizeof(PrimRec) * d->n_prims, nd = sizeof(double) * d->st.auxd_n,
                nf = sizeof(float) * d->st.auxf_n;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  CU(cudaStreamIsCapturing(s, &cap));
-  if (cap == cudaStreamCaptureStatusNone) {
-    // Off the caller's stream: the copy runs as soon as the kernels that read
-    // buffer b (two binnings ago) are done, usually long before the kernels
-    // before this call's binner finish, so no copy sits between them.
+  if (d->side_upload) CU(cudaStreamIsCapturing(s, &cap));
+  if (d->side_upload && cap == cudaStreamCaptureStatusNone) {
+    // Large grids: from pinned staging b (once its last copy has left it) on
+    // the upload stream, after the kernels that read buffer b (two binnings
+    // ago) -- usually long before the kernels ahead of this call's binner
+    // finish, so no copy sits between them.
     unsigned char* hp = static_cast<unsigned char*>(d->h_pin[b]);
-    CU(cudaEventSynchronize(d->up_done[b]));  // the staging's last copy has left it
+    const size_t od = sizeof(PrimRec) * d->n_prims, of = od + sizeof(double) * d->auxd_stride;
+    CU(cudaEventSynchronize(d->up_done[b]));
     memcpy(hp, d->h_prims.data(), np);
-    memcpy(hp + sizeof(PrimRec) * d->n_prims, d->h_auxd.data(), nd);
-    memcpy(hp + sizeof(PrimRec) * d->n_prims + sizeof(double) * d->auxd_stride, d->h_auxf.data(), nf);
+    memcpy(hp + od, d->h_auxd.data(), nd);
+    memcpy(hp + of, d->h_auxf.data(), nf);
     cudaStream_t up = d->ctx->upload;
+    CU(cudaEventRecord(d->used[d->gen], s));  // the binning being left: its kernels
     CU(cudaStreamWaitEvent(up, d->used[b], 0));
     CU(cudaMemcpyAsync(dp, hp, np, cudaMemcpyHostToDevice, up));
-    if (nd)
-      CU(cudaMemcpyAsync(dd, hp + sizeof(PrimRec) * d->n_prims, nd, cudaMemcpyHostToDevice, up));
-    if (nf)
-      CU(cudaMemcpyAsync(df, hp + sizeof(PrimRec) * d->n_prims + sizeof(double) * d->auxd_stride,
-                         nf, cudaMemcpyHostToDevice, up));
+    if (nd) CU(cudaMemcpyAsync(dd, hp + od, nd, cudaMemcpyHostToDevice, up));
+    if (nf) CU(cudaMemcpyAsync(df, hp + of, nf, cudaMemcpyHostToDevice, up));
     CU(cudaEventRecord(d->up_done[b], up));
     CU(cudaStreamWaitEvent(s, d->up_done[b], 0));
-  } else {  // captured into a graph: the copies on the caller's stream
+  } else {  // small (launch-bound) grids, or captured into a graph: on the caller's stream
     CU(cudaMemcpyAsync(dp, d->h_prims.data(), np, cudaMemcpyHostToDevice, s));
     if (nd) CU(cudaMemcpyAsync(dd, d->h_auxd.data(), nd, cudaMemcpyHostToDevice, s));
     if (nf) CU(cudaMemcpyAsync(df, d->h_auxf.data(), nf, cudaMemcpyHostToDevice, s));
@@ -669,9 +679,6 @@ adg_status run_single(adg_ctx* ctx, adg_design* d, const double* h_params, float
   adg_status st = ensure_records(d, h_params, s, &rebin);
   if (st != ADG_OK) return st;
   st = run_single_enqueue(ctx, d, rebin, d_fill, d_eps, va, d_grad, s);
-  // the next upload into this call's record buffer waits for its kernels
-  const cudaError_t e = cudaEventRecord(d->used[d->gen], s);
-  if (st == ADG_OK && e != cudaSuccess) st = fail(ADG_ECUDA, "%s", cudaGetErrorString(e));
   if (st != ADG_OK && rebin) invalidate_bins(d);
   return st;
 }
@@ -1443,6 +1450,9 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
       d->counters_dirty = false;
     }
     d->bins_valid = false;  // the batch re-bins this design with its own records
+    // the design's single-call kernels so far read record buffer gen: a later
+    // upload into it waits for them
+    CU(cudaEventRecord(d->used[d->gen], s));
     d->gen ^= 1;            // into the other counter set (cleared by the last binning)
     flipped.n = i + 1;
     if (items[i].ops & (ADG_BATCH_GRAD | ADG_BATCH_GRAD_REAL)) {
