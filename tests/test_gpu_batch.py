@@ -117,3 +117,44 @@ def test_batch_wait_is_bounded(ctx):
         assert e.status == adg.ADG_ETIMEOUT
     adg.adg_batch_wait(ctx, t, 60.0)
     assert adg.adg_batch_poll(ctx, t)
+
+
+def test_large_design_between_single_calls_and_batches(ctx):
+    """A grid large enough (3.6 M samples) that single calls copy their primitive
+    records on the context's upload stream into the record buffer the kernels
+    ahead are not reading, interleaved with batch submits that re-bin the
+    design with their own records, without synchronising in between: every
+    result equals that of a design used only by single calls, bit for bit."""
+    import torch
+    from paper_2311_05646_gb300 import adg
+    desc = I.grating_3d(n=(200, 100, 60), teeth=8, pitch=600.0)
+    mixed = adg.Design(ctx, desc)
+    plain = adg.Design(ctx, desc)
+    ef = torch.from_numpy(I.plane_wave_field(desc, 41)).cuda()
+    ea = torch.from_numpy(I.plane_wave_field(desc, 42)).cuda()
+    w = I.seeded_w(3, 43)
+    ps = [desc["params"] + 0.2 * k for k in range(6)]
+    outs, tickets = [], []
+    for k, p in enumerate(ps):
+        eps = torch.empty(mixed.shape, dtype=torch.float32, device="cuda")
+        g = torch.zeros(mixed.n_params, dtype=torch.float32, device="cuda")
+        if k % 3 == 1:
+            tickets.append(adg.adg_batch_submit(
+                ctx, [adg.BatchItem(mixed, p, eps=eps, efwd=ef, eadj=ea, w=w, grad=g)]))
+        else:
+            adg.adg_build_eps(mixed, p, eps)
+            adg.adg_grad(mixed, p, ef, ea, w, g)
+        outs.append((eps, g))
+    for t in tickets:
+        adg.adg_batch_wait(ctx, t, 60.0)
+    adg.adg_sync(ctx)
+    for p, (eps, g) in zip(ps, outs):
+        e2 = torch.empty_like(eps)
+        g2 = torch.zeros_like(g)
+        adg.adg_build_eps(plain, p, e2)
+        adg.adg_grad(plain, p, ef, ea, w, g2)
+        adg.adg_sync(ctx)
+        assert torch.equal(eps, e2)
+        assert torch.equal(g, g2)
+    mixed.close()
+    plain.close()
