@@ -83,3 +83,30 @@ def test_noalloc_gradient_of_polar_and_polygon_designs(case, oracle_mod):
         assert ok, ("vs adg_grad", err, bound)
         ok, err, bound = H.grad_ok(a, oracle_mod.grad(desc, ef, ea, w, params=p))
         assert ok, ("vs oracle", err, bound)
+
+
+@pytest.mark.parametrize("tile", [(32, 16, 4), (32, 8, 8)])
+def test_noalloc_gradient_at_2048_cell_tiles(tile, oracle_mod):
+    """The largest tile shapes (2048 cells, whose VJP blocks hold a longer
+    active-sample list) through the no-allocation entry point: against
+    adg_grad at the same tile and against the FP64 oracle."""
+    import torch
+
+    from paper_2311_05646_gb300 import adg
+
+    ctx = adg.Context(0)
+    desc = I.random_design(4107, n=(75, 53, 27), nprims=14)
+    design = adg.Design(ctx, desc, tile=tile)
+    ef, ea = I.plane_wave_field(desc, 51), I.plane_wave_field(desc, 52)
+    w = I.seeded_w(desc["grid"]["ncomp"], 53)
+    efd, ead = torch.from_numpy(ef).cuda(), torch.from_numpy(ea).cuda()
+    g_ref = torch.zeros(design.n_params, dtype=torch.float32, device="cuda")
+    adg.adg_grad(design, desc["params"], efd, ead, w, g_ref)
+    adg.adg_sync(ctx)
+    g_na = torch.full((design.n_params,), float("nan"), dtype=torch.float32, device="cuda")
+    adg.adg_grad_noalloc(desc, desc["params"], efd, ead, w, g_na, tile=tile)
+    a = g_na.cpu().numpy().astype(np.float64)
+    ok, err, bound = H.grad_ok(a, g_ref.cpu().numpy().astype(np.float64))
+    assert ok, ("vs adg_grad", err, bound)
+    ok, err, bound = H.grad_ok(a, oracle_mod.grad(desc, ef, ea, w))
+    assert ok, ("vs oracle", err, bound)
