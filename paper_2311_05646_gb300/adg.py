@@ -150,9 +150,21 @@ def adg_last_error() -> str:
     return lib().adg_last_error().decode()
 
 
-def _stream_ptr(stream):
+_RAW_STREAM = None  # torch's current-stream query (raw handle) for a device index
+
+
+def _stream_ptr(stream, device=None):
+    """The CUDA stream handle: the given stream, else torch's current stream on
+    `device` (the context's device)."""
+    global _RAW_STREAM
     if stream is None:
         import torch
+        if device is not None:
+            if _RAW_STREAM is None:
+                _RAW_STREAM = getattr(torch._C, "_cuda_getCurrentRawStream", False)
+            if _RAW_STREAM:
+                return ctypes.c_void_p(_RAW_STREAM(device))
+            return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
         return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     if hasattr(stream, "cuda_stream"):
         return ctypes.c_void_p(stream.cuda_stream)
@@ -251,7 +263,9 @@ class Design:
 
 
 def _params(design: Design, params):
-    p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    p = params
+    if not (isinstance(p, np.ndarray) and p.dtype == np.float64 and p.flags.c_contiguous):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
     if p.size != design.n_params:
         raise ValueError("expected %d parameters, got %d" % (design.n_params, p.size))
     return p
@@ -275,8 +289,8 @@ def adg_build_eps(design: Design, params, eps, fill=None, stream=None):
     if fill is not None:
         _check_cell_tensor(design, fill, "fill", torch.float32)
     _check(lib().adg_build_eps(design.ctx.handle, design.handle,
-                               p.ctypes.data_as(ctypes.c_void_p), _dptr(fill), _dptr(eps),
-                               _stream_ptr(stream)))
+                               ctypes.c_void_p(p.ctypes.data), _dptr(fill), _dptr(eps),
+                               _stream_ptr(stream, design.ctx.device)))
 
 
 def _grad_args(design: Design, efwd, eadj, w, grad):
@@ -286,14 +300,19 @@ def _grad_args(design: Design, efwd, eadj, w, grad):
     if grad.dtype != torch.float32 or grad.numel() != design.n_params or not grad.is_cuda:
         raise ValueError("grad must be a float32 CUDA tensor of n_params entries")
     C = design.ncomp
-    ef = (ctypes.c_void_p * 3)(*[efwd[c].data_ptr() if c < C else 0 for c in range(3)])
-    ea = (ctypes.c_void_p * 3)(*[eadj[c].data_ptr() if c < C else 0 for c in range(3)])
-    wc = np.asarray(w, dtype=np.complex128).reshape(-1)
-    if wc.size == 1:
-        wc = np.repeat(wc, C)
-    ww = np.zeros(6, dtype=np.float32)
-    ww[0:2 * C:2] = wc.real[:C]
-    ww[1:2 * C:2] = wc.imag[:C]
+    # component c of a contiguous [C][nz][ny][nx] complex64 tensor starts c planes in
+    bf, ba, pb = efwd.data_ptr(), eadj.data_ptr(), 8 * efwd.stride(0)
+    ef = (ctypes.c_void_p * 3)(*[bf + c * pb if c < C else 0 for c in range(3)])
+    ea = (ctypes.c_void_p * 3)(*[ba + c * pb if c < C else 0 for c in range(3)])
+    if isinstance(w, (int, float, complex)):
+        wl = [complex(w)] * C
+    else:
+        wl = [complex(v) for v in np.asarray(w).reshape(-1)]
+        if len(wl) == 1:
+            wl = wl * C
+    ww = (ctypes.c_float * 6)()
+    for c in range(C):
+        ww[2 * c], ww[2 * c + 1] = wl[c].real, wl[c].imag
     return ef, ea, ww
 
 
@@ -301,9 +320,8 @@ def adg_grad(design: Design, params, efwd, eadj, w, grad, stream=None):
     """grad <- Re sum w_c E_adj,c E_fwd,c d eps_c / d p (Eq. 1, eps term)."""
     p = _params(design, params)
     ef, ea, ww = _grad_args(design, efwd, eadj, w, grad)
-    _check(lib().adg_grad(design.ctx.handle, design.handle, p.ctypes.data_as(ctypes.c_void_p),
-                          ef, ea, ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad),
-                          _stream_ptr(stream)))
+    _check(lib().adg_grad(design.ctx.handle, design.handle, ctypes.c_void_p(p.ctypes.data),
+                          ef, ea, ww, _dptr(grad), _stream_ptr(stream, design.ctx.device)))
 
 
 def adg_grad_eh(d_eps: Design, d_mu: Design, params, efwd, eadj, w_e, hfwd, hadj, w_h, grad,
@@ -317,9 +335,8 @@ def adg_grad_eh(d_eps: Design, d_mu: Design, params, efwd, eadj, w_e, hfwd, hadj
     ef, ea, we = _grad_args(d_eps, efwd, eadj, w_e, grad)
     hf, ha, wh = _grad_args(d_mu, hfwd, hadj, w_h, grad)
     _check(lib().adg_grad_eh(d_eps.ctx.handle, d_eps.handle, d_mu.handle,
-                             p.ctypes.data_as(ctypes.c_void_p), ef, ea,
-                             we.ctypes.data_as(ctypes.c_void_p), hf, ha,
-                             wh.ctypes.data_as(ctypes.c_void_p), _dptr(grad), _stream_ptr(stream)))
+                             ctypes.c_void_p(p.ctypes.data), ef, ea, we, hf, ha, wh, _dptr(grad),
+                             _stream_ptr(stream, d_eps.ctx.device)))
 
 
 def _level_sets(sets, levels):
@@ -354,7 +371,7 @@ def adg_levels_grad(sets, levels, params, efwd, eadj, w, grad, stream=None):
     _check(lib().adg_levels_grad(sets[0].ctx.handle, handles, len(sets),
                                  lv.ctypes.data_as(ctypes.c_void_p),
                                  p.ctypes.data_as(ctypes.c_void_p), ef, ea,
-                                 ww.ctypes.data_as(ctypes.c_void_p), _dptr(grad),
+                                 ww, _dptr(grad),
                                  _stream_ptr(stream)))
 
 
@@ -364,7 +381,7 @@ def adg_grad_fd(design: Design, params, efwd, eadj, w, h, grad, stream=None):
     p = _params(design, params)
     ef, ea, ww = _grad_args(design, efwd, eadj, w, grad)
     _check(lib().adg_grad_fd(design.ctx.handle, design.handle, p.ctypes.data_as(ctypes.c_void_p),
-                             ef, ea, ww.ctypes.data_as(ctypes.c_void_p), float(h), _dptr(grad),
+                             ef, ea, ww, float(h), _dptr(grad),
                              _stream_ptr(stream)))
 
 
@@ -379,7 +396,7 @@ def adg_grad_dense(design: Design, params, efwd, eadj, w, fill, grad, gmat, stre
     if gmat.dtype != torch.float64 or gmat.numel() != 2 or not gmat.is_cuda or not gmat.is_contiguous():
         raise ValueError("gmat must be a contiguous float64 CUDA tensor of 2 entries")
     _check(lib().adg_grad_dense(design.ctx.handle, design.handle, p.ctypes.data_as(ctypes.c_void_p),
-                                ef, ea, ww.ctypes.data_as(ctypes.c_void_p), _dptr(fill),
+                                ef, ea, ww, _dptr(fill),
                                 _dptr(grad), _dptr(gmat), _stream_ptr(stream)))
 
 
