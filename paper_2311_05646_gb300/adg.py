@@ -579,15 +579,20 @@ def adg_batch_submit(ctx: Context, items, graph: bool = False, stream=None) -> i
             _check_cell_tensor(d, it.efwd, "efwd", torch.complex64)
             _check_cell_tensor(d, it.eadj, "eadj", torch.complex64)
             ops |= BATCH_GRAD
+            # component c of a contiguous [C][nz][ny][nx] complex64 tensor starts c planes in
+            bf, ba, pb = it.efwd.data_ptr(), it.eadj.data_ptr(), 8 * it.efwd.stride(0)
             for c in range(d.ncomp):
-                e.d_efwd[c] = it.efwd[c].data_ptr()
-                e.d_eadj[c] = it.eadj[c].data_ptr()
-            wc = np.asarray(it.w, dtype=np.complex128).reshape(-1)
-            if wc.size == 1:
-                wc = np.repeat(wc, d.ncomp)
+                e.d_efwd[c] = bf + c * pb
+                e.d_eadj[c] = ba + c * pb
+            if isinstance(it.w, (int, float, complex)):
+                wl = [complex(it.w)] * d.ncomp
+            else:
+                wl = [complex(v) for v in np.asarray(it.w).reshape(-1)]
+                if len(wl) == 1:
+                    wl = wl * d.ncomp
             for c in range(d.ncomp):
-                e.w[2 * c] = float(wc[c].real)
-                e.w[2 * c + 1] = float(wc[c].imag)
+                e.w[2 * c] = wl[c].real
+                e.w[2 * c + 1] = wl[c].imag
         elif it.G is not None:
             _check_cell_tensor(d, it.G, "G", torch.float32)
             ops |= BATCH_GRAD_REAL
@@ -597,32 +602,42 @@ def adg_batch_submit(ctx: Context, items, graph: bool = False, stream=None) -> i
                 raise ValueError("item %d: grad must be float32 with n_params entries" % k)
             e.d_grad = _dptr(it.grad)
         e.ops = ops
-    L = lib()
-    f = L.adg_batch_submit
-    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(adg_batch_item), ctypes.c_int32, ctypes.c_int32,
-                  ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
-    f.restype = ctypes.c_int
+    f = _batch_fns().adg_batch_submit
     t = ctypes.c_uint64(0)
-    _check(f(ctx.handle, arr, len(items), BATCH_GRAPH if graph else 0, _stream_ptr(stream),
-             ctypes.byref(t)))
+    _check(f(ctx.handle, arr, len(items), BATCH_GRAPH if graph else 0,
+             _stream_ptr(stream, ctx.device), ctypes.byref(t)))
     return int(t.value)
 
 
+_BATCH_L = None
+
+
+def _batch_fns():
+    """The library with the batch calls' signatures set (once)."""
+    global _BATCH_L
+    if _BATCH_L is None:
+        L = lib()
+        L.adg_batch_submit.argtypes = [ctypes.c_void_p, ctypes.POINTER(adg_batch_item),
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_uint64)]
+        L.adg_batch_submit.restype = ctypes.c_int
+        L.adg_batch_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)]
+        L.adg_batch_poll.restype = ctypes.c_int
+        L.adg_batch_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]
+        L.adg_batch_wait.restype = ctypes.c_int
+        _BATCH_L = L
+    return _BATCH_L
+
+
 def adg_batch_poll(ctx: Context, ticket: int) -> bool:
-    L = lib()
-    L.adg_batch_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)]
-    L.adg_batch_poll.restype = ctypes.c_int
     done = ctypes.c_int32(0)
-    _check(L.adg_batch_poll(ctx.handle, ticket, ctypes.byref(done)))
+    _check(_batch_fns().adg_batch_poll(ctx.handle, ticket, ctypes.byref(done)))
     return bool(done.value)
 
 
 def adg_batch_wait(ctx: Context, ticket: int, timeout_s: float = 60.0) -> None:
     """Wait for a batch; raises AdgError(ADG_ETIMEOUT) when it is still running."""
-    L = lib()
-    L.adg_batch_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]
-    L.adg_batch_wait.restype = ctypes.c_int
-    _check(L.adg_batch_wait(ctx.handle, ticket, int(timeout_s * 1e9)))
+    _check(_batch_fns().adg_batch_wait(ctx.handle, ticket, int(timeout_s * 1e9)))
 
 
 # ------------------------------------------------------- topology (Sec. 3.1) --
