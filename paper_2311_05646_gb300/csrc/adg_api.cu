@@ -143,6 +143,7 @@ struct adg_ctx {
   Arena arenas[2];
   int next_arena = 0;
   cudaStream_t capture = nullptr;  // graphs are captured here, launched on the caller's stream
+  cudaStream_t upload = nullptr;   // designs' primitive records go to the device here
   struct Ticket { uint64_t id; cudaEvent_t ev; };
   std::vector<Ticket> tickets;
   uint64_t next_ticket = 1;
@@ -217,16 +218,18 @@ struct adg_design {
   float* d_actc = nullptr;
   double* d_ref_coeff = nullptr;
   // primitive records, two buffers (one per counter set, below): a binning's
-  // records go into the buffer of its set while the kernel before still reads
-  // the other one
+  // records are uploaded on the context's upload stream into the buffer of
+  // its set while kernels of the binning before still read the other one
   PrimRec* d_prims = nullptr;  // 2 n_prims
   double* d_auxd = nullptr;    // 2 auxd_stride
   float* d_auxf = nullptr;     // 2 auxf_stride
   size_t auxd_stride = 1, auxf_stride = 1;
   void* h_pin[2] = {};             // pinned staging of each buffer: prims, auxd, auxf
   cudaEvent_t up_done[2] = {};     // the last copy out of staging b
-  bool side_upload = false;        // copied by the records kernel (large grids), else by
-                                   // a copy on the caller's stream (launch-bound small ones)
+  cudaEvent_t used[2] = {};        // after the last kernels that read buffer b (recorded
+                                   // when a binning moves to the other buffer)
+  bool side_upload = false;        // copies on the upload stream (large grids), else
+                                   // on the caller's stream (launch-bound small ones)
   TileProg* d_progs = nullptr;
   unsigned char* d_tclass = nullptr;
   int* d_list = nullptr;
@@ -268,9 +271,10 @@ struct adg_design {
   bool counters_dirty = false;
 };
 
-// Grids from this many samples up copy their records with the records kernel,
-// which overlaps the kernel before it.  Smaller grids are launch-bound: the
-// fewer runtime calls of a copy on the caller's stream win there.
+// Grids from this many samples up copy their records on the upload stream:
+// their kernels run long enough for the copy to hide behind the ones before.
+// Smaller grids are launch-bound: the fewer runtime calls of a copy on the
+// caller's stream win there.
 constexpr size_t kSideUploadSamples = (size_t)1 << 21;
 
 // Bytes of one record buffer: primitive records, FP64 and fp32 auxiliary
@@ -306,9 +310,11 @@ extern "C" adg_status adg_ctx_create(int32_t device, adg_ctx** out) {
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e == cudaSuccess)
     e = lib_malloc((void**)&c->d_gtape, sizeof(float) * kTapeBlockFloats * c->gtape_blocks);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->upload, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     lib_free(c->d_err);
     lib_free(c->d_gtape);
+    if (c->upload) cudaStreamDestroy(c->upload);
     delete c;
     return fail(ADG_ECUDA, "adg_ctx_create: %s", cudaGetErrorString(e));
   }
@@ -330,6 +336,7 @@ extern "C" adg_status adg_ctx_destroy(adg_ctx* ctx) {
   }
   for (auto& t : ctx->tickets) cudaEventDestroy(t.ev);
   if (ctx->capture) cudaStreamDestroy(ctx->capture);
+  if (ctx->upload) cudaStreamDestroy(ctx->upload);
   lib_free(ctx->d_err);
   lib_free(ctx->d_gtape);
   lib_free(ctx->d_mesh);
@@ -346,6 +353,7 @@ void free_design(adg_design* d) {
       cudaEventSynchronize(d->up_done[b]);  // no copy from the staging in flight
       cudaEventDestroy(d->up_done[b]);
     }
+    if (d->used[b]) cudaEventDestroy(d->used[b]);
     lib_free_host(d->h_pin[b]);
   }
   lib_free(d->d_chain);
@@ -481,6 +489,7 @@ extern "C" adg_status adg_design_create(adg_ctx* ctx, const adg_design_desc* D,
   for (int b = 0; b < 2; ++b) {
     if (e == cudaSuccess) e = lib_malloc_host(&d->h_pin[b], record_bytes(d));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d->up_done[b], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d->used[b], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_progs, sizeof(TileProg) * (size_t)d->g.T);
   if (e == cudaSuccess) e = lib_malloc((void**)&d->d_tclass, (size_t)d->g.T);
@@ -557,29 +566,24 @@ adg_status ensure_records(adg_design* d, const double* h_params, cudaStream_t s,
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (d->side_upload) CU(cudaStreamIsCapturing(s, &cap));
   if (d->side_upload && cap == cudaStreamCaptureStatusNone) {
-    // Large grids: from pinned staging b (once the last copy out of it has
-    // run) by a small kernel that overlaps the kernel before it on the stream
-    // (programmatic dependent launch): that kernel reads the other buffer, and
-    // the binner after the copy waits for it, so no copy sits between the
-    // gradient's finalize and the next binner.
+    // Large grids: from pinned staging b (once its last copy has left it) on
+    // the upload stream, after the kernels that read buffer b (two binnings
+    // ago) -- usually long before the kernels ahead of this call's binner
+    // finish, so no copy sits between them.
     unsigned char* hp = static_cast<unsigned char*>(d->h_pin[b]);
     const size_t od = sizeof(PrimRec) * d->n_prims, of = od + sizeof(double) * d->auxd_stride;
     CU(cudaEventSynchronize(d->up_done[b]));
     memcpy(hp, d->h_prims.data(), np);
     memcpy(hp + od, d->h_auxd.data(), nd);
     memcpy(hp + of, d->h_auxf.data(), nf);
-    RecCopy c{};
-    c.src[0] = reinterpret_cast<const uint32_t*>(hp);
-    c.dst[0] = reinterpret_cast<uint32_t*>(dp);
-    c.n[0] = (int)(np / 4);
-    c.src[1] = reinterpret_cast<const uint32_t*>(hp + od);
-    c.dst[1] = reinterpret_cast<uint32_t*>(dd);
-    c.n[1] = (int)(nd / 4);
-    c.src[2] = reinterpret_cast<const uint32_t*>(hp + of);
-    c.dst[2] = reinterpret_cast<uint32_t*>(df);
-    c.n[2] = (int)(nf / 4);
-    CU(launch_records(c, !d->ctx->prof, s));
-    CU(cudaEventRecord(d->up_done[b], s));
+    cudaStream_t up = d->ctx->upload;
+    CU(cudaEventRecord(d->used[d->gen], s));  // the binning being left: its kernels
+    CU(cudaStreamWaitEvent(up, d->used[b], 0));
+    CU(cudaMemcpyAsync(dp, hp, np, cudaMemcpyHostToDevice, up));
+    if (nd) CU(cudaMemcpyAsync(dd, hp + od, nd, cudaMemcpyHostToDevice, up));
+    if (nf) CU(cudaMemcpyAsync(df, hp + of, nf, cudaMemcpyHostToDevice, up));
+    CU(cudaEventRecord(d->up_done[b], up));
+    CU(cudaStreamWaitEvent(s, d->up_done[b], 0));
   } else {  // small (launch-bound) grids, or captured into a graph: on the caller's stream
     CU(cudaMemcpyAsync(dp, d->h_prims.data(), np, cudaMemcpyHostToDevice, s));
     if (nd) CU(cudaMemcpyAsync(dd, d->h_auxd.data(), nd, cudaMemcpyHostToDevice, s));
@@ -1446,6 +1450,9 @@ extern "C" adg_status adg_batch_submit(adg_ctx* ctx, const adg_batch_item* items
       d->counters_dirty = false;
     }
     d->bins_valid = false;  // the batch re-bins this design with its own records
+    // the design's single-call kernels so far read record buffer gen: a later
+    // upload into it waits for them
+    CU(cudaEventRecord(d->used[d->gen], s));
     d->gen ^= 1;            // into the other counter set (cleared by the last binning)
     flipped.n = i + 1;
     if (items[i].ops & (ADG_BATCH_GRAD | ADG_BATCH_GRAD_REAL)) {

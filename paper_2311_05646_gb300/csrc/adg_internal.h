@@ -321,17 +321,6 @@ constexpr int kMaxJobs = 1024;  // jobs in one table (one batch)
 constexpr int kMaxFillWarps = 2;
 
 cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s);
-// A binning's primitive records from pinned host staging (read by the device
-// through the unified address space) into their device buffers: n[k] 32-bit
-// words of src[k] to dst[k].  With pdl, launched to overlap the kernel before
-// it on the stream, which must not read the buffers it writes; it waits for
-// that kernel before it ends.
-struct RecCopy {
-  const uint32_t* src[3];
-  uint32_t* dst[3];
-  int n[3];
-};
-cudaError_t launch_records(const RecCopy& c, bool pdl, cudaStream_t s);
 cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s);
 // gtape: kTapeBlockFloats floats per block for gtape_blocks blocks; the grid
 // never exceeds gtape_blocks.

@@ -990,10 +990,10 @@ __device__ __forceinline__ int job_by_param(const Job* jobs, int n, int idx) {
   return lo;
 }
 
-// Programmatic dependent launch: the binner, the build, the VJP and the
-// finalize may be launched to overlap the tail of the kernel before them on
-// the stream (the launch, block scheduling and a prologue that reads only
-// tables uploaded before that kernel).  They wait here for it to complete, and for its
+// Programmatic dependent launch: the build, the VJP and the finalize may be
+// launched to overlap the tail of the kernel before them on the stream (the
+// launch, block scheduling and a prologue that reads only tables uploaded
+// before that kernel).  They wait here for it to complete, and for its
 // memory to be visible, before reading anything it may have written; a
 // kernel launched without the attribute returns from this at once.
 __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -1131,7 +1131,6 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(const Job* __restrict__ job
   int* schain = reinterpret_cast<int*>(smem);
   BinWarpBuf* wbuf = reinterpret_cast<BinWarpBuf*>(schain + kBinSeg);
   int* stb = reinterpret_cast<int*>(wbuf + kBinWarps);  // cached primitive tile boxes
-  wait_prior_grid();  // the records kernel before it (and so the kernel before that)
   __shared__ int wtot[kBinWarps];
   __shared__ int sband[kBinWarps];  // the block's band tiles
   __shared__ int sagg[4];           // band tiles, longest program, band cells, list base
@@ -2892,15 +2891,6 @@ __global__ void __launch_bounds__(256) k_dense_final(DenseArgs a) {
 // belongs to exactly one parameter, so the block that sums a row zeroes it,
 // and the first block of a job moves the active-sample count to
 // counters_last.
-// Copy of a binning's primitive records (see launch_records); the wait at the
-// end makes this kernel's completion imply the previous kernel's.
-__global__ void __launch_bounds__(256) k_records(RecCopy c) {
-  for (int k = 0; k < 3; ++k)
-    for (int i = blockIdx.x * 256 + (int)threadIdx.x; i < c.n[k]; i += (int)gridDim.x * 256)
-      c.dst[k][i] = c.src[k][i];
-  wait_prior_grid();
-}
-
 __global__ void __launch_bounds__(128) k_finalize(const Job* __restrict__ jobs, int njobs, int nparams) {
   __shared__ double wsum[4];
   const int wid = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -3002,6 +2992,11 @@ int vjp_blocks_per_sm(int njobs, bool polar, int cells) {
   return r;
 }
 
+cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s) {
+  if (t.tiles_padded <= 0) return cudaSuccess;
+  k_bin<<<t.tiles_padded / kBinWarps, kBinThreads, kBinSmem, s>>>(jobs, t.njobs, err);
+  return cudaGetLastError();
+}
 
 // A launch, with programmatic stream serialisation when pdl is set (the
 // kernel then starts as the one before it drains; see wait_prior_grid).
@@ -3019,18 +3014,6 @@ cudaError_t launch_k(bool pdl, void (*k)(P...), int grid, int block, size_t smem
   cfg.attrs = pdl ? at : nullptr;
   cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, k, args...);
-}
-
-cudaError_t launch_bin(const Job* jobs, const JobTotals& t, int* err, cudaStream_t s) {
-  if (t.tiles_padded <= 0) return cudaSuccess;
-  return launch_k(t.pdl != 0, k_bin, t.tiles_padded / kBinWarps, kBinThreads, kBinSmem, s, jobs,
-                  t.njobs, err);
-}
-
-cudaError_t launch_records(const RecCopy& c, bool pdl, cudaStream_t s) {
-  const int words = std::max(c.n[0], std::max(c.n[1], c.n[2]));
-  const int grid = std::min(std::max((words + 255) / 256, 1), 64);
-  return launch_k(pdl, k_records, grid, 256, 0, s, c);
 }
 
 cudaError_t launch_build(const Job* jobs, const JobTotals& t, int sms, cudaStream_t s) {
