@@ -324,6 +324,33 @@ def test_degenerate_designs(ctx, oracle_mod):
     _check_grad(ctx, desc, oracle_mod)
 
 
+def _degenerate_geometry(logic):
+    """Parameterised shapes at the edges of their definitions: a box that its
+    parameters turn inside out (x1 < x0: empty, zero gradient), edges exactly
+    on cell faces, two boxes sharing one edge parameter, a circle of radius 0
+    and one of negative radius, and a triangle a few cells across."""
+    D = I.Design((48, 40, 6), (10.0, 10.0, 10.0), ncomp=3, eps_bg=1.0, eps_fg=3.0, logic=logic)
+    inv = D.box(x=(P(D.param(260.0)), P(D.param(200.0))), y=(50.0, 300.0))
+    face = D.box(x=(P(D.param(100.0)), P(D.param(150.0))), y=(P(D.param(40.0)), 90.0))
+    e = D.param(330.0)
+    b1 = D.box(x=(300.0, P(e)), y=(200.0, 300.0))
+    b2 = D.box(x=(P(e), 360.0), y=(200.0, 300.0))
+    c0 = D.circle(150.0, 300.0, P(D.param(0.0)), sigma="sigmoid", kr=4.0)
+    cn = D.circle(250.0, 320.0, P(D.param(-20.0)), sigma="sigmoid", kr=4.0)
+    tri = D.polygon([(P(D.param(400.0)), 100.0), (420.0, 100.0), (410.0, P(D.param(115.0)))],
+                    sigma="sigmoid", kr=4.0)
+    D.set_program(("union", inv, face, b1, b2, c0, cn, tri))
+    return D.to_desc()
+
+
+@pytest.mark.parametrize("logic,tile", [("product", None), ("clamp", None), ("product", (32, 16, 4))])
+def test_degenerate_geometry_matches_the_oracle(ctx, oracle_mod, logic, tile):
+    desc = _degenerate_geometry(logic)
+    d = _check_build(ctx, desc, oracle_mod, tile=tile)
+    _, g = _check_grad(ctx, desc, oracle_mod, d=d)
+    assert np.all(g[:2] == 0.0)  # the inverted box drives nothing
+
+
 def test_invalid_descriptions_rejected(ctx):
     from paper_2311_05646_gb300 import adg
     desc = I.grating_2d()
