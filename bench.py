@@ -163,18 +163,90 @@ def _sample_text(desc, box):
 
 def oracle_sample(desc, ef, ea, w, target_s=15.0):
     """Time the oracle (fill + gradient, as it stands) on a block through the
-    slab, about `target_s` of CPU work.  Returns (cells/s, cores, description)."""
+    slab, about `target_s` of CPU work.  Returns (cells/s, cores, description,
+    timings: the box, the fill's and the gradient's seconds, the fill)."""
     from oracle import oracle as O
     nx = desc["grid"]["n"][0]
     box = _oracle_box(desc, ef, ea, w, target_s)
     sub, efs, eas = _sample(desc, ef, ea, box)
     t0 = time.perf_counter()
-    O.fill(sub)
+    f = O.fill(sub)
+    t1 = time.perf_counter()
     O.grad(sub, efs, eas, w)
     dt = time.perf_counter() - t0
     cells = nx * box[1] * box[3]
+    timings = {"box": box, "fill_s": t1 - t0, "grad_s": dt - (t1 - t0), "fill": f}
     return cells / dt, O.num_threads(), "%s; one oracle fill + one oracle gradient, %.1f s" % (
-        _sample_text(desc, box), dt)
+        _sample_text(desc, box), dt), timings
+
+
+def oracle_methods(desc, ef, ea, w, timings, gpu_value, target_1core_s=5.0):
+    """The oracle's two host methods on this workload, in cells/s of the whole
+    step (cells of the sample over its time):
+    - analytic: the VJP of Sec. 3 (one eps evaluation and one reverse sweep),
+      from the timed sample on all cores, and on one core on a smaller block;
+    - fd: the finite-difference baseline of Sec. 2 -- n + 1 eps builds and n
+      multiply-reduces for n parameters -- extrapolated from the timed build
+      and from four multiply-reduces timed on the sample (z = Re(w E_adj E_fwd)
+      formed once, then one dot product with a fill difference per parameter).
+    analytic_over_fd is the ratio of the two on the same host (the comparison
+    of Secs. 6.1 and 6.3); the GPU's speed-up over each is value / method."""
+    import numpy as np
+    from oracle import oracle as O
+    nx, ny, nz = desc["grid"]["n"]
+    k0, nzs, j0, nys = timings["box"]
+    cells = nx * nzs * nys
+    t_fill, t_grad = timings["fill_s"], timings["grad_s"]
+    n = len(desc["params"])
+    analytic = cells / (t_fill + t_grad)
+    # FD's multiply-reduce on the sample's arrays
+    _, efs, eas = _sample(desc, ef, ea, timings["box"])
+    f = np.asarray(timings["fill"], dtype=np.float64)
+    wv = np.asarray(w, dtype=np.complex128).reshape(-1, 1, 1, 1)
+    t0 = time.perf_counter()
+    z = np.real(wv * eas.astype(np.complex128) * efs.astype(np.complex128))
+    t_z = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for _ in range(4):
+        float(np.vdot(z.ravel(), f.ravel()))
+    t_dot = (time.perf_counter() - t0) / 4
+    t_fd = t_z + (n + 1) * t_fill + n * t_dot
+    # the analytic method on one core: one z-plane through the slab, rows
+    # sized from a short probe to about target_1core_s
+    threads = O.num_threads()
+    O.set_threads(1)
+    try:
+        kc = k0 + nzs // 2
+        probe_rows = min(ny, 8)
+        jp = (ny - probe_rows) // 2
+        sub, es, as_ = _sample(desc, ef, ea, (kc, 1, jp, probe_rows))
+        t0 = time.perf_counter()
+        O.fill(sub)
+        O.grad(sub, es, as_, w)
+        tp = max(time.perf_counter() - t0, 1e-3)
+        rows = int(max(1, min(ny, probe_rows * target_1core_s / tp)))
+        j1 = (ny - rows) // 2
+        sub, es, as_ = _sample(desc, ef, ea, (kc, 1, j1, rows))
+        t0 = time.perf_counter()
+        O.fill(sub)
+        O.grad(sub, es, as_, w)
+        t1c = time.perf_counter() - t0
+    finally:
+        O.set_threads(threads)
+    one_core = nx * rows / t1c
+    return {
+        "unit": "cells/s", "params": n,
+        "analytic_all_cores": {"value": analytic, "cores": threads,
+                               "sample": _sample_text(desc, timings["box"])},
+        "analytic_one_core": {"value": one_core, "cores": 1,
+                              "sample": _sample_text(desc, (kc, 1, j1, rows))},
+        "fd_all_cores": {"value": cells / t_fd, "cores": threads,
+                         "how": "(n + 1) timed oracle fills + n dot products of z with a fill "
+                                "difference, extrapolated from one fill and four dot products "
+                                "on the sample"},
+        "analytic_over_fd": t_fd / (t_fill + t_grad),  # the paper's AD-vs-FD comparison, one host
+        "gpu_over_analytic": gpu_value / analytic, "gpu_over_analytic_one_core": gpu_value / one_core,
+        "gpu_over_fd": gpu_value / (cells / t_fd)}
 
 
 def grid_of(args):
@@ -660,9 +732,11 @@ def run_adg(args):
         systems["serve"] = measure_serve(ctx, device=local)
 
     cpu = None
+    methods = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample = oracle_sample(desc, ef_h, ea_h, w)
+        v, cores, sample, timings = oracle_sample(desc, ef_h, ea_h, w)
         cpu = {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": sample}
+        methods = oracle_methods(desc, ef_h, ea_h, w, timings, value)
 
     if rank == 0:
         line = {
@@ -683,7 +757,8 @@ def run_adg(args):
                        "l2": "inputs larger than L2 (fields 691 MB + outputs 346 MB per step)"},
             "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
             "gpu_launches": launches,
-            "cpu_baseline": cpu, "e2e": e2e, "dense_vjp": dense, "topology": topo,
+            "cpu_baseline": cpu, "oracle_methods": methods, "e2e": e2e, "dense_vjp": dense,
+            "topology": topo,
             "fd_vs_ad": fdc, "levels": levels, "prop2_mesher": mesh,
             "batch": systems.get("batch"), "serve": systems.get("serve"),
             "te2d": systems.get("te2d"), "taper_autograd": systems.get("taper_autograd"),

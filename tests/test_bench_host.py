@@ -43,3 +43,25 @@ def test_small_grid_inputs_have_the_grating_shape():
     assert tuple(desc["grid"]["n"]) == (64, 40, 24)
     assert ef.shape == ea.shape == (3, 24, 40, 64)
     assert ef.dtype.name == "complex64" and len(w) == 3
+
+
+def test_oracle_methods_on_a_small_grating():
+    """The host baselines of the bench line: the analytic VJP on all cores and
+    on one core, and the finite-difference method extrapolated to all the
+    design's parameters -- which needs n + 1 eps builds and so is slower than
+    the analytic one; the thread count is restored afterwards."""
+    from oracle import oracle as O
+    desc, ef, ea, w = bench.make_inputs((64, 40, 24))
+    threads = O.num_threads()
+    v, cores, sample, t = bench.oracle_sample(desc, ef, ea, w, target_s=0.2)
+    assert v > 0 and cores == threads and t["fill_s"] > 0 and t["grad_s"] > 0
+    m = bench.oracle_methods(desc, ef, ea, w, t, gpu_value=1e9, target_1core_s=0.2)
+    assert O.num_threads() == threads
+    assert m["params"] == len(desc["params"]) == 120
+    for k in ("analytic_all_cores", "analytic_one_core", "fd_all_cores"):
+        assert m[k]["value"] > 0, k
+    assert m["analytic_one_core"]["cores"] == 1
+    assert m["fd_all_cores"]["value"] < m["analytic_all_cores"]["value"] / 10
+    assert abs(m["gpu_over_analytic"] * m["analytic_all_cores"]["value"] / 1e9 - 1) < 1e-9
+    assert abs(m["gpu_over_fd"] * m["fd_all_cores"]["value"] / 1e9 - 1) < 1e-9
+    assert m["analytic_over_fd"] > 10
