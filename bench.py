@@ -211,35 +211,34 @@ def oracle_methods(desc, ef, ea, w, timings, gpu_value, target_1core_s=5.0):
         float(np.vdot(z.ravel(), f.ravel()))
     t_dot = (time.perf_counter() - t0) / 4
     t_fd = t_z + (n + 1) * t_fill + n * t_dot
-    # the analytic method on one core: one z-plane through the slab, rows
-    # sized from a short probe to about target_1core_s
+    # the analytic method on one core: the same z-planes as the sample above
+    # (the same mix of slab and cladding cells), fewer y-rows, sized from a
+    # one-row probe to about target_1core_s
     threads = O.num_threads()
     O.set_threads(1)
     try:
-        kc = k0 + nzs // 2
-        probe_rows = min(ny, 8)
-        jp = (ny - probe_rows) // 2
-        sub, es, as_ = _sample(desc, ef, ea, (kc, 1, jp, probe_rows))
+        jp = j0 + nys // 2
+        sub, es, as_ = _sample(desc, ef, ea, (k0, nzs, jp, 1))
         t0 = time.perf_counter()
         O.fill(sub)
         O.grad(sub, es, as_, w)
         tp = max(time.perf_counter() - t0, 1e-3)
-        rows = int(max(1, min(ny, probe_rows * target_1core_s / tp)))
-        j1 = (ny - rows) // 2
-        sub, es, as_ = _sample(desc, ef, ea, (kc, 1, j1, rows))
+        rows = int(max(1, min(nys, target_1core_s / tp)))
+        j1 = j0 + (nys - rows) // 2
+        box1 = (k0, nzs, j1, rows)
+        sub, es, as_ = _sample(desc, ef, ea, box1)
         t0 = time.perf_counter()
         O.fill(sub)
         O.grad(sub, es, as_, w)
         t1c = time.perf_counter() - t0
     finally:
         O.set_threads(threads)
-    one_core = nx * rows / t1c
+    one_core = nx * nzs * rows / t1c
     return {
         "unit": "cells/s", "params": n,
         "analytic_all_cores": {"value": analytic, "cores": threads,
                                "sample": _sample_text(desc, timings["box"])},
-        "analytic_one_core": {"value": one_core, "cores": 1,
-                              "sample": _sample_text(desc, (kc, 1, j1, rows))},
+        "analytic_one_core": {"value": one_core, "cores": 1, "sample": _sample_text(desc, box1)},
         "fd_all_cores": {"value": cells / t_fd, "cores": threads,
                          "how": "(n + 1) timed oracle fills + n dot products of z with a fill "
                                 "difference, extrapolated from one fill and four dot products "
